@@ -1,0 +1,429 @@
+"""FP64 CPU oracle for the PDHG hot path.
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product imports this module: only the
+tests, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl
+reference`` legs of ``bench.py`` may import or run it. It shares no code with
+the CUDA path; the only common input is the seeded generator, which holds no
+step of the method.
+
+What it computes, with the passage each part follows
+-----------------------------------------------------
+* The LP pair ``min c^T x, Ax = b, x >= 0`` / ``max b^T y, A^T y + z = c,
+  z >= 0`` and the residuals ``r_P = b - A x``, ``r_D = A^T y + z - c``
+  (Section 2, "Background"); optimality = zero residuals, ``x, z >= 0`` and zero
+  gap ``c^T x - b^T y`` (equivalently ``x^T z = 0``) (Section 2).
+* The relative termination test on 2-norms, ``||r_P|| <= eps (1 + ||b||)``,
+  ``||r_D|| <= eps (1 + ||c||)``, ``|c^T x - b^T y| <= eps (1 + |c^T x| + |b^T y|)``
+  (Section 2). ``rel_kkt`` is the largest of the three ratios; it is the
+  "maxresid" that drives the snapshot schedule of Algorithm 1 (Section 3.1).
+* The PDHG iteration itself. The paper only says that its PDHG follows the
+  PDLP / cuPDLP+ line of work (Section 1, Section 4.1) and gives no formula, so
+  the iteration is the standard PDLP-style one, stated here in the notation of
+  the paper's LP:
+
+    x'   = max(0, x - tau (c - A^T y))
+    xbar = 2 x' - x
+    y'   = y + sigma (b - A xbar)
+
+  on the diagonally scaled problem ``Ahat = D_r A D_c``, ``bhat = D_r b``,
+  ``chat = D_c c`` (Ruiz equilibration followed by Pock-Chambolle scaling),
+  with ``tau = eta / omega``, ``sigma = eta * omega``, ``eta = 0.9 / ||Ahat||_2``
+  (power iteration), primal weight ``omega``, uniform averages of the iterates
+  since the last restart, and KKT-error adaptive restarts. Every choice the
+  paper leaves open is a documented reading (see ``Options``).
+* Algorithm 1's snapshot schedule: a snapshot of the current solution each time
+  ``rel_kkt`` falls to ``eps_target``, after which ``eps_target`` shrinks by
+  ``eps_factor`` (0.1 in the paper).
+
+Pins (see the tests): vertex enumeration on tiny LPs, the generator's known
+optimum, the fixed-point property of the PDHG map at an optimal pair, a
+hand-computed step and KKT on a 2x3 LP, Ruiz/Pock-Chambolle invariants, power
+iteration against a dense SVD, and an exact replay of the restart rules on
+hand-made KKT sequences.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+# restart kinds recorded in the trace
+NO_RESTART, RESTART_TO_CURRENT, RESTART_TO_AVERAGE = 0, 1, 2
+
+
+@dataclasses.dataclass
+class Options:
+    """Knobs of the method. Defaults are the large-LP configuration.
+
+    Readings of points the paper leaves open:
+      * ``ruiz_iters``/``pock_chambolle``: 10 Ruiz passes then one
+        Pock-Chambolle pass with alpha = 1.
+      * ``power_iters``: a fixed number of power iterations on Ahat^T Ahat,
+        started from the all-ones vector, so that every implementation computes
+        the same estimate.
+      * ``step_factor``: eta = step_factor / ||Ahat||_2.
+      * ``restarts``/``primal_weight`` off gives plain fixed-step PDHG with
+        omega = 1 (the tiny-LP configuration).
+      * restart thresholds (beta_suff, beta_nec, beta_art) and the primal-weight
+        smoothing theta follow PDLP's published defaults.
+    """
+
+    ruiz_iters: int = 10
+    pock_chambolle: bool = True
+    pc_alpha: float = 1.0
+    power_iters: int = 100
+    step_factor: float = 0.9
+    restarts: bool = True
+    primal_weight: bool = True
+    eval_every: int = 64
+    beta_suff: float = 0.2
+    beta_nec: float = 0.8
+    beta_art: float = 0.36
+    theta: float = 0.5
+    eps_cross: float = 0.0  # 0 disables Algorithm 1's snapshot schedule
+    eps_factor: float = 0.1
+    snapshot_every: int = 0
+
+
+def csr_matrix(m, n, row_ptr, col_idx, val) -> sp.csr_matrix:
+    return sp.csr_matrix((np.asarray(val, dtype=np.float64), np.asarray(col_idx), np.asarray(row_ptr)), shape=(m, n))
+
+
+# ---------------------------------------------------------------------------
+# Section 2: residuals, optimality measures and the relative termination test
+# ---------------------------------------------------------------------------
+
+def dual_slack(A: sp.csr_matrix, c: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """z for a dual estimate y: the smallest z >= 0 with A^T y + z - c as small as
+    possible, z = max(0, c - A^T y). (Section 2 names (x, y, z) but gives no rule
+    for z; this is the reading used throughout.)"""
+    return np.maximum(0.0, c - A.T @ y)
+
+
+def kkt(A: sp.csr_matrix, b: np.ndarray, c: np.ndarray, x: np.ndarray, y: np.ndarray,
+        z: np.ndarray | None = None) -> dict:
+    """All optimality measures of a candidate (x, y, z) on the problem as given.
+
+    r_P = b - A x and r_D = A^T y + z - c (Section 2); the three relative ratios
+    of the termination test (Section 2) and their maximum, rel_kkt."""
+    if z is None:
+        z = dual_slack(A, c, y)
+    r_p = b - A @ x
+    r_d = A.T @ y + z - c
+    cx = float(c @ x)
+    by = float(b @ y)
+    gap = abs(cx - by)
+    out = dict(
+        rp_norm2=float(np.linalg.norm(r_p)),
+        rp_norminf=float(np.max(np.abs(r_p))) if r_p.size else 0.0,
+        rd_norm2=float(np.linalg.norm(r_d)),
+        rd_norminf=float(np.max(np.abs(r_d))) if r_d.size else 0.0,
+        primal_obj=cx,
+        dual_obj=by,
+        gap=gap,
+        complementarity=float(x @ z),
+    )
+    out["rel_p"] = out["rp_norm2"] / (1.0 + float(np.linalg.norm(b)))
+    out["rel_d"] = out["rd_norm2"] / (1.0 + float(np.linalg.norm(c)))
+    out["rel_gap"] = gap / (1.0 + abs(cx) + abs(by))
+    out["rel_kkt"] = max(out["rel_p"], out["rel_d"], out["rel_gap"])
+    return out
+
+
+def satisfies_termination(info: dict, eps: float) -> bool:
+    """The three inequalities of the PDHG termination test (Section 2)."""
+    return info["rel_p"] <= eps and info["rel_d"] <= eps and info["rel_gap"] <= eps
+
+
+# ---------------------------------------------------------------------------
+# Diagonal scaling (PDLP preprocessing; the paper is silent on its details)
+# ---------------------------------------------------------------------------
+
+def _inv_sqrt_or_one(v: np.ndarray) -> np.ndarray:
+    out = np.ones_like(v)
+    nz = v > 0
+    out[nz] = 1.0 / np.sqrt(v[nz])
+    return out
+
+
+def ruiz_scaling(A: sp.csr_matrix, iters: int):
+    """Ruiz equilibration: repeat ``iters`` times
+    r_i = 1/sqrt(max_j |Ahat_ij|), s_j = 1/sqrt(max_i |Ahat_ij|) (1 for an empty
+    row/column), Ahat <- diag(r) Ahat diag(s). Returns (Ahat, d_r, d_c)."""
+    Ah = A.copy().astype(np.float64)
+    d_r = np.ones(A.shape[0])
+    d_c = np.ones(A.shape[1])
+    for _ in range(iters):
+        absA = abs(Ah)
+        row_max = np.asarray(absA.max(axis=1).todense()).ravel()
+        col_max = np.asarray(absA.max(axis=0).todense()).ravel()
+        r = _inv_sqrt_or_one(row_max)
+        s = _inv_sqrt_or_one(col_max)
+        Ah = sp.diags(r) @ Ah @ sp.diags(s)
+        d_r *= r
+        d_c *= s
+    return sp.csr_matrix(Ah), d_r, d_c
+
+
+def pock_chambolle_scaling(A: sp.csr_matrix, alpha: float = 1.0):
+    """Pock-Chambolle diagonal preconditioning with parameter alpha:
+    r_i = 1/sqrt(sum_j |A_ij|^alpha), s_j = 1/sqrt(sum_i |A_ij|^(2 - alpha)).
+    Returns (Ahat, r, s)."""
+    absA = abs(A)
+    row_sum = np.asarray(absA.power(alpha).sum(axis=1)).ravel()
+    col_sum = np.asarray(absA.power(2.0 - alpha).sum(axis=0)).ravel()
+    r = _inv_sqrt_or_one(row_sum)
+    s = _inv_sqrt_or_one(col_sum)
+    return sp.csr_matrix(sp.diags(r) @ A @ sp.diags(s)), r, s
+
+
+def scale_problem(A: sp.csr_matrix, b: np.ndarray, c: np.ndarray, opt: Options):
+    """Ahat = D_r A D_c, bhat = D_r b, chat = D_c c."""
+    Ah, d_r, d_c = ruiz_scaling(A, opt.ruiz_iters)
+    if opt.pock_chambolle:
+        Ah, r, s = pock_chambolle_scaling(Ah, opt.pc_alpha)
+        d_r = d_r * r
+        d_c = d_c * s
+    return Ah, d_r * b, d_c * c, d_r, d_c
+
+
+def power_norm(Ah: sp.csr_matrix, iters: int) -> float:
+    """Estimate ||Ahat||_2 by ``iters`` power iterations on Ahat^T Ahat from the
+    all-ones vector: u = Ahat v, w = Ahat^T u, estimate = ||u||, v <- w/||w||."""
+    n = Ah.shape[1]
+    if n == 0 or Ah.nnz == 0:
+        return 0.0
+    v = np.ones(n) / math.sqrt(n)
+    est = 0.0
+    for _ in range(iters):
+        u = Ah @ v
+        est = float(np.linalg.norm(u))
+        w = Ah.T @ u
+        wn = float(np.linalg.norm(w))
+        if wn == 0.0:
+            break
+        v = w / wn
+    return est
+
+
+# ---------------------------------------------------------------------------
+# One PDHG iteration (Algorithm 1, "Perform PDHG iteration")
+# ---------------------------------------------------------------------------
+
+def pdhg_iteration(Ah, AhT, bh, ch, x, y, tau, sigma):
+    """x' = max(0, x - tau (chat - Ahat^T y)); xbar = 2x' - x;
+    y' = y + sigma (bhat - Ahat xbar). Returns (x', xbar, y')."""
+    x_new = np.maximum(0.0, x - tau * (ch - AhT @ y))
+    xbar = 2.0 * x_new - x
+    y_new = y + sigma * (bh - Ah @ xbar)
+    return x_new, xbar, y_new
+
+
+# ---------------------------------------------------------------------------
+# Restart rules
+# ---------------------------------------------------------------------------
+
+def weighted_kkt(norms, omega: float) -> float:
+    """KKT_omega = sqrt(omega ||r_P||^2 + ||r_D||^2 / omega + gap^2) from the
+    (||r_P||, ||r_D||, gap) of a point of the scaled problem."""
+    p, d, g = norms
+    return math.sqrt(omega * p * p + d * d / omega + g * g)
+
+
+def choose_candidate(n_cur, n_avg, omega) -> int:
+    """The average wins only if its weighted KKT error is strictly smaller."""
+    return RESTART_TO_AVERAGE if weighted_kkt(n_avg, omega) < weighted_kkt(n_cur, omega) else RESTART_TO_CURRENT
+
+
+def restart_decision(k_cand, k_last_restart, k_prev_cand, t_since, k_total, opt: Options) -> bool:
+    """PDLP's three restart criteria on weighted KKT errors:
+    sufficient decay, necessary decay with no progress since the previous
+    evaluation, or an artificial restart after a long run."""
+    if k_cand <= opt.beta_suff * k_last_restart:
+        return True
+    if k_cand <= opt.beta_nec * k_last_restart and k_cand > k_prev_cand:
+        return True
+    return t_since >= opt.beta_art * k_total
+
+
+def primal_weight_update(omega: float, dx: float, dy: float, theta: float) -> float:
+    """omega <- exp(theta ln(dy/dx) + (1 - theta) ln omega) when both moves are
+    above 1e-10; unchanged otherwise."""
+    if dx > 1e-10 and dy > 1e-10:
+        return math.exp(theta * math.log(dy / dx) + (1.0 - theta) * math.log(omega))
+    return omega
+
+
+# ---------------------------------------------------------------------------
+# The solver
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class EvalRecord:
+    iteration: int
+    kind: int  # NO_RESTART / RESTART_TO_CURRENT / RESTART_TO_AVERAGE
+    candidate: int  # RESTART_TO_CURRENT / RESTART_TO_AVERAGE
+    omega: float  # after the update
+    rel_kkt: float  # of the candidate, on the problem as given
+
+
+class Oracle:
+    """Plain FP64 PDHG for ``min c^T x, Ax = b, x >= 0``."""
+
+    def __init__(self, m, n, row_ptr, col_idx, val, b, c, opt: Options | None = None,
+                 x0=None, y0=None):
+        self.opt = opt or Options()
+        self.A = csr_matrix(m, n, row_ptr, col_idx, val)
+        self.b = np.asarray(b, dtype=np.float64).copy()
+        self.c = np.asarray(c, dtype=np.float64).copy()
+        self.m, self.n = m, n
+        self.Ah, self.bh, self.ch, self.d_r, self.d_c = scale_problem(self.A, self.b, self.c, self.opt)
+        self.AhT = sp.csr_matrix(self.Ah.T)
+        self.norm_est = power_norm(self.Ah, self.opt.power_iters)
+        self.eta = self.opt.step_factor / self.norm_est if self.norm_est > 0 else 1.0
+        if self.opt.primal_weight:
+            cn, bn = float(np.linalg.norm(self.ch)), float(np.linalg.norm(self.bh))
+            self.omega = cn / bn if (cn > 1e-10 and bn > 1e-10) else 1.0
+        else:
+            self.omega = 1.0
+        # iterate in scaled space: x = D_c xhat, y = D_r yhat
+        self.x = np.zeros(n) if x0 is None else np.asarray(x0, dtype=np.float64) / self.d_c
+        self.y = np.zeros(m) if y0 is None else np.asarray(y0, dtype=np.float64) / self.d_r
+        self.x_sum = np.zeros(n)
+        self.y_sum = np.zeros(m)
+        self.t = 0
+        self.k = 0
+        self.trace: list[EvalRecord] = []
+        self.snapshots: list[dict] = []
+        self.eps_target = self.opt.eps_cross
+        self.next_snapshot = self.opt.snapshot_every
+        self.restart_count = 0
+        self.done = False
+        # restart reference = the starting point
+        self.x_r, self.y_r = self.x.copy(), self.y.copy()
+        self.n_restart = self.scaled_norms(self.x, self.y)
+        self.n_prev = self.n_restart
+
+    # -- step sizes --------------------------------------------------------
+    @property
+    def tau(self) -> float:
+        return self.eta / self.omega
+
+    @property
+    def sigma(self) -> float:
+        return self.eta * self.omega
+
+    # -- measures on the scaled problem (restart rules) --------------------
+    def scaled_norms(self, xh, yh):
+        """(||bhat - Ahat xhat||, ||max(0, Ahat^T yhat - chat)||, |chat^T xhat - bhat^T yhat|)."""
+        rp = self.bh - self.Ah @ xh
+        rd = np.maximum(0.0, self.AhT @ yh - self.ch)
+        return (float(np.linalg.norm(rp)), float(np.linalg.norm(rd)), abs(float(self.ch @ xh) - float(self.bh @ yh)))
+
+    # -- unscaled quantities -----------------------------------------------
+    def unscale(self, xh, yh):
+        """(x, y, z) of the problem as given from a scaled point."""
+        x = self.d_c * xh
+        y = self.d_r * yh
+        return x, y, dual_slack(self.A, self.c, y)
+
+    def kkt_of(self, xh, yh) -> dict:
+        x, y, z = self.unscale(xh, yh)
+        return kkt(self.A, self.b, self.c, x, y, z)
+
+    @property
+    def x_avg(self):
+        return self.x_sum / self.t if self.t > 0 else self.x.copy()
+
+    @property
+    def y_avg(self):
+        return self.y_sum / self.t if self.t > 0 else self.y.copy()
+
+    # -- iteration -----------------------------------------------------------
+    def iterate_once(self):
+        x_new, _, y_new = pdhg_iteration(self.Ah, self.AhT, self.bh, self.ch, self.x, self.y, self.tau, self.sigma)
+        self.x, self.y = x_new, y_new
+        if self.opt.restarts:
+            self.x_sum += x_new
+            self.y_sum += y_new
+        self.t += 1
+        self.k += 1
+
+    def evaluate(self, tol: float) -> bool:
+        """One evaluation: candidate choice, termination, snapshots, restart and
+        primal-weight update. Returns True when the method has converged."""
+        opt = self.opt
+        if opt.restarts and self.t > 0:
+            xa, ya = self.x_avg, self.y_avg
+            n_cur = self.scaled_norms(self.x, self.y)
+            n_avg = self.scaled_norms(xa, ya)
+            which = choose_candidate(n_cur, n_avg, self.omega)
+        else:
+            xa = ya = None
+            n_cur = self.scaled_norms(self.x, self.y)
+            n_avg = None
+            which = RESTART_TO_CURRENT
+        if which == RESTART_TO_AVERAGE:
+            xc, yc, n_c = xa, ya, n_avg
+        else:
+            xc, yc, n_c = self.x, self.y, n_cur
+        rel = self.kkt_of(xc, yc)["rel_kkt"]
+
+        converged = tol > 0 and rel <= tol
+        # Algorithm 1: snapshot when maxresid <= eps_target, then shrink eps_target.
+        if self.eps_target > 0 and rel <= self.eps_target:
+            self._snapshot(xc, yc, rel, "threshold")
+            self.eps_target *= opt.eps_factor
+        if opt.snapshot_every > 0 and self.k >= self.next_snapshot:
+            self._snapshot(xc, yc, rel, "periodic")
+            while self.next_snapshot <= self.k:
+                self.next_snapshot += opt.snapshot_every
+
+        kind = NO_RESTART
+        if converged:
+            self.x, self.y = xc.copy(), yc.copy()
+        elif opt.restarts:
+            om = self.omega
+            k_c = weighted_kkt(n_c, om)
+            if restart_decision(k_c, weighted_kkt(self.n_restart, om), weighted_kkt(self.n_prev, om),
+                                self.t, self.k, opt):
+                kind = which
+                if opt.primal_weight:
+                    dx = float(np.linalg.norm(xc - self.x_r))
+                    dy = float(np.linalg.norm(yc - self.y_r))
+                    self.omega = primal_weight_update(self.omega, dx, dy, opt.theta)
+                self.x, self.y = xc.copy(), yc.copy()
+                self.x_r, self.y_r = xc.copy(), yc.copy()
+                self.n_restart = n_c
+                self.x_sum[:] = 0.0
+                self.y_sum[:] = 0.0
+                self.t = 0
+                self.restart_count += 1
+            self.n_prev = n_c
+        self.trace.append(EvalRecord(self.k, kind, which, self.omega, rel))
+        return converged
+
+    def _snapshot(self, xh, yh, rel, why):
+        x, y, z = self.unscale(xh, yh)
+        self.snapshots.append(dict(iteration=self.k, x=x, y=y, z=z, rel_kkt=rel, why=why))
+
+    def run(self, max_iters: int, tol: float = 0.0) -> bool:
+        """Iterate until rel_kkt <= tol at an evaluation or max_iters iterations.
+        Evaluations happen every ``eval_every`` iterations when restarts are on or
+        tol > 0; with restarts off and tol = 0 this is plain fixed-step PDHG."""
+        evaluating = self.opt.restarts or tol > 0 or self.opt.eps_cross > 0 or self.opt.snapshot_every > 0
+        for _ in range(max_iters):
+            if self.done:
+                break
+            self.iterate_once()
+            if evaluating and self.k % self.opt.eval_every == 0:
+                if self.evaluate(tol):
+                    self.done = True
+        return self.done
+
+    # -- results ---------------------------------------------------------------
+    def solution(self):
+        """Unscaled (x, y, z) of the current iterate."""
+        return self.unscale(self.x, self.y)
