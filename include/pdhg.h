@@ -1,0 +1,191 @@
+/*
+ * pdhg.h - C ABI of the B300 (sm_103a) PDHG engine for the standard-form LP
+ *
+ *     min c^T x   s.t.  A x = b,  x >= 0        (primal)
+ *     max b^T y   s.t.  A^T y + z = c,  z >= 0  (dual)
+ *
+ * as stated in Section 2 ("Background") of "Concurrent Crossover for PDHG"
+ * (Rothberg, 2025). The engine runs the PDLP-style PDHG iteration on one GPU
+ * (the "Perform PDHG iteration" step of Algorithm 1, Section 3.1), reports the
+ * residuals r_P = b - A x and r_D = A^T y + z - c, the objective gap and
+ * complementarity (Section 2), and hands out snapshot iterates (x, y, z) at the
+ * points where Algorithm 1 would launch a crossover thread (Section 3.1).
+ *
+ * General rules for every call:
+ *   - Every call returns a pdhg_status; nothing aborts, traps or exits.
+ *     pdhg_last_error() gives a one-line description of the last failure.
+ *   - A pdhg_ctx is not thread-safe: one host thread at a time per context.
+ *     Different contexts are independent.
+ *   - Pointers passed in are borrowed for the duration of the call only; the
+ *     library copies what it keeps. Output buffers are owned by the caller.
+ *   - Matrices are CSR with rows = constraints, 0-based, column indices strictly
+ *     increasing within each row (so no duplicates). Sizes: 1 <= m, n < 2^31,
+ *     0 <= nnz < 2^31.
+ *   - Vectors are dense float64 arrays: x, c, z have length n; y, b length m.
+ *   - The CUDA stream argument is a cudaStream_t (for example
+ *     torch.cuda.current_stream().cuda_stream) or NULL for a stream the library
+ *     creates. All device work of the context is ordered on that stream.
+ */
+#ifndef PDHG_H
+#define PDHG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PDHG_API __attribute__((visibility("default")))
+#else
+#define PDHG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pdhg_ctx pdhg_ctx;
+
+typedef enum {
+  PDHG_OK = 0,
+  PDHG_ERR_INVALID = 1,       /* bad argument or malformed CSR */
+  PDHG_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  PDHG_ERR_OOM = 3,           /* device or pinned host allocation failed */
+  PDHG_ERR_TIMEOUT = 4,       /* a bounded device wait gave up */
+  PDHG_ERR_NUMERIC = 5,       /* NaN or Inf in the data or in the iterates */
+  PDHG_ERR_STATE = 6,         /* call not valid in the context's state */
+  PDHG_ERR_NOT_CONVERGED = 7  /* iteration limit reached before the tolerance */
+} pdhg_status;
+
+/* arithmetic of the iteration */
+enum { PDHG_FP64 = 0, PDHG_FP32 = 1, PDHG_MIXED = 2 };
+
+/* which point pdhg_kkt / pdhg_get_solution look at */
+enum { PDHG_CURRENT = 0, PDHG_AVERAGE = 1, PDHG_LAST_RESTART = 2 };
+
+/* restart kinds in the evaluation trace */
+enum { PDHG_NO_RESTART = 0, PDHG_RESTART_TO_CURRENT = 1, PDHG_RESTART_TO_AVERAGE = 2 };
+
+typedef struct {
+  int precision;          /* PDHG_FP64 (default), PDHG_FP32 or PDHG_MIXED */
+  int ruiz_iters;         /* Ruiz equilibration passes (10) */
+  int pock_chambolle;     /* 1: one Pock-Chambolle pass after Ruiz (1) */
+  double pc_alpha;        /* Pock-Chambolle alpha in [0, 2] (1.0) */
+  int power_iters;        /* power iterations for ||Ahat||_2 (100) */
+  double step_factor;     /* eta = step_factor / ||Ahat||_2 (0.9) */
+  int restarts;           /* 1: averaging + adaptive restarts (1) */
+  int primal_weight;      /* 1: omega0 = ||chat||/||bhat|| and updates at restarts (1) */
+  int eval_every;         /* iterations between evaluations (64) */
+  double beta_suff;       /* sufficient-decay restart factor (0.2) */
+  double beta_nec;        /* necessary-decay restart factor (0.8) */
+  double beta_art;        /* artificial restart fraction (0.36) */
+  double theta;           /* primal-weight smoothing (0.5) */
+  double eps_cross;       /* Algorithm 1: first snapshot target; 0 = off (0) */
+  double eps_factor;      /* Algorithm 1: target shrink factor (0.1) */
+  int64_t snapshot_every; /* periodic snapshots every this many iterations; 0 = off */
+  int inputs_on_device;   /* 1: pointers given to pdhg_create are device pointers */
+  int use_graphs;         /* 1: replay evaluation blocks as CUDA graphs (1) */
+  int kernel_timing;      /* 1: time the two step kernels with CUDA events (0) */
+  double polish_switch;   /* PDHG_MIXED: rel. KKT at which FP64 iterations take over (1e-5) */
+  int reserved[8];
+} pdhg_options;
+
+/* Scalars of one point on the problem as given (unscaled), all FP64.
+ * r_P = b - A x, r_D = A^T y + z - c with z = max(0, c - A^T y) (Section 2);
+ * rel_* are the three ratios of the relative termination test (Section 2) and
+ * rel_kkt is their maximum ("maxresid" of Algorithm 1). */
+typedef struct {
+  double rp_norm2, rp_norminf;
+  double rd_norm2, rd_norminf;
+  double primal_obj;      /* c^T x */
+  double dual_obj;        /* b^T y */
+  double gap;             /* |c^T x - b^T y| */
+  double complementarity; /* x^T z */
+  double rel_p, rel_d, rel_gap, rel_kkt;
+  int64_t iteration;
+} pdhg_kkt_info;
+
+/* Engine scalars after setup / during the solve. */
+typedef struct {
+  double norm_estimate;   /* power-iteration estimate of ||Ahat||_2 */
+  double eta, omega, tau, sigma;
+  int64_t iterations;     /* total PDHG iterations so far */
+  int64_t since_restart;
+  int64_t restarts;
+  int64_t evaluations;
+  int64_t snapshots;      /* scheduled snapshots taken so far */
+  double last_rel_kkt;    /* rel_kkt of the last evaluation's candidate */
+  int precision_now;      /* arithmetic currently used by the iteration */
+  int converged;
+  double kernel_ms_primal, kernel_ms_dual; /* summed event times (kernel_timing) */
+  int64_t kernel_launches_primal, kernel_launches_dual;
+} pdhg_info;
+
+/* One record per evaluation. */
+typedef struct {
+  int64_t iteration;
+  int32_t kind;       /* PDHG_NO_RESTART / _TO_CURRENT / _TO_AVERAGE */
+  int32_t candidate;  /* PDHG_RESTART_TO_CURRENT or _TO_AVERAGE */
+  double omega;       /* primal weight after this evaluation */
+  double rel_kkt;     /* candidate's rel_kkt on the problem as given */
+} pdhg_trace_rec;
+
+/* Fill *opt with the defaults listed above. */
+PDHG_API void pdhg_default_options(pdhg_options* opt);
+
+/* Create a solver for one LP. A (m x n, CSR: row_ptr[m+1], col_idx[nnz],
+ * val[nnz]), b[m], c[n]; x0[n] and y0[m] are an optional warm start (NULL =
+ * zeros). Setup: copy, transpose, Ruiz + Pock-Chambolle scaling, power
+ * iteration for eta, primal weight omega0, and the evaluation of the starting
+ * point. INVALID for malformed CSR or sizes out of range, NUMERIC for NaN/Inf
+ * in the data. On failure *out is NULL. */
+PDHG_API pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                                 const double* val, const double* b, const double* c, const double* x0,
+                                 const double* y0, const pdhg_options* opt, void* cuda_stream, pdhg_ctx** out);
+
+/* Free all device and pinned memory of the context. NULL-safe. */
+PDHG_API void pdhg_destroy(pdhg_ctx* ctx);
+
+/* Run PDHG iterations (Algorithm 1, "Perform PDHG iteration") until the
+ * candidate's rel_kkt <= tol at an evaluation, or max_iters more iterations.
+ * Evaluations happen every eval_every iterations (counted from the first
+ * iteration of the context) when tol > 0, restarts are on, or a snapshot
+ * schedule is set. tol = 0 with restarts off runs exactly max_iters plain
+ * iterations. Returns PDHG_OK when converged (or tol == 0), else
+ * PDHG_ERR_NOT_CONVERGED; *iters_done (nullable) gets the count run. */
+PDHG_API pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done);
+
+/* KKT measures (see pdhg_kkt_info) of the current iterate, the running average
+ * or the last restart point, in FP64 on the problem as given. */
+PDHG_API pdhg_status pdhg_kkt(pdhg_ctx* ctx, int which, pdhg_kkt_info* out);
+
+/* Copy (x, y, z) of the chosen point, on the problem as given, into caller
+ * buffers x[n], y[m], z[n] (any may be NULL). Host pointers unless
+ * on_device != 0. z = max(0, c - A^T y). Synchronous. */
+PDHG_API pdhg_status pdhg_get_solution(pdhg_ctx* ctx, int which, double* x, double* y, double* z, int on_device);
+
+/* Scheduled snapshots (Algorithm 1 thresholds eps_cross * eps_factor^j, and/or
+ * every snapshot_every iterations): the evaluation's candidate point, unscaled,
+ * packed on the GPU and copied to pinned host memory on a side stream while the
+ * iteration continues. *count gets the number taken so far, *ready whether the
+ * latest copy has landed (both nullable). Non-blocking. */
+PDHG_API pdhg_status pdhg_snapshot_poll(pdhg_ctx* ctx, int64_t* count, int* ready);
+
+/* Copy the latest scheduled snapshot into host buffers x[n], y[m], z[n]
+ * (any may be NULL); waits for its copy to land. STATE if none was taken. */
+PDHG_API pdhg_status pdhg_snapshot(pdhg_ctx* ctx, double* x, double* y, double* z, int64_t* iteration,
+                                   double* rel_kkt);
+
+/* Engine scalars. */
+PDHG_API pdhg_status pdhg_get_info(pdhg_ctx* ctx, pdhg_info* out);
+
+/* Copy up to cap evaluation records (oldest first) into recs; *count gets the
+ * number stored (at most 65536 are kept). */
+PDHG_API pdhg_status pdhg_get_trace(pdhg_ctx* ctx, pdhg_trace_rec* recs, int64_t cap, int64_t* count);
+
+/* Description of the last failure of ctx, or of the last failed pdhg_create
+ * when ctx is NULL. Never NULL. */
+PDHG_API const char* pdhg_last_error(const pdhg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDHG_H */

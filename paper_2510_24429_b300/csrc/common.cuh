@@ -1,0 +1,121 @@
+// Internal types and device helpers of the PDHG engine (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pdhg {
+
+// Quantities accumulated by one evaluation of a point (xhat, yhat) of the
+// scaled problem Ahat = D_r A D_c, bhat = D_r b, chat = D_c c.
+//   dual side (rows j of Ahat^T):  g = Ahat^T yhat, rd = max(0, g - chat)
+//   primal side (rows i of Ahat):  h = Ahat xhat,   rp = bhat - h
+// Unscaled residuals follow from r_P = D_r^{-1} rp and r_D = D_c^{-1} rd, and
+// c^T x = chat^T xhat, b^T y = bhat^T yhat, x^T z = xhat^T zhat.
+enum {
+  Q_RD2S = 0,  // sum rd^2                      (scaled ||r_D||^2)
+  Q_RD2U,      // sum (rd / d_c)^2              (||r_D||^2 as given)
+  Q_RDINF,     // max |rd / d_c|
+  Q_CX,        // sum chat * xhat               (c^T x)
+  Q_XZ,        // sum xhat * max(0, chat - g)   (x^T z)
+  Q_DX2,       // sum (xhat - xhat_restart)^2
+  Q_RP2S,      // sum rp^2
+  Q_RP2U,      // sum (rp / d_r)^2
+  Q_RPINF,     // max |rp / d_r|
+  Q_BY,        // sum bhat * yhat               (b^T y)
+  Q_DY2,       // sum (yhat - yhat_restart)^2
+  NQ
+};
+
+struct EvalSums {
+  double q[NQ];
+};
+
+// apply modes written by the decision kernel
+enum { APPLY_NONE = 0, APPLY_RESTART_CUR = 1, APPLY_RESTART_AVG = 2, APPLY_TAKE_AVG = 3 };
+enum { KIND_NONE = 0, KIND_CUR = 1, KIND_AVG = 2 };
+
+// Scalars of the method, resident in device memory so that kernels (and CUDA
+// graphs) read the current step sizes without host round trips.
+struct DevState {
+  double tau, sigma, omega, eta;
+  double norm_est;
+  double b_norm, c_norm;  // ||b||_2, ||c||_2 of the problem as given
+  // configuration
+  double tol, eps_target, eps_factor;
+  double beta_suff, beta_nec, beta_art, theta;
+  long long snapshot_every, next_snapshot;
+  int restarts_on, primal_weight_on;
+  // counters
+  long long k, t, restarts, evals, snapshots;
+  // restart reference and previous candidate: (||rp||, ||rd||, gap) scaled
+  double rs_p, rs_d, rs_g;
+  double pc_p, pc_d, pc_g;
+  // evaluation results
+  EvalSums cur, avg;
+  // decision outputs
+  int candidate, kind, apply_mode, converged;
+  int snapshot_flag, numeric, pad0, pad1;
+  double cand_rel_kkt;
+  double scratch[4];
+};
+
+struct TraceRec {
+  long long iteration;
+  int kind, candidate;
+  double omega, rel_kkt;
+};
+
+constexpr int TRACE_CAP = 65536;
+
+// CSR view (int32 indices; rows of the stored matrix)
+struct Csr {
+  int rows = 0, cols = 0;
+  long long nnz = 0;
+  int* rp = nullptr;
+  int* ci = nullptr;
+  double* v = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int off = W / 2; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off, W);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) { return group_sum<32>(v); }
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+  return v;
+}
+
+// Block-wide reduction of NV values per thread (sum, or max where is_max[q]);
+// result valid in thread 0. blockDim.x must be a multiple of 32 and <= 1024.
+template <int NV>
+__device__ __forceinline__ void block_reduce(double (&vals)[NV], const bool (&is_max)[NV]) {
+  __shared__ double sh[32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) vals[q] = is_max[q] ? warp_max(vals[q]) : warp_sum(vals[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[wid][q] = vals[q];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double v = lane < nw ? sh[lane][q] : 0.0;
+      vals[q] = is_max[q] ? warp_max(v) : warp_sum(v);
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace pdhg

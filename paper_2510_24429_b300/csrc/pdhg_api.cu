@@ -1,0 +1,702 @@
+// Host engine behind the C ABI of include/pdhg.h.
+//
+// One context = one LP resident on one GPU. Setup validates and transposes the
+// CSR on the host (a deterministic counting sort), uploads both layouts, and
+// does everything else on the device: Ruiz and Pock-Chambolle scaling, the
+// power iteration for ||Ahat||_2, the primal weight, and the evaluation of the
+// starting point. The solve loop launches the two fused half-steps per
+// iteration and, every eval_every iterations, the evaluation kernels and the
+// single-thread decision kernel; the host reads back one small status struct
+// per evaluation (Section 3.1: one CPU thread launches the GPU kernels and
+// fetches small amounts of data from GPU memory).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pdhg.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace pdhg;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+constexpr int TPB = 256;
+constexpr int EV_POOL = 256;
+
+}  // namespace
+
+struct pdhg_ctx {
+  int64_t m = 0, n = 0, nnz = 0;
+  pdhg_options opt{};
+  int device = 0, sms = 148;
+  cudaStream_t stream = nullptr, side = nullptr;
+  bool own_stream = false;
+  Csr A, At;
+  int lprA = 1, lprAt = 1;
+  double *b = nullptr, *c = nullptr, *bh = nullptr, *ch = nullptr, *dr = nullptr, *dc = nullptr;
+  double *x = nullptr, *y = nullptr, *xbar = nullptr, *xsum = nullptr, *ysum = nullptr;
+  double *xavg = nullptr, *yavg = nullptr, *xr = nullptr, *yr = nullptr;
+  double *tmp_n = nullptr, *tmp_m = nullptr, *tmp_n2 = nullptr;
+  double* partials = nullptr;
+  int nb_eval = 1;
+  double* scal = nullptr;
+  DevState* st = nullptr;
+  DevState* h_st = nullptr;  // pinned
+  EvalSums* kkt_sums = nullptr;
+  EvalSums* h_kkt = nullptr;  // pinned
+  TraceRec* trace = nullptr;
+  double* sol = nullptr;  // (x n, y m, z n)
+  // snapshot ring
+  double* snap_dev[2] = {nullptr, nullptr};
+  double* snap_host[2] = {nullptr, nullptr};
+  cudaEvent_t snap_packed[2] = {nullptr, nullptr}, snap_done[2] = {nullptr, nullptr};
+  int64_t snap_iter[2] = {0, 0};
+  double snap_rel[2] = {0, 0};
+  int64_t snap_count = 0;
+  // kernel timing
+  cudaEvent_t ev[3 * EV_POOL] = {};
+  double ms_primal = 0, ms_dual = 0;
+  int64_t launches_primal = 0, launches_dual = 0;
+  // host mirrors
+  int64_t k = 0;
+  bool converged = false;
+  std::vector<void*> allocs;
+  std::string err = "no error";
+};
+
+namespace {
+
+pdhg_status fail(pdhg_ctx* ctx, pdhg_status s, const std::string& msg) {
+  if (ctx)
+    ctx->err = msg;
+  else
+    g_create_error = msg;
+  return s;
+}
+
+pdhg_status cuda_fail(pdhg_ctx* ctx, cudaError_t e, const char* what) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(ctx, e == cudaErrorMemoryAllocation ? PDHG_ERR_OOM : PDHG_ERR_CUDA, msg);
+}
+
+#define CK(ctx, call)                                        \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(pdhg_ctx* ctx, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e == cudaSuccess) ctx->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return e;
+}
+
+int vec_grid(const pdhg_ctx* ctx, long long len) {
+  long long g = (len + TPB - 1) / TPB;
+  return (int)std::max<long long>(1, std::min<long long>(g, (long long)ctx->sms * 8));
+}
+
+int row_grid(const pdhg_ctx* ctx, long long rows, int lpr) {
+  const long long rows_per_block = TPB / lpr;
+  long long g = (rows + rows_per_block - 1) / rows_per_block;
+  return (int)std::max<long long>(1, std::min<long long>(g, (long long)ctx->sms * 16));
+}
+
+pdhg_status set_device(pdhg_ctx* ctx) {
+  int cur = -1;
+  CK(ctx, cudaGetDevice(&cur));
+  if (cur != ctx->device) CK(ctx, cudaSetDevice(ctx->device));
+  return PDHG_OK;
+}
+
+bool all_finite(const double* v, int64_t len) {
+  for (int64_t i = 0; i < len; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+pdhg_status read_state(pdhg_ctx* ctx) {
+  CK(ctx, cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return PDHG_OK;
+}
+
+// Evaluate a point into *dst (EvalSums in device memory).
+void eval_point(pdhg_ctx* ctx, const double* px, const double* py, const double* xr, const double* yr,
+                EvalSums* dst) {
+  launch_eval_point(ctx->A, ctx->lprA, ctx->At, ctx->lprAt, px, py, ctx->bh, ctx->ch, ctx->dr, ctx->dc, xr, yr,
+                    ctx->partials, ctx->nb_eval, ctx->stream);
+  launch_eval_finalize(ctx->partials, ctx->nb_eval, dst, ctx->stream);
+}
+
+void point_of(pdhg_ctx* ctx, int which, const double** px, const double** py) {
+  if (which == PDHG_AVERAGE) {
+    launch_make_average(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, (int)ctx->n, (int)ctx->m,
+                        ctx->st, vec_grid(ctx, std::max(ctx->n, ctx->m)), ctx->stream);
+    *px = ctx->xavg;
+    *py = ctx->yavg;
+  } else if (which == PDHG_LAST_RESTART) {
+    *px = ctx->xr;
+    *py = ctx->yr;
+  } else {
+    *px = ctx->x;
+    *py = ctx->y;
+  }
+}
+
+pdhg_status take_snapshot(pdhg_ctx* ctx) {
+  const int slot = (int)(ctx->snap_count % 2);
+  if (ctx->snap_count >= 2) CK(ctx, cudaEventSynchronize(ctx->snap_done[slot]));
+  const bool avg = ctx->h_st->candidate == KIND_AVG;
+  const double* px = avg ? ctx->xavg : ctx->x;
+  const double* py = avg ? ctx->yavg : ctx->y;
+  double* base = ctx->snap_dev[slot];
+  launch_pack_solution(ctx->At, ctx->lprAt, px, py, ctx->ch, ctx->dc, ctx->dr, base, base + ctx->n,
+                       base + ctx->n + ctx->m, vec_grid(ctx, ctx->n), ctx->stream);
+  CK(ctx, cudaGetLastError());
+  CK(ctx, cudaEventRecord(ctx->snap_packed[slot], ctx->stream));
+  CK(ctx, cudaStreamWaitEvent(ctx->side, ctx->snap_packed[slot], 0));
+  CK(ctx, cudaMemcpyAsync(ctx->snap_host[slot], base, sizeof(double) * (2 * ctx->n + ctx->m), cudaMemcpyDeviceToHost,
+                          ctx->side));
+  CK(ctx, cudaEventRecord(ctx->snap_done[slot], ctx->side));
+  ctx->snap_iter[slot] = ctx->h_st->k;
+  ctx->snap_rel[slot] = ctx->h_st->cand_rel_kkt;
+  ctx->snap_count += 1;
+  return PDHG_OK;
+}
+
+pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx, const double* val, const double* b,
+                  const double* c, const double* x0, const double* y0) {
+  const int64_t m = ctx->m, n = ctx->n, nnz = ctx->nnz;
+  const pdhg_options& o = ctx->opt;
+  // ---- host: int32 CSR of A and its transpose (stable counting sort) ----
+  std::vector<int> rpA(m + 1), ciA(nnz), rpT(n + 1, 0), ciT(nnz);
+  std::vector<double> vT(nnz);
+  for (int64_t i = 0; i <= m; ++i) rpA[i] = (int)row_ptr[i];
+  for (int64_t k = 0; k < nnz; ++k) {
+    ciA[k] = col_idx[k];
+    rpT[col_idx[k] + 1] += 1;
+  }
+  for (int64_t j = 0; j < n; ++j) rpT[j + 1] += rpT[j];
+  {
+    std::vector<int> next(rpT.begin(), rpT.end() - 1);
+    for (int64_t i = 0; i < m; ++i)
+      for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+        const int pos = next[col_idx[k]]++;
+        ciT[pos] = (int)i;
+        vT[pos] = val[k];
+      }
+  }
+  // ---- device allocations ----
+  Csr& A = ctx->A;
+  Csr& At = ctx->At;
+  A.rows = (int)m;
+  A.cols = (int)n;
+  A.nnz = nnz;
+  At.rows = (int)n;
+  At.cols = (int)m;
+  At.nnz = nnz;
+  CK(ctx, dalloc(ctx, &A.rp, m + 1));
+  CK(ctx, dalloc(ctx, &A.ci, nnz));
+  CK(ctx, dalloc(ctx, &A.v, nnz));
+  CK(ctx, dalloc(ctx, &At.rp, n + 1));
+  CK(ctx, dalloc(ctx, &At.ci, nnz));
+  CK(ctx, dalloc(ctx, &At.v, nnz));
+  double** vecs_n[] = {&ctx->c, &ctx->ch, &ctx->dc, &ctx->x, &ctx->xbar, &ctx->xsum, &ctx->xavg, &ctx->xr,
+                       &ctx->tmp_n, &ctx->tmp_n2};
+  double** vecs_m[] = {&ctx->b, &ctx->bh, &ctx->dr, &ctx->y, &ctx->ysum, &ctx->yavg, &ctx->yr, &ctx->tmp_m};
+  for (double** p : vecs_n) CK(ctx, dalloc(ctx, p, n));
+  for (double** p : vecs_m) CK(ctx, dalloc(ctx, p, m));
+  ctx->lprA = pick_lanes_per_row((double)nnz / (double)m);
+  ctx->lprAt = pick_lanes_per_row((double)nnz / (double)n);
+  ctx->nb_eval =
+      std::max(1, std::min(ctx->sms * 4, std::max(row_grid(ctx, m, ctx->lprA), row_grid(ctx, n, ctx->lprAt))));
+  CK(ctx, dalloc(ctx, &ctx->partials, (size_t)std::max(ctx->nb_eval, ctx->sms * 8) * NQ));
+  CK(ctx, dalloc(ctx, &ctx->scal, 16));
+  CK(ctx, dalloc(ctx, &ctx->st, 1));
+  CK(ctx, dalloc(ctx, &ctx->kkt_sums, 1));
+  CK(ctx, dalloc(ctx, &ctx->trace, TRACE_CAP));
+  CK(ctx, dalloc(ctx, &ctx->sol, 2 * n + m));
+  for (int s = 0; s < 2; ++s) {
+    CK(ctx, dalloc(ctx, &ctx->snap_dev[s], 2 * n + m));
+    CK(ctx, cudaMallocHost(&ctx->snap_host[s], sizeof(double) * (2 * n + m)));
+    CK(ctx, cudaEventCreateWithFlags(&ctx->snap_packed[s], cudaEventDisableTiming));
+    CK(ctx, cudaEventCreateWithFlags(&ctx->snap_done[s], cudaEventDisableTiming));
+  }
+  CK(ctx, cudaMallocHost(&ctx->h_st, sizeof(DevState)));
+  CK(ctx, cudaMallocHost(&ctx->h_kkt, sizeof(EvalSums)));
+  for (int i = 0; i < 3 * EV_POOL; ++i) CK(ctx, cudaEventCreate(&ctx->ev[i]));
+
+  cudaStream_t s = ctx->stream;
+  CK(ctx, cudaMemcpyAsync(A.rp, rpA.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(A.ci, ciA.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(A.v, val, sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(At.rp, rpT.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(At.ci, ciT.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(At.v, vT.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->b, b, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->c, c, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+
+  // ---- device: scaling ----
+  const int gn = vec_grid(ctx, n), gm = vec_grid(ctx, m);
+  const int grA = row_grid(ctx, m, ctx->lprA), grT = row_grid(ctx, n, ctx->lprAt);
+  launch_fill(ctx->dr, 1.0, m, gm, s);
+  launch_fill(ctx->dc, 1.0, n, gn, s);
+  double* r = ctx->tmp_m;   // row factors
+  double* sf = ctx->tmp_n;  // column factors
+  for (int it = 0; it < o.ruiz_iters; ++it) {
+    launch_row_absmax(A, ctx->lprA, r, grA, s);
+    launch_row_absmax(At, ctx->lprAt, sf, grT, s);
+    launch_inv_sqrt_or_one(r, r, (int)m, gm, s);
+    launch_inv_sqrt_or_one(sf, sf, (int)n, gn, s);
+    launch_scale_csr(A, ctx->lprA, r, sf, 0, grA, s);
+    launch_scale_csr(At, ctx->lprAt, r, sf, 1, grT, s);
+    launch_mul_inplace(ctx->dr, r, (int)m, gm, s);
+    launch_mul_inplace(ctx->dc, sf, (int)n, gn, s);
+  }
+  if (o.pock_chambolle) {
+    launch_row_abspow_sum(A, ctx->lprA, o.pc_alpha, r, grA, s);
+    launch_row_abspow_sum(At, ctx->lprAt, 2.0 - o.pc_alpha, sf, grT, s);
+    launch_inv_sqrt_or_one(r, r, (int)m, gm, s);
+    launch_inv_sqrt_or_one(sf, sf, (int)n, gn, s);
+    launch_scale_csr(A, ctx->lprA, r, sf, 0, grA, s);
+    launch_scale_csr(At, ctx->lprAt, r, sf, 1, grT, s);
+    launch_mul_inplace(ctx->dr, r, (int)m, gm, s);
+    launch_mul_inplace(ctx->dc, sf, (int)n, gn, s);
+  }
+  launch_mul(ctx->bh, ctx->dr, ctx->b, (int)m, gm, s);
+  launch_mul(ctx->ch, ctx->dc, ctx->c, (int)n, gn, s);
+  CK(ctx, cudaGetLastError());
+
+  // ---- device: power iteration for ||Ahat||_2 from the all-ones vector ----
+  double* v = ctx->tmp_n;
+  double* w = ctx->tmp_n2;
+  double* u = ctx->tmp_m;
+  const int nbs = std::min(ctx->sms * 4, std::max(gn, gm));
+  launch_fill(v, 1.0 / sqrt((double)n), n, gn, s);
+  launch_fill(ctx->scal, 0.0, 16, 1, s);
+  for (int it = 0; it < o.power_iters; ++it) {
+    launch_spmv(A, ctx->lprA, v, u, grA, s);
+    launch_sumsq(u, (int)m, ctx->partials, nbs, ctx->scal + 0, s);
+    launch_spmv(At, ctx->lprAt, u, w, grT, s);
+    launch_sumsq(w, (int)n, ctx->partials, nbs, ctx->scal + 5, s);
+    launch_div_by_norm(v, w, ctx->scal + 5, (int)n, gn, s);
+  }
+  launch_sumsq(ctx->ch, (int)n, ctx->partials, nbs, ctx->scal + 1, s);
+  launch_sumsq(ctx->bh, (int)m, ctx->partials, nbs, ctx->scal + 2, s);
+  launch_sumsq(ctx->b, (int)m, ctx->partials, nbs, ctx->scal + 3, s);
+  launch_sumsq(ctx->c, (int)n, ctx->partials, nbs, ctx->scal + 4, s);
+  CK(ctx, cudaGetLastError());
+
+  // ---- device state ----
+  DevState h{};
+  h.tol = 0.0;
+  h.eps_target = o.eps_cross;
+  h.eps_factor = o.eps_factor;
+  h.beta_suff = o.beta_suff;
+  h.beta_nec = o.beta_nec;
+  h.beta_art = o.beta_art;
+  h.theta = o.theta;
+  h.snapshot_every = o.snapshot_every;
+  h.next_snapshot = o.snapshot_every;
+  h.restarts_on = o.restarts;
+  h.primal_weight_on = o.primal_weight;
+  *ctx->h_st = h;
+  CK(ctx, cudaMemcpyAsync(ctx->st, ctx->h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  launch_finish_setup(ctx->st, ctx->scal, o.step_factor, o.primal_weight, s);
+
+  // ---- starting point (scaled: xhat = x0 / D_c, yhat = y0 / D_r) ----
+  launch_fill(ctx->x, 0.0, n, gn, s);
+  launch_fill(ctx->y, 0.0, m, gm, s);
+  if (x0) {
+    CK(ctx, cudaMemcpyAsync(ctx->tmp_n, x0, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    launch_div(ctx->x, ctx->tmp_n, ctx->dc, (int)n, gn, s);
+  }
+  if (y0) {
+    CK(ctx, cudaMemcpyAsync(ctx->tmp_m, y0, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    launch_div(ctx->y, ctx->tmp_m, ctx->dr, (int)m, gm, s);
+  }
+  launch_fill(ctx->xsum, 0.0, n, gn, s);
+  launch_fill(ctx->ysum, 0.0, m, gm, s);
+  CK(ctx, cudaMemcpyAsync(ctx->xr, ctx->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->yr, ctx->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->xavg, ctx->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->yavg, ctx->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  // restart reference = the starting point
+  eval_point(ctx, ctx->x, ctx->y, nullptr, nullptr, &ctx->st->cur);
+  launch_init_restart_ref(ctx->st, s);
+  CK(ctx, cudaGetLastError());
+  pdhg_status rs = read_state(ctx);
+  if (rs != PDHG_OK) return rs;
+  if (!std::isfinite(ctx->h_st->norm_est) || !std::isfinite(ctx->h_st->omega))
+    return fail(ctx, PDHG_ERR_NUMERIC, "non-finite norm estimate or primal weight after scaling");
+  return PDHG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pdhg_default_options(pdhg_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = PDHG_FP64;
+  o->ruiz_iters = 10;
+  o->pock_chambolle = 1;
+  o->pc_alpha = 1.0;
+  o->power_iters = 100;
+  o->step_factor = 0.9;
+  o->restarts = 1;
+  o->primal_weight = 1;
+  o->eval_every = 64;
+  o->beta_suff = 0.2;
+  o->beta_nec = 0.8;
+  o->beta_art = 0.36;
+  o->theta = 0.5;
+  o->eps_cross = 0.0;
+  o->eps_factor = 0.1;
+  o->snapshot_every = 0;
+  o->inputs_on_device = 0;
+  o->use_graphs = 1;
+  o->kernel_timing = 0;
+  o->polish_switch = 1e-5;
+}
+
+pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                        const double* val, const double* b, const double* c, const double* x0, const double* y0,
+                        const pdhg_options* opt, void* cuda_stream, pdhg_ctx** out) {
+  if (!out) return fail(nullptr, PDHG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (m < 1 || n < 1 || m >= (1LL << 31) - 1 || n >= (1LL << 31) - 1)
+    return fail(nullptr, PDHG_ERR_INVALID, "m and n must be in [1, 2^31 - 1)");
+  if (nnz < 0 || nnz >= (1LL << 31) - 1) return fail(nullptr, PDHG_ERR_INVALID, "nnz must be in [0, 2^31 - 1)");
+  if (!row_ptr || (nnz > 0 && (!col_idx || !val)) || !b || !c)
+    return fail(nullptr, PDHG_ERR_INVALID, "NULL array argument");
+  pdhg_options o;
+  if (opt)
+    o = *opt;
+  else
+    pdhg_default_options(&o);
+  if (o.precision != PDHG_FP64) return fail(nullptr, PDHG_ERR_INVALID, "only PDHG_FP64 is available in this build");
+  if (o.eval_every < 1 || o.ruiz_iters < 0 || o.power_iters < 1 || !(o.step_factor > 0.0) || o.pc_alpha < 0.0 ||
+      o.pc_alpha > 2.0 || o.snapshot_every < 0 || o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
+    return fail(nullptr, PDHG_ERR_INVALID, "option out of range");
+
+  // host copies when the caller passed device pointers
+  std::vector<int64_t> h_rp;
+  std::vector<int32_t> h_ci;
+  std::vector<double> h_v, h_b, h_c, h_x0, h_y0;
+  if (o.inputs_on_device) {
+    h_rp.resize(m + 1);
+    h_ci.resize(nnz);
+    h_v.resize(nnz);
+    h_b.resize(m);
+    h_c.resize(n);
+    cudaError_t e = cudaMemcpy(h_rp.data(), row_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && nnz) e = cudaMemcpy(h_ci.data(), col_idx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && nnz) e = cudaMemcpy(h_v.data(), val, sizeof(double) * nnz, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(h_b.data(), b, sizeof(double) * m, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(h_c.data(), c, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && x0) {
+      h_x0.resize(n);
+      e = cudaMemcpy(h_x0.data(), x0, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    }
+    if (e == cudaSuccess && y0) {
+      h_y0.resize(m);
+      e = cudaMemcpy(h_y0.data(), y0, sizeof(double) * m, cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "copy of device inputs");
+    row_ptr = h_rp.data();
+    col_idx = h_ci.data();
+    val = h_v.data();
+    b = h_b.data();
+    c = h_c.data();
+    if (x0) x0 = h_x0.data();
+    if (y0) y0 = h_y0.data();
+  }
+  // CSR validation (host logic, before any device work)
+  if (row_ptr[0] != 0 || row_ptr[m] != nnz)
+    return fail(nullptr, PDHG_ERR_INVALID, "row_ptr[0] != 0 or row_ptr[m] != nnz");
+  for (int64_t i = 0; i < m; ++i) {
+    if (row_ptr[i + 1] < row_ptr[i]) return fail(nullptr, PDHG_ERR_INVALID, "row_ptr not non-decreasing");
+    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+      if (col_idx[k] < 0 || col_idx[k] >= n) return fail(nullptr, PDHG_ERR_INVALID, "column index out of range");
+      if (k > row_ptr[i] && col_idx[k] <= col_idx[k - 1])
+        return fail(nullptr, PDHG_ERR_INVALID, "column indices not strictly increasing within a row");
+    }
+  }
+  if (!all_finite(val, nnz) || !all_finite(b, m) || !all_finite(c, n) || (x0 && !all_finite(x0, n)) ||
+      (y0 && !all_finite(y0, m)))
+    return fail(nullptr, PDHG_ERR_NUMERIC, "NaN or Inf in the input data");
+
+  pdhg_ctx* ctx = new (std::nothrow) pdhg_ctx();
+  if (!ctx) return fail(nullptr, PDHG_ERR_OOM, "host allocation of the context failed");
+  ctx->m = m;
+  ctx->n = n;
+  ctx->nnz = nnz;
+  ctx->opt = o;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) {
+      ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+      ctx->own_stream = true;
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    pdhg_status st = cuda_fail(nullptr, e, "device/stream setup");
+    pdhg_destroy(ctx);
+    return st;
+  }
+  pdhg_status st = setup(ctx, row_ptr, col_idx, val, b, c, x0, y0);
+  if (st != PDHG_OK) {
+    g_create_error = ctx->err;
+    pdhg_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return PDHG_OK;
+}
+
+void pdhg_destroy(pdhg_ctx* ctx) {
+  if (!ctx) return;
+  int cur = -1;
+  if (cudaGetDevice(&cur) == cudaSuccess && cur != ctx->device) cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->side) cudaStreamSynchronize(ctx->side);
+  for (void* p : ctx->allocs) cudaFree(p);
+  for (int s = 0; s < 2; ++s) {
+    if (ctx->snap_host[s]) cudaFreeHost(ctx->snap_host[s]);
+    if (ctx->snap_packed[s]) cudaEventDestroy(ctx->snap_packed[s]);
+    if (ctx->snap_done[s]) cudaEventDestroy(ctx->snap_done[s]);
+  }
+  for (int i = 0; i < 3 * EV_POOL; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  if (ctx->h_st) cudaFreeHost(ctx->h_st);
+  if (ctx->h_kkt) cudaFreeHost(ctx->h_kkt);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done) {
+  if (iters_done) *iters_done = 0;
+  if (!ctx) return PDHG_ERR_INVALID;
+  if (max_iters < 0 || !(tol >= 0.0)) return fail(ctx, PDHG_ERR_INVALID, "max_iters < 0 or tol < 0");
+  pdhg_status rs = set_device(ctx);
+  if (rs != PDHG_OK) return rs;
+  const pdhg_options& o = ctx->opt;
+  const bool evaluating = o.restarts || tol > 0.0 || o.eps_cross > 0.0 || o.snapshot_every > 0;
+  const int n = (int)ctx->n, m = (int)ctx->m;
+  cudaStream_t s = ctx->stream;
+  CK(ctx, cudaMemcpyAsync(&ctx->st->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
+  const int grT = row_grid(ctx, n, ctx->lprAt), grA = row_grid(ctx, m, ctx->lprA);
+  const int gv = vec_grid(ctx, std::max(n, m));
+  ctx->converged = false;
+  int64_t done = 0;
+  while (done < max_iters) {
+    int64_t nb;
+    if (evaluating)
+      nb = std::min<int64_t>(o.eval_every - (ctx->k % o.eval_every), max_iters - done);
+    else
+      nb = std::min<int64_t>(max_iters - done, o.kernel_timing ? EV_POOL : (1 << 20));
+    const bool timing = o.kernel_timing && nb <= EV_POOL;
+    for (int64_t it = 0; it < nb; ++it) {
+      if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
+      launch_primal_step(ctx->At, ctx->lprAt, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts,
+                         grT, s);
+      if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
+      launch_dual_step(ctx->A, ctx->lprA, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, grA, s);
+      if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 2], s));
+    }
+    launch_add_counters(ctx->st, nb, s);
+    CK(ctx, cudaGetLastError());
+    ctx->k += nb;
+    done += nb;
+    if (timing) {
+      CK(ctx, cudaEventSynchronize(ctx->ev[3 * (nb - 1) + 2]));
+      for (int64_t it = 0; it < nb; ++it) {
+        float a = 0.f, bms = 0.f;
+        CK(ctx, cudaEventElapsedTime(&a, ctx->ev[3 * it], ctx->ev[3 * it + 1]));
+        CK(ctx, cudaEventElapsedTime(&bms, ctx->ev[3 * it + 1], ctx->ev[3 * it + 2]));
+        ctx->ms_primal += a;
+        ctx->ms_dual += bms;
+      }
+      ctx->launches_primal += nb;
+      ctx->launches_dual += nb;
+    }
+    if (evaluating && ctx->k % o.eval_every == 0) {
+      if (o.restarts) {
+        launch_make_average(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, n, m, ctx->st, gv, s);
+        eval_point(ctx, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, &ctx->st->avg);
+      }
+      eval_point(ctx, ctx->x, ctx->y, ctx->xr, ctx->yr, &ctx->st->cur);
+      launch_decide(ctx->st, ctx->trace, s);
+      launch_apply(ctx->st, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, ctx->xsum, ctx->ysum, n, m, gv,
+                   s);
+      CK(ctx, cudaGetLastError());
+      rs = read_state(ctx);
+      if (rs != PDHG_OK) return rs;
+      if (ctx->h_st->numeric) {
+        if (iters_done) *iters_done = done;
+        return fail(ctx, PDHG_ERR_NUMERIC, "NaN or Inf in the iterates");
+      }
+      if (ctx->h_st->snapshot_flag) {
+        rs = take_snapshot(ctx);
+        if (rs != PDHG_OK) return rs;
+      }
+      if (ctx->h_st->converged) {
+        ctx->converged = true;
+        break;
+      }
+    }
+  }
+  CK(ctx, cudaStreamSynchronize(s));
+  if (iters_done) *iters_done = done;
+  if (ctx->converged || tol == 0.0) return PDHG_OK;
+  return fail(ctx, PDHG_ERR_NOT_CONVERGED, "iteration limit reached before the tolerance");
+}
+
+pdhg_status pdhg_kkt(pdhg_ctx* ctx, int which, pdhg_kkt_info* out) {
+  if (!ctx) return PDHG_ERR_INVALID;
+  if (!out) return fail(ctx, PDHG_ERR_INVALID, "out is NULL");
+  if (which < PDHG_CURRENT || which > PDHG_LAST_RESTART) return fail(ctx, PDHG_ERR_INVALID, "bad point selector");
+  pdhg_status rs = set_device(ctx);
+  if (rs != PDHG_OK) return rs;
+  const double *px, *py;
+  point_of(ctx, which, &px, &py);
+  eval_point(ctx, px, py, nullptr, nullptr, ctx->kkt_sums);
+  CK(ctx, cudaGetLastError());
+  CK(ctx, cudaMemcpyAsync(ctx->h_kkt, ctx->kkt_sums, sizeof(EvalSums), cudaMemcpyDeviceToHost, ctx->stream));
+  rs = read_state(ctx);
+  if (rs != PDHG_OK) return rs;
+  const double* q = ctx->h_kkt->q;
+  out->rp_norm2 = sqrt(q[Q_RP2U]);
+  out->rp_norminf = q[Q_RPINF];
+  out->rd_norm2 = sqrt(q[Q_RD2U]);
+  out->rd_norminf = q[Q_RDINF];
+  out->primal_obj = q[Q_CX];
+  out->dual_obj = q[Q_BY];
+  out->gap = fabs(q[Q_CX] - q[Q_BY]);
+  out->complementarity = q[Q_XZ];
+  out->rel_p = out->rp_norm2 / (1.0 + ctx->h_st->b_norm);
+  out->rel_d = out->rd_norm2 / (1.0 + ctx->h_st->c_norm);
+  out->rel_gap = out->gap / (1.0 + fabs(out->primal_obj) + fabs(out->dual_obj));
+  out->rel_kkt = std::max(out->rel_p, std::max(out->rel_d, out->rel_gap));
+  out->iteration = ctx->h_st->k;
+  return PDHG_OK;
+}
+
+pdhg_status pdhg_get_solution(pdhg_ctx* ctx, int which, double* x, double* y, double* z, int on_device) {
+  if (!ctx) return PDHG_ERR_INVALID;
+  if (which < PDHG_CURRENT || which > PDHG_LAST_RESTART) return fail(ctx, PDHG_ERR_INVALID, "bad point selector");
+  pdhg_status rs = set_device(ctx);
+  if (rs != PDHG_OK) return rs;
+  const double *px, *py;
+  point_of(ctx, which, &px, &py);
+  double* ox = ctx->sol;
+  double* oy = ctx->sol + ctx->n;
+  double* oz = ctx->sol + ctx->n + ctx->m;
+  launch_pack_solution(ctx->At, ctx->lprAt, px, py, ctx->ch, ctx->dc, ctx->dr, x ? ox : nullptr, y ? oy : nullptr,
+                       z ? oz : nullptr, vec_grid(ctx, ctx->n), ctx->stream);
+  CK(ctx, cudaGetLastError());
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (x) CK(ctx, cudaMemcpyAsync(x, ox, sizeof(double) * ctx->n, kind, ctx->stream));
+  if (y) CK(ctx, cudaMemcpyAsync(y, oy, sizeof(double) * ctx->m, kind, ctx->stream));
+  if (z) CK(ctx, cudaMemcpyAsync(z, oz, sizeof(double) * ctx->n, kind, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return PDHG_OK;
+}
+
+pdhg_status pdhg_snapshot_poll(pdhg_ctx* ctx, int64_t* count, int* ready) {
+  if (!ctx) return PDHG_ERR_INVALID;
+  if (count) *count = ctx->snap_count;
+  if (ready) {
+    *ready = 0;
+    if (ctx->snap_count > 0) {
+      cudaError_t e = cudaEventQuery(ctx->snap_done[(ctx->snap_count - 1) % 2]);
+      if (e == cudaSuccess)
+        *ready = 1;
+      else if (e != cudaErrorNotReady)
+        return cuda_fail(ctx, e, "cudaEventQuery");
+    }
+  }
+  return PDHG_OK;
+}
+
+pdhg_status pdhg_snapshot(pdhg_ctx* ctx, double* x, double* y, double* z, int64_t* iteration, double* rel_kkt) {
+  if (!ctx) return PDHG_ERR_INVALID;
+  if (ctx->snap_count == 0) return fail(ctx, PDHG_ERR_STATE, "no snapshot has been taken");
+  const int slot = (int)((ctx->snap_count - 1) % 2);
+  CK(ctx, cudaEventSynchronize(ctx->snap_done[slot]));
+  const double* h = ctx->snap_host[slot];
+  if (x) memcpy(x, h, sizeof(double) * ctx->n);
+  if (y) memcpy(y, h + ctx->n, sizeof(double) * ctx->m);
+  if (z) memcpy(z, h + ctx->n + ctx->m, sizeof(double) * ctx->n);
+  if (iteration) *iteration = ctx->snap_iter[slot];
+  if (rel_kkt) *rel_kkt = ctx->snap_rel[slot];
+  return PDHG_OK;
+}
+
+pdhg_status pdhg_get_info(pdhg_ctx* ctx, pdhg_info* out) {
+  if (!ctx) return PDHG_ERR_INVALID;
+  if (!out) return fail(ctx, PDHG_ERR_INVALID, "out is NULL");
+  pdhg_status rs = set_device(ctx);
+  if (rs != PDHG_OK) return rs;
+  rs = read_state(ctx);
+  if (rs != PDHG_OK) return rs;
+  const DevState& h = *ctx->h_st;
+  memset(out, 0, sizeof(*out));
+  out->norm_estimate = h.norm_est;
+  out->eta = h.eta;
+  out->omega = h.omega;
+  out->tau = h.tau;
+  out->sigma = h.sigma;
+  out->iterations = h.k;
+  out->since_restart = h.t;
+  out->restarts = h.restarts;
+  out->evaluations = h.evals;
+  out->snapshots = ctx->snap_count;
+  out->last_rel_kkt = h.cand_rel_kkt;
+  out->precision_now = PDHG_FP64;
+  out->converged = ctx->converged ? 1 : 0;
+  out->kernel_ms_primal = ctx->ms_primal;
+  out->kernel_ms_dual = ctx->ms_dual;
+  out->kernel_launches_primal = ctx->launches_primal;
+  out->kernel_launches_dual = ctx->launches_dual;
+  return PDHG_OK;
+}
+
+pdhg_status pdhg_get_trace(pdhg_ctx* ctx, pdhg_trace_rec* recs, int64_t cap, int64_t* count) {
+  if (!ctx) return PDHG_ERR_INVALID;
+  pdhg_status rs = set_device(ctx);
+  if (rs != PDHG_OK) return rs;
+  rs = read_state(ctx);
+  if (rs != PDHG_OK) return rs;
+  const int64_t stored = std::min<int64_t>(ctx->h_st->evals, TRACE_CAP);
+  const int64_t k = std::min<int64_t>(stored, cap < 0 ? 0 : cap);
+  if (count) *count = stored;
+  if (k > 0 && recs) {
+    static_assert(sizeof(TraceRec) == sizeof(pdhg_trace_rec), "trace record layout");
+    CK(ctx, cudaMemcpy(recs, ctx->trace, sizeof(TraceRec) * k, cudaMemcpyDeviceToHost));
+  }
+  return PDHG_OK;
+}
+
+const char* pdhg_last_error(const pdhg_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+"""Python binding of libpdhg.so (the C ABI in include/pdhg.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels. Functions carry the C names (``pdhg_create``, ``pdhg_iterate``,
+``pdhg_kkt``, ``pdhg_snapshot`` ...); ``Solver`` wraps one context.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA). PyTorch is
+used for device memory and streams only. There is no CPU fallback: if the
+library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpdhg.so")
+
+(PDHG_OK, PDHG_ERR_INVALID, PDHG_ERR_CUDA, PDHG_ERR_OOM, PDHG_ERR_TIMEOUT, PDHG_ERR_NUMERIC, PDHG_ERR_STATE,
+ PDHG_ERR_NOT_CONVERGED) = range(8)
+STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "TIMEOUT", "NUMERIC", "STATE", "NOT_CONVERGED"]
+PDHG_FP64, PDHG_FP32, PDHG_MIXED = 0, 1, 2
+PDHG_CURRENT, PDHG_AVERAGE, PDHG_LAST_RESTART = 0, 1, 2
+PDHG_NO_RESTART, PDHG_RESTART_TO_CURRENT, PDHG_RESTART_TO_AVERAGE = 0, 1, 2
+
+
+class pdhg_options(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int),
+        ("ruiz_iters", C.c_int),
+        ("pock_chambolle", C.c_int),
+        ("pc_alpha", C.c_double),
+        ("power_iters", C.c_int),
+        ("step_factor", C.c_double),
+        ("restarts", C.c_int),
+        ("primal_weight", C.c_int),
+        ("eval_every", C.c_int),
+        ("beta_suff", C.c_double),
+        ("beta_nec", C.c_double),
+        ("beta_art", C.c_double),
+        ("theta", C.c_double),
+        ("eps_cross", C.c_double),
+        ("eps_factor", C.c_double),
+        ("snapshot_every", C.c_int64),
+        ("inputs_on_device", C.c_int),
+        ("use_graphs", C.c_int),
+        ("kernel_timing", C.c_int),
+        ("polish_switch", C.c_double),
+        ("reserved", C.c_int * 8),
+    ]
+
+
+class pdhg_kkt_info(C.Structure):
+    _fields_ = [(k, C.c_double) for k in (
+        "rp_norm2", "rp_norminf", "rd_norm2", "rd_norminf", "primal_obj", "dual_obj", "gap", "complementarity",
+        "rel_p", "rel_d", "rel_gap", "rel_kkt")] + [("iteration", C.c_int64)]
+
+
+class pdhg_info(C.Structure):
+    _fields_ = [
+        ("norm_estimate", C.c_double), ("eta", C.c_double), ("omega", C.c_double), ("tau", C.c_double),
+        ("sigma", C.c_double), ("iterations", C.c_int64), ("since_restart", C.c_int64), ("restarts", C.c_int64),
+        ("evaluations", C.c_int64), ("snapshots", C.c_int64), ("last_rel_kkt", C.c_double),
+        ("precision_now", C.c_int), ("converged", C.c_int), ("kernel_ms_primal", C.c_double),
+        ("kernel_ms_dual", C.c_double), ("kernel_launches_primal", C.c_int64), ("kernel_launches_dual", C.c_int64),
+    ]
+
+
+class pdhg_trace_rec(C.Structure):
+    _fields_ = [("iteration", C.c_int64), ("kind", C.c_int32), ("candidate", C.c_int32), ("omega", C.c_double),
+                ("rel_kkt", C.c_double)]
+
+
+class PDHGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"PDHG_{name}: {msg}")
+
+
+_lib = None
+_P = C.c_void_p
+
+# every exported symbol of include/pdhg.h with its ctypes signature
+SIGNATURES = {
+    "pdhg_default_options": (None, [C.POINTER(pdhg_options)]),
+    "pdhg_create": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P, C.POINTER(pdhg_options), _P,
+                              C.POINTER(_P)]),
+    "pdhg_destroy": (None, [_P]),
+    "pdhg_iterate": (C.c_int, [_P, C.c_int64, C.c_double, C.POINTER(C.c_int64)]),
+    "pdhg_kkt": (C.c_int, [_P, C.c_int, C.POINTER(pdhg_kkt_info)]),
+    "pdhg_get_solution": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int]),
+    "pdhg_snapshot_poll": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+    "pdhg_snapshot": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "pdhg_get_info": (C.c_int, [_P, C.POINTER(pdhg_info)]),
+    "pdhg_get_trace": (C.c_int, [_P, C.POINTER(pdhg_trace_rec), C.c_int64, C.POINTER(C.c_int64)]),
+    "pdhg_last_error": (C.c_char_p, [_P]),
+}
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libpdhg.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpdhg.so not built ({path}); run __graft_entry__.build() or "
+                           "python paper_2510_24429_b300/build.py")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, ctx=None):
+    if status != PDHG_OK:
+        raise PDHGError(status, load().pdhg_last_error(ctx).decode())
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _prep(a, dtype, keep: list):
+    """Return (pointer, on_device) for an input array; keeps converted copies alive."""
+    if a is None:
+        return None, False
+    if _is_torch(a):
+        import torch
+
+        tdt = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32}[dtype]
+        t = a.to(tdt).contiguous()
+        keep.append(t)
+        return t.data_ptr(), t.is_cuda
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    keep.append(arr)
+    return arr.ctypes.data, False
+
+
+def _out_ptr(a):
+    if a is None:
+        return None, False
+    if _is_torch(a):
+        import torch
+
+        if not a.is_contiguous() or a.dtype != torch.float64:
+            raise ValueError("output tensors must be contiguous float64")
+        return a.data_ptr(), a.is_cuda
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise ValueError("output arrays must be contiguous float64 numpy arrays")
+    return a.ctypes.data, False
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one Python function per entry point
+# ---------------------------------------------------------------------------
+
+def pdhg_default_options(**overrides) -> pdhg_options:
+    o = pdhg_options()
+    load().pdhg_default_options(C.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k) or k == "reserved":
+            raise KeyError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def pdhg_create(m, n, row_ptr, col_idx, val, b, c, x0=None, y0=None, opt: pdhg_options | None = None,
+                stream=None) -> int:
+    lib = load()
+    keep: list = []
+    ptrs = [_prep(row_ptr, np.int64, keep), _prep(col_idx, np.int32, keep), _prep(val, np.float64, keep),
+            _prep(b, np.float64, keep), _prep(c, np.float64, keep), _prep(x0, np.float64, keep),
+            _prep(y0, np.float64, keep)]
+    dev = {d for p, d in ptrs if p is not None}
+    if len(dev) > 1:
+        raise ValueError("inputs must be all on the host or all on the device")
+    if opt is None:
+        opt = pdhg_default_options()
+    opt.inputs_on_device = int(dev == {True})
+    nnz = int(len(val))
+    if stream is None and opt.inputs_on_device:
+        import torch
+
+        stream = torch.cuda.current_stream().cuda_stream
+    out = C.c_void_p()
+    st = lib.pdhg_create(int(m), int(n), nnz, *[p for p, _ in ptrs], C.byref(opt),
+                         C.c_void_p(stream) if stream else None, C.byref(out))
+    _check(st, None)
+    return out.value
+
+
+def pdhg_destroy(ctx):
+    if ctx:
+        load().pdhg_destroy(ctx)
+
+
+def pdhg_iterate(ctx, max_iters: int, tol: float = 0.0, raise_on_not_converged: bool = False):
+    """Returns (status, iterations run)."""
+    done = C.c_int64()
+    st = load().pdhg_iterate(ctx, int(max_iters), float(tol), C.byref(done))
+    if st not in (PDHG_OK, PDHG_ERR_NOT_CONVERGED) or (raise_on_not_converged and st != PDHG_OK):
+        _check(st, ctx)
+    return st, done.value
+
+
+def pdhg_kkt(ctx, which: int = PDHG_CURRENT) -> dict:
+    info = pdhg_kkt_info()
+    _check(load().pdhg_kkt(ctx, int(which), C.byref(info)), ctx)
+    return {k: getattr(info, k) for k, _ in pdhg_kkt_info._fields_}
+
+
+def pdhg_get_solution(ctx, which=PDHG_CURRENT, x=None, y=None, z=None):
+    ptrs = [_out_ptr(a) for a in (x, y, z)]
+    dev = {d for p, d in ptrs if p is not None}
+    if len(dev) > 1:
+        raise ValueError("outputs must be all on the host or all on the device")
+    _check(load().pdhg_get_solution(ctx, int(which), *[p for p, _ in ptrs], int(dev == {True})), ctx)
+
+
+def pdhg_snapshot_poll(ctx):
+    cnt, ready = C.c_int64(), C.c_int()
+    _check(load().pdhg_snapshot_poll(ctx, C.byref(cnt), C.byref(ready)), ctx)
+    return cnt.value, bool(ready.value)
+
+
+def pdhg_snapshot(ctx, x=None, y=None, z=None):
+    ptrs = [_out_ptr(a) for a in (x, y, z)]
+    if any(d for _, d in ptrs):
+        raise ValueError("snapshot buffers are host arrays")
+    it, rel = C.c_int64(), C.c_double()
+    _check(load().pdhg_snapshot(ctx, *[p for p, _ in ptrs], C.byref(it), C.byref(rel)), ctx)
+    return it.value, rel.value
+
+
+def pdhg_get_info(ctx) -> dict:
+    info = pdhg_info()
+    _check(load().pdhg_get_info(ctx, C.byref(info)), ctx)
+    return {k: getattr(info, k) for k, _ in pdhg_info._fields_}
+
+
+def pdhg_get_trace(ctx) -> list[dict]:
+    lib = load()
+    cnt = C.c_int64()
+    _check(lib.pdhg_get_trace(ctx, None, 0, C.byref(cnt)), ctx)
+    recs = (pdhg_trace_rec * max(1, cnt.value))()
+    _check(lib.pdhg_get_trace(ctx, recs, cnt.value, C.byref(cnt)), ctx)
+    return [{k: getattr(r, k) for k, _ in pdhg_trace_rec._fields_} for r in recs[: cnt.value]]
+
+
+def pdhg_last_error(ctx=None) -> str:
+    return load().pdhg_last_error(ctx).decode()
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Solver:
+    """One LP resident on the GPU: ``Solver(m, n, row_ptr, col_idx, val, b, c, **options)``."""
+
+    def __init__(self, m, n, row_ptr, col_idx, val, b, c, x0=None, y0=None, stream=None, **options):
+        self.m, self.n = int(m), int(n)
+        self.ctx = None
+        self.ctx = pdhg_create(m, n, row_ptr, col_idx, val, b, c, x0, y0, pdhg_default_options(**options), stream)
+
+    @classmethod
+    def from_lp(cls, lp, **options):
+        return cls(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, **options)
+
+    def iterate(self, max_iters, tol=0.0):
+        return pdhg_iterate(self.ctx, max_iters, tol)
+
+    def kkt(self, which=PDHG_CURRENT):
+        return pdhg_kkt(self.ctx, which)
+
+    def solution(self, which=PDHG_CURRENT):
+        x, y, z = np.empty(self.n), np.empty(self.m), np.empty(self.n)
+        pdhg_get_solution(self.ctx, which, x, y, z)
+        return x, y, z
+
+    def snapshot(self):
+        x, y, z = np.empty(self.n), np.empty(self.m), np.empty(self.n)
+        it, rel = pdhg_snapshot(self.ctx, x, y, z)
+        return dict(iteration=it, rel_kkt=rel, x=x, y=y, z=z)
+
+    def snapshot_poll(self):
+        return pdhg_snapshot_poll(self.ctx)
+
+    def info(self):
+        return pdhg_get_info(self.ctx)
+
+    def trace(self):
+        return pdhg_get_trace(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            pdhg_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,48 @@
+"""Shared helpers of the GPU parity tests: build the oracle and the CUDA solver
+on the same seeded LP with the same options, and compare results."""
+import numpy as np
+
+from oracle import pdhg_oracle as O
+from paper_2510_24429_b300 import pdhg as P
+
+# option names shared by the oracle's Options and the C ABI's pdhg_options
+SHARED = ("ruiz_iters", "pock_chambolle", "pc_alpha", "power_iters", "step_factor", "restarts", "primal_weight",
+          "eval_every", "beta_suff", "beta_nec", "beta_art", "theta", "eps_cross", "eps_factor", "snapshot_every")
+
+TINY_PLAIN = dict(pock_chambolle=False, restarts=False, primal_weight=False)  # Ruiz only, fixed step, omega = 1
+
+
+def pair(lp, x0=None, y0=None, **opts):
+    """(oracle, solver) on the same LP and options."""
+    oopt = O.Options(**opts)
+    orc = O.Oracle(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, oopt, x0=x0, y0=y0)
+    copts = {k: (int(v) if isinstance(v, bool) else v) for k, v in ((k, getattr(oopt, k)) for k in SHARED)}
+    sol = P.Solver(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, x0=x0, y0=y0, **copts)
+    return orc, sol
+
+
+def rel_err(a, b):
+    """Relative error ||a - b|| / ||b|| (absolute when b is zero)."""
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def max_rel_err(a, b):
+    """Largest elementwise error relative to the largest magnitude of b."""
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    scale = float(np.max(np.abs(b))) if b.size else 1.0
+    return float(np.max(np.abs(a - b)) / (scale if scale > 0 else 1.0)) if b.size else 0.0
+
+
+def assert_iterates_close(sol, orc, tol, which=P.PDHG_CURRENT):
+    x, y, z = sol.solution(which)
+    if which == P.PDHG_CURRENT:
+        xo, yo, zo = orc.solution()
+    elif which == P.PDHG_AVERAGE:
+        xo, yo, zo = orc.unscale(orc.x_avg, orc.y_avg)
+    else:
+        xo, yo, zo = orc.unscale(orc.x_r, orc.y_r)
+    for name, a, b in (("x", x, xo), ("y", y, yo), ("z", z, zo)):
+        e1, e2 = rel_err(a, b), max_rel_err(a, b)
+        assert e1 <= tol and e2 <= tol, f"{name}: rel {e1:.3e} max-rel {e2:.3e} > {tol:.1e}"

@@ -1,0 +1,110 @@
+"""Host-side checks of the C ABI: the library loads, exports every function
+include/pdhg.h declares, the ctypes structs match the C layout, and argument
+validation rejects malformed input before any device work (no GPU needed)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2510_24429_b300 import build as B
+from paper_2510_24429_b300 import pdhg as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pdhg.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return P.load()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"PDHG_API\s+[\w\s\*]+?\b(pdhg_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared_functions()
+    assert len(declared) >= 11
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (pdhg_\w+)", out))
+    assert set(declared) <= exported, set(declared) - exported
+    assert set(declared) == set(P.SIGNATURES), set(declared) ^ set(P.SIGNATURES)
+    for name in declared:
+        assert hasattr(lib, name)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    structs = {"pdhg_options": P.pdhg_options, "pdhg_kkt_info": P.pdhg_kkt_info, "pdhg_info": P.pdhg_info,
+               "pdhg_trace_rec": P.pdhg_trace_rec}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdhg.h"', "int main(void) {"]
+    for sname, cls in structs.items():
+        lines.append(f'printf("{sname} size %zu\\n", sizeof({sname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{sname}.{f} %zu\\n", offsetof({sname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                                   check=True).stdout.splitlines())
+    for sname, cls in structs.items():
+        assert int(got[f"{sname} size"]) == C.sizeof(cls), sname
+        for f, _ in cls._fields_:
+            assert int(got[f"{sname}.{f}"]) == getattr(cls, f).offset, (sname, f)
+
+
+def test_default_options(lib):
+    o = P.pdhg_default_options()
+    assert (o.ruiz_iters, o.pock_chambolle, o.power_iters, o.eval_every) == (10, 1, 100, 64)
+    assert (o.step_factor, o.beta_suff, o.beta_nec, o.beta_art, o.theta) == (0.9, 0.2, 0.8, 0.36, 0.5)
+    assert o.precision == P.PDHG_FP64 and o.restarts == 1 and o.primal_weight == 1
+    with pytest.raises(KeyError):
+        P.pdhg_default_options(no_such_option=1)
+
+
+def _tiny_csr():
+    # A = [[1, 2, 0], [0, 1, 1]]
+    return (np.array([0, 2, 4], np.int64), np.array([0, 1, 1, 2], np.int32), np.array([1.0, 2.0, 1.0, 1.0]),
+            np.array([3.0, 2.0]), np.array([1.0, 1.0, 1.0]))
+
+
+@pytest.mark.parametrize("mutate,status", [
+    (lambda rp, ci, v, b, c: (np.array([0, 2, 5], np.int64), ci, v, b, c), P.PDHG_ERR_INVALID),  # rp[m] != nnz
+    (lambda rp, ci, v, b, c: (rp, np.array([0, 3, 1, 2], np.int32), v, b, c), P.PDHG_ERR_INVALID),  # col out of range
+    (lambda rp, ci, v, b, c: (rp, np.array([1, 0, 1, 2], np.int32), v, b, c), P.PDHG_ERR_INVALID),  # unsorted
+    (lambda rp, ci, v, b, c: (rp, np.array([1, 1, 1, 2], np.int32), v, b, c), P.PDHG_ERR_INVALID),  # duplicate
+    (lambda rp, ci, v, b, c: (np.array([0, 3, 2], np.int64), ci, v, b, c), P.PDHG_ERR_INVALID),  # decreasing rp
+    (lambda rp, ci, v, b, c: (rp, ci, v, b, np.array([1.0, np.nan, 1.0])), P.PDHG_ERR_NUMERIC),  # NaN in c
+    (lambda rp, ci, v, b, c: (rp, ci, np.array([1.0, np.inf, 1.0, 1.0]), b, c), P.PDHG_ERR_NUMERIC),  # Inf in A
+])
+def test_invalid_input_rejected_before_device_work(lib, mutate, status):
+    rp, ci, v, b, c = mutate(*_tiny_csr())
+    with pytest.raises(P.PDHGError) as ei:
+        P.pdhg_create(2, 3, rp, ci, v, b, c)
+    assert ei.value.status == status
+    assert P.pdhg_last_error(None)
+
+
+def test_bad_sizes_and_options(lib):
+    rp, ci, v, b, c = _tiny_csr()
+    with pytest.raises(P.PDHGError) as ei:
+        P.pdhg_create(0, 3, np.array([0], np.int64), ci[:0], v[:0], b[:0], c)
+    assert ei.value.status == P.PDHG_ERR_INVALID
+    for bad in (dict(eval_every=0), dict(eps_factor=1.5), dict(pc_alpha=3.0), dict(power_iters=0),
+                dict(precision=7)):
+        with pytest.raises(P.PDHGError) as ei:
+            P.pdhg_create(2, 3, rp, ci, v, b, c, opt=P.pdhg_default_options(**bad))
+        assert ei.value.status == P.PDHG_ERR_INVALID, bad
+
+
+def test_null_context_is_safe(lib):
+    lib.pdhg_destroy(None)
+    assert lib.pdhg_iterate(None, 1, 0.0, None) == P.PDHG_ERR_INVALID
+    assert lib.pdhg_kkt(None, 0, None) == P.PDHG_ERR_INVALID
+    assert lib.pdhg_snapshot(None, None, None, None, None, None) == P.PDHG_ERR_INVALID
