@@ -68,13 +68,29 @@ struct TraceRec {
 
 constexpr int TRACE_CAP = 65536;
 
-// CSR view (int32 indices; rows of the stored matrix)
-struct Csr {
+// Device layout of one copy of the scaled matrix (Ahat, or Ahat^T).
+//
+// Rows are stored in order of decreasing length (the engine permutes the
+// variables and constraints internally to get there). The leading n_long rows
+// (at least `long_row_min` entries each) are plain CSR and are reduced by one
+// warp per row. The remaining rows are cut into slices of 32 consecutive
+// rows; a slice is padded to the length of its first (longest) row and stored
+// column-major, so entry e of the slice's row `lane` sits at
+// soff[s] + 32 e + lane and one thread per row reads fully coalesced
+// 128-byte index and 256-byte value lines. Padding slots hold value 0 and
+// column 0. A "unit" is one long row or one slice; units are numbered long
+// rows first.
+struct Hyb {
   int rows = 0, cols = 0;
-  long long nnz = 0;
-  int* rp = nullptr;
-  int* ci = nullptr;
-  double* v = nullptr;
+  int n_long = 0;
+  int n_slices = 0;
+  long long nnz = 0;    // stored entries (without padding)
+  long long slots = 0;  // entry slots including padding
+  long long* loff = nullptr;  // [n_long + 1] offsets of the long rows
+  long long* soff = nullptr;  // [n_slices + 1] offsets of the slices
+  int* ci = nullptr;          // [slots] column index (internal numbering)
+  double* v = nullptr;        // [slots] value
+  int units() const { return n_long + n_slices; }
 };
 
 // ---------------------------------------------------------------------------

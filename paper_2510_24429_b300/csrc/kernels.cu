@@ -1,11 +1,16 @@
 // CUDA kernels of the PDHG engine (sm_103a).
 //
 // The iteration is bandwidth bound: each half-step streams one copy of the
-// scaled matrix (CSR of Ahat for the dual step, CSR of Ahat^T for the primal
-// step) exactly once, gathers one vector, and fuses the vector update of the
-// step into the epilogue of the row reduction, so the step's vectors are read
-// and written once. Tensor cores play no part: SpMV is not a dense
-// contraction.
+// scaled matrix (Ahat for the dual step, Ahat^T for the primal step) exactly
+// once, gathers one vector, and fuses the vector update of the step into the
+// epilogue of the row reduction, so the step's vectors are read and written
+// once. Tensor cores play no part: SpMV is not a dense contraction.
+//
+// Cache policy: everything that is touched once per half-step (matrix
+// indices and values, the step's own vectors) is loaded and stored with the
+// streaming (evict-first) policy, so that the vector the next half-step
+// gathers (xbar, written by the primal step; y, written by the dual step)
+// stays resident in the 126 MB L2.
 #include <math.h>
 
 #include "common.cuh"
@@ -15,70 +20,113 @@ namespace pdhg {
 
 namespace {
 
-constexpr int TPB = 256;
-
 __device__ __forceinline__ double relu(double v) { return v < 0.0 ? 0.0 : v; }  // NaN passes through
 
-template <int W>
-__device__ __forceinline__ double group_max(double v) {
-#pragma unroll
-  for (int off = W / 2; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off, W));
-  return v;
-}
-
-// Every group of LPR lanes owns one row per pass; a warp handles 32/LPR rows
-// per pass and all lanes of a warp make the same number of passes, so the
-// group shuffles always run with the full warp.
-template <int LPR, class Fn>
-__device__ __forceinline__ void for_each_row(int nrows, Fn&& fn) {
-  constexpr int RPW = 32 / LPR;
+// Visit every row of M once. Each warp takes units (a long row, or a slice of
+// 32 rows) in a grid-stride loop; a long row is reduced across the warp, a
+// slice row by its own lane. `op` sees begin(r) before the row's entries
+// (to issue its epilogue loads early), entry(acc, k, r) for every slot k of
+// the row (padding included: value 0, column 0) and finish(r, acc) after.
+// For long rows only lane 0 calls begin/finish. MAX selects the warp
+// combine of partial results (max instead of sum).
+template <bool MAX, class Op>
+__device__ __forceinline__ void hyb_rows(const Hyb& H, Op& op) {
   const int lane = threadIdx.x & 31;
-  const int sub = lane / LPR, gl = lane % LPR;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long base = warp * RPW; base < nrows; base += nwarps * RPW) {
-    const long long row = base + sub;
-    fn((int)row, row < nrows, gl);
+  const int gwarp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
+  const int units = H.n_long + H.n_slices;
+  for (int u = gwarp; u < units; u += nwarps) {
+    if (u < H.n_long) {
+      const long long beg = H.loff[u], end = H.loff[u + 1];
+      if (lane == 0) op.begin(u);
+      double acc = 0.0;
+#pragma unroll 4
+      for (long long k = beg + lane; k < end; k += 32) acc = op.entry(acc, k, u);
+      acc = MAX ? warp_max(acc) : warp_sum(acc);
+      if (lane == 0) op.finish(u, acc);
+    } else {
+      const int s = u - H.n_long;
+      const int r = H.n_long + s * 32 + lane;
+      const long long base = H.soff[s];
+      const int L = (int)((H.soff[s + 1] - base) >> 5);
+      const bool valid = r < H.rows;
+      if (valid) op.begin(r);
+      double acc = 0.0;
+      long long k = base + lane;
+#pragma unroll 4
+      for (int e = 0; e < L; ++e, k += 32) acc = op.entry(acc, k, r);
+      if (valid) op.finish(r, acc);
+    }
   }
 }
 
-// Row dot product sum_k M_rk vec[col_k]; result valid in group lane 0.
-template <int LPR>
-__device__ __forceinline__ double row_dot(const Csr& M, int row, bool valid, int gl, const double* __restrict__ vec) {
-  double acc = 0.0;
-  if (valid) {
-    const int beg = __ldg(M.rp + row), end = __ldg(M.rp + row + 1);
-    for (int k = beg + gl; k < end; k += LPR) acc += __ldg(M.v + k) * __ldg(vec + __ldg(M.ci + k));
+// acc + a_k * vec[col_k] with the streaming policy on the matrix
+struct DotEntry {
+  const int* __restrict__ ci;
+  const double* __restrict__ v;
+  const double* __restrict__ vec;
+  __device__ __forceinline__ double entry(double acc, long long k, int) const {
+    const int c = __ldcs(ci + k);
+    return acc + __ldcs(v + k) * __ldg(vec + c);
   }
-  return group_sum<LPR>(acc);
-}
+};
 
 // ---------------------------------------------------------------------------
 // setup kernels
 // ---------------------------------------------------------------------------
-template <int LPR>
-__global__ void __launch_bounds__(TPB) k_row_absmax(Csr M, double* __restrict__ out) {
-  for_each_row<LPR>(M.rows, [&](int r, bool valid, int gl) {
-    double mx = 0.0;
-    if (valid)
-      for (int k = M.rp[r] + gl; k < M.rp[r + 1]; k += LPR) mx = fmax(mx, fabs(M.v[k]));
-    mx = group_max<LPR>(mx);
-    if (valid && gl == 0) out[r] = mx;
-  });
+struct AbsMaxOp {
+  const double* __restrict__ v;
+  double* __restrict__ out;
+  __device__ __forceinline__ void begin(int) {}
+  __device__ __forceinline__ double entry(double acc, long long k, int) const { return fmax(acc, fabs(v[k])); }
+  __device__ __forceinline__ void finish(int r, double acc) { out[r] = acc; }
+};
+
+__global__ void __launch_bounds__(TPB) k_row_absmax(Hyb M, double* __restrict__ out) {
+  AbsMaxOp op{M.v, out};
+  hyb_rows<true>(M, op);
 }
 
-template <int LPR>
-__global__ void __launch_bounds__(TPB) k_row_abspow_sum(Csr M, double alpha, double* __restrict__ out) {
-  for_each_row<LPR>(M.rows, [&](int r, bool valid, int gl) {
-    double acc = 0.0;
-    if (valid)
-      for (int k = M.rp[r] + gl; k < M.rp[r + 1]; k += LPR) {
-        const double a = fabs(M.v[k]);
-        acc += alpha == 1.0 ? a : pow(a, alpha);
-      }
-    acc = group_sum<LPR>(acc);
-    if (valid && gl == 0) out[r] = acc;
-  });
+struct AbsPowSumOp {
+  const double* __restrict__ v;
+  double alpha;
+  double* __restrict__ out;
+  __device__ __forceinline__ void begin(int) {}
+  __device__ __forceinline__ double entry(double acc, long long k, int) const {
+    const double a = fabs(v[k]);
+    return acc + (alpha == 1.0 ? a : (a > 0.0 ? pow(a, alpha) : 0.0));
+  }
+  __device__ __forceinline__ void finish(int r, double acc) { out[r] = acc; }
+};
+
+__global__ void __launch_bounds__(TPB) k_row_abspow_sum(Hyb M, double alpha, double* __restrict__ out) {
+  AbsPowSumOp op{M.v, alpha, out};
+  hyb_rows<false>(M, op);
+}
+
+struct ScaleOp {
+  const int* __restrict__ ci;
+  double* __restrict__ v;
+  const double* __restrict__ rf;  // row factors of A (length m)
+  const double* __restrict__ sf;  // column factors of A (length n)
+  int transposed, rows;
+  __device__ __forceinline__ void begin(int) {}
+  __device__ __forceinline__ double entry(double acc, long long k, int r) const {
+    if (r < rows) {
+      const int c = ci[k];
+      const double ri = transposed ? rf[c] : rf[r];
+      const double sj = transposed ? sf[r] : sf[c];
+      v[k] = (ri * v[k]) * sj;
+    }
+    return acc;
+  }
+  __device__ __forceinline__ void finish(int, double) {}
+};
+
+__global__ void __launch_bounds__(TPB) k_scale(Hyb M, const double* __restrict__ r, const double* __restrict__ s,
+                                               int transposed) {
+  ScaleOp op{M.ci, M.v, r, s, transposed, M.rows};
+  hyb_rows<false>(M, op);
 }
 
 __global__ void k_inv_sqrt_or_one(const double* __restrict__ in, double* __restrict__ out, int len) {
@@ -86,20 +134,6 @@ __global__ void k_inv_sqrt_or_one(const double* __restrict__ in, double* __restr
     const double v = in[i];
     out[i] = v > 0.0 ? 1.0 / sqrt(v) : 1.0;
   }
-}
-
-template <int LPR>
-__global__ void __launch_bounds__(TPB) k_scale_csr(Csr M, const double* __restrict__ r, const double* __restrict__ s,
-                                                   int transposed) {
-  for_each_row<LPR>(M.rows, [&](int row, bool valid, int gl) {
-    if (!valid) return;
-    for (int k = M.rp[row] + gl; k < M.rp[row + 1]; k += LPR) {
-      const int col = M.ci[k];
-      const double ri = transposed ? r[col] : r[row];
-      const double sj = transposed ? s[row] : s[col];
-      M.v[k] = (ri * M.v[k]) * sj;
-    }
-  });
 }
 
 __global__ void k_mul_inplace(double* __restrict__ d, const double* __restrict__ f, int len) {
@@ -122,15 +156,23 @@ __global__ void k_fill(double* __restrict__ v, double val, long long len) {
     v[i] = val;
 }
 
-template <int LPR>
-__global__ void __launch_bounds__(TPB) k_spmv(Csr M, const double* __restrict__ x, double* __restrict__ y) {
-  for_each_row<LPR>(M.rows, [&](int r, bool valid, int gl) {
-    const double acc = row_dot<LPR>(M, r, valid, gl, x);
-    if (valid && gl == 0) y[r] = acc;
-  });
+struct SpmvOp : DotEntry {
+  double* __restrict__ out;
+  __device__ __forceinline__ void begin(int) {}
+  __device__ __forceinline__ void finish(int r, double acc) { out[r] = acc; }
+};
+
+__global__ void __launch_bounds__(TPB) k_spmv(Hyb M, const double* __restrict__ x, double* __restrict__ y) {
+  SpmvOp op;
+  op.ci = M.ci;
+  op.v = M.v;
+  op.vec = x;
+  op.out = y;
+  hyb_rows<false>(M, op);
 }
 
-__global__ void __launch_bounds__(TPB) k_sumsq_partials(const double* __restrict__ v, int len, double* __restrict__ partials) {
+__global__ void __launch_bounds__(TPB) k_sumsq_partials(const double* __restrict__ v, int len,
+                                                        double* __restrict__ partials) {
   double vals[1] = {0.0};
   const bool mx[1] = {false};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
@@ -147,7 +189,8 @@ __global__ void k_sum_partials(const double* __restrict__ partials, int nb, doub
   if (threadIdx.x == 0) *out = acc;
 }
 
-__global__ void k_div_by_norm(double* __restrict__ v, const double* __restrict__ w, const double* __restrict__ s2, int len) {
+__global__ void k_div_by_norm(double* __restrict__ v, const double* __restrict__ w, const double* __restrict__ s2,
+                              int len) {
   const double s = sqrt(*s2);
   if (!(s > 0.0)) return;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
@@ -175,37 +218,77 @@ __global__ void k_finish_setup(DevState* st, const double* __restrict__ scal, do
 // ---------------------------------------------------------------------------
 // the two fused half-steps of one PDHG iteration
 // ---------------------------------------------------------------------------
-template <int LPR>
-__global__ void __launch_bounds__(TPB) k_primal_step(Csr At, const double* __restrict__ y, const double* __restrict__ ch,
-                                                     double* __restrict__ x, double* __restrict__ xbar,
-                                                     double* __restrict__ xsum, const DevState* __restrict__ st,
-                                                     int accumulate) {
-  const double tau = st->tau;
-  for_each_row<LPR>(At.rows, [&](int j, bool valid, int gl) {
-    const double g = row_dot<LPR>(At, j, valid, gl, y);
-    if (valid && gl == 0) {
-      const double xj = x[j];
-      const double xn = relu(xj - tau * (ch[j] - g));
-      xbar[j] = 2.0 * xn - xj;
-      x[j] = xn;
-      if (accumulate) xsum[j] += xn;
-    }
-  });
+struct PrimalOp : DotEntry {
+  const double* __restrict__ ch;
+  double* __restrict__ x;
+  double* __restrict__ xbar;
+  double* __restrict__ xsum;
+  double tau;
+  int accumulate;
+  double xj, cj, sj;
+  __device__ __forceinline__ void begin(int j) {
+    xj = __ldcs(x + j);
+    cj = __ldcs(ch + j);
+    sj = accumulate ? __ldcs(xsum + j) : 0.0;
+  }
+  __device__ __forceinline__ void finish(int j, double g) {
+    const double xn = relu(xj - tau * (cj - g));
+    xbar[j] = 2.0 * xn - xj;  // default policy: gathered by the dual step next
+    __stcs(x + j, xn);
+    if (accumulate) __stcs(xsum + j, sj + xn);
+  }
+};
+
+__global__ void __launch_bounds__(TPB) k_primal_step(Hyb At, const double* __restrict__ y,
+                                                     const double* __restrict__ ch, double* __restrict__ x,
+                                                     double* __restrict__ xbar, double* __restrict__ xsum,
+                                                     const DevState* __restrict__ st, int accumulate) {
+  PrimalOp op;
+  op.ci = At.ci;
+  op.v = At.v;
+  op.vec = y;
+  op.ch = ch;
+  op.x = x;
+  op.xbar = xbar;
+  op.xsum = xsum;
+  op.tau = st->tau;
+  op.accumulate = accumulate;
+  hyb_rows<false>(At, op);
 }
 
-template <int LPR>
-__global__ void __launch_bounds__(TPB) k_dual_step(Csr A, const double* __restrict__ xbar, const double* __restrict__ bh,
-                                                   double* __restrict__ y, double* __restrict__ ysum,
-                                                   const DevState* __restrict__ st, int accumulate) {
-  const double sigma = st->sigma;
-  for_each_row<LPR>(A.rows, [&](int i, bool valid, int gl) {
-    const double h = row_dot<LPR>(A, i, valid, gl, xbar);
-    if (valid && gl == 0) {
-      const double yn = y[i] + sigma * (bh[i] - h);
-      y[i] = yn;
-      if (accumulate) ysum[i] += yn;
-    }
-  });
+struct DualOp : DotEntry {
+  const double* __restrict__ bh;
+  double* __restrict__ y;
+  double* __restrict__ ysum;
+  double sigma;
+  int accumulate;
+  double yi, bi, si;
+  __device__ __forceinline__ void begin(int i) {
+    yi = y[i];
+    bi = __ldcs(bh + i);
+    si = accumulate ? __ldcs(ysum + i) : 0.0;
+  }
+  __device__ __forceinline__ void finish(int i, double h) {
+    const double yn = yi + sigma * (bi - h);
+    y[i] = yn;  // default policy: gathered by the primal step next
+    if (accumulate) __stcs(ysum + i, si + yn);
+  }
+};
+
+__global__ void __launch_bounds__(TPB) k_dual_step(Hyb A, const double* __restrict__ xbar,
+                                                   const double* __restrict__ bh, double* __restrict__ y,
+                                                   double* __restrict__ ysum, const DevState* __restrict__ st,
+                                                   int accumulate) {
+  DualOp op;
+  op.ci = A.ci;
+  op.v = A.v;
+  op.vec = xbar;
+  op.bh = bh;
+  op.y = y;
+  op.ysum = ysum;
+  op.sigma = st->sigma;
+  op.accumulate = accumulate;
+  hyb_rows<false>(A, op);
 }
 
 __global__ void k_add_counters(DevState* st, long long dk) {
@@ -216,9 +299,9 @@ __global__ void k_add_counters(DevState* st, long long dk) {
 // ---------------------------------------------------------------------------
 // evaluation
 // ---------------------------------------------------------------------------
-__global__ void k_make_average(const double* __restrict__ xs, const double* __restrict__ ys, const double* __restrict__ x,
-                               const double* __restrict__ y, double* __restrict__ xa, double* __restrict__ ya, int n,
-                               int m, const DevState* __restrict__ st) {
+__global__ void k_make_average(const double* __restrict__ xs, const double* __restrict__ ys,
+                               const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ xa,
+                               double* __restrict__ ya, int n, int m, const DevState* __restrict__ st) {
   const long long t = st->t;
   const double td = (double)t;
   const int len = n > m ? n : m;
@@ -228,74 +311,102 @@ __global__ void k_make_average(const double* __restrict__ xs, const double* __re
   }
 }
 
-template <int LPR>
-__global__ void __launch_bounds__(TPB) k_eval_dual(Csr At, const double* __restrict__ py, const double* __restrict__ ch,
-                                                   const double* __restrict__ dc, const double* __restrict__ px,
-                                                   const double* __restrict__ xr, double* __restrict__ partials) {
-  double v[6] = {0, 0, 0, 0, 0, 0};
-  const bool mx[6] = {false, false, true, false, false, false};
-  for_each_row<LPR>(At.rows, [&](int j, bool valid, int gl) {
-    const double g = row_dot<LPR>(At, j, valid, gl, py);
-    if (valid && gl == 0) {
-      const double c = ch[j];
-      const double rd = relu(g - c);
-      const double zh = relu(c - g);
-      const double rdu = rd / dc[j];
-      const double xj = px[j];
-      v[0] += rd * rd;
-      v[1] += rdu * rdu;
-      v[2] = fmax(v[2], fabs(rdu));
-      v[3] += c * xj;
-      v[4] += xj * zh;
-      if (xr) {
-        const double d = xj - xr[j];
-        v[5] += d * d;
-      }
+struct EvalDualOp : DotEntry {
+  const double* __restrict__ ch;
+  const double* __restrict__ dc;
+  const double* __restrict__ px;
+  const double* __restrict__ xr;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  __device__ __forceinline__ void begin(int) {}
+  __device__ __forceinline__ void finish(int j, double g) {
+    const double c = ch[j];
+    const double rd = relu(g - c);
+    const double zh = relu(c - g);
+    const double rdu = rd / dc[j];
+    const double xj = px[j];
+    acc[0] += rd * rd;
+    acc[1] += rdu * rdu;
+    acc[2] = fmax(acc[2], fabs(rdu));
+    acc[3] += c * xj;
+    acc[4] += xj * zh;
+    if (xr) {
+      const double d = xj - xr[j];
+      acc[5] += d * d;
     }
-  });
-  block_reduce<6>(v, mx);
+  }
+};
+
+__global__ void __launch_bounds__(TPB) k_eval_dual(Hyb At, const double* __restrict__ py,
+                                                   const double* __restrict__ ch, const double* __restrict__ dc,
+                                                   const double* __restrict__ px, const double* __restrict__ xr,
+                                                   double* __restrict__ partials) {
+  EvalDualOp op;
+  op.ci = At.ci;
+  op.v = At.v;
+  op.vec = py;
+  op.ch = ch;
+  op.dc = dc;
+  op.px = px;
+  op.xr = xr;
+  hyb_rows<false>(At, op);
+  const bool mx[6] = {false, false, true, false, false, false};
+  block_reduce<6>(op.acc, mx);
   if (threadIdx.x == 0) {
     double* p = partials + (size_t)blockIdx.x * NQ;
-    p[Q_RD2S] = v[0];
-    p[Q_RD2U] = v[1];
-    p[Q_RDINF] = v[2];
-    p[Q_CX] = v[3];
-    p[Q_XZ] = v[4];
-    p[Q_DX2] = v[5];
+    p[Q_RD2S] = op.acc[0];
+    p[Q_RD2U] = op.acc[1];
+    p[Q_RDINF] = op.acc[2];
+    p[Q_CX] = op.acc[3];
+    p[Q_XZ] = op.acc[4];
+    p[Q_DX2] = op.acc[5];
   }
 }
 
-template <int LPR>
-__global__ void __launch_bounds__(TPB) k_eval_primal(Csr A, const double* __restrict__ px, const double* __restrict__ bh,
-                                                     const double* __restrict__ dr, const double* __restrict__ py,
-                                                     const double* __restrict__ yr, double* __restrict__ partials) {
-  double v[5] = {0, 0, 0, 0, 0};
-  const bool mx[5] = {false, false, true, false, false};
-  for_each_row<LPR>(A.rows, [&](int i, bool valid, int gl) {
-    const double h = row_dot<LPR>(A, i, valid, gl, px);
-    if (valid && gl == 0) {
-      const double b = bh[i];
-      const double rp = b - h;
-      const double rpu = rp / dr[i];
-      const double yi = py[i];
-      v[0] += rp * rp;
-      v[1] += rpu * rpu;
-      v[2] = fmax(v[2], fabs(rpu));
-      v[3] += b * yi;
-      if (yr) {
-        const double d = yi - yr[i];
-        v[4] += d * d;
-      }
+struct EvalPrimalOp : DotEntry {
+  const double* __restrict__ bh;
+  const double* __restrict__ dr;
+  const double* __restrict__ py;
+  const double* __restrict__ yr;
+  double acc[5] = {0, 0, 0, 0, 0};
+  __device__ __forceinline__ void begin(int) {}
+  __device__ __forceinline__ void finish(int i, double h) {
+    const double b = bh[i];
+    const double rp = b - h;
+    const double rpu = rp / dr[i];
+    const double yi = py[i];
+    acc[0] += rp * rp;
+    acc[1] += rpu * rpu;
+    acc[2] = fmax(acc[2], fabs(rpu));
+    acc[3] += b * yi;
+    if (yr) {
+      const double d = yi - yr[i];
+      acc[4] += d * d;
     }
-  });
-  block_reduce<5>(v, mx);
+  }
+};
+
+__global__ void __launch_bounds__(TPB) k_eval_primal(Hyb A, const double* __restrict__ px,
+                                                     const double* __restrict__ bh, const double* __restrict__ dr,
+                                                     const double* __restrict__ py, const double* __restrict__ yr,
+                                                     double* __restrict__ partials) {
+  EvalPrimalOp op;
+  op.ci = A.ci;
+  op.v = A.v;
+  op.vec = px;
+  op.bh = bh;
+  op.dr = dr;
+  op.py = py;
+  op.yr = yr;
+  hyb_rows<false>(A, op);
+  const bool mx[5] = {false, false, true, false, false};
+  block_reduce<5>(op.acc, mx);
   if (threadIdx.x == 0) {
     double* p = partials + (size_t)blockIdx.x * NQ;
-    p[Q_RP2S] = v[0];
-    p[Q_RP2U] = v[1];
-    p[Q_RPINF] = v[2];
-    p[Q_BY] = v[3];
-    p[Q_DY2] = v[4];
+    p[Q_RP2S] = op.acc[0];
+    p[Q_RP2U] = op.acc[1];
+    p[Q_RPINF] = op.acc[2];
+    p[Q_BY] = op.acc[3];
+    p[Q_DY2] = op.acc[4];
   }
 }
 
@@ -437,55 +548,57 @@ __global__ void k_apply(const DevState* __restrict__ st, double* __restrict__ x,
   }
 }
 
-template <int LPR>
-__global__ void __launch_bounds__(TPB) k_pack_dual(Csr At, const double* __restrict__ px, const double* __restrict__ py,
+struct PackDualOp : DotEntry {
+  const int* __restrict__ perm;
+  const double* __restrict__ px;
+  const double* __restrict__ ch;
+  const double* __restrict__ dc;
+  double* __restrict__ ox;
+  double* __restrict__ oz;
+  __device__ __forceinline__ void begin(int) {}
+  __device__ __forceinline__ void finish(int j, double g) {
+    const int o = perm[j];
+    if (ox) ox[o] = dc[j] * px[j];
+    if (oz) oz[o] = relu(ch[j] - g) / dc[j];
+  }
+};
+
+__global__ void __launch_bounds__(TPB) k_pack_dual(Hyb At, const int* __restrict__ perm,
+                                                   const double* __restrict__ px, const double* __restrict__ py,
                                                    const double* __restrict__ ch, const double* __restrict__ dc,
                                                    double* __restrict__ ox, double* __restrict__ oz) {
-  for_each_row<LPR>(At.rows, [&](int j, bool valid, int gl) {
-    const double g = oz ? row_dot<LPR>(At, j, valid, gl, py) : 0.0;
-    if (valid && gl == 0) {
-      if (ox) ox[j] = dc[j] * px[j];
-      if (oz) oz[j] = relu(ch[j] - g) / dc[j];
-    }
-  });
+  PackDualOp op;
+  op.ci = At.ci;
+  op.v = At.v;
+  op.vec = py;
+  op.perm = perm;
+  op.px = px;
+  op.ch = ch;
+  op.dc = dc;
+  op.ox = ox;
+  op.oz = oz;
+  hyb_rows<false>(At, op);
 }
 
-__global__ void k_pack_y(const double* __restrict__ py, const double* __restrict__ dr, double* __restrict__ oy, int m) {
+__global__ void k_pack_y(const int* __restrict__ perm, const double* __restrict__ py, const double* __restrict__ dr,
+                         double* __restrict__ oy, int m) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
-    oy[i] = dr[i] * py[i];
+    oy[perm[i]] = dr[i] * py[i];
 }
-
-// dispatch on lanes-per-row
-#define PDHG_DISPATCH_LPR(lpr, KERNEL, GRID, STREAM, ...)                         \
-  switch (lpr) {                                                                 \
-    case 1: KERNEL<1><<<GRID, TPB, 0, STREAM>>>(__VA_ARGS__); break;             \
-    case 2: KERNEL<2><<<GRID, TPB, 0, STREAM>>>(__VA_ARGS__); break;             \
-    case 4: KERNEL<4><<<GRID, TPB, 0, STREAM>>>(__VA_ARGS__); break;             \
-    case 8: KERNEL<8><<<GRID, TPB, 0, STREAM>>>(__VA_ARGS__); break;             \
-    case 16: KERNEL<16><<<GRID, TPB, 0, STREAM>>>(__VA_ARGS__); break;           \
-    default: KERNEL<32><<<GRID, TPB, 0, STREAM>>>(__VA_ARGS__); break;           \
-  }
 
 }  // namespace
 
-int pick_lanes_per_row(double mean_row_len) {
-  int l = 1;
-  while (l < 32 && l * 1.5 < mean_row_len) l *= 2;
-  return l;
+void launch_row_absmax(const Hyb& M, double* out, int grid, cudaStream_t s) {
+  k_row_absmax<<<grid, TPB, 0, s>>>(M, out);
 }
-
-void launch_row_absmax(const Csr& M, int lpr, double* out, int grid, cudaStream_t s) {
-  PDHG_DISPATCH_LPR(lpr, k_row_absmax, grid, s, M, out);
-}
-void launch_row_abspow_sum(const Csr& M, int lpr, double alpha, double* out, int grid, cudaStream_t s) {
-  PDHG_DISPATCH_LPR(lpr, k_row_abspow_sum, grid, s, M, alpha, out);
+void launch_row_abspow_sum(const Hyb& M, double alpha, double* out, int grid, cudaStream_t s) {
+  k_row_abspow_sum<<<grid, TPB, 0, s>>>(M, alpha, out);
 }
 void launch_inv_sqrt_or_one(const double* in, double* out, int len, int grid, cudaStream_t s) {
   k_inv_sqrt_or_one<<<grid, TPB, 0, s>>>(in, out, len);
 }
-void launch_scale_csr(const Csr& M, int lpr, const double* r, const double* s, int transposed, int grid,
-                      cudaStream_t st) {
-  PDHG_DISPATCH_LPR(lpr, k_scale_csr, grid, st, M, r, s, transposed);
+void launch_scale(const Hyb& M, const double* r, const double* s, int transposed, int grid, cudaStream_t st) {
+  k_scale<<<grid, TPB, 0, st>>>(M, r, s, transposed);
 }
 void launch_mul_inplace(double* d, const double* f, int len, int grid, cudaStream_t s) {
   k_mul_inplace<<<grid, TPB, 0, s>>>(d, f, len);
@@ -499,8 +612,8 @@ void launch_div(double* out, const double* a, const double* b, int len, int grid
 void launch_fill(double* v, double val, long long len, int grid, cudaStream_t s) {
   k_fill<<<grid, TPB, 0, s>>>(v, val, len);
 }
-void launch_spmv(const Csr& M, int lpr, const double* x, double* y, int grid, cudaStream_t s) {
-  PDHG_DISPATCH_LPR(lpr, k_spmv, grid, s, M, x, y);
+void launch_spmv(const Hyb& M, const double* x, double* y, int grid, cudaStream_t s) {
+  k_spmv<<<grid, TPB, 0, s>>>(M, x, y);
 }
 void launch_sumsq(const double* v, int len, double* partials, int nb, double* out, cudaStream_t s) {
   k_sumsq_partials<<<nb, TPB, 0, s>>>(v, len, partials);
@@ -512,24 +625,24 @@ void launch_div_by_norm(double* v, const double* w, const double* s2, int len, i
 void launch_finish_setup(DevState* st, const double* scal, double step_factor, int primal_weight, cudaStream_t s) {
   k_finish_setup<<<1, 1, 0, s>>>(st, scal, step_factor, primal_weight);
 }
-void launch_primal_step(const Csr& At, int lpr, const double* y, const double* ch, double* x, double* xbar,
-                        double* xsum, const DevState* st, int accumulate, int grid, cudaStream_t s) {
-  PDHG_DISPATCH_LPR(lpr, k_primal_step, grid, s, At, y, ch, x, xbar, xsum, st, accumulate);
+void launch_primal_step(const Hyb& At, const double* y, const double* ch, double* x, double* xbar, double* xsum,
+                        const DevState* st, int accumulate, int grid, cudaStream_t s) {
+  k_primal_step<<<grid, TPB, 0, s>>>(At, y, ch, x, xbar, xsum, st, accumulate);
 }
-void launch_dual_step(const Csr& A, int lpr, const double* xbar, const double* bh, double* y, double* ysum,
+void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
                       const DevState* st, int accumulate, int grid, cudaStream_t s) {
-  PDHG_DISPATCH_LPR(lpr, k_dual_step, grid, s, A, xbar, bh, y, ysum, st, accumulate);
+  k_dual_step<<<grid, TPB, 0, s>>>(A, xbar, bh, y, ysum, st, accumulate);
 }
 void launch_add_counters(DevState* st, long long dk, cudaStream_t s) { k_add_counters<<<1, 1, 0, s>>>(st, dk); }
 void launch_make_average(const double* xs, const double* ys, const double* x, const double* y, double* xa,
                          double* ya, int n, int m, const DevState* st, int grid, cudaStream_t s) {
   k_make_average<<<grid, TPB, 0, s>>>(xs, ys, x, y, xa, ya, n, m, st);
 }
-void launch_eval_point(const Csr& A, int lprA, const Csr& At, int lprAt, const double* px, const double* py,
-                       const double* bh, const double* ch, const double* dr, const double* dc, const double* xr,
-                       const double* yr, double* partials, int nb, cudaStream_t s) {
-  PDHG_DISPATCH_LPR(lprAt, k_eval_dual, nb, s, At, py, ch, dc, px, xr, partials);
-  PDHG_DISPATCH_LPR(lprA, k_eval_primal, nb, s, A, px, bh, dr, py, yr, partials);
+void launch_eval_point(const Hyb& A, const Hyb& At, const double* px, const double* py, const double* bh,
+                       const double* ch, const double* dr, const double* dc, const double* xr, const double* yr,
+                       double* partials, int nb, cudaStream_t s) {
+  k_eval_dual<<<nb, TPB, 0, s>>>(At, py, ch, dc, px, xr, partials);
+  k_eval_primal<<<nb, TPB, 0, s>>>(A, px, bh, dr, py, yr, partials);
 }
 void launch_eval_finalize(const double* partials, int nb, EvalSums* out, cudaStream_t s) {
   k_eval_finalize<<<1, 32 * NQ, 0, s>>>(partials, nb, out);
@@ -540,11 +653,11 @@ void launch_apply(const DevState* st, double* x, double* y, const double* xa, co
                   double* yr, double* xs, double* ys, int n, int m, int grid, cudaStream_t s) {
   k_apply<<<grid, TPB, 0, s>>>(st, x, y, xa, ya, xr, yr, xs, ys, n, m);
 }
-void launch_pack_solution(const Csr& At, int lprAt, const double* px, const double* py, const double* ch,
-                          const double* dc, const double* dr, double* ox, double* oy, double* oz, int grid,
-                          cudaStream_t s) {
-  if (ox || oz) PDHG_DISPATCH_LPR(lprAt, k_pack_dual, grid, s, At, px, py, ch, dc, ox, oz);
-  if (oy) k_pack_y<<<grid, TPB, 0, s>>>(py, dr, oy, At.cols);
+void launch_pack_solution(const Hyb& At, const int* perm_x, const int* perm_y, const double* px, const double* py,
+                          const double* ch, const double* dc, const double* dr, double* ox, double* oy, double* oz,
+                          int grid, cudaStream_t s) {
+  if (ox || oz) k_pack_dual<<<grid, TPB, 0, s>>>(At, perm_x, px, py, ch, dc, ox, oz);
+  if (oy) k_pack_y<<<grid, TPB, 0, s>>>(perm_y, py, dr, oy, At.cols);
 }
 
 }  // namespace pdhg

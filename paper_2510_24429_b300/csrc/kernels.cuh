@@ -5,23 +5,22 @@
 
 namespace pdhg {
 
-// lanes per row used by a CSR kernel for a matrix with this mean row length
-int pick_lanes_per_row(double mean_row_len);
+constexpr int TPB = 256;  // threads per block of every row kernel
+constexpr int WARPS_PER_BLOCK = TPB / 32;
 
 // ---- setup (scaling, power iteration, vector helpers) ----------------------
-void launch_row_absmax(const Csr& M, int lpr, double* out, int grid, cudaStream_t s);
-void launch_row_abspow_sum(const Csr& M, int lpr, double alpha, double* out, int grid, cudaStream_t s);
+void launch_row_absmax(const Hyb& M, double* out, int grid, cudaStream_t s);
+void launch_row_abspow_sum(const Hyb& M, double alpha, double* out, int grid, cudaStream_t s);
 void launch_inv_sqrt_or_one(const double* in, double* out, int len, int grid, cudaStream_t s);
-// transposed == 0: M is A (rows i, cols j); 1: M is A^T (rows j, cols i).
+// transposed == 0: M is Ahat (rows i, cols j); 1: M is Ahat^T (rows j, cols i).
 // Every entry becomes (r_i * a_ij) * s_j, the same operation order in both
 // layouts so that the two copies of Ahat stay bit-identical.
-void launch_scale_csr(const Csr& M, int lpr, const double* r, const double* s, int transposed, int grid,
-                      cudaStream_t st);
+void launch_scale(const Hyb& M, const double* r, const double* s, int transposed, int grid, cudaStream_t st);
 void launch_mul_inplace(double* d, const double* f, int len, int grid, cudaStream_t s);
 void launch_mul(double* out, const double* a, const double* b, int len, int grid, cudaStream_t s);
 void launch_div(double* out, const double* a, const double* b, int len, int grid, cudaStream_t s);
 void launch_fill(double* v, double val, long long len, int grid, cudaStream_t s);
-void launch_spmv(const Csr& M, int lpr, const double* x, double* y, int grid, cudaStream_t s);
+void launch_spmv(const Hyb& M, const double* x, double* y, int grid, cudaStream_t s);
 // out[0] = sum v^2 (deterministic two-stage reduction through `partials`)
 void launch_sumsq(const double* v, int len, double* partials, int nb, double* out, cudaStream_t s);
 // v = w / sqrt(*s2) when *s2 > 0 (else v unchanged)
@@ -31,10 +30,10 @@ void launch_finish_setup(DevState* st, const double* scal, double step_factor, i
 
 // ---- iteration --------------------------------------------------------------
 // x' = max(0, x - tau (chat - Ahat^T y)); xbar = 2x' - x; x <- x'; xsum += x'
-void launch_primal_step(const Csr& At, int lpr, const double* y, const double* ch, double* x, double* xbar,
-                        double* xsum, const DevState* st, int accumulate, int grid, cudaStream_t s);
+void launch_primal_step(const Hyb& At, const double* y, const double* ch, double* x, double* xbar, double* xsum,
+                        const DevState* st, int accumulate, int grid, cudaStream_t s);
 // y' = y + sigma (bhat - Ahat xbar); y <- y'; ysum += y'
-void launch_dual_step(const Csr& A, int lpr, const double* xbar, const double* bh, double* y, double* ysum,
+void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
                       const DevState* st, int accumulate, int grid, cudaStream_t s);
 void launch_add_counters(DevState* st, long long dk, cudaStream_t s);
 
@@ -42,18 +41,20 @@ void launch_add_counters(DevState* st, long long dk, cudaStream_t s);
 void launch_make_average(const double* xs, const double* ys, const double* x, const double* y, double* xa,
                          double* ya, int n, int m, const DevState* st, int grid, cudaStream_t s);
 // Partial sums of one point into partials[nb][NQ]; xr/yr may be null (no
-// restart distances). Both sides use the same nb.
-void launch_eval_point(const Csr& A, int lprA, const Csr& At, int lprAt, const double* px, const double* py,
-                       const double* bh, const double* ch, const double* dr, const double* dc, const double* xr,
-                       const double* yr, double* partials, int nb, cudaStream_t s);
+// restart distances). Both sides use the same nb blocks.
+void launch_eval_point(const Hyb& A, const Hyb& At, const double* px, const double* py, const double* bh,
+                       const double* ch, const double* dr, const double* dc, const double* xr, const double* yr,
+                       double* partials, int nb, cudaStream_t s);
 void launch_eval_finalize(const double* partials, int nb, EvalSums* out, cudaStream_t s);
 void launch_init_restart_ref(DevState* st, cudaStream_t s);
 void launch_decide(DevState* st, TraceRec* trace, cudaStream_t s);
 void launch_apply(const DevState* st, double* x, double* y, const double* xa, const double* ya, double* xr,
                   double* yr, double* xs, double* ys, int n, int m, int grid, cudaStream_t s);
-// Unscaled (x, y, z) of a point: x = D_c xhat, y = D_r yhat, z = max(0, chat - Ahat^T yhat) / D_c.
-void launch_pack_solution(const Csr& At, int lprAt, const double* px, const double* py, const double* ch,
-                          const double* dc, const double* dr, double* ox, double* oy, double* oz, int grid,
-                          cudaStream_t s);
+// (x, y, z) on the problem as given, in the caller's numbering:
+// x[perm_x[j]] = D_c xhat_j, y[perm_y[i]] = D_r yhat_i,
+// z[perm_x[j]] = max(0, chat_j - (Ahat^T yhat)_j) / D_c_j.
+void launch_pack_solution(const Hyb& At, const int* perm_x, const int* perm_y, const double* px, const double* py,
+                          const double* ch, const double* dc, const double* dr, double* ox, double* oy, double* oz,
+                          int grid, cudaStream_t s);
 
 }  // namespace pdhg

@@ -1,8 +1,10 @@
 // Host engine behind the C ABI of include/pdhg.h.
 //
-// One context = one LP resident on one GPU. Setup validates and transposes the
-// CSR on the host (a deterministic counting sort), uploads both layouts, and
-// does everything else on the device: Ruiz and Pock-Chambolle scaling, the
+// One context = one LP resident on one GPU. Setup validates the CSR on the
+// host, renumbers rows and columns by decreasing length, builds the two
+// device layouts of the matrix (A and its transpose, each as long rows plus
+// 32-row column-major slices; see Hyb), uploads them, and does everything
+// else on the device: Ruiz and Pock-Chambolle scaling, the
 // power iteration for ||Ahat||_2, the primal weight, and the evaluation of the
 // starting point. The solve loop launches the two fused half-steps per
 // iteration and, every eval_every iterations, the evaluation kernels and the
@@ -28,7 +30,6 @@ using namespace pdhg;
 namespace {
 
 thread_local std::string g_create_error = "no error";
-constexpr int TPB = 256;
 constexpr int EV_POOL = 256;
 
 }  // namespace
@@ -39,8 +40,9 @@ struct pdhg_ctx {
   int device = 0, sms = 148;
   cudaStream_t stream = nullptr, side = nullptr;
   bool own_stream = false;
-  Csr A, At;
-  int lprA = 1, lprAt = 1;
+  Hyb A, At;
+  int* perm_x = nullptr;  // internal column -> caller's column
+  int* perm_y = nullptr;  // internal row -> caller's row
   double *b = nullptr, *c = nullptr, *bh = nullptr, *ch = nullptr, *dr = nullptr, *dc = nullptr;
   double *x = nullptr, *y = nullptr, *xbar = nullptr, *xsum = nullptr, *ysum = nullptr;
   double *xavg = nullptr, *yavg = nullptr, *xr = nullptr, *yr = nullptr;
@@ -107,11 +109,13 @@ int vec_grid(const pdhg_ctx* ctx, long long len) {
   return (int)std::max<long long>(1, std::min<long long>(g, (long long)ctx->sms * 8));
 }
 
-int row_grid(const pdhg_ctx* ctx, long long rows, int lpr) {
-  const long long rows_per_block = TPB / lpr;
-  long long g = (rows + rows_per_block - 1) / rows_per_block;
-  return (int)std::max<long long>(1, std::min<long long>(g, (long long)ctx->sms * 16));
+// one unit (long row or 32-row slice) per warp
+int unit_grid(const Hyb& H) {
+  return std::max(1, (H.units() + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
 }
+
+// grid-stride launches (setup and evaluation kernels)
+int stride_grid(const pdhg_ctx* ctx, const Hyb& H) { return std::min(unit_grid(H), ctx->sms * 8); }
 
 pdhg_status set_device(pdhg_ctx* ctx) {
   int cur = -1;
@@ -135,8 +139,8 @@ pdhg_status read_state(pdhg_ctx* ctx) {
 // Evaluate a point into *dst (EvalSums in device memory).
 void eval_point(pdhg_ctx* ctx, const double* px, const double* py, const double* xr, const double* yr,
                 EvalSums* dst) {
-  launch_eval_point(ctx->A, ctx->lprA, ctx->At, ctx->lprAt, px, py, ctx->bh, ctx->ch, ctx->dr, ctx->dc, xr, yr,
-                    ctx->partials, ctx->nb_eval, ctx->stream);
+  launch_eval_point(ctx->A, ctx->At, px, py, ctx->bh, ctx->ch, ctx->dr, ctx->dc, xr, yr, ctx->partials,
+                    ctx->nb_eval, ctx->stream);
   launch_eval_finalize(ctx->partials, ctx->nb_eval, dst, ctx->stream);
 }
 
@@ -162,8 +166,8 @@ pdhg_status take_snapshot(pdhg_ctx* ctx) {
   const double* px = avg ? ctx->xavg : ctx->x;
   const double* py = avg ? ctx->yavg : ctx->y;
   double* base = ctx->snap_dev[slot];
-  launch_pack_solution(ctx->At, ctx->lprAt, px, py, ctx->ch, ctx->dc, ctx->dr, base, base + ctx->n,
-                       base + ctx->n + ctx->m, vec_grid(ctx, ctx->n), ctx->stream);
+  launch_pack_solution(ctx->At, ctx->perm_x, ctx->perm_y, px, py, ctx->ch, ctx->dc, ctx->dr, base, base + ctx->n,
+                       base + ctx->n + ctx->m, stride_grid(ctx, ctx->At), ctx->stream);
   CK(ctx, cudaGetLastError());
   CK(ctx, cudaEventRecord(ctx->snap_packed[slot], ctx->stream));
   CK(ctx, cudaStreamWaitEvent(ctx->side, ctx->snap_packed[slot], 0));
@@ -176,52 +180,165 @@ pdhg_status take_snapshot(pdhg_ctx* ctx) {
   return PDHG_OK;
 }
 
+// ---- host-side layout construction ---------------------------------------
+
+// Rows in order of decreasing length; rows of equal length keep their order.
+std::vector<int> order_by_length(const std::vector<int>& len) {
+  int mx = 0;
+  for (int l : len) mx = std::max(mx, l);
+  std::vector<int64_t> start(mx + 2, 0);
+  for (int l : len) start[mx - l + 1] += 1;
+  for (int b = 0; b <= mx; ++b) start[b + 1] += start[b];
+  std::vector<int> order(len.size());
+  for (size_t i = 0; i < len.size(); ++i) order[start[mx - len[i]]++] = (int)i;
+  return order;
+}
+
+struct HostHyb {
+  int rows = 0, cols = 0, n_long = 0, n_slices = 0;
+  int64_t nnz = 0;
+  std::vector<long long> loff, soff;
+  std::vector<int> ci;
+  std::vector<double> v;
+};
+
+// CSR with rows already sorted by decreasing length -> long rows + slices.
+HostHyb make_hyb(int rows, int cols, const std::vector<int64_t>& rp, const std::vector<int>& ci,
+                 const std::vector<double>& v, int long_min) {
+  HostHyb H;
+  H.rows = rows;
+  H.cols = cols;
+  H.nnz = rp[rows];
+  auto len = [&](int r) { return (int)(rp[r + 1] - rp[r]); };
+  while (H.n_long < rows && len(H.n_long) >= long_min) ++H.n_long;
+  H.loff.assign(rp.begin(), rp.begin() + H.n_long + 1);
+  const int rest = rows - H.n_long;
+  H.n_slices = (rest + 31) / 32;
+  H.soff.resize(H.n_slices + 1);
+  H.soff[0] = rp[H.n_long];
+  for (int s = 0; s < H.n_slices; ++s) H.soff[s + 1] = H.soff[s] + 32LL * len(H.n_long + 32 * s);
+  const int64_t slots = H.soff[H.n_slices];
+  H.ci.assign(slots, 0);
+  H.v.assign(slots, 0.0);
+  std::copy(ci.begin(), ci.begin() + rp[H.n_long], H.ci.begin());
+  std::copy(v.begin(), v.begin() + rp[H.n_long], H.v.begin());
+  for (int s = 0; s < H.n_slices; ++s)
+    for (int lane = 0; lane < 32; ++lane) {
+      const int r = H.n_long + 32 * s + lane;
+      if (r >= rows) break;
+      for (int e = 0; e < len(r); ++e) {
+        H.ci[H.soff[s] + 32LL * e + lane] = ci[rp[r] + e];
+        H.v[H.soff[s] + 32LL * e + lane] = v[rp[r] + e];
+      }
+    }
+  return H;
+}
+
+pdhg_status upload_hyb(pdhg_ctx* ctx, const HostHyb& h, Hyb& d) {
+  d.rows = h.rows;
+  d.cols = h.cols;
+  d.n_long = h.n_long;
+  d.n_slices = h.n_slices;
+  d.nnz = h.nnz;
+  d.slots = (long long)h.v.size();
+  CK(ctx, dalloc(ctx, &d.loff, h.loff.size()));
+  CK(ctx, dalloc(ctx, &d.soff, h.soff.size()));
+  CK(ctx, dalloc(ctx, &d.ci, h.ci.size()));
+  CK(ctx, dalloc(ctx, &d.v, h.v.size()));
+  cudaStream_t s = ctx->stream;
+  CK(ctx, cudaMemcpyAsync(d.loff, h.loff.data(), sizeof(long long) * h.loff.size(), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(d.soff, h.soff.data(), sizeof(long long) * h.soff.size(), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(d.ci, h.ci.data(), sizeof(int) * h.ci.size(), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(d.v, h.v.data(), sizeof(double) * h.v.size(), cudaMemcpyHostToDevice, s));
+  // the host vectors are freed when setup returns: wait for the copies
+  CK(ctx, cudaStreamSynchronize(s));
+  return PDHG_OK;
+}
+
 pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx, const double* val, const double* b,
                   const double* c, const double* x0, const double* y0) {
   const int64_t m = ctx->m, n = ctx->n, nnz = ctx->nnz;
   const pdhg_options& o = ctx->opt;
-  // ---- host: int32 CSR of A and its transpose (stable counting sort) ----
-  std::vector<int> rpA(m + 1), ciA(nnz), rpT(n + 1, 0), ciT(nnz);
-  std::vector<double> vT(nnz);
-  for (int64_t i = 0; i <= m; ++i) rpA[i] = (int)row_ptr[i];
-  for (int64_t k = 0; k < nnz; ++k) {
-    ciA[k] = col_idx[k];
-    rpT[col_idx[k] + 1] += 1;
-  }
-  for (int64_t j = 0; j < n; ++j) rpT[j + 1] += rpT[j];
+  // ---- host: internal numbering (rows and columns by decreasing length) ----
+  std::vector<int> lenA(m), lenT(n, 0);
+  for (int64_t i = 0; i < m; ++i) lenA[i] = (int)(row_ptr[i + 1] - row_ptr[i]);
+  for (int64_t k = 0; k < nnz; ++k) lenT[col_idx[k]] += 1;
+  const std::vector<int> py = order_by_length(lenA);  // internal row -> caller's row
+  const std::vector<int> px = order_by_length(lenT);  // internal column -> caller's column
+  std::vector<int> iy(m), ix(n);
+  for (int64_t r = 0; r < m; ++r) iy[py[r]] = (int)r;
+  for (int64_t r = 0; r < n; ++r) ix[px[r]] = (int)r;
+  HostHyb hA, hT;
   {
-    std::vector<int> next(rpT.begin(), rpT.end() - 1);
-    for (int64_t i = 0; i < m; ++i)
-      for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-        const int pos = next[col_idx[k]]++;
-        ciT[pos] = (int)i;
-        vT[pos] = val[k];
+    // internal CSR of A (entries keep the caller's order within a row)
+    std::vector<int64_t> rp(m + 1, 0);
+    std::vector<int> ci(nnz);
+    std::vector<double> v(nnz);
+    for (int64_t r = 0; r < m; ++r) rp[r + 1] = rp[r] + lenA[py[r]];
+    for (int64_t r = 0; r < m; ++r) {
+      const int i = py[r];
+      int64_t q = rp[r];
+      for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k, ++q) {
+        ci[q] = ix[col_idx[k]];
+        v[q] = val[k];
       }
+    }
+    hA = make_hyb((int)m, (int)n, rp, ci, v, o.long_row_min);
   }
-  // ---- device allocations ----
-  Csr& A = ctx->A;
-  Csr& At = ctx->At;
-  A.rows = (int)m;
-  A.cols = (int)n;
-  A.nnz = nnz;
-  At.rows = (int)n;
-  At.cols = (int)m;
-  At.nnz = nnz;
-  CK(ctx, dalloc(ctx, &A.rp, m + 1));
-  CK(ctx, dalloc(ctx, &A.ci, nnz));
-  CK(ctx, dalloc(ctx, &A.v, nnz));
-  CK(ctx, dalloc(ctx, &At.rp, n + 1));
-  CK(ctx, dalloc(ctx, &At.ci, nnz));
-  CK(ctx, dalloc(ctx, &At.v, nnz));
+  {
+    // transpose (stable counting sort over the caller's columns), then the
+    // internal order of its rows
+    std::vector<int64_t> tp(n + 1, 0);
+    for (int64_t j = 0; j < n; ++j) tp[j + 1] = tp[j] + lenT[j];
+    std::vector<int> tci(nnz);
+    std::vector<double> tv(nnz);
+    {
+      std::vector<int64_t> next(tp.begin(), tp.end() - 1);
+      for (int64_t i = 0; i < m; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+          const int64_t pos = next[col_idx[k]]++;
+          tci[pos] = iy[i];
+          tv[pos] = val[k];
+        }
+    }
+    std::vector<int64_t> rp(n + 1, 0);
+    std::vector<int> ci(nnz);
+    std::vector<double> v(nnz);
+    for (int64_t r = 0; r < n; ++r) rp[r + 1] = rp[r] + lenT[px[r]];
+    for (int64_t r = 0; r < n; ++r) {
+      const int j = px[r];
+      std::copy(tci.begin() + tp[j], tci.begin() + tp[j + 1], ci.begin() + rp[r]);
+      std::copy(tv.begin() + tp[j], tv.begin() + tp[j + 1], v.begin() + rp[r]);
+    }
+    hT = make_hyb((int)n, (int)m, rp, ci, v, o.long_row_min);
+  }
+  std::vector<double> bi(m), cI(n), x0i, y0i;
+  for (int64_t r = 0; r < m; ++r) bi[r] = b[py[r]];
+  for (int64_t r = 0; r < n; ++r) cI[r] = c[px[r]];
+  if (x0) {
+    x0i.resize(n);
+    for (int64_t r = 0; r < n; ++r) x0i[r] = x0[px[r]];
+  }
+  if (y0) {
+    y0i.resize(m);
+    for (int64_t r = 0; r < m; ++r) y0i[r] = y0[py[r]];
+  }
+
+  // ---- device allocations and uploads ----
+  pdhg_status rs = upload_hyb(ctx, hA, ctx->A);
+  if (rs != PDHG_OK) return rs;
+  rs = upload_hyb(ctx, hT, ctx->At);
+  if (rs != PDHG_OK) return rs;
+  Hyb& A = ctx->A;
+  Hyb& At = ctx->At;
+  CK(ctx, dalloc(ctx, &ctx->perm_x, n));
+  CK(ctx, dalloc(ctx, &ctx->perm_y, m));
   double** vecs_n[] = {&ctx->c, &ctx->ch, &ctx->dc, &ctx->x, &ctx->xbar, &ctx->xsum, &ctx->xavg, &ctx->xr,
                        &ctx->tmp_n, &ctx->tmp_n2};
   double** vecs_m[] = {&ctx->b, &ctx->bh, &ctx->dr, &ctx->y, &ctx->ysum, &ctx->yavg, &ctx->yr, &ctx->tmp_m};
   for (double** p : vecs_n) CK(ctx, dalloc(ctx, p, n));
   for (double** p : vecs_m) CK(ctx, dalloc(ctx, p, m));
-  ctx->lprA = pick_lanes_per_row((double)nnz / (double)m);
-  ctx->lprAt = pick_lanes_per_row((double)nnz / (double)n);
-  ctx->nb_eval =
-      std::max(1, std::min(ctx->sms * 4, std::max(row_grid(ctx, m, ctx->lprA), row_grid(ctx, n, ctx->lprAt))));
+  ctx->nb_eval = std::max(1, std::min(ctx->sms * 4, std::max(unit_grid(A), unit_grid(At))));
   CK(ctx, dalloc(ctx, &ctx->partials, (size_t)std::max(ctx->nb_eval, ctx->sms * 8) * NQ));
   CK(ctx, dalloc(ctx, &ctx->scal, 16));
   CK(ctx, dalloc(ctx, &ctx->st, 1));
@@ -239,39 +356,35 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   for (int i = 0; i < 3 * EV_POOL; ++i) CK(ctx, cudaEventCreate(&ctx->ev[i]));
 
   cudaStream_t s = ctx->stream;
-  CK(ctx, cudaMemcpyAsync(A.rp, rpA.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(A.ci, ciA.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(A.v, val, sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(At.rp, rpT.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(At.ci, ciT.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(At.v, vT.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(ctx->b, b, sizeof(double) * m, cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(ctx->c, c, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->perm_x, px.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->perm_y, py.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->b, bi.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->c, cI.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
 
   // ---- device: scaling ----
   const int gn = vec_grid(ctx, n), gm = vec_grid(ctx, m);
-  const int grA = row_grid(ctx, m, ctx->lprA), grT = row_grid(ctx, n, ctx->lprAt);
+  const int grA = stride_grid(ctx, A), grT = stride_grid(ctx, At);
   launch_fill(ctx->dr, 1.0, m, gm, s);
   launch_fill(ctx->dc, 1.0, n, gn, s);
   double* r = ctx->tmp_m;   // row factors
   double* sf = ctx->tmp_n;  // column factors
   for (int it = 0; it < o.ruiz_iters; ++it) {
-    launch_row_absmax(A, ctx->lprA, r, grA, s);
-    launch_row_absmax(At, ctx->lprAt, sf, grT, s);
+    launch_row_absmax(A, r, grA, s);
+    launch_row_absmax(At, sf, grT, s);
     launch_inv_sqrt_or_one(r, r, (int)m, gm, s);
     launch_inv_sqrt_or_one(sf, sf, (int)n, gn, s);
-    launch_scale_csr(A, ctx->lprA, r, sf, 0, grA, s);
-    launch_scale_csr(At, ctx->lprAt, r, sf, 1, grT, s);
+    launch_scale(A, r, sf, 0, grA, s);
+    launch_scale(At, r, sf, 1, grT, s);
     launch_mul_inplace(ctx->dr, r, (int)m, gm, s);
     launch_mul_inplace(ctx->dc, sf, (int)n, gn, s);
   }
   if (o.pock_chambolle) {
-    launch_row_abspow_sum(A, ctx->lprA, o.pc_alpha, r, grA, s);
-    launch_row_abspow_sum(At, ctx->lprAt, 2.0 - o.pc_alpha, sf, grT, s);
+    launch_row_abspow_sum(A, o.pc_alpha, r, grA, s);
+    launch_row_abspow_sum(At, 2.0 - o.pc_alpha, sf, grT, s);
     launch_inv_sqrt_or_one(r, r, (int)m, gm, s);
     launch_inv_sqrt_or_one(sf, sf, (int)n, gn, s);
-    launch_scale_csr(A, ctx->lprA, r, sf, 0, grA, s);
-    launch_scale_csr(At, ctx->lprAt, r, sf, 1, grT, s);
+    launch_scale(A, r, sf, 0, grA, s);
+    launch_scale(At, r, sf, 1, grT, s);
     launch_mul_inplace(ctx->dr, r, (int)m, gm, s);
     launch_mul_inplace(ctx->dc, sf, (int)n, gn, s);
   }
@@ -287,9 +400,9 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   launch_fill(v, 1.0 / sqrt((double)n), n, gn, s);
   launch_fill(ctx->scal, 0.0, 16, 1, s);
   for (int it = 0; it < o.power_iters; ++it) {
-    launch_spmv(A, ctx->lprA, v, u, grA, s);
+    launch_spmv(A, v, u, grA, s);
     launch_sumsq(u, (int)m, ctx->partials, nbs, ctx->scal + 0, s);
-    launch_spmv(At, ctx->lprAt, u, w, grT, s);
+    launch_spmv(At, u, w, grT, s);
     launch_sumsq(w, (int)n, ctx->partials, nbs, ctx->scal + 5, s);
     launch_div_by_norm(v, w, ctx->scal + 5, (int)n, gn, s);
   }
@@ -320,11 +433,11 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   launch_fill(ctx->x, 0.0, n, gn, s);
   launch_fill(ctx->y, 0.0, m, gm, s);
   if (x0) {
-    CK(ctx, cudaMemcpyAsync(ctx->tmp_n, x0, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CK(ctx, cudaMemcpyAsync(ctx->tmp_n, x0i.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
     launch_div(ctx->x, ctx->tmp_n, ctx->dc, (int)n, gn, s);
   }
   if (y0) {
-    CK(ctx, cudaMemcpyAsync(ctx->tmp_m, y0, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    CK(ctx, cudaMemcpyAsync(ctx->tmp_m, y0i.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
     launch_div(ctx->y, ctx->tmp_m, ctx->dr, (int)m, gm, s);
   }
   launch_fill(ctx->xsum, 0.0, n, gn, s);
@@ -337,7 +450,7 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   eval_point(ctx, ctx->x, ctx->y, nullptr, nullptr, &ctx->st->cur);
   launch_init_restart_ref(ctx->st, s);
   CK(ctx, cudaGetLastError());
-  pdhg_status rs = read_state(ctx);
+  rs = read_state(ctx);
   if (rs != PDHG_OK) return rs;
   if (!std::isfinite(ctx->h_st->norm_est) || !std::isfinite(ctx->h_st->omega))
     return fail(ctx, PDHG_ERR_NUMERIC, "non-finite norm estimate or primal weight after scaling");
@@ -371,6 +484,7 @@ void pdhg_default_options(pdhg_options* o) {
   o->use_graphs = 1;
   o->kernel_timing = 0;
   o->polish_switch = 1e-5;
+  o->long_row_min = 64;
 }
 
 pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
@@ -390,7 +504,7 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     pdhg_default_options(&o);
   if (o.precision != PDHG_FP64) return fail(nullptr, PDHG_ERR_INVALID, "only PDHG_FP64 is available in this build");
   if (o.eval_every < 1 || o.ruiz_iters < 0 || o.power_iters < 1 || !(o.step_factor > 0.0) || o.pc_alpha < 0.0 ||
-      o.pc_alpha > 2.0 || o.snapshot_every < 0 || o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
+      o.pc_alpha > 2.0 || o.long_row_min < 1 || o.snapshot_every < 0 || o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
     return fail(nullptr, PDHG_ERR_INVALID, "option out of range");
 
   // host copies when the caller passed device pointers
@@ -504,7 +618,7 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
   const int n = (int)ctx->n, m = (int)ctx->m;
   cudaStream_t s = ctx->stream;
   CK(ctx, cudaMemcpyAsync(&ctx->st->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
-  const int grT = row_grid(ctx, n, ctx->lprAt), grA = row_grid(ctx, m, ctx->lprA);
+  const int grT = unit_grid(ctx->At), grA = unit_grid(ctx->A);
   const int gv = vec_grid(ctx, std::max(n, m));
   ctx->converged = false;
   int64_t done = 0;
@@ -517,10 +631,9 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
     const bool timing = o.kernel_timing && nb <= EV_POOL;
     for (int64_t it = 0; it < nb; ++it) {
       if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
-      launch_primal_step(ctx->At, ctx->lprAt, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts,
-                         grT, s);
+      launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, grT, s);
       if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
-      launch_dual_step(ctx->A, ctx->lprA, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, grA, s);
+      launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, grA, s);
       if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 2], s));
     }
     launch_add_counters(ctx->st, nb, s);
@@ -611,8 +724,8 @@ pdhg_status pdhg_get_solution(pdhg_ctx* ctx, int which, double* x, double* y, do
   double* ox = ctx->sol;
   double* oy = ctx->sol + ctx->n;
   double* oz = ctx->sol + ctx->n + ctx->m;
-  launch_pack_solution(ctx->At, ctx->lprAt, px, py, ctx->ch, ctx->dc, ctx->dr, x ? ox : nullptr, y ? oy : nullptr,
-                       z ? oz : nullptr, vec_grid(ctx, ctx->n), ctx->stream);
+  launch_pack_solution(ctx->At, ctx->perm_x, ctx->perm_y, px, py, ctx->ch, ctx->dc, ctx->dr, x ? ox : nullptr,
+                       y ? oy : nullptr, z ? oz : nullptr, stride_grid(ctx, ctx->At), ctx->stream);
   CK(ctx, cudaGetLastError());
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (x) CK(ctx, cudaMemcpyAsync(x, ox, sizeof(double) * ctx->n, kind, ctx->stream));

@@ -48,6 +48,7 @@ class pdhg_options(C.Structure):
         ("use_graphs", C.c_int),
         ("kernel_timing", C.c_int),
         ("polish_switch", C.c_double),
+        ("long_row_min", C.c_int),
         ("reserved", C.c_int * 8),
     ]
 
