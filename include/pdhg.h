@@ -117,6 +117,7 @@ typedef struct {
   int converged;
   double kernel_ms_primal, kernel_ms_dual; /* summed event times (kernel_timing) */
   int64_t kernel_launches_primal, kernel_launches_dual;
+  int64_t kernel_launches; /* all kernels launched by pdhg_iterate so far */
 } pdhg_info;
 
 /* One record per evaluation. */

@@ -248,6 +248,11 @@ def restart_decision(k_cand, k_last_restart, k_prev_cand, t_since, k_total, opt:
     return t_since >= opt.beta_art * k_total
 
 
+def _rel_gap(a: float, b: float) -> float:
+    d = max(abs(a), abs(b))
+    return abs(a - b) / d if d > 0 else 0.0
+
+
 def primal_weight_update(omega: float, dx: float, dy: float, theta: float) -> float:
     """omega <- exp(theta ln(dy/dx) + (1 - theta) ln omega) when both moves are
     above 1e-10; unchanged otherwise."""
@@ -267,6 +272,11 @@ class EvalRecord:
     candidate: int  # RESTART_TO_CURRENT / RESTART_TO_AVERAGE
     omega: float  # after the update
     rel_kkt: float  # of the candidate, on the problem as given
+    # smallest relative gap between the two sides of any comparison that took
+    # part in this evaluation's decisions (candidate choice, restart tests);
+    # an implementation that rounds differently may decide otherwise only
+    # when this is at rounding level
+    margin: float = math.inf
 
 
 class Oracle:
@@ -382,13 +392,19 @@ class Oracle:
                 self.next_snapshot += opt.snapshot_every
 
         kind = NO_RESTART
+        margin = math.inf
+        if n_avg is not None:
+            ka, kc0 = weighted_kkt(n_avg, self.omega), weighted_kkt(n_cur, self.omega)
+            margin = _rel_gap(ka, kc0)
         if converged:
             self.x, self.y = xc.copy(), yc.copy()
         elif opt.restarts:
             om = self.omega
             k_c = weighted_kkt(n_c, om)
-            if restart_decision(k_c, weighted_kkt(self.n_restart, om), weighted_kkt(self.n_prev, om),
-                                self.t, self.k, opt):
+            k_r, k_p = weighted_kkt(self.n_restart, om), weighted_kkt(self.n_prev, om)
+            margin = min(margin, _rel_gap(k_c, opt.beta_suff * k_r), _rel_gap(k_c, opt.beta_nec * k_r),
+                         _rel_gap(k_c, k_p))
+            if restart_decision(k_c, k_r, k_p, self.t, self.k, opt):
                 kind = which
                 if opt.primal_weight:
                     dx = float(np.linalg.norm(xc - self.x_r))
@@ -402,7 +418,7 @@ class Oracle:
                 self.t = 0
                 self.restart_count += 1
             self.n_prev = n_c
-        self.trace.append(EvalRecord(self.k, kind, which, self.omega, rel))
+        self.trace.append(EvalRecord(self.k, kind, which, self.omega, rel, margin))
         return converged
 
     def _snapshot(self, xh, yh, rel, why):

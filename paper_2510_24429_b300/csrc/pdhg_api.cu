@@ -67,6 +67,7 @@ struct pdhg_ctx {
   cudaEvent_t ev[3 * EV_POOL] = {};
   double ms_primal = 0, ms_dual = 0;
   int64_t launches_primal = 0, launches_dual = 0;
+  int64_t launches = 0;  // kernels launched by pdhg_iterate (snapshot packing included)
   // host mirrors
   int64_t k = 0;
   bool converged = false;
@@ -637,6 +638,7 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
       if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 2], s));
     }
     launch_add_counters(ctx->st, nb, s);
+    ctx->launches += 2 * nb + 1;
     CK(ctx, cudaGetLastError());
     ctx->k += nb;
     done += nb;
@@ -661,6 +663,7 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
       launch_decide(ctx->st, ctx->trace, s);
       launch_apply(ctx->st, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, ctx->xsum, ctx->ysum, n, m, gv,
                    s);
+      ctx->launches += (o.restarts ? 4 : 0) + 3 + 2;
       CK(ctx, cudaGetLastError());
       rs = read_state(ctx);
       if (rs != PDHG_OK) return rs;
@@ -671,6 +674,7 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
       if (ctx->h_st->snapshot_flag) {
         rs = take_snapshot(ctx);
         if (rs != PDHG_OK) return rs;
+        ctx->launches += 2;
       }
       if (ctx->h_st->converged) {
         ctx->converged = true;
@@ -791,6 +795,7 @@ pdhg_status pdhg_get_info(pdhg_ctx* ctx, pdhg_info* out) {
   out->kernel_ms_dual = ctx->ms_dual;
   out->kernel_launches_primal = ctx->launches_primal;
   out->kernel_launches_dual = ctx->launches_dual;
+  out->kernel_launches = ctx->launches;
   return PDHG_OK;
 }
 

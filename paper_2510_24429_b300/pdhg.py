@@ -66,6 +66,7 @@ class pdhg_info(C.Structure):
         ("evaluations", C.c_int64), ("snapshots", C.c_int64), ("last_rel_kkt", C.c_double),
         ("precision_now", C.c_int), ("converged", C.c_int), ("kernel_ms_primal", C.c_double),
         ("kernel_ms_dual", C.c_double), ("kernel_launches_primal", C.c_int64), ("kernel_launches_dual", C.c_int64),
+        ("kernel_launches", C.c_int64),
     ]
 
 

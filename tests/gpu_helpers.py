@@ -52,3 +52,18 @@ def assert_iterates_close(sol, orc, tol, which=P.PDHG_CURRENT):
         mb = max(float(np.max(np.abs(b))) if b.size else 0.0, floor / max(1.0, np.sqrt(b.size)))
         e2 = float(np.max(np.abs(np.asarray(a) - b))) / (mb if mb > 0 else 1.0) if b.size else 0.0
         assert e1 <= tol and e2 <= tol, f"{name}: rel {e1:.3e} max-rel {e2:.3e} > {tol:.1e}"
+
+
+def compare_traces(gpu_trace, orc_trace, near_tie=1e-6):
+    """Decisions (iteration, kind, candidate) must agree. A differing decision
+    is accepted only where the oracle's decision margin is at rounding level
+    (a near-tie that a different summation order can flip); the trajectories
+    may part after it, so comparison stops there. Returns the number of
+    evaluations compared."""
+    assert len(gpu_trace) == len(orc_trace)
+    for i, (g, o) in enumerate(zip(gpu_trace, orc_trace)):
+        if (g["iteration"], g["kind"], g["candidate"]) != (o.iteration, o.kind, o.candidate):
+            assert g["iteration"] == o.iteration
+            assert o.margin <= near_tie, (i, g, o)
+            return i
+    return len(orc_trace)
