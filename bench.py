@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the PDHG hot path on the large synthetic LP.
+
+Workload: m = 1e6 constraints, n = 3e6 variables, nnz ~ 3e7 with Zipf(1.5)-
+shaped column counts, FP64, PDLP-style PDHG with adaptive restarts, primal
+weight, an evaluation every 64 iterations and a snapshot (x, y, z) every 1000
+iterations. One step = 1000 PDHG iterations, i.e. one pass of every part of
+the hot path (both fused half-steps, evaluations, restart logic, snapshot).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). With --impl reference the FP64 CPU oracle is
+timed instead, on the same workload and metric. Multi-GPU runs (torchrun) are
+independent replicas: the method has no cross-GPU exchange on one LP.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PDHG iters/s + HBM GB/s (% peak); time-to-1e-6 rel KKT, FP32-refined vs FP64"
+ITERS_PER_STEP = 1000
+SNAPSHOT_EVERY = 1000
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--small", action="store_true", help="a 1/10-size LP (m=1e5, n=3e5, nnz~3e6) for profiling")
+    p.add_argument("--skip-extras", action="store_true", help="skip e2e, time-to-tolerance and the CPU baseline")
+    return p.parse_args()
+
+
+def make_lp(args):
+    from paper_2510_24429_b300 import lpgen
+
+    if args.small:
+        return lpgen.large_lp(args.seed, m=100_000, n=300_000, nnz=3_000_000), "zipf-lp m=1e5 n=3e5 nnz~3e6 FP64"
+    return lpgen.large_lp(args.seed), "zipf-lp m=1e6 n=3e6 nnz~3e7 FP64"
+
+
+def config_of(args, lp, name):
+    return {
+        "workload": name,
+        "m": lp.m,
+        "n": lp.n,
+        "nnz": lp.nnz,
+        "iterations_per_step": ITERS_PER_STEP,
+        "restarts": True,
+        "eval_every": 64,
+        "snapshot_every": SNAPSHOT_EVERY,
+        "seed": args.seed,
+        "l2_policy": (f"inputs larger than L2 (matrix {24 * lp.nnz / 1e6:.0f} MB streamed per iteration vs 126 MB "
+                      "L2); no flush" if 24 * lp.nnz > 126e6 else "working set fits in L2 (profiling size only)"),
+        "parallelism": "replicas" if args.gpus > 1 else "single-gpu",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "common.cuh", "kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2510_24429_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources and this workload."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e or e.get("source_sha") != kernel_source_sha() or e.get("workload") != workload:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+def dist_init(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_rate(lp, iterations: int, warm: int = 2):
+    """Iterations/s of the FP64 oracle (setup excluded; its step size comes
+    from 2 power iterations, which does not change the per-iteration cost)."""
+    from oracle import pdhg_oracle as O
+
+    orc = O.Oracle(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, O.Options(power_iters=2))
+    for _ in range(warm):
+        orc.iterate_once()
+    t0 = time.perf_counter()
+    for _ in range(iterations):
+        orc.iterate_once()
+    return iterations / (time.perf_counter() - t0), orc
+
+
+def run_reference(args):
+    rank, world, _ = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
+    if rank != 0:
+        return
+    lp, name = make_lp(args)
+    from oracle import pdhg_oracle as O
+
+    per_step = 4  # oracle iterations per step (a bounded sample of the 1000-iteration step)
+    orc = O.Oracle(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, O.Options(power_iters=2))
+    for _ in range(args.warmup * per_step):
+        orc.iterate_once()
+    t0 = time.perf_counter()
+    for _ in range(args.steps * per_step):
+        orc.iterate_once()
+    el = time.perf_counter() - t0
+    value = args.steps * per_step / el
+    sample = f"{args.steps} steps x {per_step} oracle iterations (of the 1000 per step), setup excluded"
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * ITERS_PER_STEP / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(args, lp, name),
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "host_cores": os.cpu_count()},
+        "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+# our engine
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2510_24429_b300 import build
+    from paper_2510_24429_b300 import pdhg as P
+
+    build.build()
+    rank, world, local = dist_init(args)
+    lp, name = make_lp(args)
+    stream = torch.cuda.current_stream()
+
+    # ---- device-resident timing (value) ----
+    t0 = time.perf_counter()
+    sol = P.Solver(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, stream=stream.cuda_stream,
+                   snapshot_every=SNAPSHOT_EVERY, kernel_timing=1)
+    setup_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        sol.iterate(ITERS_PER_STEP)
+    info0 = sol.info()
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sol.iterate(ITERS_PER_STEP)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    info1 = sol.info()
+    snaps, _ = sol.snapshot_poll()
+    iters = args.steps * ITERS_PER_STEP
+    value = world * iters / (ms / 1000.0)
+
+    # per-kernel times (CUDA events on the launching stream, every launch of the timed region)
+    lp_ = info1["kernel_launches_primal"] - info0["kernel_launches_primal"]
+    ld_ = info1["kernel_launches_dual"] - info0["kernel_launches_dual"]
+    t_primal = (info1["kernel_ms_primal"] - info0["kernel_ms_primal"]) / lp_
+    t_dual = (info1["kernel_ms_dual"] - info0["kernel_ms_dual"]) / ld_
+    m, n, nnz = lp.m, lp.n, lp.nnz
+    bytes_primal = 12 * nnz + 8 * m + 48 * n  # A^T entries, y gathered once, x/c/xsum read + x/xbar/xsum written
+    bytes_dual = 12 * nnz + 8 * n + 40 * m  # A entries, xbar gathered once, y/b/ysum read + y/ysum written
+    peak, peak_kind = measured_peaks()
+    if t_primal >= t_dual:
+        kname, kb, kt = "k_primal_step", bytes_primal, t_primal
+    else:
+        kname, kb, kt = "k_dual_step", bytes_dual, t_dual
+    achieved = kb / (kt / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": profiled_traffic(kname, name),
+                "algorithmic_bytes_per_launch": kb, "ms_per_launch": kt,
+                "other_kernel": {"name": "k_dual_step" if kname == "k_primal_step" else "k_primal_step",
+                                 "ms_per_launch": t_dual if kname == "k_primal_step" else t_primal,
+                                 "achieved_gbs": (bytes_dual / (t_dual / 1000.0) if kname == "k_primal_step"
+                                                  else bytes_primal / (t_primal / 1000.0)) / 1e9}}
+    launches = info1["kernel_launches"] - info0["kernel_launches"]
+    iter_bytes = bytes_primal + bytes_dual
+    sol.close()
+
+    extras = {}
+    if not args.skip_extras and rank == 0:
+        # ---- time to tolerance (fresh solve, setup excluded) ----
+        ttt = {}
+        for tol in (1e-4, 1e-6):
+            with P.Solver(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, stream=stream.cuda_stream) as s2:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, done = s2.iterate(200_000, tol)
+                torch.cuda.synchronize()
+                ttt[f"{tol:g}"] = {"seconds": time.perf_counter() - t0, "iterations": done,
+                                   "converged": st == P.PDHG_OK, "rel_kkt": s2.kkt()["rel_kkt"]}
+        extras["time_to_tol"] = {"fp64": ttt, "mixed": None}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.skip_extras:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        h_rp, h_ci, h_v, h_b, h_c = (pin(lp.row_ptr), pin(lp.col_idx.astype(np.int32)), pin(lp.val), pin(lp.b),
+                                     pin(lp.c))
+        out_x, out_y, out_z = pin(np.empty(lp.n)), pin(np.empty(lp.m)), pin(np.empty(lp.n))
+        h2d = h_rp.nbytes + h_ci.nbytes + h_v.nbytes + h_b.nbytes + h_c.nbytes
+        d2h = out_x.nbytes + out_y.nbytes + out_z.nbytes
+        e2e_steps = max(1, min(args.steps, 3))
+
+        def e2e_step():
+            with P.Solver(lp.m, lp.n, h_rp, h_ci, h_v, h_b, h_c, snapshot_every=SNAPSHOT_EVERY) as s3:
+                s3.iterate(ITERS_PER_STEP)
+                P.pdhg_get_solution(s3.ctx, P.PDHG_CURRENT, out_x, out_y, out_z)
+
+        e2e_step()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": world * e2e_steps * ITERS_PER_STEP / el, "unit": "iters/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+               "includes": "pdhg_create from pinned host CSR (validation, renumbering, upload, scaling, power "
+                           "iteration), 1000 iterations, solution read back, destroy"}
+
+    cpu = None
+    if not args.skip_extras and rank == 0 and world == 1:
+        n_it = 32
+        rate, _ = oracle_rate(lp, n_it)
+        cpu = {"value": rate, "unit": "iters/s", "cores": 1, "kind": "oracle", "host_cores": os.cpu_count(),
+               "sample": f"{n_it} PDHG iterations of the FP64 oracle (numpy/scipy, single thread) on the same LP, "
+                         "setup excluded"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args, lp, name),
+            "hbm_gbs_per_iteration_model": iter_bytes * value / world / 1e9,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "setup_s": setup_s, "snapshots_taken": snaps,
+        }
+        out.update(extras)
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
