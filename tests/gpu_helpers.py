@@ -57,13 +57,15 @@ def assert_iterates_close(sol, orc, tol, which=P.PDHG_CURRENT):
 def compare_traces(gpu_trace, orc_trace, near_tie=1e-6):
     """Decisions (iteration, kind, candidate) must agree. A differing decision
     is accepted only where the oracle's decision margin is at rounding level
-    (a near-tie that a different summation order can flip); the trajectories
+    (a near-tie that a different summation order can flip) or the method has
+    already converged to rounding noise (rel. KKT <= 1e-12); the trajectories
     may part after it, so comparison stops there. Returns the number of
     evaluations compared."""
     assert len(gpu_trace) == len(orc_trace)
     for i, (g, o) in enumerate(zip(gpu_trace, orc_trace)):
         if (g["iteration"], g["kind"], g["candidate"]) != (o.iteration, o.kind, o.candidate):
             assert g["iteration"] == o.iteration
-            assert o.margin <= near_tie, (i, g, o)
+            # a near-tie, or KKT errors already at the FP64 noise floor
+            assert o.margin <= near_tie or o.rel_kkt <= 1e-12, (i, g, o)
             return i
     return len(orc_trace)

@@ -77,10 +77,10 @@ def test_restarted_trace_and_iterates(tiny_lp):
     rounding-level differences in the iterates grow by ||x|| / ||dx|| in omega;
     omega and the iterates are held to 1e-6 here."""
     orc, sol = pair(tiny_lp)
-    orc.run(3000)
-    sol.iterate(3000)
+    orc.run(3000, 1e-10)
+    sol.iterate(3000, 1e-10)
     tr = sol.trace()
-    assert len(tr) == len(orc.trace) == 3000 // 64
+    assert len(tr) == len(orc.trace) >= 20
     agreed = compare_traces(tr, orc.trace)
     assert agreed >= 20
     for g, o in zip(tr[:agreed], orc.trace[:agreed]):
