@@ -182,8 +182,37 @@ PDHG_API pdhg_status pdhg_get_info(pdhg_ctx* ctx, pdhg_info* out);
  * number stored (at most 65536 are kept). */
 PDHG_API pdhg_status pdhg_get_trace(pdhg_ctx* ctx, pdhg_trace_rec* recs, int64_t cap, int64_t* count);
 
-/* Description of the last failure of ctx, or of the last failed pdhg_create
- * when ctx is NULL. Never NULL. */
+/* KKT measures (as pdhg_kkt) of a point (x, y), z = max(0, c - A^T y), of an LP
+ * the caller keeps on the device, computed WITHOUT ALLOCATING ANY MEMORY. The
+ * paper has no counterpart; this entry point exists for callers that cannot
+ * let a library allocate: applications whose device memory belongs to their
+ * own pool or framework allocator, services held to a fixed memory budget, and
+ * latency-critical code where cudaMalloc/cudaFree would synchronize the device.
+ *   Inputs (all DEVICE pointers, borrowed for the call): A as CSR
+ *   (a_row_ptr[m+1] int64, a_col_idx[nnz] int32, a_val[nnz]) and its transpose
+ *   as CSR (at_row_ptr[n+1], at_col_idx[nnz], at_val[nnz]); b[m], c[n], x[n],
+ *   y[m]. Indices are not checked and must be in range. Output: *out in HOST
+ *   memory (iteration = -1). Work runs on cuda_stream (NULL = legacy default
+ *   stream); the call waits for it to finish.
+ *   blocks: blocks per pass, 0 = 4 per SM; at most 1024, because the partial
+ *   sums live in one fixed 96 KiB array in device memory that the library
+ *   declares statically (every GPU that loads the library holds it until the
+ *   process exits). Larger values return PDHG_ERR_INVALID.
+ *   The first call on a device looks up that array's device address (once per
+ *   device); make that first call before any stream capture.
+ *   All calls on a device share the array and leave their partial sums in it;
+ *   each call overwrites what it reads, so nothing needs clearing, but calls
+ *   that overlap on the GPU (unordered streams or threads) race and return
+ *   wrong values: order them on one stream.
+ *   Errors: INVALID (bad sizes, NULL pointers, blocks > 1024), CUDA, NUMERIC
+ *   (non-finite result); pdhg_last_error(NULL) describes the failure. */
+PDHG_API pdhg_status pdhg_kkt_noalloc(int64_t m, int64_t n, const int64_t* a_row_ptr, const int32_t* a_col_idx,
+                                      const double* a_val, const int64_t* at_row_ptr, const int32_t* at_col_idx,
+                                      const double* at_val, const double* b, const double* c, const double* x,
+                                      const double* y, int blocks, void* cuda_stream, pdhg_kkt_info* out);
+
+/* Description of the last failure of ctx, or of the last failed context-free
+ * call (pdhg_create, pdhg_kkt_noalloc) when ctx is NULL. Never NULL. */
 PDHG_API const char* pdhg_last_error(const pdhg_ctx* ctx);
 
 #ifdef __cplusplus

@@ -34,6 +34,10 @@ constexpr int EV_POOL = 256;
 
 }  // namespace
 
+// failures of calls without a context (pdhg_create, pdhg_kkt_noalloc) are
+// reported by pdhg_last_error(NULL)
+void pdhg_set_global_error(const char* msg) { g_create_error = msg; }
+
 struct pdhg_ctx {
   int64_t m = 0, n = 0, nnz = 0;
   pdhg_options opt{};

@@ -99,6 +99,8 @@ SIGNATURES = {
     "pdhg_get_info": (C.c_int, [_P, C.POINTER(pdhg_info)]),
     "pdhg_get_trace": (C.c_int, [_P, C.POINTER(pdhg_trace_rec), C.c_int64, C.POINTER(C.c_int64)]),
     "pdhg_last_error": (C.c_char_p, [_P]),
+    "pdhg_kkt_noalloc": (C.c_int, [C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P,
+                                   C.POINTER(pdhg_kkt_info)]),
 }
 
 
@@ -261,6 +263,29 @@ def pdhg_get_trace(ctx) -> list[dict]:
 
 def pdhg_last_error(ctx=None) -> str:
     return load().pdhg_last_error(ctx).decode()
+
+
+def pdhg_kkt_noalloc(m, n, a_row_ptr, a_col_idx, a_val, at_row_ptr, at_col_idx, at_val, b, c, x, y, blocks=0,
+                     stream=None) -> dict:
+    """KKT measures of (x, y) for an LP held on the device as CSR of A and A^T,
+    through the allocation-free entry point. Every array must already be a
+    contiguous CUDA tensor of the right dtype (int64 row pointers, int32
+    column indices, float64 values and vectors): nothing is converted or
+    copied here, so the call allocates nothing."""
+    import torch
+
+    args = [a_row_ptr, a_col_idx, a_val, at_row_ptr, at_col_idx, at_val, b, c, x, y]
+    want = [torch.int64, torch.int32, torch.float64] * 2 + [torch.float64] * 4
+    for a, dt in zip(args, want):
+        if not (_is_torch(a) and a.is_cuda and a.is_contiguous() and a.dtype == dt):
+            raise ValueError("pdhg_kkt_noalloc takes contiguous CUDA tensors of the documented dtypes")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    info = pdhg_kkt_info()
+    st = load().pdhg_kkt_noalloc(int(m), int(n), *[a.data_ptr() for a in args], int(blocks),
+                                 C.c_void_p(stream) if stream else None, C.byref(info))
+    _check(st, None)
+    return {k: getattr(info, k) for k, _ in pdhg_kkt_info._fields_}
 
 
 # ---------------------------------------------------------------------------
