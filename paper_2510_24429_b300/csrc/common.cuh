@@ -70,24 +70,33 @@ constexpr int TRACE_CAP = 65536;
 
 // Device layout of one copy of the scaled matrix (Ahat, or Ahat^T).
 //
-// Rows are stored in order of decreasing length (the engine permutes the
-// variables and constraints internally to get there). The leading n_long rows
-// (at least `long_row_min` entries each) are plain CSR and are reduced by one
-// warp per row. The remaining rows are cut into slices of 32 consecutive
-// rows; a slice is padded to the length of its first (longest) row and stored
-// column-major, so entry e of the slice's row `lane` sits at
-// soff[s] + 32 e + lane and one thread per row reads fully coalesced
-// 128-byte index and 256-byte value lines. Padding slots hold value 0 and
-// column 0. A "unit" is one long row or one slice; units are numbered long
-// rows first.
+// Rows are stored in order of decreasing length (the engine renumbers the
+// variables and constraints internally to get there).
+//
+// Long rows: the leading n_long rows (at least `long_row_min` entries each)
+// are CSR reduced by one warp per row. Each starts at an entry offset that is
+// a multiple of 4 and is padded to a multiple of 4 entries, so a lane loads 4
+// indices (16 B) and 4 values (2 x 16 B) per step.
+//
+// Slices: the remaining rows are cut into slices of 32*R rows (R = rows per
+// thread, 1, 2 or 4, chosen per slice from its length). A slice is padded to
+// the length Lp of its first (longest) row; when Lp > 1 it is rounded up to an
+// even number and entries are stored in pairs: entry e of the slice's row
+// (32 q + lane) sits at
+//     soff[s] + ((e / 2) * R + q) * 64 + 2 * lane + (e % 2)
+// so one thread loads its row's next two indices and values with one 8-byte
+// and one 16-byte load and a warp reads contiguous 256 B / 512 B lines; when
+// Lp == 1 the slice is simply soff[s] + 32 q + lane. Padding slots hold value 0
+// and column 0. A "unit" is one long row or one slice; long rows come first.
 struct Hyb {
   int rows = 0, cols = 0;
   int n_long = 0;
   int n_slices = 0;
   long long nnz = 0;    // stored entries (without padding)
   long long slots = 0;  // entry slots including padding
-  long long* loff = nullptr;  // [n_long + 1] offsets of the long rows
+  long long* loff = nullptr;  // [n_long + 1] offsets of the long rows (multiples of 4)
   long long* soff = nullptr;  // [n_slices + 1] offsets of the slices
+  int2* sinfo = nullptr;      // [n_slices] (first row, rows per thread R)
   int* ci = nullptr;          // [slots] column index (internal numbering)
   double* v = nullptr;        // [slots] value
   int units() const { return n_long + n_slices; }

@@ -6,15 +6,22 @@
 // epilogue of the row reduction, so the step's vectors are read and written
 // once. Tensor cores play no part: SpMV is not a dense contraction.
 //
-// Cache policy: everything that is touched once per half-step (matrix
-// indices and values, the step's own vectors) is loaded and stored with the
-// streaming (evict-first) policy, so that the vector the next half-step
-// gathers (xbar, written by the primal step; y, written by the dual step)
-// stays resident in the 126 MB L2.
+// Cache policy: the matrix is read with no L1 allocation and the L2
+// evict-first policy; the step's own vectors are read and written with the
+// streaming policy. The vector the next half-step gathers (xbar, written by
+// the primal step; y, written by the dual step) is written with the default
+// policy, so it stays resident in the 126 MB L2, and the gathers go through
+// L1 (which then holds the most frequently gathered entries, numbered first).
 #include <math.h>
 
 #include "common.cuh"
 #include "kernels.cuh"
+
+// minimum resident blocks per SM requested for the two step kernels (caps
+// their registers); 1 leaves the register count to the compiler
+#ifndef PDHG_STEP_MIN_BLOCKS
+#define PDHG_STEP_MIN_BLOCKS 1
+#endif
 
 namespace pdhg {
 
@@ -22,13 +29,59 @@ namespace {
 
 __device__ __forceinline__ double relu(double v) { return v < 0.0 ? 0.0 : v; }  // NaN passes through
 
-// Visit every row of M once. Each warp takes units (a long row, or a slice of
-// 32 rows) in a grid-stride loop; a long row is reduced across the warp, a
-// slice row by its own lane. `op` sees begin(r) before the row's entries
-// (to issue its epilogue loads early), entry(acc, k, r) for every slot k of
-// the row (padding included: value 0, column 0) and finish(r, acc) after.
-// For long rows only lane 0 calls begin/finish. MAX selects the warp
-// combine of partial results (max instead of sum).
+// ---- cache-policy loads ----------------------------------------------------
+__device__ __forceinline__ unsigned long long stream_policy() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ int ld_stream(const int* p, unsigned long long pol) {
+  int r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ double ld_stream(const double* p, unsigned long long pol) {
+  double r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ int2 ld_stream2(const int* p, unsigned long long pol) {
+  int2 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.s32 {%0, %1}, [%2], %3;"
+      : "=r"(r.x), "=r"(r.y)
+      : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ double2 ld_stream2(const double* p, unsigned long long pol) {
+  double2 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+      : "=d"(r.x), "=d"(r.y)
+      : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ int4 ld_stream4(const int* p, unsigned long long pol) {
+  int4 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p), "l"(pol));
+  return r;
+}
+
+// slot of entry e of row (32 q + lane) in a slice (see Hyb)
+__device__ __forceinline__ long long slice_slot(long long base, int Lp, int R, int q, int e, int lane) {
+  return Lp == 1 ? base + 32 * q + lane : base + ((long long)(e >> 1) * R + q) * 64 + 2 * lane + (e & 1);
+}
+
+__device__ __forceinline__ void slice_shape(const Hyb& H, int s, int2& info, long long& base, int& Lp) {
+  info = H.sinfo[s];
+  base = H.soff[s];
+  Lp = (int)((H.soff[s + 1] - base) / (32 * info.y));
+}
+
+// Scalar visitor (setup kernels): every warp takes units in a grid-stride
+// loop; op.entry(acc, k, r) sees every slot k of row r (padding included:
+// value 0, column 0), op.finish(r, acc) the combined result (max or sum).
+// For long rows only lane 0 calls finish.
 template <bool MAX, class Op>
 __device__ __forceinline__ void hyb_rows(const Hyb& H, Op& op) {
   const int lane = threadIdx.x & 31;
@@ -37,39 +90,114 @@ __device__ __forceinline__ void hyb_rows(const Hyb& H, Op& op) {
   const int units = H.n_long + H.n_slices;
   for (int u = gwarp; u < units; u += nwarps) {
     if (u < H.n_long) {
-      const long long beg = H.loff[u], end = H.loff[u + 1];
-      if (lane == 0) op.begin(u);
       double acc = 0.0;
-#pragma unroll 4
-      for (long long k = beg + lane; k < end; k += 32) acc = op.entry(acc, k, u);
+      for (long long k = H.loff[u] + lane; k < H.loff[u + 1]; k += 32) acc = op.entry(acc, k, u);
       acc = MAX ? warp_max(acc) : warp_sum(acc);
       if (lane == 0) op.finish(u, acc);
     } else {
-      const int s = u - H.n_long;
-      const int r = H.n_long + s * 32 + lane;
-      const long long base = H.soff[s];
-      const int L = (int)((H.soff[s + 1] - base) >> 5);
-      const bool valid = r < H.rows;
-      if (valid) op.begin(r);
-      double acc = 0.0;
-      long long k = base + lane;
-#pragma unroll 4
-      for (int e = 0; e < L; ++e, k += 32) acc = op.entry(acc, k, r);
-      if (valid) op.finish(r, acc);
+      int2 info;
+      long long base;
+      int Lp;
+      slice_shape(H, u - H.n_long, info, base, Lp);
+      for (int q = 0; q < info.y; ++q) {
+        const int r = info.x + 32 * q + lane;
+        double acc = 0.0;
+        for (int e = 0; e < Lp; ++e) acc = op.entry(acc, slice_slot(base, Lp, info.y, q, e, lane), r);
+        if (r < H.rows) op.finish(r, acc);
+      }
     }
   }
 }
 
-// acc + a_k * vec[col_k] with the streaming policy on the matrix
-struct DotEntry {
-  const int* __restrict__ ci;
-  const double* __restrict__ v;
-  const double* __restrict__ vec;
-  __device__ __forceinline__ double entry(double acc, long long k, int) const {
-    const int c = __ldcs(ci + k);
-    return acc + __ldcs(v + k) * __ldg(vec + c);
+// Dot-product visitor (hot path): acc_r = sum over row r of a_rk vec[col_k].
+// `op` supplies State begin(r) (its epilogue loads, issued before the row's
+// entries) and finish(r, acc, state). Long rows: a warp per row, 4 entries per
+// lane per step. Slices: R rows per thread, 2 entries per load, so a thread
+// has 2R independent gathers in flight per step.
+template <int R, class Op>
+__device__ __forceinline__ void slice_dot(const Hyb& H, int row0, long long base, int Lp,
+                                          const double* __restrict__ vec, Op& op, unsigned long long pol,
+                                          int lane) {
+  typename Op::State st[R];
+  double acc[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int r = row0 + 32 * q + lane;
+    if (r < H.rows) st[q] = op.begin(r);
+    acc[q] = 0.0;
   }
-};
+  if (Lp == 1) {
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const long long k = base + 32 * q + lane;
+      const int c = ld_stream(H.ci + k, pol);
+      acc[q] += ld_stream(H.v + k, pol) * __ldg(vec + c);
+    }
+  } else {
+    const int L2 = Lp >> 1;
+    long long k = base + 2 * lane;
+#pragma unroll 2
+    for (int e2 = 0; e2 < L2; ++e2) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int2 c = ld_stream2(H.ci + k + 64 * q, pol);
+        const double2 a = ld_stream2(H.v + k + 64 * q, pol);
+        const double g0 = __ldg(vec + c.x), g1 = __ldg(vec + c.y);
+        acc[q] += a.x * g0;
+        acc[q] += a.y * g1;
+      }
+      k += 64 * R;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int r = row0 + 32 * q + lane;
+    if (r < H.rows) op.finish(r, acc[q], st[q]);
+  }
+}
+
+template <class Op>
+__device__ __forceinline__ void hyb_dot(const Hyb& H, const double* __restrict__ vec, Op& op) {
+  const unsigned long long pol = stream_policy();
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
+  const int units = H.n_long + H.n_slices;
+  for (int u = gwarp; u < units; u += nwarps) {
+    if (u < H.n_long) {
+      const long long beg = H.loff[u], end = H.loff[u + 1];
+      typename Op::State st{};
+      if (lane == 0) st = op.begin(u);
+      double acc = 0.0;
+#pragma unroll 2
+      for (long long k = beg + 4 * lane; k < end; k += 128) {
+        const int4 c = ld_stream4(H.ci + k, pol);
+        const double2 a = ld_stream2(H.v + k, pol);
+        const double2 b = ld_stream2(H.v + k + 2, pol);
+        const double g0 = __ldg(vec + c.x), g1 = __ldg(vec + c.y), g2 = __ldg(vec + c.z), g3 = __ldg(vec + c.w);
+        acc += a.x * g0;
+        acc += a.y * g1;
+        acc += b.x * g2;
+        acc += b.y * g3;
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) op.finish(u, acc, st);
+    } else {
+      int2 info;
+      long long base;
+      int Lp;
+      slice_shape(H, u - H.n_long, info, base, Lp);
+      if (info.y == 4)
+        slice_dot<4>(H, info.x, base, Lp, vec, op, pol, lane);
+      else if (info.y == 2)
+        slice_dot<2>(H, info.x, base, Lp, vec, op, pol, lane);
+      else
+        slice_dot<1>(H, info.x, base, Lp, vec, op, pol, lane);
+    }
+  }
+}
+
+struct NoState {};
 
 // ---------------------------------------------------------------------------
 // setup kernels
@@ -77,7 +205,6 @@ struct DotEntry {
 struct AbsMaxOp {
   const double* __restrict__ v;
   double* __restrict__ out;
-  __device__ __forceinline__ void begin(int) {}
   __device__ __forceinline__ double entry(double acc, long long k, int) const { return fmax(acc, fabs(v[k])); }
   __device__ __forceinline__ void finish(int r, double acc) { out[r] = acc; }
 };
@@ -91,7 +218,6 @@ struct AbsPowSumOp {
   const double* __restrict__ v;
   double alpha;
   double* __restrict__ out;
-  __device__ __forceinline__ void begin(int) {}
   __device__ __forceinline__ double entry(double acc, long long k, int) const {
     const double a = fabs(v[k]);
     return acc + (alpha == 1.0 ? a : (a > 0.0 ? pow(a, alpha) : 0.0));
@@ -110,7 +236,6 @@ struct ScaleOp {
   const double* __restrict__ rf;  // row factors of A (length m)
   const double* __restrict__ sf;  // column factors of A (length n)
   int transposed, rows;
-  __device__ __forceinline__ void begin(int) {}
   __device__ __forceinline__ double entry(double acc, long long k, int r) const {
     if (r < rows) {
       const int c = ci[k];
@@ -156,19 +281,16 @@ __global__ void k_fill(double* __restrict__ v, double val, long long len) {
     v[i] = val;
 }
 
-struct SpmvOp : DotEntry {
+struct SpmvOp {
+  using State = NoState;
   double* __restrict__ out;
-  __device__ __forceinline__ void begin(int) {}
-  __device__ __forceinline__ void finish(int r, double acc) { out[r] = acc; }
+  __device__ __forceinline__ State begin(int) { return {}; }
+  __device__ __forceinline__ void finish(int r, double acc, const State&) { out[r] = acc; }
 };
 
 __global__ void __launch_bounds__(TPB) k_spmv(Hyb M, const double* __restrict__ x, double* __restrict__ y) {
-  SpmvOp op;
-  op.ci = M.ci;
-  op.v = M.v;
-  op.vec = x;
-  op.out = y;
-  hyb_rows<false>(M, op);
+  SpmvOp op{y};
+  hyb_dot(M, x, op);
 }
 
 __global__ void __launch_bounds__(TPB) k_sumsq_partials(const double* __restrict__ v, int len,
@@ -218,77 +340,60 @@ __global__ void k_finish_setup(DevState* st, const double* __restrict__ scal, do
 // ---------------------------------------------------------------------------
 // the two fused half-steps of one PDHG iteration
 // ---------------------------------------------------------------------------
-struct PrimalOp : DotEntry {
+struct PrimalOp {
+  struct State {
+    double x, c, s;
+  };
   const double* __restrict__ ch;
   double* __restrict__ x;
   double* __restrict__ xbar;
   double* __restrict__ xsum;
   double tau;
   int accumulate;
-  double xj, cj, sj;
-  __device__ __forceinline__ void begin(int j) {
-    xj = __ldcs(x + j);
-    cj = __ldcs(ch + j);
-    sj = accumulate ? __ldcs(xsum + j) : 0.0;
+  __device__ __forceinline__ State begin(int j) {
+    return {__ldcs(x + j), __ldcs(ch + j), accumulate ? __ldcs(xsum + j) : 0.0};
   }
-  __device__ __forceinline__ void finish(int j, double g) {
-    const double xn = relu(xj - tau * (cj - g));
-    xbar[j] = 2.0 * xn - xj;  // default policy: gathered by the dual step next
+  __device__ __forceinline__ void finish(int j, double g, const State& s) {
+    const double xn = relu(s.x - tau * (s.c - g));
+    xbar[j] = 2.0 * xn - s.x;  // default policy: gathered by the dual step next
     __stcs(x + j, xn);
-    if (accumulate) __stcs(xsum + j, sj + xn);
+    if (accumulate) __stcs(xsum + j, s.s + xn);
   }
 };
 
-__global__ void __launch_bounds__(TPB) k_primal_step(Hyb At, const double* __restrict__ y,
+__global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS) k_primal_step(Hyb At, const double* __restrict__ y,
                                                      const double* __restrict__ ch, double* __restrict__ x,
                                                      double* __restrict__ xbar, double* __restrict__ xsum,
                                                      const DevState* __restrict__ st, int accumulate) {
-  PrimalOp op;
-  op.ci = At.ci;
-  op.v = At.v;
-  op.vec = y;
-  op.ch = ch;
-  op.x = x;
-  op.xbar = xbar;
-  op.xsum = xsum;
-  op.tau = st->tau;
-  op.accumulate = accumulate;
-  hyb_rows<false>(At, op);
+  PrimalOp op{ch, x, xbar, xsum, st->tau, accumulate};
+  hyb_dot(At, y, op);
 }
 
-struct DualOp : DotEntry {
+struct DualOp {
+  struct State {
+    double y, b, s;
+  };
   const double* __restrict__ bh;
   double* __restrict__ y;
   double* __restrict__ ysum;
   double sigma;
   int accumulate;
-  double yi, bi, si;
-  __device__ __forceinline__ void begin(int i) {
-    yi = y[i];
-    bi = __ldcs(bh + i);
-    si = accumulate ? __ldcs(ysum + i) : 0.0;
+  __device__ __forceinline__ State begin(int i) {
+    return {y[i], __ldcs(bh + i), accumulate ? __ldcs(ysum + i) : 0.0};
   }
-  __device__ __forceinline__ void finish(int i, double h) {
-    const double yn = yi + sigma * (bi - h);
+  __device__ __forceinline__ void finish(int i, double h, const State& s) {
+    const double yn = s.y + sigma * (s.b - h);
     y[i] = yn;  // default policy: gathered by the primal step next
-    if (accumulate) __stcs(ysum + i, si + yn);
+    if (accumulate) __stcs(ysum + i, s.s + yn);
   }
 };
 
-__global__ void __launch_bounds__(TPB) k_dual_step(Hyb A, const double* __restrict__ xbar,
+__global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS) k_dual_step(Hyb A, const double* __restrict__ xbar,
                                                    const double* __restrict__ bh, double* __restrict__ y,
                                                    double* __restrict__ ysum, const DevState* __restrict__ st,
                                                    int accumulate) {
-  DualOp op;
-  op.ci = A.ci;
-  op.v = A.v;
-  op.vec = xbar;
-  op.bh = bh;
-  op.y = y;
-  op.ysum = ysum;
-  op.sigma = st->sigma;
-  op.accumulate = accumulate;
-  hyb_rows<false>(A, op);
+  DualOp op{bh, y, ysum, st->sigma, accumulate};
+  hyb_dot(A, xbar, op);
 }
 
 __global__ void k_add_counters(DevState* st, long long dk) {
@@ -311,14 +416,15 @@ __global__ void k_make_average(const double* __restrict__ xs, const double* __re
   }
 }
 
-struct EvalDualOp : DotEntry {
+struct EvalDualOp {
+  using State = NoState;
   const double* __restrict__ ch;
   const double* __restrict__ dc;
   const double* __restrict__ px;
   const double* __restrict__ xr;
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  __device__ __forceinline__ void begin(int) {}
-  __device__ __forceinline__ void finish(int j, double g) {
+  __device__ __forceinline__ State begin(int) { return {}; }
+  __device__ __forceinline__ void finish(int j, double g, const State&) {
     const double c = ch[j];
     const double rd = relu(g - c);
     const double zh = relu(c - g);
@@ -341,14 +447,11 @@ __global__ void __launch_bounds__(TPB) k_eval_dual(Hyb At, const double* __restr
                                                    const double* __restrict__ px, const double* __restrict__ xr,
                                                    double* __restrict__ partials) {
   EvalDualOp op;
-  op.ci = At.ci;
-  op.v = At.v;
-  op.vec = py;
   op.ch = ch;
   op.dc = dc;
   op.px = px;
   op.xr = xr;
-  hyb_rows<false>(At, op);
+  hyb_dot(At, py, op);
   const bool mx[6] = {false, false, true, false, false, false};
   block_reduce<6>(op.acc, mx);
   if (threadIdx.x == 0) {
@@ -362,14 +465,15 @@ __global__ void __launch_bounds__(TPB) k_eval_dual(Hyb At, const double* __restr
   }
 }
 
-struct EvalPrimalOp : DotEntry {
+struct EvalPrimalOp {
+  using State = NoState;
   const double* __restrict__ bh;
   const double* __restrict__ dr;
   const double* __restrict__ py;
   const double* __restrict__ yr;
   double acc[5] = {0, 0, 0, 0, 0};
-  __device__ __forceinline__ void begin(int) {}
-  __device__ __forceinline__ void finish(int i, double h) {
+  __device__ __forceinline__ State begin(int) { return {}; }
+  __device__ __forceinline__ void finish(int i, double h, const State&) {
     const double b = bh[i];
     const double rp = b - h;
     const double rpu = rp / dr[i];
@@ -390,14 +494,11 @@ __global__ void __launch_bounds__(TPB) k_eval_primal(Hyb A, const double* __rest
                                                      const double* __restrict__ py, const double* __restrict__ yr,
                                                      double* __restrict__ partials) {
   EvalPrimalOp op;
-  op.ci = A.ci;
-  op.v = A.v;
-  op.vec = px;
   op.bh = bh;
   op.dr = dr;
   op.py = py;
   op.yr = yr;
-  hyb_rows<false>(A, op);
+  hyb_dot(A, px, op);
   const bool mx[5] = {false, false, true, false, false};
   block_reduce<5>(op.acc, mx);
   if (threadIdx.x == 0) {
@@ -548,15 +649,16 @@ __global__ void k_apply(const DevState* __restrict__ st, double* __restrict__ x,
   }
 }
 
-struct PackDualOp : DotEntry {
+struct PackDualOp {
+  using State = NoState;
   const int* __restrict__ perm;
   const double* __restrict__ px;
   const double* __restrict__ ch;
   const double* __restrict__ dc;
   double* __restrict__ ox;
   double* __restrict__ oz;
-  __device__ __forceinline__ void begin(int) {}
-  __device__ __forceinline__ void finish(int j, double g) {
+  __device__ __forceinline__ State begin(int) { return {}; }
+  __device__ __forceinline__ void finish(int j, double g, const State&) {
     const int o = perm[j];
     if (ox) ox[o] = dc[j] * px[j];
     if (oz) oz[o] = relu(ch[j] - g) / dc[j];
@@ -567,17 +669,8 @@ __global__ void __launch_bounds__(TPB) k_pack_dual(Hyb At, const int* __restrict
                                                    const double* __restrict__ px, const double* __restrict__ py,
                                                    const double* __restrict__ ch, const double* __restrict__ dc,
                                                    double* __restrict__ ox, double* __restrict__ oz) {
-  PackDualOp op;
-  op.ci = At.ci;
-  op.v = At.v;
-  op.vec = py;
-  op.perm = perm;
-  op.px = px;
-  op.ch = ch;
-  op.dc = dc;
-  op.ox = ox;
-  op.oz = oz;
-  hyb_rows<false>(At, op);
+  PackDualOp op{perm, px, ch, dc, ox, oz};
+  hyb_dot(At, py, op);
 }
 
 __global__ void k_pack_y(const int* __restrict__ perm, const double* __restrict__ py, const double* __restrict__ dr,
@@ -658,6 +751,13 @@ void launch_pack_solution(const Hyb& At, const int* perm_x, const int* perm_y, c
                           int grid, cudaStream_t s) {
   if (ox || oz) k_pack_dual<<<grid, TPB, 0, s>>>(At, perm_x, px, py, ch, dc, ox, oz);
   if (oy) k_pack_y<<<grid, TPB, 0, s>>>(perm_y, py, dr, oy, At.cols);
+}
+
+void prefer_l1_for_step_kernels() {
+  // the step kernels use no shared memory: give the on-chip memory to L1,
+  // which caches the gathered vector
+  cudaFuncSetAttribute(k_primal_step, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_dual_step, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
 }
 
 }  // namespace pdhg

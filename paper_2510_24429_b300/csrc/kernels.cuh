@@ -57,4 +57,7 @@ void launch_pack_solution(const Hyb& At, const int* perm_x, const int* perm_y, c
                           const double* ch, const double* dc, const double* dr, double* ox, double* oy, double* oz,
                           int grid, cudaStream_t s);
 
+// the step kernels use no shared memory: prefer the largest L1
+void prefer_l1_for_step_kernels();
+
 }  // namespace pdhg

@@ -203,39 +203,68 @@ struct HostHyb {
   int rows = 0, cols = 0, n_long = 0, n_slices = 0;
   int64_t nnz = 0;
   std::vector<long long> loff, soff;
+  std::vector<int> sinfo;  // pairs (first row, rows per thread)
   std::vector<int> ci;
   std::vector<double> v;
 };
 
-// CSR with rows already sorted by decreasing length -> long rows + slices.
+// CSR with rows already sorted by decreasing length -> the Hyb layout (long
+// rows 4-aligned and padded to a multiple of 4; slices of 32*R rows, R = 4
+// for rows of length <= 1, 2 for length <= 8, else 1, capped by max_rpt;
+// slice length rounded up to even when above 1, entries stored in pairs).
 HostHyb make_hyb(int rows, int cols, const std::vector<int64_t>& rp, const std::vector<int>& ci,
-                 const std::vector<double>& v, int long_min) {
+                 const std::vector<double>& v, int long_min, int max_rpt) {
   HostHyb H;
   H.rows = rows;
   H.cols = cols;
   H.nnz = rp[rows];
   auto len = [&](int r) { return (int)(rp[r + 1] - rp[r]); };
   while (H.n_long < rows && len(H.n_long) >= long_min) ++H.n_long;
-  H.loff.assign(rp.begin(), rp.begin() + H.n_long + 1);
-  const int rest = rows - H.n_long;
-  H.n_slices = (rest + 31) / 32;
+  H.loff.resize(H.n_long + 1);
+  H.loff[0] = 0;
+  for (int r = 0; r < H.n_long; ++r) H.loff[r + 1] = H.loff[r] + ((len(r) + 3) / 4) * 4;
+  // slices
+  std::vector<int> s_row0, s_R, s_Lp;
+  for (int r = H.n_long; r < rows;) {
+    const int L = len(r);
+    int R = L <= 1 ? 4 : (L <= 8 ? 2 : 1);
+    R = std::max(1, std::min(R, max_rpt));
+    s_row0.push_back(r);
+    s_R.push_back(R);
+    s_Lp.push_back(L <= 1 ? L : (L + 1) / 2 * 2);
+    r += 32 * R;
+  }
+  H.n_slices = (int)s_row0.size();
   H.soff.resize(H.n_slices + 1);
-  H.soff[0] = rp[H.n_long];
-  for (int s = 0; s < H.n_slices; ++s) H.soff[s + 1] = H.soff[s] + 32LL * len(H.n_long + 32 * s);
+  H.soff[0] = H.loff[H.n_long];
+  H.sinfo.resize(2 * H.n_slices);
+  for (int s = 0; s < H.n_slices; ++s) {
+    H.soff[s + 1] = H.soff[s] + 32LL * s_R[s] * s_Lp[s];
+    H.sinfo[2 * s] = s_row0[s];
+    H.sinfo[2 * s + 1] = s_R[s];
+  }
   const int64_t slots = H.soff[H.n_slices];
   H.ci.assign(slots, 0);
   H.v.assign(slots, 0.0);
-  std::copy(ci.begin(), ci.begin() + rp[H.n_long], H.ci.begin());
-  std::copy(v.begin(), v.begin() + rp[H.n_long], H.v.begin());
-  for (int s = 0; s < H.n_slices; ++s)
-    for (int lane = 0; lane < 32; ++lane) {
-      const int r = H.n_long + 32 * s + lane;
-      if (r >= rows) break;
-      for (int e = 0; e < len(r); ++e) {
-        H.ci[H.soff[s] + 32LL * e + lane] = ci[rp[r] + e];
-        H.v[H.soff[s] + 32LL * e + lane] = v[rp[r] + e];
-      }
+  for (int r = 0; r < H.n_long; ++r)
+    for (int e = 0; e < len(r); ++e) {
+      H.ci[H.loff[r] + e] = ci[rp[r] + e];
+      H.v[H.loff[r] + e] = v[rp[r] + e];
     }
+  for (int s = 0; s < H.n_slices; ++s) {
+    const int R = s_R[s], Lp = s_Lp[s];
+    for (int q = 0; q < R; ++q)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int r = s_row0[s] + 32 * q + lane;
+        if (r >= rows) continue;
+        for (int e = 0; e < len(r); ++e) {
+          const long long k = Lp == 1 ? H.soff[s] + 32 * q + lane
+                                      : H.soff[s] + ((long long)(e / 2) * R + q) * 64 + 2 * lane + (e % 2);
+          H.ci[k] = ci[rp[r] + e];
+          H.v[k] = v[rp[r] + e];
+        }
+      }
+  }
   return H;
 }
 
@@ -248,11 +277,14 @@ pdhg_status upload_hyb(pdhg_ctx* ctx, const HostHyb& h, Hyb& d) {
   d.slots = (long long)h.v.size();
   CK(ctx, dalloc(ctx, &d.loff, h.loff.size()));
   CK(ctx, dalloc(ctx, &d.soff, h.soff.size()));
+  CK(ctx, dalloc(ctx, &d.sinfo, std::max<size_t>(1, h.sinfo.size() / 2)));
   CK(ctx, dalloc(ctx, &d.ci, h.ci.size()));
   CK(ctx, dalloc(ctx, &d.v, h.v.size()));
   cudaStream_t s = ctx->stream;
   CK(ctx, cudaMemcpyAsync(d.loff, h.loff.data(), sizeof(long long) * h.loff.size(), cudaMemcpyHostToDevice, s));
   CK(ctx, cudaMemcpyAsync(d.soff, h.soff.data(), sizeof(long long) * h.soff.size(), cudaMemcpyHostToDevice, s));
+  if (!h.sinfo.empty())
+    CK(ctx, cudaMemcpyAsync(d.sinfo, h.sinfo.data(), sizeof(int) * h.sinfo.size(), cudaMemcpyHostToDevice, s));
   CK(ctx, cudaMemcpyAsync(d.ci, h.ci.data(), sizeof(int) * h.ci.size(), cudaMemcpyHostToDevice, s));
   CK(ctx, cudaMemcpyAsync(d.v, h.v.data(), sizeof(double) * h.v.size(), cudaMemcpyHostToDevice, s));
   // the host vectors are freed when setup returns: wait for the copies
@@ -288,7 +320,7 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
         v[q] = val[k];
       }
     }
-    hA = make_hyb((int)m, (int)n, rp, ci, v, o.long_row_min);
+    hA = make_hyb((int)m, (int)n, rp, ci, v, o.long_row_min, o.rows_per_thread);
   }
   {
     // transpose (stable counting sort over the caller's columns), then the
@@ -315,7 +347,7 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
       std::copy(tci.begin() + tp[j], tci.begin() + tp[j + 1], ci.begin() + rp[r]);
       std::copy(tv.begin() + tp[j], tv.begin() + tp[j + 1], v.begin() + rp[r]);
     }
-    hT = make_hyb((int)n, (int)m, rp, ci, v, o.long_row_min);
+    hT = make_hyb((int)n, (int)m, rp, ci, v, o.long_row_min, o.rows_per_thread);
   }
   std::vector<double> bi(m), cI(n), x0i, y0i;
   for (int64_t r = 0; r < m; ++r) bi[r] = b[py[r]];
@@ -343,7 +375,8 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   double** vecs_m[] = {&ctx->b, &ctx->bh, &ctx->dr, &ctx->y, &ctx->ysum, &ctx->yavg, &ctx->yr, &ctx->tmp_m};
   for (double** p : vecs_n) CK(ctx, dalloc(ctx, p, n));
   for (double** p : vecs_m) CK(ctx, dalloc(ctx, p, m));
-  ctx->nb_eval = std::max(1, std::min(ctx->sms * 4, std::max(unit_grid(A), unit_grid(At))));
+  ctx->nb_eval = std::max(1, std::min(ctx->sms * 16, std::max(unit_grid(A), unit_grid(At))));
+  prefer_l1_for_step_kernels();
   CK(ctx, dalloc(ctx, &ctx->partials, (size_t)std::max(ctx->nb_eval, ctx->sms * 8) * NQ));
   CK(ctx, dalloc(ctx, &ctx->scal, 16));
   CK(ctx, dalloc(ctx, &ctx->st, 1));
@@ -490,6 +523,7 @@ void pdhg_default_options(pdhg_options* o) {
   o->kernel_timing = 0;
   o->polish_switch = 1e-5;
   o->long_row_min = 64;
+  o->rows_per_thread = 4;
 }
 
 pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
@@ -509,7 +543,7 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     pdhg_default_options(&o);
   if (o.precision != PDHG_FP64) return fail(nullptr, PDHG_ERR_INVALID, "only PDHG_FP64 is available in this build");
   if (o.eval_every < 1 || o.ruiz_iters < 0 || o.power_iters < 1 || !(o.step_factor > 0.0) || o.pc_alpha < 0.0 ||
-      o.pc_alpha > 2.0 || o.long_row_min < 1 || o.snapshot_every < 0 || o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
+      o.pc_alpha > 2.0 || o.long_row_min < 1 || !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4) || o.snapshot_every < 0 || o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
     return fail(nullptr, PDHG_ERR_INVALID, "option out of range");
 
   // host copies when the caller passed device pointers

@@ -49,6 +49,7 @@ class pdhg_options(C.Structure):
         ("kernel_timing", C.c_int),
         ("polish_switch", C.c_double),
         ("long_row_min", C.c_int),
+        ("rows_per_thread", C.c_int),
         ("reserved", C.c_int * 8),
     ]
 
