@@ -84,7 +84,7 @@ typedef struct {
   int use_graphs;         /* 1: replay evaluation blocks as CUDA graphs (1) */
   int kernel_timing;      /* 1: time the two step kernels with CUDA events (0) */
   double polish_switch;   /* PDHG_MIXED: rel. KKT at which FP64 iterations take over (1e-5) */
-  int long_row_min;       /* rows with at least this many entries get a warp each (64) */
+  int long_row_min;       /* rows with at least this many entries get a warp each (128) */
   int rows_per_thread;    /* most rows one thread reduces at once in short rows: 1, 2 or 4 (4) */
   int reserved[8];
 } pdhg_options;

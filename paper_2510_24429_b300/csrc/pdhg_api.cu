@@ -522,7 +522,7 @@ void pdhg_default_options(pdhg_options* o) {
   o->use_graphs = 1;
   o->kernel_timing = 0;
   o->polish_switch = 1e-5;
-  o->long_row_min = 64;
+  o->long_row_min = 128;
   o->rows_per_thread = 4;
 }
 
