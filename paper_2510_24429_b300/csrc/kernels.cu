@@ -21,6 +21,8 @@
 // kernels are latency bound, so occupancy matters more than registers: with
 // 6 blocks of 256 threads (<= 40 registers) they ran ~1.9x faster on the
 // large LP than with the compiler's free choice (80 registers, 3 blocks).
+// The epilogue loads are issued when a row finishes (not prefetched) so the
+// 40 registers suffice without spills.
 #ifndef PDHG_STEP_MIN_BLOCKS
 #define PDHG_STEP_MIN_BLOCKS 6
 #endif
@@ -114,7 +116,7 @@ __device__ __forceinline__ void hyb_rows(const Hyb& H, Op& op) {
 // Dot-product visitor (hot path): acc_r = sum over row r of a_rk vec[col_k].
 // `op` supplies State begin(r) (its epilogue loads, issued before the row's
 // entries) and finish(r, acc, state). Long rows: a warp per row, 4 entries per
-// lane per step. Slices: R rows per thread, 2 entries per load, so a thread
+// lane per step (two pairs from two contiguous halves). Slices: R rows per thread, 2 entries per load, so a thread
 // has 2R independent gathers in flight per step.
 template <int R, class Op>
 __device__ __forceinline__ void slice_dot(const Hyb& H, int row0, long long base, int Lp,
@@ -171,12 +173,18 @@ __device__ __forceinline__ void hyb_dot(const Hyb& H, const double* __restrict__
       typename Op::State st{};
       if (lane == 0) st = op.begin(u);
       double acc = 0.0;
+      // a step covers 128 entries as two contiguous 64-entry halves; lane L
+      // takes entries 2L, 2L+1 of each half, so every load instruction of the
+      // warp reads whole sectors (256 B of indices, 512 B of values)
 #pragma unroll 2
-      for (long long k = beg + 4 * lane; k < end; k += 128) {
-        const int4 c = ld_stream4(H.ci + k, pol);
+      for (long long k = beg + 2 * lane; k < end; k += 128) {
+        const int2 c0 = ld_stream2(H.ci + k, pol);
         const double2 a = ld_stream2(H.v + k, pol);
-        const double2 b = ld_stream2(H.v + k + 2, pol);
-        const double g0 = __ldg(vec + c.x), g1 = __ldg(vec + c.y), g2 = __ldg(vec + c.z), g3 = __ldg(vec + c.w);
+        const bool second = k + 64 < end;
+        const int2 c1 = second ? ld_stream2(H.ci + k + 64, pol) : make_int2(0, 0);
+        const double2 b = second ? ld_stream2(H.v + k + 64, pol) : make_double2(0.0, 0.0);
+        const double g0 = __ldg(vec + c0.x), g1 = __ldg(vec + c0.y);
+        const double g2 = __ldg(vec + c1.x), g3 = __ldg(vec + c1.y);
         acc += a.x * g0;
         acc += a.y * g1;
         acc += b.x * g2;
@@ -343,23 +351,20 @@ __global__ void k_finish_setup(DevState* st, const double* __restrict__ scal, do
 // the two fused half-steps of one PDHG iteration
 // ---------------------------------------------------------------------------
 struct PrimalOp {
-  struct State {
-    double x, c, s;
-  };
+  using State = NoState;
   const double* __restrict__ ch;
   double* __restrict__ x;
   double* __restrict__ xbar;
   double* __restrict__ xsum;
   double tau;
   int accumulate;
-  __device__ __forceinline__ State begin(int j) {
-    return {__ldcs(x + j), __ldcs(ch + j), accumulate ? __ldcs(xsum + j) : 0.0};
-  }
-  __device__ __forceinline__ void finish(int j, double g, const State& s) {
-    const double xn = relu(s.x - tau * (s.c - g));
-    xbar[j] = 2.0 * xn - s.x;  // default policy: gathered by the dual step next
+  __device__ __forceinline__ State begin(int) { return {}; }
+  __device__ __forceinline__ void finish(int j, double g, const State&) {
+    const double xj = __ldcs(x + j);
+    const double xn = relu(xj - tau * (__ldcs(ch + j) - g));
+    xbar[j] = 2.0 * xn - xj;  // default policy: gathered by the dual step next
     __stcs(x + j, xn);
-    if (accumulate) __stcs(xsum + j, s.s + xn);
+    if (accumulate) __stcs(xsum + j, __ldcs(xsum + j) + xn);
   }
 };
 
@@ -372,21 +377,17 @@ __global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS) k_primal_step(Hyb A
 }
 
 struct DualOp {
-  struct State {
-    double y, b, s;
-  };
+  using State = NoState;
   const double* __restrict__ bh;
   double* __restrict__ y;
   double* __restrict__ ysum;
   double sigma;
   int accumulate;
-  __device__ __forceinline__ State begin(int i) {
-    return {y[i], __ldcs(bh + i), accumulate ? __ldcs(ysum + i) : 0.0};
-  }
-  __device__ __forceinline__ void finish(int i, double h, const State& s) {
-    const double yn = s.y + sigma * (s.b - h);
+  __device__ __forceinline__ State begin(int) { return {}; }
+  __device__ __forceinline__ void finish(int i, double h, const State&) {
+    const double yn = y[i] + sigma * (__ldcs(bh + i) - h);
     y[i] = yn;  // default policy: gathered by the primal step next
-    if (accumulate) __stcs(ysum + i, s.s + yn);
+    if (accumulate) __stcs(ysum + i, __ldcs(ysum + i) + yn);
   }
 };
 
