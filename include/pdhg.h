@@ -86,6 +86,7 @@ typedef struct {
   double polish_switch;   /* PDHG_MIXED: rel. KKT at which FP64 iterations take over (1e-5) */
   int long_row_min;       /* rows with at least this many entries get a warp each (128) */
   int rows_per_thread;    /* most rows one thread reduces at once in short rows: 1, 2 or 4 (4) */
+  int dual_hot_cols;      /* entries of xbar the dual step stages in shared memory, 0 = off; <= 24576 (0) */
   int reserved[8];
 } pdhg_options;
 

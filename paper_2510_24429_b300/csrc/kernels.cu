@@ -113,15 +113,27 @@ __device__ __forceinline__ void hyb_rows(const Hyb& H, Op& op) {
   }
 }
 
+// How the dot-product visitor reads the gathered vector: through L1 from
+// global memory, or, for the first `hot` entries, from a shared-memory copy.
+struct GlobalGather {
+  const double* __restrict__ vec;
+  __device__ __forceinline__ double operator()(int c) const { return __ldg(vec + c); }
+};
+struct HotGather {
+  const double* __restrict__ vec;
+  const double* hot_vals;  // shared memory copy of vec[0, hot)
+  int hot;
+  __device__ __forceinline__ double operator()(int c) const { return c < hot ? hot_vals[c] : __ldg(vec + c); }
+};
+
 // Dot-product visitor (hot path): acc_r = sum over row r of a_rk vec[col_k].
 // `op` supplies State begin(r) (its epilogue loads, issued before the row's
 // entries) and finish(r, acc, state). Long rows: a warp per row, 4 entries per
 // lane per step (two pairs from two contiguous halves). Slices: R rows per thread, 2 entries per load, so a thread
 // has 2R independent gathers in flight per step.
-template <int R, class Op>
-__device__ __forceinline__ void slice_dot(const Hyb& H, int row0, long long base, int Lp,
-                                          const double* __restrict__ vec, Op& op, unsigned long long pol,
-                                          int lane) {
+template <int R, class Op, class G>
+__device__ __forceinline__ void slice_dot(const Hyb& H, int row0, long long base, int Lp, const G& gather, Op& op,
+                                          unsigned long long pol, int lane) {
   typename Op::State st[R];
   double acc[R];
 #pragma unroll
@@ -135,7 +147,7 @@ __device__ __forceinline__ void slice_dot(const Hyb& H, int row0, long long base
     for (int q = 0; q < R; ++q) {
       const long long k = base + 32 * q + lane;
       const int c = ld_stream(H.ci + k, pol);
-      acc[q] += ld_stream(H.v + k, pol) * __ldg(vec + c);
+      acc[q] += ld_stream(H.v + k, pol) * gather(c);
     }
   } else {
     const int L2 = Lp >> 1;
@@ -146,7 +158,7 @@ __device__ __forceinline__ void slice_dot(const Hyb& H, int row0, long long base
       for (int q = 0; q < R; ++q) {
         const int2 c = ld_stream2(H.ci + k + 64 * q, pol);
         const double2 a = ld_stream2(H.v + k + 64 * q, pol);
-        const double g0 = __ldg(vec + c.x), g1 = __ldg(vec + c.y);
+        const double g0 = gather(c.x), g1 = gather(c.y);
         acc[q] += a.x * g0;
         acc[q] += a.y * g1;
       }
@@ -160,8 +172,8 @@ __device__ __forceinline__ void slice_dot(const Hyb& H, int row0, long long base
   }
 }
 
-template <class Op>
-__device__ __forceinline__ void hyb_dot(const Hyb& H, const double* __restrict__ vec, Op& op) {
+template <class Op, class G>
+__device__ __forceinline__ void hyb_dot(const Hyb& H, const G& gather, Op& op) {
   const unsigned long long pol = stream_policy();
   const int lane = threadIdx.x & 31;
   const int gwarp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
@@ -183,8 +195,8 @@ __device__ __forceinline__ void hyb_dot(const Hyb& H, const double* __restrict__
         const bool second = k + 64 < end;
         const int2 c1 = second ? ld_stream2(H.ci + k + 64, pol) : make_int2(0, 0);
         const double2 b = second ? ld_stream2(H.v + k + 64, pol) : make_double2(0.0, 0.0);
-        const double g0 = __ldg(vec + c0.x), g1 = __ldg(vec + c0.y);
-        const double g2 = __ldg(vec + c1.x), g3 = __ldg(vec + c1.y);
+        const double g0 = gather(c0.x), g1 = gather(c0.y);
+        const double g2 = gather(c1.x), g3 = gather(c1.y);
         acc += a.x * g0;
         acc += a.y * g1;
         acc += b.x * g2;
@@ -198,11 +210,11 @@ __device__ __forceinline__ void hyb_dot(const Hyb& H, const double* __restrict__
       int Lp;
       slice_shape(H, u - H.n_long, info, base, Lp);
       if (info.y == 4)
-        slice_dot<4>(H, info.x, base, Lp, vec, op, pol, lane);
+        slice_dot<4>(H, info.x, base, Lp, gather, op, pol, lane);
       else if (info.y == 2)
-        slice_dot<2>(H, info.x, base, Lp, vec, op, pol, lane);
+        slice_dot<2>(H, info.x, base, Lp, gather, op, pol, lane);
       else
-        slice_dot<1>(H, info.x, base, Lp, vec, op, pol, lane);
+        slice_dot<1>(H, info.x, base, Lp, gather, op, pol, lane);
     }
   }
 }
@@ -300,7 +312,7 @@ struct SpmvOp {
 
 __global__ void __launch_bounds__(TPB) k_spmv(Hyb M, const double* __restrict__ x, double* __restrict__ y) {
   SpmvOp op{y};
-  hyb_dot(M, x, op);
+  hyb_dot(M, GlobalGather{x}, op);
 }
 
 __global__ void __launch_bounds__(TPB) k_sumsq_partials(const double* __restrict__ v, int len,
@@ -373,7 +385,7 @@ __global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS) k_primal_step(Hyb A
                                                      double* __restrict__ xbar, double* __restrict__ xsum,
                                                      const DevState* __restrict__ st, int accumulate) {
   PrimalOp op{ch, x, xbar, xsum, st->tau, accumulate};
-  hyb_dot(At, y, op);
+  hyb_dot(At, GlobalGather{y}, op);
 }
 
 struct DualOp {
@@ -396,7 +408,23 @@ __global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS) k_dual_step(Hyb A, 
                                                    double* __restrict__ ysum, const DevState* __restrict__ st,
                                                    int accumulate) {
   DualOp op{bh, y, ysum, st->sigma, accumulate};
-  hyb_dot(A, xbar, op);
+  hyb_dot(A, GlobalGather{xbar}, op);
+}
+
+// The dual step as a persistent kernel (one 1024-thread block per SM) that
+// first copies xbar[0, hot) into shared memory. With the variables numbered by
+// decreasing column length, these are the most frequently gathered entries,
+// and their gathers then stay off the L1-to-L2 request path that bounds the
+// random gathers.
+__global__ void __launch_bounds__(HOT_TPB, 1) k_dual_step_hot(Hyb A, const double* __restrict__ xbar, int hot,
+                                                             const double* __restrict__ bh, double* __restrict__ y,
+                                                             double* __restrict__ ysum,
+                                                             const DevState* __restrict__ st, int accumulate) {
+  extern __shared__ double sh_hot[];
+  for (int i = threadIdx.x; i < hot; i += blockDim.x) sh_hot[i] = xbar[i];
+  __syncthreads();
+  DualOp op{bh, y, ysum, st->sigma, accumulate};
+  hyb_dot(A, HotGather{xbar, sh_hot, hot}, op);
 }
 
 __global__ void k_add_counters(DevState* st, long long dk) {
@@ -454,7 +482,7 @@ __global__ void __launch_bounds__(TPB) k_eval_dual(Hyb At, const double* __restr
   op.dc = dc;
   op.px = px;
   op.xr = xr;
-  hyb_dot(At, py, op);
+  hyb_dot(At, GlobalGather{py}, op);
   const bool mx[6] = {false, false, true, false, false, false};
   block_reduce<6>(op.acc, mx);
   if (threadIdx.x == 0) {
@@ -501,7 +529,7 @@ __global__ void __launch_bounds__(TPB) k_eval_primal(Hyb A, const double* __rest
   op.dr = dr;
   op.py = py;
   op.yr = yr;
-  hyb_dot(A, px, op);
+  hyb_dot(A, GlobalGather{px}, op);
   const bool mx[5] = {false, false, true, false, false};
   block_reduce<5>(op.acc, mx);
   if (threadIdx.x == 0) {
@@ -673,7 +701,7 @@ __global__ void __launch_bounds__(TPB) k_pack_dual(Hyb At, const int* __restrict
                                                    const double* __restrict__ ch, const double* __restrict__ dc,
                                                    double* __restrict__ ox, double* __restrict__ oz) {
   PackDualOp op{perm, px, ch, dc, ox, oz};
-  hyb_dot(At, py, op);
+  hyb_dot(At, GlobalGather{py}, op);
 }
 
 __global__ void k_pack_y(const int* __restrict__ perm, const double* __restrict__ py, const double* __restrict__ dr,
@@ -729,6 +757,10 @@ void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double
                       const DevState* st, int accumulate, int grid, cudaStream_t s) {
   k_dual_step<<<grid, TPB, 0, s>>>(A, xbar, bh, y, ysum, st, accumulate);
 }
+void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,
+                          const DevState* st, int accumulate, int grid, cudaStream_t s) {
+  k_dual_step_hot<<<grid, HOT_TPB, (size_t)hot * sizeof(double), s>>>(A, xbar, hot, bh, y, ysum, st, accumulate);
+}
 void launch_add_counters(DevState* st, long long dk, cudaStream_t s) { k_add_counters<<<1, 1, 0, s>>>(st, dk); }
 void launch_make_average(const double* xs, const double* ys, const double* x, const double* y, double* xa,
                          double* ya, int n, int m, const DevState* st, int grid, cudaStream_t s) {
@@ -761,6 +793,8 @@ void prefer_l1_for_step_kernels() {
   // which caches the gathered vector
   cudaFuncSetAttribute(k_primal_step, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_dual_step, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_dual_step_hot, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(HOT_MAX * sizeof(double)));
 }
 
 }  // namespace pdhg

@@ -7,6 +7,8 @@ namespace pdhg {
 
 constexpr int TPB = 256;  // threads per block of every row kernel
 constexpr int WARPS_PER_BLOCK = TPB / 32;
+constexpr int HOT_TPB = 1024;       // threads per block of the persistent dual step
+constexpr int HOT_MAX = 24576;      // most xbar entries it stages in shared memory (192 KiB)
 
 // ---- setup (scaling, power iteration, vector helpers) ----------------------
 void launch_row_absmax(const Hyb& M, double* out, int grid, cudaStream_t s);
@@ -35,6 +37,10 @@ void launch_primal_step(const Hyb& At, const double* y, const double* ch, double
 // y' = y + sigma (bhat - Ahat xbar); y <- y'; ysum += y'
 void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
                       const DevState* st, int accumulate, int grid, cudaStream_t s);
+// the same step, persistent (grid = number of SMs), with xbar[0, hot) staged
+// in shared memory; hot <= HOT_MAX
+void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,
+                          const DevState* st, int accumulate, int grid, cudaStream_t s);
 void launch_add_counters(DevState* st, long long dk, cudaStream_t s);
 
 // ---- evaluation -------------------------------------------------------------

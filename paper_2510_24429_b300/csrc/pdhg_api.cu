@@ -524,6 +524,7 @@ void pdhg_default_options(pdhg_options* o) {
   o->polish_switch = 1e-5;
   o->long_row_min = 128;
   o->rows_per_thread = 4;
+  o->dual_hot_cols = 0;
 }
 
 pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
@@ -543,7 +544,7 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     pdhg_default_options(&o);
   if (o.precision != PDHG_FP64) return fail(nullptr, PDHG_ERR_INVALID, "only PDHG_FP64 is available in this build");
   if (o.eval_every < 1 || o.ruiz_iters < 0 || o.power_iters < 1 || !(o.step_factor > 0.0) || o.pc_alpha < 0.0 ||
-      o.pc_alpha > 2.0 || o.long_row_min < 1 || !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4) || o.snapshot_every < 0 || o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
+      o.pc_alpha > 2.0 || o.long_row_min < 1 || o.dual_hot_cols < 0 || o.dual_hot_cols > HOT_MAX || !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4) || o.snapshot_every < 0 || o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
     return fail(nullptr, PDHG_ERR_INVALID, "option out of range");
 
   // host copies when the caller passed device pointers
@@ -658,6 +659,7 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
   cudaStream_t s = ctx->stream;
   CK(ctx, cudaMemcpyAsync(&ctx->st->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
   const int grT = unit_grid(ctx->At), grA = unit_grid(ctx->A);
+  const int hot = (int)std::min<int64_t>(o.dual_hot_cols, ctx->n);
   const int gv = vec_grid(ctx, std::max(n, m));
   ctx->converged = false;
   int64_t done = 0;
@@ -672,7 +674,10 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
       if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
       launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, grT, s);
       if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
-      launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, grA, s);
+      if (hot > 0)
+        launch_dual_step_hot(ctx->A, ctx->xbar, hot, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, ctx->sms, s);
+      else
+        launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, grA, s);
       if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 2], s));
     }
     launch_add_counters(ctx->st, nb, s);

@@ -50,6 +50,7 @@ class pdhg_options(C.Structure):
         ("polish_switch", C.c_double),
         ("long_row_min", C.c_int),
         ("rows_per_thread", C.c_int),
+        ("dual_hot_cols", C.c_int),
         ("reserved", C.c_int * 8),
     ]
 

@@ -265,3 +265,22 @@ def test_large_setup_and_first_iterations_match_oracle(large_lp):
     sol.iterate(2)
     assert_iterates_close(sol, orc, 1e-10)
     sol.close()
+
+
+@pytest.mark.parametrize("hot", [64, 500])
+def test_dual_step_with_shared_memory_hot_columns(tiny_lp, hot):
+    """The persistent dual step that stages xbar[0, hot) in shared memory gives
+    the same iterates (hot = 64: part staged, part gathered from global
+    memory; hot = 500: all of xbar staged)."""
+    orc, _ = pair(tiny_lp, **TINY_PLAIN)
+    orc.run(100)
+    sol = P.Solver.from_lp(tiny_lp, pock_chambolle=0, restarts=0, primal_weight=0, dual_hot_cols=hot)
+    sol.iterate(100)
+    assert_iterates_close(sol, orc, 1e-10)
+    lp = lpgen.generate(3001, 7919, 5, nnz_per_col=5, support=0.3)
+    orc, _ = pair(lp)
+    orc.run(640, 1e-9)
+    sol = P.Solver.from_lp(lp, dual_hot_cols=hot * 4)
+    sol.iterate(640, 1e-9)
+    if compare_traces(sol.trace(), orc.trace) == len(orc.trace):
+        assert_iterates_close(sol, orc, 1e-7)
