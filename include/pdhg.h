@@ -64,7 +64,9 @@ enum { PDHG_CURRENT = 0, PDHG_AVERAGE = 1, PDHG_LAST_RESTART = 2 };
 enum { PDHG_NO_RESTART = 0, PDHG_RESTART_TO_CURRENT = 1, PDHG_RESTART_TO_AVERAGE = 2 };
 
 typedef struct {
-  int precision;          /* PDHG_FP64 (default), PDHG_FP32 or PDHG_MIXED */
+  int precision;          /* PDHG_FP64 (default); PDHG_FP32: both half-steps in FP32 (matrix values,
+                             vectors, accumulation) with FP64 evaluation and restart decisions;
+                             PDHG_MIXED: as PDHG_FP32 until rel. KKT <= polish_switch, then FP64 */
   int ruiz_iters;         /* Ruiz equilibration passes (10) */
   int pock_chambolle;     /* 1: one Pock-Chambolle pass after Ruiz (1) */
   double pc_alpha;        /* Pock-Chambolle alpha in [0, 2] (1.0) */
@@ -120,6 +122,7 @@ typedef struct {
   double kernel_ms_primal, kernel_ms_dual; /* summed event times (kernel_timing) */
   int64_t kernel_launches_primal, kernel_launches_dual;
   int64_t kernel_launches; /* all kernels launched by pdhg_iterate so far */
+  int64_t polish_started_at; /* PDHG_MIXED: iteration where FP64 took over, -1 if not (yet) */
 } pdhg_info;
 
 /* One record per evaluation. */

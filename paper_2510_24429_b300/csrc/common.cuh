@@ -99,6 +99,7 @@ struct Hyb {
   int2* sinfo = nullptr;      // [n_slices] (first row, rows per thread R)
   int* ci = nullptr;          // [slots] column index (internal numbering)
   double* v = nullptr;        // [slots] value
+  float* v32 = nullptr;       // [slots] value rounded to FP32 (FP32 / mixed precision only)
   int units() const { return n_long + n_slices; }
 };
 

@@ -32,6 +32,7 @@ namespace pdhg {
 namespace {
 
 __device__ __forceinline__ double relu(double v) { return v < 0.0 ? 0.0 : v; }  // NaN passes through
+__device__ __forceinline__ float relu(float v) { return v < 0.0f ? 0.0f : v; }
 
 // ---- cache-policy loads ----------------------------------------------------
 __device__ __forceinline__ unsigned long long stream_policy() {
@@ -63,6 +64,28 @@ __device__ __forceinline__ double2 ld_stream2(const double* p, unsigned long lon
       : "l"(p), "l"(pol));
   return r;
 }
+__device__ __forceinline__ float ld_stream(const float* p, unsigned long long pol) {
+  float r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ float2 ld_stream2(const float* p, unsigned long long pol) {
+  float2 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+      : "=f"(r.x), "=f"(r.y)
+      : "l"(p), "l"(pol));
+  return r;
+}
+template <class T>
+struct Pair;
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+template <>
+struct Pair<float> {
+  using type = float2;
+};
 __device__ __forceinline__ int4 ld_stream4(const int* p, unsigned long long pol) {
   int4 r;
   asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
@@ -115,9 +138,10 @@ __device__ __forceinline__ void hyb_rows(const Hyb& H, Op& op) {
 
 // How the dot-product visitor reads the gathered vector: through L1 from
 // global memory, or, for the first `hot` entries, from a shared-memory copy.
+template <class T>
 struct GlobalGather {
-  const double* __restrict__ vec;
-  __device__ __forceinline__ double operator()(int c) const { return __ldg(vec + c); }
+  const T* __restrict__ vec;
+  __device__ __forceinline__ T operator()(int c) const { return __ldg(vec + c); }
 };
 struct HotGather {
   const double* __restrict__ vec;
@@ -131,23 +155,23 @@ struct HotGather {
 // entries) and finish(r, acc, state). Long rows: a warp per row, 4 entries per
 // lane per step (two pairs from two contiguous halves). Slices: R rows per thread, 2 entries per load, so a thread
 // has 2R independent gathers in flight per step.
-template <int R, class Op, class G>
-__device__ __forceinline__ void slice_dot(const Hyb& H, int row0, long long base, int Lp, const G& gather, Op& op,
-                                          unsigned long long pol, int lane) {
+template <int R, class T, class Op, class G>
+__device__ __forceinline__ void slice_dot(const Hyb& H, const T* __restrict__ vals, int row0, long long base, int Lp,
+                                          const G& gather, Op& op, unsigned long long pol, int lane) {
   typename Op::State st[R];
-  double acc[R];
+  T acc[R];
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     const int r = row0 + 32 * q + lane;
     if (r < H.rows) st[q] = op.begin(r);
-    acc[q] = 0.0;
+    acc[q] = T(0);
   }
   if (Lp == 1) {
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const long long k = base + 32 * q + lane;
       const int c = ld_stream(H.ci + k, pol);
-      acc[q] += ld_stream(H.v + k, pol) * gather(c);
+      acc[q] += ld_stream(vals + k, pol) * gather(c);
     }
   } else {
     const int L2 = Lp >> 1;
@@ -157,8 +181,8 @@ __device__ __forceinline__ void slice_dot(const Hyb& H, int row0, long long base
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         const int2 c = ld_stream2(H.ci + k + 64 * q, pol);
-        const double2 a = ld_stream2(H.v + k + 64 * q, pol);
-        const double g0 = gather(c.x), g1 = gather(c.y);
+        const typename Pair<T>::type a = ld_stream2(vals + k + 64 * q, pol);
+        const T g0 = gather(c.x), g1 = gather(c.y);
         acc[q] += a.x * g0;
         acc[q] += a.y * g1;
       }
@@ -172,8 +196,8 @@ __device__ __forceinline__ void slice_dot(const Hyb& H, int row0, long long base
   }
 }
 
-template <class Op, class G>
-__device__ __forceinline__ void hyb_dot(const Hyb& H, const G& gather, Op& op) {
+template <class T, class Op, class G>
+__device__ __forceinline__ void hyb_dot(const Hyb& H, const T* __restrict__ vals, const G& gather, Op& op) {
   const unsigned long long pol = stream_policy();
   const int lane = threadIdx.x & 31;
   const int gwarp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
@@ -184,19 +208,22 @@ __device__ __forceinline__ void hyb_dot(const Hyb& H, const G& gather, Op& op) {
       const long long beg = H.loff[u], end = H.loff[u + 1];
       typename Op::State st{};
       if (lane == 0) st = op.begin(u);
-      double acc = 0.0;
+      T acc = T(0);
       // a step covers 128 entries as two contiguous 64-entry halves; lane L
       // takes entries 2L, 2L+1 of each half, so every load instruction of the
       // warp reads whole sectors (256 B of indices, 512 B of values)
 #pragma unroll 2
       for (long long k = beg + 2 * lane; k < end; k += 128) {
         const int2 c0 = ld_stream2(H.ci + k, pol);
-        const double2 a = ld_stream2(H.v + k, pol);
+        const typename Pair<T>::type a = ld_stream2(vals + k, pol);
         const bool second = k + 64 < end;
         const int2 c1 = second ? ld_stream2(H.ci + k + 64, pol) : make_int2(0, 0);
-        const double2 b = second ? ld_stream2(H.v + k + 64, pol) : make_double2(0.0, 0.0);
-        const double g0 = gather(c0.x), g1 = gather(c0.y);
-        const double g2 = gather(c1.x), g3 = gather(c1.y);
+        typename Pair<T>::type b;
+        b.x = T(0);
+        b.y = T(0);
+        if (second) b = ld_stream2(vals + k + 64, pol);
+        const T g0 = gather(c0.x), g1 = gather(c0.y);
+        const T g2 = gather(c1.x), g3 = gather(c1.y);
         acc += a.x * g0;
         acc += a.y * g1;
         acc += b.x * g2;
@@ -210,11 +237,11 @@ __device__ __forceinline__ void hyb_dot(const Hyb& H, const G& gather, Op& op) {
       int Lp;
       slice_shape(H, u - H.n_long, info, base, Lp);
       if (info.y == 4)
-        slice_dot<4>(H, info.x, base, Lp, gather, op, pol, lane);
+        slice_dot<4>(H, vals, info.x, base, Lp, gather, op, pol, lane);
       else if (info.y == 2)
-        slice_dot<2>(H, info.x, base, Lp, gather, op, pol, lane);
+        slice_dot<2>(H, vals, info.x, base, Lp, gather, op, pol, lane);
       else
-        slice_dot<1>(H, info.x, base, Lp, gather, op, pol, lane);
+        slice_dot<1>(H, vals, info.x, base, Lp, gather, op, pol, lane);
     }
   }
 }
@@ -312,7 +339,7 @@ struct SpmvOp {
 
 __global__ void __launch_bounds__(TPB) k_spmv(Hyb M, const double* __restrict__ x, double* __restrict__ y) {
   SpmvOp op{y};
-  hyb_dot(M, GlobalGather{x}, op);
+  hyb_dot(M, M.v, GlobalGather<double>{x}, op);
 }
 
 __global__ void __launch_bounds__(TPB) k_sumsq_partials(const double* __restrict__ v, int len,
@@ -362,53 +389,56 @@ __global__ void k_finish_setup(DevState* st, const double* __restrict__ scal, do
 // ---------------------------------------------------------------------------
 // the two fused half-steps of one PDHG iteration
 // ---------------------------------------------------------------------------
+template <class T>
 struct PrimalOp {
   using State = NoState;
-  const double* __restrict__ ch;
-  double* __restrict__ x;
-  double* __restrict__ xbar;
-  double* __restrict__ xsum;
-  double tau;
+  const T* __restrict__ ch;
+  T* __restrict__ x;
+  T* __restrict__ xbar;
+  T* __restrict__ xsum;
+  T tau;
   int accumulate;
   __device__ __forceinline__ State begin(int) { return {}; }
-  __device__ __forceinline__ void finish(int j, double g, const State&) {
-    const double xj = __ldcs(x + j);
-    const double xn = relu(xj - tau * (__ldcs(ch + j) - g));
-    xbar[j] = 2.0 * xn - xj;  // default policy: gathered by the dual step next
+  __device__ __forceinline__ void finish(int j, T g, const State&) {
+    const T xj = __ldcs(x + j);
+    const T xn = relu(xj - tau * (__ldcs(ch + j) - g));
+    xbar[j] = T(2) * xn - xj;  // default policy: gathered by the dual step next
     __stcs(x + j, xn);
     if (accumulate) __stcs(xsum + j, __ldcs(xsum + j) + xn);
   }
 };
 
-__global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS) k_primal_step(Hyb At, const double* __restrict__ y,
-                                                     const double* __restrict__ ch, double* __restrict__ x,
-                                                     double* __restrict__ xbar, double* __restrict__ xsum,
-                                                     const DevState* __restrict__ st, int accumulate) {
-  PrimalOp op{ch, x, xbar, xsum, st->tau, accumulate};
-  hyb_dot(At, GlobalGather{y}, op);
+template <class T>
+__global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS)
+    k_primal_step(Hyb At, const T* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
+                  T* __restrict__ x, T* __restrict__ xbar, T* __restrict__ xsum, const DevState* __restrict__ st,
+                  int accumulate) {
+  PrimalOp<T> op{ch, x, xbar, xsum, (T)st->tau, accumulate};
+  hyb_dot(At, vals, GlobalGather<T>{y}, op);
 }
 
+template <class T>
 struct DualOp {
   using State = NoState;
-  const double* __restrict__ bh;
-  double* __restrict__ y;
-  double* __restrict__ ysum;
-  double sigma;
+  const T* __restrict__ bh;
+  T* __restrict__ y;
+  T* __restrict__ ysum;
+  T sigma;
   int accumulate;
   __device__ __forceinline__ State begin(int) { return {}; }
-  __device__ __forceinline__ void finish(int i, double h, const State&) {
-    const double yn = y[i] + sigma * (__ldcs(bh + i) - h);
+  __device__ __forceinline__ void finish(int i, T h, const State&) {
+    const T yn = y[i] + sigma * (__ldcs(bh + i) - h);
     y[i] = yn;  // default policy: gathered by the primal step next
     if (accumulate) __stcs(ysum + i, __ldcs(ysum + i) + yn);
   }
 };
 
-__global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS) k_dual_step(Hyb A, const double* __restrict__ xbar,
-                                                   const double* __restrict__ bh, double* __restrict__ y,
-                                                   double* __restrict__ ysum, const DevState* __restrict__ st,
-                                                   int accumulate) {
-  DualOp op{bh, y, ysum, st->sigma, accumulate};
-  hyb_dot(A, GlobalGather{xbar}, op);
+template <class T>
+__global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS)
+    k_dual_step(Hyb A, const T* __restrict__ vals, const T* __restrict__ xbar, const T* __restrict__ bh,
+                T* __restrict__ y, T* __restrict__ ysum, const DevState* __restrict__ st, int accumulate) {
+  DualOp<T> op{bh, y, ysum, (T)st->sigma, accumulate};
+  hyb_dot(A, vals, GlobalGather<T>{xbar}, op);
 }
 
 // The dual step as a persistent kernel (one 1024-thread block per SM) that
@@ -423,8 +453,8 @@ __global__ void __launch_bounds__(HOT_TPB, 1) k_dual_step_hot(Hyb A, const doubl
   extern __shared__ double sh_hot[];
   for (int i = threadIdx.x; i < hot; i += blockDim.x) sh_hot[i] = xbar[i];
   __syncthreads();
-  DualOp op{bh, y, ysum, st->sigma, accumulate};
-  hyb_dot(A, HotGather{xbar, sh_hot, hot}, op);
+  DualOp<double> op{bh, y, ysum, st->sigma, accumulate};
+  hyb_dot(A, A.v, HotGather{xbar, sh_hot, hot}, op);
 }
 
 __global__ void k_add_counters(DevState* st, long long dk) {
@@ -482,7 +512,7 @@ __global__ void __launch_bounds__(TPB) k_eval_dual(Hyb At, const double* __restr
   op.dc = dc;
   op.px = px;
   op.xr = xr;
-  hyb_dot(At, GlobalGather{py}, op);
+  hyb_dot(At, At.v, GlobalGather<double>{py}, op);
   const bool mx[6] = {false, false, true, false, false, false};
   block_reduce<6>(op.acc, mx);
   if (threadIdx.x == 0) {
@@ -529,7 +559,7 @@ __global__ void __launch_bounds__(TPB) k_eval_primal(Hyb A, const double* __rest
   op.dr = dr;
   op.py = py;
   op.yr = yr;
-  hyb_dot(A, GlobalGather{px}, op);
+  hyb_dot(A, A.v, GlobalGather<double>{px}, op);
   const bool mx[5] = {false, false, true, false, false};
   block_reduce<5>(op.acc, mx);
   if (threadIdx.x == 0) {
@@ -680,6 +710,85 @@ __global__ void k_apply(const DevState* __restrict__ st, double* __restrict__ x,
   }
 }
 
+// ---------------------------------------------------------------------------
+// mixed precision: FP32 iteration state, FP64 evaluation and restarts
+// ---------------------------------------------------------------------------
+__global__ void k_narrow(float* __restrict__ dst, const double* __restrict__ src, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+__global__ void k_widen(double* __restrict__ dst, const float* __restrict__ src, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
+// FP64 averages from FP32 running sums
+__global__ void k_make_average32(const float* __restrict__ xs, const float* __restrict__ ys,
+                                 const float* __restrict__ x, const float* __restrict__ y, double* __restrict__ xa,
+                                 double* __restrict__ ya, int n, int m, const DevState* __restrict__ st) {
+  const long long t = st->t;
+  const double td = (double)t;
+  const int len = n > m ? n : m;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+    if (i < n) xa[i] = t > 0 ? (double)xs[i] / td : (double)x[i];
+    if (i < m) ya[i] = t > 0 ? (double)ys[i] / td : (double)y[i];
+  }
+}
+
+// The decision of k_decide applied to an FP32 iteration: the FP32 state takes
+// the candidate (rounded), the FP64 copies (x, y = evaluation point, xr, yr =
+// restart reference) follow the FP32 state exactly, the FP32 sums restart.
+__global__ void k_apply32(const DevState* __restrict__ st, float* __restrict__ x32, float* __restrict__ y32,
+                          double* __restrict__ x, double* __restrict__ y, const double* __restrict__ xa,
+                          const double* __restrict__ ya, double* __restrict__ xr, double* __restrict__ yr,
+                          float* __restrict__ xs, float* __restrict__ ys, int n, int m) {
+  const int mode = st->apply_mode;
+  if (mode == APPLY_NONE) return;
+  const int len = n > m ? n : m;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+    if (i < n) {
+      if (mode == APPLY_TAKE_AVG) {
+        x[i] = xa[i];
+        x32[i] = (float)xa[i];
+      } else {
+        if (mode == APPLY_RESTART_AVG) {
+          const float v = (float)xa[i];
+          x32[i] = v;
+          x[i] = (double)v;
+        }
+        xr[i] = x[i];
+        xs[i] = 0.0f;
+      }
+    }
+    if (i < m) {
+      if (mode == APPLY_TAKE_AVG) {
+        y[i] = ya[i];
+        y32[i] = (float)ya[i];
+      } else {
+        if (mode == APPLY_RESTART_AVG) {
+          const float v = (float)ya[i];
+          y32[i] = v;
+          y[i] = (double)v;
+        }
+        yr[i] = y[i];
+        ys[i] = 0.0f;
+      }
+    }
+  }
+}
+
+// Start of the FP64 phase: the point just evaluated into st->cur becomes the
+// restart reference and the count since the last restart starts over.
+__global__ void k_promote_state(DevState* st) {
+  double p, d, g;
+  scaled_norms(st->cur, p, d, g);
+  st->rs_p = st->pc_p = p;
+  st->rs_d = st->pc_d = d;
+  st->rs_g = st->pc_g = g;
+  st->t = 0;
+}
+
 struct PackDualOp {
   using State = NoState;
   const int* __restrict__ perm;
@@ -701,7 +810,7 @@ __global__ void __launch_bounds__(TPB) k_pack_dual(Hyb At, const int* __restrict
                                                    const double* __restrict__ ch, const double* __restrict__ dc,
                                                    double* __restrict__ ox, double* __restrict__ oz) {
   PackDualOp op{perm, px, ch, dc, ox, oz};
-  hyb_dot(At, GlobalGather{py}, op);
+  hyb_dot(At, At.v, GlobalGather<double>{py}, op);
 }
 
 __global__ void k_pack_y(const int* __restrict__ perm, const double* __restrict__ py, const double* __restrict__ dr,
@@ -751,11 +860,19 @@ void launch_finish_setup(DevState* st, const double* scal, double step_factor, i
 }
 void launch_primal_step(const Hyb& At, const double* y, const double* ch, double* x, double* xbar, double* xsum,
                         const DevState* st, int accumulate, int grid, cudaStream_t s) {
-  k_primal_step<<<grid, TPB, 0, s>>>(At, y, ch, x, xbar, xsum, st, accumulate);
+  k_primal_step<double><<<grid, TPB, 0, s>>>(At, At.v, y, ch, x, xbar, xsum, st, accumulate);
 }
 void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
                       const DevState* st, int accumulate, int grid, cudaStream_t s) {
-  k_dual_step<<<grid, TPB, 0, s>>>(A, xbar, bh, y, ysum, st, accumulate);
+  k_dual_step<double><<<grid, TPB, 0, s>>>(A, A.v, xbar, bh, y, ysum, st, accumulate);
+}
+void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float* x, float* xbar, float* xsum,
+                          const DevState* st, int accumulate, int grid, cudaStream_t s) {
+  k_primal_step<float><<<grid, TPB, 0, s>>>(At, At.v32, y, ch, x, xbar, xsum, st, accumulate);
+}
+void launch_dual_step32(const Hyb& A, const float* xbar, const float* bh, float* y, float* ysum, const DevState* st,
+                        int accumulate, int grid, cudaStream_t s) {
+  k_dual_step<float><<<grid, TPB, 0, s>>>(A, A.v32, xbar, bh, y, ysum, st, accumulate);
 }
 void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,
                           const DevState* st, int accumulate, int grid, cudaStream_t s) {
@@ -788,11 +905,30 @@ void launch_pack_solution(const Hyb& At, const int* perm_x, const int* perm_y, c
   if (oy) k_pack_y<<<grid, TPB, 0, s>>>(perm_y, py, dr, oy, At.cols);
 }
 
+void launch_narrow(float* dst, const double* src, long long len, int grid, cudaStream_t s) {
+  k_narrow<<<grid, TPB, 0, s>>>(dst, src, len);
+}
+void launch_widen(double* dst, const float* src, long long len, int grid, cudaStream_t s) {
+  k_widen<<<grid, TPB, 0, s>>>(dst, src, len);
+}
+void launch_make_average32(const float* xs, const float* ys, const float* x, const float* y, double* xa, double* ya,
+                           int n, int m, const DevState* st, int grid, cudaStream_t s) {
+  k_make_average32<<<grid, TPB, 0, s>>>(xs, ys, x, y, xa, ya, n, m, st);
+}
+void launch_apply32(const DevState* st, float* x32, float* y32, double* x, double* y, const double* xa,
+                    const double* ya, double* xr, double* yr, float* xs, float* ys, int n, int m, int grid,
+                    cudaStream_t s) {
+  k_apply32<<<grid, TPB, 0, s>>>(st, x32, y32, x, y, xa, ya, xr, yr, xs, ys, n, m);
+}
+void launch_promote_state(DevState* st, cudaStream_t s) { k_promote_state<<<1, 1, 0, s>>>(st); }
+
 void prefer_l1_for_step_kernels() {
   // the step kernels use no shared memory: give the on-chip memory to L1,
   // which caches the gathered vector
-  cudaFuncSetAttribute(k_primal_step, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-  cudaFuncSetAttribute(k_dual_step, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_primal_step<double>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_dual_step<double>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_primal_step<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_dual_step<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_dual_step_hot, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(HOT_MAX * sizeof(double)));
 }

@@ -37,6 +37,22 @@ void launch_primal_step(const Hyb& At, const double* y, const double* ch, double
 // y' = y + sigma (bhat - Ahat xbar); y <- y'; ysum += y'
 void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
                       const DevState* st, int accumulate, int grid, cudaStream_t s);
+// the same two half-steps in FP32 (values At.v32 / A.v32, FP32 vectors and
+// accumulation); tau and sigma are read from the FP64 state and rounded
+void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float* x, float* xbar, float* xsum,
+                          const DevState* st, int accumulate, int grid, cudaStream_t s);
+void launch_dual_step32(const Hyb& A, const float* xbar, const float* bh, float* y, float* ysum, const DevState* st,
+                        int accumulate, int grid, cudaStream_t s);
+// precision conversions and the FP32 counterparts of make_average / apply
+void launch_narrow(float* dst, const double* src, long long len, int grid, cudaStream_t s);
+void launch_widen(double* dst, const float* src, long long len, int grid, cudaStream_t s);
+void launch_make_average32(const float* xs, const float* ys, const float* x, const float* y, double* xa, double* ya,
+                           int n, int m, const DevState* st, int grid, cudaStream_t s);
+void launch_apply32(const DevState* st, float* x32, float* y32, double* x, double* y, const double* xa,
+                    const double* ya, double* xr, double* yr, float* xs, float* ys, int n, int m, int grid,
+                    cudaStream_t s);
+// restart reference := st->cur, t := 0 (start of the FP64 polishing phase)
+void launch_promote_state(DevState* st, cudaStream_t s);
 // the same step, persistent (grid = number of SMs), with xbar[0, hot) staged
 // in shared memory; hot <= HOT_MAX
 void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,

@@ -51,6 +51,11 @@ struct pdhg_ctx {
   double *x = nullptr, *y = nullptr, *xbar = nullptr, *xsum = nullptr, *ysum = nullptr;
   double *xavg = nullptr, *yavg = nullptr, *xr = nullptr, *yr = nullptr;
   double *tmp_n = nullptr, *tmp_m = nullptr, *tmp_n2 = nullptr;
+  // FP32 iteration state (PDHG_FP32 / PDHG_MIXED); the FP64 vectors above then
+  // hold the evaluation copies until the FP64 polishing phase takes over
+  float *x32 = nullptr, *xbar32 = nullptr, *xsum32 = nullptr, *y32 = nullptr, *ysum32 = nullptr;
+  float *ch32 = nullptr, *bh32 = nullptr;
+  bool phase32 = false;
   double* partials = nullptr;
   int nb_eval = 1;
   double* scal = nullptr;
@@ -74,6 +79,7 @@ struct pdhg_ctx {
   int64_t launches = 0;  // kernels launched by pdhg_iterate (snapshot packing included)
   // host mirrors
   int64_t k = 0;
+  int64_t promoted_at = -1;  // iteration at which the FP64 polishing phase began
   bool converged = false;
   std::vector<void*> allocs;
   std::string err = "no error";
@@ -149,10 +155,21 @@ void eval_point(pdhg_ctx* ctx, const double* px, const double* py, const double*
   launch_eval_finalize(ctx->partials, ctx->nb_eval, dst, ctx->stream);
 }
 
+// During the FP32 phase: refresh the FP64 copies of the current iterate.
+void widen_current(pdhg_ctx* ctx) {
+  launch_widen(ctx->x, ctx->x32, ctx->n, vec_grid(ctx, ctx->n), ctx->stream);
+  launch_widen(ctx->y, ctx->y32, ctx->m, vec_grid(ctx, ctx->m), ctx->stream);
+}
+
 void point_of(pdhg_ctx* ctx, int which, const double** px, const double** py) {
+  if (ctx->phase32) widen_current(ctx);
   if (which == PDHG_AVERAGE) {
-    launch_make_average(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, (int)ctx->n, (int)ctx->m,
-                        ctx->st, vec_grid(ctx, std::max(ctx->n, ctx->m)), ctx->stream);
+    if (ctx->phase32)
+      launch_make_average32(ctx->xsum32, ctx->ysum32, ctx->x32, ctx->y32, ctx->xavg, ctx->yavg, (int)ctx->n,
+                            (int)ctx->m, ctx->st, vec_grid(ctx, std::max(ctx->n, ctx->m)), ctx->stream);
+    else
+      launch_make_average(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, (int)ctx->n, (int)ctx->m,
+                          ctx->st, vec_grid(ctx, std::max(ctx->n, ctx->m)), ctx->stream);
     *px = ctx->xavg;
     *py = ctx->yavg;
   } else if (which == PDHG_LAST_RESTART) {
@@ -484,6 +501,29 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   CK(ctx, cudaMemcpyAsync(ctx->yr, ctx->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
   CK(ctx, cudaMemcpyAsync(ctx->xavg, ctx->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   CK(ctx, cudaMemcpyAsync(ctx->yavg, ctx->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  // FP32 iteration state: rounded copies of the scaled matrix and vectors
+  if (o.precision != PDHG_FP64) {
+    CK(ctx, dalloc(ctx, &A.v32, A.slots));
+    CK(ctx, dalloc(ctx, &At.v32, At.slots));
+    float** f_n[] = {&ctx->x32, &ctx->xbar32, &ctx->xsum32, &ctx->ch32};
+    float** f_m[] = {&ctx->y32, &ctx->ysum32, &ctx->bh32};
+    for (float** p : f_n) CK(ctx, dalloc(ctx, p, n));
+    for (float** p : f_m) CK(ctx, dalloc(ctx, p, m));
+    launch_narrow(A.v32, A.v, A.slots, vec_grid(ctx, A.slots), s);
+    launch_narrow(At.v32, At.v, At.slots, vec_grid(ctx, At.slots), s);
+    launch_narrow(ctx->ch32, ctx->ch, n, gn, s);
+    launch_narrow(ctx->bh32, ctx->bh, m, gm, s);
+    launch_narrow(ctx->x32, ctx->x, n, gn, s);
+    launch_narrow(ctx->y32, ctx->y, m, gm, s);
+    CK(ctx, cudaMemsetAsync(ctx->xsum32, 0, sizeof(float) * n, s));
+    CK(ctx, cudaMemsetAsync(ctx->ysum32, 0, sizeof(float) * m, s));
+    // the FP64 evaluation point is the FP32 iterate, exactly
+    launch_widen(ctx->x, ctx->x32, n, gn, s);
+    launch_widen(ctx->y, ctx->y32, m, gm, s);
+    CK(ctx, cudaMemcpyAsync(ctx->xr, ctx->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(ctx, cudaMemcpyAsync(ctx->yr, ctx->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    ctx->phase32 = true;
+  }
   // restart reference = the starting point
   eval_point(ctx, ctx->x, ctx->y, nullptr, nullptr, &ctx->st->cur);
   launch_init_restart_ref(ctx->st, s);
@@ -542,7 +582,8 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     o = *opt;
   else
     pdhg_default_options(&o);
-  if (o.precision != PDHG_FP64) return fail(nullptr, PDHG_ERR_INVALID, "only PDHG_FP64 is available in this build");
+  if (o.precision != PDHG_FP64 && o.precision != PDHG_FP32 && o.precision != PDHG_MIXED)
+    return fail(nullptr, PDHG_ERR_INVALID, "precision must be PDHG_FP64, PDHG_FP32 or PDHG_MIXED");
   if (o.eval_every < 1 || o.ruiz_iters < 0 || o.power_iters < 1 || !(o.step_factor > 0.0) || o.pc_alpha < 0.0 ||
       o.pc_alpha > 2.0 || o.long_row_min < 1 || o.dual_hot_cols < 0 || o.dual_hot_cols > HOT_MAX || !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4) || o.snapshot_every < 0 || o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
     return fail(nullptr, PDHG_ERR_INVALID, "option out of range");
@@ -672,9 +713,15 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
     const bool timing = o.kernel_timing && nb <= EV_POOL;
     for (int64_t it = 0; it < nb; ++it) {
       if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
-      launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, grT, s);
+      if (ctx->phase32)
+        launch_primal_step32(ctx->At, ctx->y32, ctx->ch32, ctx->x32, ctx->xbar32, ctx->xsum32, ctx->st, o.restarts,
+                             grT, s);
+      else
+        launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, grT, s);
       if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
-      if (hot > 0)
+      if (ctx->phase32)
+        launch_dual_step32(ctx->A, ctx->xbar32, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st, o.restarts, grA, s);
+      else if (hot > 0)
         launch_dual_step_hot(ctx->A, ctx->xbar, hot, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, ctx->sms, s);
       else
         launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, grA, s);
@@ -698,14 +745,27 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
       ctx->launches_dual += nb;
     }
     if (evaluating && ctx->k % o.eval_every == 0) {
+      const bool p32 = ctx->phase32;
+      if (p32) {
+        widen_current(ctx);
+        ctx->launches += 2;
+      }
       if (o.restarts) {
-        launch_make_average(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, n, m, ctx->st, gv, s);
+        if (p32)
+          launch_make_average32(ctx->xsum32, ctx->ysum32, ctx->x32, ctx->y32, ctx->xavg, ctx->yavg, n, m, ctx->st,
+                                gv, s);
+        else
+          launch_make_average(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, n, m, ctx->st, gv, s);
         eval_point(ctx, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, &ctx->st->avg);
       }
       eval_point(ctx, ctx->x, ctx->y, ctx->xr, ctx->yr, &ctx->st->cur);
       launch_decide(ctx->st, ctx->trace, s);
-      launch_apply(ctx->st, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, ctx->xsum, ctx->ysum, n, m, gv,
-                   s);
+      if (p32)
+        launch_apply32(ctx->st, ctx->x32, ctx->y32, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr,
+                       ctx->xsum32, ctx->ysum32, n, m, gv, s);
+      else
+        launch_apply(ctx->st, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, ctx->xsum, ctx->ysum, n, m,
+                     gv, s);
       ctx->launches += (o.restarts ? 4 : 0) + 3 + 2;
       CK(ctx, cudaGetLastError());
       rs = read_state(ctx);
@@ -722,6 +782,21 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
       if (ctx->h_st->converged) {
         ctx->converged = true;
         break;
+      }
+      if (ctx->phase32 && o.precision == PDHG_MIXED && ctx->h_st->cand_rel_kkt <= o.polish_switch) {
+        // FP64 polishing phase: continue in FP64 from the FP32 iterate (held
+        // exactly in x, y), keeping D_r, D_c, eta and omega; the iterate
+        // becomes the restart reference and the FP64 averages start empty
+        eval_point(ctx, ctx->x, ctx->y, nullptr, nullptr, &ctx->st->cur);
+        launch_promote_state(ctx->st, s);
+        CK(ctx, cudaMemsetAsync(ctx->xsum, 0, sizeof(double) * n, s));
+        CK(ctx, cudaMemsetAsync(ctx->ysum, 0, sizeof(double) * m, s));
+        CK(ctx, cudaMemcpyAsync(ctx->xr, ctx->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        CK(ctx, cudaMemcpyAsync(ctx->yr, ctx->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+        CK(ctx, cudaGetLastError());
+        ctx->launches += 4;
+        ctx->phase32 = false;
+        ctx->promoted_at = ctx->k;
       }
     }
   }
@@ -832,7 +907,8 @@ pdhg_status pdhg_get_info(pdhg_ctx* ctx, pdhg_info* out) {
   out->evaluations = h.evals;
   out->snapshots = ctx->snap_count;
   out->last_rel_kkt = h.cand_rel_kkt;
-  out->precision_now = PDHG_FP64;
+  out->precision_now = ctx->phase32 ? PDHG_FP32 : PDHG_FP64;
+  out->polish_started_at = ctx->promoted_at;
   out->converged = ctx->converged ? 1 : 0;
   out->kernel_ms_primal = ctx->ms_primal;
   out->kernel_ms_dual = ctx->ms_dual;

@@ -69,6 +69,7 @@ class pdhg_info(C.Structure):
         ("precision_now", C.c_int), ("converged", C.c_int), ("kernel_ms_primal", C.c_double),
         ("kernel_ms_dual", C.c_double), ("kernel_launches_primal", C.c_int64), ("kernel_launches_dual", C.c_int64),
         ("kernel_launches", C.c_int64),
+        ("polish_started_at", C.c_int64),
     ]
 
 
