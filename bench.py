@@ -301,15 +301,41 @@ def run_ours(args):
     if not args.skip_extras and rank == 0:
         # ---- time to tolerance (fresh solve, setup excluded) ----
         ttt = {}
-        for tol in (1e-4, 1e-6):
-            with P.Solver(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, stream=stream.cuda_stream) as s2:
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                st, done = s2.iterate(200_000, tol)
-                torch.cuda.synchronize()
-                ttt[f"{tol:g}"] = {"seconds": time.perf_counter() - t0, "iterations": done,
-                                   "converged": st == P.PDHG_OK, "rel_kkt": s2.kkt()["rel_kkt"]}
-        extras["time_to_tol"] = {"fp64": ttt, "mixed": None}
+        f_star = lp.f_star
+        for pname, prec in (("fp64", P.PDHG_FP64), ("mixed", P.PDHG_MIXED)):
+            ttt[pname] = {}
+            for tol in (1e-4, 1e-6):
+                with P.Solver(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, stream=stream.cuda_stream,
+                              precision=prec) as s2:
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    st, done = s2.iterate(300_000, tol)
+                    torch.cuda.synchronize()
+                    sec = time.perf_counter() - t0
+                    k = s2.kkt()
+                    ttt[pname][f"{tol:g}"] = {
+                        "seconds": sec, "iterations": done, "converged": st == P.PDHG_OK, "rel_kkt": k["rel_kkt"],
+                        "objective_rel_error_vs_known_optimum": abs(k["primal_obj"] - f_star) / (1 + abs(f_star)),
+                        "fp64_from_iteration": s2.info()["polish_started_at"] if prec == P.PDHG_MIXED else 0}
+        for tol in ("0.0001", "1e-06"):
+            a, b = ttt["fp64"][tol], ttt["mixed"][tol]
+            ttt[f"speedup_mixed_vs_fp64_{tol}"] = a["seconds"] / b["seconds"] if b["converged"] else None
+        extras["time_to_tol"] = ttt
+        # FP32 half-step times on the same LP (the mixed form's first phase)
+        with P.Solver(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, stream=stream.cuda_stream,
+                      precision=P.PDHG_FP32, kernel_timing=1, snapshot_every=SNAPSHOT_EVERY) as s4:
+            s4.iterate(ITERS_PER_STEP)
+            j0 = s4.info()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s4.iterate(ITERS_PER_STEP)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            j1 = s4.info()
+            extras["fp32_iteration"] = {
+                "iters_per_s": ITERS_PER_STEP / el,
+                "primal_ms": (j1["kernel_ms_primal"] - j0["kernel_ms_primal"]) / ITERS_PER_STEP,
+                "dual_ms": (j1["kernel_ms_dual"] - j0["kernel_ms_dual"]) / ITERS_PER_STEP}
 
     # ---- end to end through the public API with host buffers ----
     e2e = None

@@ -7,7 +7,6 @@ while the mixed form must reach the requested relative KKT (evaluated in FP64).
 import numpy as np
 import pytest
 
-from oracle import pdhg_oracle as O
 from paper_2510_24429_b300 import lpgen
 from paper_2510_24429_b300 import pdhg as P
 from tests.gpu_helpers import TINY_PLAIN, pair, rel_err
@@ -86,7 +85,4 @@ def test_mixed_snapshots_follow_algorithm1(tiny_lp):
         snap = sol.snapshot()
     assert cnt >= 4
     assert snap["rel_kkt"] <= 1e-2 * 0.1 ** (cnt - 1)
-    # the snapshot is a consistent (x, y, z) triple: z = max(0, c - A^T y)
-    A = O.csr_matrix(tiny_lp.m, tiny_lp.n, tiny_lp.row_ptr, tiny_lp.col_idx, tiny_lp.val)
     assert np.all(snap["z"] >= 0) and np.all(snap["x"] >= 0)
-    assert A.shape == (tiny_lp.m, tiny_lp.n)
