@@ -31,6 +31,8 @@ namespace {
 
 thread_local std::string g_create_error = "no error";
 constexpr int EV_POOL = 256;
+// PDHG_MIXED: iterations without a 10% gain in the FP32 phase before FP64 takes over
+constexpr int64_t STALL_ITERS = 2048;
 
 }  // namespace
 
@@ -80,6 +82,8 @@ struct pdhg_ctx {
   // host mirrors
   int64_t k = 0;
   int64_t promoted_at = -1;  // iteration at which the FP64 polishing phase began
+  double best32 = 1e300;     // best relative KKT seen in the FP32 phase, and where
+  int64_t best32_k = 0;
   bool converged = false;
   std::vector<void*> allocs;
   std::string err = "no error";
@@ -561,7 +565,7 @@ void pdhg_default_options(pdhg_options* o) {
   o->inputs_on_device = 0;
   o->use_graphs = 1;
   o->kernel_timing = 0;
-  o->polish_switch = 1e-5;
+  o->polish_switch = 1e-7;
   o->long_row_min = 128;
   o->rows_per_thread = 4;
   o->dual_hot_cols = 0;
@@ -783,7 +787,18 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
         ctx->converged = true;
         break;
       }
-      if (ctx->phase32 && o.precision == PDHG_MIXED && ctx->h_st->cand_rel_kkt <= o.polish_switch) {
+      bool stalled = false;
+      if (ctx->phase32) {
+        // FP32 stall: the best relative KKT of the FP32 phase has not
+        // improved by 10% over the last STALL_ITERS iterations
+        const double r = ctx->h_st->cand_rel_kkt;
+        if (r < 0.9 * ctx->best32) {
+          ctx->best32 = r;
+          ctx->best32_k = ctx->k;
+        }
+        stalled = ctx->k - ctx->best32_k >= STALL_ITERS;
+      }
+      if (ctx->phase32 && o.precision == PDHG_MIXED && (ctx->h_st->cand_rel_kkt <= o.polish_switch || stalled)) {
         // FP64 polishing phase: continue in FP64 from the FP32 iterate (held
         // exactly in x, y), keeping D_r, D_c, eta and omega; the iterate
         // becomes the restart reference and the FP64 averages start empty
