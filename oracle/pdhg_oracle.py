@@ -443,3 +443,56 @@ class Oracle:
     def solution(self):
         """Unscaled (x, y, z) of the current iterate."""
         return self.unscale(self.x, self.y)
+
+
+# ---------------------------------------------------------------------------
+# Differentiating K unrolled iterations (fixed step, no restarts, omega fixed)
+# ---------------------------------------------------------------------------
+
+def unrolled_forward(orc: Oracle, K: int, c=None, b=None):
+    """K plain PDHG iterations of ``orc``'s scaled problem from its current
+    point, optionally with a different objective c or right-hand side b (the
+    scaling, eta and omega stay those of ``orc``). Returns the scaled iterates
+    x_0..x_K and y_0..y_K."""
+    ch = orc.d_c * (orc.c if c is None else np.asarray(c, dtype=np.float64))
+    bh = orc.d_r * (orc.b if b is None else np.asarray(b, dtype=np.float64))
+    xs, ys = [orc.x.copy()], [orc.y.copy()]
+    for _ in range(K):
+        x1, _, y1 = pdhg_iteration(orc.Ah, orc.AhT, bh, ch, xs[-1], ys[-1], orc.tau, orc.sigma)
+        xs.append(x1)
+        ys.append(y1)
+    return xs, ys
+
+
+def unrolled_adjoint(orc: Oracle, K: int, gx_K, gy_K=None):
+    """Reverse pass through K unrolled iterations: given dL/dx_K and dL/dy_K
+    on the problem as given (x = D_c xhat, y = D_r yhat), return (dL/dc, dL/db).
+
+    One iteration, u = x - tau (chat - Ahat^T y), x' = max(u, 0),
+    v = 2x' - x, y' = y + sigma (bhat - Ahat v), is reversed as
+        g_v   = -sigma Ahat^T g_y'
+        g_u   = [u > 0] (g_x' + 2 g_v)        (derivative 0 at u = 0)
+        g_x   = -g_v + g_u
+        g_y   = g_y' + tau Ahat g_u
+        g_bhat += sigma g_y',  g_chat += -tau g_u
+    with chat = D_c c and bhat = D_r b."""
+    xs, _ = unrolled_forward(orc, K)
+    gx = orc.d_c * np.asarray(gx_K, dtype=np.float64)
+    gy = np.zeros(orc.m) if gy_K is None else orc.d_r * np.asarray(gy_K, dtype=np.float64)
+    g_ch = np.zeros(orc.n)
+    g_bh = np.zeros(orc.m)
+    for k in range(K - 1, -1, -1):
+        g_v = -orc.sigma * (orc.AhT @ gy)
+        g_u = np.where(xs[k + 1] > 0, gx + 2.0 * g_v, 0.0)
+        g_bh += orc.sigma * gy
+        g_ch += -orc.tau * g_u
+        gx = -g_v + g_u
+        gy = gy + orc.tau * (orc.Ah @ g_u)
+    return orc.d_c * g_ch, orc.d_r * g_bh
+
+
+def unrolled_loss(orc: Oracle, K: int, x_target, c=None, b=None) -> float:
+    """0.5 ||x_K - x_target||^2 with x_K on the problem as given."""
+    xs, _ = unrolled_forward(orc, K, c=c, b=b)
+    r = orc.d_c * xs[-1] - x_target
+    return 0.5 * float(r @ r)
