@@ -90,6 +90,9 @@ typedef struct {
   int long_row_min;       /* rows with at least this many entries get a warp each (128) */
   int rows_per_thread;    /* most rows one thread reduces at once in short rows: 1, 2 or 4 (4) */
   int dual_hot_cols;      /* entries of xbar the dual step stages in shared memory, 0 = off; <= 24576 (0) */
+  int record_for_backward; /* 1: keep checkpoints for pdhg_backward; needs restarts = 0, primal_weight = 0,
+                              precision FP64 or FP32 (0) */
+  int64_t checkpoint_every; /* iterations between adjoint checkpoints (50) */
   int reserved[8];
 } pdhg_options;
 
@@ -180,6 +183,19 @@ PDHG_API pdhg_status pdhg_snapshot_poll(pdhg_ctx* ctx, int64_t* count, int* read
  * (any may be NULL); waits for its copy to land. STATE if none was taken. */
 PDHG_API pdhg_status pdhg_snapshot(pdhg_ctx* ctx, double* x, double* y, double* z, int64_t* iteration,
                                    double* rel_kkt);
+
+/* Reverse pass through every iteration run so far (all of them plain
+ * fixed-step PDHG iterations: the context must have been created with
+ * record_for_backward = 1). Given dL/dx_K[n] and optionally dL/dy_K[m] (NULL =
+ * 0) for the current iterate on the problem as given, writes dL/dc[n] and
+ * dL/db[m], holding the scaling, eta and omega fixed (they depend on A only).
+ * Checkpoints of (x, y) every checkpoint_every iterations are kept during
+ * pdhg_iterate; each segment is recomputed from its checkpoint and reversed
+ * with one A^T and one A SpMV per iteration, in the context's precision. The
+ * derivative of max(u, 0) at u = 0 is taken as 0. Pointers are host memory
+ * unless on_device != 0. STATE if recording is off. */
+PDHG_API pdhg_status pdhg_backward(pdhg_ctx* ctx, const double* dL_dxK, const double* dL_dyK, double* dL_dc,
+                                   double* dL_db, int on_device);
 
 /* Engine scalars. */
 PDHG_API pdhg_status pdhg_get_info(pdhg_ctx* ctx, pdhg_info* out);

@@ -14,6 +14,8 @@
 // L1 (which then holds the most frequently gathered entries, numbered first).
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -789,6 +791,79 @@ __global__ void k_promote_state(DevState* st) {
   st->t = 0;
 }
 
+// ---------------------------------------------------------------------------
+// adjoint of one PDHG iteration (fixed step, no restarts)
+//   forward: u = x - tau (chat - Ahat^T y), x' = max(u, 0), v = 2x' - x,
+//            y' = y + sigma (bhat - Ahat v)
+//   reverse: g_v = -sigma Ahat^T g_y',  g_u = [x' > 0] (g_x' + 2 g_v),
+//            g_x = -g_v + g_u,  g_chat -= tau g_u,
+//            g_y = g_y' + tau Ahat g_u,  g_bhat += sigma g_y'
+// ([x' > 0] is [u > 0]; the derivative of max(u, 0) at u = 0 is taken as 0)
+// ---------------------------------------------------------------------------
+template <class T>
+struct AdjPrimalOp {
+  using State = NoState;
+  const T* __restrict__ xnext;  // x_{k+1} of the recomputed forward pass
+  T* __restrict__ gx;           // in: adjoint of x_{k+1}; out: adjoint of x_k
+  T* __restrict__ gu;           // out: adjoint of u_k
+  T* __restrict__ gch;          // accumulated adjoint of chat
+  T sigma, tau;
+  __device__ __forceinline__ State begin(int) { return {}; }
+  __device__ __forceinline__ void finish(int j, T acc, const State&) {
+    const T gv = -sigma * acc;
+    const T g = xnext[j] > T(0) ? gx[j] + T(2) * gv : T(0);
+    gu[j] = g;
+    gx[j] = g - gv;
+    gch[j] -= tau * g;
+  }
+};
+
+template <class T>
+__global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS)
+    k_adj_primal(Hyb At, const T* __restrict__ vals, const T* __restrict__ gy, const T* __restrict__ xnext,
+                 T* __restrict__ gx, T* __restrict__ gu, T* __restrict__ gch, const DevState* __restrict__ st) {
+  AdjPrimalOp<T> op{xnext, gx, gu, gch, (T)st->sigma, (T)st->tau};
+  hyb_dot(At, vals, GlobalGather<T>{gy}, op);
+}
+
+template <class T>
+struct AdjDualOp {
+  using State = NoState;
+  T* __restrict__ gy;   // in: adjoint of y_{k+1}; out: adjoint of y_k
+  T* __restrict__ gbh;  // accumulated adjoint of bhat
+  T sigma, tau;
+  __device__ __forceinline__ State begin(int) { return {}; }
+  __device__ __forceinline__ void finish(int i, T acc, const State&) {
+    const T g = gy[i];
+    gbh[i] += sigma * g;
+    gy[i] = g + tau * acc;
+  }
+};
+
+template <class T>
+__global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS)
+    k_adj_dual(Hyb A, const T* __restrict__ vals, const T* __restrict__ gu, T* __restrict__ gy, T* __restrict__ gbh,
+               const DevState* __restrict__ st) {
+  AdjDualOp<T> op{gy, gbh, (T)st->sigma, (T)st->tau};
+  hyb_dot(A, vals, GlobalGather<T>{gu}, op);
+}
+
+// g[j] = d[j] * in[perm[j]] (caller numbering -> internal, scaled); 0 if in is null
+template <class T>
+__global__ void k_adj_seed(T* __restrict__ g, const double* __restrict__ in, const int* __restrict__ perm,
+                           const double* __restrict__ d, int len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    g[i] = in ? (T)(d[i] * in[perm[i]]) : T(0);
+}
+
+// out[perm[j]] = d[j] * g[j] (internal, scaled -> caller numbering)
+template <class T>
+__global__ void k_adj_unseed(double* __restrict__ out, const T* __restrict__ g, const int* __restrict__ perm,
+                             const double* __restrict__ d, int len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    out[perm[i]] = d[i] * (double)g[i];
+}
+
 struct PackDualOp {
   using State = NoState;
   const int* __restrict__ perm;
@@ -921,6 +996,34 @@ void launch_apply32(const DevState* st, float* x32, float* y32, double* x, doubl
   k_apply32<<<grid, TPB, 0, s>>>(st, x32, y32, x, y, xa, ya, xr, yr, xs, ys, n, m);
 }
 void launch_promote_state(DevState* st, cudaStream_t s) { k_promote_state<<<1, 1, 0, s>>>(st); }
+
+template <class T>
+void launch_adj_step(const Hyb& A, const Hyb& At, const T* valsA, const T* valsAt, const T* xnext, T* gx, T* gy,
+                     T* gu, T* gch, T* gbh, const DevState* st, cudaStream_t s) {
+  k_adj_primal<T><<<std::max(1, (At.units() + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK), TPB, 0, s>>>(
+      At, valsAt, gy, xnext, gx, gu, gch, st);
+  k_adj_dual<T><<<std::max(1, (A.units() + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK), TPB, 0, s>>>(A, valsA, gu, gy,
+                                                                                                    gbh, st);
+}
+template void launch_adj_step<double>(const Hyb&, const Hyb&, const double*, const double*, const double*, double*,
+                                      double*, double*, double*, double*, const DevState*, cudaStream_t);
+template void launch_adj_step<float>(const Hyb&, const Hyb&, const float*, const float*, const float*, float*, float*,
+                                     float*, float*, float*, const DevState*, cudaStream_t);
+
+template <class T>
+void launch_adj_seed(T* g, const double* in, const int* perm, const double* d, int len, int grid, cudaStream_t s) {
+  k_adj_seed<T><<<grid, TPB, 0, s>>>(g, in, perm, d, len);
+}
+template void launch_adj_seed<double>(double*, const double*, const int*, const double*, int, int, cudaStream_t);
+template void launch_adj_seed<float>(float*, const double*, const int*, const double*, int, int, cudaStream_t);
+
+template <class T>
+void launch_adj_unseed(double* out, const T* g, const int* perm, const double* d, int len, int grid,
+                       cudaStream_t s) {
+  k_adj_unseed<T><<<grid, TPB, 0, s>>>(out, g, perm, d, len);
+}
+template void launch_adj_unseed<double>(double*, const double*, const int*, const double*, int, int, cudaStream_t);
+template void launch_adj_unseed<float>(double*, const float*, const int*, const double*, int, int, cudaStream_t);
 
 void prefer_l1_for_step_kernels() {
   // the step kernels use no shared memory: give the on-chip memory to L1,

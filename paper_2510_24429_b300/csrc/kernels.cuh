@@ -53,6 +53,16 @@ void launch_apply32(const DevState* st, float* x32, float* y32, double* x, doubl
                     cudaStream_t s);
 // restart reference := st->cur, t := 0 (start of the FP64 polishing phase)
 void launch_promote_state(DevState* st, cudaStream_t s);
+// ---- adjoint ----------------------------------------------------------------
+// one reversed iteration: adjoint primal half-step over Ahat^T then adjoint
+// dual half-step over Ahat (values valsAt / valsA in precision T)
+template <class T>
+void launch_adj_step(const Hyb& A, const Hyb& At, const T* valsA, const T* valsAt, const T* xnext, T* gx, T* gy,
+                     T* gu, T* gch, T* gbh, const DevState* st, cudaStream_t s);
+template <class T>
+void launch_adj_seed(T* g, const double* in, const int* perm, const double* d, int len, int grid, cudaStream_t s);
+template <class T>
+void launch_adj_unseed(double* out, const T* g, const int* perm, const double* d, int len, int grid, cudaStream_t s);
 // the same step, persistent (grid = number of SMs), with xbar[0, hot) staged
 // in shared memory; hot <= HOT_MAX
 void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pdhg.h"
@@ -59,6 +60,10 @@ struct pdhg_ctx {
   float *x32 = nullptr, *xbar32 = nullptr, *xsum32 = nullptr, *y32 = nullptr, *ysum32 = nullptr;
   float *ch32 = nullptr, *bh32 = nullptr;
   bool phase32 = false;
+  // recording for the adjoint: (x_k, y_k) every checkpoint_every iterations
+  std::vector<void*> ck_x, ck_y;
+  void *w_x = nullptr, *w_y = nullptr, *w_xbar = nullptr, *w_seg = nullptr;
+  void *g_x = nullptr, *g_y = nullptr, *g_u = nullptr, *g_ch = nullptr, *g_bh = nullptr;
   double* partials = nullptr;
   int nb_eval = 1;
   double* scal = nullptr;
@@ -184,6 +189,78 @@ void point_of(pdhg_ctx* ctx, int which, const double** px, const double** py) {
     *px = ctx->x;
     *py = ctx->y;
   }
+}
+
+// Save (x_k, y_k) when k is a multiple of checkpoint_every and not saved yet.
+pdhg_status record_checkpoint(pdhg_ctx* ctx, int64_t k) {
+  const int64_t C = ctx->opt.checkpoint_every;
+  if (k % C != 0 || (int64_t)ctx->ck_x.size() != k / C) return PDHG_OK;
+  const size_t es = ctx->phase32 ? sizeof(float) : sizeof(double);
+  char *cx = nullptr, *cy = nullptr;
+  CK(ctx, dalloc(ctx, &cx, es * ctx->n));
+  CK(ctx, dalloc(ctx, &cy, es * ctx->m));
+  CK(ctx, cudaMemcpyAsync(cx, ctx->phase32 ? (void*)ctx->x32 : (void*)ctx->x, es * ctx->n, cudaMemcpyDeviceToDevice,
+                          ctx->stream));
+  CK(ctx, cudaMemcpyAsync(cy, ctx->phase32 ? (void*)ctx->y32 : (void*)ctx->y, es * ctx->m, cudaMemcpyDeviceToDevice,
+                          ctx->stream));
+  ctx->ck_x.push_back(cx);
+  ctx->ck_y.push_back(cy);
+  return PDHG_OK;
+}
+
+// Reverse pass over every iteration run so far, in precision T.
+template <class T>
+pdhg_status backward_impl(pdhg_ctx* ctx, const double* dx, const double* dy, double* dc, double* db) {
+  const int64_t K = ctx->k, C = ctx->opt.checkpoint_every, n = ctx->n, m = ctx->m;
+  const bool f32 = std::is_same<T, float>::value;
+  cudaStream_t s = ctx->stream;
+  if (!ctx->g_x) {
+    CK(ctx, dalloc(ctx, (T**)&ctx->w_x, n));
+    CK(ctx, dalloc(ctx, (T**)&ctx->w_y, m));
+    CK(ctx, dalloc(ctx, (T**)&ctx->w_xbar, n));
+    CK(ctx, dalloc(ctx, (T**)&ctx->w_seg, (size_t)C * n));
+    CK(ctx, dalloc(ctx, (T**)&ctx->g_x, n));
+    CK(ctx, dalloc(ctx, (T**)&ctx->g_y, m));
+    CK(ctx, dalloc(ctx, (T**)&ctx->g_u, n));
+    CK(ctx, dalloc(ctx, (T**)&ctx->g_ch, n));
+    CK(ctx, dalloc(ctx, (T**)&ctx->g_bh, m));
+  }
+  T *wx = (T*)ctx->w_x, *wy = (T*)ctx->w_y, *wxbar = (T*)ctx->w_xbar, *seg = (T*)ctx->w_seg;
+  T *gx = (T*)ctx->g_x, *gy = (T*)ctx->g_y, *gu = (T*)ctx->g_u, *gch = (T*)ctx->g_ch, *gbh = (T*)ctx->g_bh;
+  const int gn = vec_grid(ctx, n), gm = vec_grid(ctx, m);
+  const int grT = unit_grid(ctx->At), grA = unit_grid(ctx->A);
+  launch_adj_seed<T>(gx, dx, ctx->perm_x, ctx->dc, (int)n, gn, s);
+  launch_adj_seed<T>(gy, dy, ctx->perm_y, ctx->dr, (int)m, gm, s);
+  CK(ctx, cudaMemsetAsync(gch, 0, sizeof(T) * n, s));
+  CK(ctx, cudaMemsetAsync(gbh, 0, sizeof(T) * m, s));
+  for (int64_t sg = (K - 1) / C; sg >= 0 && K > 0; --sg) {
+    const int64_t start = sg * C, end = std::min(start + C, K);
+    // recompute the segment's forward pass from its checkpoint
+    CK(ctx, cudaMemcpyAsync(wx, ctx->ck_x[sg], sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+    CK(ctx, cudaMemcpyAsync(wy, ctx->ck_y[sg], sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
+    for (int64_t k = start; k < end; ++k) {
+      if (f32) {
+        launch_primal_step32(ctx->At, (const float*)wy, ctx->ch32, (float*)wx, (float*)wxbar, nullptr, ctx->st, 0,
+                             grT, s);
+        launch_dual_step32(ctx->A, (const float*)wxbar, ctx->bh32, (float*)wy, nullptr, ctx->st, 0, grA, s);
+      } else {
+        launch_primal_step(ctx->At, (const double*)wy, ctx->ch, (double*)wx, (double*)wxbar, nullptr, ctx->st, 0,
+                           grT, s);
+        launch_dual_step(ctx->A, (const double*)wxbar, ctx->bh, (double*)wy, nullptr, ctx->st, 0, grA, s);
+      }
+      CK(ctx, cudaMemcpyAsync(seg + (k - start) * n, wx, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    // reverse it
+    const T* valsA = f32 ? (const T*)ctx->A.v32 : (const T*)ctx->A.v;
+    const T* valsAt = f32 ? (const T*)ctx->At.v32 : (const T*)ctx->At.v;
+    for (int64_t k = end - 1; k >= start; --k)
+      launch_adj_step<T>(ctx->A, ctx->At, valsA, valsAt, seg + (k - start) * n, gx, gy, gu, gch, gbh, ctx->st, s);
+    CK(ctx, cudaGetLastError());
+  }
+  launch_adj_unseed<T>(dc, gch, ctx->perm_x, ctx->dc, (int)n, gn, s);
+  launch_adj_unseed<T>(db, gbh, ctx->perm_y, ctx->dr, (int)m, gm, s);
+  CK(ctx, cudaGetLastError());
+  return PDHG_OK;
 }
 
 pdhg_status take_snapshot(pdhg_ctx* ctx) {
@@ -570,6 +647,8 @@ void pdhg_default_options(pdhg_options* o) {
   o->long_row_min = 128;
   o->rows_per_thread = 4;
   o->dual_hot_cols = 0;
+  o->record_for_backward = 0;
+  o->checkpoint_every = 50;
 }
 
 pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
@@ -589,6 +668,11 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     pdhg_default_options(&o);
   if (o.precision != PDHG_FP64 && o.precision != PDHG_FP32 && o.precision != PDHG_MIXED)
     return fail(nullptr, PDHG_ERR_INVALID, "precision must be PDHG_FP64, PDHG_FP32 or PDHG_MIXED");
+  if (o.record_for_backward &&
+      (o.restarts || o.primal_weight || o.precision == PDHG_MIXED || o.checkpoint_every < 1))
+    return fail(nullptr, PDHG_ERR_INVALID,
+                "record_for_backward needs restarts = 0, primal_weight = 0 (fixed steps), precision FP64 or FP32 "
+                "and checkpoint_every >= 1");
   if (o.eval_every < 1 || o.ruiz_iters < 0 || o.power_iters < 1 || !(o.step_factor > 0.0) || o.pc_alpha < 0.0 ||
       o.pc_alpha > 2.0 || o.long_row_min < 1 || o.dual_hot_cols < 0 || o.dual_hot_cols > HOT_MAX || !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4) || o.snapshot_every < 0 || o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
     return fail(nullptr, PDHG_ERR_INVALID, "option out of range");
@@ -717,6 +801,10 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
       nb = std::min<int64_t>(max_iters - done, o.kernel_timing ? EV_POOL : (1 << 20));
     const bool timing = o.kernel_timing && nb <= EV_POOL;
     for (int64_t it = 0; it < nb; ++it) {
+      if (o.record_for_backward) {
+        rs = record_checkpoint(ctx, ctx->k + it);
+        if (rs != PDHG_OK) return rs;
+      }
       if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
       if (ctx->phase32)
         launch_primal_step32(ctx->At, ctx->y32, ctx->ch32, ctx->x32, ctx->xbar32, ctx->xsum32, ctx->st, o.restarts,
@@ -947,6 +1035,33 @@ pdhg_status pdhg_get_trace(pdhg_ctx* ctx, pdhg_trace_rec* recs, int64_t cap, int
     static_assert(sizeof(TraceRec) == sizeof(pdhg_trace_rec), "trace record layout");
     CK(ctx, cudaMemcpy(recs, ctx->trace, sizeof(TraceRec) * k, cudaMemcpyDeviceToHost));
   }
+  return PDHG_OK;
+}
+
+pdhg_status pdhg_backward(pdhg_ctx* ctx, const double* dL_dxK, const double* dL_dyK, double* dL_dc, double* dL_db,
+                          int on_device) {
+  if (!ctx) return PDHG_ERR_INVALID;
+  if (!ctx->opt.record_for_backward)
+    return fail(ctx, PDHG_ERR_STATE, "the context was not created with record_for_backward = 1");
+  if (!dL_dxK || !dL_dc || !dL_db) return fail(ctx, PDHG_ERR_INVALID, "NULL argument");
+  pdhg_status rs = set_device(ctx);
+  if (rs != PDHG_OK) return rs;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n, m = ctx->m;
+  // inputs into device scratch (tmp_n, tmp_m), outputs through sol
+  const cudaMemcpyKind in_kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(ctx, cudaMemcpyAsync(ctx->tmp_n, dL_dxK, sizeof(double) * n, in_kind, s));
+  if (dL_dyK) CK(ctx, cudaMemcpyAsync(ctx->tmp_m, dL_dyK, sizeof(double) * m, in_kind, s));
+  double* out_c = ctx->sol;
+  double* out_b = ctx->sol + n;
+  rs = ctx->opt.precision == PDHG_FP32
+           ? backward_impl<float>(ctx, ctx->tmp_n, dL_dyK ? ctx->tmp_m : nullptr, out_c, out_b)
+           : backward_impl<double>(ctx, ctx->tmp_n, dL_dyK ? ctx->tmp_m : nullptr, out_c, out_b);
+  if (rs != PDHG_OK) return rs;
+  const cudaMemcpyKind out_kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(ctx, cudaMemcpyAsync(dL_dc, out_c, sizeof(double) * n, out_kind, s));
+  CK(ctx, cudaMemcpyAsync(dL_db, out_b, sizeof(double) * m, out_kind, s));
+  CK(ctx, cudaStreamSynchronize(s));
   return PDHG_OK;
 }
 

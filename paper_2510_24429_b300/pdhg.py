@@ -51,6 +51,8 @@ class pdhg_options(C.Structure):
         ("long_row_min", C.c_int),
         ("rows_per_thread", C.c_int),
         ("dual_hot_cols", C.c_int),
+        ("record_for_backward", C.c_int),
+        ("checkpoint_every", C.c_int64),
         ("reserved", C.c_int * 8),
     ]
 
@@ -100,6 +102,7 @@ SIGNATURES = {
     "pdhg_snapshot_poll": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
     "pdhg_snapshot": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "pdhg_get_info": (C.c_int, [_P, C.POINTER(pdhg_info)]),
+    "pdhg_backward": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
     "pdhg_get_trace": (C.c_int, [_P, C.POINTER(pdhg_trace_rec), C.c_int64, C.POINTER(C.c_int64)]),
     "pdhg_last_error": (C.c_char_p, [_P]),
     "pdhg_kkt_noalloc": (C.c_int, [C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P,
@@ -249,6 +252,20 @@ def pdhg_snapshot(ctx, x=None, y=None, z=None):
     return it.value, rel.value
 
 
+def pdhg_backward(ctx, dL_dx, dL_dc, dL_db, dL_dy=None):
+    """Gradients of a loss of the current iterate with respect to c and b
+    (outputs dL_dc[n], dL_db[m] supplied by the caller, all host or all CUDA)."""
+    keep: list = []
+    px, dev = _prep(dL_dx, np.float64, keep)
+    py, devy = _prep(dL_dy, np.float64, keep)
+    pc, devc = _out_ptr(dL_dc)
+    pb, devb = _out_ptr(dL_db)
+    devs = {dev, devc, devb} | ({devy} if py is not None else set())
+    if len(devs) != 1:
+        raise ValueError("pdhg_backward: arrays must be all on the host or all on the device")
+    _check(load().pdhg_backward(ctx, px, py, pc, pb, int(dev)), ctx)
+
+
 def pdhg_get_info(ctx) -> dict:
     info = pdhg_info()
     _check(load().pdhg_get_info(ctx, C.byref(info)), ctx)
@@ -329,6 +346,19 @@ class Solver:
     def info(self):
         return pdhg_get_info(self.ctx)
 
+    def backward(self, dL_dx, dL_dy=None):
+        """(dL/dc, dL/db) through every iteration run so far (needs
+        record_for_backward=1). CUDA tensors in give CUDA tensors out."""
+        if _is_torch(dL_dx) and dL_dx.is_cuda:
+            import torch
+
+            gc = torch.empty(self.n, dtype=torch.float64, device=dL_dx.device)
+            gb = torch.empty(self.m, dtype=torch.float64, device=dL_dx.device)
+        else:
+            gc, gb = np.empty(self.n), np.empty(self.m)
+        pdhg_backward(self.ctx, dL_dx, gc, gb, dL_dy)
+        return gc, gb
+
     def trace(self):
         return pdhg_get_trace(self.ctx)
 
@@ -348,3 +378,49 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# differentiable unrolled PDHG
+# ---------------------------------------------------------------------------
+
+def _unroll_function():
+    import torch
+
+    class PDHGUnroll(torch.autograd.Function):
+        """x_K(c, b): K fixed-step PDHG iterations (no restarts, omega = 1) from
+        zero on the LP with matrix ``csr = (m, n, row_ptr, col_idx, val)``;
+        backward runs the library's adjoint (pdhg_backward) with checkpoints
+        every ``checkpoint_every`` iterations. Scaling and step size depend on A
+        only and are held fixed."""
+
+        @staticmethod
+        def forward(fctx, c, b, csr, iters, options):
+            m, n, row_ptr, col_idx, val = csr
+            sol = Solver(m, n, row_ptr, col_idx, val, b.detach().cpu().numpy(), c.detach().cpu().numpy(),
+                         record_for_backward=1, restarts=0, primal_weight=0, **(options or {}))
+            sol.iterate(int(iters))
+            x = torch.empty(n, dtype=torch.float64, device=c.device)
+            if x.is_cuda:
+                pdhg_get_solution(sol.ctx, PDHG_CURRENT, x=x)
+            else:
+                xn = np.empty(n)
+                pdhg_get_solution(sol.ctx, PDHG_CURRENT, x=xn)
+                x.copy_(torch.from_numpy(xn))
+            fctx.solver = sol
+            return x
+
+        @staticmethod
+        def backward(fctx, grad_x):
+            gc, gb = fctx.solver.backward(grad_x.detach().to(torch.float64).contiguous())
+            fctx.solver.close()
+            if not _is_torch(gc):
+                gc, gb = torch.from_numpy(gc), torch.from_numpy(gb)
+            return gc.to(grad_x.device), gb.to(grad_x.device), None, None, None
+
+    return PDHGUnroll
+
+
+def pdhg_unroll(c, b, csr, iters, **options):
+    """Differentiable x_K(c, b) (see PDHGUnroll)."""
+    return _unroll_function().apply(c, b, csr, iters, options)
