@@ -232,6 +232,57 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# the differentiable form: 500 unrolled iterations, FP32 forward
+# ---------------------------------------------------------------------------
+def run_adjoint(P, torch, K=500, C=50, n_dirs=20, h=1e-6):
+    """Loss 0.5 ||x_K - x_target||^2 on the m=1e5, n=3e5, 6-per-column LP:
+    FP32 forward with checkpoints every C iterations and the hand-written
+    adjoint, timed; the directional derivatives are checked against central
+    differences of the FP64 forward on n_dirs unit directions in (c, b)."""
+    import numpy as np
+
+    from paper_2510_24429_b300 import lpgen
+
+    lp = lpgen.adjoint_lp(0)
+    xt = lpgen.x_target(lp, 1)
+    base = dict(restarts=0, primal_weight=0)
+
+    def loss64(c, b):
+        with P.Solver(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, b, c, **base) as s:
+            s.iterate(K)
+            x, _, _ = s.solution()
+        return 0.5 * float((x - xt) @ (x - xt))
+
+    with P.Solver(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, precision=P.PDHG_FP32,
+                  record_for_backward=1, checkpoint_every=C, **base) as s:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.iterate(K)
+        torch.cuda.synchronize()
+        t_fwd = time.perf_counter() - t0
+        x, _, _ = s.solution()
+        s.backward(x - xt)  # warm-up (allocates the reverse-pass buffers)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gc, gb = s.backward(x - xt)
+        torch.cuda.synchronize()
+        t_bwd = time.perf_counter() - t0
+    rng = np.random.default_rng(2024)
+    errs = []
+    for _ in range(n_dirs):
+        dc, db = rng.standard_normal(lp.n), rng.standard_normal(lp.m)
+        nrm = np.sqrt(dc @ dc + db @ db)
+        dc, db = dc / nrm, db / nrm
+        fd = (loss64(lp.c + h * dc, lp.b + h * db) - loss64(lp.c - h * dc, lp.b - h * db)) / (2 * h)
+        ad = float(gc @ dc + gb @ db)
+        errs.append(abs(ad - fd) / max(abs(fd), 1e-12))
+    return {"workload": f"adjoint-lp m={lp.m} n={lp.n} nnz={lp.nnz} K={K} checkpoints every {C}, FP32 forward",
+            "forward_s": t_fwd, "backward_s": t_bwd,
+            "fd_check": {"directions": n_dirs, "h": h, "reference": "central differences of the FP64 forward",
+                         "rel_err_median": float(np.median(errs)), "rel_err_max": float(np.max(errs))}}
+
+
+# ---------------------------------------------------------------------------
 # our engine
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -365,6 +416,9 @@ def run_ours(args):
                "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                "includes": "pdhg_create from pinned host CSR (validation, renumbering, upload, scaling, power "
                            "iteration), 1000 iterations, solution read back, destroy"}
+
+    if not args.skip_extras and rank == 0:
+        extras["adjoint"] = run_adjoint(P, torch)
 
     cpu = None
     if not args.skip_extras and rank == 0 and world == 1:
