@@ -268,7 +268,8 @@ def run_adjoint(P, torch, K=500, C=50, n_dirs=20, h=1e-6):
         torch.cuda.synchronize()
         t_bwd = time.perf_counter() - t0
     rng = np.random.default_rng(2024)
-    errs = []
+    gnorm = float(np.sqrt(gc @ gc + gb @ gb))
+    errs, errs_g = [], []
     for _ in range(n_dirs):
         dc, db = rng.standard_normal(lp.n), rng.standard_normal(lp.m)
         nrm = np.sqrt(dc @ dc + db @ db)
@@ -276,10 +277,12 @@ def run_adjoint(P, torch, K=500, C=50, n_dirs=20, h=1e-6):
         fd = (loss64(lp.c + h * dc, lp.b + h * db) - loss64(lp.c - h * dc, lp.b - h * db)) / (2 * h)
         ad = float(gc @ dc + gb @ db)
         errs.append(abs(ad - fd) / max(abs(fd), 1e-12))
+        errs_g.append(abs(ad - fd) / gnorm)
     return {"workload": f"adjoint-lp m={lp.m} n={lp.n} nnz={lp.nnz} K={K} checkpoints every {C}, FP32 forward",
             "forward_s": t_fwd, "backward_s": t_bwd,
             "fd_check": {"directions": n_dirs, "h": h, "reference": "central differences of the FP64 forward",
-                         "rel_err_median": float(np.median(errs)), "rel_err_max": float(np.max(errs))}}
+                         "rel_err_median": float(np.median(errs)), "rel_err_max": float(np.max(errs)),
+                         "err_over_grad_norm_max": float(np.max(errs_g))}}
 
 
 # ---------------------------------------------------------------------------

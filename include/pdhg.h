@@ -85,7 +85,7 @@ typedef struct {
   int inputs_on_device;   /* 1: pointers given to pdhg_create are device pointers */
   int use_graphs;         /* 1: replay evaluation blocks as CUDA graphs (1) */
   int kernel_timing;      /* 1: time the two step kernels with CUDA events (0) */
-  double polish_switch;   /* PDHG_MIXED: rel. KKT at which FP64 iterations take over (1e-7); they also
+  double polish_switch;   /* PDHG_MIXED: rel. KKT at which FP64 iterations take over (1e-5); they also
                              take over when the FP32 phase stalls (no 10% gain in 16384 iterations) */
   int long_row_min;       /* rows with at least this many entries get a warp each (128) */
   int rows_per_thread;    /* most rows one thread reduces at once in short rows: 1, 2 or 4 (4) */

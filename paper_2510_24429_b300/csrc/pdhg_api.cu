@@ -643,7 +643,7 @@ void pdhg_default_options(pdhg_options* o) {
   o->inputs_on_device = 0;
   o->use_graphs = 1;
   o->kernel_timing = 0;
-  o->polish_switch = 1e-7;
+  o->polish_switch = 1e-5;
   o->long_row_min = 128;
   o->rows_per_thread = 4;
   o->dual_hot_cols = 0;
