@@ -71,36 +71,35 @@ constexpr int TRACE_CAP = 65536;
 // Device layout of one copy of the scaled matrix (Ahat, or Ahat^T).
 //
 // Rows are stored in order of decreasing length (the engine renumbers the
-// variables and constraints internally to get there).
-//
-// Long rows: the leading n_long rows (at least `long_row_min` entries each)
-// are CSR reduced by one warp per row. Each starts at an entry offset that is
-// a multiple of 4 and is padded to a multiple of 4 entries, so a lane loads 4
-// indices (16 B) and 4 values (2 x 16 B) per step.
-//
-// Slices: the remaining rows are cut into slices of 32*R rows (R = rows per
-// thread, 1, 2 or 4, chosen per slice from its length). A slice is padded to
-// the length Lp of its first (longest) row; when Lp > 1 it is rounded up to an
-// even number and entries are stored in pairs: entry e of the slice's row
-// (32 q + lane) sits at
-//     soff[s] + ((e / 2) * R + q) * 64 + 2 * lane + (e % 2)
-// so one thread loads its row's next two indices and values with one 8-byte
-// and one 16-byte load and a warp reads contiguous 256 B / 512 B lines; when
-// Lp == 1 the slice is simply soff[s] + 32 q + lane. Padding slots hold value 0
-// and column 0. A "unit" is one long row or one slice; long rows come first.
+// variables and constraints internally to get there) and grouped into
+// "units", each processed by one warp:
+//   - a long row (at least `long_row_min` entries): CSR, reduced by the whole
+//     warp; it starts at an entry offset that is a multiple of 4 and is padded
+//     to a multiple of 4 entries;
+//   - a slice of 32*R shorter rows (R = rows per thread: 1, 2 or 4, chosen
+//     from the slice's length), padded to the length Lp of its first
+//     (longest) row; when Lp > 1 it is rounded up to an even number and the
+//     entries are stored in pairs: entry e of the slice's row (32 q + lane)
+//     sits at
+//         uoff[u] + ((e / 2) * R + q) * 64 + 2 * lane + (e % 2)
+//     so one thread loads its row's next two indices and values with one
+//     8-byte and one 16-byte load and a warp reads contiguous 256 B / 512 B
+//     lines; when Lp == 1 the entry of row (32 q + lane) sits at
+//     uoff[u] + 32 q + lane.
+// Padding slots hold value 0 and column 0. Rows numbered >= rows in a unit
+// are padding (a batch also pads each instance to whole blocks with empty
+// units whose first row is `rows`).
 struct Hyb {
   int rows = 0, cols = 0;
-  int n_long = 0;
-  int n_slices = 0;
-  long long nnz = 0;    // stored entries (without padding)
-  long long slots = 0;  // entry slots including padding
-  long long* loff = nullptr;  // [n_long + 1] offsets of the long rows (multiples of 4)
-  long long* soff = nullptr;  // [n_slices + 1] offsets of the slices
-  int2* sinfo = nullptr;      // [n_slices] (first row, rows per thread R)
+  int n_units = 0;
+  long long nnz = 0;          // stored entries (without padding)
+  long long slots = 0;        // entry slots including padding
+  long long* uoff = nullptr;  // [n_units + 1] entry offset of each unit
+  int2* uinfo = nullptr;      // [n_units] (first row, R); R = 0 marks a long row
   int* ci = nullptr;          // [slots] column index (internal numbering)
   double* v = nullptr;        // [slots] value
   float* v32 = nullptr;       // [slots] value rounded to FP32 (FP32 / mixed precision only)
-  int units() const { return n_long + n_slices; }
+  int units() const { return n_units; }
 };
 
 // ---------------------------------------------------------------------------

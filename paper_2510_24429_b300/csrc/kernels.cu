@@ -101,12 +101,6 @@ __device__ __forceinline__ long long slice_slot(long long base, int Lp, int R, i
   return Lp == 1 ? base + 32 * q + lane : base + ((long long)(e >> 1) * R + q) * 64 + 2 * lane + (e & 1);
 }
 
-__device__ __forceinline__ void slice_shape(const Hyb& H, int s, int2& info, long long& base, int& Lp) {
-  info = H.sinfo[s];
-  base = H.soff[s];
-  Lp = (int)((H.soff[s + 1] - base) / (32 * info.y));
-}
-
 // Scalar visitor (setup kernels): every warp takes units in a grid-stride
 // loop; op.entry(acc, k, r) sees every slot k of row r (padding included:
 // value 0, column 0), op.finish(r, acc) the combined result (max or sum).
@@ -116,18 +110,16 @@ __device__ __forceinline__ void hyb_rows(const Hyb& H, Op& op) {
   const int lane = threadIdx.x & 31;
   const int gwarp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
-  const int units = H.n_long + H.n_slices;
-  for (int u = gwarp; u < units; u += nwarps) {
-    if (u < H.n_long) {
+  for (int u = gwarp; u < H.n_units; u += nwarps) {
+    const int2 info = H.uinfo[u];
+    const long long base = H.uoff[u], end = H.uoff[u + 1];
+    if (info.y == 0) {
       double acc = 0.0;
-      for (long long k = H.loff[u] + lane; k < H.loff[u + 1]; k += 32) acc = op.entry(acc, k, u);
+      for (long long k = base + lane; k < end; k += 32) acc = op.entry(acc, k, info.x);
       acc = MAX ? warp_max(acc) : warp_sum(acc);
-      if (lane == 0) op.finish(u, acc);
+      if (lane == 0) op.finish(info.x, acc);
     } else {
-      int2 info;
-      long long base;
-      int Lp;
-      slice_shape(H, u - H.n_long, info, base, Lp);
+      const int Lp = (int)((end - base) / (32 * info.y));
       for (int q = 0; q < info.y; ++q) {
         const int r = info.x + 32 * q + lane;
         double acc = 0.0;
@@ -204,12 +196,13 @@ __device__ __forceinline__ void hyb_dot(const Hyb& H, const T* __restrict__ vals
   const int lane = threadIdx.x & 31;
   const int gwarp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
-  const int units = H.n_long + H.n_slices;
-  for (int u = gwarp; u < units; u += nwarps) {
-    if (u < H.n_long) {
-      const long long beg = H.loff[u], end = H.loff[u + 1];
+  for (int u = gwarp; u < H.n_units; u += nwarps) {
+    const int2 info = H.uinfo[u];
+    const long long beg = H.uoff[u], end = H.uoff[u + 1];
+    if (info.y == 0) {
+      const int row = info.x;
       typename Op::State st{};
-      if (lane == 0) st = op.begin(u);
+      if (lane == 0) st = op.begin(row);
       T acc = T(0);
       // a step covers 128 entries as two contiguous 64-entry halves; lane L
       // takes entries 2L, 2L+1 of each half, so every load instruction of the
@@ -232,12 +225,10 @@ __device__ __forceinline__ void hyb_dot(const Hyb& H, const T* __restrict__ vals
         acc += b.y * g3;
       }
       acc = warp_sum(acc);
-      if (lane == 0) op.finish(u, acc, st);
+      if (lane == 0) op.finish(row, acc, st);
     } else {
-      int2 info;
-      long long base;
-      int Lp;
-      slice_shape(H, u - H.n_long, info, base, Lp);
+      const long long base = beg;
+      const int Lp = (int)((end - beg) / (32 * info.y));
       if (info.y == 4)
         slice_dot<4>(H, vals, info.x, base, Lp, gather, op, pol, lane);
       else if (info.y == 2)

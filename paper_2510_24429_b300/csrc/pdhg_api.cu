@@ -299,93 +299,97 @@ std::vector<int> order_by_length(const std::vector<int>& len) {
 }
 
 struct HostHyb {
-  int rows = 0, cols = 0, n_long = 0, n_slices = 0;
+  int rows = 0, cols = 0;
   int64_t nnz = 0;
-  std::vector<long long> loff, soff;
-  std::vector<int> sinfo;  // pairs (first row, rows per thread)
+  std::vector<long long> uoff{0};  // unit offsets (n_units + 1)
+  std::vector<int> uinfo;          // pairs (first row, R); R = 0: long row
   std::vector<int> ci;
   std::vector<double> v;
+  int n_units() const { return (int)uinfo.size() / 2; }
 };
 
-// CSR with rows already sorted by decreasing length -> the Hyb layout (long
-// rows 4-aligned and padded to a multiple of 4; slices of 32*R rows, R = 4
-// for rows of length <= 1, 2 for length <= 8, else 1, capped by max_rpt;
-// slice length rounded up to even when above 1, entries stored in pairs).
-HostHyb make_hyb(int rows, int cols, const std::vector<int64_t>& rp, const std::vector<int>& ci,
-                 const std::vector<double>& v, int long_min, int max_rpt) {
-  HostHyb H;
-  H.rows = rows;
-  H.cols = cols;
-  H.nnz = rp[rows];
+// Append the units of `nrows` rows, given as CSR (rp local, 0-based; column
+// indices already in the final numbering) with rows sorted by decreasing
+// length, numbered from row_base. Long rows (>= long_min entries) become
+// 4-aligned, 4-padded warp units; the rest slices of 32*R rows, R = 4 for rows
+// of length <= 1, 2 for length <= 8, else 1 (capped by max_rpt), with the
+// slice length rounded up to even when above 1 and entries stored in pairs.
+void append_units(HostHyb& H, int row_base, int nrows, const std::vector<int64_t>& rp, const std::vector<int>& ci,
+                  const std::vector<double>& v, int long_min, int max_rpt) {
   auto len = [&](int r) { return (int)(rp[r + 1] - rp[r]); };
-  while (H.n_long < rows && len(H.n_long) >= long_min) ++H.n_long;
-  H.loff.resize(H.n_long + 1);
-  H.loff[0] = 0;
-  for (int r = 0; r < H.n_long; ++r) H.loff[r + 1] = H.loff[r] + ((len(r) + 3) / 4) * 4;
-  // slices
-  std::vector<int> s_row0, s_R, s_Lp;
-  for (int r = H.n_long; r < rows;) {
+  auto put = [&](long long k, int64_t src) {
+    if ((long long)H.ci.size() <= k) {
+      H.ci.resize(k + 1, 0);
+      H.v.resize(k + 1, 0.0);
+    }
+    H.ci[k] = ci[src];
+    H.v[k] = v[src];
+  };
+  H.nnz += rp[nrows];
+  int r = 0;
+  for (; r < nrows && len(r) >= long_min; ++r) {
+    const long long base = H.uoff.back();
+    const long long slots = ((len(r) + 3) / 4) * 4;
+    H.ci.resize(base + slots, 0);
+    H.v.resize(base + slots, 0.0);
+    for (int e = 0; e < len(r); ++e) put(base + e, rp[r] + e);
+    H.uinfo.push_back(row_base + r);
+    H.uinfo.push_back(0);
+    H.uoff.push_back(base + slots);
+  }
+  while (r < nrows) {
     const int L = len(r);
     int R = L <= 1 ? 4 : (L <= 8 ? 2 : 1);
     R = std::max(1, std::min(R, max_rpt));
-    s_row0.push_back(r);
-    s_R.push_back(R);
-    s_Lp.push_back(L <= 1 ? L : (L + 1) / 2 * 2);
-    r += 32 * R;
-  }
-  H.n_slices = (int)s_row0.size();
-  H.soff.resize(H.n_slices + 1);
-  H.soff[0] = H.loff[H.n_long];
-  H.sinfo.resize(2 * H.n_slices);
-  for (int s = 0; s < H.n_slices; ++s) {
-    H.soff[s + 1] = H.soff[s] + 32LL * s_R[s] * s_Lp[s];
-    H.sinfo[2 * s] = s_row0[s];
-    H.sinfo[2 * s + 1] = s_R[s];
-  }
-  const int64_t slots = H.soff[H.n_slices];
-  H.ci.assign(slots, 0);
-  H.v.assign(slots, 0.0);
-  for (int r = 0; r < H.n_long; ++r)
-    for (int e = 0; e < len(r); ++e) {
-      H.ci[H.loff[r] + e] = ci[rp[r] + e];
-      H.v[H.loff[r] + e] = v[rp[r] + e];
-    }
-  for (int s = 0; s < H.n_slices; ++s) {
-    const int R = s_R[s], Lp = s_Lp[s];
+    const int Lp = L <= 1 ? L : (L + 1) / 2 * 2;
+    const long long base = H.uoff.back();
+    const long long slots = 32LL * R * Lp;
+    H.ci.resize(base + slots, 0);
+    H.v.resize(base + slots, 0.0);
     for (int q = 0; q < R; ++q)
       for (int lane = 0; lane < 32; ++lane) {
-        const int r = s_row0[s] + 32 * q + lane;
-        if (r >= rows) continue;
-        for (int e = 0; e < len(r); ++e) {
-          const long long k = Lp == 1 ? H.soff[s] + 32 * q + lane
-                                      : H.soff[s] + ((long long)(e / 2) * R + q) * 64 + 2 * lane + (e % 2);
-          H.ci[k] = ci[rp[r] + e];
-          H.v[k] = v[rp[r] + e];
+        const int rr = r + 32 * q + lane;
+        if (rr >= nrows) continue;
+        for (int e = 0; e < len(rr); ++e) {
+          const long long k =
+              Lp == 1 ? base + 32 * q + lane : base + ((long long)(e / 2) * R + q) * 64 + 2 * lane + (e % 2);
+          put(k, rp[rr] + e);
         }
       }
+    H.uinfo.push_back(row_base + r);
+    H.uinfo.push_back(R);
+    H.uoff.push_back(base + slots);
+    r += 32 * R;
   }
-  return H;
+}
+
+// Empty units (no rows, no entries) so that a batch instance fills whole blocks.
+void pad_units(HostHyb& H, int multiple, int empty_row) {
+  while (H.n_units() % multiple != 0) {
+    H.uinfo.push_back(empty_row);
+    H.uinfo.push_back(1);
+    H.uoff.push_back(H.uoff.back());
+  }
 }
 
 pdhg_status upload_hyb(pdhg_ctx* ctx, const HostHyb& h, Hyb& d) {
   d.rows = h.rows;
   d.cols = h.cols;
-  d.n_long = h.n_long;
-  d.n_slices = h.n_slices;
+  d.n_units = h.n_units();
   d.nnz = h.nnz;
   d.slots = (long long)h.v.size();
-  CK(ctx, dalloc(ctx, &d.loff, h.loff.size()));
-  CK(ctx, dalloc(ctx, &d.soff, h.soff.size()));
-  CK(ctx, dalloc(ctx, &d.sinfo, std::max<size_t>(1, h.sinfo.size() / 2)));
+  CK(ctx, dalloc(ctx, &d.uoff, h.uoff.size()));
+  CK(ctx, dalloc(ctx, &d.uinfo, std::max<size_t>(1, h.uinfo.size() / 2)));
   CK(ctx, dalloc(ctx, &d.ci, h.ci.size()));
   CK(ctx, dalloc(ctx, &d.v, h.v.size()));
   cudaStream_t s = ctx->stream;
-  CK(ctx, cudaMemcpyAsync(d.loff, h.loff.data(), sizeof(long long) * h.loff.size(), cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(d.soff, h.soff.data(), sizeof(long long) * h.soff.size(), cudaMemcpyHostToDevice, s));
-  if (!h.sinfo.empty())
-    CK(ctx, cudaMemcpyAsync(d.sinfo, h.sinfo.data(), sizeof(int) * h.sinfo.size(), cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(d.ci, h.ci.data(), sizeof(int) * h.ci.size(), cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(d.v, h.v.data(), sizeof(double) * h.v.size(), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(d.uoff, h.uoff.data(), sizeof(long long) * h.uoff.size(), cudaMemcpyHostToDevice, s));
+  if (!h.uinfo.empty())
+    CK(ctx, cudaMemcpyAsync(d.uinfo, h.uinfo.data(), sizeof(int) * h.uinfo.size(), cudaMemcpyHostToDevice, s));
+  if (!h.ci.empty()) {
+    CK(ctx, cudaMemcpyAsync(d.ci, h.ci.data(), sizeof(int) * h.ci.size(), cudaMemcpyHostToDevice, s));
+    CK(ctx, cudaMemcpyAsync(d.v, h.v.data(), sizeof(double) * h.v.size(), cudaMemcpyHostToDevice, s));
+  }
   // the host vectors are freed when setup returns: wait for the copies
   CK(ctx, cudaStreamSynchronize(s));
   return PDHG_OK;
@@ -419,7 +423,9 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
         v[q] = val[k];
       }
     }
-    hA = make_hyb((int)m, (int)n, rp, ci, v, o.long_row_min, o.rows_per_thread);
+    hA.rows = (int)m;
+    hA.cols = (int)n;
+    append_units(hA, 0, (int)m, rp, ci, v, o.long_row_min, o.rows_per_thread);
   }
   {
     // transpose (stable counting sort over the caller's columns), then the
@@ -446,7 +452,9 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
       std::copy(tci.begin() + tp[j], tci.begin() + tp[j + 1], ci.begin() + rp[r]);
       std::copy(tv.begin() + tp[j], tv.begin() + tp[j + 1], v.begin() + rp[r]);
     }
-    hT = make_hyb((int)n, (int)m, rp, ci, v, o.long_row_min, o.rows_per_thread);
+    hT.rows = (int)n;
+    hT.cols = (int)m;
+    append_units(hT, 0, (int)n, rp, ci, v, o.long_row_min, o.rows_per_thread);
   }
   std::vector<double> bi(m), cI(n), x0i, y0i;
   for (int64_t r = 0; r < m; ++r) bi[r] = b[py[r]];
