@@ -233,6 +233,38 @@ PDHG_API pdhg_status pdhg_kkt_noalloc(int64_t m, int64_t n, const int64_t* a_row
                                       const double* at_val, const double* b, const double* c, const double* x,
                                       const double* y, int blocks, void* cuda_stream, pdhg_kkt_info* out);
 
+/* One LP of a batch (host pointers; same CSR rules as pdhg_create). */
+typedef struct {
+  int64_t m, n, nnz;
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+  const double* val;
+  const double* b;
+  const double* c;
+} pdhg_lp_desc;
+
+/* A batch of independent LPs of uneven sizes solved together: every PDHG
+ * half-step is one launch over all instances (their matrices laid out block-
+ * diagonally, each instance renumbered on its own and padded to whole thread
+ * blocks), while scaling, step sizes, primal weight, averages, restarts and
+ * termination are per instance; an instance that has converged stops (its
+ * blocks return at once). FP64, host inputs, starting point zero; snapshots,
+ * recording and warm starts are not available for batches. Use pdhg_iterate
+ * (runs until every instance meets tol, or max_iters), pdhg_batch_info and
+ * pdhg_batch_solution; pdhg_kkt and pdhg_get_solution return STATE. */
+PDHG_API pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_options* opt,
+                                       void* cuda_stream, pdhg_ctx** out);
+
+/* Per-instance arrays of length count (any may be NULL): iterations run,
+ * converged (rel_kkt <= tol at an evaluation), last candidate rel_kkt,
+ * restarts. Also valid for a single-LP context (count = 1). */
+PDHG_API pdhg_status pdhg_batch_info(pdhg_ctx* ctx, int64_t* iterations, int* converged, double* rel_kkt,
+                                     int64_t* restarts);
+
+/* (x, y, z) of one instance on its problem as given, into host buffers of its
+ * n, m, n (any may be NULL). */
+PDHG_API pdhg_status pdhg_batch_solution(pdhg_ctx* ctx, int instance, double* x, double* y, double* z);
+
 /* Description of the last failure of ctx, or of the last failed context-free
  * call (pdhg_create, pdhg_kkt_noalloc) when ctx is NULL. Never NULL. */
 PDHG_API const char* pdhg_last_error(const pdhg_ctx* ctx);

@@ -55,7 +55,9 @@ struct DevState {
   EvalSums cur, avg;
   // decision outputs
   int candidate, kind, apply_mode, converged;
-  int snapshot_flag, numeric, pad0, pad1;
+  int snapshot_flag, numeric;
+  int frozen;  // batch: the instance has converged; its blocks skip all work
+  int pad0;
   double cand_rel_kkt;
   double scratch[4];
 };

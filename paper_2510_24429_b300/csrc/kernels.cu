@@ -363,7 +363,8 @@ __global__ void k_div_by_norm(double* __restrict__ v, const double* __restrict__
 
 // scal: [0] = ||Ahat v||^2 of the last power iteration, [1] = ||chat||^2,
 // [2] = ||bhat||^2, [3] = ||b||^2, [4] = ||c||^2
-__global__ void k_finish_setup(DevState* st, const double* __restrict__ scal, double step_factor, int primal_weight) {
+__device__ void k_finish_setup_body(DevState* st, const double* __restrict__ scal, double step_factor,
+                                    int primal_weight) {
   const double est = sqrt(scal[0]);
   st->norm_est = est;
   st->eta = est > 0.0 ? step_factor / est : 1.0;
@@ -377,6 +378,10 @@ __global__ void k_finish_setup(DevState* st, const double* __restrict__ scal, do
   st->sigma = st->eta * omega;
   st->b_norm = sqrt(scal[3]);
   st->c_norm = sqrt(scal[4]);
+}
+
+__global__ void k_finish_setup(DevState* st, const double* __restrict__ scal, double step_factor, int primal_weight) {
+  k_finish_setup_body(st, scal, step_factor, primal_weight);
 }
 
 // ---------------------------------------------------------------------------
@@ -401,11 +406,19 @@ struct PrimalOp {
   }
 };
 
+// State of the problem a block works on: a batch maps every block to one
+// instance (binst); a single problem has binst == nullptr.
+__device__ __forceinline__ const DevState* block_state(const DevState* sts, const int* binst) {
+  return binst ? sts + binst[blockIdx.x] : sts;
+}
+
 template <class T>
 __global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS)
     k_primal_step(Hyb At, const T* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
-                  T* __restrict__ x, T* __restrict__ xbar, T* __restrict__ xsum, const DevState* __restrict__ st,
-                  int accumulate) {
+                  T* __restrict__ x, T* __restrict__ xbar, T* __restrict__ xsum, const DevState* __restrict__ sts,
+                  const int* __restrict__ binst, int accumulate) {
+  const DevState* st = block_state(sts, binst);
+  if (st->frozen) return;
   PrimalOp<T> op{ch, x, xbar, xsum, (T)st->tau, accumulate};
   hyb_dot(At, vals, GlobalGather<T>{y}, op);
 }
@@ -429,7 +442,10 @@ struct DualOp {
 template <class T>
 __global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS)
     k_dual_step(Hyb A, const T* __restrict__ vals, const T* __restrict__ xbar, const T* __restrict__ bh,
-                T* __restrict__ y, T* __restrict__ ysum, const DevState* __restrict__ st, int accumulate) {
+                T* __restrict__ y, T* __restrict__ ysum, const DevState* __restrict__ sts,
+                const int* __restrict__ binst, int accumulate) {
+  const DevState* st = block_state(sts, binst);
+  if (st->frozen) return;
   DualOp<T> op{bh, y, ysum, (T)st->sigma, accumulate};
   hyb_dot(A, vals, GlobalGather<T>{xbar}, op);
 }
@@ -499,7 +515,12 @@ struct EvalDualOp {
 __global__ void __launch_bounds__(TPB) k_eval_dual(Hyb At, const double* __restrict__ py,
                                                    const double* __restrict__ ch, const double* __restrict__ dc,
                                                    const double* __restrict__ px, const double* __restrict__ xr,
-                                                   double* __restrict__ partials) {
+                                                   double* __restrict__ partials, const DevState* __restrict__ sts,
+                                                   const int* __restrict__ binst) {
+  if (binst && sts[binst[blockIdx.x]].frozen) {
+    if (threadIdx.x < 6) partials[(size_t)blockIdx.x * NQ + Q_RD2S + threadIdx.x] = 0.0;
+    return;
+  }
   EvalDualOp op;
   op.ch = ch;
   op.dc = dc;
@@ -546,7 +567,12 @@ struct EvalPrimalOp {
 __global__ void __launch_bounds__(TPB) k_eval_primal(Hyb A, const double* __restrict__ px,
                                                      const double* __restrict__ bh, const double* __restrict__ dr,
                                                      const double* __restrict__ py, const double* __restrict__ yr,
-                                                     double* __restrict__ partials) {
+                                                     double* __restrict__ partials, const DevState* __restrict__ sts,
+                                                     const int* __restrict__ binst) {
+  if (binst && sts[binst[blockIdx.x]].frozen) {
+    if (threadIdx.x < 5) partials[(size_t)blockIdx.x * NQ + Q_RP2S + threadIdx.x] = 0.0;
+    return;
+  }
   EvalPrimalOp op;
   op.bh = bh;
   op.dr = dr;
@@ -599,7 +625,7 @@ __global__ void k_init_restart_ref(DevState* st) {
 
 // One evaluation's decisions (single thread): candidate, termination,
 // snapshot schedule (Algorithm 1), restart test, primal-weight update.
-__global__ void k_decide(DevState* st, TraceRec* trace) {
+__device__ void decide_one(DevState* st, TraceRec* trace) {
   double cp, cd, cg;
   scaled_norms(st->cur, cp, cd, cg);
   int which = KIND_CUR;
@@ -668,7 +694,7 @@ __global__ void k_decide(DevState* st, TraceRec* trace) {
   st->converged = converged;
   st->tau = st->eta / st->omega;
   st->sigma = st->eta * st->omega;
-  if (st->evals < TRACE_CAP) {
+  if (trace && st->evals < TRACE_CAP) {
     TraceRec& r = trace[st->evals];
     r.iteration = st->k;
     r.kind = kind;
@@ -677,6 +703,127 @@ __global__ void k_decide(DevState* st, TraceRec* trace) {
     r.rel_kkt = rel;
   }
   st->evals += 1;
+}
+
+__global__ void k_decide(DevState* st, TraceRec* trace) { decide_one(st, trace); }
+
+// ---------------------------------------------------------------------------
+// batch: per-instance counterparts (instance = blockIdx.y for vector kernels,
+// one thread per instance for scalar kernels)
+// ---------------------------------------------------------------------------
+__global__ void k_decide_b(DevState* sts, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count || sts[i].frozen) return;
+  decide_one(sts + i, nullptr);
+  if (sts[i].converged) sts[i].frozen = 1;
+}
+
+__global__ void k_add_counters_b(DevState* sts, int count, long long dk) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count || sts[i].frozen) return;
+  sts[i].k += dk;
+  sts[i].t += dk;
+}
+
+__global__ void k_init_restart_ref_b(DevState* sts, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double p, d, g;
+  scaled_norms(sts[i].cur, p, d, g);
+  sts[i].rs_p = sts[i].pc_p = p;
+  sts[i].rs_d = sts[i].pc_d = d;
+  sts[i].rs_g = sts[i].pc_g = g;
+}
+
+// per-instance sums of the per-block partials (blocks [bstart[i], bstart[i+1]))
+// into *(EvalSums*)((char*)out + i * stride)
+__global__ void k_eval_finalize_b(const double* __restrict__ partials, const int* __restrict__ bstart, char* out,
+                                  size_t stride) {
+  const int i = blockIdx.x;
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (q >= NQ) return;
+  const bool is_max = (q == Q_RDINF || q == Q_RPINF);
+  double acc = 0.0;
+  for (int b = bstart[i] + lane; b < bstart[i + 1]; b += 32) {
+    const double v = partials[(size_t)b * NQ + q];
+    acc = is_max ? fmax(acc, v) : acc + v;
+  }
+  acc = is_max ? warp_max(acc) : warp_sum(acc);
+  if (lane == 0) reinterpret_cast<EvalSums*>(out + (size_t)i * stride)->q[q] = acc;
+}
+
+__global__ void k_make_average_b(const double* __restrict__ xs, const double* __restrict__ ys,
+                                 const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ xa,
+                                 double* __restrict__ ya, const int* __restrict__ xoff, const int* __restrict__ yoff,
+                                 const DevState* __restrict__ sts) {
+  const int i = blockIdx.y;
+  if (sts[i].frozen) return;
+  const long long t = sts[i].t;
+  const double td = (double)t;
+  for (int j = xoff[i] + blockIdx.x * blockDim.x + threadIdx.x; j < xoff[i + 1]; j += gridDim.x * blockDim.x)
+    xa[j] = t > 0 ? xs[j] / td : x[j];
+  for (int r = yoff[i] + blockIdx.x * blockDim.x + threadIdx.x; r < yoff[i + 1]; r += gridDim.x * blockDim.x)
+    ya[r] = t > 0 ? ys[r] / td : y[r];
+}
+
+__global__ void k_apply_b(const DevState* __restrict__ sts, double* __restrict__ x, double* __restrict__ y,
+                          const double* __restrict__ xa, const double* __restrict__ ya, double* __restrict__ xr,
+                          double* __restrict__ yr, double* __restrict__ xs, double* __restrict__ ys,
+                          const int* __restrict__ xoff, const int* __restrict__ yoff) {
+  const int i = blockIdx.y;
+  const int mode = sts[i].apply_mode;
+  if (mode == APPLY_NONE) return;
+  for (int j = xoff[i] + blockIdx.x * blockDim.x + threadIdx.x; j < xoff[i + 1]; j += gridDim.x * blockDim.x) {
+    if (mode == APPLY_RESTART_AVG || mode == APPLY_TAKE_AVG) x[j] = xa[j];
+    if (mode != APPLY_TAKE_AVG) {
+      xr[j] = x[j];
+      xs[j] = 0.0;
+    }
+  }
+  for (int r = yoff[i] + blockIdx.x * blockDim.x + threadIdx.x; r < yoff[i + 1]; r += gridDim.x * blockDim.x) {
+    if (mode == APPLY_RESTART_AVG || mode == APPLY_TAKE_AVG) y[r] = ya[r];
+    if (mode != APPLY_TAKE_AVG) {
+      yr[r] = y[r];
+      ys[r] = 0.0;
+    }
+  }
+}
+
+// per-instance sum of squares of v over [off[i], off[i+1]) into out[i * ostride]
+// (one block per instance; deterministic)
+__global__ void __launch_bounds__(TPB) k_sumsq_b(const double* __restrict__ v, const int* __restrict__ off,
+                                                 double* __restrict__ out, int ostride) {
+  const int i = blockIdx.x;
+  double vals[1] = {0.0};
+  const bool mx[1] = {false};
+  for (int j = off[i] + threadIdx.x; j < off[i + 1]; j += blockDim.x) vals[0] += v[j] * v[j];
+  block_reduce<1>(vals, mx);
+  if (threadIdx.x == 0) out[(size_t)i * ostride] = vals[0];
+}
+
+// v = w / sqrt(s2[i * sstride]) on instance i's range when positive
+__global__ void k_div_by_norm_b(double* __restrict__ v, const double* __restrict__ w, const double* __restrict__ s2,
+                                int sstride, const int* __restrict__ off) {
+  const int i = blockIdx.y;
+  const double s = sqrt(s2[(size_t)i * sstride]);
+  if (!(s > 0.0)) return;
+  for (int j = off[i] + blockIdx.x * blockDim.x + threadIdx.x; j < off[i + 1]; j += gridDim.x * blockDim.x)
+    v[j] = w[j] / s;
+}
+
+// v = 1 / sqrt(count of instance i) on instance i's range (power-iteration start)
+__global__ void k_fill_unit_b(double* __restrict__ v, const int* __restrict__ off) {
+  const int i = blockIdx.y;
+  const double val = 1.0 / sqrt((double)(off[i + 1] - off[i]));
+  for (int j = off[i] + blockIdx.x * blockDim.x + threadIdx.x; j < off[i + 1]; j += gridDim.x * blockDim.x)
+    v[j] = val;
+}
+
+__global__ void k_finish_setup_b(DevState* sts, int count, const double* __restrict__ scal, int sstride,
+                                 double step_factor, int primal_weight) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  k_finish_setup_body(sts + i, scal + (size_t)i * sstride, step_factor, primal_weight);
 }
 
 __global__ void k_apply(const DevState* __restrict__ st, double* __restrict__ x, double* __restrict__ y,
@@ -925,20 +1072,20 @@ void launch_finish_setup(DevState* st, const double* scal, double step_factor, i
   k_finish_setup<<<1, 1, 0, s>>>(st, scal, step_factor, primal_weight);
 }
 void launch_primal_step(const Hyb& At, const double* y, const double* ch, double* x, double* xbar, double* xsum,
-                        const DevState* st, int accumulate, int grid, cudaStream_t s) {
-  k_primal_step<double><<<grid, TPB, 0, s>>>(At, At.v, y, ch, x, xbar, xsum, st, accumulate);
+                        const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst) {
+  k_primal_step<double><<<grid, TPB, 0, s>>>(At, At.v, y, ch, x, xbar, xsum, st, binst, accumulate);
 }
 void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
-                      const DevState* st, int accumulate, int grid, cudaStream_t s) {
-  k_dual_step<double><<<grid, TPB, 0, s>>>(A, A.v, xbar, bh, y, ysum, st, accumulate);
+                      const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst) {
+  k_dual_step<double><<<grid, TPB, 0, s>>>(A, A.v, xbar, bh, y, ysum, st, binst, accumulate);
 }
 void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float* x, float* xbar, float* xsum,
                           const DevState* st, int accumulate, int grid, cudaStream_t s) {
-  k_primal_step<float><<<grid, TPB, 0, s>>>(At, At.v32, y, ch, x, xbar, xsum, st, accumulate);
+  k_primal_step<float><<<grid, TPB, 0, s>>>(At, At.v32, y, ch, x, xbar, xsum, st, nullptr, accumulate);
 }
 void launch_dual_step32(const Hyb& A, const float* xbar, const float* bh, float* y, float* ysum, const DevState* st,
                         int accumulate, int grid, cudaStream_t s) {
-  k_dual_step<float><<<grid, TPB, 0, s>>>(A, A.v32, xbar, bh, y, ysum, st, accumulate);
+  k_dual_step<float><<<grid, TPB, 0, s>>>(A, A.v32, xbar, bh, y, ysum, st, nullptr, accumulate);
 }
 void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,
                           const DevState* st, int accumulate, int grid, cudaStream_t s) {
@@ -951,9 +1098,44 @@ void launch_make_average(const double* xs, const double* ys, const double* x, co
 }
 void launch_eval_point(const Hyb& A, const Hyb& At, const double* px, const double* py, const double* bh,
                        const double* ch, const double* dr, const double* dc, const double* xr, const double* yr,
-                       double* partials, int nb, cudaStream_t s) {
-  k_eval_dual<<<nb, TPB, 0, s>>>(At, py, ch, dc, px, xr, partials);
-  k_eval_primal<<<nb, TPB, 0, s>>>(A, px, bh, dr, py, yr, partials);
+                       double* partials, int nb, cudaStream_t s, const DevState* sts, const int* binst) {
+  k_eval_dual<<<nb, TPB, 0, s>>>(At, py, ch, dc, px, xr, partials, sts, binst);
+  k_eval_primal<<<nb, TPB, 0, s>>>(A, px, bh, dr, py, yr, partials, sts, binst);
+}
+void launch_decide_b(DevState* sts, int count, cudaStream_t s) { k_decide_b<<<(count + 127) / 128, 128, 0, s>>>(sts, count); }
+void launch_add_counters_b(DevState* sts, int count, long long dk, cudaStream_t s) {
+  k_add_counters_b<<<(count + 127) / 128, 128, 0, s>>>(sts, count, dk);
+}
+void launch_init_restart_ref_b(DevState* sts, int count, cudaStream_t s) {
+  k_init_restart_ref_b<<<(count + 127) / 128, 128, 0, s>>>(sts, count);
+}
+void launch_eval_finalize_b(const double* partials, const int* bstart, int count, EvalSums* out0, size_t stride,
+                            cudaStream_t s) {
+  k_eval_finalize_b<<<count, 32 * NQ, 0, s>>>(partials, bstart, reinterpret_cast<char*>(out0), stride);
+}
+void launch_make_average_b(const double* xs, const double* ys, const double* x, const double* y, double* xa,
+                           double* ya, const int* xoff, const int* yoff, const DevState* sts, int count, int gx,
+                           cudaStream_t s) {
+  k_make_average_b<<<dim3(gx, count), TPB, 0, s>>>(xs, ys, x, y, xa, ya, xoff, yoff, sts);
+}
+void launch_apply_b(const DevState* sts, double* x, double* y, const double* xa, const double* ya, double* xr,
+                    double* yr, double* xs, double* ys, const int* xoff, const int* yoff, int count, int gx,
+                    cudaStream_t s) {
+  k_apply_b<<<dim3(gx, count), TPB, 0, s>>>(sts, x, y, xa, ya, xr, yr, xs, ys, xoff, yoff);
+}
+void launch_sumsq_b(const double* v, const int* off, int count, double* out, int ostride, cudaStream_t s) {
+  k_sumsq_b<<<count, TPB, 0, s>>>(v, off, out, ostride);
+}
+void launch_div_by_norm_b(double* v, const double* w, const double* s2, int sstride, const int* off, int count,
+                          int gx, cudaStream_t s) {
+  k_div_by_norm_b<<<dim3(gx, count), TPB, 0, s>>>(v, w, s2, sstride, off);
+}
+void launch_fill_unit_b(double* v, const int* off, int count, int gx, cudaStream_t s) {
+  k_fill_unit_b<<<dim3(gx, count), TPB, 0, s>>>(v, off);
+}
+void launch_finish_setup_b(DevState* sts, int count, const double* scal, int sstride, double step_factor,
+                           int primal_weight, cudaStream_t s) {
+  k_finish_setup_b<<<(count + 127) / 128, 128, 0, s>>>(sts, count, scal, sstride, step_factor, primal_weight);
 }
 void launch_eval_finalize(const double* partials, int nb, EvalSums* out, cudaStream_t s) {
   k_eval_finalize<<<1, 32 * NQ, 0, s>>>(partials, nb, out);

@@ -32,11 +32,13 @@ void launch_finish_setup(DevState* st, const double* scal, double step_factor, i
 
 // ---- iteration --------------------------------------------------------------
 // x' = max(0, x - tau (chat - Ahat^T y)); xbar = 2x' - x; x <- x'; xsum += x'
+// st: the problem's state; for a batch, the instances' states and binst maps
+// every block to its instance (blocks of converged instances return at once)
 void launch_primal_step(const Hyb& At, const double* y, const double* ch, double* x, double* xbar, double* xsum,
-                        const DevState* st, int accumulate, int grid, cudaStream_t s);
+                        const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst = nullptr);
 // y' = y + sigma (bhat - Ahat xbar); y <- y'; ysum += y'
 void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
-                      const DevState* st, int accumulate, int grid, cudaStream_t s);
+                      const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst = nullptr);
 // the same two half-steps in FP32 (values At.v32 / A.v32, FP32 vectors and
 // accumulation); tau and sigma are read from the FP64 state and rounded
 void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float* x, float* xbar, float* xsum,
@@ -76,7 +78,27 @@ void launch_make_average(const double* xs, const double* ys, const double* x, co
 // restart distances). Both sides use the same nb blocks.
 void launch_eval_point(const Hyb& A, const Hyb& At, const double* px, const double* py, const double* bh,
                        const double* ch, const double* dr, const double* dc, const double* xr, const double* yr,
-                       double* partials, int nb, cudaStream_t s);
+                       double* partials, int nb, cudaStream_t s, const DevState* sts = nullptr,
+                       const int* binst = nullptr);
+// ---- batch (count instances; xoff/yoff: instance ranges of the column and row vectors) ----
+void launch_decide_b(DevState* sts, int count, cudaStream_t s);
+void launch_add_counters_b(DevState* sts, int count, long long dk, cudaStream_t s);
+void launch_init_restart_ref_b(DevState* sts, int count, cudaStream_t s);
+// sums of each instance's block partials into the EvalSums at out0 + i * stride bytes
+void launch_eval_finalize_b(const double* partials, const int* bstart, int count, EvalSums* out0, size_t stride,
+                            cudaStream_t s);
+void launch_make_average_b(const double* xs, const double* ys, const double* x, const double* y, double* xa,
+                           double* ya, const int* xoff, const int* yoff, const DevState* sts, int count, int gx,
+                           cudaStream_t s);
+void launch_apply_b(const DevState* sts, double* x, double* y, const double* xa, const double* ya, double* xr,
+                    double* yr, double* xs, double* ys, const int* xoff, const int* yoff, int count, int gx,
+                    cudaStream_t s);
+void launch_sumsq_b(const double* v, const int* off, int count, double* out, int ostride, cudaStream_t s);
+void launch_div_by_norm_b(double* v, const double* w, const double* s2, int sstride, const int* off, int count,
+                          int gx, cudaStream_t s);
+void launch_fill_unit_b(double* v, const int* off, int count, int gx, cudaStream_t s);
+void launch_finish_setup_b(DevState* sts, int count, const double* scal, int sstride, double step_factor,
+                           int primal_weight, cudaStream_t s);
 void launch_eval_finalize(const double* partials, int nb, EvalSums* out, cudaStream_t s);
 void launch_init_restart_ref(DevState* st, cudaStream_t s);
 void launch_decide(DevState* st, TraceRec* trace, cudaStream_t s);

@@ -60,6 +60,13 @@ struct pdhg_ctx {
   float *x32 = nullptr, *xbar32 = nullptr, *xsum32 = nullptr, *y32 = nullptr, *ysum32 = nullptr;
   float *ch32 = nullptr, *bh32 = nullptr;
   bool phase32 = false;
+  // batch (count > 1): instance-major layouts; instance i owns columns
+  // [xoff[i], xoff[i+1]) and rows [yoff[i], yoff[i+1]) of the internal
+  // numbering and blocks [bstart[i], bstart[i+1]) of every unit-grid launch
+  int count = 1;
+  std::vector<int> xoff_h, yoff_h, bstart_h;
+  int *xoff = nullptr, *yoff = nullptr, *binst = nullptr, *bstart = nullptr;
+  int nblocks = 0;
   // recording for the adjoint: (x_k, y_k) every checkpoint_every iterations
   std::vector<void*> ck_x, ck_y;
   void *w_x = nullptr, *w_y = nullptr, *w_xbar = nullptr, *w_seg = nullptr;
@@ -149,6 +156,29 @@ bool all_finite(const double* v, int64_t len) {
   for (int64_t i = 0; i < len; ++i)
     if (!std::isfinite(v[i])) return false;
   return true;
+}
+
+// Host checks of one LP (before any device work).
+pdhg_status validate_lp(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                        const double* val, const double* b, const double* c) {
+  if (m < 1 || n < 1 || m >= (1LL << 31) - 1 || n >= (1LL << 31) - 1)
+    return fail(nullptr, PDHG_ERR_INVALID, "m and n must be in [1, 2^31 - 1)");
+  if (nnz < 0 || nnz >= (1LL << 31) - 1) return fail(nullptr, PDHG_ERR_INVALID, "nnz must be in [0, 2^31 - 1)");
+  if (!row_ptr || (nnz > 0 && (!col_idx || !val)) || !b || !c)
+    return fail(nullptr, PDHG_ERR_INVALID, "NULL array argument");
+  if (row_ptr[0] != 0 || row_ptr[m] != nnz)
+    return fail(nullptr, PDHG_ERR_INVALID, "row_ptr[0] != 0 or row_ptr[m] != nnz");
+  for (int64_t i = 0; i < m; ++i) {
+    if (row_ptr[i + 1] < row_ptr[i]) return fail(nullptr, PDHG_ERR_INVALID, "row_ptr not non-decreasing");
+    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+      if (col_idx[k] < 0 || col_idx[k] >= n) return fail(nullptr, PDHG_ERR_INVALID, "column index out of range");
+      if (k > row_ptr[i] && col_idx[k] <= col_idx[k - 1])
+        return fail(nullptr, PDHG_ERR_INVALID, "column indices not strictly increasing within a row");
+    }
+  }
+  if (!all_finite(val, nnz) || !all_finite(b, m) || !all_finite(c, n))
+    return fail(nullptr, PDHG_ERR_NUMERIC, "NaN or Inf in the input data");
+  return PDHG_OK;
 }
 
 pdhg_status read_state(pdhg_ctx* ctx) {
@@ -363,9 +393,11 @@ void append_units(HostHyb& H, int row_base, int nrows, const std::vector<int64_t
   }
 }
 
-// Empty units (no rows, no entries) so that a batch instance fills whole blocks.
-void pad_units(HostHyb& H, int multiple, int empty_row) {
-  while (H.n_units() % multiple != 0) {
+// Append empty units (no entries; rows numbered from `empty_row`, which is
+// past the last row) until the layout has `target` units, so that a batch
+// instance fills whole blocks.
+void pad_units_to(HostHyb& H, int target, int empty_row) {
+  while (H.n_units() < target) {
     H.uinfo.push_back(empty_row);
     H.uinfo.push_back(1);
     H.uoff.push_back(H.uoff.back());
@@ -625,6 +657,296 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   return PDHG_OK;
 }
 
+// ---- batch -------------------------------------------------------------------
+
+pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
+  const pdhg_options& o = ctx->opt;
+  ctx->count = count;
+  ctx->xoff_h.assign(count + 1, 0);
+  ctx->yoff_h.assign(count + 1, 0);
+  for (int i = 0; i < count; ++i) {
+    ctx->xoff_h[i + 1] = ctx->xoff_h[i] + (int)lps[i].n;
+    ctx->yoff_h[i + 1] = ctx->yoff_h[i] + (int)lps[i].m;
+  }
+  const int64_t m = ctx->m, n = ctx->n;
+  HostHyb hA, hT;
+  hA.rows = (int)m;
+  hA.cols = (int)n;
+  hT.rows = (int)n;
+  hT.cols = (int)m;
+  std::vector<int> perm_x(n), perm_y(m), binst;
+  std::vector<double> bi(m), cI(n);
+  ctx->bstart_h.assign(count + 1, 0);
+  for (int inst = 0; inst < count; ++inst) {
+    const pdhg_lp_desc& L = lps[inst];
+    const int x0 = ctx->xoff_h[inst], y0 = ctx->yoff_h[inst];
+    const int64_t mi = L.m, ni = L.n, nzi = L.nnz;
+    std::vector<int> lenA(mi), lenT(ni, 0);
+    for (int64_t i = 0; i < mi; ++i) lenA[i] = (int)(L.row_ptr[i + 1] - L.row_ptr[i]);
+    for (int64_t k = 0; k < nzi; ++k) lenT[L.col_idx[k]] += 1;
+    const std::vector<int> py = order_by_length(lenA), px = order_by_length(lenT);
+    std::vector<int> iy(mi), ix(ni);
+    for (int64_t r = 0; r < mi; ++r) iy[py[r]] = (int)r;
+    for (int64_t r = 0; r < ni; ++r) ix[px[r]] = (int)r;
+    for (int64_t r = 0; r < mi; ++r) {
+      perm_y[y0 + r] = y0 + py[r];
+      bi[y0 + r] = L.b[py[r]];
+    }
+    for (int64_t r = 0; r < ni; ++r) {
+      perm_x[x0 + r] = x0 + px[r];
+      cI[x0 + r] = L.c[px[r]];
+    }
+    const int units_before = hA.n_units();
+    {
+      std::vector<int64_t> rp(mi + 1, 0);
+      std::vector<int> ci(nzi);
+      std::vector<double> v(nzi);
+      for (int64_t r = 0; r < mi; ++r) rp[r + 1] = rp[r] + lenA[py[r]];
+      for (int64_t r = 0; r < mi; ++r) {
+        int64_t q = rp[r];
+        for (int64_t k = L.row_ptr[py[r]]; k < L.row_ptr[py[r] + 1]; ++k, ++q) {
+          ci[q] = x0 + ix[L.col_idx[k]];
+          v[q] = L.val[k];
+        }
+      }
+      append_units(hA, y0, (int)mi, rp, ci, v, o.long_row_min, o.rows_per_thread);
+    }
+    {
+      std::vector<int64_t> tp(ni + 1, 0);
+      for (int64_t j = 0; j < ni; ++j) tp[j + 1] = tp[j] + lenT[j];
+      std::vector<int> tci(nzi);
+      std::vector<double> tv(nzi);
+      std::vector<int64_t> next(tp.begin(), tp.end() - 1);
+      for (int64_t i = 0; i < mi; ++i)
+        for (int64_t k = L.row_ptr[i]; k < L.row_ptr[i + 1]; ++k) {
+          const int64_t pos = next[L.col_idx[k]]++;
+          tci[pos] = y0 + iy[i];
+          tv[pos] = L.val[k];
+        }
+      std::vector<int64_t> rp(ni + 1, 0);
+      std::vector<int> ci(nzi);
+      std::vector<double> v(nzi);
+      for (int64_t r = 0; r < ni; ++r) rp[r + 1] = rp[r] + lenT[px[r]];
+      for (int64_t r = 0; r < ni; ++r) {
+        std::copy(tci.begin() + tp[px[r]], tci.begin() + tp[px[r] + 1], ci.begin() + rp[r]);
+        std::copy(tv.begin() + tp[px[r]], tv.begin() + tp[px[r] + 1], v.begin() + rp[r]);
+      }
+      append_units(hT, x0, (int)ni, rp, ci, v, o.long_row_min, o.rows_per_thread);
+    }
+    // both layouts get the same whole number of blocks for this instance
+    const int uA = hA.n_units() - units_before, uT = hT.n_units() - units_before;
+    const int blocks = (std::max(uA, uT) + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+    pad_units_to(hA, units_before + blocks * WARPS_PER_BLOCK, (int)m);
+    pad_units_to(hT, units_before + blocks * WARPS_PER_BLOCK, (int)n);
+    ctx->bstart_h[inst + 1] = ctx->bstart_h[inst] + blocks;
+    for (int b = 0; b < blocks; ++b) binst.push_back(inst);
+  }
+  ctx->nblocks = ctx->bstart_h[count];
+
+  pdhg_status rs = upload_hyb(ctx, hA, ctx->A);
+  if (rs != PDHG_OK) return rs;
+  rs = upload_hyb(ctx, hT, ctx->At);
+  if (rs != PDHG_OK) return rs;
+  Hyb& A = ctx->A;
+  Hyb& At = ctx->At;
+  cudaStream_t s = ctx->stream;
+  CK(ctx, dalloc(ctx, &ctx->perm_x, n));
+  CK(ctx, dalloc(ctx, &ctx->perm_y, m));
+  CK(ctx, dalloc(ctx, &ctx->xoff, count + 1));
+  CK(ctx, dalloc(ctx, &ctx->yoff, count + 1));
+  CK(ctx, dalloc(ctx, &ctx->bstart, count + 1));
+  CK(ctx, dalloc(ctx, &ctx->binst, ctx->nblocks));
+  double** vecs_n[] = {&ctx->c, &ctx->ch, &ctx->dc, &ctx->x, &ctx->xbar, &ctx->xsum, &ctx->xavg, &ctx->xr,
+                       &ctx->tmp_n, &ctx->tmp_n2};
+  double** vecs_m[] = {&ctx->b, &ctx->bh, &ctx->dr, &ctx->y, &ctx->ysum, &ctx->yavg, &ctx->yr, &ctx->tmp_m};
+  for (double** p : vecs_n) CK(ctx, dalloc(ctx, p, n));
+  for (double** p : vecs_m) CK(ctx, dalloc(ctx, p, m));
+  ctx->nb_eval = ctx->nblocks;
+  CK(ctx, dalloc(ctx, &ctx->partials, (size_t)ctx->nblocks * NQ));
+  CK(ctx, dalloc(ctx, &ctx->scal, (size_t)8 * count));
+  CK(ctx, dalloc(ctx, &ctx->st, count));
+  CK(ctx, dalloc(ctx, &ctx->kkt_sums, 1));
+  CK(ctx, dalloc(ctx, &ctx->trace, 1));
+  CK(ctx, dalloc(ctx, &ctx->sol, 2 * n + m));
+  CK(ctx, cudaMallocHost(&ctx->h_st, sizeof(DevState) * count));
+  CK(ctx, cudaMallocHost(&ctx->h_kkt, sizeof(EvalSums)));
+  for (int i = 0; i < 3 * EV_POOL; ++i) CK(ctx, cudaEventCreate(&ctx->ev[i]));
+  prefer_l1_for_step_kernels();
+  CK(ctx, cudaMemcpyAsync(ctx->perm_x, perm_x.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->perm_y, perm_y.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->xoff, ctx->xoff_h.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->yoff, ctx->yoff_h.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->bstart, ctx->bstart_h.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->binst, binst.data(), sizeof(int) * ctx->nblocks, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->b, bi.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->c, cI.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+
+  // scaling: row and column factors are per row / column, so one pass over
+  // the block-diagonal layouts scales every instance by its own factors
+  const int gn = vec_grid(ctx, n), gm = vec_grid(ctx, m);
+  const int grA = stride_grid(ctx, A), grT = stride_grid(ctx, At);
+  launch_fill(ctx->dr, 1.0, m, gm, s);
+  launch_fill(ctx->dc, 1.0, n, gn, s);
+  double* r = ctx->tmp_m;
+  double* sf = ctx->tmp_n;
+  for (int it = 0; it < o.ruiz_iters; ++it) {
+    launch_row_absmax(A, r, grA, s);
+    launch_row_absmax(At, sf, grT, s);
+    launch_inv_sqrt_or_one(r, r, (int)m, gm, s);
+    launch_inv_sqrt_or_one(sf, sf, (int)n, gn, s);
+    launch_scale(A, r, sf, 0, grA, s);
+    launch_scale(At, r, sf, 1, grT, s);
+    launch_mul_inplace(ctx->dr, r, (int)m, gm, s);
+    launch_mul_inplace(ctx->dc, sf, (int)n, gn, s);
+  }
+  if (o.pock_chambolle) {
+    launch_row_abspow_sum(A, o.pc_alpha, r, grA, s);
+    launch_row_abspow_sum(At, 2.0 - o.pc_alpha, sf, grT, s);
+    launch_inv_sqrt_or_one(r, r, (int)m, gm, s);
+    launch_inv_sqrt_or_one(sf, sf, (int)n, gn, s);
+    launch_scale(A, r, sf, 0, grA, s);
+    launch_scale(At, r, sf, 1, grT, s);
+    launch_mul_inplace(ctx->dr, r, (int)m, gm, s);
+    launch_mul_inplace(ctx->dc, sf, (int)n, gn, s);
+  }
+  launch_mul(ctx->bh, ctx->dr, ctx->b, (int)m, gm, s);
+  launch_mul(ctx->ch, ctx->dc, ctx->c, (int)n, gn, s);
+
+  // power iteration, norms and step sizes per instance
+  const int gx = std::max(1, std::min(64, (int)(n / count / TPB + 1)));
+  double* v = ctx->tmp_n;
+  double* w = ctx->tmp_n2;
+  double* u = ctx->tmp_m;
+  launch_fill_unit_b(v, ctx->xoff, count, gx, s);
+  launch_fill(ctx->scal, 0.0, (long long)8 * count, vec_grid(ctx, 8 * count), s);
+  for (int it = 0; it < o.power_iters; ++it) {
+    launch_spmv(A, v, u, grA, s);
+    launch_sumsq_b(u, ctx->yoff, count, ctx->scal + 0, 8, s);
+    launch_spmv(At, u, w, grT, s);
+    launch_sumsq_b(w, ctx->xoff, count, ctx->scal + 5, 8, s);
+    launch_div_by_norm_b(v, w, ctx->scal + 5, 8, ctx->xoff, count, gx, s);
+  }
+  launch_sumsq_b(ctx->ch, ctx->xoff, count, ctx->scal + 1, 8, s);
+  launch_sumsq_b(ctx->bh, ctx->yoff, count, ctx->scal + 2, 8, s);
+  launch_sumsq_b(ctx->b, ctx->yoff, count, ctx->scal + 3, 8, s);
+  launch_sumsq_b(ctx->c, ctx->xoff, count, ctx->scal + 4, 8, s);
+  CK(ctx, cudaGetLastError());
+  DevState h{};
+  h.eps_factor = o.eps_factor;
+  h.beta_suff = o.beta_suff;
+  h.beta_nec = o.beta_nec;
+  h.beta_art = o.beta_art;
+  h.theta = o.theta;
+  h.restarts_on = o.restarts;
+  h.primal_weight_on = o.primal_weight;
+  for (int i = 0; i < count; ++i) ctx->h_st[i] = h;
+  CK(ctx, cudaMemcpyAsync(ctx->st, ctx->h_st, sizeof(DevState) * count, cudaMemcpyHostToDevice, s));
+  launch_finish_setup_b(ctx->st, count, ctx->scal, 8, o.step_factor, o.primal_weight, s);
+
+  // start at zero; the starting point is each instance's restart reference
+  launch_fill(ctx->x, 0.0, n, gn, s);
+  launch_fill(ctx->y, 0.0, m, gm, s);
+  launch_fill(ctx->xsum, 0.0, n, gn, s);
+  launch_fill(ctx->ysum, 0.0, m, gm, s);
+  launch_fill(ctx->xr, 0.0, n, gn, s);
+  launch_fill(ctx->yr, 0.0, m, gm, s);
+  launch_fill(ctx->xavg, 0.0, n, gn, s);
+  launch_fill(ctx->yavg, 0.0, m, gm, s);
+  launch_eval_point(A, At, ctx->x, ctx->y, ctx->bh, ctx->ch, ctx->dr, ctx->dc, nullptr, nullptr, ctx->partials,
+                    ctx->nblocks, s, ctx->st, ctx->binst);
+  launch_eval_finalize_b(ctx->partials, ctx->bstart, count, &ctx->st->cur, sizeof(DevState), s);
+  launch_init_restart_ref_b(ctx->st, count, s);
+  CK(ctx, cudaGetLastError());
+  CK(ctx, cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevState) * count, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  for (int i = 0; i < count; ++i)
+    if (!std::isfinite(ctx->h_st[i].norm_est) || !std::isfinite(ctx->h_st[i].omega))
+      return fail(ctx, PDHG_ERR_NUMERIC, "non-finite norm estimate or primal weight after scaling");
+  return PDHG_OK;
+}
+
+// Evaluate the current and average points of every active instance.
+void eval_batch(pdhg_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  const int count = ctx->count;
+  const int gx = std::max(1, std::min(64, (int)(ctx->n / count / TPB + 1)));
+  if (ctx->opt.restarts) {
+    launch_make_average_b(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xoff, ctx->yoff, ctx->st,
+                          count, gx, s);
+    launch_eval_point(ctx->A, ctx->At, ctx->xavg, ctx->yavg, ctx->bh, ctx->ch, ctx->dr, ctx->dc, ctx->xr, ctx->yr,
+                      ctx->partials, ctx->nblocks, s, ctx->st, ctx->binst);
+    launch_eval_finalize_b(ctx->partials, ctx->bstart, count, &ctx->st->avg, sizeof(DevState), s);
+  }
+  launch_eval_point(ctx->A, ctx->At, ctx->x, ctx->y, ctx->bh, ctx->ch, ctx->dr, ctx->dc, ctx->xr, ctx->yr,
+                    ctx->partials, ctx->nblocks, s, ctx->st, ctx->binst);
+  launch_eval_finalize_b(ctx->partials, ctx->bstart, count, &ctx->st->cur, sizeof(DevState), s);
+  launch_decide_b(ctx->st, count, s);
+  launch_apply_b(ctx->st, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, ctx->xsum, ctx->ysum, ctx->xoff,
+                 ctx->yoff, count, gx, s);
+}
+
+pdhg_status iterate_batch(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done) {
+  const pdhg_options& o = ctx->opt;
+  cudaStream_t s = ctx->stream;
+  const int count = ctx->count;
+  for (int i = 0; i < count; ++i) ctx->h_st[i].tol = tol;
+  // tolerance of every instance (the rest of the state stays on the device)
+  for (int i = 0; i < count; ++i)
+    CK(ctx, cudaMemcpyAsync(&ctx->st[i].tol, &ctx->h_st[i].tol, sizeof(double), cudaMemcpyHostToDevice, s));
+  int64_t done = 0;
+  bool all_done = false;
+  while (done < max_iters && !all_done) {
+    const int64_t nb = std::min<int64_t>(o.eval_every - (ctx->k % o.eval_every), max_iters - done);
+    const bool timing = o.kernel_timing && nb <= EV_POOL;
+    for (int64_t it = 0; it < nb; ++it) {
+      if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
+      launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, ctx->nblocks,
+                         s, ctx->binst);
+      if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
+      launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, ctx->nblocks, s,
+                       ctx->binst);
+      if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 2], s));
+    }
+    launch_add_counters_b(ctx->st, count, nb, s);
+    ctx->launches += 2 * nb + 1;
+    CK(ctx, cudaGetLastError());
+    ctx->k += nb;
+    done += nb;
+    if (timing) {
+      CK(ctx, cudaEventSynchronize(ctx->ev[3 * (nb - 1) + 2]));
+      for (int64_t it = 0; it < nb; ++it) {
+        float a = 0.f, bms = 0.f;
+        CK(ctx, cudaEventElapsedTime(&a, ctx->ev[3 * it], ctx->ev[3 * it + 1]));
+        CK(ctx, cudaEventElapsedTime(&bms, ctx->ev[3 * it + 1], ctx->ev[3 * it + 2]));
+        ctx->ms_primal += a;
+        ctx->ms_dual += bms;
+      }
+      ctx->launches_primal += nb;
+      ctx->launches_dual += nb;
+    }
+    if (ctx->k % o.eval_every == 0) {
+      eval_batch(ctx);
+      ctx->launches += (o.restarts ? 4 : 0) + 3 + 2;
+      CK(ctx, cudaGetLastError());
+      CK(ctx, cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevState) * count, cudaMemcpyDeviceToHost, s));
+      CK(ctx, cudaStreamSynchronize(s));
+      all_done = true;
+      for (int i = 0; i < count; ++i) {
+        if (ctx->h_st[i].numeric && !ctx->h_st[i].frozen) {
+          if (iters_done) *iters_done = done;
+          return fail(ctx, PDHG_ERR_NUMERIC, "NaN or Inf in the iterates of instance " + std::to_string(i));
+        }
+        all_done = all_done && ctx->h_st[i].frozen;
+      }
+    }
+  }
+  CK(ctx, cudaStreamSynchronize(s));
+  if (iters_done) *iters_done = done;
+  ctx->converged = all_done;
+  if (all_done || tol == 0.0) return PDHG_OK;
+  return fail(ctx, PDHG_ERR_NOT_CONVERGED, "iteration limit reached before every instance met the tolerance");
+}
+
 }  // namespace
 
 extern "C" {
@@ -718,18 +1040,9 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     if (y0) y0 = h_y0.data();
   }
   // CSR validation (host logic, before any device work)
-  if (row_ptr[0] != 0 || row_ptr[m] != nnz)
-    return fail(nullptr, PDHG_ERR_INVALID, "row_ptr[0] != 0 or row_ptr[m] != nnz");
-  for (int64_t i = 0; i < m; ++i) {
-    if (row_ptr[i + 1] < row_ptr[i]) return fail(nullptr, PDHG_ERR_INVALID, "row_ptr not non-decreasing");
-    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-      if (col_idx[k] < 0 || col_idx[k] >= n) return fail(nullptr, PDHG_ERR_INVALID, "column index out of range");
-      if (k > row_ptr[i] && col_idx[k] <= col_idx[k - 1])
-        return fail(nullptr, PDHG_ERR_INVALID, "column indices not strictly increasing within a row");
-    }
-  }
-  if (!all_finite(val, nnz) || !all_finite(b, m) || !all_finite(c, n) || (x0 && !all_finite(x0, n)) ||
-      (y0 && !all_finite(y0, m)))
+  pdhg_status vs = validate_lp(m, n, nnz, row_ptr, col_idx, val, b, c);
+  if (vs != PDHG_OK) return vs;
+  if ((x0 && !all_finite(x0, n)) || (y0 && !all_finite(y0, m)))
     return fail(nullptr, PDHG_ERR_NUMERIC, "NaN or Inf in the input data");
 
   pdhg_ctx* ctx = new (std::nothrow) pdhg_ctx();
@@ -791,6 +1104,7 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
   if (max_iters < 0 || !(tol >= 0.0)) return fail(ctx, PDHG_ERR_INVALID, "max_iters < 0 or tol < 0");
   pdhg_status rs = set_device(ctx);
   if (rs != PDHG_OK) return rs;
+  if (ctx->count > 1) return iterate_batch(ctx, max_iters, tol, iters_done);
   const pdhg_options& o = ctx->opt;
   const bool evaluating = o.restarts || tol > 0.0 || o.eps_cross > 0.0 || o.snapshot_every > 0;
   const int n = (int)ctx->n, m = (int)ctx->m;
@@ -920,6 +1234,7 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
 
 pdhg_status pdhg_kkt(pdhg_ctx* ctx, int which, pdhg_kkt_info* out) {
   if (!ctx) return PDHG_ERR_INVALID;
+  if (ctx->count > 1) return fail(ctx, PDHG_ERR_STATE, "batch context: use pdhg_batch_info");
   if (!out) return fail(ctx, PDHG_ERR_INVALID, "out is NULL");
   if (which < PDHG_CURRENT || which > PDHG_LAST_RESTART) return fail(ctx, PDHG_ERR_INVALID, "bad point selector");
   pdhg_status rs = set_device(ctx);
@@ -950,6 +1265,7 @@ pdhg_status pdhg_kkt(pdhg_ctx* ctx, int which, pdhg_kkt_info* out) {
 
 pdhg_status pdhg_get_solution(pdhg_ctx* ctx, int which, double* x, double* y, double* z, int on_device) {
   if (!ctx) return PDHG_ERR_INVALID;
+  if (ctx->count > 1) return fail(ctx, PDHG_ERR_STATE, "batch context: use pdhg_batch_solution");
   if (which < PDHG_CURRENT || which > PDHG_LAST_RESTART) return fail(ctx, PDHG_ERR_INVALID, "bad point selector");
   pdhg_status rs = set_device(ctx);
   if (rs != PDHG_OK) return rs;
@@ -1070,6 +1386,106 @@ pdhg_status pdhg_backward(pdhg_ctx* ctx, const double* dL_dxK, const double* dL_
   CK(ctx, cudaMemcpyAsync(dL_dc, out_c, sizeof(double) * n, out_kind, s));
   CK(ctx, cudaMemcpyAsync(dL_db, out_b, sizeof(double) * m, out_kind, s));
   CK(ctx, cudaStreamSynchronize(s));
+  return PDHG_OK;
+}
+
+pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_options* opt, void* cuda_stream,
+                              pdhg_ctx** out) {
+  if (!out) return fail(nullptr, PDHG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !lps) return fail(nullptr, PDHG_ERR_INVALID, "count < 1 or lps is NULL");
+  pdhg_options o;
+  if (opt)
+    o = *opt;
+  else
+    pdhg_default_options(&o);
+  if (o.precision != PDHG_FP64 || o.record_for_backward || o.eps_cross > 0.0 || o.snapshot_every > 0 ||
+      o.inputs_on_device || o.dual_hot_cols || o.eval_every < 1 || o.ruiz_iters < 0 || o.power_iters < 1 ||
+      !(o.step_factor > 0.0) || o.long_row_min < 1 ||
+      !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4))
+    return fail(nullptr, PDHG_ERR_INVALID,
+                "batch: FP64, host inputs, no snapshots, no recording, no shared-memory hot columns, valid options");
+  int64_t mt = 0, nt = 0, zt = 0;
+  for (int i = 0; i < count; ++i) {
+    const pdhg_lp_desc& L = lps[i];
+    pdhg_status vs = validate_lp(L.m, L.n, L.nnz, L.row_ptr, L.col_idx, L.val, L.b, L.c);
+    if (vs != PDHG_OK) {
+      g_create_error = "instance " + std::to_string(i) + ": " + g_create_error;
+      return vs;
+    }
+    mt += L.m;
+    nt += L.n;
+    zt += L.nnz;
+  }
+  if (mt >= (1LL << 31) - 1 || nt >= (1LL << 31) - 1 || zt >= (1LL << 31) - 1)
+    return fail(nullptr, PDHG_ERR_INVALID, "batch totals of m, n and nnz must be below 2^31 - 1");
+  pdhg_ctx* ctx = new (std::nothrow) pdhg_ctx();
+  if (!ctx) return fail(nullptr, PDHG_ERR_OOM, "host allocation of the context failed");
+  ctx->m = mt;
+  ctx->n = nt;
+  ctx->nnz = zt;
+  ctx->opt = o;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) {
+      ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+      ctx->own_stream = true;
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    pdhg_status st = cuda_fail(nullptr, e, "device/stream setup");
+    pdhg_destroy(ctx);
+    return st;
+  }
+  pdhg_status st = setup_batch(ctx, count, lps);
+  if (st != PDHG_OK) {
+    g_create_error = ctx->err;
+    pdhg_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return PDHG_OK;
+}
+
+pdhg_status pdhg_batch_info(pdhg_ctx* ctx, int64_t* iterations, int* converged, double* rel_kkt, int64_t* restarts) {
+  if (!ctx) return PDHG_ERR_INVALID;
+  pdhg_status rs = set_device(ctx);
+  if (rs != PDHG_OK) return rs;
+  CK(ctx, cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevState) * ctx->count, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < ctx->count; ++i) {
+    const DevState& h = ctx->h_st[i];
+    if (iterations) iterations[i] = h.k;
+    if (converged) converged[i] = ctx->count > 1 ? h.frozen : (ctx->converged ? 1 : 0);
+    if (rel_kkt) rel_kkt[i] = h.cand_rel_kkt;
+    if (restarts) restarts[i] = h.restarts;
+  }
+  return PDHG_OK;
+}
+
+pdhg_status pdhg_batch_solution(pdhg_ctx* ctx, int instance, double* x, double* y, double* z) {
+  if (!ctx) return PDHG_ERR_INVALID;
+  if (instance < 0 || instance >= ctx->count) return fail(ctx, PDHG_ERR_INVALID, "instance out of range");
+  pdhg_status rs = set_device(ctx);
+  if (rs != PDHG_OK) return rs;
+  double* ox = ctx->sol;
+  double* oy = ctx->sol + ctx->n;
+  double* oz = ctx->sol + ctx->n + ctx->m;
+  launch_pack_solution(ctx->At, ctx->perm_x, ctx->perm_y, ctx->x, ctx->y, ctx->ch, ctx->dc, ctx->dr, ox, oy, oz,
+                       stride_grid(ctx, ctx->At), ctx->stream);
+  CK(ctx, cudaGetLastError());
+  const int x0 = ctx->count > 1 ? ctx->xoff_h[instance] : 0;
+  const int y0 = ctx->count > 1 ? ctx->yoff_h[instance] : 0;
+  const int64_t ni = ctx->count > 1 ? ctx->xoff_h[instance + 1] - x0 : ctx->n;
+  const int64_t mi = ctx->count > 1 ? ctx->yoff_h[instance + 1] - y0 : ctx->m;
+  if (x) CK(ctx, cudaMemcpyAsync(x, ox + x0, sizeof(double) * ni, cudaMemcpyDeviceToHost, ctx->stream));
+  if (y) CK(ctx, cudaMemcpyAsync(y, oy + y0, sizeof(double) * mi, cudaMemcpyDeviceToHost, ctx->stream));
+  if (z) CK(ctx, cudaMemcpyAsync(z, oz + x0, sizeof(double) * ni, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
   return PDHG_OK;
 }
 

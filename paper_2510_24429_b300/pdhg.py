@@ -80,6 +80,11 @@ class pdhg_trace_rec(C.Structure):
                 ("rel_kkt", C.c_double)]
 
 
+class pdhg_lp_desc(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col_idx", C.c_void_p), ("val", C.c_void_p), ("b", C.c_void_p), ("c", C.c_void_p)]
+
+
 class PDHGError(RuntimeError):
     def __init__(self, status: int, msg: str):
         self.status = status
@@ -105,6 +110,9 @@ SIGNATURES = {
     "pdhg_backward": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
     "pdhg_get_trace": (C.c_int, [_P, C.POINTER(pdhg_trace_rec), C.c_int64, C.POINTER(C.c_int64)]),
     "pdhg_last_error": (C.c_char_p, [_P]),
+    "pdhg_create_batch": (C.c_int, [C.c_int, C.POINTER(pdhg_lp_desc), C.POINTER(pdhg_options), _P, C.POINTER(_P)]),
+    "pdhg_batch_info": (C.c_int, [_P, _P, _P, _P, _P]),
+    "pdhg_batch_solution": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "pdhg_kkt_noalloc": (C.c_int, [C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P,
                                    C.POINTER(pdhg_kkt_info)]),
 }
@@ -306,6 +314,80 @@ def pdhg_kkt_noalloc(m, n, a_row_ptr, a_col_idx, a_val, at_row_ptr, at_col_idx, 
                                  C.c_void_p(stream) if stream else None, C.byref(info))
     _check(st, None)
     return {k: getattr(info, k) for k, _ in pdhg_kkt_info._fields_}
+
+
+def pdhg_create_batch(lps, opt: pdhg_options | None = None, stream=None):
+    """One context for many LPs; ``lps`` is a sequence of (m, n, row_ptr,
+    col_idx, val, b, c) tuples or objects with those attributes (host arrays)."""
+    keep: list = []
+    descs = (pdhg_lp_desc * len(lps))()
+    for d, lp in zip(descs, lps):
+        m, n, rp, ci, v, b, c = (lp if isinstance(lp, tuple) else
+                                 (lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c))
+        arrs = [np.ascontiguousarray(rp, np.int64), np.ascontiguousarray(ci, np.int32),
+                np.ascontiguousarray(v, np.float64), np.ascontiguousarray(b, np.float64),
+                np.ascontiguousarray(c, np.float64)]
+        keep.extend(arrs)
+        d.m, d.n, d.nnz = int(m), int(n), int(len(arrs[2]))
+        d.row_ptr, d.col_idx, d.val, d.b, d.c = [a.ctypes.data for a in arrs]
+    if opt is None:
+        opt = pdhg_default_options()
+    out = C.c_void_p()
+    _check(load().pdhg_create_batch(len(lps), descs, C.byref(opt), C.c_void_p(stream) if stream else None,
+                                    C.byref(out)), None)
+    return out.value
+
+
+def pdhg_batch_info(ctx, count):
+    it, conv = np.zeros(count, np.int64), np.zeros(count, np.int32)
+    rel, rs = np.zeros(count), np.zeros(count, np.int64)
+    _check(load().pdhg_batch_info(ctx, it.ctypes.data, conv.ctypes.data, rel.ctypes.data, rs.ctypes.data), ctx)
+    return dict(iterations=it, converged=conv.astype(bool), rel_kkt=rel, restarts=rs)
+
+
+def pdhg_batch_solution(ctx, instance, m, n):
+    x, y, z = np.empty(n), np.empty(m), np.empty(n)
+    _check(load().pdhg_batch_solution(ctx, int(instance), x.ctypes.data, y.ctypes.data, z.ctypes.data), ctx)
+    return x, y, z
+
+
+class BatchSolver:
+    """Many LPs solved together (see pdhg_create_batch in include/pdhg.h)."""
+
+    def __init__(self, lps, stream=None, **options):
+        self.sizes = [(lp.m, lp.n) if not isinstance(lp, tuple) else (lp[0], lp[1]) for lp in lps]
+        self.ctx = None
+        self.ctx = pdhg_create_batch(lps, pdhg_default_options(**options), stream)
+
+    def iterate(self, max_iters, tol=0.0):
+        return pdhg_iterate(self.ctx, max_iters, tol)
+
+    def info(self):
+        return pdhg_batch_info(self.ctx, len(self.sizes))
+
+    def solution(self, i):
+        m, n = self.sizes[i]
+        return pdhg_batch_solution(self.ctx, i, m, n)
+
+    def engine_info(self):
+        return pdhg_get_info(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            pdhg_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------------------
