@@ -88,16 +88,18 @@ constexpr int TRACE_CAP = 65536;
 //     8-byte and one 16-byte load and a warp reads contiguous 256 B / 512 B
 //     lines; when Lp == 1 the entry of row (32 q + lane) sits at
 //     uoff[u] + 32 q + lane.
-// Padding slots hold value 0 and column 0. Rows numbered >= rows in a unit
-// are padding (a batch also pads each instance to whole blocks with empty
-// units whose first row is `rows`).
+// Padding slots hold value 0 and column 0. Only the first `valid` rows of a
+// unit exist (slice row index 32 q + lane < valid); the rest are padding. In a
+// batch the rows after a slice's last valid row belong to the next instance,
+// so validity is never judged by row number. Empty units (valid = 0) pad each
+// batch instance to whole blocks.
 struct Hyb {
   int rows = 0, cols = 0;
   int n_units = 0;
   long long nnz = 0;          // stored entries (without padding)
   long long slots = 0;        // entry slots including padding
   long long* uoff = nullptr;  // [n_units + 1] entry offset of each unit
-  int2* uinfo = nullptr;      // [n_units] (first row, R); R = 0 marks a long row
+  int4* uinfo = nullptr;      // [n_units] (first row, R, valid rows, 0); R = 0 marks a long row
   int* ci = nullptr;          // [slots] column index (internal numbering)
   double* v = nullptr;        // [slots] value
   float* v32 = nullptr;       // [slots] value rounded to FP32 (FP32 / mixed precision only)

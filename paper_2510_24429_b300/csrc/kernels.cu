@@ -111,7 +111,7 @@ __device__ __forceinline__ void hyb_rows(const Hyb& H, Op& op) {
   const int gwarp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
   for (int u = gwarp; u < H.n_units; u += nwarps) {
-    const int2 info = H.uinfo[u];
+    const int4 info = H.uinfo[u];
     const long long base = H.uoff[u], end = H.uoff[u + 1];
     if (info.y == 0) {
       double acc = 0.0;
@@ -121,10 +121,11 @@ __device__ __forceinline__ void hyb_rows(const Hyb& H, Op& op) {
     } else {
       const int Lp = (int)((end - base) / (32 * info.y));
       for (int q = 0; q < info.y; ++q) {
-        const int r = info.x + 32 * q + lane;
+        const bool valid = 32 * q + lane < info.z;
+        const int r = valid ? info.x + 32 * q + lane : -1;  // -1: padding row
         double acc = 0.0;
         for (int e = 0; e < Lp; ++e) acc = op.entry(acc, slice_slot(base, Lp, info.y, q, e, lane), r);
-        if (r < H.rows) op.finish(r, acc);
+        if (valid) op.finish(r, acc);
       }
     }
   }
@@ -150,14 +151,15 @@ struct HotGather {
 // lane per step (two pairs from two contiguous halves). Slices: R rows per thread, 2 entries per load, so a thread
 // has 2R independent gathers in flight per step.
 template <int R, class T, class Op, class G>
-__device__ __forceinline__ void slice_dot(const Hyb& H, const T* __restrict__ vals, int row0, long long base, int Lp,
-                                          const G& gather, Op& op, unsigned long long pol, int lane) {
+__device__ __forceinline__ void slice_dot(const Hyb& H, const T* __restrict__ vals, int row0, int nvalid,
+                                          long long base, int Lp, const G& gather, Op& op, unsigned long long pol,
+                                          int lane) {
   typename Op::State st[R];
   T acc[R];
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     const int r = row0 + 32 * q + lane;
-    if (r < H.rows) st[q] = op.begin(r);
+    if (32 * q + lane < nvalid) st[q] = op.begin(r);
     acc[q] = T(0);
   }
   if (Lp == 1) {
@@ -186,7 +188,7 @@ __device__ __forceinline__ void slice_dot(const Hyb& H, const T* __restrict__ va
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     const int r = row0 + 32 * q + lane;
-    if (r < H.rows) op.finish(r, acc[q], st[q]);
+    if (32 * q + lane < nvalid) op.finish(r, acc[q], st[q]);
   }
 }
 
@@ -197,7 +199,7 @@ __device__ __forceinline__ void hyb_dot(const Hyb& H, const T* __restrict__ vals
   const int gwarp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
   for (int u = gwarp; u < H.n_units; u += nwarps) {
-    const int2 info = H.uinfo[u];
+    const int4 info = H.uinfo[u];
     const long long beg = H.uoff[u], end = H.uoff[u + 1];
     if (info.y == 0) {
       const int row = info.x;
@@ -230,11 +232,11 @@ __device__ __forceinline__ void hyb_dot(const Hyb& H, const T* __restrict__ vals
       const long long base = beg;
       const int Lp = (int)((end - beg) / (32 * info.y));
       if (info.y == 4)
-        slice_dot<4>(H, vals, info.x, base, Lp, gather, op, pol, lane);
+        slice_dot<4>(H, vals, info.x, info.z, base, Lp, gather, op, pol, lane);
       else if (info.y == 2)
-        slice_dot<2>(H, vals, info.x, base, Lp, gather, op, pol, lane);
+        slice_dot<2>(H, vals, info.x, info.z, base, Lp, gather, op, pol, lane);
       else
-        slice_dot<1>(H, vals, info.x, base, Lp, gather, op, pol, lane);
+        slice_dot<1>(H, vals, info.x, info.z, base, Lp, gather, op, pol, lane);
     }
   }
 }
@@ -279,7 +281,7 @@ struct ScaleOp {
   const double* __restrict__ sf;  // column factors of A (length n)
   int transposed, rows;
   __device__ __forceinline__ double entry(double acc, long long k, int r) const {
-    if (r < rows) {
+    if (r >= 0) {  // not a padding row
       const int c = ci[k];
       const double ri = transposed ? rf[c] : rf[r];
       const double sj = transposed ? sf[r] : sf[c];

@@ -332,10 +332,14 @@ struct HostHyb {
   int rows = 0, cols = 0;
   int64_t nnz = 0;
   std::vector<long long> uoff{0};  // unit offsets (n_units + 1)
-  std::vector<int> uinfo;          // pairs (first row, R); R = 0: long row
+  std::vector<int> uinfo;          // (first row, R, valid rows, 0) per unit; R = 0: long row
   std::vector<int> ci;
   std::vector<double> v;
-  int n_units() const { return (int)uinfo.size() / 2; }
+  int n_units() const { return (int)uinfo.size() / 4; }
+  void add_unit(int row0, int R, int valid, long long end) {
+    uinfo.insert(uinfo.end(), {row0, R, valid, 0});
+    uoff.push_back(end);
+  }
 };
 
 // Append the units of `nrows` rows, given as CSR (rp local, 0-based; column
@@ -363,9 +367,7 @@ void append_units(HostHyb& H, int row_base, int nrows, const std::vector<int64_t
     H.ci.resize(base + slots, 0);
     H.v.resize(base + slots, 0.0);
     for (int e = 0; e < len(r); ++e) put(base + e, rp[r] + e);
-    H.uinfo.push_back(row_base + r);
-    H.uinfo.push_back(0);
-    H.uoff.push_back(base + slots);
+    H.add_unit(row_base + r, 0, 1, base + slots);
   }
   while (r < nrows) {
     const int L = len(r);
@@ -386,9 +388,7 @@ void append_units(HostHyb& H, int row_base, int nrows, const std::vector<int64_t
           put(k, rp[rr] + e);
         }
       }
-    H.uinfo.push_back(row_base + r);
-    H.uinfo.push_back(R);
-    H.uoff.push_back(base + slots);
+    H.add_unit(row_base + r, R, std::min(32 * R, nrows - r), base + slots);
     r += 32 * R;
   }
 }
@@ -397,11 +397,7 @@ void append_units(HostHyb& H, int row_base, int nrows, const std::vector<int64_t
 // past the last row) until the layout has `target` units, so that a batch
 // instance fills whole blocks.
 void pad_units_to(HostHyb& H, int target, int empty_row) {
-  while (H.n_units() < target) {
-    H.uinfo.push_back(empty_row);
-    H.uinfo.push_back(1);
-    H.uoff.push_back(H.uoff.back());
-  }
+  while (H.n_units() < target) H.add_unit(empty_row, 1, 0, H.uoff.back());
 }
 
 pdhg_status upload_hyb(pdhg_ctx* ctx, const HostHyb& h, Hyb& d) {
@@ -411,7 +407,7 @@ pdhg_status upload_hyb(pdhg_ctx* ctx, const HostHyb& h, Hyb& d) {
   d.nnz = h.nnz;
   d.slots = (long long)h.v.size();
   CK(ctx, dalloc(ctx, &d.uoff, h.uoff.size()));
-  CK(ctx, dalloc(ctx, &d.uinfo, std::max<size_t>(1, h.uinfo.size() / 2)));
+  CK(ctx, dalloc(ctx, &d.uinfo, std::max<size_t>(1, h.uinfo.size() / 4)));
   CK(ctx, dalloc(ctx, &d.ci, h.ci.size()));
   CK(ctx, dalloc(ctx, &d.v, h.v.size()));
   cudaStream_t s = ctx->stream;
