@@ -232,6 +232,25 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# the tiny LP: latency bound, iterations/s with and without CUDA graphs
+# ---------------------------------------------------------------------------
+def run_tiny(P, torch, iters=20_000):
+    from paper_2510_24429_b300 import lpgen
+
+    lp = lpgen.tiny_lp(0)
+    out = {"workload": "tiny-lp m=200 n=500 nnz=2500 FP64, restarts, eval every 64"}
+    for g in (0, 1):
+        with P.Solver.from_lp(lp, use_graphs=g) as s:
+            s.iterate(640)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.iterate(iters)
+            torch.cuda.synchronize()
+            out["iters_per_s_graphs" if g else "iters_per_s_direct"] = iters / (time.perf_counter() - t0)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # the differentiable form: 500 unrolled iterations, FP32 forward
 # ---------------------------------------------------------------------------
 def run_adjoint(P, torch, K=500, C=50, n_dirs=20, h=1e-6):
@@ -422,6 +441,7 @@ def run_ours(args):
 
     if not args.skip_extras and rank == 0:
         extras["adjoint"] = run_adjoint(P, torch)
+        extras["tiny_lp"] = run_tiny(P, torch)
 
     cpu = None
     if not args.skip_extras and rank == 0 and world == 1:

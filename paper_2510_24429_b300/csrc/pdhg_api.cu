@@ -67,6 +67,9 @@ struct pdhg_ctx {
   std::vector<int> xoff_h, yoff_h, bstart_h;
   int *xoff = nullptr, *yoff = nullptr, *binst = nullptr, *bstart = nullptr;
   int nblocks = 0;
+  // CUDA graphs of one evaluation block, per precision phase (FP64, FP32)
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  int64_t graph_launches[2] = {0, 0};
   // recording for the adjoint: (x_k, y_k) every checkpoint_every iterations
   std::vector<void*> ck_x, ck_y;
   void *w_x = nullptr, *w_y = nullptr, *w_xbar = nullptr, *w_seg = nullptr;
@@ -653,6 +656,112 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   return PDHG_OK;
 }
 
+// ---- one evaluation block -------------------------------------------------------
+
+// The step launches of nb iterations (plus adjoint checkpoints and kernel
+// timing events when asked) and the counter update.
+pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
+  const pdhg_options& o = ctx->opt;
+  cudaStream_t s = ctx->stream;
+  const int grT = unit_grid(ctx->At), grA = unit_grid(ctx->A);
+  const int hot = (int)std::min<int64_t>(o.dual_hot_cols, ctx->n);
+  for (int64_t it = 0; it < nb; ++it) {
+    if (o.record_for_backward) {
+      pdhg_status rs = record_checkpoint(ctx, ctx->k + it);
+      if (rs != PDHG_OK) return rs;
+    }
+    if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
+    if (ctx->phase32)
+      launch_primal_step32(ctx->At, ctx->y32, ctx->ch32, ctx->x32, ctx->xbar32, ctx->xsum32, ctx->st, o.restarts,
+                           grT, s);
+    else
+      launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, grT, s);
+    if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
+    if (ctx->phase32)
+      launch_dual_step32(ctx->A, ctx->xbar32, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st, o.restarts, grA, s);
+    else if (hot > 0)
+      launch_dual_step_hot(ctx->A, ctx->xbar, hot, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, ctx->sms, s);
+    else
+      launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, grA, s);
+    if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 2], s));
+  }
+  launch_add_counters(ctx->st, nb, s);
+  ctx->launches += 2 * nb + 1;
+  CK(ctx, cudaGetLastError());
+  return PDHG_OK;
+}
+
+// One evaluation: candidate measures, decisions, their application, and the
+// copy of the state struct to pinned host memory (the host waits for it).
+pdhg_status enqueue_eval(pdhg_ctx* ctx) {
+  const pdhg_options& o = ctx->opt;
+  cudaStream_t s = ctx->stream;
+  const int n = (int)ctx->n, m = (int)ctx->m;
+  const int gv = vec_grid(ctx, std::max(n, m));
+  const bool p32 = ctx->phase32;
+  if (p32) {
+    widen_current(ctx);
+    ctx->launches += 2;
+  }
+  if (o.restarts) {
+    if (p32)
+      launch_make_average32(ctx->xsum32, ctx->ysum32, ctx->x32, ctx->y32, ctx->xavg, ctx->yavg, n, m, ctx->st, gv,
+                            s);
+    else
+      launch_make_average(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, n, m, ctx->st, gv, s);
+    eval_point(ctx, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, &ctx->st->avg);
+  }
+  eval_point(ctx, ctx->x, ctx->y, ctx->xr, ctx->yr, &ctx->st->cur);
+  launch_decide(ctx->st, ctx->trace, s);
+  if (p32)
+    launch_apply32(ctx->st, ctx->x32, ctx->y32, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, ctx->xsum32,
+                   ctx->ysum32, n, m, gv, s);
+  else
+    launch_apply(ctx->st, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, ctx->xsum, ctx->ysum, n, m, gv, s);
+  ctx->launches += (o.restarts ? 4 : 0) + 3 + 2;
+  CK(ctx, cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevState) * ctx->count, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaGetLastError());
+  return PDHG_OK;
+}
+
+pdhg_status enqueue_block(pdhg_ctx* ctx, int64_t nb);
+pdhg_status enqueue_steps_batch(pdhg_ctx* ctx, int64_t nb, bool timing);
+pdhg_status enqueue_eval_batch(pdhg_ctx* ctx);
+
+// A whole evaluation block (nb = eval_every iterations + evaluation) as a CUDA
+// graph: captured on first use for the current precision phase, replayed
+// after. Kernel arguments are fixed pointers and the step sizes, tolerance
+// and counters live in device memory, so one capture serves every block.
+pdhg_status run_block_graph(pdhg_ctx* ctx, int64_t nb) {
+  const int slot = ctx->phase32 ? 1 : 0;
+  if (!ctx->graph_exec[slot]) {
+    const int64_t launches0 = ctx->launches;
+    cudaGraph_t g = nullptr;
+    CK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    pdhg_status rs = enqueue_block(ctx, nb);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (rs != PDHG_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rs;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->graph_exec[slot], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    ctx->graph_launches[slot] = ctx->launches - launches0;
+    ctx->launches = launches0;
+  }
+  CK(ctx, cudaGraphLaunch(ctx->graph_exec[slot], ctx->stream));
+  ctx->launches += ctx->graph_launches[slot];
+  return PDHG_OK;
+}
+
+pdhg_status enqueue_block(pdhg_ctx* ctx, int64_t nb) {
+  pdhg_status rs = ctx->count > 1 ? enqueue_steps_batch(ctx, nb, false) : enqueue_steps(ctx, nb, false);
+  if (rs != PDHG_OK) return rs;
+  return ctx->count > 1 ? enqueue_eval_batch(ctx) : enqueue_eval(ctx);
+}
+
 // ---- batch -------------------------------------------------------------------
 
 pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
@@ -881,31 +990,55 @@ void eval_batch(pdhg_ctx* ctx) {
                  ctx->yoff, count, gx, s);
 }
 
+pdhg_status enqueue_steps_batch(pdhg_ctx* ctx, int64_t nb, bool timing) {
+  const pdhg_options& o = ctx->opt;
+  cudaStream_t s = ctx->stream;
+  for (int64_t it = 0; it < nb; ++it) {
+    if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
+    launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, ctx->nblocks, s,
+                       ctx->binst);
+    if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
+    launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, ctx->nblocks, s,
+                     ctx->binst);
+    if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 2], s));
+  }
+  launch_add_counters_b(ctx->st, ctx->count, nb, s);
+  ctx->launches += 2 * nb + 1;
+  CK(ctx, cudaGetLastError());
+  return PDHG_OK;
+}
+
+pdhg_status enqueue_eval_batch(pdhg_ctx* ctx) {
+  eval_batch(ctx);
+  ctx->launches += (ctx->opt.restarts ? 4 : 0) + 3 + 2;
+  CK(ctx, cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevState) * ctx->count, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaGetLastError());
+  return PDHG_OK;
+}
+
 pdhg_status iterate_batch(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done) {
   const pdhg_options& o = ctx->opt;
   cudaStream_t s = ctx->stream;
   const int count = ctx->count;
-  for (int i = 0; i < count; ++i) ctx->h_st[i].tol = tol;
   // tolerance of every instance (the rest of the state stays on the device)
+  for (int i = 0; i < count; ++i) ctx->h_st[i].tol = tol;
   for (int i = 0; i < count; ++i)
     CK(ctx, cudaMemcpyAsync(&ctx->st[i].tol, &ctx->h_st[i].tol, sizeof(double), cudaMemcpyHostToDevice, s));
+  const bool graphs = o.use_graphs && !o.kernel_timing;
   int64_t done = 0;
   bool all_done = false;
   while (done < max_iters && !all_done) {
     const int64_t nb = std::min<int64_t>(o.eval_every - (ctx->k % o.eval_every), max_iters - done);
     const bool timing = o.kernel_timing && nb <= EV_POOL;
-    for (int64_t it = 0; it < nb; ++it) {
-      if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
-      launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, ctx->nblocks,
-                         s, ctx->binst);
-      if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
-      launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, ctx->nblocks, s,
-                       ctx->binst);
-      if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 2], s));
+    const bool eval_now = (ctx->k + nb) % o.eval_every == 0;
+    pdhg_status rs;
+    if (graphs && eval_now && nb == o.eval_every) {
+      rs = run_block_graph(ctx, nb);
+    } else {
+      rs = enqueue_steps_batch(ctx, nb, timing);
+      if (rs == PDHG_OK && eval_now) rs = enqueue_eval_batch(ctx);
     }
-    launch_add_counters_b(ctx->st, count, nb, s);
-    ctx->launches += 2 * nb + 1;
-    CK(ctx, cudaGetLastError());
+    if (rs != PDHG_OK) return rs;
     ctx->k += nb;
     done += nb;
     if (timing) {
@@ -920,11 +1053,7 @@ pdhg_status iterate_batch(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t*
       ctx->launches_primal += nb;
       ctx->launches_dual += nb;
     }
-    if (ctx->k % o.eval_every == 0) {
-      eval_batch(ctx);
-      ctx->launches += (o.restarts ? 4 : 0) + 3 + 2;
-      CK(ctx, cudaGetLastError());
-      CK(ctx, cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevState) * count, cudaMemcpyDeviceToHost, s));
+    if (eval_now) {
       CK(ctx, cudaStreamSynchronize(s));
       all_done = true;
       for (int i = 0; i < count; ++i) {
@@ -1087,6 +1216,8 @@ void pdhg_destroy(pdhg_ctx* ctx) {
   }
   for (int i = 0; i < 3 * EV_POOL; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  for (int g = 0; g < 2; ++g)
+    if (ctx->graph_exec[g]) cudaGraphExecDestroy(ctx->graph_exec[g]);
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
   if (ctx->h_kkt) cudaFreeHost(ctx->h_kkt);
   if (ctx->side) cudaStreamDestroy(ctx->side);
@@ -1106,9 +1237,7 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
   const int n = (int)ctx->n, m = (int)ctx->m;
   cudaStream_t s = ctx->stream;
   CK(ctx, cudaMemcpyAsync(&ctx->st->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
-  const int grT = unit_grid(ctx->At), grA = unit_grid(ctx->A);
-  const int hot = (int)std::min<int64_t>(o.dual_hot_cols, ctx->n);
-  const int gv = vec_grid(ctx, std::max(n, m));
+  const bool graphs = o.use_graphs && evaluating && !o.kernel_timing && !o.record_for_backward;
   ctx->converged = false;
   int64_t done = 0;
   while (done < max_iters) {
@@ -1118,29 +1247,14 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
     else
       nb = std::min<int64_t>(max_iters - done, o.kernel_timing ? EV_POOL : (1 << 20));
     const bool timing = o.kernel_timing && nb <= EV_POOL;
-    for (int64_t it = 0; it < nb; ++it) {
-      if (o.record_for_backward) {
-        rs = record_checkpoint(ctx, ctx->k + it);
-        if (rs != PDHG_OK) return rs;
-      }
-      if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
-      if (ctx->phase32)
-        launch_primal_step32(ctx->At, ctx->y32, ctx->ch32, ctx->x32, ctx->xbar32, ctx->xsum32, ctx->st, o.restarts,
-                             grT, s);
-      else
-        launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, grT, s);
-      if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
-      if (ctx->phase32)
-        launch_dual_step32(ctx->A, ctx->xbar32, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st, o.restarts, grA, s);
-      else if (hot > 0)
-        launch_dual_step_hot(ctx->A, ctx->xbar, hot, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, ctx->sms, s);
-      else
-        launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, grA, s);
-      if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 2], s));
+    const bool eval_now = evaluating && (ctx->k + nb) % o.eval_every == 0;
+    if (graphs && eval_now && nb == o.eval_every) {
+      rs = run_block_graph(ctx, nb);
+    } else {
+      rs = enqueue_steps(ctx, nb, timing);
+      if (rs == PDHG_OK && eval_now) rs = enqueue_eval(ctx);
     }
-    launch_add_counters(ctx->st, nb, s);
-    ctx->launches += 2 * nb + 1;
-    CK(ctx, cudaGetLastError());
+    if (rs != PDHG_OK) return rs;
     ctx->k += nb;
     done += nb;
     if (timing) {
@@ -1155,32 +1269,8 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
       ctx->launches_primal += nb;
       ctx->launches_dual += nb;
     }
-    if (evaluating && ctx->k % o.eval_every == 0) {
-      const bool p32 = ctx->phase32;
-      if (p32) {
-        widen_current(ctx);
-        ctx->launches += 2;
-      }
-      if (o.restarts) {
-        if (p32)
-          launch_make_average32(ctx->xsum32, ctx->ysum32, ctx->x32, ctx->y32, ctx->xavg, ctx->yavg, n, m, ctx->st,
-                                gv, s);
-        else
-          launch_make_average(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, n, m, ctx->st, gv, s);
-        eval_point(ctx, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, &ctx->st->avg);
-      }
-      eval_point(ctx, ctx->x, ctx->y, ctx->xr, ctx->yr, &ctx->st->cur);
-      launch_decide(ctx->st, ctx->trace, s);
-      if (p32)
-        launch_apply32(ctx->st, ctx->x32, ctx->y32, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr,
-                       ctx->xsum32, ctx->ysum32, n, m, gv, s);
-      else
-        launch_apply(ctx->st, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, ctx->xsum, ctx->ysum, n, m,
-                     gv, s);
-      ctx->launches += (o.restarts ? 4 : 0) + 3 + 2;
-      CK(ctx, cudaGetLastError());
-      rs = read_state(ctx);
-      if (rs != PDHG_OK) return rs;
+    if (eval_now) {
+      CK(ctx, cudaStreamSynchronize(s));  // the state copy of the evaluation has landed
       if (ctx->h_st->numeric) {
         if (iters_done) *iters_done = done;
         return fail(ctx, PDHG_ERR_NUMERIC, "NaN or Inf in the iterates");
