@@ -232,6 +232,39 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# batched: 256 LPs of uneven sizes solved together to 1e-6
+# ---------------------------------------------------------------------------
+def run_batch(P, torch, count=256, tol=1e-6, seed=0):
+    import numpy as np
+
+    from paper_2510_24429_b300 import lpgen
+
+    sizes = lpgen.batch_sizes(seed, count)
+    lps = [lpgen.batch_lp(seed, i, m) for i, m in enumerate(sizes)]
+    t0 = time.perf_counter()
+    bs = P.BatchSolver(lps)
+    setup_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, done = bs.iterate(200_000, tol)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    info = bs.info()
+    eng = bs.engine_info()
+    bs.close()
+    it = info["iterations"].astype(np.float64)
+    per_iter_bytes = np.array([24.0 * lp.nnz + 56.0 * lp.n + 48.0 * lp.m for lp in lps])
+    peak, _ = measured_peaks()
+    gbs = float((it * per_iter_bytes).sum() / sec / 1e9)
+    return {"workload": f"{count} LPs, m log-uniform in [1e3, 1e5] (sum {sum(sizes)}), n = 2.5 m, 5 per column, "
+                        f"nnz {sum(lp.nnz for lp in lps)}, FP64, each to rel. KKT {tol:g}",
+            "seconds_to_all_converged": sec, "setup_s": setup_s, "all_converged": bool(info["converged"].all()),
+            "iterations_max": int(it.max()), "iterations_median": float(np.median(it)),
+            "aggregate_iters_per_s": float(it.sum() / sec), "hbm_gbs_active": gbs, "hbm_frac_active": gbs / peak,
+            "gpu_launches": eng["kernel_launches"]}
+
+
+# ---------------------------------------------------------------------------
 # the tiny LP: latency bound, iterations/s with and without CUDA graphs
 # ---------------------------------------------------------------------------
 def run_tiny(P, torch, iters=20_000):
@@ -442,6 +475,7 @@ def run_ours(args):
     if not args.skip_extras and rank == 0:
         extras["adjoint"] = run_adjoint(P, torch)
         extras["tiny_lp"] = run_tiny(P, torch)
+        extras["batch"] = run_batch(P, torch)
 
     cpu = None
     if not args.skip_extras and rank == 0 and world == 1:
