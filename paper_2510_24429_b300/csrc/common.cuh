@@ -109,6 +109,13 @@ struct Hyb {
 // ---------------------------------------------------------------------------
 // device helpers
 // ---------------------------------------------------------------------------
+// slot of entry e of row (32 q + lane) in a slice of 32 R rows padded to Lp
+// entries per row: pairs of entries are interleaved across the slice's
+// threads, so a thread reads entries 2p and 2p+1 of its row with one load
+__device__ __forceinline__ long long slice_slot(long long base, int Lp, int R, int q, int e, int lane) {
+  return Lp == 1 ? base + 32 * q + lane : base + ((long long)(e >> 1) * R + q) * 64 + 2 * lane + (e & 1);
+}
+
 template <int W>
 __device__ __forceinline__ double group_sum(double v) {
 #pragma unroll

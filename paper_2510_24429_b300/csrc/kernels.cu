@@ -96,11 +96,6 @@ __device__ __forceinline__ int4 ld_stream4(const int* p, unsigned long long pol)
   return r;
 }
 
-// slot of entry e of row (32 q + lane) in a slice (see Hyb)
-__device__ __forceinline__ long long slice_slot(long long base, int Lp, int R, int q, int e, int lane) {
-  return Lp == 1 ? base + 32 * q + lane : base + ((long long)(e >> 1) * R + q) * 64 + 2 * lane + (e & 1);
-}
-
 // Scalar visitor (setup kernels): every warp takes units in a grid-stride
 // loop; op.entry(acc, k, r) sees every slot k of row r (padding included:
 // value 0, column 0), op.finish(r, acc) the combined result (max or sum).

@@ -111,6 +111,46 @@ void launch_pack_solution(const Hyb& At, const int* perm_x, const int* perm_y, c
                           const double* ch, const double* dc, const double* dr, double* ox, double* oy, double* oz,
                           int grid, cudaStream_t s);
 
+// ---- layout construction (layout.cu) ----------------------------------------
+// error bits of the device-side CSR validation
+enum { LAYOUT_BAD_ROW_PTR = 1, LAYOUT_BAD_COLUMN = 2, LAYOUT_UNSORTED = 4, LAYOUT_NOT_FINITE = 8 };
+void launch_validate_csr(long long m, long long n, long long nnz, const long long* rp, const int* ci,
+                         const double* v, int* flags, cudaStream_t s);
+void launch_check_finite(const double* v, long long len, int* flags, cudaStream_t s);
+// out[i] = instance of element i given the count + 1 offsets off
+void launch_instance_of(const int* off, int count, long long len, int* out, cudaStream_t s);
+// block-diagonal global CSR (grp [M+1], gci [Z]) and the global row of every
+// entry from the instances' local arrays (instance i: rows from lrp + rpoff[i],
+// entries from zoff[i], columns shifted by xoff[i]); rinst null for one LP
+void launch_globalize(const long long* lrp, const int* lci, const long long* rpoff, const long long* zoff,
+                      const int* xoff, const int* yoff, const int* rinst, long long M, long long Z, long long* grp,
+                      int* gci, int* rowid, cudaStream_t s);
+// row lengths of A (lenA), of A^T (lenT), and their maxima (maxes[0], maxes[1])
+void launch_lengths(const long long* grp, long long M, const int* gci, long long Z, long long N, int* lenA,
+                    int* lenT, unsigned* maxes, cudaStream_t s);
+void launch_length_keys(const int* len, long long cnt, const int* inst, int maxlen, int lbits,
+                        unsigned long long* keys, int* vals, cudaStream_t s);
+void launch_transpose_keys(const int* gci, long long Z, const int* ix, unsigned* keys, int* vals, cudaStream_t s);
+void launch_invert(const int* p, long long len, int* inv, cudaStream_t s);
+void launch_gather_int(const int* src, const int* p, long long len, int* out, cudaStream_t s);
+void launch_gather_double(const double* src, const int* p, long long len, double* out, cudaStream_t s);
+// workspace lengths (long long elements) of the radix sort's histogram and of the scan
+long long radix_hist_len(long long N);
+long long scan_ws_len(long long len);
+// Stable ascending sort of N (key, value) pairs on the low `bits` bits of the
+// keys; returns 0 if the result is in (keys, vals), 1 if in (keys_alt, vals_alt).
+// hist: radix_hist_len(N) elements; ws: scan_ws_len(radix_hist_len(N)).
+template <class K>
+int radix_sort_pairs(K* keys, int* vals, K* keys_alt, int* vals_alt, long long N, int bits, long long* hist,
+                     long long* ws, cudaStream_t s);
+// out[0..len] = exclusive prefix sums of in[0..len) (out[len] = total); ws: scan_ws_len(len)
+void launch_scan_int(const int* in, long long len, long long* out, long long* ws, cudaStream_t s);
+// write the entries of every unit of H (unit tables, ci and v allocated; ci, v zeroed)
+void launch_fill_units_A(const Hyb& H, const int* slen, const long long* grp, const int* py, const int* gci,
+                         const int* ix, const double* v, cudaStream_t s);
+void launch_fill_units_T(const Hyb& H, const int* slen, const long long* tp, const int* sval, const int* rowid,
+                         const int* iy, const double* v, cudaStream_t s);
+
 // the step kernels use no shared memory: prefer the largest L1
 void prefer_l1_for_step_kernels();
 

@@ -1,12 +1,12 @@
 // Host engine behind the C ABI of include/pdhg.h.
 //
-// One context = one LP resident on one GPU. Setup validates the CSR on the
-// host, renumbers rows and columns by decreasing length, builds the two
-// device layouts of the matrix (A and its transpose, each as long rows plus
-// 32-row column-major slices; see Hyb), uploads them, and does everything
-// else on the device: Ruiz and Pock-Chambolle scaling, the
-// power iteration for ||Ahat||_2, the primal weight, and the evaluation of the
-// starting point. The solve loop launches the two fused half-steps per
+// One context = one LP (or one batch of LPs) resident on one GPU. Setup
+// validates the CSR (host inputs on the host, device inputs on the device),
+// copies it to the device, and does everything else there: the renumbering of
+// rows and columns by decreasing length, the transpose, the packing into the
+// two matrix layouts (A and its transpose as long rows plus slices; see Hyb
+// and layout.cu), Ruiz and Pock-Chambolle scaling, the power iteration for
+// ||Ahat||_2, the primal weight, and the evaluation of the starting point. The solve loop launches the two fused half-steps per
 // iteration and, every eval_every iterations, the evaluation kernels and the
 // single-thread decision kernel; the host reads back one small status struct
 // per evaluation (Section 3.1: one CPU thread launches the GPU kernels and
@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -155,13 +156,41 @@ pdhg_status set_device(pdhg_ctx* ctx) {
   return PDHG_OK;
 }
 
-bool all_finite(const double* v, int64_t len) {
-  for (int64_t i = 0; i < len; ++i)
-    if (!std::isfinite(v[i])) return false;
-  return true;
+// Runs fn(t) for t in [0, T) on T host threads (the calling thread included).
+template <class F>
+void parallel_for(int T, F fn) {
+  std::vector<std::thread> th;
+  th.reserve(T > 1 ? T - 1 : 0);
+  for (int t = 1; t < T; ++t) th.emplace_back(fn, t);
+  fn(0);
+  for (auto& x : th) x.join();
 }
 
-// Host checks of one LP (before any device work).
+// host threads for a pass over `work` elements
+int host_threads(int64_t work) {
+  if (work < (1 << 20)) return 1;
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  return (int)std::min<int64_t>({(int64_t)hw, 16, work >> 19});
+}
+
+bool all_finite(const double* v, int64_t len) {
+  const int T = host_threads(len);
+  std::vector<char> ok(T, 1);
+  parallel_for(T, [&](int t) {
+    const int64_t a = len * t / T, b = len * (t + 1) / T;
+    for (int64_t i = a; i < b; ++i)
+      if (!std::isfinite(v[i])) {
+        ok[t] = 0;
+        return;
+      }
+  });
+  return std::all_of(ok.begin(), ok.end(), [](char c) { return c != 0; });
+}
+
+// Host checks of one LP (before any device work). The row pointers are
+// checked first, so that every row's entries lie in [0, nnz) when the entries
+// are checked (in parallel over row ranges; the first failing row decides the
+// message).
 pdhg_status validate_lp(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
                         const double* val, const double* b, const double* c) {
   if (m < 1 || n < 1 || m >= (1LL << 31) - 1 || n >= (1LL << 31) - 1)
@@ -171,13 +200,29 @@ pdhg_status validate_lp(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     return fail(nullptr, PDHG_ERR_INVALID, "NULL array argument");
   if (row_ptr[0] != 0 || row_ptr[m] != nnz)
     return fail(nullptr, PDHG_ERR_INVALID, "row_ptr[0] != 0 or row_ptr[m] != nnz");
-  for (int64_t i = 0; i < m; ++i) {
+  for (int64_t i = 0; i < m; ++i)
     if (row_ptr[i + 1] < row_ptr[i]) return fail(nullptr, PDHG_ERR_INVALID, "row_ptr not non-decreasing");
-    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-      if (col_idx[k] < 0 || col_idx[k] >= n) return fail(nullptr, PDHG_ERR_INVALID, "column index out of range");
-      if (k > row_ptr[i] && col_idx[k] <= col_idx[k - 1])
-        return fail(nullptr, PDHG_ERR_INVALID, "column indices not strictly increasing within a row");
-    }
+  const int T = host_threads(nnz);
+  std::vector<int> bad_kind(T, 0);
+  parallel_for(T, [&](int t) {
+    const int64_t r0 = m * t / T, r1 = m * (t + 1) / T;
+    for (int64_t i = r0; i < r1; ++i)
+      for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+        int kind = 0;
+        if (col_idx[k] < 0 || col_idx[k] >= n)
+          kind = 1;
+        else if (k > row_ptr[i] && col_idx[k] <= col_idx[k - 1])
+          kind = 2;
+        if (kind) {
+          bad_kind[t] = kind;
+          return;
+        }
+      }
+  });
+  for (int t = 0; t < T; ++t) {
+    if (bad_kind[t] == 1) return fail(nullptr, PDHG_ERR_INVALID, "column index out of range");
+    if (bad_kind[t] == 2)
+      return fail(nullptr, PDHG_ERR_INVALID, "column indices not strictly increasing within a row");
   }
   if (!all_finite(val, nnz) || !all_finite(b, m) || !all_finite(c, n))
     return fail(nullptr, PDHG_ERR_NUMERIC, "NaN or Inf in the input data");
@@ -317,111 +362,235 @@ pdhg_status take_snapshot(pdhg_ctx* ctx) {
   return PDHG_OK;
 }
 
-// ---- host-side layout construction ---------------------------------------
+// ---- layout construction ---------------------------------------------------
 
-// Rows in order of decreasing length; rows of equal length keep their order.
-std::vector<int> order_by_length(const std::vector<int>& len) {
-  int mx = 0;
-  for (int l : len) mx = std::max(mx, l);
-  std::vector<int64_t> start(mx + 2, 0);
-  for (int l : len) start[mx - l + 1] += 1;
-  for (int b = 0; b <= mx; ++b) start[b + 1] += start[b];
-  std::vector<int> order(len.size());
-  for (size_t i = 0; i < len.size(); ++i) order[start[mx - len[i]]++] = (int)i;
-  return order;
-}
-
-struct HostHyb {
-  int rows = 0, cols = 0;
-  int64_t nnz = 0;
-  std::vector<long long> uoff{0};  // unit offsets (n_units + 1)
-  std::vector<int> uinfo;          // (first row, R, valid rows, 0) per unit; R = 0: long row
-  std::vector<int> ci;
-  std::vector<double> v;
-  int n_units() const { return (int)uinfo.size() / 4; }
-  void add_unit(int row0, int R, int valid, long long end) {
-    uinfo.insert(uinfo.end(), {row0, R, valid, 0});
-    uoff.push_back(end);
+// Device memory owned by one setup call, released (after the stream is idle)
+// when the call returns.
+struct Scratch {
+  cudaStream_t s = nullptr;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  ~Scratch() {
+    if (s) cudaStreamSynchronize(s);
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  cudaError_t take(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(1, count) * sizeof(T));
+    if (e == cudaSuccess) {
+      ptrs.push_back(q);
+      *p = static_cast<T*>(q);
+    }
+    return e;
   }
 };
 
-// Append the units of `nrows` rows, given as CSR (rp local, 0-based; column
-// indices already in the final numbering) with rows sorted by decreasing
-// length, numbered from row_base. Long rows (>= long_min entries) become
-// 4-aligned, 4-padded warp units; the rest slices of 32*R rows, R = 4 for rows
-// of length <= 1, 2 for length <= 8, else 1 (capped by max_rpt), with the
-// slice length rounded up to even when above 1 and entries stored in pairs.
-void append_units(HostHyb& H, int row_base, int nrows, const std::vector<int64_t>& rp, const std::vector<int>& ci,
-                  const std::vector<double>& v, int long_min, int max_rpt) {
-  auto len = [&](int r) { return (int)(rp[r + 1] - rp[r]); };
-  auto put = [&](long long k, int64_t src) {
-    if ((long long)H.ci.size() <= k) {
-      H.ci.resize(k + 1, 0);
-      H.v.resize(k + 1, 0.0);
-    }
-    H.ci[k] = ci[src];
-    H.v[k] = v[src];
-  };
-  H.nnz += rp[nrows];
-  int r = 0;
-  for (; r < nrows && len(r) >= long_min; ++r) {
-    const long long base = H.uoff.back();
-    const long long slots = ((len(r) + 3) / 4) * 4;
-    H.ci.resize(base + slots, 0);
-    H.v.resize(base + slots, 0.0);
-    for (int e = 0; e < len(r); ++e) put(base + e, rp[r] + e);
-    H.add_unit(row_base + r, 0, 1, base + slots);
+// Unit table of one layout (see Hyb), built on the host from the sorted row
+// lengths; the entries are packed on the device.
+struct HostUnits {
+  int64_t nnz = 0;
+  std::vector<long long> uoff{0};  // unit offsets (n_units + 1)
+  std::vector<int> uinfo;          // (first row, R, valid rows, 0) per unit; R = 0: long row
+  int n_units() const { return (int)uinfo.size() / 4; }
+  void add(int row0, int R, int valid, long long slots) {
+    uinfo.insert(uinfo.end(), {row0, R, valid, 0});
+    uoff.push_back(uoff.back() + slots);
   }
+};
+
+// Units of `nrows` rows numbered from row_base whose lengths slen are sorted
+// in decreasing order. Rows with >= long_min entries become 4-aligned,
+// 4-padded warp units; the rest slices of 32*R rows, R = 4 for rows of length
+// <= 1, 2 for length <= 8, else 1 (capped by max_rpt), padded to the slice's
+// first (longest) row, rounded up to even when above 1 (entries in pairs).
+void append_unit_table(HostUnits& H, int row_base, int nrows, const int* slen, int long_min, int max_rpt) {
+  for (int r = 0; r < nrows; ++r) H.nnz += slen[r];
+  int r = 0;
+  for (; r < nrows && slen[r] >= long_min; ++r) H.add(row_base + r, 0, 1, ((slen[r] + 3LL) / 4) * 4);
   while (r < nrows) {
-    const int L = len(r);
+    const int L = slen[r];
     int R = L <= 1 ? 4 : (L <= 8 ? 2 : 1);
     R = std::max(1, std::min(R, max_rpt));
     const int Lp = L <= 1 ? L : (L + 1) / 2 * 2;
-    const long long base = H.uoff.back();
-    const long long slots = 32LL * R * Lp;
-    H.ci.resize(base + slots, 0);
-    H.v.resize(base + slots, 0.0);
-    for (int q = 0; q < R; ++q)
-      for (int lane = 0; lane < 32; ++lane) {
-        const int rr = r + 32 * q + lane;
-        if (rr >= nrows) continue;
-        for (int e = 0; e < len(rr); ++e) {
-          const long long k =
-              Lp == 1 ? base + 32 * q + lane : base + ((long long)(e / 2) * R + q) * 64 + 2 * lane + (e % 2);
-          put(k, rp[rr] + e);
-        }
-      }
-    H.add_unit(row_base + r, R, std::min(32 * R, nrows - r), base + slots);
+    H.add(row_base + r, R, std::min(32 * R, nrows - r), 32LL * R * Lp);
     r += 32 * R;
   }
 }
 
 // Append empty units (no entries; rows numbered from `empty_row`, which is
-// past the last row) until the layout has `target` units, so that a batch
+// past the last row) until the table has `target` units, so that a batch
 // instance fills whole blocks.
-void pad_units_to(HostHyb& H, int target, int empty_row) {
-  while (H.n_units() < target) H.add_unit(empty_row, 1, 0, H.uoff.back());
+void pad_units_to(HostUnits& H, int target, int empty_row) {
+  while (H.n_units() < target) H.add(empty_row, 1, 0, 0);
 }
 
-pdhg_status upload_hyb(pdhg_ctx* ctx, const HostHyb& h, Hyb& d) {
-  d.rows = h.rows;
-  d.cols = h.cols;
+pdhg_status upload_units(pdhg_ctx* ctx, const HostUnits& h, int rows, int cols, Hyb& d) {
+  d.rows = rows;
+  d.cols = cols;
   d.n_units = h.n_units();
   d.nnz = h.nnz;
-  d.slots = (long long)h.v.size();
+  d.slots = h.uoff.back();
   CK(ctx, dalloc(ctx, &d.uoff, h.uoff.size()));
   CK(ctx, dalloc(ctx, &d.uinfo, std::max<size_t>(1, h.uinfo.size() / 4)));
-  CK(ctx, dalloc(ctx, &d.ci, h.ci.size()));
-  CK(ctx, dalloc(ctx, &d.v, h.v.size()));
+  CK(ctx, dalloc(ctx, &d.ci, std::max<long long>(1, d.slots)));
+  CK(ctx, dalloc(ctx, &d.v, std::max<long long>(1, d.slots)));
   cudaStream_t s = ctx->stream;
   CK(ctx, cudaMemcpyAsync(d.uoff, h.uoff.data(), sizeof(long long) * h.uoff.size(), cudaMemcpyHostToDevice, s));
   if (!h.uinfo.empty())
     CK(ctx, cudaMemcpyAsync(d.uinfo, h.uinfo.data(), sizeof(int) * h.uinfo.size(), cudaMemcpyHostToDevice, s));
-  if (!h.ci.empty()) {
-    CK(ctx, cudaMemcpyAsync(d.ci, h.ci.data(), sizeof(int) * h.ci.size(), cudaMemcpyHostToDevice, s));
-    CK(ctx, cudaMemcpyAsync(d.v, h.v.data(), sizeof(double) * h.v.size(), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemsetAsync(d.ci, 0, sizeof(int) * std::max<long long>(1, d.slots), s));
+  CK(ctx, cudaMemsetAsync(d.v, 0, sizeof(double) * std::max<long long>(1, d.slots), s));
+  return PDHG_OK;
+}
+
+// bits needed to hold the values 0..v
+int bit_length(unsigned long long v) {
+  int b = 0;
+  while (v) {
+    ++b;
+    v >>= 1;
   }
-  // the host vectors are freed when setup returns: wait for the copies
+  return b;
+}
+
+// Builds ctx->A, ctx->At, ctx->perm_x, ctx->perm_y (and for a batch ctx->binst,
+// ctx->bstart, ctx->nblocks) on the device from the instances' CSRs in device
+// memory: instance i's m_i + 1 row pointers start at lrp + rpoff_h[i], its
+// column indices and values at lci + zoff_h[i], val + zoff_h[i]; its rows and
+// columns are ctx->yoff_h[i].. and ctx->xoff_h[i].. of the stacked problem.
+// Internal numbering: every instance's rows (and columns) by decreasing
+// length, stable, each instance keeping its own range.
+pdhg_status build_layouts(pdhg_ctx* ctx, Scratch& sc, const long long* lrp, const int* lci, const double* val,
+                          const std::vector<long long>& rpoff_h, const std::vector<long long>& zoff_h) {
+  const pdhg_options& o = ctx->opt;
+  const int count = ctx->count;
+  const bool batch = count > 1;
+  const long long M = ctx->m, N = ctx->n, Z = ctx->nnz;
+  cudaStream_t s = ctx->stream;
+
+  long long *d_rpoff = nullptr, *d_zoff = nullptr;
+  int *d_xoff = nullptr, *d_yoff = nullptr;
+  CK(ctx, sc.take(&d_rpoff, count));
+  CK(ctx, sc.take(&d_zoff, count + 1));
+  CK(ctx, sc.take(&d_xoff, count + 1));
+  CK(ctx, sc.take(&d_yoff, count + 1));
+  CK(ctx, cudaMemcpyAsync(d_rpoff, rpoff_h.data(), sizeof(long long) * count, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(d_zoff, zoff_h.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(d_xoff, ctx->xoff_h.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(d_yoff, ctx->yoff_h.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, s));
+  int *rinst = nullptr, *cinst = nullptr;
+  if (batch) {
+    CK(ctx, sc.take(&rinst, M));
+    CK(ctx, sc.take(&cinst, N));
+    launch_instance_of(d_yoff, count, M, rinst, s);
+    launch_instance_of(d_xoff, count, N, cinst, s);
+  }
+
+  // stacked CSR, row lengths of A and A^T
+  long long* grp = nullptr;
+  int *gci = nullptr, *rowid = nullptr, *lenA = nullptr, *lenT = nullptr;
+  unsigned* maxes = nullptr;
+  CK(ctx, sc.take(&grp, M + 1));
+  CK(ctx, sc.take(&gci, Z));
+  CK(ctx, sc.take(&rowid, Z));
+  CK(ctx, sc.take(&lenA, M));
+  CK(ctx, sc.take(&lenT, N));
+  CK(ctx, sc.take(&maxes, 2));
+  launch_globalize(lrp, lci, d_rpoff, d_zoff, d_xoff, d_yoff, rinst, M, Z, grp, gci, rowid, s);
+  launch_lengths(grp, M, gci, Z, N, lenA, lenT, maxes, s);
+  unsigned h_max[2] = {0, 0};
+  CK(ctx, cudaMemcpyAsync(h_max, maxes, sizeof(h_max), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+
+  // renumbering: stable sort by (instance, decreasing length)
+  const long long MN = std::max(M, N);
+  const long long hist_len = radix_hist_len(std::max(MN, Z));
+  unsigned long long *k64a = nullptr, *k64b = nullptr;
+  int *va = nullptr, *vb = nullptr;
+  long long *hist = nullptr, *ws = nullptr;
+  CK(ctx, sc.take(&k64a, MN));
+  CK(ctx, sc.take(&k64b, MN));
+  CK(ctx, sc.take(&va, MN));
+  CK(ctx, sc.take(&vb, MN));
+  CK(ctx, sc.take(&hist, hist_len));
+  CK(ctx, sc.take(&ws, scan_ws_len(std::max(hist_len, N))));
+  CK(ctx, dalloc(ctx, &ctx->perm_y, M));
+  CK(ctx, dalloc(ctx, &ctx->perm_x, N));
+  const int ibits = batch ? bit_length((unsigned long long)(count - 1)) : 0;
+  const int* lens[2] = {lenA, lenT};
+  const int* insts[2] = {rinst, cinst};
+  const long long cnts[2] = {M, N};
+  int* perms[2] = {ctx->perm_y, ctx->perm_x};
+  for (int side = 0; side < 2; ++side) {
+    const int lbits = bit_length(h_max[side]);
+    launch_length_keys(lens[side], cnts[side], insts[side], (int)h_max[side], lbits, k64a, va, s);
+    const int alt = radix_sort_pairs<unsigned long long>(k64a, va, k64b, vb, cnts[side], lbits + ibits, hist, ws, s);
+    CK(ctx, cudaMemcpyAsync(perms[side], alt ? vb : va, sizeof(int) * cnts[side], cudaMemcpyDeviceToDevice, s));
+  }
+  int *iy = nullptr, *ix = nullptr, *slA = nullptr, *slT = nullptr;
+  CK(ctx, sc.take(&iy, M));
+  CK(ctx, sc.take(&ix, N));
+  CK(ctx, sc.take(&slA, M));
+  CK(ctx, sc.take(&slT, N));
+  launch_invert(ctx->perm_y, M, iy, s);
+  launch_invert(ctx->perm_x, N, ix, s);
+  launch_gather_int(lenA, ctx->perm_y, M, slA, s);
+  launch_gather_int(lenT, ctx->perm_x, N, slT, s);
+
+  // transpose: entries by internal column, in the caller's row order within one
+  unsigned *k32a = nullptr, *k32b = nullptr;
+  int *za = nullptr, *zb = nullptr;
+  long long* tp = nullptr;
+  CK(ctx, sc.take(&k32a, Z));
+  CK(ctx, sc.take(&k32b, Z));
+  CK(ctx, sc.take(&za, Z));
+  CK(ctx, sc.take(&zb, Z));
+  CK(ctx, sc.take(&tp, N + 1));
+  launch_transpose_keys(gci, Z, ix, k32a, za, s);
+  const int alt = radix_sort_pairs<unsigned>(k32a, za, k32b, zb, Z, bit_length((unsigned long long)(N - 1)), hist,
+                                             ws, s);
+  const int* sval = alt ? zb : za;
+  launch_scan_int(slT, N, tp, ws, s);
+
+  // unit tables from the sorted lengths
+  std::vector<int> hA(M), hT(N);
+  CK(ctx, cudaMemcpyAsync(hA.data(), slA, sizeof(int) * M, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaMemcpyAsync(hT.data(), slT, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  HostUnits uA, uT;
+  std::vector<int> binst;
+  ctx->bstart_h.assign(count + 1, 0);
+  for (int inst = 0; inst < count; ++inst) {
+    const int y0 = ctx->yoff_h[inst], x0 = ctx->xoff_h[inst];
+    const int before = uA.n_units();
+    append_unit_table(uA, y0, ctx->yoff_h[inst + 1] - y0, hA.data() + y0, o.long_row_min, o.rows_per_thread);
+    append_unit_table(uT, x0, ctx->xoff_h[inst + 1] - x0, hT.data() + x0, o.long_row_min, o.rows_per_thread);
+    if (batch) {
+      // both layouts get the same whole number of blocks for this instance
+      const int units = std::max(uA.n_units(), uT.n_units()) - before;
+      const int blocks = (units + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+      pad_units_to(uA, before + blocks * WARPS_PER_BLOCK, (int)M);
+      pad_units_to(uT, before + blocks * WARPS_PER_BLOCK, (int)N);
+      ctx->bstart_h[inst + 1] = ctx->bstart_h[inst] + blocks;
+      for (int b = 0; b < blocks; ++b) binst.push_back(inst);
+    }
+  }
+  pdhg_status rs = upload_units(ctx, uA, (int)M, (int)N, ctx->A);
+  if (rs != PDHG_OK) return rs;
+  rs = upload_units(ctx, uT, (int)N, (int)M, ctx->At);
+  if (rs != PDHG_OK) return rs;
+  launch_fill_units_A(ctx->A, slA, grp, ctx->perm_y, gci, ix, val, s);
+  launch_fill_units_T(ctx->At, slT, tp, sval, rowid, iy, val, s);
+  CK(ctx, cudaGetLastError());
+  if (batch) {
+    ctx->nblocks = ctx->bstart_h[count];
+    CK(ctx, dalloc(ctx, &ctx->binst, ctx->nblocks));
+    CK(ctx, cudaMemcpyAsync(ctx->binst, binst.data(), sizeof(int) * ctx->nblocks, cudaMemcpyHostToDevice, s));
+  }
+  // the host tables are released on return: wait for their copies
   CK(ctx, cudaStreamSynchronize(s));
   return PDHG_OK;
 }
@@ -430,84 +599,80 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
                   const double* c, const double* x0, const double* y0) {
   const int64_t m = ctx->m, n = ctx->n, nnz = ctx->nnz;
   const pdhg_options& o = ctx->opt;
-  // ---- host: internal numbering (rows and columns by decreasing length) ----
-  std::vector<int> lenA(m), lenT(n, 0);
-  for (int64_t i = 0; i < m; ++i) lenA[i] = (int)(row_ptr[i + 1] - row_ptr[i]);
-  for (int64_t k = 0; k < nnz; ++k) lenT[col_idx[k]] += 1;
-  const std::vector<int> py = order_by_length(lenA);  // internal row -> caller's row
-  const std::vector<int> px = order_by_length(lenT);  // internal column -> caller's column
-  std::vector<int> iy(m), ix(n);
-  for (int64_t r = 0; r < m; ++r) iy[py[r]] = (int)r;
-  for (int64_t r = 0; r < n; ++r) ix[px[r]] = (int)r;
-  HostHyb hA, hT;
-  {
-    // internal CSR of A (entries keep the caller's order within a row)
-    std::vector<int64_t> rp(m + 1, 0);
-    std::vector<int> ci(nnz);
-    std::vector<double> v(nnz);
-    for (int64_t r = 0; r < m; ++r) rp[r + 1] = rp[r] + lenA[py[r]];
-    for (int64_t r = 0; r < m; ++r) {
-      const int i = py[r];
-      int64_t q = rp[r];
-      for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k, ++q) {
-        ci[q] = ix[col_idx[k]];
-        v[q] = val[k];
-      }
+  cudaStream_t s = ctx->stream;
+  Scratch sc(s);
+  ctx->count = 1;
+  ctx->xoff_h = {0, (int)n};
+  ctx->yoff_h = {0, (int)m};
+  // the caller's arrays on the device
+  const long long* d_rp = nullptr;
+  const int* d_ci = nullptr;
+  const double *d_v = nullptr, *d_b = nullptr, *d_c = nullptr, *d_x0 = nullptr, *d_y0 = nullptr;
+  if (o.inputs_on_device) {
+    d_rp = reinterpret_cast<const long long*>(row_ptr);
+    d_ci = col_idx;
+    d_v = val;
+    d_b = b;
+    d_c = c;
+    d_x0 = x0;
+    d_y0 = y0;
+    // the checks pdhg_create makes on host inputs, on the device
+    int* flags = nullptr;
+    CK(ctx, sc.take(&flags, 1));
+    CK(ctx, cudaMemsetAsync(flags, 0, sizeof(int), s));
+    launch_validate_csr(m, n, nnz, d_rp, d_ci, d_v, flags, s);
+    launch_check_finite(d_b, m, flags, s);
+    launch_check_finite(d_c, n, flags, s);
+    if (d_x0) launch_check_finite(d_x0, n, flags, s);
+    if (d_y0) launch_check_finite(d_y0, m, flags, s);
+    int hf = 0;
+    CK(ctx, cudaGetLastError());
+    CK(ctx, cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(ctx, cudaStreamSynchronize(s));
+    if (hf & LAYOUT_BAD_ROW_PTR)
+      return fail(ctx, PDHG_ERR_INVALID, "row_ptr[0] != 0, row_ptr[m] != nnz or row_ptr not non-decreasing");
+    if (hf & LAYOUT_BAD_COLUMN) return fail(ctx, PDHG_ERR_INVALID, "column index out of range");
+    if (hf & LAYOUT_UNSORTED)
+      return fail(ctx, PDHG_ERR_INVALID, "column indices not strictly increasing within a row");
+    if (hf & LAYOUT_NOT_FINITE) return fail(ctx, PDHG_ERR_NUMERIC, "NaN or Inf in the input data");
+  } else {
+    long long* rp_ = nullptr;
+    int* ci_ = nullptr;
+    double *v_ = nullptr, *b_ = nullptr, *c_ = nullptr;
+    CK(ctx, sc.take(&rp_, m + 1));
+    CK(ctx, sc.take(&ci_, nnz));
+    CK(ctx, sc.take(&v_, nnz));
+    CK(ctx, sc.take(&b_, m));
+    CK(ctx, sc.take(&c_, n));
+    CK(ctx, cudaMemcpyAsync(rp_, row_ptr, sizeof(long long) * (m + 1), cudaMemcpyHostToDevice, s));
+    if (nnz) {
+      CK(ctx, cudaMemcpyAsync(ci_, col_idx, sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
+      CK(ctx, cudaMemcpyAsync(v_, val, sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
     }
-    hA.rows = (int)m;
-    hA.cols = (int)n;
-    append_units(hA, 0, (int)m, rp, ci, v, o.long_row_min, o.rows_per_thread);
-  }
-  {
-    // transpose (stable counting sort over the caller's columns), then the
-    // internal order of its rows
-    std::vector<int64_t> tp(n + 1, 0);
-    for (int64_t j = 0; j < n; ++j) tp[j + 1] = tp[j] + lenT[j];
-    std::vector<int> tci(nnz);
-    std::vector<double> tv(nnz);
-    {
-      std::vector<int64_t> next(tp.begin(), tp.end() - 1);
-      for (int64_t i = 0; i < m; ++i)
-        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-          const int64_t pos = next[col_idx[k]]++;
-          tci[pos] = iy[i];
-          tv[pos] = val[k];
-        }
+    CK(ctx, cudaMemcpyAsync(b_, b, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    CK(ctx, cudaMemcpyAsync(c_, c, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    if (x0) {
+      double* x0_ = nullptr;
+      CK(ctx, sc.take(&x0_, n));
+      CK(ctx, cudaMemcpyAsync(x0_, x0, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      d_x0 = x0_;
     }
-    std::vector<int64_t> rp(n + 1, 0);
-    std::vector<int> ci(nnz);
-    std::vector<double> v(nnz);
-    for (int64_t r = 0; r < n; ++r) rp[r + 1] = rp[r] + lenT[px[r]];
-    for (int64_t r = 0; r < n; ++r) {
-      const int j = px[r];
-      std::copy(tci.begin() + tp[j], tci.begin() + tp[j + 1], ci.begin() + rp[r]);
-      std::copy(tv.begin() + tp[j], tv.begin() + tp[j + 1], v.begin() + rp[r]);
+    if (y0) {
+      double* y0_ = nullptr;
+      CK(ctx, sc.take(&y0_, m));
+      CK(ctx, cudaMemcpyAsync(y0_, y0, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+      d_y0 = y0_;
     }
-    hT.rows = (int)n;
-    hT.cols = (int)m;
-    append_units(hT, 0, (int)n, rp, ci, v, o.long_row_min, o.rows_per_thread);
+    d_rp = rp_;
+    d_ci = ci_;
+    d_v = v_;
+    d_b = b_;
+    d_c = c_;
   }
-  std::vector<double> bi(m), cI(n), x0i, y0i;
-  for (int64_t r = 0; r < m; ++r) bi[r] = b[py[r]];
-  for (int64_t r = 0; r < n; ++r) cI[r] = c[px[r]];
-  if (x0) {
-    x0i.resize(n);
-    for (int64_t r = 0; r < n; ++r) x0i[r] = x0[px[r]];
-  }
-  if (y0) {
-    y0i.resize(m);
-    for (int64_t r = 0; r < m; ++r) y0i[r] = y0[py[r]];
-  }
-
-  // ---- device allocations and uploads ----
-  pdhg_status rs = upload_hyb(ctx, hA, ctx->A);
-  if (rs != PDHG_OK) return rs;
-  rs = upload_hyb(ctx, hT, ctx->At);
+  pdhg_status rs = build_layouts(ctx, sc, d_rp, d_ci, d_v, {0}, {0, (long long)nnz});
   if (rs != PDHG_OK) return rs;
   Hyb& A = ctx->A;
   Hyb& At = ctx->At;
-  CK(ctx, dalloc(ctx, &ctx->perm_x, n));
-  CK(ctx, dalloc(ctx, &ctx->perm_y, m));
   double** vecs_n[] = {&ctx->c, &ctx->ch, &ctx->dc, &ctx->x, &ctx->xbar, &ctx->xsum, &ctx->xavg, &ctx->xr,
                        &ctx->tmp_n, &ctx->tmp_n2};
   double** vecs_m[] = {&ctx->b, &ctx->bh, &ctx->dr, &ctx->y, &ctx->ysum, &ctx->yavg, &ctx->yr, &ctx->tmp_m};
@@ -531,11 +696,8 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   CK(ctx, cudaMallocHost(&ctx->h_kkt, sizeof(EvalSums)));
   for (int i = 0; i < 3 * EV_POOL; ++i) CK(ctx, cudaEventCreate(&ctx->ev[i]));
 
-  cudaStream_t s = ctx->stream;
-  CK(ctx, cudaMemcpyAsync(ctx->perm_x, px.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(ctx->perm_y, py.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(ctx->b, bi.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(ctx->c, cI.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  launch_gather_double(d_b, ctx->perm_y, m, ctx->b, s);
+  launch_gather_double(d_c, ctx->perm_x, n, ctx->c, s);
 
   // ---- device: scaling ----
   const int gn = vec_grid(ctx, n), gm = vec_grid(ctx, m);
@@ -608,12 +770,12 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   // ---- starting point (scaled: xhat = x0 / D_c, yhat = y0 / D_r) ----
   launch_fill(ctx->x, 0.0, n, gn, s);
   launch_fill(ctx->y, 0.0, m, gm, s);
-  if (x0) {
-    CK(ctx, cudaMemcpyAsync(ctx->tmp_n, x0i.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  if (d_x0) {
+    launch_gather_double(d_x0, ctx->perm_x, n, ctx->tmp_n, s);
     launch_div(ctx->x, ctx->tmp_n, ctx->dc, (int)n, gn, s);
   }
-  if (y0) {
-    CK(ctx, cudaMemcpyAsync(ctx->tmp_m, y0i.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+  if (d_y0) {
+    launch_gather_double(d_y0, ctx->perm_y, m, ctx->tmp_m, s);
     launch_div(ctx->y, ctx->tmp_m, ctx->dr, (int)m, gm, s);
   }
   launch_fill(ctx->xsum, 0.0, n, gn, s);
@@ -773,94 +935,40 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
     ctx->xoff_h[i + 1] = ctx->xoff_h[i] + (int)lps[i].n;
     ctx->yoff_h[i + 1] = ctx->yoff_h[i] + (int)lps[i].m;
   }
-  const int64_t m = ctx->m, n = ctx->n;
-  HostHyb hA, hT;
-  hA.rows = (int)m;
-  hA.cols = (int)n;
-  hT.rows = (int)n;
-  hT.cols = (int)m;
-  std::vector<int> perm_x(n), perm_y(m), binst;
-  std::vector<double> bi(m), cI(n);
-  ctx->bstart_h.assign(count + 1, 0);
-  for (int inst = 0; inst < count; ++inst) {
-    const pdhg_lp_desc& L = lps[inst];
-    const int x0 = ctx->xoff_h[inst], y0 = ctx->yoff_h[inst];
-    const int64_t mi = L.m, ni = L.n, nzi = L.nnz;
-    std::vector<int> lenA(mi), lenT(ni, 0);
-    for (int64_t i = 0; i < mi; ++i) lenA[i] = (int)(L.row_ptr[i + 1] - L.row_ptr[i]);
-    for (int64_t k = 0; k < nzi; ++k) lenT[L.col_idx[k]] += 1;
-    const std::vector<int> py = order_by_length(lenA), px = order_by_length(lenT);
-    std::vector<int> iy(mi), ix(ni);
-    for (int64_t r = 0; r < mi; ++r) iy[py[r]] = (int)r;
-    for (int64_t r = 0; r < ni; ++r) ix[px[r]] = (int)r;
-    for (int64_t r = 0; r < mi; ++r) {
-      perm_y[y0 + r] = y0 + py[r];
-      bi[y0 + r] = L.b[py[r]];
-    }
-    for (int64_t r = 0; r < ni; ++r) {
-      perm_x[x0 + r] = x0 + px[r];
-      cI[x0 + r] = L.c[px[r]];
-    }
-    const int units_before = hA.n_units();
-    {
-      std::vector<int64_t> rp(mi + 1, 0);
-      std::vector<int> ci(nzi);
-      std::vector<double> v(nzi);
-      for (int64_t r = 0; r < mi; ++r) rp[r + 1] = rp[r] + lenA[py[r]];
-      for (int64_t r = 0; r < mi; ++r) {
-        int64_t q = rp[r];
-        for (int64_t k = L.row_ptr[py[r]]; k < L.row_ptr[py[r] + 1]; ++k, ++q) {
-          ci[q] = x0 + ix[L.col_idx[k]];
-          v[q] = L.val[k];
-        }
-      }
-      append_units(hA, y0, (int)mi, rp, ci, v, o.long_row_min, o.rows_per_thread);
-    }
-    {
-      std::vector<int64_t> tp(ni + 1, 0);
-      for (int64_t j = 0; j < ni; ++j) tp[j + 1] = tp[j] + lenT[j];
-      std::vector<int> tci(nzi);
-      std::vector<double> tv(nzi);
-      std::vector<int64_t> next(tp.begin(), tp.end() - 1);
-      for (int64_t i = 0; i < mi; ++i)
-        for (int64_t k = L.row_ptr[i]; k < L.row_ptr[i + 1]; ++k) {
-          const int64_t pos = next[L.col_idx[k]]++;
-          tci[pos] = y0 + iy[i];
-          tv[pos] = L.val[k];
-        }
-      std::vector<int64_t> rp(ni + 1, 0);
-      std::vector<int> ci(nzi);
-      std::vector<double> v(nzi);
-      for (int64_t r = 0; r < ni; ++r) rp[r + 1] = rp[r] + lenT[px[r]];
-      for (int64_t r = 0; r < ni; ++r) {
-        std::copy(tci.begin() + tp[px[r]], tci.begin() + tp[px[r] + 1], ci.begin() + rp[r]);
-        std::copy(tv.begin() + tp[px[r]], tv.begin() + tp[px[r] + 1], v.begin() + rp[r]);
-      }
-      append_units(hT, x0, (int)ni, rp, ci, v, o.long_row_min, o.rows_per_thread);
-    }
-    // both layouts get the same whole number of blocks for this instance
-    const int uA = hA.n_units() - units_before, uT = hT.n_units() - units_before;
-    const int blocks = (std::max(uA, uT) + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
-    pad_units_to(hA, units_before + blocks * WARPS_PER_BLOCK, (int)m);
-    pad_units_to(hT, units_before + blocks * WARPS_PER_BLOCK, (int)n);
-    ctx->bstart_h[inst + 1] = ctx->bstart_h[inst] + blocks;
-    for (int b = 0; b < blocks; ++b) binst.push_back(inst);
+  const int64_t m = ctx->m, n = ctx->n, nnz = ctx->nnz;
+  cudaStream_t s = ctx->stream;
+  Scratch sc(s);
+  // the instances' arrays, concatenated on the device
+  std::vector<long long> rpoff(count), zoff(count + 1, 0);
+  for (int i = 0; i < count; ++i) {
+    rpoff[i] = (long long)ctx->yoff_h[i] + i;
+    zoff[i + 1] = zoff[i] + lps[i].nnz;
   }
-  ctx->nblocks = ctx->bstart_h[count];
-
-  pdhg_status rs = upload_hyb(ctx, hA, ctx->A);
-  if (rs != PDHG_OK) return rs;
-  rs = upload_hyb(ctx, hT, ctx->At);
+  long long* lrp = nullptr;
+  int* lci = nullptr;
+  double *lv = nullptr, *lb = nullptr, *lc = nullptr;
+  CK(ctx, sc.take(&lrp, m + count));
+  CK(ctx, sc.take(&lci, nnz));
+  CK(ctx, sc.take(&lv, nnz));
+  CK(ctx, sc.take(&lb, m));
+  CK(ctx, sc.take(&lc, n));
+  for (int i = 0; i < count; ++i) {
+    const pdhg_lp_desc& L = lps[i];
+    CK(ctx, cudaMemcpyAsync(lrp + rpoff[i], L.row_ptr, sizeof(long long) * (L.m + 1), cudaMemcpyHostToDevice, s));
+    if (L.nnz) {
+      CK(ctx, cudaMemcpyAsync(lci + zoff[i], L.col_idx, sizeof(int) * L.nnz, cudaMemcpyHostToDevice, s));
+      CK(ctx, cudaMemcpyAsync(lv + zoff[i], L.val, sizeof(double) * L.nnz, cudaMemcpyHostToDevice, s));
+    }
+    CK(ctx, cudaMemcpyAsync(lb + ctx->yoff_h[i], L.b, sizeof(double) * L.m, cudaMemcpyHostToDevice, s));
+    CK(ctx, cudaMemcpyAsync(lc + ctx->xoff_h[i], L.c, sizeof(double) * L.n, cudaMemcpyHostToDevice, s));
+  }
+  pdhg_status rs = build_layouts(ctx, sc, lrp, lci, lv, rpoff, zoff);
   if (rs != PDHG_OK) return rs;
   Hyb& A = ctx->A;
   Hyb& At = ctx->At;
-  cudaStream_t s = ctx->stream;
-  CK(ctx, dalloc(ctx, &ctx->perm_x, n));
-  CK(ctx, dalloc(ctx, &ctx->perm_y, m));
   CK(ctx, dalloc(ctx, &ctx->xoff, count + 1));
   CK(ctx, dalloc(ctx, &ctx->yoff, count + 1));
   CK(ctx, dalloc(ctx, &ctx->bstart, count + 1));
-  CK(ctx, dalloc(ctx, &ctx->binst, ctx->nblocks));
   double** vecs_n[] = {&ctx->c, &ctx->ch, &ctx->dc, &ctx->x, &ctx->xbar, &ctx->xsum, &ctx->xavg, &ctx->xr,
                        &ctx->tmp_n, &ctx->tmp_n2};
   double** vecs_m[] = {&ctx->b, &ctx->bh, &ctx->dr, &ctx->y, &ctx->ysum, &ctx->yavg, &ctx->yr, &ctx->tmp_m};
@@ -877,14 +985,11 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
   CK(ctx, cudaMallocHost(&ctx->h_kkt, sizeof(EvalSums)));
   for (int i = 0; i < 3 * EV_POOL; ++i) CK(ctx, cudaEventCreate(&ctx->ev[i]));
   prefer_l1_for_step_kernels();
-  CK(ctx, cudaMemcpyAsync(ctx->perm_x, perm_x.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(ctx->perm_y, perm_y.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
   CK(ctx, cudaMemcpyAsync(ctx->xoff, ctx->xoff_h.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, s));
   CK(ctx, cudaMemcpyAsync(ctx->yoff, ctx->yoff_h.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, s));
   CK(ctx, cudaMemcpyAsync(ctx->bstart, ctx->bstart_h.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(ctx->binst, binst.data(), sizeof(int) * ctx->nblocks, cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(ctx->b, bi.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaMemcpyAsync(ctx->c, cI.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  launch_gather_double(lb, ctx->perm_y, m, ctx->b, s);
+  launch_gather_double(lc, ctx->perm_x, n, ctx->c, s);
 
   // scaling: row and column factors are per row / column, so one pass over
   // the block-diagonal layouts scales every instance by its own factors
@@ -1132,43 +1237,14 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
       o.pc_alpha > 2.0 || o.long_row_min < 1 || o.dual_hot_cols < 0 || o.dual_hot_cols > HOT_MAX || !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4) || o.snapshot_every < 0 || o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
     return fail(nullptr, PDHG_ERR_INVALID, "option out of range");
 
-  // host copies when the caller passed device pointers
-  std::vector<int64_t> h_rp;
-  std::vector<int32_t> h_ci;
-  std::vector<double> h_v, h_b, h_c, h_x0, h_y0;
-  if (o.inputs_on_device) {
-    h_rp.resize(m + 1);
-    h_ci.resize(nnz);
-    h_v.resize(nnz);
-    h_b.resize(m);
-    h_c.resize(n);
-    cudaError_t e = cudaMemcpy(h_rp.data(), row_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && nnz) e = cudaMemcpy(h_ci.data(), col_idx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && nnz) e = cudaMemcpy(h_v.data(), val, sizeof(double) * nnz, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(h_b.data(), b, sizeof(double) * m, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(h_c.data(), c, sizeof(double) * n, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && x0) {
-      h_x0.resize(n);
-      e = cudaMemcpy(h_x0.data(), x0, sizeof(double) * n, cudaMemcpyDeviceToHost);
-    }
-    if (e == cudaSuccess && y0) {
-      h_y0.resize(m);
-      e = cudaMemcpy(h_y0.data(), y0, sizeof(double) * m, cudaMemcpyDeviceToHost);
-    }
-    if (e != cudaSuccess) return cuda_fail(nullptr, e, "copy of device inputs");
-    row_ptr = h_rp.data();
-    col_idx = h_ci.data();
-    val = h_v.data();
-    b = h_b.data();
-    c = h_c.data();
-    if (x0) x0 = h_x0.data();
-    if (y0) y0 = h_y0.data();
+  // CSR validation of host inputs (host logic, before any device work);
+  // device inputs are checked on the device during setup
+  if (!o.inputs_on_device) {
+    pdhg_status vs = validate_lp(m, n, nnz, row_ptr, col_idx, val, b, c);
+    if (vs != PDHG_OK) return vs;
+    if ((x0 && !all_finite(x0, n)) || (y0 && !all_finite(y0, m)))
+      return fail(nullptr, PDHG_ERR_NUMERIC, "NaN or Inf in the input data");
   }
-  // CSR validation (host logic, before any device work)
-  pdhg_status vs = validate_lp(m, n, nnz, row_ptr, col_idx, val, b, c);
-  if (vs != PDHG_OK) return vs;
-  if ((x0 && !all_finite(x0, n)) || (y0 && !all_finite(y0, m)))
-    return fail(nullptr, PDHG_ERR_NUMERIC, "NaN or Inf in the input data");
 
   pdhg_ctx* ctx = new (std::nothrow) pdhg_ctx();
   if (!ctx) return fail(nullptr, PDHG_ERR_OOM, "host allocation of the context failed");
