@@ -272,14 +272,17 @@ def run_tiny(P, torch, iters=20_000):
 
     lp = lpgen.tiny_lp(0)
     out = {"workload": "tiny-lp m=200 n=500 nnz=2500 FP64, restarts, eval every 64"}
-    for g in (0, 1):
-        with P.Solver.from_lp(lp, use_graphs=g) as s:
+    # two launches per iteration (direct, or replayed from CUDA graphs), and
+    # the single-block solve loop (one launch for all iterations)
+    for key, opts in (("iters_per_s_direct", dict(use_graphs=0)), ("iters_per_s_graphs", dict(use_graphs=1)),
+                      ("iters_per_s_persistent", dict(persistent=1))):
+        with P.Solver.from_lp(lp, **opts) as s:
             s.iterate(640)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             s.iterate(iters)
             torch.cuda.synchronize()
-            out["iters_per_s_graphs" if g else "iters_per_s_direct"] = iters / (time.perf_counter() - t0)
+            out[key] = iters / (time.perf_counter() - t0)
     return out
 
 

@@ -93,7 +93,11 @@ typedef struct {
   int record_for_backward; /* 1: keep checkpoints for pdhg_backward; needs restarts = 0, primal_weight = 0,
                               precision FP64 or FP32 (0) */
   int64_t checkpoint_every; /* iterations between adjoint checkpoints (50) */
-  int reserved[8];
+  int persistent;         /* 1: run the solve loop of each LP in one thread block: a single launch does the
+                             iterations, evaluations, restarts and termination test with the LP's vectors in
+                             shared memory (LPs with 7n + 6m <= 28672, i.e. up to ~224 KiB of vectors; FP64,
+                             no recording, no kernel timing); 0: two launches per iteration (0) */
+  int reserved[7];
 } pdhg_options;
 
 /* Scalars of one point on the problem as given (unscaled), all FP64.

@@ -109,6 +109,9 @@ struct Hyb {
 // ---------------------------------------------------------------------------
 // device helpers
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double relu(double v) { return v < 0.0 ? 0.0 : v; }  // NaN passes through
+__device__ __forceinline__ float relu(float v) { return v < 0.0f ? 0.0f : v; }
+
 // slot of entry e of row (32 q + lane) in a slice of 32 R rows padded to Lp
 // entries per row: pairs of entries are interleaved across the slice's
 // threads, so a thread reads entries 2p and 2p+1 of its row with one load

@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "decide.cuh"
 
 // Minimum resident blocks per SM requested for the two step kernels. The
 // kernels are latency bound, so occupancy matters more than registers: with
@@ -33,8 +34,6 @@ namespace pdhg {
 
 namespace {
 
-__device__ __forceinline__ double relu(double v) { return v < 0.0 ? 0.0 : v; }  // NaN passes through
-__device__ __forceinline__ float relu(float v) { return v < 0.0f ? 0.0f : v; }
 
 // ---- cache-policy loads ----------------------------------------------------
 __device__ __forceinline__ unsigned long long stream_policy() {
@@ -602,104 +601,12 @@ __global__ void k_eval_finalize(const double* __restrict__ partials, int nb, Eva
   if (lane == 0) out->q[q] = acc;
 }
 
-__device__ __forceinline__ void scaled_norms(const EvalSums& e, double& p, double& d, double& g) {
-  p = sqrt(e.q[Q_RP2S]);
-  d = sqrt(e.q[Q_RD2S]);
-  g = fabs(e.q[Q_CX] - e.q[Q_BY]);
-}
-
-__device__ __forceinline__ double weighted_kkt(double p, double d, double g, double omega) {
-  return sqrt(omega * p * p + d * d / omega + g * g);
-}
-
 __global__ void k_init_restart_ref(DevState* st) {
   double p, d, g;
   scaled_norms(st->cur, p, d, g);
   st->rs_p = st->pc_p = p;
   st->rs_d = st->pc_d = d;
   st->rs_g = st->pc_g = g;
-}
-
-// One evaluation's decisions (single thread): candidate, termination,
-// snapshot schedule (Algorithm 1), restart test, primal-weight update.
-__device__ void decide_one(DevState* st, TraceRec* trace) {
-  double cp, cd, cg;
-  scaled_norms(st->cur, cp, cd, cg);
-  int which = KIND_CUR;
-  if (st->restarts_on && st->t > 0) {
-    double ap, ad, ag;
-    scaled_norms(st->avg, ap, ad, ag);
-    if (weighted_kkt(ap, ad, ag, st->omega) < weighted_kkt(cp, cd, cg, st->omega)) {
-      which = KIND_AVG;
-      cp = ap;
-      cd = ad;
-      cg = ag;
-    }
-  }
-  const EvalSums& e = which == KIND_AVG ? st->avg : st->cur;
-  const double cx = e.q[Q_CX], by = e.q[Q_BY];
-  const double rel_p = sqrt(e.q[Q_RP2U]) / (1.0 + st->b_norm);
-  const double rel_d = sqrt(e.q[Q_RD2U]) / (1.0 + st->c_norm);
-  const double rel_g = fabs(cx - by) / (1.0 + fabs(cx) + fabs(by));
-  const double rel = fmax(rel_p, fmax(rel_d, rel_g));
-  st->numeric = !(isfinite(rel_p) && isfinite(rel_d) && isfinite(rel_g) && isfinite(cp) && isfinite(cd));
-  st->candidate = which;
-  st->cand_rel_kkt = rel;
-
-  const int converged = st->tol > 0.0 && rel <= st->tol;
-  int snap = 0;
-  if (st->eps_target > 0.0 && rel <= st->eps_target) {
-    snap = 1;
-    st->eps_target *= st->eps_factor;
-  }
-  if (st->snapshot_every > 0 && st->k >= st->next_snapshot) {
-    snap = 1;
-    while (st->next_snapshot <= st->k) st->next_snapshot += st->snapshot_every;
-  }
-  st->snapshot_flag = snap;
-  if (snap) st->snapshots += 1;
-
-  int kind = KIND_NONE, apply = APPLY_NONE;
-  if (converged) {
-    apply = which == KIND_AVG ? APPLY_TAKE_AVG : APPLY_NONE;
-  } else if (st->restarts_on) {
-    const double om = st->omega;
-    const double kc = weighted_kkt(cp, cd, cg, om);
-    const double kr = weighted_kkt(st->rs_p, st->rs_d, st->rs_g, om);
-    const double kp = weighted_kkt(st->pc_p, st->pc_d, st->pc_g, om);
-    const bool restart = (kc <= st->beta_suff * kr) || (kc <= st->beta_nec * kr && kc > kp) ||
-                         ((double)st->t >= st->beta_art * (double)st->k);
-    if (restart) {
-      kind = which;
-      if (st->primal_weight_on) {
-        const double dx = sqrt(e.q[Q_DX2]), dy = sqrt(e.q[Q_DY2]);
-        if (dx > 1e-10 && dy > 1e-10) st->omega = exp(st->theta * log(dy / dx) + (1.0 - st->theta) * log(om));
-      }
-      apply = which == KIND_AVG ? APPLY_RESTART_AVG : APPLY_RESTART_CUR;
-      st->rs_p = cp;
-      st->rs_d = cd;
-      st->rs_g = cg;
-      st->t = 0;
-      st->restarts += 1;
-    }
-    st->pc_p = cp;
-    st->pc_d = cd;
-    st->pc_g = cg;
-  }
-  st->kind = kind;
-  st->apply_mode = apply;
-  st->converged = converged;
-  st->tau = st->eta / st->omega;
-  st->sigma = st->eta * st->omega;
-  if (trace && st->evals < TRACE_CAP) {
-    TraceRec& r = trace[st->evals];
-    r.iteration = st->k;
-    r.kind = kind;
-    r.candidate = which;
-    r.omega = st->omega;
-    r.rel_kkt = rel;
-  }
-  st->evals += 1;
 }
 
 __global__ void k_decide(DevState* st, TraceRec* trace) { decide_one(st, trace); }

@@ -151,6 +151,23 @@ void launch_fill_units_A(const Hyb& H, const int* slen, const long long* grp, co
 void launch_fill_units_T(const Hyb& H, const int* slen, const long long* tp, const int* sval, const int* rowid,
                          const int* iy, const double* v, cudaStream_t s);
 
+// ---- single-block solve loop (persistent.cu) ----------------------------------
+constexpr int PERSIST_TPB = 512;
+// most doubles of vectors one block holds in shared memory (7 n + 6 m)
+constexpr long long PERSIST_MAX_DOUBLES = 28672;
+struct PersistentArgs {
+  long long max_iters;
+  int eval_every, evaluating, restarts, batch;
+  int n, m;                         // one LP: its sizes (xoff == nullptr)
+  const int *xoff, *yoff, *ustart;  // batch: column, row and unit ranges per instance
+  double *x, *xbar, *xsum, *xr, *xavg, *y, *ysum, *yr, *yavg;
+  const double *ch, *dc, *bh, *dr;
+};
+size_t persistent_smem_bytes(long long n, long long m);
+// one block per instance; trace may be null
+cudaError_t launch_solve_block(const Hyb& A, const Hyb& At, const PersistentArgs& a, int blocks, size_t smem,
+                               DevState* sts, TraceRec* trace, cudaStream_t s);
+
 // the step kernels use no shared memory: prefer the largest L1
 void prefer_l1_for_step_kernels();
 

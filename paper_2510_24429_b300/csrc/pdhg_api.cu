@@ -68,6 +68,10 @@ struct pdhg_ctx {
   std::vector<int> xoff_h, yoff_h, bstart_h;
   int *xoff = nullptr, *yoff = nullptr, *binst = nullptr, *bstart = nullptr;
   int nblocks = 0;
+  // option persistent: first unit of every instance (count + 1; batch only) and
+  // the shared memory of the single-block solve loop
+  int* ustart = nullptr;
+  size_t persist_smem = 0;
   // CUDA graphs of one evaluation block, per precision phase (FP64, FP32)
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   int64_t graph_launches[2] = {0, 0};
@@ -671,6 +675,7 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   }
   pdhg_status rs = build_layouts(ctx, sc, d_rp, d_ci, d_v, {0}, {0, (long long)nnz});
   if (rs != PDHG_OK) return rs;
+  ctx->persist_smem = persistent_smem_bytes(n, m);
   Hyb& A = ctx->A;
   Hyb& At = ctx->At;
   double** vecs_n[] = {&ctx->c, &ctx->ch, &ctx->dc, &ctx->x, &ctx->xbar, &ctx->xsum, &ctx->xavg, &ctx->xr,
@@ -964,6 +969,15 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
   }
   pdhg_status rs = build_layouts(ctx, sc, lrp, lci, lv, rpoff, zoff);
   if (rs != PDHG_OK) return rs;
+  {
+    std::vector<int> ustart(count + 1);
+    for (int i = 0; i <= count; ++i) ustart[i] = ctx->bstart_h[i] * WARPS_PER_BLOCK;
+    CK(ctx, dalloc(ctx, &ctx->ustart, count + 1));
+    CK(ctx, cudaMemcpyAsync(ctx->ustart, ustart.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, s));
+    CK(ctx, cudaStreamSynchronize(s));
+    for (int i = 0; i < count; ++i)
+      ctx->persist_smem = std::max(ctx->persist_smem, persistent_smem_bytes(lps[i].n, lps[i].m));
+  }
   Hyb& A = ctx->A;
   Hyb& At = ctx->At;
   CK(ctx, dalloc(ctx, &ctx->xoff, count + 1));
@@ -1121,6 +1135,80 @@ pdhg_status enqueue_eval_batch(pdhg_ctx* ctx) {
   return PDHG_OK;
 }
 
+// pdhg_iterate with option persistent: the solve loop runs on the device, one
+// block per LP; the host launches again only after a snapshot it has to take.
+pdhg_status iterate_persistent(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done) {
+  const pdhg_options& o = ctx->opt;
+  cudaStream_t s = ctx->stream;
+  const int count = ctx->count;
+  const bool batch = count > 1;
+  for (int i = 0; i < count; ++i) {
+    ctx->h_st[i].tol = tol;
+    CK(ctx, cudaMemcpyAsync(&ctx->st[i].tol, &ctx->h_st[i].tol, sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  PersistentArgs a{};
+  a.eval_every = o.eval_every;
+  a.evaluating = batch || o.restarts || tol > 0.0 || o.eps_cross > 0.0 || o.snapshot_every > 0;
+  a.restarts = o.restarts;
+  a.batch = batch;
+  a.n = (int)ctx->n;
+  a.m = (int)ctx->m;
+  a.xoff = batch ? ctx->xoff : nullptr;
+  a.yoff = batch ? ctx->yoff : nullptr;
+  a.ustart = batch ? ctx->ustart : nullptr;
+  a.x = ctx->x;
+  a.xbar = ctx->xbar;
+  a.xsum = ctx->xsum;
+  a.xr = ctx->xr;
+  a.xavg = ctx->xavg;
+  a.y = ctx->y;
+  a.ysum = ctx->ysum;
+  a.yr = ctx->yr;
+  a.yavg = ctx->yavg;
+  a.ch = ctx->ch;
+  a.dc = ctx->dc;
+  a.bh = ctx->bh;
+  a.dr = ctx->dr;
+  ctx->converged = false;
+  int64_t done = 0;
+  while (done < max_iters) {
+    a.max_iters = max_iters - done;
+    CK(ctx, launch_solve_block(ctx->A, ctx->At, a, count, ctx->persist_smem, ctx->st, batch ? nullptr : ctx->trace,
+                               s));
+    ctx->launches += 1;
+    CK(ctx, cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevState) * count, cudaMemcpyDeviceToHost, s));
+    CK(ctx, cudaStreamSynchronize(s));
+    int64_t k_new = ctx->k;
+    bool all_done = true;
+    for (int i = 0; i < count; ++i) {
+      const DevState& h = ctx->h_st[i];
+      if (h.numeric && !(batch && h.frozen)) {
+        if (iters_done) *iters_done = done;
+        return fail(ctx, PDHG_ERR_NUMERIC,
+                    batch ? "NaN or Inf in the iterates of instance " + std::to_string(i) : "NaN or Inf in the iterates");
+      }
+      k_new = std::max<int64_t>(k_new, h.k);
+      all_done = all_done && (batch ? h.frozen != 0 : h.converged != 0);
+    }
+    const int64_t step = k_new - ctx->k;
+    ctx->k = k_new;
+    done += step;
+    if (!batch && ctx->h_st->snapshot_flag) {
+      pdhg_status rs = take_snapshot(ctx);
+      if (rs != PDHG_OK) return rs;
+      ctx->launches += 2;
+    }
+    if (all_done) {
+      ctx->converged = true;
+      break;
+    }
+    if (batch || step == 0) break;  // a batch launch runs every instance to its end
+  }
+  if (iters_done) *iters_done = done;
+  if (ctx->converged || tol == 0.0) return PDHG_OK;
+  return fail(ctx, PDHG_ERR_NOT_CONVERGED, "iteration limit reached before the tolerance");
+}
+
 pdhg_status iterate_batch(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done) {
   const pdhg_options& o = ctx->opt;
   cudaStream_t s = ctx->stream;
@@ -1236,6 +1324,15 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
   if (o.eval_every < 1 || o.ruiz_iters < 0 || o.power_iters < 1 || !(o.step_factor > 0.0) || o.pc_alpha < 0.0 ||
       o.pc_alpha > 2.0 || o.long_row_min < 1 || o.dual_hot_cols < 0 || o.dual_hot_cols > HOT_MAX || !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4) || o.snapshot_every < 0 || o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
     return fail(nullptr, PDHG_ERR_INVALID, "option out of range");
+  if (o.persistent) {
+    if (o.persistent != 1 || o.precision != PDHG_FP64 || o.record_for_backward || o.kernel_timing ||
+        o.dual_hot_cols)
+      return fail(nullptr, PDHG_ERR_INVALID,
+                  "persistent = 1 needs precision FP64 and no recording, kernel timing or hot columns");
+    if (7 * n + 6 * m > PERSIST_MAX_DOUBLES)
+      return fail(nullptr, PDHG_ERR_INVALID,
+                  "persistent: the LP's vectors (7n + 6m doubles) exceed one block's shared memory (28672)");
+  }
 
   // CSR validation of host inputs (host logic, before any device work);
   // device inputs are checked on the device during setup
@@ -1307,6 +1404,7 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
   if (max_iters < 0 || !(tol >= 0.0)) return fail(ctx, PDHG_ERR_INVALID, "max_iters < 0 or tol < 0");
   pdhg_status rs = set_device(ctx);
   if (rs != PDHG_OK) return rs;
+  if (ctx->opt.persistent) return iterate_persistent(ctx, max_iters, tol, iters_done);
   if (ctx->count > 1) return iterate_batch(ctx, max_iters, tol, iters_done);
   const pdhg_options& o = ctx->opt;
   const bool evaluating = o.restarts || tol > 0.0 || o.eps_cross > 0.0 || o.snapshot_every > 0;
@@ -1567,6 +1665,8 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
       !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4))
     return fail(nullptr, PDHG_ERR_INVALID,
                 "batch: FP64, host inputs, no snapshots, no recording, no shared-memory hot columns, valid options");
+  if (o.persistent != 0 && (o.persistent != 1 || o.kernel_timing))
+    return fail(nullptr, PDHG_ERR_INVALID, "persistent must be 0 or 1, and 1 excludes kernel timing");
   int64_t mt = 0, nt = 0, zt = 0;
   for (int i = 0; i < count; ++i) {
     const pdhg_lp_desc& L = lps[i];
@@ -1578,6 +1678,10 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
     mt += L.m;
     nt += L.n;
     zt += L.nnz;
+    if (o.persistent && 7 * L.n + 6 * L.m > PERSIST_MAX_DOUBLES)
+      return fail(nullptr, PDHG_ERR_INVALID,
+                  "persistent: the vectors of instance " + std::to_string(i) +
+                      " (7n + 6m doubles) exceed one block's shared memory (28672)");
   }
   if (mt >= (1LL << 31) - 1 || nt >= (1LL << 31) - 1 || zt >= (1LL << 31) - 1)
     return fail(nullptr, PDHG_ERR_INVALID, "batch totals of m, n and nnz must be below 2^31 - 1");

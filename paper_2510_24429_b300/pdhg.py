@@ -53,7 +53,8 @@ class pdhg_options(C.Structure):
         ("dual_hot_cols", C.c_int),
         ("record_for_backward", C.c_int),
         ("checkpoint_every", C.c_int64),
-        ("reserved", C.c_int * 8),
+        ("persistent", C.c_int),
+        ("reserved", C.c_int * 7),
     ]
 
 
