@@ -314,6 +314,11 @@ __global__ void k_div(double* __restrict__ out, const double* __restrict__ a, co
     out[i] = a[i] / b[i];
 }
 
+__global__ void k_reciprocal(double* __restrict__ out, const double* __restrict__ in, int len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    out[i] = 1.0 / in[i];
+}
+
 __global__ void k_fill(double* __restrict__ v, double val, long long len) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
     v[i] = val;
@@ -353,8 +358,9 @@ __global__ void k_div_by_norm(double* __restrict__ v, const double* __restrict__
                               int len) {
   const double s = sqrt(*s2);
   if (!(s > 0.0)) return;
+  const double is = 1.0 / s;  // one division per thread: FP64 division is costly on this GPU
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
-    v[i] = w[i] / s;
+    v[i] = w[i] * is;
 }
 
 // scal: [0] = ||Ahat v||^2 of the last power iteration, [1] = ||chat||^2,
@@ -474,18 +480,18 @@ __global__ void k_make_average(const double* __restrict__ xs, const double* __re
                                const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ xa,
                                double* __restrict__ ya, int n, int m, const DevState* __restrict__ st) {
   const long long t = st->t;
-  const double td = (double)t;
+  const double it = t > 0 ? 1.0 / (double)t : 0.0;  // one division; FP64 division is costly on this GPU
   const int len = n > m ? n : m;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
-    if (i < n) xa[i] = t > 0 ? xs[i] / td : x[i];
-    if (i < m) ya[i] = t > 0 ? ys[i] / td : y[i];
+    if (i < n) xa[i] = t > 0 ? xs[i] * it : x[i];
+    if (i < m) ya[i] = t > 0 ? ys[i] * it : y[i];
   }
 }
 
 struct EvalDualOp {
   using State = NoState;
   const double* __restrict__ ch;
-  const double* __restrict__ dc;
+  const double* __restrict__ idc;  // 1 / D_c
   const double* __restrict__ px;
   const double* __restrict__ xr;
   double acc[6] = {0, 0, 0, 0, 0, 0};
@@ -494,7 +500,7 @@ struct EvalDualOp {
     const double c = ch[j];
     const double rd = relu(g - c);
     const double zh = relu(c - g);
-    const double rdu = rd / dc[j];
+    const double rdu = rd * idc[j];
     const double xj = px[j];
     acc[0] += rd * rd;
     acc[1] += rdu * rdu;
@@ -509,7 +515,7 @@ struct EvalDualOp {
 };
 
 __global__ void __launch_bounds__(TPB) k_eval_dual(Hyb At, const double* __restrict__ py,
-                                                   const double* __restrict__ ch, const double* __restrict__ dc,
+                                                   const double* __restrict__ ch, const double* __restrict__ idc,
                                                    const double* __restrict__ px, const double* __restrict__ xr,
                                                    double* __restrict__ partials, const DevState* __restrict__ sts,
                                                    const int* __restrict__ binst) {
@@ -519,7 +525,7 @@ __global__ void __launch_bounds__(TPB) k_eval_dual(Hyb At, const double* __restr
   }
   EvalDualOp op;
   op.ch = ch;
-  op.dc = dc;
+  op.idc = idc;
   op.px = px;
   op.xr = xr;
   hyb_dot(At, At.v, GlobalGather<double>{py}, op);
@@ -539,7 +545,7 @@ __global__ void __launch_bounds__(TPB) k_eval_dual(Hyb At, const double* __restr
 struct EvalPrimalOp {
   using State = NoState;
   const double* __restrict__ bh;
-  const double* __restrict__ dr;
+  const double* __restrict__ idr;  // 1 / D_r
   const double* __restrict__ py;
   const double* __restrict__ yr;
   double acc[5] = {0, 0, 0, 0, 0};
@@ -547,7 +553,7 @@ struct EvalPrimalOp {
   __device__ __forceinline__ void finish(int i, double h, const State&) {
     const double b = bh[i];
     const double rp = b - h;
-    const double rpu = rp / dr[i];
+    const double rpu = rp * idr[i];
     const double yi = py[i];
     acc[0] += rp * rp;
     acc[1] += rpu * rpu;
@@ -561,7 +567,7 @@ struct EvalPrimalOp {
 };
 
 __global__ void __launch_bounds__(TPB) k_eval_primal(Hyb A, const double* __restrict__ px,
-                                                     const double* __restrict__ bh, const double* __restrict__ dr,
+                                                     const double* __restrict__ bh, const double* __restrict__ idr,
                                                      const double* __restrict__ py, const double* __restrict__ yr,
                                                      double* __restrict__ partials, const DevState* __restrict__ sts,
                                                      const int* __restrict__ binst) {
@@ -571,7 +577,7 @@ __global__ void __launch_bounds__(TPB) k_eval_primal(Hyb A, const double* __rest
   }
   EvalPrimalOp op;
   op.bh = bh;
-  op.dr = dr;
+  op.idr = idr;
   op.py = py;
   op.yr = yr;
   hyb_dot(A, A.v, GlobalGather<double>{px}, op);
@@ -663,11 +669,11 @@ __global__ void k_make_average_b(const double* __restrict__ xs, const double* __
   const int i = blockIdx.y;
   if (sts[i].frozen) return;
   const long long t = sts[i].t;
-  const double td = (double)t;
+  const double it = t > 0 ? 1.0 / (double)t : 0.0;
   for (int j = xoff[i] + blockIdx.x * blockDim.x + threadIdx.x; j < xoff[i + 1]; j += gridDim.x * blockDim.x)
-    xa[j] = t > 0 ? xs[j] / td : x[j];
+    xa[j] = t > 0 ? xs[j] * it : x[j];
   for (int r = yoff[i] + blockIdx.x * blockDim.x + threadIdx.x; r < yoff[i + 1]; r += gridDim.x * blockDim.x)
-    ya[r] = t > 0 ? ys[r] / td : y[r];
+    ya[r] = t > 0 ? ys[r] * it : y[r];
 }
 
 __global__ void k_apply_b(const DevState* __restrict__ sts, double* __restrict__ x, double* __restrict__ y,
@@ -711,8 +717,9 @@ __global__ void k_div_by_norm_b(double* __restrict__ v, const double* __restrict
   const int i = blockIdx.y;
   const double s = sqrt(s2[(size_t)i * sstride]);
   if (!(s > 0.0)) return;
+  const double is = 1.0 / s;
   for (int j = off[i] + blockIdx.x * blockDim.x + threadIdx.x; j < off[i + 1]; j += gridDim.x * blockDim.x)
-    v[j] = w[j] / s;
+    v[j] = w[j] * is;
 }
 
 // v = 1 / sqrt(count of instance i) on instance i's range (power-iteration start)
@@ -772,11 +779,11 @@ __global__ void k_make_average32(const float* __restrict__ xs, const float* __re
                                  const float* __restrict__ x, const float* __restrict__ y, double* __restrict__ xa,
                                  double* __restrict__ ya, int n, int m, const DevState* __restrict__ st) {
   const long long t = st->t;
-  const double td = (double)t;
+  const double it = t > 0 ? 1.0 / (double)t : 0.0;
   const int len = n > m ? n : m;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
-    if (i < n) xa[i] = t > 0 ? (double)xs[i] / td : (double)x[i];
-    if (i < m) ya[i] = t > 0 ? (double)ys[i] / td : (double)y[i];
+    if (i < n) xa[i] = t > 0 ? (double)xs[i] * it : (double)x[i];
+    if (i < m) ya[i] = t > 0 ? (double)ys[i] * it : (double)y[i];
   }
 }
 
@@ -959,6 +966,9 @@ void launch_mul(double* out, const double* a, const double* b, int len, int grid
 void launch_div(double* out, const double* a, const double* b, int len, int grid, cudaStream_t s) {
   k_div<<<grid, TPB, 0, s>>>(out, a, b, len);
 }
+void launch_reciprocal(double* out, const double* in, int len, int grid, cudaStream_t s) {
+  k_reciprocal<<<grid, TPB, 0, s>>>(out, in, len);
+}
 void launch_fill(double* v, double val, long long len, int grid, cudaStream_t s) {
   k_fill<<<grid, TPB, 0, s>>>(v, val, len);
 }
@@ -1001,10 +1011,10 @@ void launch_make_average(const double* xs, const double* ys, const double* x, co
   k_make_average<<<grid, TPB, 0, s>>>(xs, ys, x, y, xa, ya, n, m, st);
 }
 void launch_eval_point(const Hyb& A, const Hyb& At, const double* px, const double* py, const double* bh,
-                       const double* ch, const double* dr, const double* dc, const double* xr, const double* yr,
+                       const double* ch, const double* idr, const double* idc, const double* xr, const double* yr,
                        double* partials, int nb, cudaStream_t s, const DevState* sts, const int* binst) {
-  k_eval_dual<<<nb, TPB, 0, s>>>(At, py, ch, dc, px, xr, partials, sts, binst);
-  k_eval_primal<<<nb, TPB, 0, s>>>(A, px, bh, dr, py, yr, partials, sts, binst);
+  k_eval_dual<<<nb, TPB, 0, s>>>(At, py, ch, idc, px, xr, partials, sts, binst);
+  k_eval_primal<<<nb, TPB, 0, s>>>(A, px, bh, idr, py, yr, partials, sts, binst);
 }
 void launch_decide_b(DevState* sts, int count, cudaStream_t s) { k_decide_b<<<(count + 127) / 128, 128, 0, s>>>(sts, count); }
 void launch_add_counters_b(DevState* sts, int count, long long dk, cudaStream_t s) {

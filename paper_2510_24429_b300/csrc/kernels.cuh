@@ -22,6 +22,7 @@ void launch_mul_inplace(double* d, const double* f, int len, int grid, cudaStrea
 void launch_mul(double* out, const double* a, const double* b, int len, int grid, cudaStream_t s);
 void launch_div(double* out, const double* a, const double* b, int len, int grid, cudaStream_t s);
 void launch_fill(double* v, double val, long long len, int grid, cudaStream_t s);
+void launch_reciprocal(double* out, const double* in, int len, int grid, cudaStream_t s);
 void launch_spmv(const Hyb& M, const double* x, double* y, int grid, cudaStream_t s);
 // out[0] = sum v^2 (deterministic two-stage reduction through `partials`)
 void launch_sumsq(const double* v, int len, double* partials, int nb, double* out, cudaStream_t s);
@@ -75,9 +76,9 @@ void launch_add_counters(DevState* st, long long dk, cudaStream_t s);
 void launch_make_average(const double* xs, const double* ys, const double* x, const double* y, double* xa,
                          double* ya, int n, int m, const DevState* st, int grid, cudaStream_t s);
 // Partial sums of one point into partials[nb][NQ]; xr/yr may be null (no
-// restart distances). Both sides use the same nb blocks.
+// restart distances); idr, idc = 1 / D_r, 1 / D_c. Both sides use the same nb blocks.
 void launch_eval_point(const Hyb& A, const Hyb& At, const double* px, const double* py, const double* bh,
-                       const double* ch, const double* dr, const double* dc, const double* xr, const double* yr,
+                       const double* ch, const double* idr, const double* idc, const double* xr, const double* yr,
                        double* partials, int nb, cudaStream_t s, const DevState* sts = nullptr,
                        const int* binst = nullptr);
 // ---- batch (count instances; xoff/yoff: instance ranges of the column and row vectors) ----
@@ -161,7 +162,7 @@ struct PersistentArgs {
   int n, m;                         // one LP: its sizes (xoff == nullptr)
   const int *xoff, *yoff, *ustart;  // batch: column, row and unit ranges per instance
   double *x, *xbar, *xsum, *xr, *xavg, *y, *ysum, *yr, *yavg;
-  const double *ch, *dc, *bh, *dr;
+  const double *ch, *idc, *bh, *idr;  // idc, idr: 1 / D_c, 1 / D_r
 };
 size_t persistent_smem_bytes(long long n, long long m);
 // one block per instance; trace may be null

@@ -53,6 +53,7 @@ struct pdhg_ctx {
   int* perm_x = nullptr;  // internal column -> caller's column
   int* perm_y = nullptr;  // internal row -> caller's row
   double *b = nullptr, *c = nullptr, *bh = nullptr, *ch = nullptr, *dr = nullptr, *dc = nullptr;
+  double *idr = nullptr, *idc = nullptr;  // 1 / D_r, 1 / D_c (the evaluation multiplies)
   double *x = nullptr, *y = nullptr, *xbar = nullptr, *xsum = nullptr, *ysum = nullptr;
   double *xavg = nullptr, *yavg = nullptr, *xr = nullptr, *yr = nullptr;
   double *tmp_n = nullptr, *tmp_m = nullptr, *tmp_n2 = nullptr;
@@ -242,7 +243,7 @@ pdhg_status read_state(pdhg_ctx* ctx) {
 // Evaluate a point into *dst (EvalSums in device memory).
 void eval_point(pdhg_ctx* ctx, const double* px, const double* py, const double* xr, const double* yr,
                 EvalSums* dst) {
-  launch_eval_point(ctx->A, ctx->At, px, py, ctx->bh, ctx->ch, ctx->dr, ctx->dc, xr, yr, ctx->partials,
+  launch_eval_point(ctx->A, ctx->At, px, py, ctx->bh, ctx->ch, ctx->idr, ctx->idc, xr, yr, ctx->partials,
                     ctx->nb_eval, ctx->stream);
   launch_eval_finalize(ctx->partials, ctx->nb_eval, dst, ctx->stream);
 }
@@ -678,9 +679,10 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   ctx->persist_smem = persistent_smem_bytes(n, m);
   Hyb& A = ctx->A;
   Hyb& At = ctx->At;
-  double** vecs_n[] = {&ctx->c, &ctx->ch, &ctx->dc, &ctx->x, &ctx->xbar, &ctx->xsum, &ctx->xavg, &ctx->xr,
-                       &ctx->tmp_n, &ctx->tmp_n2};
-  double** vecs_m[] = {&ctx->b, &ctx->bh, &ctx->dr, &ctx->y, &ctx->ysum, &ctx->yavg, &ctx->yr, &ctx->tmp_m};
+  double** vecs_n[] = {&ctx->c, &ctx->ch, &ctx->dc, &ctx->idc, &ctx->x, &ctx->xbar, &ctx->xsum, &ctx->xavg,
+                       &ctx->xr, &ctx->tmp_n, &ctx->tmp_n2};
+  double** vecs_m[] = {&ctx->b, &ctx->bh, &ctx->dr, &ctx->idr, &ctx->y, &ctx->ysum, &ctx->yavg, &ctx->yr,
+                       &ctx->tmp_m};
   for (double** p : vecs_n) CK(ctx, dalloc(ctx, p, n));
   for (double** p : vecs_m) CK(ctx, dalloc(ctx, p, m));
   ctx->nb_eval = std::max(1, std::min(ctx->sms * 16, std::max(unit_grid(A), unit_grid(At))));
@@ -733,6 +735,8 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   }
   launch_mul(ctx->bh, ctx->dr, ctx->b, (int)m, gm, s);
   launch_mul(ctx->ch, ctx->dc, ctx->c, (int)n, gn, s);
+  launch_reciprocal(ctx->idr, ctx->dr, (int)m, gm, s);
+  launch_reciprocal(ctx->idc, ctx->dc, (int)n, gn, s);
   CK(ctx, cudaGetLastError());
 
   // ---- device: power iteration for ||Ahat||_2 from the all-ones vector ----
@@ -983,9 +987,10 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
   CK(ctx, dalloc(ctx, &ctx->xoff, count + 1));
   CK(ctx, dalloc(ctx, &ctx->yoff, count + 1));
   CK(ctx, dalloc(ctx, &ctx->bstart, count + 1));
-  double** vecs_n[] = {&ctx->c, &ctx->ch, &ctx->dc, &ctx->x, &ctx->xbar, &ctx->xsum, &ctx->xavg, &ctx->xr,
-                       &ctx->tmp_n, &ctx->tmp_n2};
-  double** vecs_m[] = {&ctx->b, &ctx->bh, &ctx->dr, &ctx->y, &ctx->ysum, &ctx->yavg, &ctx->yr, &ctx->tmp_m};
+  double** vecs_n[] = {&ctx->c, &ctx->ch, &ctx->dc, &ctx->idc, &ctx->x, &ctx->xbar, &ctx->xsum, &ctx->xavg,
+                       &ctx->xr, &ctx->tmp_n, &ctx->tmp_n2};
+  double** vecs_m[] = {&ctx->b, &ctx->bh, &ctx->dr, &ctx->idr, &ctx->y, &ctx->ysum, &ctx->yavg, &ctx->yr,
+                       &ctx->tmp_m};
   for (double** p : vecs_n) CK(ctx, dalloc(ctx, p, n));
   for (double** p : vecs_m) CK(ctx, dalloc(ctx, p, m));
   ctx->nb_eval = ctx->nblocks;
@@ -1035,6 +1040,8 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
   }
   launch_mul(ctx->bh, ctx->dr, ctx->b, (int)m, gm, s);
   launch_mul(ctx->ch, ctx->dc, ctx->c, (int)n, gn, s);
+  launch_reciprocal(ctx->idr, ctx->dr, (int)m, gm, s);
+  launch_reciprocal(ctx->idc, ctx->dc, (int)n, gn, s);
 
   // power iteration, norms and step sizes per instance
   const int gx = std::max(1, std::min(64, (int)(n / count / TPB + 1)));
@@ -1076,7 +1083,7 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
   launch_fill(ctx->yr, 0.0, m, gm, s);
   launch_fill(ctx->xavg, 0.0, n, gn, s);
   launch_fill(ctx->yavg, 0.0, m, gm, s);
-  launch_eval_point(A, At, ctx->x, ctx->y, ctx->bh, ctx->ch, ctx->dr, ctx->dc, nullptr, nullptr, ctx->partials,
+  launch_eval_point(A, At, ctx->x, ctx->y, ctx->bh, ctx->ch, ctx->idr, ctx->idc, nullptr, nullptr, ctx->partials,
                     ctx->nblocks, s, ctx->st, ctx->binst);
   launch_eval_finalize_b(ctx->partials, ctx->bstart, count, &ctx->st->cur, sizeof(DevState), s);
   launch_init_restart_ref_b(ctx->st, count, s);
@@ -1097,11 +1104,11 @@ void eval_batch(pdhg_ctx* ctx) {
   if (ctx->opt.restarts) {
     launch_make_average_b(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xoff, ctx->yoff, ctx->st,
                           count, gx, s);
-    launch_eval_point(ctx->A, ctx->At, ctx->xavg, ctx->yavg, ctx->bh, ctx->ch, ctx->dr, ctx->dc, ctx->xr, ctx->yr,
+    launch_eval_point(ctx->A, ctx->At, ctx->xavg, ctx->yavg, ctx->bh, ctx->ch, ctx->idr, ctx->idc, ctx->xr, ctx->yr,
                       ctx->partials, ctx->nblocks, s, ctx->st, ctx->binst);
     launch_eval_finalize_b(ctx->partials, ctx->bstart, count, &ctx->st->avg, sizeof(DevState), s);
   }
-  launch_eval_point(ctx->A, ctx->At, ctx->x, ctx->y, ctx->bh, ctx->ch, ctx->dr, ctx->dc, ctx->xr, ctx->yr,
+  launch_eval_point(ctx->A, ctx->At, ctx->x, ctx->y, ctx->bh, ctx->ch, ctx->idr, ctx->idc, ctx->xr, ctx->yr,
                     ctx->partials, ctx->nblocks, s, ctx->st, ctx->binst);
   launch_eval_finalize_b(ctx->partials, ctx->bstart, count, &ctx->st->cur, sizeof(DevState), s);
   launch_decide_b(ctx->st, count, s);
@@ -1166,9 +1173,9 @@ pdhg_status iterate_persistent(pdhg_ctx* ctx, int64_t max_iters, double tol, int
   a.yr = ctx->yr;
   a.yavg = ctx->yavg;
   a.ch = ctx->ch;
-  a.dc = ctx->dc;
+  a.idc = ctx->idc;
   a.bh = ctx->bh;
-  a.dr = ctx->dr;
+  a.idr = ctx->idr;
   ctx->converged = false;
   int64_t done = 0;
   while (done < max_iters) {

@@ -89,8 +89,8 @@ __device__ __forceinline__ void cta_dot(const Hyb& H, int u0, int u1, const Shar
 
 // shared-memory vectors of the block's LP, indexed locally
 struct Vecs {
-  double *x, *xbar, *xsum, *xr, *ch, *dc, *xa;  // n each
-  double *y, *ysum, *yr, *bh, *dr, *ya;         // m each
+  double *x, *xbar, *xsum, *xr, *ch, *idc, *xa;  // n each (idc = 1 / D_c)
+  double *y, *ysum, *yr, *bh, *idr, *ya;         // m each (idr = 1 / D_r)
   int x0, n, y0, m;
 };
 
@@ -130,7 +130,7 @@ struct EvalDual {
     const double c = v.ch[j];
     const double rd = relu(g - c);
     const double zh = relu(c - g);
-    const double rdu = rd / v.dc[j];
+    const double rdu = rd * v.idc[j];
     const double xj = px[j];
     const double d = xj - v.xr[j];
     acc[Q_RD2S] += rd * rd;
@@ -150,7 +150,7 @@ struct EvalPrimal {
     const int i = row - v.y0;
     const double b = v.bh[i];
     const double rp = b - h;
-    const double rpu = rp / v.dr[i];
+    const double rpu = rp * v.idr[i];
     const double yi = py[i];
     const double d = yi - v.yr[i];
     acc[Q_RP2S] += rp * rp;
@@ -200,13 +200,13 @@ __global__ void __launch_bounds__(PERSIST_TPB, 1)
   v.xsum = sh + 2 * v.n;
   v.xr = sh + 3 * v.n;
   v.ch = sh + 4 * v.n;
-  v.dc = sh + 5 * v.n;
+  v.idc = sh + 5 * v.n;
   v.xa = sh + 6 * v.n;
   v.y = sh + 7 * v.n;
   v.ysum = v.y + v.m;
   v.yr = v.y + 2 * v.m;
   v.bh = v.y + 3 * v.m;
-  v.dr = v.y + 4 * v.m;
+  v.idr = v.y + 4 * v.m;
   v.ya = v.y + 5 * v.m;
   for (int j = threadIdx.x; j < v.n; j += blockDim.x) {
     const int g = v.x0 + j;
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(PERSIST_TPB, 1)
     v.xsum[j] = a.xsum[g];
     v.xr[j] = a.xr[g];
     v.ch[j] = a.ch[g];
-    v.dc[j] = a.dc[g];
+    v.idc[j] = a.idc[g];
     v.xa[j] = a.xavg[g];
   }
   for (int i = threadIdx.x; i < v.m; i += blockDim.x) {
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(PERSIST_TPB, 1)
     v.ysum[i] = a.ysum[g];
     v.yr[i] = a.yr[g];
     v.bh[i] = a.bh[g];
-    v.dr[i] = a.dr[g];
+    v.idr[i] = a.idr[g];
     v.ya[i] = a.yavg[g];
   }
   long long k = st->k, t = st->t;
@@ -251,9 +251,9 @@ __global__ void __launch_bounds__(PERSIST_TPB, 1)
 
     // evaluation: the average (restarts on) and the current point
     if (a.restarts) {
-      const double td = (double)t;
-      for (int j = threadIdx.x; j < v.n; j += blockDim.x) v.xa[j] = t > 0 ? v.xsum[j] / td : v.x[j];
-      for (int i = threadIdx.x; i < v.m; i += blockDim.x) v.ya[i] = t > 0 ? v.ysum[i] / td : v.y[i];
+      const double it = t > 0 ? 1.0 / (double)t : 0.0;
+      for (int j = threadIdx.x; j < v.n; j += blockDim.x) v.xa[j] = t > 0 ? v.xsum[j] * it : v.x[j];
+      for (int i = threadIdx.x; i < v.m; i += blockDim.x) v.ya[i] = t > 0 ? v.ysum[i] * it : v.y[i];
       __syncthreads();
       eval_point(A, At, ua0, ua1, ut0, ut1, v, v.xa, v.ya, &st->avg);
     }
