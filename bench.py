@@ -241,8 +241,14 @@ def run_batch(P, torch, count=256, tol=1e-6, seed=0):
 
     sizes = lpgen.batch_sizes(seed, count)
     lps = [lpgen.batch_lp(seed, i, m) for i, m in enumerate(sizes)]
+    # layout autotuner: time candidate block shapes on this batch (no cache,
+    # so that every run measures), then solve with the choice
     t0 = time.perf_counter()
-    bs = P.BatchSolver(lps)
+    tuned, _ = P.pdhg_autotune(lps)
+    tune_s = time.perf_counter() - t0
+    layout = {k: getattr(tuned, k) for k in ("step_block", "rows_per_thread", "long_row_min")}
+    t0 = time.perf_counter()
+    bs = P.BatchSolver(lps, **layout)
     setup_s = time.perf_counter() - t0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -261,7 +267,7 @@ def run_batch(P, torch, count=256, tol=1e-6, seed=0):
             "seconds_to_all_converged": sec, "setup_s": setup_s, "all_converged": bool(info["converged"].all()),
             "iterations_max": int(it.max()), "iterations_median": float(np.median(it)),
             "aggregate_iters_per_s": float(it.sum() / sec), "hbm_gbs_active": gbs, "hbm_frac_active": gbs / peak,
-            "gpu_launches": eng["kernel_launches"]}
+            "gpu_launches": eng["kernel_launches"], "autotuned_layout": layout, "autotune_s": tune_s}
 
 
 # ---------------------------------------------------------------------------

@@ -97,7 +97,8 @@ typedef struct {
                              iterations, evaluations, restarts and termination test with the LP's vectors in
                              shared memory (LPs with 7n + 6m <= 28672, i.e. up to ~224 KiB of vectors; FP64,
                              no recording, no kernel timing); 0: two launches per iteration (0) */
-  int reserved[7];
+  int step_block;         /* threads per block of the step and evaluation kernels: 128, 256 or 512 (256) */
+  int reserved[6];
 } pdhg_options;
 
 /* Scalars of one point on the problem as given (unscaled), all FP64.
@@ -268,6 +269,28 @@ PDHG_API pdhg_status pdhg_batch_info(pdhg_ctx* ctx, int64_t* iterations, int* co
 /* (x, y, z) of one instance on its problem as given, into host buffers of its
  * n, m, n (any may be NULL). */
 PDHG_API pdhg_status pdhg_batch_solution(pdhg_ctx* ctx, int instance, double* x, double* y, double* z);
+
+/* Layout autotuner (no counterpart in the paper: a tuning aid for the step
+ * kernels). Times the two step kernels with CUDA events on this LP (count = 1)
+ * or batch (count > 1) for candidate layouts, by coordinate search over
+ * long_row_min in {32, 64, 128, 256, 512}, then rows_per_thread in {1, 2, 4},
+ * then step_block in {128, 256, 512}, each starting from the best so far, and
+ * writes into *tuned a copy of *opt (defaults if NULL) with the fastest three.
+ * With cache_path != NULL, a choice stored there for an LP of the same profile
+ * (see pdhg_profile_key) is returned without any device work (*from_cache = 1;
+ * from_cache may be NULL), and a newly timed choice is appended as one line
+ * "key step_block rows_per_thread long_row_min ms_per_iteration". Host inputs
+ * only; each candidate builds and frees its own context on cuda_stream. */
+PDHG_API pdhg_status pdhg_autotune(int count, const pdhg_lp_desc* lps, const pdhg_options* opt,
+                                   const char* cache_path, void* cuda_stream, pdhg_options* tuned,
+                                   int* from_cache);
+
+/* The profile under which pdhg_autotune stores its choice, into buf (at most
+ * cap bytes including the terminating NUL): precision, the number of
+ * instances, m, n and nnz on a log2 scale in steps of 1/2, and the share of
+ * the rows of A and of A^T in each power-of-two length class, rounded to 10%.
+ * Host logic only. */
+PDHG_API pdhg_status pdhg_profile_key(int count, const pdhg_lp_desc* lps, int precision, char* buf, int64_t cap);
 
 /* Description of the last failure of ctx, or of the last failed context-free
  * call (pdhg_create, pdhg_kkt_noalloc) when ctx is NULL. Never NULL. */

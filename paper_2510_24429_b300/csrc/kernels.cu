@@ -22,7 +22,8 @@
 
 // Minimum resident blocks per SM requested for the two step kernels. The
 // kernels are latency bound, so occupancy matters more than registers: with
-// 6 blocks of 256 threads (<= 40 registers) they ran ~1.9x faster on the
+// 6 blocks of 256 threads (<= 40 registers; the bound is written for the
+// largest block, 512 threads x 3) they ran ~1.9x faster on the
 // large LP than with the compiler's free choice (80 registers, 3 blocks).
 // The epilogue loads are issued when a row finishes (not prefetched) so the
 // 40 registers suffice without spills.
@@ -415,7 +416,7 @@ __device__ __forceinline__ const DevState* block_state(const DevState* sts, cons
 }
 
 template <class T>
-__global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
     k_primal_step(Hyb At, const T* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
                   T* __restrict__ x, T* __restrict__ xbar, T* __restrict__ xsum, const DevState* __restrict__ sts,
                   const int* __restrict__ binst, int accumulate) {
@@ -442,7 +443,7 @@ struct DualOp {
 };
 
 template <class T>
-__global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
     k_dual_step(Hyb A, const T* __restrict__ vals, const T* __restrict__ xbar, const T* __restrict__ bh,
                 T* __restrict__ y, T* __restrict__ ysum, const DevState* __restrict__ sts,
                 const int* __restrict__ binst, int accumulate) {
@@ -514,7 +515,7 @@ struct EvalDualOp {
   }
 };
 
-__global__ void __launch_bounds__(TPB) k_eval_dual(Hyb At, const double* __restrict__ py,
+__global__ void __launch_bounds__(STEP_TPB_MAX) k_eval_dual(Hyb At, const double* __restrict__ py,
                                                    const double* __restrict__ ch, const double* __restrict__ idc,
                                                    const double* __restrict__ px, const double* __restrict__ xr,
                                                    double* __restrict__ partials, const DevState* __restrict__ sts,
@@ -566,7 +567,7 @@ struct EvalPrimalOp {
   }
 };
 
-__global__ void __launch_bounds__(TPB) k_eval_primal(Hyb A, const double* __restrict__ px,
+__global__ void __launch_bounds__(STEP_TPB_MAX) k_eval_primal(Hyb A, const double* __restrict__ px,
                                                      const double* __restrict__ bh, const double* __restrict__ idr,
                                                      const double* __restrict__ py, const double* __restrict__ yr,
                                                      double* __restrict__ partials, const DevState* __restrict__ sts,
@@ -868,7 +869,7 @@ struct AdjPrimalOp {
 };
 
 template <class T>
-__global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
     k_adj_primal(Hyb At, const T* __restrict__ vals, const T* __restrict__ gy, const T* __restrict__ xnext,
                  T* __restrict__ gx, T* __restrict__ gu, T* __restrict__ gch, const DevState* __restrict__ st) {
   AdjPrimalOp<T> op{xnext, gx, gu, gch, (T)st->sigma, (T)st->tau};
@@ -890,7 +891,7 @@ struct AdjDualOp {
 };
 
 template <class T>
-__global__ void __launch_bounds__(TPB, PDHG_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
     k_adj_dual(Hyb A, const T* __restrict__ vals, const T* __restrict__ gu, T* __restrict__ gy, T* __restrict__ gbh,
                const DevState* __restrict__ st) {
   AdjDualOp<T> op{gy, gbh, (T)st->sigma, (T)st->tau};
@@ -986,20 +987,20 @@ void launch_finish_setup(DevState* st, const double* scal, double step_factor, i
   k_finish_setup<<<1, 1, 0, s>>>(st, scal, step_factor, primal_weight);
 }
 void launch_primal_step(const Hyb& At, const double* y, const double* ch, double* x, double* xbar, double* xsum,
-                        const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst) {
-  k_primal_step<double><<<grid, TPB, 0, s>>>(At, At.v, y, ch, x, xbar, xsum, st, binst, accumulate);
+                        const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst, int tpb) {
+  k_primal_step<double><<<grid, tpb, 0, s>>>(At, At.v, y, ch, x, xbar, xsum, st, binst, accumulate);
 }
 void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
-                      const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst) {
-  k_dual_step<double><<<grid, TPB, 0, s>>>(A, A.v, xbar, bh, y, ysum, st, binst, accumulate);
+                      const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst, int tpb) {
+  k_dual_step<double><<<grid, tpb, 0, s>>>(A, A.v, xbar, bh, y, ysum, st, binst, accumulate);
 }
 void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float* x, float* xbar, float* xsum,
-                          const DevState* st, int accumulate, int grid, cudaStream_t s) {
-  k_primal_step<float><<<grid, TPB, 0, s>>>(At, At.v32, y, ch, x, xbar, xsum, st, nullptr, accumulate);
+                          const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb) {
+  k_primal_step<float><<<grid, tpb, 0, s>>>(At, At.v32, y, ch, x, xbar, xsum, st, nullptr, accumulate);
 }
 void launch_dual_step32(const Hyb& A, const float* xbar, const float* bh, float* y, float* ysum, const DevState* st,
-                        int accumulate, int grid, cudaStream_t s) {
-  k_dual_step<float><<<grid, TPB, 0, s>>>(A, A.v32, xbar, bh, y, ysum, st, nullptr, accumulate);
+                        int accumulate, int grid, cudaStream_t s, int tpb) {
+  k_dual_step<float><<<grid, tpb, 0, s>>>(A, A.v32, xbar, bh, y, ysum, st, nullptr, accumulate);
 }
 void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,
                           const DevState* st, int accumulate, int grid, cudaStream_t s) {
@@ -1012,9 +1013,9 @@ void launch_make_average(const double* xs, const double* ys, const double* x, co
 }
 void launch_eval_point(const Hyb& A, const Hyb& At, const double* px, const double* py, const double* bh,
                        const double* ch, const double* idr, const double* idc, const double* xr, const double* yr,
-                       double* partials, int nb, cudaStream_t s, const DevState* sts, const int* binst) {
-  k_eval_dual<<<nb, TPB, 0, s>>>(At, py, ch, idc, px, xr, partials, sts, binst);
-  k_eval_primal<<<nb, TPB, 0, s>>>(A, px, bh, idr, py, yr, partials, sts, binst);
+                       double* partials, int nb, cudaStream_t s, const DevState* sts, const int* binst, int tpb) {
+  k_eval_dual<<<nb, tpb, 0, s>>>(At, py, ch, idc, px, xr, partials, sts, binst);
+  k_eval_primal<<<nb, tpb, 0, s>>>(A, px, bh, idr, py, yr, partials, sts, binst);
 }
 void launch_decide_b(DevState* sts, int count, cudaStream_t s) { k_decide_b<<<(count + 127) / 128, 128, 0, s>>>(sts, count); }
 void launch_add_counters_b(DevState* sts, int count, long long dk, cudaStream_t s) {

@@ -7,6 +7,7 @@ namespace pdhg {
 
 constexpr int TPB = 256;  // threads per block of every row kernel
 constexpr int WARPS_PER_BLOCK = TPB / 32;
+constexpr int STEP_TPB_MAX = 512;  // largest block of the step and evaluation kernels (option step_block)
 constexpr int HOT_TPB = 1024;       // threads per block of the persistent dual step
 constexpr int HOT_MAX = 24576;      // most xbar entries it stages in shared memory (192 KiB)
 
@@ -36,16 +37,18 @@ void launch_finish_setup(DevState* st, const double* scal, double step_factor, i
 // st: the problem's state; for a batch, the instances' states and binst maps
 // every block to its instance (blocks of converged instances return at once)
 void launch_primal_step(const Hyb& At, const double* y, const double* ch, double* x, double* xbar, double* xsum,
-                        const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst = nullptr);
+                        const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst = nullptr,
+                        int tpb = TPB);
 // y' = y + sigma (bhat - Ahat xbar); y <- y'; ysum += y'
 void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
-                      const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst = nullptr);
+                      const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst = nullptr,
+                      int tpb = TPB);
 // the same two half-steps in FP32 (values At.v32 / A.v32, FP32 vectors and
 // accumulation); tau and sigma are read from the FP64 state and rounded
 void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float* x, float* xbar, float* xsum,
-                          const DevState* st, int accumulate, int grid, cudaStream_t s);
+                          const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb = TPB);
 void launch_dual_step32(const Hyb& A, const float* xbar, const float* bh, float* y, float* ysum, const DevState* st,
-                        int accumulate, int grid, cudaStream_t s);
+                        int accumulate, int grid, cudaStream_t s, int tpb = TPB);
 // precision conversions and the FP32 counterparts of make_average / apply
 void launch_narrow(float* dst, const double* src, long long len, int grid, cudaStream_t s);
 void launch_widen(double* dst, const float* src, long long len, int grid, cudaStream_t s);
@@ -80,7 +83,7 @@ void launch_make_average(const double* xs, const double* ys, const double* x, co
 void launch_eval_point(const Hyb& A, const Hyb& At, const double* px, const double* py, const double* bh,
                        const double* ch, const double* idr, const double* idc, const double* xr, const double* yr,
                        double* partials, int nb, cudaStream_t s, const DevState* sts = nullptr,
-                       const int* binst = nullptr);
+                       const int* binst = nullptr, int tpb = TPB);
 // ---- batch (count instances; xoff/yoff: instance ranges of the column and row vectors) ----
 void launch_decide_b(DevState* sts, int count, cudaStream_t s);
 void launch_add_counters_b(DevState* sts, int count, long long dk, cudaStream_t s);

@@ -73,6 +73,8 @@ struct pdhg_ctx {
   // the shared memory of the single-block solve loop
   int* ustart = nullptr;
   size_t persist_smem = 0;
+  // warps per block of the step and evaluation kernels (option step_block)
+  int wpb = WARPS_PER_BLOCK;
   // CUDA graphs of one evaluation block, per precision phase (FP64, FP32)
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   int64_t graph_launches[2] = {0, 0};
@@ -147,12 +149,12 @@ int vec_grid(const pdhg_ctx* ctx, long long len) {
 }
 
 // one unit (long row or 32-row slice) per warp
-int unit_grid(const Hyb& H) {
-  return std::max(1, (H.units() + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+int unit_grid(const pdhg_ctx* ctx, const Hyb& H) {
+  return std::max(1, (H.units() + ctx->wpb - 1) / ctx->wpb);
 }
 
 // grid-stride launches (setup and evaluation kernels)
-int stride_grid(const pdhg_ctx* ctx, const Hyb& H) { return std::min(unit_grid(H), ctx->sms * 8); }
+int stride_grid(const pdhg_ctx* ctx, const Hyb& H) { return std::min(unit_grid(ctx, H), ctx->sms * 8); }
 
 pdhg_status set_device(pdhg_ctx* ctx) {
   int cur = -1;
@@ -244,7 +246,7 @@ pdhg_status read_state(pdhg_ctx* ctx) {
 void eval_point(pdhg_ctx* ctx, const double* px, const double* py, const double* xr, const double* yr,
                 EvalSums* dst) {
   launch_eval_point(ctx->A, ctx->At, px, py, ctx->bh, ctx->ch, ctx->idr, ctx->idc, xr, yr, ctx->partials,
-                    ctx->nb_eval, ctx->stream);
+                    ctx->nb_eval, ctx->stream, nullptr, nullptr, 32 * ctx->wpb);
   launch_eval_finalize(ctx->partials, ctx->nb_eval, dst, ctx->stream);
 }
 
@@ -311,7 +313,7 @@ pdhg_status backward_impl(pdhg_ctx* ctx, const double* dx, const double* dy, dou
   T *wx = (T*)ctx->w_x, *wy = (T*)ctx->w_y, *wxbar = (T*)ctx->w_xbar, *seg = (T*)ctx->w_seg;
   T *gx = (T*)ctx->g_x, *gy = (T*)ctx->g_y, *gu = (T*)ctx->g_u, *gch = (T*)ctx->g_ch, *gbh = (T*)ctx->g_bh;
   const int gn = vec_grid(ctx, n), gm = vec_grid(ctx, m);
-  const int grT = unit_grid(ctx->At), grA = unit_grid(ctx->A);
+  const int grT = unit_grid(ctx, ctx->At), grA = unit_grid(ctx, ctx->A), tpb = 32 * ctx->wpb;
   launch_adj_seed<T>(gx, dx, ctx->perm_x, ctx->dc, (int)n, gn, s);
   launch_adj_seed<T>(gy, dy, ctx->perm_y, ctx->dr, (int)m, gm, s);
   CK(ctx, cudaMemsetAsync(gch, 0, sizeof(T) * n, s));
@@ -324,12 +326,13 @@ pdhg_status backward_impl(pdhg_ctx* ctx, const double* dx, const double* dy, dou
     for (int64_t k = start; k < end; ++k) {
       if (f32) {
         launch_primal_step32(ctx->At, (const float*)wy, ctx->ch32, (float*)wx, (float*)wxbar, nullptr, ctx->st, 0,
-                             grT, s);
-        launch_dual_step32(ctx->A, (const float*)wxbar, ctx->bh32, (float*)wy, nullptr, ctx->st, 0, grA, s);
+                             grT, s, tpb);
+        launch_dual_step32(ctx->A, (const float*)wxbar, ctx->bh32, (float*)wy, nullptr, ctx->st, 0, grA, s, tpb);
       } else {
         launch_primal_step(ctx->At, (const double*)wy, ctx->ch, (double*)wx, (double*)wxbar, nullptr, ctx->st, 0,
-                           grT, s);
-        launch_dual_step(ctx->A, (const double*)wxbar, ctx->bh, (double*)wy, nullptr, ctx->st, 0, grA, s);
+                           grT, s, nullptr, tpb);
+        launch_dual_step(ctx->A, (const double*)wxbar, ctx->bh, (double*)wy, nullptr, ctx->st, 0, grA, s, nullptr,
+                         tpb);
       }
       CK(ctx, cudaMemcpyAsync(seg + (k - start) * n, wx, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
     }
@@ -576,9 +579,9 @@ pdhg_status build_layouts(pdhg_ctx* ctx, Scratch& sc, const long long* lrp, cons
     if (batch) {
       // both layouts get the same whole number of blocks for this instance
       const int units = std::max(uA.n_units(), uT.n_units()) - before;
-      const int blocks = (units + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
-      pad_units_to(uA, before + blocks * WARPS_PER_BLOCK, (int)M);
-      pad_units_to(uT, before + blocks * WARPS_PER_BLOCK, (int)N);
+      const int blocks = (units + ctx->wpb - 1) / ctx->wpb;
+      pad_units_to(uA, before + blocks * ctx->wpb, (int)M);
+      pad_units_to(uT, before + blocks * ctx->wpb, (int)N);
       ctx->bstart_h[inst + 1] = ctx->bstart_h[inst] + blocks;
       for (int b = 0; b < blocks; ++b) binst.push_back(inst);
     }
@@ -685,7 +688,7 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
                        &ctx->tmp_m};
   for (double** p : vecs_n) CK(ctx, dalloc(ctx, p, n));
   for (double** p : vecs_m) CK(ctx, dalloc(ctx, p, m));
-  ctx->nb_eval = std::max(1, std::min(ctx->sms * 16, std::max(unit_grid(A), unit_grid(At))));
+  ctx->nb_eval = std::max(1, std::min(ctx->sms * 16, std::max(unit_grid(ctx, A), unit_grid(ctx, At))));
   prefer_l1_for_step_kernels();
   CK(ctx, dalloc(ctx, &ctx->partials, (size_t)std::max(ctx->nb_eval, ctx->sms * 8) * NQ));
   CK(ctx, dalloc(ctx, &ctx->scal, 16));
@@ -834,7 +837,7 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
 pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
   const pdhg_options& o = ctx->opt;
   cudaStream_t s = ctx->stream;
-  const int grT = unit_grid(ctx->At), grA = unit_grid(ctx->A);
+  const int grT = unit_grid(ctx, ctx->At), grA = unit_grid(ctx, ctx->A), tpb = 32 * ctx->wpb;
   const int hot = (int)std::min<int64_t>(o.dual_hot_cols, ctx->n);
   for (int64_t it = 0; it < nb; ++it) {
     if (o.record_for_backward) {
@@ -844,16 +847,17 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
     if (ctx->phase32)
       launch_primal_step32(ctx->At, ctx->y32, ctx->ch32, ctx->x32, ctx->xbar32, ctx->xsum32, ctx->st, o.restarts,
-                           grT, s);
+                           grT, s, tpb);
     else
-      launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, grT, s);
+      launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, grT, s, nullptr,
+                         tpb);
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
     if (ctx->phase32)
-      launch_dual_step32(ctx->A, ctx->xbar32, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st, o.restarts, grA, s);
+      launch_dual_step32(ctx->A, ctx->xbar32, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st, o.restarts, grA, s, tpb);
     else if (hot > 0)
       launch_dual_step_hot(ctx->A, ctx->xbar, hot, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, ctx->sms, s);
     else
-      launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, grA, s);
+      launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, grA, s, nullptr, tpb);
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 2], s));
   }
   launch_add_counters(ctx->st, nb, s);
@@ -975,7 +979,7 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
   if (rs != PDHG_OK) return rs;
   {
     std::vector<int> ustart(count + 1);
-    for (int i = 0; i <= count; ++i) ustart[i] = ctx->bstart_h[i] * WARPS_PER_BLOCK;
+    for (int i = 0; i <= count; ++i) ustart[i] = ctx->bstart_h[i] * ctx->wpb;
     CK(ctx, dalloc(ctx, &ctx->ustart, count + 1));
     CK(ctx, cudaMemcpyAsync(ctx->ustart, ustart.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, s));
     CK(ctx, cudaStreamSynchronize(s));
@@ -1084,7 +1088,7 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
   launch_fill(ctx->xavg, 0.0, n, gn, s);
   launch_fill(ctx->yavg, 0.0, m, gm, s);
   launch_eval_point(A, At, ctx->x, ctx->y, ctx->bh, ctx->ch, ctx->idr, ctx->idc, nullptr, nullptr, ctx->partials,
-                    ctx->nblocks, s, ctx->st, ctx->binst);
+                    ctx->nblocks, s, ctx->st, ctx->binst, 32 * ctx->wpb);
   launch_eval_finalize_b(ctx->partials, ctx->bstart, count, &ctx->st->cur, sizeof(DevState), s);
   launch_init_restart_ref_b(ctx->st, count, s);
   CK(ctx, cudaGetLastError());
@@ -1105,11 +1109,11 @@ void eval_batch(pdhg_ctx* ctx) {
     launch_make_average_b(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xoff, ctx->yoff, ctx->st,
                           count, gx, s);
     launch_eval_point(ctx->A, ctx->At, ctx->xavg, ctx->yavg, ctx->bh, ctx->ch, ctx->idr, ctx->idc, ctx->xr, ctx->yr,
-                      ctx->partials, ctx->nblocks, s, ctx->st, ctx->binst);
+                      ctx->partials, ctx->nblocks, s, ctx->st, ctx->binst, 32 * ctx->wpb);
     launch_eval_finalize_b(ctx->partials, ctx->bstart, count, &ctx->st->avg, sizeof(DevState), s);
   }
   launch_eval_point(ctx->A, ctx->At, ctx->x, ctx->y, ctx->bh, ctx->ch, ctx->idr, ctx->idc, ctx->xr, ctx->yr,
-                    ctx->partials, ctx->nblocks, s, ctx->st, ctx->binst);
+                    ctx->partials, ctx->nblocks, s, ctx->st, ctx->binst, 32 * ctx->wpb);
   launch_eval_finalize_b(ctx->partials, ctx->bstart, count, &ctx->st->cur, sizeof(DevState), s);
   launch_decide_b(ctx->st, count, s);
   launch_apply_b(ctx->st, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, ctx->xsum, ctx->ysum, ctx->xoff,
@@ -1122,10 +1126,10 @@ pdhg_status enqueue_steps_batch(pdhg_ctx* ctx, int64_t nb, bool timing) {
   for (int64_t it = 0; it < nb; ++it) {
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
     launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, ctx->nblocks, s,
-                       ctx->binst);
+                       ctx->binst, 32 * ctx->wpb);
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
     launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, ctx->nblocks, s,
-                     ctx->binst);
+                     ctx->binst, 32 * ctx->wpb);
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 2], s));
   }
   launch_add_counters_b(ctx->st, ctx->count, nb, s);
@@ -1304,6 +1308,7 @@ void pdhg_default_options(pdhg_options* o) {
   o->dual_hot_cols = 0;
   o->record_for_backward = 0;
   o->checkpoint_every = 50;
+  o->step_block = 256;
 }
 
 pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
@@ -1331,6 +1336,8 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
   if (o.eval_every < 1 || o.ruiz_iters < 0 || o.power_iters < 1 || !(o.step_factor > 0.0) || o.pc_alpha < 0.0 ||
       o.pc_alpha > 2.0 || o.long_row_min < 1 || o.dual_hot_cols < 0 || o.dual_hot_cols > HOT_MAX || !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4) || o.snapshot_every < 0 || o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
     return fail(nullptr, PDHG_ERR_INVALID, "option out of range");
+  if (!(o.step_block == 0 || o.step_block == 128 || o.step_block == 256 || o.step_block == 512))
+    return fail(nullptr, PDHG_ERR_INVALID, "step_block must be 128, 256 or 512");
   if (o.persistent) {
     if (o.persistent != 1 || o.precision != PDHG_FP64 || o.record_for_backward || o.kernel_timing ||
         o.dual_hot_cols)
@@ -1356,6 +1363,7 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
   ctx->n = n;
   ctx->nnz = nnz;
   ctx->opt = o;
+  ctx->wpb = (o.step_block ? o.step_block : TPB) / 32;
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
   if (e == cudaSuccess) {
@@ -1672,6 +1680,8 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
       !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4))
     return fail(nullptr, PDHG_ERR_INVALID,
                 "batch: FP64, host inputs, no snapshots, no recording, no shared-memory hot columns, valid options");
+  if (!(o.step_block == 0 || o.step_block == 128 || o.step_block == 256 || o.step_block == 512))
+    return fail(nullptr, PDHG_ERR_INVALID, "step_block must be 128, 256 or 512");
   if (o.persistent != 0 && (o.persistent != 1 || o.kernel_timing))
     return fail(nullptr, PDHG_ERR_INVALID, "persistent must be 0 or 1, and 1 excludes kernel timing");
   int64_t mt = 0, nt = 0, zt = 0;
@@ -1698,6 +1708,7 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
   ctx->n = nt;
   ctx->nnz = zt;
   ctx->opt = o;
+  ctx->wpb = (o.step_block ? o.step_block : TPB) / 32;
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
   if (e == cudaSuccess) {

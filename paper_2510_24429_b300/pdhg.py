@@ -54,7 +54,8 @@ class pdhg_options(C.Structure):
         ("record_for_backward", C.c_int),
         ("checkpoint_every", C.c_int64),
         ("persistent", C.c_int),
-        ("reserved", C.c_int * 7),
+        ("step_block", C.c_int),
+        ("reserved", C.c_int * 6),
     ]
 
 
@@ -116,6 +117,9 @@ SIGNATURES = {
     "pdhg_batch_solution": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "pdhg_kkt_noalloc": (C.c_int, [C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P,
                                    C.POINTER(pdhg_kkt_info)]),
+    "pdhg_autotune": (C.c_int, [C.c_int, C.POINTER(pdhg_lp_desc), C.POINTER(pdhg_options), C.c_char_p, _P,
+                                C.POINTER(pdhg_options), C.POINTER(C.c_int)]),
+    "pdhg_profile_key": (C.c_int, [C.c_int, C.POINTER(pdhg_lp_desc), C.c_int, C.c_char_p, C.c_int64]),
 }
 
 
@@ -317,9 +321,10 @@ def pdhg_kkt_noalloc(m, n, a_row_ptr, a_col_idx, a_val, at_row_ptr, at_col_idx, 
     return {k: getattr(info, k) for k, _ in pdhg_kkt_info._fields_}
 
 
-def pdhg_create_batch(lps, opt: pdhg_options | None = None, stream=None):
-    """One context for many LPs; ``lps`` is a sequence of (m, n, row_ptr,
-    col_idx, val, b, c) tuples or objects with those attributes (host arrays)."""
+def _lp_descs(lps):
+    """pdhg_lp_desc array for a sequence of (m, n, row_ptr, col_idx, val, b, c)
+    tuples or objects with those attributes (host arrays); returns the array
+    and the list of numpy arrays it points into (keep it alive)."""
     keep: list = []
     descs = (pdhg_lp_desc * len(lps))()
     for d, lp in zip(descs, lps):
@@ -331,6 +336,32 @@ def pdhg_create_batch(lps, opt: pdhg_options | None = None, stream=None):
         keep.extend(arrs)
         d.m, d.n, d.nnz = int(m), int(n), int(len(arrs[2]))
         d.row_ptr, d.col_idx, d.val, d.b, d.c = [a.ctypes.data for a in arrs]
+    return descs, keep
+
+
+def pdhg_autotune(lps, opt: pdhg_options | None = None, cache_path: str | None = None, stream=None):
+    """Tuned layout options for one LP (a sequence of one) or a batch; returns
+    (options, from_cache)."""
+    descs, _keep = _lp_descs(lps)
+    if opt is None:
+        opt = pdhg_default_options()
+    tuned, hit = pdhg_options(), C.c_int(0)
+    _check(load().pdhg_autotune(len(lps), descs, C.byref(opt), cache_path.encode() if cache_path else None,
+                                C.c_void_p(stream) if stream else None, C.byref(tuned), C.byref(hit)), None)
+    return tuned, bool(hit.value)
+
+
+def pdhg_profile_key(lps, precision: int = 0) -> str:
+    descs, _keep = _lp_descs(lps)
+    buf = C.create_string_buffer(4096)
+    _check(load().pdhg_profile_key(len(lps), descs, int(precision), buf, len(buf)), None)
+    return buf.value.decode()
+
+
+def pdhg_create_batch(lps, opt: pdhg_options | None = None, stream=None):
+    """One context for many LPs; ``lps`` is a sequence of (m, n, row_ptr,
+    col_idx, val, b, c) tuples or objects with those attributes (host arrays)."""
+    descs, _keep = _lp_descs(lps)
     if opt is None:
         opt = pdhg_default_options()
     out = C.c_void_p()
