@@ -88,13 +88,6 @@ template <>
 struct Pair<float> {
   using type = float2;
 };
-__device__ __forceinline__ int4 ld_stream4(const int* p, unsigned long long pol) {
-  int4 r;
-  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
-      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-      : "l"(p), "l"(pol));
-  return r;
-}
 
 // Scalar visitor (setup kernels): every warp takes units in a grid-stride
 // loop; op.entry(acc, k, r) sees every slot k of row r (padding included:
@@ -187,53 +180,59 @@ __device__ __forceinline__ void slice_dot(const Hyb& H, const T* __restrict__ va
   }
 }
 
+// One unit of H (a long row, or a slice of 32*R rows) for the dot-product
+// visitor below.
+template <class T, class Op, class G>
+__device__ __forceinline__ void unit_dot(const Hyb& H, const T* __restrict__ vals, int u, const G& gather, Op& op,
+                                         unsigned long long pol, int lane) {
+  const int4 info = H.uinfo[u];
+  const long long beg = H.uoff[u], end = H.uoff[u + 1];
+  if (info.y == 0) {
+    const int row = info.x;
+    typename Op::State st{};
+    if (lane == 0) st = op.begin(row);
+    T acc = T(0);
+    // a step covers 128 entries as two contiguous 64-entry halves; lane L
+    // takes entries 2L, 2L+1 of each half, so every load instruction of the
+    // warp reads whole sectors (256 B of indices, 512 B of values)
+#pragma unroll 2
+    for (long long k = beg + 2 * lane; k < end; k += 128) {
+      const int2 c0 = ld_stream2(H.ci + k, pol);
+      const typename Pair<T>::type a = ld_stream2(vals + k, pol);
+      const bool second = k + 64 < end;
+      const int2 c1 = second ? ld_stream2(H.ci + k + 64, pol) : make_int2(0, 0);
+      typename Pair<T>::type b;
+      b.x = T(0);
+      b.y = T(0);
+      if (second) b = ld_stream2(vals + k + 64, pol);
+      const T g0 = gather(c0.x), g1 = gather(c0.y);
+      const T g2 = gather(c1.x), g3 = gather(c1.y);
+      acc += a.x * g0;
+      acc += a.y * g1;
+      acc += b.x * g2;
+      acc += b.y * g3;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) op.finish(row, acc, st);
+  } else {
+    const int Lp = (int)((end - beg) / (32 * info.y));
+    if (info.y == 4)
+      slice_dot<4>(H, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
+    else if (info.y == 2)
+      slice_dot<2>(H, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
+    else
+      slice_dot<1>(H, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
+  }
+}
+
+// every unit of H, one warp per unit in a grid-stride loop
 template <class T, class Op, class G>
 __device__ __forceinline__ void hyb_dot(const Hyb& H, const T* __restrict__ vals, const G& gather, Op& op) {
   const unsigned long long pol = stream_policy();
   const int lane = threadIdx.x & 31;
   const int gwarp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
-  for (int u = gwarp; u < H.n_units; u += nwarps) {
-    const int4 info = H.uinfo[u];
-    const long long beg = H.uoff[u], end = H.uoff[u + 1];
-    if (info.y == 0) {
-      const int row = info.x;
-      typename Op::State st{};
-      if (lane == 0) st = op.begin(row);
-      T acc = T(0);
-      // a step covers 128 entries as two contiguous 64-entry halves; lane L
-      // takes entries 2L, 2L+1 of each half, so every load instruction of the
-      // warp reads whole sectors (256 B of indices, 512 B of values)
-#pragma unroll 2
-      for (long long k = beg + 2 * lane; k < end; k += 128) {
-        const int2 c0 = ld_stream2(H.ci + k, pol);
-        const typename Pair<T>::type a = ld_stream2(vals + k, pol);
-        const bool second = k + 64 < end;
-        const int2 c1 = second ? ld_stream2(H.ci + k + 64, pol) : make_int2(0, 0);
-        typename Pair<T>::type b;
-        b.x = T(0);
-        b.y = T(0);
-        if (second) b = ld_stream2(vals + k + 64, pol);
-        const T g0 = gather(c0.x), g1 = gather(c0.y);
-        const T g2 = gather(c1.x), g3 = gather(c1.y);
-        acc += a.x * g0;
-        acc += a.y * g1;
-        acc += b.x * g2;
-        acc += b.y * g3;
-      }
-      acc = warp_sum(acc);
-      if (lane == 0) op.finish(row, acc, st);
-    } else {
-      const long long base = beg;
-      const int Lp = (int)((end - beg) / (32 * info.y));
-      if (info.y == 4)
-        slice_dot<4>(H, vals, info.x, info.z, base, Lp, gather, op, pol, lane);
-      else if (info.y == 2)
-        slice_dot<2>(H, vals, info.x, info.z, base, Lp, gather, op, pol, lane);
-      else
-        slice_dot<1>(H, vals, info.x, info.z, base, Lp, gather, op, pol, lane);
-    }
-  }
+  for (int u = gwarp; u < H.n_units; u += nwarps) unit_dot(H, vals, u, gather, op, pol, lane);
 }
 
 struct NoState {};
@@ -274,12 +273,23 @@ struct ScaleOp {
   double* __restrict__ v;
   const double* __restrict__ rf;  // row factors of A (length m)
   const double* __restrict__ sf;  // column factors of A (length n)
-  int transposed, rows;
+  int transposed;                 // 0: M is A; 1: M is A^T; 2: M is the panel layout of A^T
+  const int* __restrict__ pcol;   // panel layout: column of A of every segment row
+  const int* __restrict__ pbase;  // panel layout: first row of A of the segment row's panel
   __device__ __forceinline__ double entry(double acc, long long k, int r) const {
     if (r >= 0) {  // not a padding row
       const int c = ci[k];
-      const double ri = transposed ? rf[c] : rf[r];
-      const double sj = transposed ? sf[r] : sf[c];
+      double ri, sj;
+      if (transposed == 0) {
+        ri = rf[r];
+        sj = sf[c];
+      } else if (transposed == 1) {
+        ri = rf[c];
+        sj = sf[r];
+      } else {
+        ri = rf[pbase[r] + c];
+        sj = sf[pcol[r]];
+      }
       v[k] = (ri * v[k]) * sj;
     }
     return acc;
@@ -288,8 +298,9 @@ struct ScaleOp {
 };
 
 __global__ void __launch_bounds__(TPB) k_scale(Hyb M, const double* __restrict__ r, const double* __restrict__ s,
-                                               int transposed) {
-  ScaleOp op{M.ci, M.v, r, s, transposed, M.rows};
+                                               int transposed, const int* __restrict__ pcol,
+                                               const int* __restrict__ pbase) {
+  ScaleOp op{M.ci, M.v, r, s, transposed, pcol, pbase};
   hyb_rows<false>(M, op);
 }
 
@@ -424,6 +435,88 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STE
   if (st->frozen) return;
   PrimalOp<T> op{ch, x, xbar, xsum, (T)st->tau, accumulate};
   hyb_dot(At, vals, GlobalGather<T>{y}, op);
+}
+
+// ---- panel-tiled primal half-step (option primal_panels) --------------------
+// The rows of A^T are cut into segments by panels of panel_rows consecutive
+// entries of y. Pass 1: every block stages one panel of y in shared memory and
+// reduces its panel's segments (Hyb layout Pn, local row indices) with the
+// gathers served from shared memory, writing one partial sum per segment at
+// its column-major position. Pass 2: one thread per column adds its partial
+// sums in panel order and applies the primal update. The random gathers of y
+// that bound k_primal_step (one L2 request each) become shared-memory reads,
+// and the L2 traffic left is the partial sums' writes and coalesced reads.
+template <class T>
+struct SmemGather {
+  const T* s;
+  __device__ __forceinline__ T operator()(int c) const { return s[c]; }
+};
+
+// the output position of a segment row is loaded when the row starts, so its
+// latency overlaps the entries' loads
+template <class T>
+struct PartialOp {
+  struct State {
+    int pos;
+  };
+  T* __restrict__ partial;
+  const int* __restrict__ segout;
+  __device__ __forceinline__ State begin(int r) { return {__ldg(segout + r)}; }
+  __device__ __forceinline__ void finish(int, T acc, const State& st) { partial[st.pos] = acc; }
+};
+
+// FP32 panels take half the shared memory, so two blocks could share an SM
+template <class T>
+__global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
+    k_primal_panels(Hyb Pn, const T* __restrict__ vals, const T* __restrict__ y, int m, int H, int kpp,
+                    const int* __restrict__ ustart, const int* __restrict__ segout, T* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char panel_smem[];
+  T* ys = reinterpret_cast<T*>(panel_smem);
+  const int p = blockIdx.x / kpp, sub = blockIdx.x - p * kpp;
+  const int i0 = p * H, len = min(H, m - i0);
+  // the panel of y into shared memory with asynchronous 16-byte copies, all in
+  // flight at once, when the panel starts on a 16-byte boundary (the default
+  // panel height is a multiple of 16 entries); the rest with plain loads
+  {
+    constexpr int PER = 16 / (int)sizeof(T);
+    const T* src = y + i0;
+    const int nv = (reinterpret_cast<unsigned long long>(src) & 15ull) == 0 ? len / PER : 0;
+    const unsigned dst0 = (unsigned)__cvta_generic_to_shared(ys);
+    for (int v = threadIdx.x; v < nv; v += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst0 + 16u * (unsigned)v), "l"(src + v * PER)
+                   : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    for (int t = nv * PER + threadIdx.x; t < len; t += blockDim.x) ys[t] = src[t];
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  }
+  __syncthreads();
+  const unsigned long long pol = stream_policy();
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  PartialOp<T> op{partial, segout};
+  const int u1 = ustart[p + 1];
+  for (int u = ustart[p] + sub * nw + (threadIdx.x >> 5); u < u1; u += kpp * nw)
+    unit_dot(Pn, vals, u, SmemGather<T>{ys}, op, pol, lane);
+}
+
+// one thread per column; the update's operands are loaded before the partial
+// sums so that their latencies overlap (same arithmetic as PrimalOp)
+template <class T>
+__global__ void __launch_bounds__(TPB) k_primal_combine(const int* __restrict__ cptr, const T* __restrict__ partial,
+                                                        const T* __restrict__ ch, T* __restrict__ x,
+                                                        T* __restrict__ xbar, T* __restrict__ xsum, int n,
+                                                        const DevState* __restrict__ st, int accumulate) {
+  const T tau = (T)st->tau;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    const T xj = __ldcs(x + j), cj = __ldcs(ch + j);
+    const T sj = accumulate ? __ldcs(xsum + j) : T(0);
+    const int q0 = __ldg(cptr + j), q1 = __ldg(cptr + j + 1);
+    T g = T(0);
+    for (int q = q0; q < q1; ++q) g += __ldcs(partial + q);
+    const T xn = relu(xj - tau * (cj - g));
+    xbar[j] = T(2) * xn - xj;  // default policy: gathered by the dual step next
+    __stcs(x + j, xn);
+    if (accumulate) __stcs(xsum + j, sj + xn);
+  }
 }
 
 template <class T>
@@ -955,8 +1048,9 @@ void launch_row_abspow_sum(const Hyb& M, double alpha, double* out, int grid, cu
 void launch_inv_sqrt_or_one(const double* in, double* out, int len, int grid, cudaStream_t s) {
   k_inv_sqrt_or_one<<<grid, TPB, 0, s>>>(in, out, len);
 }
-void launch_scale(const Hyb& M, const double* r, const double* s, int transposed, int grid, cudaStream_t st) {
-  k_scale<<<grid, TPB, 0, st>>>(M, r, s, transposed);
+void launch_scale(const Hyb& M, const double* r, const double* s, int transposed, int grid, cudaStream_t st,
+                  const int* pcol, const int* pbase) {
+  k_scale<<<grid, TPB, 0, st>>>(M, r, s, transposed, pcol, pbase);
 }
 void launch_mul_inplace(double* d, const double* f, int len, int grid, cudaStream_t s) {
   k_mul_inplace<<<grid, TPB, 0, s>>>(d, f, len);
@@ -1002,6 +1096,29 @@ void launch_dual_step32(const Hyb& A, const float* xbar, const float* bh, float*
                         int accumulate, int grid, cudaStream_t s, int tpb) {
   k_dual_step<float><<<grid, tpb, 0, s>>>(A, A.v32, xbar, bh, y, ysum, st, nullptr, accumulate);
 }
+cudaError_t configure_primal_panels() {
+  cudaError_t e = cudaFuncSetAttribute(k_primal_panels<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       PANEL_SMEM_MAX);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_primal_panels<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_MAX);
+  return e;
+}
+template <class T>
+cudaError_t launch_primal_panels(const Hyb& Pn, const T* vals, const PanelLayout& L, const T* y, const T* ch, T* x,
+                                 T* xbar, T* xsum, T* partial, const DevState* st, int accumulate, int kpp, int n,
+                                 int grid_n, cudaStream_t s) {
+  const size_t smem = sizeof(T) * (size_t)L.rows;
+  k_primal_panels<T><<<L.panels * kpp, PANEL_TPB, smem, s>>>(Pn, vals, y, L.m, L.rows, kpp, L.ustart, L.segout,
+                                                              partial);
+  k_primal_combine<T><<<(n + TPB - 1) / TPB, TPB, 0, s>>>(L.cptr, partial, ch, x, xbar, xsum, n, st, accumulate);
+  return cudaGetLastError();
+}
+template cudaError_t launch_primal_panels<double>(const Hyb&, const double*, const PanelLayout&, const double*,
+                                                  const double*, double*, double*, double*, double*,
+                                                  const DevState*, int, int, int, int, cudaStream_t);
+template cudaError_t launch_primal_panels<float>(const Hyb&, const float*, const PanelLayout&, const float*,
+                                                 const float*, float*, float*, float*, float*, const DevState*, int,
+                                                 int, int, int, cudaStream_t);
 void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,
                           const DevState* st, int accumulate, int grid, cudaStream_t s) {
   k_dual_step_hot<<<grid, HOT_TPB, (size_t)hot * sizeof(double), s>>>(A, xbar, hot, bh, y, ysum, st, accumulate);

@@ -15,10 +15,13 @@ constexpr int HOT_MAX = 24576;      // most xbar entries it stages in shared mem
 void launch_row_absmax(const Hyb& M, double* out, int grid, cudaStream_t s);
 void launch_row_abspow_sum(const Hyb& M, double alpha, double* out, int grid, cudaStream_t s);
 void launch_inv_sqrt_or_one(const double* in, double* out, int len, int grid, cudaStream_t s);
-// transposed == 0: M is Ahat (rows i, cols j); 1: M is Ahat^T (rows j, cols i).
-// Every entry becomes (r_i * a_ij) * s_j, the same operation order in both
-// layouts so that the two copies of Ahat stay bit-identical.
-void launch_scale(const Hyb& M, const double* r, const double* s, int transposed, int grid, cudaStream_t st);
+// transposed == 0: M is Ahat (rows i, cols j); 1: M is Ahat^T (rows j, cols i);
+// 2: M is the panel layout of Ahat^T (segment row r: column pcol[r], local
+// row index c of row pbase[r] + c). Every entry becomes (r_i * a_ij) * s_j,
+// the same operation order in every layout so that the copies of Ahat stay
+// bit-identical.
+void launch_scale(const Hyb& M, const double* r, const double* s, int transposed, int grid, cudaStream_t st,
+                  const int* pcol = nullptr, const int* pbase = nullptr);
 void launch_mul_inplace(double* d, const double* f, int len, int grid, cudaStream_t s);
 void launch_mul(double* out, const double* a, const double* b, int len, int grid, cudaStream_t s);
 void launch_div(double* out, const double* a, const double* b, int len, int grid, cudaStream_t s);
@@ -69,6 +72,33 @@ template <class T>
 void launch_adj_seed(T* g, const double* in, const int* perm, const double* d, int len, int grid, cudaStream_t s);
 template <class T>
 void launch_adj_unseed(double* out, const T* g, const int* perm, const double* d, int len, int grid, cudaStream_t s);
+// ---- panel-tiled primal half-step (option primal_panels) --------------------
+#ifndef PDHG_PANEL_TPB
+#define PDHG_PANEL_TPB 1024
+#endif
+#ifndef PDHG_PANEL_MINB32
+#define PDHG_PANEL_MINB32 1
+#endif
+constexpr int PANEL_TPB = PDHG_PANEL_TPB;     // threads per block of the panel pass
+// resident FP32 panel blocks per SM the compiler plans for: one (64 registers, no spills) ran
+// faster than two (32 registers, spilling) on the 1e6 x 3e6 LP
+constexpr int PANEL_MINB32 = PDHG_PANEL_MINB32;
+constexpr int PANEL_SMEM_MAX = 220 * 1024;  // shared memory of one panel block
+struct PanelLayout {
+  int m = 0;                // rows of A (length of y)
+  int rows = 0;             // panel height: entries of y per panel
+  int panels = 0;           // ceil(m / rows)
+  int* ustart = nullptr;    // [panels + 1] first unit of every panel in Pn
+  int* segout = nullptr;    // [segments] column-major position of every segment row of Pn
+  int* cptr = nullptr;      // [n + 1] first segment position of every column
+};
+// allow the panel kernels their shared memory (once per device, outside graph capture)
+cudaError_t configure_primal_panels();
+// both passes; kpp = blocks per panel, grid_n = grid of the per-column pass
+template <class T>
+cudaError_t launch_primal_panels(const Hyb& Pn, const T* vals, const PanelLayout& L, const T* y, const T* ch, T* x,
+                                 T* xbar, T* xsum, T* partial, const DevState* st, int accumulate, int kpp, int n,
+                                 int grid_n, cudaStream_t s);
 // the same step, persistent (grid = number of SMs), with xbar[0, hot) staged
 // in shared memory; hot <= HOT_MAX
 void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,
@@ -134,7 +164,25 @@ void launch_lengths(const long long* grp, long long M, const int* gci, long long
                     int* lenT, unsigned* maxes, cudaStream_t s);
 void launch_length_keys(const int* len, long long cnt, const int* inst, int maxlen, int lbits,
                         unsigned long long* keys, int* vals, cudaStream_t s);
-void launch_transpose_keys(const int* gci, long long Z, const int* ix, unsigned* keys, int* vals, cudaStream_t s);
+// transpose sort keys, fed in internal row order (rpi: exclusive scan of the
+// internal rows' lengths)
+void launch_transpose_keys(const long long* grp, const int* py, const long long* rpi, long long M, const int* gci,
+                           const int* ix, unsigned* keys, int* vals, cudaStream_t s);
+// panel layout of A^T (segments = runs of one row of A^T inside one panel of
+// panel_rows internal rows); see build_panels in pdhg_api.cu
+void launch_panel_heads(const long long* tp, long long N, const int* sval, const int* rowid, const int* iy, int H,
+                        int* head, int* panel, int* col, cudaStream_t s);
+void launch_panel_segments(const int* head, const int* panel, const int* col, const long long* segpos, long long Z,
+                           long long S, long long* seg_start, int* seg_panel, int* seg_col, cudaStream_t s);
+void launch_panel_rowinfo(const int* sp, const int* seg_col, const int* seg_panel, int H, long long S, int* pcol,
+                          int* pbase, cudaStream_t s);
+void launch_panel_keys(const long long* seg_start, const int* seg_panel, long long S, int maxlen, int lbits,
+                       int* seg_len, unsigned long long* keys, int* vals, int* pcount, cudaStream_t s);
+void launch_panel_cptr(const long long* tp, const long long* segpos, long long N, int* cptr, cudaStream_t s);
+void launch_max_int(const int* v, long long len, unsigned* out, cudaStream_t s);
+void launch_fill_units_P(const Hyb& H, const int* slen, const int* sp, const long long* seg_start,
+                         const int* seg_panel, const int* sval, const int* rowid, const int* iy, const double* v,
+                         int panel_rows, cudaStream_t s);
 void launch_invert(const int* p, long long len, int* inv, cudaStream_t s);
 void launch_gather_int(const int* src, const int* p, long long len, int* out, cudaStream_t s);
 void launch_gather_double(const double* src, const int* p, long long len, double* out, cudaStream_t s);

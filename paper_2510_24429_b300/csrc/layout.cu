@@ -115,13 +115,89 @@ __global__ void k_length_keys(const int* __restrict__ len, long long cnt, const 
   }
 }
 
-// sort keys of the transpose: entry k goes to the row of its internal column
-__global__ void k_transpose_keys(const int* __restrict__ gci, long long Z, const int* __restrict__ ix,
-                                 unsigned* __restrict__ keys, int* __restrict__ vals) {
-  for (long long k = gtid(); k < Z; k += gstride()) {
-    keys[k] = (unsigned)ix[gci[k]];
-    vals[k] = (int)k;
+// sort keys of the transpose, fed in internal row order (internal row r =
+// the caller's row py[r], entries from grp[py[r]]; rpi: its exclusive scan of
+// lengths), so that every row of A^T lists its entries by increasing
+// internal row: entry k goes to the row of its internal column
+__global__ void k_transpose_keys(const long long* __restrict__ grp, const int* __restrict__ py,
+                                 const long long* __restrict__ rpi, long long M, const int* __restrict__ gci,
+                                 const int* __restrict__ ix, unsigned* __restrict__ keys, int* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = gtid() >> 5, nw = gstride() >> 5;
+  for (long long r = w0; r < M; r += nw) {
+    const long long s = grp[py[r]], len = rpi[r + 1] - rpi[r], o = rpi[r];
+    for (long long e = lane; e < len; e += 32) {
+      const long long k = s + e;
+      keys[o + e] = (unsigned)ix[gci[k]];
+      vals[o + e] = (int)k;
+    }
   }
+}
+
+// ---- panel layout of A^T (panel-tiled primal step) ---------------------------
+
+// head[p] = 1 where a segment (a maximal run of one row of A^T inside one
+// panel of H internal rows) starts; panel[p] = its panel
+__global__ void k_panel_heads(const long long* __restrict__ tp, long long N, const int* __restrict__ sval,
+                              const int* __restrict__ rowid, const int* __restrict__ iy, int H,
+                              int* __restrict__ head, int* __restrict__ panel, int* __restrict__ col) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = gtid() >> 5, nw = gstride() >> 5;
+  for (long long j = w0; j < N; j += nw) {
+    const long long a = tp[j], b = tp[j + 1];
+    for (long long q = a + lane; q < b; q += 32) {
+      const int pq = iy[rowid[sval[q]]] / H;
+      const int pp = q > a ? iy[rowid[sval[q - 1]]] / H : -1;
+      head[q] = pq != pp;
+      panel[q] = pq;
+      col[q] = (int)j;
+    }
+  }
+}
+
+// per segment s (numbered in order of position, i.e. column by column): its
+// first position, panel and column; segpos = exclusive scan of head
+__global__ void k_panel_segments(const int* __restrict__ head, const int* __restrict__ panel,
+                                 const int* __restrict__ col, const long long* __restrict__ segpos, long long Z,
+                                 long long S, long long* __restrict__ seg_start, int* __restrict__ seg_panel,
+                                 int* __restrict__ seg_col) {
+  for (long long q = gtid(); q < Z; q += gstride())
+    if (head[q]) {
+      const long long sid = segpos[q];
+      seg_start[sid] = q;
+      seg_panel[sid] = panel[q];
+      seg_col[sid] = col[q];
+    }
+  if (gtid() == 0) seg_start[S] = Z;
+}
+
+__global__ void k_panel_keys(const long long* __restrict__ seg_start, const int* __restrict__ seg_panel, long long S,
+                             int maxlen, int lbits, int* __restrict__ seg_len, unsigned long long* __restrict__ keys,
+                             int* __restrict__ vals, int* __restrict__ pcount) {
+  for (long long sid = gtid(); sid < S; sid += gstride()) {
+    const int len = (int)(seg_start[sid + 1] - seg_start[sid]);
+    seg_len[sid] = len;
+    keys[sid] = ((unsigned long long)seg_panel[sid] << lbits) | (unsigned long long)(maxlen - len);
+    vals[sid] = (int)sid;
+    atomicAdd(&pcount[seg_panel[sid]], 1);
+  }
+}
+
+// column and first row of A of every segment row r (segment sp[r])
+__global__ void k_panel_rowinfo(const int* __restrict__ sp, const int* __restrict__ seg_col,
+                                const int* __restrict__ seg_panel, int H, long long S, int* __restrict__ pcol,
+                                int* __restrict__ pbase) {
+  for (long long r = gtid(); r < S; r += gstride()) {
+    const int sid = sp[r];
+    pcol[r] = seg_col[sid];
+    pbase[r] = seg_panel[sid] * H;
+  }
+}
+
+// first segment of every column: cptr[j] = segpos[tp[j]] (cptr[N] = S)
+__global__ void k_panel_cptr(const long long* __restrict__ tp, const long long* __restrict__ segpos, long long N,
+                             int* __restrict__ cptr) {
+  for (long long j = gtid(); j <= N; j += gstride()) cptr[j] = (int)segpos[tp[j]];
 }
 
 __global__ void k_invert(const int* __restrict__ p, long long len, int* __restrict__ inv) {
@@ -271,7 +347,7 @@ struct SrcA {
   const int* ix;
   const double* v;
   __device__ long long start(int row) const { return grp[py[row]]; }
-  __device__ void get(long long p, int& c, double& x) const {
+  __device__ void get(int, long long p, int& c, double& x) const {
     c = ix[gci[p]];
     x = v[p];
   }
@@ -286,9 +362,29 @@ struct SrcT {
   const int* iy;
   const double* v;
   __device__ long long start(int row) const { return tp[row]; }
-  __device__ void get(long long p, int& c, double& x) const {
+  __device__ void get(int, long long p, int& c, double& x) const {
     const int k = sval[p];
     c = iy[rowid[k]];
+    x = v[k];
+  }
+};
+
+// entries of segment row `row` of the panel layout: positions from
+// seg_start[sp[row]] of the A^T entries (sorted by internal column, then
+// internal row), with the row index taken relative to the segment's panel
+struct SrcPanel {
+  const int* sp;
+  const long long* seg_start;
+  const int* seg_panel;
+  const int* sval;
+  const int* rowid;
+  const int* iy;
+  const double* v;
+  int H;
+  __device__ long long start(int row) const { return seg_start[sp[row]]; }
+  __device__ void get(int row, long long p, int& c, double& x) const {
+    const int k = sval[p];
+    c = iy[rowid[k]] - seg_panel[sp[row]] * H;
     x = v[k];
   }
 };
@@ -308,7 +404,7 @@ __global__ void k_fill_units(const int4* __restrict__ uinfo, const long long* __
       for (int e = lane; e < len; e += 32) {
         int c;
         double x;
-        src.get(s + e, c, x);
+        src.get(info.x, s + e, c, x);
         ci[base + e] = c;
         v[base + e] = x;
       }
@@ -323,7 +419,7 @@ __global__ void k_fill_units(const int4* __restrict__ uinfo, const long long* __
         for (int e = 0; e < len; ++e) {
           int c;
           double x;
-          src.get(s + e, c, x);
+          src.get(row, s + e, c, x);
           const long long k = slice_slot(base, Lp, R, q, e, lane);
           ci[k] = c;
           v[k] = x;
@@ -396,8 +492,49 @@ void launch_length_keys(const int* len, long long cnt, const int* inst, int maxl
   k_length_keys<<<grid_of(cnt), LT_TPB, 0, s>>>(len, cnt, inst, maxlen, lbits, keys, vals);
 }
 
-void launch_transpose_keys(const int* gci, long long Z, const int* ix, unsigned* keys, int* vals, cudaStream_t s) {
-  if (Z > 0) k_transpose_keys<<<grid_of(Z), LT_TPB, 0, s>>>(gci, Z, ix, keys, vals);
+void launch_transpose_keys(const long long* grp, const int* py, const long long* rpi, long long M, const int* gci,
+                           const int* ix, unsigned* keys, int* vals, cudaStream_t s) {
+  k_transpose_keys<<<grid_of(32 * M), LT_TPB, 0, s>>>(grp, py, rpi, M, gci, ix, keys, vals);
+}
+
+void launch_panel_heads(const long long* tp, long long N, const int* sval, const int* rowid, const int* iy, int H,
+                        int* head, int* panel, int* col, cudaStream_t s) {
+  k_panel_heads<<<grid_of(32 * N), LT_TPB, 0, s>>>(tp, N, sval, rowid, iy, H, head, panel, col);
+}
+
+void launch_panel_segments(const int* head, const int* panel, const int* col, const long long* segpos, long long Z,
+                           long long S, long long* seg_start, int* seg_panel, int* seg_col, cudaStream_t s) {
+  k_panel_segments<<<grid_of(std::max(1LL, Z)), LT_TPB, 0, s>>>(head, panel, col, segpos, Z, S, seg_start, seg_panel,
+                                                                 seg_col);
+}
+
+void launch_panel_rowinfo(const int* sp, const int* seg_col, const int* seg_panel, int H, long long S, int* pcol,
+                          int* pbase, cudaStream_t s) {
+  if (S > 0) k_panel_rowinfo<<<grid_of(S), LT_TPB, 0, s>>>(sp, seg_col, seg_panel, H, S, pcol, pbase);
+}
+
+void launch_panel_keys(const long long* seg_start, const int* seg_panel, long long S, int maxlen, int lbits,
+                       int* seg_len, unsigned long long* keys, int* vals, int* pcount, cudaStream_t s) {
+  if (S > 0) k_panel_keys<<<grid_of(S), LT_TPB, 0, s>>>(seg_start, seg_panel, S, maxlen, lbits, seg_len, keys, vals,
+                                                         pcount);
+}
+
+void launch_panel_cptr(const long long* tp, const long long* segpos, long long N, int* cptr, cudaStream_t s) {
+  k_panel_cptr<<<grid_of(N + 1), LT_TPB, 0, s>>>(tp, segpos, N, cptr);
+}
+
+void launch_max_int(const int* v, long long len, unsigned* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, sizeof(unsigned), s);
+  if (len > 0) k_max_int<<<grid_of(len), LT_TPB, 0, s>>>(v, len, out);
+}
+
+void launch_fill_units_P(const Hyb& H, const int* slen, const int* sp, const long long* seg_start,
+                         const int* seg_panel, const int* sval, const int* rowid, const int* iy, const double* v,
+                         int panel_rows, cudaStream_t s) {
+  if (H.n_units == 0) return;
+  SrcPanel src{sp, seg_start, seg_panel, sval, rowid, iy, v, panel_rows};
+  k_fill_units<SrcPanel><<<grid_of(32LL * H.n_units), LT_TPB, 0, s>>>(H.uinfo, H.uoff, H.n_units, slen, src, H.ci,
+                                                                      H.v);
 }
 
 void launch_invert(const int* p, long long len, int* inv, cudaStream_t s) {

@@ -75,6 +75,16 @@ struct pdhg_ctx {
   size_t persist_smem = 0;
   // warps per block of the step and evaluation kernels (option step_block)
   int wpb = WARPS_PER_BLOCK;
+  // panel-tiled primal step (option primal_panels): the panel layout of Ahat^T,
+  // its partial sums (FP64, FP32), blocks per panel, and for setup only the
+  // column and first row of every segment row (for its scaling)
+  bool panels_on = false;
+  Hyb Pn;
+  PanelLayout pl;
+  int panel_kpp = 1, panel_kpp32 = 1;  // blocks per panel (one wave of resident blocks)
+  double* pn_partial = nullptr;
+  float* pn_partial32 = nullptr;
+  int *pn_col = nullptr, *pn_base = nullptr;
   // CUDA graphs of one evaluation block, per precision phase (FP64, FP32)
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   int64_t graph_launches[2] = {0, 0};
@@ -294,6 +304,9 @@ pdhg_status record_checkpoint(pdhg_ctx* ctx, int64_t k) {
 }
 
 // Reverse pass over every iteration run so far, in precision T.
+pdhg_status primal_step(pdhg_ctx* ctx, bool f32, const void* y, void* x, void* xbar, void* xsum, int accumulate,
+                        int grT, int tpb);
+
 template <class T>
 pdhg_status backward_impl(pdhg_ctx* ctx, const double* dx, const double* dy, double* dc, double* db) {
   const int64_t K = ctx->k, C = ctx->opt.checkpoint_every, n = ctx->n, m = ctx->m;
@@ -324,16 +337,13 @@ pdhg_status backward_impl(pdhg_ctx* ctx, const double* dx, const double* dy, dou
     CK(ctx, cudaMemcpyAsync(wx, ctx->ck_x[sg], sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
     CK(ctx, cudaMemcpyAsync(wy, ctx->ck_y[sg], sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
     for (int64_t k = start; k < end; ++k) {
-      if (f32) {
-        launch_primal_step32(ctx->At, (const float*)wy, ctx->ch32, (float*)wx, (float*)wxbar, nullptr, ctx->st, 0,
-                             grT, s, tpb);
+      pdhg_status rs = primal_step(ctx, f32, wy, wx, wxbar, nullptr, 0, grT, tpb);
+      if (rs != PDHG_OK) return rs;
+      if (f32)
         launch_dual_step32(ctx->A, (const float*)wxbar, ctx->bh32, (float*)wy, nullptr, ctx->st, 0, grA, s, tpb);
-      } else {
-        launch_primal_step(ctx->At, (const double*)wy, ctx->ch, (double*)wx, (double*)wxbar, nullptr, ctx->st, 0,
-                           grT, s, nullptr, tpb);
+      else
         launch_dual_step(ctx->A, (const double*)wxbar, ctx->bh, (double*)wy, nullptr, ctx->st, 0, grA, s, nullptr,
                          tpb);
-      }
       CK(ctx, cudaMemcpyAsync(seg + (k - start) * n, wx, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
     }
     // reverse it
@@ -464,6 +474,83 @@ int bit_length(unsigned long long v) {
   return b;
 }
 
+// Panel layout of Ahat^T for the panel-tiled primal step (one LP): the entries
+// of every row j of A^T (sorted by internal row i) are cut into segments, one
+// per panel of ctx->pl.rows consecutive rows i; the segments of each panel,
+// sorted by decreasing length, become the rows of the Hyb ctx->Pn with row
+// indices relative to the panel. Segments are numbered column by column
+// (their partial sums' positions, segout), so that column j's partial sums
+// are positions [cptr[j], cptr[j+1]) in panel order.
+pdhg_status build_panels(pdhg_ctx* ctx, Scratch& sc, const long long* tp, const int* sval, const int* rowid,
+                         const int* iy, const double* val, unsigned max_col_len, long long* hist, long long* ws) {
+  const pdhg_options& o = ctx->opt;
+  const long long N = ctx->n, Z = ctx->nnz;
+  const int H = ctx->pl.rows, P = ctx->pl.panels;
+  cudaStream_t s = ctx->stream;
+  int *head = nullptr, *panel = nullptr, *col = nullptr;
+  long long* segpos = nullptr;
+  CK(ctx, sc.take(&head, Z));
+  CK(ctx, sc.take(&panel, Z));
+  CK(ctx, sc.take(&col, Z));
+  CK(ctx, sc.take(&segpos, Z + 1));
+  launch_panel_heads(tp, N, sval, rowid, iy, H, head, panel, col, s);
+  launch_scan_int(head, Z, segpos, ws, s);
+  long long S = 0;
+  CK(ctx, cudaMemcpyAsync(&S, segpos + Z, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  long long* seg_start = nullptr;
+  int *seg_panel = nullptr, *seg_col = nullptr, *seg_len = nullptr, *va = nullptr, *vb = nullptr, *pcount = nullptr;
+  int* slen = nullptr;
+  unsigned long long *ka = nullptr, *kb = nullptr;
+  CK(ctx, sc.take(&seg_start, S + 1));
+  CK(ctx, sc.take(&seg_panel, S));
+  CK(ctx, sc.take(&seg_col, S));
+  CK(ctx, sc.take(&seg_len, S));
+  CK(ctx, sc.take(&ka, S));
+  CK(ctx, sc.take(&kb, S));
+  CK(ctx, sc.take(&va, S));
+  CK(ctx, sc.take(&vb, S));
+  CK(ctx, sc.take(&pcount, P));
+  CK(ctx, sc.take(&slen, S));
+  CK(ctx, sc.take(&ctx->pn_col, S));
+  CK(ctx, sc.take(&ctx->pn_base, S));
+  launch_panel_segments(head, panel, col, segpos, Z, S, seg_start, seg_panel, seg_col, s);
+  CK(ctx, cudaMemsetAsync(pcount, 0, sizeof(int) * P, s));
+  const int lbits = bit_length(max_col_len);
+  launch_panel_keys(seg_start, seg_panel, S, (int)max_col_len, lbits, seg_len, ka, va, pcount, s);
+  const int alt = radix_sort_pairs<unsigned long long>(ka, va, kb, vb, S,
+                                                        lbits + bit_length((unsigned long long)(P - 1)), hist, ws, s);
+  const int* sp = alt ? vb : va;
+  CK(ctx, dalloc(ctx, &ctx->pl.segout, S));
+  CK(ctx, cudaMemcpyAsync(ctx->pl.segout, sp, sizeof(int) * S, cudaMemcpyDeviceToDevice, s));
+  launch_gather_int(seg_len, sp, S, slen, s);
+  launch_panel_rowinfo(sp, seg_col, seg_panel, H, S, ctx->pn_col, ctx->pn_base, s);
+  CK(ctx, dalloc(ctx, &ctx->pl.cptr, N + 1));
+  launch_panel_cptr(tp, segpos, N, ctx->pl.cptr, s);
+  std::vector<int> hs(S), hc(P);
+  CK(ctx, cudaMemcpyAsync(hs.data(), slen, sizeof(int) * S, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaMemcpyAsync(hc.data(), pcount, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  HostUnits uP;
+  std::vector<int> ust(P + 1, 0);
+  long long base = 0;
+  for (int p = 0; p < P; ++p) {
+    ust[p] = uP.n_units();
+    append_unit_table(uP, (int)base, hc[p], hs.data() + base, o.long_row_min, o.rows_per_thread);
+    base += hc[p];
+  }
+  ust[P] = uP.n_units();
+  pdhg_status rs = upload_units(ctx, uP, (int)S, H, ctx->Pn);
+  if (rs != PDHG_OK) return rs;
+  CK(ctx, dalloc(ctx, &ctx->pl.ustart, P + 1));
+  CK(ctx, cudaMemcpyAsync(ctx->pl.ustart, ust.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice, s));
+  launch_fill_units_P(ctx->Pn, slen, sp, seg_start, seg_panel, sval, rowid, iy, val, H, s);
+  CK(ctx, dalloc(ctx, &ctx->pn_partial, std::max<long long>(1, S)));
+  CK(ctx, cudaGetLastError());
+  CK(ctx, cudaStreamSynchronize(s));  // the host tables are released on return
+  return PDHG_OK;
+}
+
 // Builds ctx->A, ctx->At, ctx->perm_x, ctx->perm_y (and for a batch ctx->binst,
 // ctx->bstart, ctx->nblocks) on the device from the instances' CSRs in device
 // memory: instance i's m_i + 1 row pointers start at lrp + rpoff_h[i], its
@@ -524,7 +611,7 @@ pdhg_status build_layouts(pdhg_ctx* ctx, Scratch& sc, const long long* lrp, cons
   CK(ctx, sc.take(&va, MN));
   CK(ctx, sc.take(&vb, MN));
   CK(ctx, sc.take(&hist, hist_len));
-  CK(ctx, sc.take(&ws, scan_ws_len(std::max(hist_len, N))));
+  CK(ctx, sc.take(&ws, scan_ws_len(std::max({hist_len, M, N, Z}))));
   CK(ctx, dalloc(ctx, &ctx->perm_y, M));
   CK(ctx, dalloc(ctx, &ctx->perm_x, N));
   const int ibits = batch ? bit_length((unsigned long long)(count - 1)) : 0;
@@ -548,16 +635,18 @@ pdhg_status build_layouts(pdhg_ctx* ctx, Scratch& sc, const long long* lrp, cons
   launch_gather_int(lenA, ctx->perm_y, M, slA, s);
   launch_gather_int(lenT, ctx->perm_x, N, slT, s);
 
-  // transpose: entries by internal column, in the caller's row order within one
+  // transpose: entries by internal column, by increasing internal row within one
   unsigned *k32a = nullptr, *k32b = nullptr;
   int *za = nullptr, *zb = nullptr;
-  long long* tp = nullptr;
+  long long *tp = nullptr, *rpi = nullptr;
   CK(ctx, sc.take(&k32a, Z));
   CK(ctx, sc.take(&k32b, Z));
   CK(ctx, sc.take(&za, Z));
   CK(ctx, sc.take(&zb, Z));
   CK(ctx, sc.take(&tp, N + 1));
-  launch_transpose_keys(gci, Z, ix, k32a, za, s);
+  CK(ctx, sc.take(&rpi, M + 1));
+  launch_scan_int(slA, M, rpi, ws, s);
+  launch_transpose_keys(grp, ctx->perm_y, rpi, M, gci, ix, k32a, za, s);
   const int alt = radix_sort_pairs<unsigned>(k32a, za, k32b, zb, Z, bit_length((unsigned long long)(N - 1)), hist,
                                              ws, s);
   const int* sval = alt ? zb : za;
@@ -593,6 +682,10 @@ pdhg_status build_layouts(pdhg_ctx* ctx, Scratch& sc, const long long* lrp, cons
   launch_fill_units_A(ctx->A, slA, grp, ctx->perm_y, gci, ix, val, s);
   launch_fill_units_T(ctx->At, slT, tp, sval, rowid, iy, val, s);
   CK(ctx, cudaGetLastError());
+  if (ctx->panels_on) {
+    rs = build_panels(ctx, sc, tp, sval, rowid, iy, val, h_max[1], hist, ws);
+    if (rs != PDHG_OK) return rs;
+  }
   if (batch) {
     ctx->nblocks = ctx->bstart_h[count];
     CK(ctx, dalloc(ctx, &ctx->binst, ctx->nblocks));
@@ -680,6 +773,11 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   pdhg_status rs = build_layouts(ctx, sc, d_rp, d_ci, d_v, {0}, {0, (long long)nnz});
   if (rs != PDHG_OK) return rs;
   ctx->persist_smem = persistent_smem_bytes(n, m);
+  if (ctx->panels_on) {
+    ctx->panel_kpp = std::max(1, ctx->sms / ctx->pl.panels);
+    ctx->panel_kpp32 = std::max(1, PANEL_MINB32 * ctx->sms / ctx->pl.panels);
+    CK(ctx, configure_primal_panels());
+  }
   Hyb& A = ctx->A;
   Hyb& At = ctx->At;
   double** vecs_n[] = {&ctx->c, &ctx->ch, &ctx->dc, &ctx->idc, &ctx->x, &ctx->xbar, &ctx->xsum, &ctx->xavg,
@@ -723,6 +821,7 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
     launch_inv_sqrt_or_one(sf, sf, (int)n, gn, s);
     launch_scale(A, r, sf, 0, grA, s);
     launch_scale(At, r, sf, 1, grT, s);
+    if (ctx->panels_on) launch_scale(ctx->Pn, r, sf, 2, stride_grid(ctx, ctx->Pn), s, ctx->pn_col, ctx->pn_base);
     launch_mul_inplace(ctx->dr, r, (int)m, gm, s);
     launch_mul_inplace(ctx->dc, sf, (int)n, gn, s);
   }
@@ -733,6 +832,7 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
     launch_inv_sqrt_or_one(sf, sf, (int)n, gn, s);
     launch_scale(A, r, sf, 0, grA, s);
     launch_scale(At, r, sf, 1, grT, s);
+    if (ctx->panels_on) launch_scale(ctx->Pn, r, sf, 2, stride_grid(ctx, ctx->Pn), s, ctx->pn_col, ctx->pn_base);
     launch_mul_inplace(ctx->dr, r, (int)m, gm, s);
     launch_mul_inplace(ctx->dc, sf, (int)n, gn, s);
   }
@@ -806,6 +906,11 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
     for (float** p : f_m) CK(ctx, dalloc(ctx, p, m));
     launch_narrow(A.v32, A.v, A.slots, vec_grid(ctx, A.slots), s);
     launch_narrow(At.v32, At.v, At.slots, vec_grid(ctx, At.slots), s);
+    if (ctx->panels_on) {
+      CK(ctx, dalloc(ctx, &ctx->Pn.v32, ctx->Pn.slots));
+      CK(ctx, dalloc(ctx, &ctx->pn_partial32, std::max<long long>(1, ctx->Pn.rows)));
+      launch_narrow(ctx->Pn.v32, ctx->Pn.v, ctx->Pn.slots, vec_grid(ctx, ctx->Pn.slots), s);
+    }
     launch_narrow(ctx->ch32, ctx->ch, n, gn, s);
     launch_narrow(ctx->bh32, ctx->bh, m, gm, s);
     launch_narrow(ctx->x32, ctx->x, n, gn, s);
@@ -825,12 +930,41 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   CK(ctx, cudaGetLastError());
   rs = read_state(ctx);
   if (rs != PDHG_OK) return rs;
+  ctx->pn_col = ctx->pn_base = nullptr;  // setup scratch, released on return
   if (!std::isfinite(ctx->h_st->norm_est) || !std::isfinite(ctx->h_st->omega))
     return fail(ctx, PDHG_ERR_NUMERIC, "non-finite norm estimate or primal weight after scaling");
   return PDHG_OK;
 }
 
 // ---- one evaluation block -------------------------------------------------------
+
+// The primal half-step on (y, x, xbar, xsum) in FP32 or FP64: the panel-tiled
+// form (two kernels) in FP32 phases when its layout exists, and in FP64 phases
+// too when primal_panels = 1; else the direct one. (In FP64 the per-column
+// pass is bound by FP64 arithmetic, and the direct step is as fast.)
+pdhg_status primal_step(pdhg_ctx* ctx, bool f32, const void* y, void* x, void* xbar, void* xsum, int accumulate,
+                        int grT, int tpb) {
+  cudaStream_t s = ctx->stream;
+  if (ctx->panels_on && (f32 || ctx->opt.primal_panels == 1)) {
+    const int gn = vec_grid(ctx, ctx->n);
+    cudaError_t e =
+        f32 ? launch_primal_panels<float>(ctx->Pn, ctx->Pn.v32, ctx->pl, (const float*)y, ctx->ch32, (float*)x,
+                                          (float*)xbar, (float*)xsum, ctx->pn_partial32, ctx->st, accumulate,
+                                          ctx->panel_kpp32, (int)ctx->n, gn, s)
+            : launch_primal_panels<double>(ctx->Pn, ctx->Pn.v, ctx->pl, (const double*)y, ctx->ch, (double*)x,
+                                           (double*)xbar, (double*)xsum, ctx->pn_partial, ctx->st, accumulate,
+                                           ctx->panel_kpp, (int)ctx->n, gn, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "panel-tiled primal step");
+    ctx->launches += 1;  // the second kernel
+  } else if (f32) {
+    launch_primal_step32(ctx->At, (const float*)y, ctx->ch32, (float*)x, (float*)xbar, (float*)xsum, ctx->st,
+                         accumulate, grT, s, tpb);
+  } else {
+    launch_primal_step(ctx->At, (const double*)y, ctx->ch, (double*)x, (double*)xbar, (double*)xsum, ctx->st,
+                       accumulate, grT, s, nullptr, tpb);
+  }
+  return PDHG_OK;
+}
 
 // The step launches of nb iterations (plus adjoint checkpoints and kernel
 // timing events when asked) and the counter update.
@@ -845,12 +979,13 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
       if (rs != PDHG_OK) return rs;
     }
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
-    if (ctx->phase32)
-      launch_primal_step32(ctx->At, ctx->y32, ctx->ch32, ctx->x32, ctx->xbar32, ctx->xsum32, ctx->st, o.restarts,
-                           grT, s, tpb);
-    else
-      launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, grT, s, nullptr,
-                         tpb);
+    {
+      pdhg_status rs = ctx->phase32 ? primal_step(ctx, true, ctx->y32, ctx->x32, ctx->xbar32, ctx->xsum32,
+                                                  o.restarts, grT, tpb)
+                                    : primal_step(ctx, false, ctx->y, ctx->x, ctx->xbar, ctx->xsum, o.restarts, grT,
+                                                  tpb);
+      if (rs != PDHG_OK) return rs;
+    }
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
     if (ctx->phase32)
       launch_dual_step32(ctx->A, ctx->xbar32, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st, o.restarts, grA, s, tpb);
@@ -1029,6 +1164,7 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
     launch_inv_sqrt_or_one(sf, sf, (int)n, gn, s);
     launch_scale(A, r, sf, 0, grA, s);
     launch_scale(At, r, sf, 1, grT, s);
+    if (ctx->panels_on) launch_scale(ctx->Pn, r, sf, 2, stride_grid(ctx, ctx->Pn), s, ctx->pn_col, ctx->pn_base);
     launch_mul_inplace(ctx->dr, r, (int)m, gm, s);
     launch_mul_inplace(ctx->dc, sf, (int)n, gn, s);
   }
@@ -1039,6 +1175,7 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
     launch_inv_sqrt_or_one(sf, sf, (int)n, gn, s);
     launch_scale(A, r, sf, 0, grA, s);
     launch_scale(At, r, sf, 1, grT, s);
+    if (ctx->panels_on) launch_scale(ctx->Pn, r, sf, 2, stride_grid(ctx, ctx->Pn), s, ctx->pn_col, ctx->pn_base);
     launch_mul_inplace(ctx->dr, r, (int)m, gm, s);
     launch_mul_inplace(ctx->dc, sf, (int)n, gn, s);
   }
@@ -1309,6 +1446,8 @@ void pdhg_default_options(pdhg_options* o) {
   o->record_for_backward = 0;
   o->checkpoint_every = 50;
   o->step_block = 256;
+  o->primal_panels = -1;
+  o->panel_rows = 0;
 }
 
 pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
@@ -1338,6 +1477,10 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     return fail(nullptr, PDHG_ERR_INVALID, "option out of range");
   if (!(o.step_block == 0 || o.step_block == 128 || o.step_block == 256 || o.step_block == 512))
     return fail(nullptr, PDHG_ERR_INVALID, "step_block must be 128, 256 or 512");
+  if (o.primal_panels < -1 || o.primal_panels > 1 || o.panel_rows < 0 || o.panel_rows > PANEL_SMEM_MAX / 8)
+    return fail(nullptr, PDHG_ERR_INVALID, "primal_panels must be -1, 0 or 1 and panel_rows in [0, 28160]");
+  if (o.persistent && o.primal_panels == 1)
+    return fail(nullptr, PDHG_ERR_INVALID, "persistent = 1 and primal_panels = 1 exclude each other");
   if (o.persistent) {
     if (o.persistent != 1 || o.precision != PDHG_FP64 || o.record_for_backward || o.kernel_timing ||
         o.dual_hot_cols)
@@ -1364,6 +1507,18 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
   ctx->nnz = nnz;
   ctx->opt = o;
   ctx->wpb = (o.step_block ? o.step_block : TPB) / 32;
+  ctx->panels_on = !o.persistent && (o.primal_panels == 1 || (o.primal_panels < 0 && o.precision != PDHG_FP64 &&
+                                                                m >= 65536 && nnz >= (1 << 20)));
+  if (ctx->panels_on) {
+    const long long hmax = PANEL_SMEM_MAX / (long long)sizeof(double);
+    const long long P0 = (m + hmax - 1) / hmax;
+    // a multiple of 16 entries keeps every panel's start 16-byte aligned for
+    // the asynchronous copies of y (FP32 and FP64)
+    const long long H = o.panel_rows > 0 ? o.panel_rows : std::min(hmax, ((m + P0 - 1) / P0 + 15) / 16 * 16);
+    ctx->pl.m = (int)m;
+    ctx->pl.rows = (int)H;
+    ctx->pl.panels = (int)((m + H - 1) / H);
+  }
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
   if (e == cudaSuccess) {
@@ -1682,6 +1837,8 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
                 "batch: FP64, host inputs, no snapshots, no recording, no shared-memory hot columns, valid options");
   if (!(o.step_block == 0 || o.step_block == 128 || o.step_block == 256 || o.step_block == 512))
     return fail(nullptr, PDHG_ERR_INVALID, "step_block must be 128, 256 or 512");
+  if (o.primal_panels == 1)
+    return fail(nullptr, PDHG_ERR_INVALID, "primal_panels = 1 is for single LPs (batches use the direct primal step)");
   if (o.persistent != 0 && (o.persistent != 1 || o.kernel_timing))
     return fail(nullptr, PDHG_ERR_INVALID, "persistent must be 0 or 1, and 1 excludes kernel timing");
   int64_t mt = 0, nt = 0, zt = 0;

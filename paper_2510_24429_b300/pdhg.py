@@ -55,7 +55,9 @@ class pdhg_options(C.Structure):
         ("checkpoint_every", C.c_int64),
         ("persistent", C.c_int),
         ("step_block", C.c_int),
-        ("reserved", C.c_int * 6),
+        ("primal_panels", C.c_int),
+        ("panel_rows", C.c_int),
+        ("reserved", C.c_int * 4),
     ]
 
 
