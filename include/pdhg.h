@@ -100,8 +100,8 @@ typedef struct {
   int step_block;         /* threads per block of the step and evaluation kernels: 128, 256 or 512 (256) */
   int primal_panels;      /* panel-tiled primal half-step: y is cut into panels that fit in shared memory and
                              A^T into per-panel segments whose partial sums are added per column; 1 = on in
-                             every precision, 0 = off, -1 = on in FP32 phases of single LPs with m >= 65536
-                             and nnz >= 2^20 (-1) */
+                             every precision, 0 = off, -1 = on in FP32 phases of single LPs with m >= 2^18
+                             and nnz >= 2^23 (-1) */
   int panel_rows;         /* entries of y per panel; 0 = as many as fit in shared memory (0; at most 28160) */
   int reserved[4];
 } pdhg_options;

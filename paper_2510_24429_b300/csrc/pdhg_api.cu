@@ -1507,8 +1507,10 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
   ctx->nnz = nnz;
   ctx->opt = o;
   ctx->wpb = (o.step_block ? o.step_block : TPB) / 32;
+  // auto: only where the matrix stream dwarfs the panels' copies of y (every
+  // block copies one panel, ~H entries, per step)
   ctx->panels_on = !o.persistent && (o.primal_panels == 1 || (o.primal_panels < 0 && o.precision != PDHG_FP64 &&
-                                                                m >= 65536 && nnz >= (1 << 20)));
+                                                                m >= (1 << 18) && nnz >= (1 << 23)));
   if (ctx->panels_on) {
     const long long hmax = PANEL_SMEM_MAX / (long long)sizeof(double);
     const long long P0 = (m + hmax - 1) / hmax;
