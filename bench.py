@@ -42,6 +42,10 @@ def parse_args():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--small", action="store_true", help="a 1/10-size LP (m=1e5, n=3e5, nnz~3e6) for profiling")
     p.add_argument("--skip-extras", action="store_true", help="skip e2e, time-to-tolerance and the CPU baseline")
+    p.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
+                   help="arithmetic of the timed iterations (fp32: the FP32 engine, for profiling it)")
+    p.add_argument("--extra", choices=["tiny", "batch", "adjoint"], default=None,
+                   help="run only this secondary workload and print its result (for profiling it)")
     return p.parse_args()
 
 
@@ -366,13 +370,23 @@ def run_ours(args):
 
     build.build()
     rank, world, local = dist_init(args)
+    if args.extra:
+        fn = {"tiny": run_tiny, "batch": run_batch, "adjoint": run_adjoint}[args.extra]
+        if rank == 0:
+            print(json.dumps({"extra": args.extra, **fn(P, torch)}))
+        return
     lp, name = make_lp(args)
     stream = torch.cuda.current_stream()
+
+    prec = P.PDHG_FP32 if args.precision == "fp32" else P.PDHG_FP64
+    w = 4 if args.precision == "fp32" else 8  # value width
+    if args.precision == "fp32":
+        name = name.replace("FP64", "FP32")
 
     # ---- device-resident timing (value) ----
     t0 = time.perf_counter()
     sol = P.Solver(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, stream=stream.cuda_stream,
-                   snapshot_every=SNAPSHOT_EVERY, kernel_timing=1)
+                   snapshot_every=SNAPSHOT_EVERY, kernel_timing=1, precision=prec)
     setup_s = time.perf_counter() - t0
     for _ in range(args.warmup):
         sol.iterate(ITERS_PER_STEP)
@@ -401,20 +415,25 @@ def run_ours(args):
     t_primal = (info1["kernel_ms_primal"] - info0["kernel_ms_primal"]) / lp_
     t_dual = (info1["kernel_ms_dual"] - info0["kernel_ms_dual"]) / ld_
     m, n, nnz = lp.m, lp.n, lp.nnz
-    bytes_primal = 12 * nnz + 8 * m + 48 * n  # A^T entries, y gathered once, x/c/xsum read + x/xbar/xsum written
-    bytes_dual = 12 * nnz + 8 * n + 40 * m  # A entries, xbar gathered once, y/b/ysum read + y/ysum written
+    # A^T entries, y gathered once, x/c/xsum read + x/xbar/xsum written
+    bytes_primal = (4 + w) * nnz + w * m + 6 * w * n
+    # A entries, xbar gathered once, y/b/ysum read + y/ysum written
+    bytes_dual = (4 + w) * nnz + w * n + 5 * w * m
     peak, peak_kind = measured_peaks()
+    # FP32 runs the panel-tiled primal half-step on large LPs (two kernels, timed together)
+    pname, dname = (("primal half-step (FP32)", "k_dual_step<float>") if args.precision == "fp32"
+                    else ("k_primal_step", "k_dual_step"))
     if t_primal >= t_dual:
-        kname, kb, kt = "k_primal_step", bytes_primal, t_primal
+        kname, kb, kt = pname, bytes_primal, t_primal
     else:
-        kname, kb, kt = "k_dual_step", bytes_dual, t_dual
+        kname, kb, kt = dname, bytes_dual, t_dual
     achieved = kb / (kt / 1000.0) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": profiled_traffic(kname, name),
                 "algorithmic_bytes_per_launch": kb, "ms_per_launch": kt,
-                "other_kernel": {"name": "k_dual_step" if kname == "k_primal_step" else "k_primal_step",
-                                 "ms_per_launch": t_dual if kname == "k_primal_step" else t_primal,
-                                 "achieved_gbs": (bytes_dual / (t_dual / 1000.0) if kname == "k_primal_step"
+                "other_kernel": {"name": dname if kname == pname else pname,
+                                 "ms_per_launch": t_dual if kname == pname else t_primal,
+                                 "achieved_gbs": (bytes_dual / (t_dual / 1000.0) if kname == pname
                                                   else bytes_primal / (t_primal / 1000.0)) / 1e9}}
     launches = info1["kernel_launches"] - info0["kernel_launches"]
     iter_bytes = bytes_primal + bytes_dual
@@ -526,7 +545,8 @@ def run_ours(args):
         out = {
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args, lp, name),
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": config_of(args, lp, name),
             "hbm_gbs_per_iteration_model": iter_bytes * value / world / 1e9,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "setup_s": setup_s, "snapshots_taken": snaps,
