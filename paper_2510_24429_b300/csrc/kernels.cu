@@ -468,11 +468,15 @@ struct PartialOp {
 // FP32 panels take half the shared memory, so two blocks could share an SM
 template <class T>
 __global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
-    k_primal_panels(Hyb Pn, const T* __restrict__ vals, const T* __restrict__ y, int m, int H, int kpp,
-                    const int* __restrict__ ustart, const int* __restrict__ segout, T* __restrict__ partial) {
+    k_primal_panels(Hyb Pn, const T* __restrict__ vals, const T* __restrict__ y, int m, int H,
+                    const int4* __restrict__ binfo, const int* __restrict__ ustart, const int* __restrict__ segout,
+                    T* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char panel_smem[];
   T* ys = reinterpret_cast<T*>(panel_smem);
-  const int p = blockIdx.x / kpp, sub = blockIdx.x - p * kpp;
+  // panels get blocks in proportion to their stored entries (the first panels,
+  // holding the longest rows of A, have the most)
+  const int4 bi = binfo[blockIdx.x];
+  const int p = bi.x, sub = bi.y, kpp = bi.z;
   const int i0 = p * H, len = min(H, m - i0);
   // the panel of y into shared memory with asynchronous 16-byte copies, all in
   // flight at once, when the panel starts on a 16-byte boundary (the default
@@ -1105,20 +1109,20 @@ cudaError_t configure_primal_panels() {
 }
 template <class T>
 cudaError_t launch_primal_panels(const Hyb& Pn, const T* vals, const PanelLayout& L, const T* y, const T* ch, T* x,
-                                 T* xbar, T* xsum, T* partial, const DevState* st, int accumulate, int kpp, int n,
-                                 int grid_n, cudaStream_t s) {
+                                 T* xbar, T* xsum, T* partial, const DevState* st, int accumulate, int n, int grid_n,
+                                 cudaStream_t s) {
   const size_t smem = sizeof(T) * (size_t)L.rows;
-  k_primal_panels<T><<<L.panels * kpp, PANEL_TPB, smem, s>>>(Pn, vals, y, L.m, L.rows, kpp, L.ustart, L.segout,
-                                                              partial);
+  k_primal_panels<T><<<L.blocks, PANEL_TPB, smem, s>>>(Pn, vals, y, L.m, L.rows, L.binfo, L.ustart, L.segout,
+                                                        partial);
   k_primal_combine<T><<<(n + TPB - 1) / TPB, TPB, 0, s>>>(L.cptr, partial, ch, x, xbar, xsum, n, st, accumulate);
   return cudaGetLastError();
 }
 template cudaError_t launch_primal_panels<double>(const Hyb&, const double*, const PanelLayout&, const double*,
                                                   const double*, double*, double*, double*, double*,
-                                                  const DevState*, int, int, int, int, cudaStream_t);
+                                                  const DevState*, int, int, int, cudaStream_t);
 template cudaError_t launch_primal_panels<float>(const Hyb&, const float*, const PanelLayout&, const float*,
                                                  const float*, float*, float*, float*, float*, const DevState*, int,
-                                                 int, int, int, cudaStream_t);
+                                                 int, int, cudaStream_t);
 void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,
                           const DevState* st, int accumulate, int grid, cudaStream_t s) {
   k_dual_step_hot<<<grid, HOT_TPB, (size_t)hot * sizeof(double), s>>>(A, xbar, hot, bh, y, ysum, st, accumulate);

@@ -91,14 +91,16 @@ struct PanelLayout {
   int* ustart = nullptr;    // [panels + 1] first unit of every panel in Pn
   int* segout = nullptr;    // [segments] column-major position of every segment row of Pn
   int* cptr = nullptr;      // [n + 1] first segment position of every column
+  int blocks = 0;           // blocks of the panel pass (one wave)
+  int4* binfo = nullptr;    // [blocks] (panel, index among its panel's blocks, its panel's block count, 0)
 };
 // allow the panel kernels their shared memory (once per device, outside graph capture)
 cudaError_t configure_primal_panels();
-// both passes; kpp = blocks per panel, grid_n = grid of the per-column pass
+// both passes (grid_n: grid of the per-column pass)
 template <class T>
 cudaError_t launch_primal_panels(const Hyb& Pn, const T* vals, const PanelLayout& L, const T* y, const T* ch, T* x,
-                                 T* xbar, T* xsum, T* partial, const DevState* st, int accumulate, int kpp, int n,
-                                 int grid_n, cudaStream_t s);
+                                 T* xbar, T* xsum, T* partial, const DevState* st, int accumulate, int n, int grid_n,
+                                 cudaStream_t s);
 // the same step, persistent (grid = number of SMs), with xbar[0, hot) staged
 // in shared memory; hot <= HOT_MAX
 void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,

@@ -81,7 +81,6 @@ struct pdhg_ctx {
   bool panels_on = false;
   Hyb Pn;
   PanelLayout pl;
-  int panel_kpp = 1, panel_kpp32 = 1;  // blocks per panel (one wave of resident blocks)
   double* pn_partial = nullptr;
   float* pn_partial32 = nullptr;
   int *pn_col = nullptr, *pn_base = nullptr;
@@ -540,6 +539,33 @@ pdhg_status build_panels(pdhg_ctx* ctx, Scratch& sc, const long long* tp, const 
     base += hc[p];
   }
   ust[P] = uP.n_units();
+  // one wave of blocks (PANEL_MINB32 per SM), shared among the panels in
+  // proportion to their stored entries, at least one each
+  std::vector<int> nb(P, 1);
+  {
+    const int total = std::max(PANEL_MINB32 * ctx->sms, P);
+    const double slots = (double)std::max(1LL, uP.uoff.back());
+    auto work = [&](int p) { return (double)(uP.uoff[ust[p + 1]] - uP.uoff[ust[p]]); };
+    int used = 0;
+    for (int p = 0; p < P; ++p) {
+      nb[p] = std::max(1, (int)std::floor(work(p) / slots * total));
+      used += nb[p];
+    }
+    // what rounding left goes to the panels with the most entries per block
+    while (used < total) {
+      int best = 0;
+      for (int p = 1; p < P; ++p)
+        if (work(p) / nb[p] > work(best) / nb[best]) best = p;
+      nb[best] += 1;
+      ++used;
+    }
+  }
+  std::vector<int> binfo;
+  for (int p = 0; p < P; ++p)
+    for (int b = 0; b < nb[p]; ++b) binfo.insert(binfo.end(), {p, b, nb[p], 0});
+  ctx->pl.blocks = (int)(binfo.size() / 4);
+  CK(ctx, dalloc(ctx, &ctx->pl.binfo, ctx->pl.blocks));
+  CK(ctx, cudaMemcpyAsync(ctx->pl.binfo, binfo.data(), sizeof(int) * binfo.size(), cudaMemcpyHostToDevice, s));
   pdhg_status rs = upload_units(ctx, uP, (int)S, H, ctx->Pn);
   if (rs != PDHG_OK) return rs;
   CK(ctx, dalloc(ctx, &ctx->pl.ustart, P + 1));
@@ -773,11 +799,7 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   pdhg_status rs = build_layouts(ctx, sc, d_rp, d_ci, d_v, {0}, {0, (long long)nnz});
   if (rs != PDHG_OK) return rs;
   ctx->persist_smem = persistent_smem_bytes(n, m);
-  if (ctx->panels_on) {
-    ctx->panel_kpp = std::max(1, ctx->sms / ctx->pl.panels);
-    ctx->panel_kpp32 = std::max(1, PANEL_MINB32 * ctx->sms / ctx->pl.panels);
-    CK(ctx, configure_primal_panels());
-  }
+  if (ctx->panels_on) CK(ctx, configure_primal_panels());
   Hyb& A = ctx->A;
   Hyb& At = ctx->At;
   double** vecs_n[] = {&ctx->c, &ctx->ch, &ctx->dc, &ctx->idc, &ctx->x, &ctx->xbar, &ctx->xsum, &ctx->xavg,
@@ -950,10 +972,10 @@ pdhg_status primal_step(pdhg_ctx* ctx, bool f32, const void* y, void* x, void* x
     cudaError_t e =
         f32 ? launch_primal_panels<float>(ctx->Pn, ctx->Pn.v32, ctx->pl, (const float*)y, ctx->ch32, (float*)x,
                                           (float*)xbar, (float*)xsum, ctx->pn_partial32, ctx->st, accumulate,
-                                          ctx->panel_kpp32, (int)ctx->n, gn, s)
+                                          (int)ctx->n, gn, s)
             : launch_primal_panels<double>(ctx->Pn, ctx->Pn.v, ctx->pl, (const double*)y, ctx->ch, (double*)x,
                                            (double*)xbar, (double*)xsum, ctx->pn_partial, ctx->st, accumulate,
-                                           ctx->panel_kpp, (int)ctx->n, gn, s);
+                                           (int)ctx->n, gn, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "panel-tiled primal step");
     ctx->launches += 1;  // the second kernel
   } else if (f32) {
