@@ -283,6 +283,56 @@ def run_batch(P, torch, count=256, tol=1e-6, seed=0):
 
 
 # ---------------------------------------------------------------------------
+# Algorithm 1's hand-off: snapshots consumed by another host thread
+# ---------------------------------------------------------------------------
+def run_snapshot_handoff(P, torch, lp, iters=2000, every=250):
+    """Iterations/s on the large LP without snapshots and with a snapshot every
+    `every` iterations consumed by a concurrent host thread (pdhg_snapshot_wait
+    copies each (x, y, z) out of the pinned ring: 2n + m doubles)."""
+    import threading
+
+    out = {"workload": f"zipf-lp m={lp.m} n={lp.n}, {iters} iterations, snapshot every {every}, one consumer thread"}
+    with P.Solver.from_lp(lp) as s:
+        s.iterate(256)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.iterate(iters)
+        torch.cuda.synchronize()
+        out["iters_per_s_no_snapshots"] = iters / (time.perf_counter() - t0)
+    with P.Solver.from_lp(lp, snapshot_every=every) as s:
+        s.iterate(256)
+        got, stop = [], threading.Event()
+
+        def consumer():
+            last = 0
+            while not stop.is_set():
+                try:
+                    snap = s.snapshot_wait(last, timeout_ms=100)
+                except P.PDHGError:
+                    continue
+                last = snap["index"]
+                got.append(last)
+
+        th = threading.Thread(target=consumer)
+        th.start()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.iterate(iters)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        count, _ = s.snapshot_poll()
+        time.sleep(0.3)
+        stop.set()
+        th.join()
+    out["iters_per_s_with_snapshots"] = iters / el
+    out["overhead"] = 1.0 - out["iters_per_s_with_snapshots"] / out["iters_per_s_no_snapshots"]
+    out["snapshots_taken"] = count
+    out["snapshots_received_by_consumer"] = len(got)
+    out["bytes_per_snapshot"] = 8 * (2 * lp.n + lp.m)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # the tiny LP: latency bound, iterations/s with and without CUDA graphs
 # ---------------------------------------------------------------------------
 def run_tiny(P, torch, iters=20_000):
@@ -529,6 +579,7 @@ def run_ours(args):
                            "iteration), 1000 iterations, solution read back, destroy"}
 
     if not args.skip_extras and rank == 0:
+        extras["snapshot_handoff"] = run_snapshot_handoff(P, torch, lp)
         extras["adjoint"] = run_adjoint(P, torch)
         extras["tiny_lp"] = run_tiny(P, torch)
         extras["batch"] = run_batch(P, torch)

@@ -194,6 +194,21 @@ PDHG_API pdhg_status pdhg_snapshot_poll(pdhg_ctx* ctx, int64_t* count, int* read
 PDHG_API pdhg_status pdhg_snapshot(pdhg_ctx* ctx, double* x, double* y, double* z, int64_t* iteration,
                                    double* rel_kkt);
 
+/* Algorithm 1's hand-off to a concurrent consumer (a crossover thread): blocks
+ * until a snapshot newer than number `after` (1-based count of snapshots taken;
+ * 0 = any) has reached pinned host memory, then copies the newest one into the
+ * caller's host buffers x (n), y (m), z (n) (any may be NULL) and returns its
+ * number (index), iteration and rel_kkt. It may be called from threads other
+ * than the one running pdhg_iterate, concurrently with it; the snapshot being
+ * copied is protected from reuse until the copy is done (the iterating thread
+ * waits for it, at most 60 s, before overwriting that ring slot). Returns
+ * PDHG_ERR_TIMEOUT when no newer snapshot completes within timeout_ms (a host
+ * wait: nothing waits on the GPU); does not update pdhg_last_error. The
+ * context must outlive the calls (destroy it only after its consumers have
+ * returned). */
+PDHG_API pdhg_status pdhg_snapshot_wait(pdhg_ctx* ctx, int64_t after, int64_t timeout_ms, double* x, double* y,
+                                        double* z, int64_t* index, int64_t* iteration, double* rel_kkt);
+
 /* Reverse pass through every iteration run so far (all of them plain
  * fixed-step PDHG iterations: the context must have been created with
  * record_for_backward = 1). Given dL/dx_K[n] and optionally dL/dy_K[m] (NULL =

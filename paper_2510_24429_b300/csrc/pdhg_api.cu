@@ -17,6 +17,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
@@ -33,6 +36,7 @@ namespace {
 
 thread_local std::string g_create_error = "no error";
 constexpr int EV_POOL = 256;
+constexpr int SNAP_SLOTS = 3;  // pinned host ring of completed snapshots
 // PDHG_MIXED: iterations without a 10% gain in the FP32 phase before FP64
 // takes over (PDHG itself plateaus for a few thousand iterations at times)
 constexpr int64_t STALL_ITERS = 16384;
@@ -101,12 +105,26 @@ struct pdhg_ctx {
   TraceRec* trace = nullptr;
   double* sol = nullptr;  // (x n, y m, z n)
   // snapshot ring
-  double* snap_dev[2] = {nullptr, nullptr};
-  double* snap_host[2] = {nullptr, nullptr};
-  cudaEvent_t snap_packed[2] = {nullptr, nullptr}, snap_done[2] = {nullptr, nullptr};
-  int64_t snap_iter[2] = {0, 0};
-  double snap_rel[2] = {0, 0};
-  int64_t snap_count = 0;
+  double* snap_dev[SNAP_SLOTS] = {};
+  double* snap_host[SNAP_SLOTS] = {};
+  cudaEvent_t snap_packed[SNAP_SLOTS] = {}, snap_done[SNAP_SLOTS] = {};
+  int64_t snap_iter[SNAP_SLOTS] = {};
+  double snap_rel[SNAP_SLOTS] = {};
+  int64_t snap_count = 0;  // snapshots started (by the thread that iterates)
+  // hand-off to consumer threads (pdhg_snapshot_wait): a host callback on the
+  // side stream marks a slot complete; consumers copy it out holding a reader
+  // count, and a slot is reused only when no reader holds it
+  struct SnapLanded {
+    pdhg_ctx* ctx;
+    int slot;
+    int64_t seq;
+  };
+  std::mutex snap_mu;
+  std::condition_variable snap_cv;
+  int64_t snap_seq[SNAP_SLOTS] = {};  // 1-based index of the complete snapshot in a slot, 0 while written
+  int snap_readers[SNAP_SLOTS] = {};
+  int64_t snap_latest = 0;  // index of the newest complete snapshot
+  SnapLanded snap_cb[SNAP_SLOTS] = {};
   // kernel timing
   cudaEvent_t ev[3 * EV_POOL] = {};
   double ms_primal = 0, ms_dual = 0;
@@ -358,9 +376,32 @@ pdhg_status backward_impl(pdhg_ctx* ctx, const double* dx, const double* dy, dou
   return PDHG_OK;
 }
 
+// host callback after a snapshot's copy to pinned memory (runs on a CUDA
+// thread: no CUDA calls here)
+void CUDART_CB snapshot_landed(void* p) {
+  auto* d = static_cast<pdhg_ctx::SnapLanded*>(p);
+  pdhg_ctx* ctx = d->ctx;
+  {
+    std::lock_guard<std::mutex> lk(ctx->snap_mu);
+    ctx->snap_seq[d->slot] = d->seq;
+    ctx->snap_latest = std::max(ctx->snap_latest, d->seq);
+  }
+  ctx->snap_cv.notify_all();
+}
+
 pdhg_status take_snapshot(pdhg_ctx* ctx) {
-  const int slot = (int)(ctx->snap_count % 2);
-  if (ctx->snap_count >= 2) CK(ctx, cudaEventSynchronize(ctx->snap_done[slot]));
+  const int slot = (int)(ctx->snap_count % SNAP_SLOTS);
+  // the slot's previous copy and its callback are done
+  if (ctx->snap_count >= SNAP_SLOTS) CK(ctx, cudaEventSynchronize(ctx->snap_done[slot]));
+  {
+    std::unique_lock<std::mutex> lk(ctx->snap_mu);
+    // a consumer thread still copying this slot out: wait for it (bounded)
+    if (!ctx->snap_cv.wait_for(lk, std::chrono::seconds(60), [&] { return ctx->snap_readers[slot] == 0; }))
+      return fail(ctx, PDHG_ERR_TIMEOUT, "a snapshot consumer held a ring slot for more than 60 s");
+    ctx->snap_seq[slot] = 0;
+    ctx->snap_iter[slot] = ctx->h_st->k;
+    ctx->snap_rel[slot] = ctx->h_st->cand_rel_kkt;
+  }
   const bool avg = ctx->h_st->candidate == KIND_AVG;
   const double* px = avg ? ctx->xavg : ctx->x;
   const double* py = avg ? ctx->yavg : ctx->y;
@@ -372,9 +413,10 @@ pdhg_status take_snapshot(pdhg_ctx* ctx) {
   CK(ctx, cudaStreamWaitEvent(ctx->side, ctx->snap_packed[slot], 0));
   CK(ctx, cudaMemcpyAsync(ctx->snap_host[slot], base, sizeof(double) * (2 * ctx->n + ctx->m), cudaMemcpyDeviceToHost,
                           ctx->side));
+  ctx->snap_cb[slot] = {ctx, slot, ctx->snap_count + 1};
+  CK(ctx, cudaLaunchHostFunc(ctx->side, snapshot_landed, &ctx->snap_cb[slot]));
+  // recorded after the callback, so that waiting on it also waits for the callback
   CK(ctx, cudaEventRecord(ctx->snap_done[slot], ctx->side));
-  ctx->snap_iter[slot] = ctx->h_st->k;
-  ctx->snap_rel[slot] = ctx->h_st->cand_rel_kkt;
   ctx->snap_count += 1;
   return PDHG_OK;
 }
@@ -816,7 +858,7 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   CK(ctx, dalloc(ctx, &ctx->kkt_sums, 1));
   CK(ctx, dalloc(ctx, &ctx->trace, TRACE_CAP));
   CK(ctx, dalloc(ctx, &ctx->sol, 2 * n + m));
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < SNAP_SLOTS; ++s) {
     CK(ctx, dalloc(ctx, &ctx->snap_dev[s], 2 * n + m));
     CK(ctx, cudaMallocHost(&ctx->snap_host[s], sizeof(double) * (2 * n + m)));
     CK(ctx, cudaEventCreateWithFlags(&ctx->snap_packed[s], cudaEventDisableTiming));
@@ -1576,7 +1618,7 @@ void pdhg_destroy(pdhg_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->side) cudaStreamSynchronize(ctx->side);
   for (void* p : ctx->allocs) cudaFree(p);
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < SNAP_SLOTS; ++s) {
     if (ctx->snap_host[s]) cudaFreeHost(ctx->snap_host[s]);
     if (ctx->snap_packed[s]) cudaEventDestroy(ctx->snap_packed[s]);
     if (ctx->snap_done[s]) cudaEventDestroy(ctx->snap_done[s]);
@@ -1745,7 +1787,7 @@ pdhg_status pdhg_snapshot_poll(pdhg_ctx* ctx, int64_t* count, int* ready) {
   if (ready) {
     *ready = 0;
     if (ctx->snap_count > 0) {
-      cudaError_t e = cudaEventQuery(ctx->snap_done[(ctx->snap_count - 1) % 2]);
+      cudaError_t e = cudaEventQuery(ctx->snap_done[(ctx->snap_count - 1) % SNAP_SLOTS]);
       if (e == cudaSuccess)
         *ready = 1;
       else if (e != cudaErrorNotReady)
@@ -1758,7 +1800,7 @@ pdhg_status pdhg_snapshot_poll(pdhg_ctx* ctx, int64_t* count, int* ready) {
 pdhg_status pdhg_snapshot(pdhg_ctx* ctx, double* x, double* y, double* z, int64_t* iteration, double* rel_kkt) {
   if (!ctx) return PDHG_ERR_INVALID;
   if (ctx->snap_count == 0) return fail(ctx, PDHG_ERR_STATE, "no snapshot has been taken");
-  const int slot = (int)((ctx->snap_count - 1) % 2);
+  const int slot = (int)((ctx->snap_count - 1) % SNAP_SLOTS);
   CK(ctx, cudaEventSynchronize(ctx->snap_done[slot]));
   const double* h = ctx->snap_host[slot];
   if (x) memcpy(x, h, sizeof(double) * ctx->n);
@@ -1766,6 +1808,36 @@ pdhg_status pdhg_snapshot(pdhg_ctx* ctx, double* x, double* y, double* z, int64_
   if (z) memcpy(z, h + ctx->n + ctx->m, sizeof(double) * ctx->n);
   if (iteration) *iteration = ctx->snap_iter[slot];
   if (rel_kkt) *rel_kkt = ctx->snap_rel[slot];
+  return PDHG_OK;
+}
+
+pdhg_status pdhg_snapshot_wait(pdhg_ctx* ctx, int64_t after, int64_t timeout_ms, double* x, double* y, double* z,
+                               int64_t* index, int64_t* iteration, double* rel_kkt) {
+  if (!ctx || timeout_ms < 0) return PDHG_ERR_INVALID;
+  int slot = -1;
+  int64_t seq = 0;
+  {
+    std::unique_lock<std::mutex> lk(ctx->snap_mu);
+    if (!ctx->snap_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return ctx->snap_latest > after; }))
+      return PDHG_ERR_TIMEOUT;
+    seq = ctx->snap_latest;
+    for (int s = 0; s < SNAP_SLOTS; ++s)
+      if (ctx->snap_seq[s] == seq) slot = s;
+    if (slot < 0) return PDHG_ERR_STATE;
+    ctx->snap_readers[slot] += 1;
+  }
+  const double* h = ctx->snap_host[slot];
+  if (x) memcpy(x, h, sizeof(double) * ctx->n);
+  if (y) memcpy(y, h + ctx->n, sizeof(double) * ctx->m);
+  if (z) memcpy(z, h + ctx->n + ctx->m, sizeof(double) * ctx->n);
+  if (iteration) *iteration = ctx->snap_iter[slot];
+  if (rel_kkt) *rel_kkt = ctx->snap_rel[slot];
+  if (index) *index = seq;
+  {
+    std::lock_guard<std::mutex> lk(ctx->snap_mu);
+    ctx->snap_readers[slot] -= 1;
+  }
+  ctx->snap_cv.notify_all();
   return PDHG_OK;
 }
 

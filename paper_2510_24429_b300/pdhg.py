@@ -110,6 +110,8 @@ SIGNATURES = {
     "pdhg_get_solution": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int]),
     "pdhg_snapshot_poll": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
     "pdhg_snapshot": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "pdhg_snapshot_wait": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, _P, C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "pdhg_get_info": (C.c_int, [_P, C.POINTER(pdhg_info)]),
     "pdhg_backward": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
     "pdhg_get_trace": (C.c_int, [_P, C.POINTER(pdhg_trace_rec), C.c_int64, C.POINTER(C.c_int64)]),
@@ -265,6 +267,21 @@ def pdhg_snapshot(ctx, x=None, y=None, z=None):
     it, rel = C.c_int64(), C.c_double()
     _check(load().pdhg_snapshot(ctx, *[p for p, _ in ptrs], C.byref(it), C.byref(rel)), ctx)
     return it.value, rel.value
+
+
+def pdhg_snapshot_wait(ctx, after=0, timeout_ms=1000, x=None, y=None, z=None):
+    """Newest snapshot numbered above ``after`` (blocks up to timeout_ms; may
+    run in another thread while pdhg_iterate runs): (index, iteration,
+    rel_kkt). Raises PDHGError(PDHG_ERR_TIMEOUT) if none completes in time."""
+    ptrs = [_out_ptr(a) for a in (x, y, z)]
+    if any(d for _, d in ptrs):
+        raise ValueError("snapshot buffers are host arrays")
+    idx, it, rel = C.c_int64(), C.c_int64(), C.c_double()
+    st = load().pdhg_snapshot_wait(ctx, int(after), int(timeout_ms), *[p for p, _ in ptrs], C.byref(idx),
+                                   C.byref(it), C.byref(rel))
+    if st != PDHG_OK:
+        raise PDHGError(st, "no newer snapshot within the timeout" if st == PDHG_ERR_TIMEOUT else "snapshot_wait failed")
+    return idx.value, it.value, rel.value
 
 
 def pdhg_backward(ctx, dL_dx, dL_dc, dL_db, dL_dy=None):
@@ -458,6 +475,12 @@ class Solver:
 
     def snapshot_poll(self):
         return pdhg_snapshot_poll(self.ctx)
+
+    def snapshot_wait(self, after=0, timeout_ms=1000):
+        """Thread-safe hand-off of the newest snapshot numbered above ``after``."""
+        x, y, z = np.empty(self.n), np.empty(self.m), np.empty(self.n)
+        idx, it, rel = pdhg_snapshot_wait(self.ctx, after, timeout_ms, x, y, z)
+        return dict(index=idx, iteration=it, rel_kkt=rel, x=x, y=y, z=z)
 
     def info(self):
         return pdhg_get_info(self.ctx)
