@@ -286,6 +286,10 @@ PDHG_API pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const
 PDHG_API pdhg_status pdhg_batch_info(pdhg_ctx* ctx, int64_t* iterations, int* converged, double* rel_kkt,
                                      int64_t* restarts);
 
+/* pdhg_kkt for one instance of a batch (the same measures, on that instance's
+ * problem as given): its current, average or last-restart point. */
+PDHG_API pdhg_status pdhg_batch_kkt(pdhg_ctx* ctx, int instance, int which, pdhg_kkt_info* out);
+
 /* (x, y, z) of one instance on its problem as given, into host buffers of its
  * n, m, n (any may be NULL). */
 PDHG_API pdhg_status pdhg_batch_solution(pdhg_ctx* ctx, int instance, double* x, double* y, double* z);

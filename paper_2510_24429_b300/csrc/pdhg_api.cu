@@ -2004,6 +2004,50 @@ pdhg_status pdhg_batch_info(pdhg_ctx* ctx, int64_t* iterations, int* converged, 
   return PDHG_OK;
 }
 
+pdhg_status pdhg_batch_kkt(pdhg_ctx* ctx, int instance, int which, pdhg_kkt_info* out) {
+  if (!ctx) return PDHG_ERR_INVALID;
+  if (!out) return fail(ctx, PDHG_ERR_INVALID, "out is NULL");
+  if (instance < 0 || instance >= ctx->count) return fail(ctx, PDHG_ERR_INVALID, "instance out of range");
+  if (which < PDHG_CURRENT || which > PDHG_LAST_RESTART) return fail(ctx, PDHG_ERR_INVALID, "bad point selector");
+  pdhg_status rs = set_device(ctx);
+  if (rs != PDHG_OK) return rs;
+  if (ctx->count == 1) return pdhg_kkt(ctx, which, out);
+  const double* px = which == PDHG_AVERAGE ? ctx->xavg : (which == PDHG_LAST_RESTART ? ctx->xr : ctx->x);
+  const double* py = which == PDHG_AVERAGE ? ctx->yavg : (which == PDHG_LAST_RESTART ? ctx->yr : ctx->y);
+  // the instance's units form a contiguous range of both layouts (whole blocks)
+  const int b0 = ctx->bstart_h[instance], nb = ctx->bstart_h[instance + 1] - b0;
+  Hyb Ai = ctx->A, Ti = ctx->At;
+  for (Hyb* H : {&Ai, &Ti}) {
+    H->uoff += (size_t)b0 * ctx->wpb;
+    H->uinfo += (size_t)b0 * ctx->wpb;
+    H->n_units = nb * ctx->wpb;
+  }
+  cudaStream_t s = ctx->stream;
+  launch_eval_point(Ai, Ti, px, py, ctx->bh, ctx->ch, ctx->idr, ctx->idc, nullptr, nullptr, ctx->partials, nb, s,
+                    nullptr, nullptr, 32 * ctx->wpb);
+  launch_eval_finalize(ctx->partials, nb, ctx->kkt_sums, s);
+  CK(ctx, cudaGetLastError());
+  CK(ctx, cudaMemcpyAsync(ctx->h_kkt, ctx->kkt_sums, sizeof(EvalSums), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaMemcpyAsync(ctx->h_st + instance, ctx->st + instance, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  const double* q = ctx->h_kkt->q;
+  const DevState& h = ctx->h_st[instance];
+  out->rp_norm2 = sqrt(q[Q_RP2U]);
+  out->rp_norminf = q[Q_RPINF];
+  out->rd_norm2 = sqrt(q[Q_RD2U]);
+  out->rd_norminf = q[Q_RDINF];
+  out->primal_obj = q[Q_CX];
+  out->dual_obj = q[Q_BY];
+  out->gap = fabs(q[Q_CX] - q[Q_BY]);
+  out->complementarity = q[Q_XZ];
+  out->rel_p = out->rp_norm2 / (1.0 + h.b_norm);
+  out->rel_d = out->rd_norm2 / (1.0 + h.c_norm);
+  out->rel_gap = out->gap / (1.0 + fabs(out->primal_obj) + fabs(out->dual_obj));
+  out->rel_kkt = std::max(out->rel_p, std::max(out->rel_d, out->rel_gap));
+  out->iteration = h.k;
+  return PDHG_OK;
+}
+
 pdhg_status pdhg_batch_solution(pdhg_ctx* ctx, int instance, double* x, double* y, double* z) {
   if (!ctx) return PDHG_ERR_INVALID;
   if (instance < 0 || instance >= ctx->count) return fail(ctx, PDHG_ERR_INVALID, "instance out of range");

@@ -119,6 +119,7 @@ SIGNATURES = {
     "pdhg_create_batch": (C.c_int, [C.c_int, C.POINTER(pdhg_lp_desc), C.POINTER(pdhg_options), _P, C.POINTER(_P)]),
     "pdhg_batch_info": (C.c_int, [_P, _P, _P, _P, _P]),
     "pdhg_batch_solution": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "pdhg_batch_kkt": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(pdhg_kkt_info)]),
     "pdhg_kkt_noalloc": (C.c_int, [C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P,
                                    C.POINTER(pdhg_kkt_info)]),
     "pdhg_autotune": (C.c_int, [C.c_int, C.POINTER(pdhg_lp_desc), C.POINTER(pdhg_options), C.c_char_p, _P,
@@ -415,6 +416,12 @@ class BatchSolver:
 
     def info(self):
         return pdhg_batch_info(self.ctx, len(self.sizes))
+
+    def kkt(self, i, which=PDHG_CURRENT):
+        """KKT measures of instance i (pdhg_batch_kkt)."""
+        info = pdhg_kkt_info()
+        _check(load().pdhg_batch_kkt(self.ctx, int(i), int(which), C.byref(info)), self.ctx)
+        return {k: getattr(info, k) for k, _ in pdhg_kkt_info._fields_}
 
     def solution(self, i):
         m, n = self.sizes[i]

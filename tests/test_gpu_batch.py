@@ -88,3 +88,25 @@ def test_batch_validation():
     assert ei.value.status == P.PDHG_ERR_INVALID and "instance 3" in str(ei.value)
     with pytest.raises(P.PDHGError):
         P.BatchSolver(lps, precision=P.PDHG_MIXED)
+
+
+def test_batch_kkt_per_instance():
+    """pdhg_batch_kkt of every instance equals the KKT measures of its
+    returned solution on its problem as given (oracle's definition)."""
+    lps = _batch_lps()
+    tol = 1e-6
+    with P.BatchSolver(lps) as bs:
+        bs.iterate(100000, tol)
+        for i, lp in enumerate(lps):
+            k = bs.kkt(i)
+            x, y, _ = bs.solution(i)
+            A = O.csr_matrix(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val)
+            ko = O.kkt(A, lp.b, lp.c, x, y)
+            assert k["rel_kkt"] <= tol, i
+            # residual norms near convergence are differences of O(1) terms:
+            # rounding enters at ~1e-16 of ||A|| ||x|| relative to a ~1e-6 residual
+            for key, rel in (("rp_norm2", 1e-6), ("rd_norm2", 1e-6), ("rel_kkt", 1e-6), ("primal_obj", 1e-10),
+                             ("dual_obj", 1e-10)):
+                assert k[key] == pytest.approx(ko[key], rel=rel, abs=1e-12), (i, key)
+        with pytest.raises(P.PDHGError):
+            bs.kkt(len(lps))
