@@ -31,6 +31,12 @@ What it computes, with the passage each part follows
   (power iteration), primal weight ``omega``, uniform averages of the iterates
   since the last restart, and KKT-error adaptive restarts. Every choice the
   paper leaves open is a documented reading (see ``Options``).
+* The reflected Halpern variant of that iteration, from the cuPDLP+ line the
+  paper's solver follows (Section 4.1; formula not given in the paper, so a
+  reading): ``z <- w ((1 + rho) T(z) - rho z) + (1 - w) z_r`` with ``T`` the map
+  above, ``w = (t + 1) / (t + 2)``, ``t`` the iterations since the last restart
+  and ``z_r`` the last restart point; the current iterate is the only restart
+  candidate (no averages).
 * Algorithm 1's snapshot schedule: a snapshot of the current solution each time
   ``rel_kkt`` falls to ``eps_target``, after which ``eps_target`` shrinks by
   ``eps_factor`` (0.1 in the paper).
@@ -39,7 +45,9 @@ Pins (see the tests): vertex enumeration on tiny LPs, the generator's known
 optimum, the fixed-point property of the PDHG map at an optimal pair, a
 hand-computed step and KKT on a 2x3 LP, Ruiz/Pock-Chambolle invariants, power
 iteration against a dense SVD, and an exact replay of the restart rules on
-hand-made KKT sequences.
+hand-made KKT sequences. The Halpern variant: the fixed point, the reduction
+to the PDHG map at w = 1, rho = 0, and Halpern's O(1/k) bound on the
+fixed-point residual in the PDHG metric.
 """
 from __future__ import annotations
 
@@ -85,6 +93,13 @@ class Options:
     eps_cross: float = 0.0  # 0 disables Algorithm 1's snapshot schedule
     eps_factor: float = 0.1
     snapshot_every: int = 0
+    # reflected Halpern iteration (the cuPDLP+ line the paper's solver follows,
+    # Section 4.1): z <- w ((1 + rho) T(z) - rho z) + (1 - w) z_r with T the
+    # PDHG map, w = (t + 1) / (t + 2), t the iterations since the last restart
+    # and z_r the last restart point; no averaging (the candidate is always the
+    # current iterate)
+    halpern: bool = False
+    halpern_reflect: float = 1.0
 
 
 def csr_matrix(m, n, row_ptr, col_idx, val) -> sp.csr_matrix:
@@ -221,6 +236,18 @@ def pdhg_iteration(Ah, AhT, bh, ch, x, y, tau, sigma):
     return x_new, xbar, y_new
 
 
+def halpern_iteration(Ah, AhT, bh, ch, x, y, x_anchor, y_anchor, tau, sigma, t, rho):
+    """One reflected Halpern step: with (x~, y~) = T(x, y) the PDHG map above,
+    w = (t + 1) / (t + 2), returns w ((1 + rho) (x~, y~) - rho (x, y)) + (1 - w)
+    (x_anchor, y_anchor). rho = 0 is the plain Halpern iteration of T; rho = 1
+    applies it to the reflection 2T - I."""
+    xt, _, yt = pdhg_iteration(Ah, AhT, bh, ch, x, y, tau, sigma)
+    w = (t + 1.0) / (t + 2.0)
+    x_new = w * ((1.0 + rho) * xt - rho * x) + (1.0 - w) * x_anchor
+    y_new = w * ((1.0 + rho) * yt - rho * y) + (1.0 - w) * y_anchor
+    return x_new, y_new
+
+
 # ---------------------------------------------------------------------------
 # Restart rules
 # ---------------------------------------------------------------------------
@@ -353,6 +380,12 @@ class Oracle:
 
     # -- iteration -----------------------------------------------------------
     def iterate_once(self):
+        if self.opt.halpern:
+            self.x, self.y = halpern_iteration(self.Ah, self.AhT, self.bh, self.ch, self.x, self.y, self.x_r, self.y_r,
+                                               self.tau, self.sigma, self.t, self.opt.halpern_reflect)
+            self.t += 1
+            self.k += 1
+            return
         x_new, _, y_new = pdhg_iteration(self.Ah, self.AhT, self.bh, self.ch, self.x, self.y, self.tau, self.sigma)
         self.x, self.y = x_new, y_new
         if self.opt.restarts:
@@ -365,7 +398,7 @@ class Oracle:
         """One evaluation: candidate choice, termination, snapshots, restart and
         primal-weight update. Returns True when the method has converged."""
         opt = self.opt
-        if opt.restarts and self.t > 0:
+        if opt.restarts and self.t > 0 and not opt.halpern:
             xa, ya = self.x_avg, self.y_avg
             n_cur = self.scaled_norms(self.x, self.y)
             n_avg = self.scaled_norms(xa, ya)
