@@ -494,11 +494,13 @@ def run_ours(args):
         # ---- time to tolerance (fresh solve, setup excluded) ----
         ttt = {}
         f_star = lp.f_star
-        for pname, prec in (("fp64", P.PDHG_FP64), ("mixed", P.PDHG_MIXED)):
+        # fp64_halpern: the reflected Halpern form of the iteration (option halpern)
+        for pname, prec, extra in (("fp64", P.PDHG_FP64, {}), ("mixed", P.PDHG_MIXED, {}),
+                                   ("fp64_halpern", P.PDHG_FP64, {"halpern": 1})):
             ttt[pname] = {}
             for tol in (1e-4, 1e-6):
                 with P.Solver(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, stream=stream.cuda_stream,
-                              precision=prec) as s2:
+                              precision=prec, **extra) as s2:
                     torch.cuda.synchronize()
                     t0 = time.perf_counter()
                     st, done = s2.iterate(300_000, tol)

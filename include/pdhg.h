@@ -103,6 +103,11 @@ typedef struct {
                              every precision, 0 = off, -1 = on in FP32 phases of single LPs with m >= 2^18
                              and nnz >= 2^23 (-1) */
   int panel_rows;         /* entries of y per panel; 0 = as many as fit in shared memory (0; at most 28160) */
+  int halpern;            /* 1: reflected Halpern iteration (the cuPDLP+ line, Section 4.1): z <- w ((1 + rho)
+                             T(z) - rho z) + (1 - w) z_r with T the PDHG map, w = (t + 1) / (t + 2), t the
+                             iterations since the last restart, z_r the last restart point; no averaging (the
+                             current iterate is the restart candidate). FP64 single LPs, not persistent (0) */
+  double halpern_reflect; /* rho in [0, 1] (1.0) */
   int reserved[4];
 } pdhg_options;
 

@@ -58,6 +58,9 @@ struct DevState {
   int snapshot_flag, numeric;
   int frozen;  // batch: the instance has converged; its blocks skip all work
   int pad0;
+  // reflected Halpern iteration: on, and the reflection rho
+  int halpern, pad1;
+  double rho;
   double cand_rel_kkt;
   double scratch[4];
 };

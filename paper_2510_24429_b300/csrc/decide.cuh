@@ -23,7 +23,7 @@ static __device__ void decide_one(DevState* st, TraceRec* trace) {
   double cp, cd, cg;
   scaled_norms(st->cur, cp, cd, cg);
   int which = KIND_CUR;
-  if (st->restarts_on && st->t > 0) {
+  if (st->restarts_on && st->t > 0 && !st->halpern) {  // Halpern: no averages
     double ap, ad, ag;
     scaled_norms(st->avg, ap, ad, ag);
     if (weighted_kkt(ap, ad, ag, st->omega) < weighted_kkt(cp, cd, cg, st->omega)) {

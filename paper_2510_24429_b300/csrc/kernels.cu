@@ -523,6 +523,61 @@ __global__ void __launch_bounds__(TPB) k_primal_combine(const int* __restrict__ 
   }
 }
 
+// ---- reflected Halpern form of the two half-steps (option halpern) ----------
+// With (x~, y~) the PDHG map's output, w = (t + 1) / (t + 2) (t = iterations
+// since the last restart, before this step) and the last restart point
+// (xr, yr) as anchor: x <- w ((1 + rho) x~ - rho x) + (1 - w) xr, likewise y;
+// the dual step still gathers xbar = 2 x~ - x.
+__device__ __forceinline__ double halpern_weight(const DevState* st, int it) {
+  const double t = (double)(st->t + it);
+  return (t + 1.0) / (t + 2.0);
+}
+
+struct PrimalHalpernOp {
+  using State = NoState;
+  const double* __restrict__ ch;
+  double* __restrict__ x;
+  double* __restrict__ xbar;
+  const double* __restrict__ xr;
+  double tau, w, rho;
+  __device__ __forceinline__ State begin(int) { return {}; }
+  __device__ __forceinline__ void finish(int j, double g, const State&) {
+    const double xj = __ldcs(x + j);
+    const double xt = relu(xj - tau * (__ldcs(ch + j) - g));
+    xbar[j] = 2.0 * xt - xj;
+    __stcs(x + j, w * ((1.0 + rho) * xt - rho * xj) + (1.0 - w) * __ldcs(xr + j));
+  }
+};
+
+struct DualHalpernOp {
+  using State = NoState;
+  const double* __restrict__ bh;
+  double* __restrict__ y;
+  const double* __restrict__ yr;
+  double sigma, w, rho;
+  __device__ __forceinline__ State begin(int) { return {}; }
+  __device__ __forceinline__ void finish(int i, double h, const State&) {
+    const double yi = y[i];
+    const double yt = yi + sigma * (__ldcs(bh + i) - h);
+    y[i] = w * ((1.0 + rho) * yt - rho * yi) + (1.0 - w) * __ldcs(yr + i);
+  }
+};
+
+__global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
+    k_primal_step_halpern(Hyb At, const double* __restrict__ y, const double* __restrict__ ch, double* __restrict__ x,
+                          double* __restrict__ xbar, const double* __restrict__ xr, const DevState* __restrict__ st,
+                          int it) {
+  PrimalHalpernOp op{ch, x, xbar, xr, st->tau, halpern_weight(st, it), st->rho};
+  hyb_dot(At, At.v, GlobalGather<double>{y}, op);
+}
+
+__global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
+    k_dual_step_halpern(Hyb A, const double* __restrict__ xbar, const double* __restrict__ bh, double* __restrict__ y,
+                        const double* __restrict__ yr, const DevState* __restrict__ st, int it) {
+  DualHalpernOp op{bh, y, yr, st->sigma, halpern_weight(st, it), st->rho};
+  hyb_dot(A, A.v, GlobalGather<double>{xbar}, op);
+}
+
 template <class T>
 struct DualOp {
   using State = NoState;
@@ -1123,6 +1178,14 @@ template cudaError_t launch_primal_panels<double>(const Hyb&, const double*, con
 template cudaError_t launch_primal_panels<float>(const Hyb&, const float*, const PanelLayout&, const float*,
                                                  const float*, float*, float*, float*, float*, const DevState*, int,
                                                  int, int, cudaStream_t);
+void launch_primal_step_halpern(const Hyb& At, const double* y, const double* ch, double* x, double* xbar,
+                                const double* xr, const DevState* st, int it, int grid, cudaStream_t s, int tpb) {
+  k_primal_step_halpern<<<grid, tpb, 0, s>>>(At, y, ch, x, xbar, xr, st, it);
+}
+void launch_dual_step_halpern(const Hyb& A, const double* xbar, const double* bh, double* y, const double* yr,
+                              const DevState* st, int it, int grid, cudaStream_t s, int tpb) {
+  k_dual_step_halpern<<<grid, tpb, 0, s>>>(A, xbar, bh, y, yr, st, it);
+}
 void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,
                           const DevState* st, int accumulate, int grid, cudaStream_t s) {
   k_dual_step_hot<<<grid, HOT_TPB, (size_t)hot * sizeof(double), s>>>(A, xbar, hot, bh, y, ysum, st, accumulate);

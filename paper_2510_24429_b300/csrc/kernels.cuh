@@ -46,6 +46,12 @@ void launch_primal_step(const Hyb& At, const double* y, const double* ch, double
 void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
                       const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst = nullptr,
                       int tpb = TPB);
+// reflected Halpern form of the two half-steps (FP64): it = index of the step
+// within the launch sequence since st->t was last updated; xr, yr = anchor
+void launch_primal_step_halpern(const Hyb& At, const double* y, const double* ch, double* x, double* xbar,
+                                const double* xr, const DevState* st, int it, int grid, cudaStream_t s, int tpb);
+void launch_dual_step_halpern(const Hyb& A, const double* xbar, const double* bh, double* y, const double* yr,
+                              const DevState* st, int it, int grid, cudaStream_t s, int tpb);
 // the same two half-steps in FP32 (values At.v32 / A.v32, FP32 vectors and
 // accumulation); tau and sigma are read from the FP64 state and rounded
 void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float* x, float* xbar, float* xsum,

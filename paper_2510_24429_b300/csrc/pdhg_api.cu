@@ -939,6 +939,8 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   h.next_snapshot = o.snapshot_every;
   h.restarts_on = o.restarts;
   h.primal_weight_on = o.primal_weight;
+  h.halpern = o.halpern;
+  h.rho = o.halpern_reflect;
   *ctx->h_st = h;
   CK(ctx, cudaMemcpyAsync(ctx->st, ctx->h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
   launch_finish_setup(ctx->st, ctx->scal, o.step_factor, o.primal_weight, s);
@@ -1043,7 +1045,9 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
       if (rs != PDHG_OK) return rs;
     }
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
-    {
+    if (o.halpern) {
+      launch_primal_step_halpern(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xr, ctx->st, (int)it, grT, s, tpb);
+    } else {
       pdhg_status rs = ctx->phase32 ? primal_step(ctx, true, ctx->y32, ctx->x32, ctx->xbar32, ctx->xsum32,
                                                   o.restarts, grT, tpb)
                                     : primal_step(ctx, false, ctx->y, ctx->x, ctx->xbar, ctx->xsum, o.restarts, grT,
@@ -1051,7 +1055,9 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
       if (rs != PDHG_OK) return rs;
     }
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
-    if (ctx->phase32)
+    if (o.halpern)
+      launch_dual_step_halpern(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->yr, ctx->st, (int)it, grA, s, tpb);
+    else if (ctx->phase32)
       launch_dual_step32(ctx->A, ctx->xbar32, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st, o.restarts, grA, s, tpb);
     else if (hot > 0)
       launch_dual_step_hot(ctx->A, ctx->xbar, hot, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, ctx->sms, s);
@@ -1077,7 +1083,7 @@ pdhg_status enqueue_eval(pdhg_ctx* ctx) {
     widen_current(ctx);
     ctx->launches += 2;
   }
-  if (o.restarts) {
+  if (o.restarts && !o.halpern) {  // Halpern: no averages
     if (p32)
       launch_make_average32(ctx->xsum32, ctx->ysum32, ctx->x32, ctx->y32, ctx->xavg, ctx->yavg, n, m, ctx->st, gv,
                             s);
@@ -1092,7 +1098,7 @@ pdhg_status enqueue_eval(pdhg_ctx* ctx) {
                    ctx->ysum32, n, m, gv, s);
   else
     launch_apply(ctx->st, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, ctx->xsum, ctx->ysum, n, m, gv, s);
-  ctx->launches += (o.restarts ? 4 : 0) + 3 + 2;
+  ctx->launches += (o.restarts && !o.halpern ? 4 : 0) + 3 + 2;
   CK(ctx, cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevState) * ctx->count, cudaMemcpyDeviceToHost, s));
   CK(ctx, cudaGetLastError());
   return PDHG_OK;
@@ -1512,6 +1518,8 @@ void pdhg_default_options(pdhg_options* o) {
   o->step_block = 256;
   o->primal_panels = -1;
   o->panel_rows = 0;
+  o->halpern = 0;
+  o->halpern_reflect = 1.0;
 }
 
 pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
@@ -1545,6 +1553,12 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     return fail(nullptr, PDHG_ERR_INVALID, "primal_panels must be -1, 0 or 1 and panel_rows in [0, 28160]");
   if (o.persistent && o.primal_panels == 1)
     return fail(nullptr, PDHG_ERR_INVALID, "persistent = 1 and primal_panels = 1 exclude each other");
+  if (o.halpern != 0 && (o.halpern != 1 || o.precision != PDHG_FP64 || o.persistent || o.primal_panels == 1 ||
+                         o.record_for_backward || o.dual_hot_cols || !(o.halpern_reflect >= 0.0) ||
+                         !(o.halpern_reflect <= 1.0)))
+    return fail(nullptr, PDHG_ERR_INVALID,
+                "halpern = 1 needs precision FP64, halpern_reflect in [0, 1], and no persistent loop, forced panels, "
+                "recording or hot columns");
   if (o.persistent) {
     if (o.persistent != 1 || o.precision != PDHG_FP64 || o.record_for_backward || o.kernel_timing ||
         o.dual_hot_cols)
@@ -1935,6 +1949,7 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
     return fail(nullptr, PDHG_ERR_INVALID, "step_block must be 128, 256 or 512");
   if (o.primal_panels == 1)
     return fail(nullptr, PDHG_ERR_INVALID, "primal_panels = 1 is for single LPs (batches use the direct primal step)");
+  if (o.halpern) return fail(nullptr, PDHG_ERR_INVALID, "halpern = 1 is for single LPs");
   if (o.persistent != 0 && (o.persistent != 1 || o.kernel_timing))
     return fail(nullptr, PDHG_ERR_INVALID, "persistent must be 0 or 1, and 1 excludes kernel timing");
   int64_t mt = 0, nt = 0, zt = 0;

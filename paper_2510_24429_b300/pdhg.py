@@ -57,6 +57,8 @@ class pdhg_options(C.Structure):
         ("step_block", C.c_int),
         ("primal_panels", C.c_int),
         ("panel_rows", C.c_int),
+        ("halpern", C.c_int),
+        ("halpern_reflect", C.c_double),
         ("reserved", C.c_int * 4),
     ]
 
