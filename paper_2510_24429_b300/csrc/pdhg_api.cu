@@ -391,6 +391,14 @@ void CUDART_CB snapshot_landed(void* p) {
 
 pdhg_status take_snapshot(pdhg_ctx* ctx) {
   const int slot = (int)(ctx->snap_count % SNAP_SLOTS);
+  if (!ctx->snap_host[slot]) {
+    // ring slots are allocated on first use (pinned memory is slow to allocate)
+    const int64_t len = 2 * ctx->n + ctx->m;
+    CK(ctx, dalloc(ctx, &ctx->snap_dev[slot], len));
+    CK(ctx, cudaMallocHost(&ctx->snap_host[slot], sizeof(double) * len));
+    CK(ctx, cudaEventCreateWithFlags(&ctx->snap_packed[slot], cudaEventDisableTiming));
+    CK(ctx, cudaEventCreateWithFlags(&ctx->snap_done[slot], cudaEventDisableTiming));
+  }
   // the slot's previous copy and its callback are done
   if (ctx->snap_count >= SNAP_SLOTS) CK(ctx, cudaEventSynchronize(ctx->snap_done[slot]));
   {
@@ -858,12 +866,6 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   CK(ctx, dalloc(ctx, &ctx->kkt_sums, 1));
   CK(ctx, dalloc(ctx, &ctx->trace, TRACE_CAP));
   CK(ctx, dalloc(ctx, &ctx->sol, 2 * n + m));
-  for (int s = 0; s < SNAP_SLOTS; ++s) {
-    CK(ctx, dalloc(ctx, &ctx->snap_dev[s], 2 * n + m));
-    CK(ctx, cudaMallocHost(&ctx->snap_host[s], sizeof(double) * (2 * n + m)));
-    CK(ctx, cudaEventCreateWithFlags(&ctx->snap_packed[s], cudaEventDisableTiming));
-    CK(ctx, cudaEventCreateWithFlags(&ctx->snap_done[s], cudaEventDisableTiming));
-  }
   CK(ctx, cudaMallocHost(&ctx->h_st, sizeof(DevState)));
   CK(ctx, cudaMallocHost(&ctx->h_kkt, sizeof(EvalSums)));
   for (int i = 0; i < 3 * EV_POOL; ++i) CK(ctx, cudaEventCreate(&ctx->ev[i]));
