@@ -106,7 +106,8 @@ typedef struct {
   int halpern;            /* 1: reflected Halpern iteration (the cuPDLP+ line, Section 4.1): z <- w ((1 + rho)
                              T(z) - rho z) + (1 - w) z_r with T the PDHG map, w = (t + 1) / (t + 2), t the
                              iterations since the last restart, z_r the last restart point; no averaging (the
-                             current iterate is the restart candidate). FP64 single LPs, not persistent (0) */
+                             current iterate is the restart candidate). Single LPs, every precision, not
+                             persistent (0) */
   double halpern_reflect; /* rho in [0, 1] (1.0) */
   int reserved[4];
 } pdhg_options;

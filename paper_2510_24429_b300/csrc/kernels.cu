@@ -437,6 +437,13 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STE
   hyb_dot(At, vals, GlobalGather<T>{y}, op);
 }
 
+// weight w = (t + 1) / (t + 2) of the reflected Halpern step that runs as step
+// `it` after st->t was last updated (t = iterations since the last restart)
+__device__ __forceinline__ double halpern_weight(const DevState* st, int it) {
+  const double t = (double)(st->t + it);
+  return (t + 1.0) / (t + 2.0);
+}
+
 // ---- panel-tiled primal half-step (option primal_panels) --------------------
 // The rows of A^T are cut into segments by panels of panel_rows consecutive
 // entries of y. Pass 1: every block stages one panel of y in shared memory and
@@ -504,22 +511,31 @@ __global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
 
 // one thread per column; the update's operands are loaded before the partial
 // sums so that their latencies overlap (same arithmetic as PrimalOp)
+// halpern_it >= 0: the reflected Halpern update with xsum as the anchor (the
+// Halpern form keeps its anchor where the sums would be; see PrimalHalpernOp)
 template <class T>
 __global__ void __launch_bounds__(TPB) k_primal_combine(const int* __restrict__ cptr, const T* __restrict__ partial,
                                                         const T* __restrict__ ch, T* __restrict__ x,
                                                         T* __restrict__ xbar, T* __restrict__ xsum, int n,
-                                                        const DevState* __restrict__ st, int accumulate) {
+                                                        const DevState* __restrict__ st, int accumulate,
+                                                        int halpern_it) {
   const T tau = (T)st->tau;
+  const bool halp = halpern_it >= 0;
+  const T w = halp ? (T)halpern_weight(st, halpern_it) : T(0), rho = (T)st->rho;
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
     const T xj = __ldcs(x + j), cj = __ldcs(ch + j);
-    const T sj = accumulate ? __ldcs(xsum + j) : T(0);
+    const T sj = (accumulate || halp) ? __ldcs(xsum + j) : T(0);
     const int q0 = __ldg(cptr + j), q1 = __ldg(cptr + j + 1);
     T g = T(0);
     for (int q = q0; q < q1; ++q) g += __ldcs(partial + q);
     const T xn = relu(xj - tau * (cj - g));
     xbar[j] = T(2) * xn - xj;  // default policy: gathered by the dual step next
-    __stcs(x + j, xn);
-    if (accumulate) __stcs(xsum + j, sj + xn);
+    if (halp) {
+      __stcs(x + j, w * ((T(1) + rho) * xn - rho * xj) + (T(1) - w) * sj);
+    } else {
+      __stcs(x + j, xn);
+      if (accumulate) __stcs(xsum + j, sj + xn);
+    }
   }
 }
 
@@ -528,54 +544,53 @@ __global__ void __launch_bounds__(TPB) k_primal_combine(const int* __restrict__ 
 // since the last restart, before this step) and the last restart point
 // (xr, yr) as anchor: x <- w ((1 + rho) x~ - rho x) + (1 - w) xr, likewise y;
 // the dual step still gathers xbar = 2 x~ - x.
-__device__ __forceinline__ double halpern_weight(const DevState* st, int it) {
-  const double t = (double)(st->t + it);
-  return (t + 1.0) / (t + 2.0);
-}
-
+template <class T>
 struct PrimalHalpernOp {
   using State = NoState;
-  const double* __restrict__ ch;
-  double* __restrict__ x;
-  double* __restrict__ xbar;
-  const double* __restrict__ xr;
-  double tau, w, rho;
+  const T* __restrict__ ch;
+  T* __restrict__ x;
+  T* __restrict__ xbar;
+  const T* __restrict__ xr;
+  T tau, w, rho;
   __device__ __forceinline__ State begin(int) { return {}; }
-  __device__ __forceinline__ void finish(int j, double g, const State&) {
-    const double xj = __ldcs(x + j);
-    const double xt = relu(xj - tau * (__ldcs(ch + j) - g));
-    xbar[j] = 2.0 * xt - xj;
-    __stcs(x + j, w * ((1.0 + rho) * xt - rho * xj) + (1.0 - w) * __ldcs(xr + j));
+  __device__ __forceinline__ void finish(int j, T g, const State&) {
+    const T xj = __ldcs(x + j);
+    const T xt = relu(xj - tau * (__ldcs(ch + j) - g));
+    xbar[j] = T(2) * xt - xj;
+    __stcs(x + j, w * ((T(1) + rho) * xt - rho * xj) + (T(1) - w) * __ldcs(xr + j));
   }
 };
 
+template <class T>
 struct DualHalpernOp {
   using State = NoState;
-  const double* __restrict__ bh;
-  double* __restrict__ y;
-  const double* __restrict__ yr;
-  double sigma, w, rho;
+  const T* __restrict__ bh;
+  T* __restrict__ y;
+  const T* __restrict__ yr;
+  T sigma, w, rho;
   __device__ __forceinline__ State begin(int) { return {}; }
-  __device__ __forceinline__ void finish(int i, double h, const State&) {
-    const double yi = y[i];
-    const double yt = yi + sigma * (__ldcs(bh + i) - h);
-    y[i] = w * ((1.0 + rho) * yt - rho * yi) + (1.0 - w) * __ldcs(yr + i);
+  __device__ __forceinline__ void finish(int i, T h, const State&) {
+    const T yi = y[i];
+    const T yt = yi + sigma * (__ldcs(bh + i) - h);
+    y[i] = w * ((T(1) + rho) * yt - rho * yi) + (T(1) - w) * __ldcs(yr + i);
   }
 };
 
+template <class T>
 __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
-    k_primal_step_halpern(Hyb At, const double* __restrict__ y, const double* __restrict__ ch, double* __restrict__ x,
-                          double* __restrict__ xbar, const double* __restrict__ xr, const DevState* __restrict__ st,
-                          int it) {
-  PrimalHalpernOp op{ch, x, xbar, xr, st->tau, halpern_weight(st, it), st->rho};
-  hyb_dot(At, At.v, GlobalGather<double>{y}, op);
+    k_primal_step_halpern(Hyb At, const T* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
+                          T* __restrict__ x, T* __restrict__ xbar, const T* __restrict__ xr,
+                          const DevState* __restrict__ st, int it) {
+  PrimalHalpernOp<T> op{ch, x, xbar, xr, (T)st->tau, (T)halpern_weight(st, it), (T)st->rho};
+  hyb_dot(At, vals, GlobalGather<T>{y}, op);
 }
 
+template <class T>
 __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
-    k_dual_step_halpern(Hyb A, const double* __restrict__ xbar, const double* __restrict__ bh, double* __restrict__ y,
-                        const double* __restrict__ yr, const DevState* __restrict__ st, int it) {
-  DualHalpernOp op{bh, y, yr, st->sigma, halpern_weight(st, it), st->rho};
-  hyb_dot(A, A.v, GlobalGather<double>{xbar}, op);
+    k_dual_step_halpern(Hyb A, const T* __restrict__ vals, const T* __restrict__ xbar, const T* __restrict__ bh,
+                        T* __restrict__ y, const T* __restrict__ yr, const DevState* __restrict__ st, int it) {
+  DualHalpernOp<T> op{bh, y, yr, (T)st->sigma, (T)halpern_weight(st, it), (T)st->rho};
+  hyb_dot(A, vals, GlobalGather<T>{xbar}, op);
 }
 
 template <class T>
@@ -962,7 +977,7 @@ __global__ void k_apply32(const DevState* __restrict__ st, float* __restrict__ x
           x[i] = (double)v;
         }
         xr[i] = x[i];
-        xs[i] = 0.0f;
+        xs[i] = st->halpern ? x32[i] : 0.0f;  // Halpern: the FP32 anchor
       }
     }
     if (i < m) {
@@ -976,7 +991,7 @@ __global__ void k_apply32(const DevState* __restrict__ st, float* __restrict__ x
           y[i] = (double)v;
         }
         yr[i] = y[i];
-        ys[i] = 0.0f;
+        ys[i] = st->halpern ? y32[i] : 0.0f;
       }
     }
   }
@@ -1165,27 +1180,39 @@ cudaError_t configure_primal_panels() {
 template <class T>
 cudaError_t launch_primal_panels(const Hyb& Pn, const T* vals, const PanelLayout& L, const T* y, const T* ch, T* x,
                                  T* xbar, T* xsum, T* partial, const DevState* st, int accumulate, int n, int grid_n,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, int halpern_it) {
   const size_t smem = sizeof(T) * (size_t)L.rows;
   k_primal_panels<T><<<L.blocks, PANEL_TPB, smem, s>>>(Pn, vals, y, L.m, L.rows, L.binfo, L.ustart, L.segout,
                                                         partial);
-  k_primal_combine<T><<<(n + TPB - 1) / TPB, TPB, 0, s>>>(L.cptr, partial, ch, x, xbar, xsum, n, st, accumulate);
+  k_primal_combine<T><<<(n + TPB - 1) / TPB, TPB, 0, s>>>(L.cptr, partial, ch, x, xbar, xsum, n, st, accumulate,
+                                                          halpern_it);
   return cudaGetLastError();
 }
 template cudaError_t launch_primal_panels<double>(const Hyb&, const double*, const PanelLayout&, const double*,
                                                   const double*, double*, double*, double*, double*,
-                                                  const DevState*, int, int, int, cudaStream_t);
+                                                  const DevState*, int, int, int, cudaStream_t, int);
 template cudaError_t launch_primal_panels<float>(const Hyb&, const float*, const PanelLayout&, const float*,
                                                  const float*, float*, float*, float*, float*, const DevState*, int,
-                                                 int, int, cudaStream_t);
-void launch_primal_step_halpern(const Hyb& At, const double* y, const double* ch, double* x, double* xbar,
-                                const double* xr, const DevState* st, int it, int grid, cudaStream_t s, int tpb) {
-  k_primal_step_halpern<<<grid, tpb, 0, s>>>(At, y, ch, x, xbar, xr, st, it);
+                                                 int, int, cudaStream_t, int);
+template <class T>
+void launch_primal_step_halpern(const Hyb& At, const T* vals, const T* y, const T* ch, T* x, T* xbar, const T* xr,
+                                const DevState* st, int it, int grid, cudaStream_t s, int tpb) {
+  k_primal_step_halpern<T><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xr, st, it);
 }
-void launch_dual_step_halpern(const Hyb& A, const double* xbar, const double* bh, double* y, const double* yr,
+template <class T>
+void launch_dual_step_halpern(const Hyb& A, const T* vals, const T* xbar, const T* bh, T* y, const T* yr,
                               const DevState* st, int it, int grid, cudaStream_t s, int tpb) {
-  k_dual_step_halpern<<<grid, tpb, 0, s>>>(A, xbar, bh, y, yr, st, it);
+  k_dual_step_halpern<T><<<grid, tpb, 0, s>>>(A, vals, xbar, bh, y, yr, st, it);
 }
+template void launch_primal_step_halpern<double>(const Hyb&, const double*, const double*, const double*, double*,
+                                                 double*, const double*, const DevState*, int, int, cudaStream_t,
+                                                 int);
+template void launch_primal_step_halpern<float>(const Hyb&, const float*, const float*, const float*, float*, float*,
+                                                const float*, const DevState*, int, int, cudaStream_t, int);
+template void launch_dual_step_halpern<double>(const Hyb&, const double*, const double*, const double*, double*,
+                                               const double*, const DevState*, int, int, cudaStream_t, int);
+template void launch_dual_step_halpern<float>(const Hyb&, const float*, const float*, const float*, float*,
+                                              const float*, const DevState*, int, int, cudaStream_t, int);
 void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,
                           const DevState* st, int accumulate, int grid, cudaStream_t s) {
   k_dual_step_hot<<<grid, HOT_TPB, (size_t)hot * sizeof(double), s>>>(A, xbar, hot, bh, y, ysum, st, accumulate);

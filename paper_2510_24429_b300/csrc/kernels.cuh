@@ -46,11 +46,14 @@ void launch_primal_step(const Hyb& At, const double* y, const double* ch, double
 void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
                       const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst = nullptr,
                       int tpb = TPB);
-// reflected Halpern form of the two half-steps (FP64): it = index of the step
-// within the launch sequence since st->t was last updated; xr, yr = anchor
-void launch_primal_step_halpern(const Hyb& At, const double* y, const double* ch, double* x, double* xbar,
-                                const double* xr, const DevState* st, int it, int grid, cudaStream_t s, int tpb);
-void launch_dual_step_halpern(const Hyb& A, const double* xbar, const double* bh, double* y, const double* yr,
+// reflected Halpern form of the two half-steps (values vals in precision T):
+// it = index of the step within the launches since st->t was last updated;
+// xr, yr = the anchor (the last restart point)
+template <class T>
+void launch_primal_step_halpern(const Hyb& At, const T* vals, const T* y, const T* ch, T* x, T* xbar, const T* xr,
+                                const DevState* st, int it, int grid, cudaStream_t s, int tpb);
+template <class T>
+void launch_dual_step_halpern(const Hyb& A, const T* vals, const T* xbar, const T* bh, T* y, const T* yr,
                               const DevState* st, int it, int grid, cudaStream_t s, int tpb);
 // the same two half-steps in FP32 (values At.v32 / A.v32, FP32 vectors and
 // accumulation); tau and sigma are read from the FP64 state and rounded
@@ -102,11 +105,12 @@ struct PanelLayout {
 };
 // allow the panel kernels their shared memory (once per device, outside graph capture)
 cudaError_t configure_primal_panels();
-// both passes (grid_n: grid of the per-column pass)
+// both passes (grid_n: grid of the per-column pass); halpern_it >= 0: the
+// reflected Halpern update of step halpern_it with xsum as the anchor
 template <class T>
 cudaError_t launch_primal_panels(const Hyb& Pn, const T* vals, const PanelLayout& L, const T* y, const T* ch, T* x,
                                  T* xbar, T* xsum, T* partial, const DevState* st, int accumulate, int n, int grid_n,
-                                 cudaStream_t s);
+                                 cudaStream_t s, int halpern_it = -1);
 // the same step, persistent (grid = number of SMs), with xbar[0, hot) staged
 // in shared memory; hot <= HOT_MAX
 void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,

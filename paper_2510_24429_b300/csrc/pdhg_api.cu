@@ -983,8 +983,13 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
     launch_narrow(ctx->bh32, ctx->bh, m, gm, s);
     launch_narrow(ctx->x32, ctx->x, n, gn, s);
     launch_narrow(ctx->y32, ctx->y, m, gm, s);
-    CK(ctx, cudaMemsetAsync(ctx->xsum32, 0, sizeof(float) * n, s));
-    CK(ctx, cudaMemsetAsync(ctx->ysum32, 0, sizeof(float) * m, s));
+    if (o.halpern) {  // the FP32 sums hold the Halpern anchor: the starting point
+      CK(ctx, cudaMemcpyAsync(ctx->xsum32, ctx->x32, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+      CK(ctx, cudaMemcpyAsync(ctx->ysum32, ctx->y32, sizeof(float) * m, cudaMemcpyDeviceToDevice, s));
+    } else {
+      CK(ctx, cudaMemsetAsync(ctx->xsum32, 0, sizeof(float) * n, s));
+      CK(ctx, cudaMemsetAsync(ctx->ysum32, 0, sizeof(float) * m, s));
+    }
     // the FP64 evaluation point is the FP32 iterate, exactly
     launch_widen(ctx->x, ctx->x32, n, gn, s);
     launch_widen(ctx->y, ctx->y32, m, gm, s);
@@ -1047,8 +1052,21 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
       if (rs != PDHG_OK) return rs;
     }
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
-    if (o.halpern) {
-      launch_primal_step_halpern(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xr, ctx->st, (int)it, grT, s, tpb);
+    if (o.halpern && !ctx->phase32) {
+      launch_primal_step_halpern<double>(ctx->At, ctx->At.v, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xr, ctx->st,
+                                         (int)it, grT, s, tpb);
+    } else if (o.halpern) {
+      // FP32 Halpern: the FP32 sums hold the FP32 anchor (no averages in this form)
+      if (ctx->panels_on) {
+        cudaError_t e = launch_primal_panels<float>(ctx->Pn, ctx->Pn.v32, ctx->pl, ctx->y32, ctx->ch32, ctx->x32,
+                                                    ctx->xbar32, ctx->xsum32, ctx->pn_partial32, ctx->st, 0,
+                                                    (int)ctx->n, vec_grid(ctx, ctx->n), s, (int)it);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "panel-tiled primal step");
+        ctx->launches += 1;
+      } else {
+        launch_primal_step_halpern<float>(ctx->At, ctx->At.v32, ctx->y32, ctx->ch32, ctx->x32, ctx->xbar32,
+                                          ctx->xsum32, ctx->st, (int)it, grT, s, tpb);
+      }
     } else {
       pdhg_status rs = ctx->phase32 ? primal_step(ctx, true, ctx->y32, ctx->x32, ctx->xbar32, ctx->xsum32,
                                                   o.restarts, grT, tpb)
@@ -1057,8 +1075,12 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
       if (rs != PDHG_OK) return rs;
     }
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
-    if (o.halpern)
-      launch_dual_step_halpern(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->yr, ctx->st, (int)it, grA, s, tpb);
+    if (o.halpern && !ctx->phase32)
+      launch_dual_step_halpern<double>(ctx->A, ctx->A.v, ctx->xbar, ctx->bh, ctx->y, ctx->yr, ctx->st, (int)it, grA,
+                                       s, tpb);
+    else if (o.halpern)
+      launch_dual_step_halpern<float>(ctx->A, ctx->A.v32, ctx->xbar32, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st,
+                                      (int)it, grA, s, tpb);
     else if (ctx->phase32)
       launch_dual_step32(ctx->A, ctx->xbar32, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st, o.restarts, grA, s, tpb);
     else if (hot > 0)
@@ -1555,12 +1577,11 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     return fail(nullptr, PDHG_ERR_INVALID, "primal_panels must be -1, 0 or 1 and panel_rows in [0, 28160]");
   if (o.persistent && o.primal_panels == 1)
     return fail(nullptr, PDHG_ERR_INVALID, "persistent = 1 and primal_panels = 1 exclude each other");
-  if (o.halpern != 0 && (o.halpern != 1 || o.precision != PDHG_FP64 || o.persistent || o.primal_panels == 1 ||
-                         o.record_for_backward || o.dual_hot_cols || !(o.halpern_reflect >= 0.0) ||
-                         !(o.halpern_reflect <= 1.0)))
+  // (FP64 phases of the Halpern form always run the direct primal step)
+  if (o.halpern != 0 && (o.halpern != 1 || o.persistent || o.record_for_backward || o.dual_hot_cols ||
+                         !(o.halpern_reflect >= 0.0) || !(o.halpern_reflect <= 1.0)))
     return fail(nullptr, PDHG_ERR_INVALID,
-                "halpern = 1 needs precision FP64, halpern_reflect in [0, 1], and no persistent loop, forced panels, "
-                "recording or hot columns");
+                "halpern = 1 needs halpern_reflect in [0, 1], and no persistent loop, recording or hot columns");
   if (o.persistent) {
     if (o.persistent != 1 || o.precision != PDHG_FP64 || o.record_for_backward || o.kernel_timing ||
         o.dual_hot_cols)

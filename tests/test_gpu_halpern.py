@@ -82,8 +82,43 @@ def test_graph_replay_matches_direct_launches(tiny_lp):
         np.testing.assert_array_equal(a, b)
 
 
+def test_fp32_close_to_fp64_oracle(tiny_lp):
+    orc, _ = _pair(tiny_lp, **TINY_PLAIN)
+    orc.run(100)
+    with P.Solver.from_lp(tiny_lp, precision=P.PDHG_FP32, halpern=1, pock_chambolle=0, restarts=0,
+                          primal_weight=0) as sol:
+        sol.iterate(100)
+        x, y, _ = sol.solution()
+    xo, yo, _ = orc.solution()
+    assert rel_err(x, xo) < 1e-4 and rel_err(y, yo) < 1e-4
+    assert rel_err(x, xo) > 0
+
+
+def test_fp32_panels_match_direct_fp32(tiny_lp):
+    runs = []
+    for opts in (dict(primal_panels=1, panel_rows=32), dict(primal_panels=0)):
+        with P.Solver.from_lp(tiny_lp, precision=P.PDHG_FP32, halpern=1, **opts) as sol:
+            sol.iterate(640)
+            runs.append(sol.solution())
+    for a, b in zip(*runs):
+        assert rel_err(a, b) <= 1e-4
+
+
+@pytest.mark.parametrize("panels", [0, 1])
+def test_mixed_reaches_tolerance_and_optimum(tiny_lp, panels):
+    lp = tiny_lp
+    with P.Solver.from_lp(lp, precision=P.PDHG_MIXED, halpern=1, primal_panels=panels, panel_rows=48) as sol:
+        st, done = sol.iterate(200000, 1e-8)
+        info = sol.info()
+        k = sol.kkt()
+    assert st == P.PDHG_OK and k["rel_kkt"] <= 1e-8
+    assert info["precision_now"] == P.PDHG_FP64 and 0 < info["polish_started_at"] <= done
+    assert k["primal_obj"] == pytest.approx(lp.f_star, rel=1e-7)
+
+
 def test_option_checks(tiny_lp):
-    for bad in (dict(precision=P.PDHG_FP32), dict(persistent=1), dict(halpern_reflect=1.5), dict(primal_panels=1)):
+    for bad in (dict(persistent=1), dict(halpern_reflect=1.5), dict(record_for_backward=1, restarts=0,
+                                                                      primal_weight=0)):
         with pytest.raises(P.PDHGError) as ei:
             P.Solver.from_lp(tiny_lp, halpern=1, **bad)
         assert ei.value.status == P.PDHG_ERR_INVALID, bad
