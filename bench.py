@@ -275,12 +275,23 @@ def run_batch(P, torch, count=256, tol=1e-6, seed=0):
     per_iter_bytes = np.array([24.0 * lp.nnz + 56.0 * lp.n + 48.0 * lp.m for lp in lps])
     peak, _ = measured_peaks()
     gbs = float((it * per_iter_bytes).sum() / sec / 1e9)
+    # the same batch with the reflected Halpern form
+    with P.BatchSolver(lps, halpern=1, **layout) as bh:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sth, _ = bh.iterate(200_000, tol)
+        torch.cuda.synchronize()
+        sec_h = time.perf_counter() - t0
+        ih = bh.info()
+    halpern = {"seconds_to_all_converged": sec_h, "all_converged": bool(ih["converged"].all()),
+               "iterations_max": int(ih["iterations"].max()), "iterations_median": float(np.median(ih["iterations"]))}
     return {"workload": f"{count} LPs, m log-uniform in [1e3, 1e5] (sum {sum(sizes)}), n = 2.5 m, 5 per column, "
                         f"nnz {sum(lp.nnz for lp in lps)}, FP64, each to rel. KKT {tol:g}",
             "seconds_to_all_converged": sec, "setup_s": setup_s, "all_converged": bool(info["converged"].all()),
             "iterations_max": int(it.max()), "iterations_median": float(np.median(it)),
             "aggregate_iters_per_s": float(it.sum() / sec), "hbm_gbs_active": gbs, "hbm_frac_active": gbs / peak,
-            "gpu_launches": eng["kernel_launches"], "autotuned_layout": layout, "autotune_s": tune_s}
+            "gpu_launches": eng["kernel_launches"], "autotuned_layout": layout, "autotune_s": tune_s,
+            "halpern": halpern}
 
 
 # ---------------------------------------------------------------------------

@@ -580,7 +580,9 @@ template <class T>
 __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
     k_primal_step_halpern(Hyb At, const T* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
                           T* __restrict__ x, T* __restrict__ xbar, const T* __restrict__ xr,
-                          const DevState* __restrict__ st, int it) {
+                          const DevState* __restrict__ sts, const int* __restrict__ binst, int it) {
+  const DevState* st = block_state(sts, binst);
+  if (st->frozen) return;
   PrimalHalpernOp<T> op{ch, x, xbar, xr, (T)st->tau, (T)halpern_weight(st, it), (T)st->rho};
   hyb_dot(At, vals, GlobalGather<T>{y}, op);
 }
@@ -588,7 +590,10 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STE
 template <class T>
 __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
     k_dual_step_halpern(Hyb A, const T* __restrict__ vals, const T* __restrict__ xbar, const T* __restrict__ bh,
-                        T* __restrict__ y, const T* __restrict__ yr, const DevState* __restrict__ st, int it) {
+                        T* __restrict__ y, const T* __restrict__ yr, const DevState* __restrict__ sts,
+                        const int* __restrict__ binst, int it) {
+  const DevState* st = block_state(sts, binst);
+  if (st->frozen) return;
   DualHalpernOp<T> op{bh, y, yr, (T)st->sigma, (T)halpern_weight(st, it), (T)st->rho};
   hyb_dot(A, vals, GlobalGather<T>{xbar}, op);
 }
@@ -1196,23 +1201,25 @@ template cudaError_t launch_primal_panels<float>(const Hyb&, const float*, const
                                                  int, int, cudaStream_t, int);
 template <class T>
 void launch_primal_step_halpern(const Hyb& At, const T* vals, const T* y, const T* ch, T* x, T* xbar, const T* xr,
-                                const DevState* st, int it, int grid, cudaStream_t s, int tpb) {
-  k_primal_step_halpern<T><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xr, st, it);
+                                const DevState* st, int it, int grid, cudaStream_t s, int tpb, const int* binst) {
+  k_primal_step_halpern<T><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xr, st, binst, it);
 }
 template <class T>
 void launch_dual_step_halpern(const Hyb& A, const T* vals, const T* xbar, const T* bh, T* y, const T* yr,
-                              const DevState* st, int it, int grid, cudaStream_t s, int tpb) {
-  k_dual_step_halpern<T><<<grid, tpb, 0, s>>>(A, vals, xbar, bh, y, yr, st, it);
+                              const DevState* st, int it, int grid, cudaStream_t s, int tpb, const int* binst) {
+  k_dual_step_halpern<T><<<grid, tpb, 0, s>>>(A, vals, xbar, bh, y, yr, st, binst, it);
 }
 template void launch_primal_step_halpern<double>(const Hyb&, const double*, const double*, const double*, double*,
                                                  double*, const double*, const DevState*, int, int, cudaStream_t,
-                                                 int);
+                                                 int, const int*);
 template void launch_primal_step_halpern<float>(const Hyb&, const float*, const float*, const float*, float*, float*,
-                                                const float*, const DevState*, int, int, cudaStream_t, int);
+                                                const float*, const DevState*, int, int, cudaStream_t, int,
+                                                const int*);
 template void launch_dual_step_halpern<double>(const Hyb&, const double*, const double*, const double*, double*,
-                                               const double*, const DevState*, int, int, cudaStream_t, int);
+                                               const double*, const DevState*, int, int, cudaStream_t, int,
+                                               const int*);
 template void launch_dual_step_halpern<float>(const Hyb&, const float*, const float*, const float*, float*,
-                                              const float*, const DevState*, int, int, cudaStream_t, int);
+                                              const float*, const DevState*, int, int, cudaStream_t, int, const int*);
 void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,
                           const DevState* st, int accumulate, int grid, cudaStream_t s) {
   k_dual_step_hot<<<grid, HOT_TPB, (size_t)hot * sizeof(double), s>>>(A, xbar, hot, bh, y, ysum, st, accumulate);

@@ -51,10 +51,12 @@ void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double
 // xr, yr = the anchor (the last restart point)
 template <class T>
 void launch_primal_step_halpern(const Hyb& At, const T* vals, const T* y, const T* ch, T* x, T* xbar, const T* xr,
-                                const DevState* st, int it, int grid, cudaStream_t s, int tpb);
+                                const DevState* st, int it, int grid, cudaStream_t s, int tpb,
+                                const int* binst = nullptr);
 template <class T>
 void launch_dual_step_halpern(const Hyb& A, const T* vals, const T* xbar, const T* bh, T* y, const T* yr,
-                              const DevState* st, int it, int grid, cudaStream_t s, int tpb);
+                              const DevState* st, int it, int grid, cudaStream_t s, int tpb,
+                              const int* binst = nullptr);
 // the same two half-steps in FP32 (values At.v32 / A.v32, FP32 vectors and
 // accumulation); tau and sigma are read from the FP64 state and rounded
 void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float* x, float* xbar, float* xsum,

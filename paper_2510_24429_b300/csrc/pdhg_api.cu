@@ -1305,6 +1305,8 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
   h.theta = o.theta;
   h.restarts_on = o.restarts;
   h.primal_weight_on = o.primal_weight;
+  h.halpern = o.halpern;
+  h.rho = o.halpern_reflect;
   for (int i = 0; i < count; ++i) ctx->h_st[i] = h;
   CK(ctx, cudaMemcpyAsync(ctx->st, ctx->h_st, sizeof(DevState) * count, cudaMemcpyHostToDevice, s));
   launch_finish_setup_b(ctx->st, count, ctx->scal, 8, o.step_factor, o.primal_weight, s);
@@ -1336,7 +1338,7 @@ void eval_batch(pdhg_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   const int count = ctx->count;
   const int gx = std::max(1, std::min(64, (int)(ctx->n / count / TPB + 1)));
-  if (ctx->opt.restarts) {
+  if (ctx->opt.restarts && !ctx->opt.halpern) {  // Halpern: no averages
     launch_make_average_b(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xoff, ctx->yoff, ctx->st,
                           count, gx, s);
     launch_eval_point(ctx->A, ctx->At, ctx->xavg, ctx->yavg, ctx->bh, ctx->ch, ctx->idr, ctx->idc, ctx->xr, ctx->yr,
@@ -1356,11 +1358,19 @@ pdhg_status enqueue_steps_batch(pdhg_ctx* ctx, int64_t nb, bool timing) {
   cudaStream_t s = ctx->stream;
   for (int64_t it = 0; it < nb; ++it) {
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
-    launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, ctx->nblocks, s,
-                       ctx->binst, 32 * ctx->wpb);
+    if (o.halpern)
+      launch_primal_step_halpern<double>(ctx->At, ctx->At.v, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xr, ctx->st,
+                                         (int)it, ctx->nblocks, s, 32 * ctx->wpb, ctx->binst);
+    else
+      launch_primal_step(ctx->At, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xsum, ctx->st, o.restarts, ctx->nblocks, s,
+                         ctx->binst, 32 * ctx->wpb);
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
-    launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, ctx->nblocks, s,
-                     ctx->binst, 32 * ctx->wpb);
+    if (o.halpern)
+      launch_dual_step_halpern<double>(ctx->A, ctx->A.v, ctx->xbar, ctx->bh, ctx->y, ctx->yr, ctx->st, (int)it,
+                                       ctx->nblocks, s, 32 * ctx->wpb, ctx->binst);
+    else
+      launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, ctx->nblocks, s,
+                       ctx->binst, 32 * ctx->wpb);
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 2], s));
   }
   launch_add_counters_b(ctx->st, ctx->count, nb, s);
@@ -1972,7 +1982,8 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
     return fail(nullptr, PDHG_ERR_INVALID, "step_block must be 128, 256 or 512");
   if (o.primal_panels == 1)
     return fail(nullptr, PDHG_ERR_INVALID, "primal_panels = 1 is for single LPs (batches use the direct primal step)");
-  if (o.halpern) return fail(nullptr, PDHG_ERR_INVALID, "halpern = 1 is for single LPs");
+  if (o.halpern && (o.persistent || !(o.halpern_reflect >= 0.0) || !(o.halpern_reflect <= 1.0)))
+    return fail(nullptr, PDHG_ERR_INVALID, "halpern = 1 needs halpern_reflect in [0, 1] and no persistent loop");
   if (o.persistent != 0 && (o.persistent != 1 || o.kernel_timing))
     return fail(nullptr, PDHG_ERR_INVALID, "persistent must be 0 or 1, and 1 excludes kernel timing");
   int64_t mt = 0, nt = 0, zt = 0;

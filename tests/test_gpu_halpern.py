@@ -123,4 +123,26 @@ def test_option_checks(tiny_lp):
             P.Solver.from_lp(tiny_lp, halpern=1, **bad)
         assert ei.value.status == P.PDHG_ERR_INVALID, bad
     with pytest.raises(P.PDHGError):
-        P.BatchSolver([tiny_lp, tiny_lp], halpern=1)
+        P.BatchSolver([tiny_lp, tiny_lp], halpern=1, persistent=1)
+
+
+def test_batch_matches_single_lp_engine():
+    from paper_2510_24429_b300 import lpgen
+
+    sizes = [200, 17, 1000, 333, 50]
+    lps = [lpgen.generate(m, max(1, int(round(2.5 * m))), 500 + i, nnz_per_col=min(5, m), support=0.3)
+           for i, m in enumerate(sizes)]
+    lps.append(lpgen.tiny_lp(0))
+    tol = 1e-6
+    with P.BatchSolver(lps, halpern=1) as bs:
+        st, _ = bs.iterate(100000, tol)
+        info = bs.info()
+        sols = [bs.solution(i) for i in range(len(lps))]
+    assert st == P.PDHG_OK and info["converged"].all()
+    for i, lp in enumerate(lps):
+        with P.Solver.from_lp(lp, halpern=1) as s:
+            st1, k1 = s.iterate(100000, tol)
+        assert st1 == P.PDHG_OK
+        assert abs(int(info["iterations"][i]) - k1) <= 2 * 64, (i, info["iterations"][i], k1)
+        x = sols[i][0]
+        assert float(lp.c @ x) == pytest.approx(lp.f_star, rel=10 * tol, abs=10 * tol), i
