@@ -37,6 +37,10 @@ What it computes, with the passage each part follows
   above, ``w = (t + 1) / (t + 2)``, ``t`` the iterations since the last restart
   and ``z_r`` the last restart point; the current iterate is the only restart
   candidate (no averages).
+* Feasibility polishing (Section 5 describes it as periodically running PDHG
+  with a zero objective inside the main solve to reach primal feasibility; the
+  dual counterpart zeroes the right-hand side). The rules of when and for how
+  long are readings, listed at ``Options.feas_polish``.
 * Algorithm 1's snapshot schedule: a snapshot of the current solution each time
   ``rel_kkt`` falls to ``eps_target``, after which ``eps_target`` shrinks by
   ``eps_factor`` (0.1 in the paper).
@@ -47,7 +51,11 @@ hand-computed step and KKT on a 2x3 LP, Ruiz/Pock-Chambolle invariants, power
 iteration against a dense SVD, and an exact replay of the restart rules on
 hand-made KKT sequences. The Halpern variant: the fixed point, the reduction
 to the PDHG map at w = 1, rho = 0, and Halpern's O(1/k) bound on the
-fixed-point residual in the PDHG metric.
+fixed-point residual in the PDHG metric. Feasibility polishing: a feasible
+start is a fixed point of each phase, the primal phase reaches A^{-1} b where
+that is the only feasible point, the dual phase's primal iterate goes to 0,
+the phase results meet their feasibility tolerance, and the schedule of
+attempts follows its rules.
 """
 from __future__ import annotations
 
@@ -100,6 +108,22 @@ class Options:
     # current iterate)
     halpern: bool = False
     halpern_reflect: float = 1.0
+    # feasibility polishing (the PDLP variant the paper describes in Section 5:
+    # PDHG iterations with a zero objective, to reach primal feasibility, inside
+    # the main solve). Readings: tried at an evaluation whose candidate has
+    # rel_gap <= tol but is not yet converged, at most once until the iteration
+    # count has doubled; a primal phase (objective 0, from (x_c, 0)) until
+    # rel_p <= tol, then a dual phase (right-hand side 0, from (0, y_c)) until
+    # rel_d <= tol, each for at most polish_div-th of the main iterations so far
+    # (rounded up to whole evaluation periods); the pair (x_p, y_d) ends the
+    # solve if its rel_kkt <= tol, otherwise the main iteration goes on as if
+    # nothing had happened
+    feas_polish: bool = False
+    polish_div: int = 8
+    # relative-gap tolerance of the termination test; 0 = the same tolerance as
+    # the two residuals (the single-eps test of Section 2). Feasibility
+    # polishing pays off when the gap tolerance is the looser one.
+    gap_tol: float = 0.0
 
 
 def csr_matrix(m, n, row_ptr, col_idx, val) -> sp.csr_matrix:
@@ -304,6 +328,7 @@ class EvalRecord:
     # an implementation that rounds differently may decide otherwise only
     # when this is at rounding level
     margin: float = math.inf
+    rel_gap: float = math.nan  # of the candidate, on the problem as given
 
 
 class Oracle:
@@ -338,6 +363,11 @@ class Oracle:
         self.next_snapshot = self.opt.snapshot_every
         self.restart_count = 0
         self.done = False
+        # termination measure: "rel_kkt" for the LP itself, "rel_p" / "rel_d" in
+        # the phases of feasibility polishing
+        self.term = "rel_kkt"
+        self.next_polish = 0
+        self.polish_log: list[dict] = []
         # restart reference = the starting point
         self.x_r, self.y_r = self.x.copy(), self.y.copy()
         self.n_restart = self.scaled_norms(self.x, self.y)
@@ -412,9 +442,14 @@ class Oracle:
             xc, yc, n_c = xa, ya, n_avg
         else:
             xc, yc, n_c = self.x, self.y, n_cur
-        rel = self.kkt_of(xc, yc)["rel_kkt"]
+        kk = self.kkt_of(xc, yc)
+        rel = kk[self.term]
+        gtol = opt.gap_tol if opt.gap_tol > 0 else tol
 
-        converged = tol > 0 and rel <= tol
+        if self.term == "rel_kkt":
+            converged = tol > 0 and kk["rel_p"] <= tol and kk["rel_d"] <= tol and kk["rel_gap"] <= gtol
+        else:
+            converged = tol > 0 and rel <= tol
         # Algorithm 1: snapshot when maxresid <= eps_target, then shrink eps_target.
         if self.eps_target > 0 and rel <= self.eps_target:
             self._snapshot(xc, yc, rel, "threshold")
@@ -451,15 +486,87 @@ class Oracle:
                 self.t = 0
                 self.restart_count += 1
             self.n_prev = n_c
-        self.trace.append(EvalRecord(self.k, kind, which, self.omega, rel, margin))
+        self.trace.append(EvalRecord(self.k, kind, which, self.omega, rel, margin, kk["rel_gap"]))
+        if (not converged and opt.feas_polish and tol > 0 and self.term == "rel_kkt" and self.k >= self.next_polish
+                and kk["rel_gap"] <= gtol):
+            self.next_polish = 2 * self.k
+            polished = self.feasibility_polish(xc, yc, tol)
+            if polished is not None:
+                self.x, self.y = polished
+                converged = True
         return converged
+
+    # -- feasibility polishing ---------------------------------------------
+    def feasibility_phase(self, xh0, yh0, kind: str, tol: float, budget: int):
+        """PDHG on the problem with the objective (kind "primal") or the
+        right-hand side (kind "dual") set to zero, from the scaled point
+        (xh0, yh0), with this solver's scaling, eta and current primal weight,
+        fresh averages and restart reference, and the same restart rules; it
+        stops at the first evaluation where rel_p (primal) or rel_d (dual) of
+        its candidate is <= tol, or after ``budget`` iterations. Returns
+        (xhat, yhat, iterations, reached)."""
+        sub = Oracle.__new__(Oracle)
+        sub.__dict__.update(self.__dict__)
+        sub.opt = dataclasses.replace(self.opt, eps_cross=0.0, snapshot_every=0, feas_polish=False)
+        if kind == "primal":
+            sub.c = np.zeros(self.n)
+            sub.ch = np.zeros(self.n)
+            sub.term = "rel_p"
+        else:
+            sub.b = np.zeros(self.m)
+            sub.bh = np.zeros(self.m)
+            sub.term = "rel_d"
+        sub.x, sub.y = np.array(xh0, dtype=np.float64), np.array(yh0, dtype=np.float64)
+        sub.x_sum, sub.y_sum = np.zeros(self.n), np.zeros(self.m)
+        sub.t = sub.k = 0
+        sub.trace, sub.snapshots, sub.polish_log = [], [], []
+        sub.eps_target, sub.next_snapshot = 0.0, 0
+        sub.restart_count = 0
+        sub.done = False
+        sub.x_r, sub.y_r = sub.x.copy(), sub.y.copy()
+        sub.n_restart = sub.scaled_norms(sub.x, sub.y)
+        sub.n_prev = sub.n_restart
+        reached = sub.run(budget, tol)
+        return sub.x, sub.y, sub.k, reached
+
+    def polish_budget(self) -> int:
+        """Iterations allowed to each phase: the main iterations so far divided
+        by polish_div, rounded up to whole evaluation periods (at least one)."""
+        e = self.opt.eval_every
+        return e * max(1, -(-self.k // (self.opt.polish_div * e)))
+
+    def feasibility_polish(self, xh_c, yh_c, tol: float):
+        """One attempt: primal phase from (x_c, 0), then (if it reached rel_p <=
+        tol) dual phase from (0, y_c); returns the scaled pair (x_p, y_d) when
+        it passes the termination test on the LP as given, else None."""
+        budget = self.polish_budget()
+        rec = dict(iteration=self.k, budget=budget, primal_iters=0, primal_ok=False, dual_iters=0, dual_ok=False,
+                   rel_kkt=math.inf)
+        self.polish_log.append(rec)
+        xp, _, kp, okp = self.feasibility_phase(xh_c, np.zeros(self.m), "primal", tol, budget)
+        rec.update(primal_iters=kp, primal_ok=okp)
+        if not okp:
+            return None
+        _, yd, kd, okd = self.feasibility_phase(np.zeros(self.n), yh_c, "dual", tol, budget)
+        rec.update(dual_iters=kd, dual_ok=okd)
+        if not okd:
+            return None
+        kk = self.kkt_of(xp, yd)
+        rec["rel_kkt"] = kk["rel_kkt"]
+        rec["rel_gap"] = kk["rel_gap"]
+        gtol = self.opt.gap_tol if self.opt.gap_tol > 0 else tol
+        if kk["rel_p"] <= tol and kk["rel_d"] <= tol and kk["rel_gap"] <= gtol:
+            return xp.copy(), yd.copy()
+        return None
 
     def _snapshot(self, xh, yh, rel, why):
         x, y, z = self.unscale(xh, yh)
         self.snapshots.append(dict(iteration=self.k, x=x, y=y, z=z, rel_kkt=rel, why=why))
 
     def run(self, max_iters: int, tol: float = 0.0) -> bool:
-        """Iterate until rel_kkt <= tol at an evaluation or max_iters iterations.
+        """Iterate until the candidate passes the termination test (rel_p, rel_d
+        <= tol and rel_gap <= gap_tol, or tol) at an evaluation or max_iters
+        iterations.
         Evaluations happen every ``eval_every`` iterations when restarts are on or
         tol > 0; with restarts off and tol = 0 this is plain fixed-step PDHG."""
         evaluating = self.opt.restarts or tol > 0 or self.opt.eps_cross > 0 or self.opt.snapshot_every > 0
