@@ -109,7 +109,19 @@ typedef struct {
                              current iterate is the restart candidate). Single LPs, every precision, not
                              persistent (0) */
   double halpern_reflect; /* rho in [0, 1] (1.0) */
-  int reserved[4];
+  double gap_tol;         /* relative-gap tolerance of the termination test: converged when rel_p <= tol,
+                             rel_d <= tol and rel_gap <= gap_tol; 0 = tol (Section 2's single eps) (0) */
+  int feas_polish;        /* 1: feasibility polishing, the PDLP variant Section 5 describes (PDHG iterations
+                             with a zero objective inside the main solve): at an evaluation whose candidate has
+                             rel_gap <= gap_tol but fails the test, at most once until the iteration count has
+                             doubled, run PDHG with c = 0 from (x_c, 0) until rel_p <= tol, then with b = 0 from
+                             (0, y_c) until rel_d <= tol, each phase with the current scaling, step and primal
+                             weight and at most polish_div-th of the iterations so far (whole evaluation
+                             periods); the solve ends with (x_p, y_d) if that pair passes the test, otherwise it
+                             goes on unchanged. Single LPs, FP64 phases only (in PDHG_MIXED after the switch),
+                             not persistent, no recording (0) */
+  int polish_div;         /* polishing phase budget divisor (8) */
+  int reserved[2];
 } pdhg_options;
 
 /* Scalars of one point on the problem as given (unscaled), all FP64.
@@ -143,7 +155,19 @@ typedef struct {
   int64_t kernel_launches_primal, kernel_launches_dual;
   int64_t kernel_launches; /* all kernels launched by pdhg_iterate so far */
   int64_t polish_started_at; /* PDHG_MIXED: iteration where FP64 took over, -1 if not (yet) */
+  int64_t feas_polish_attempts;   /* feasibility polishing attempts so far */
+  int64_t feas_polish_iterations; /* iterations run in polishing phases (not counted in `iterations`) */
+  int feas_polished;              /* 1: the current iterate is a polished pair (x_p, y_d) that passed the test */
 } pdhg_info;
+
+/* One feasibility polishing attempt. */
+typedef struct {
+  int64_t iteration;     /* main iteration count at the attempt */
+  int64_t budget;        /* iteration limit of each phase */
+  int64_t primal_iters, dual_iters;
+  int32_t primal_ok, dual_ok; /* the phase reached rel_p <= tol (rel_d <= tol) */
+  double rel_kkt, rel_gap;    /* of the pair (x_p, y_d) on the problem as given; +inf if a phase failed */
+} pdhg_polish_rec;
 
 /* One record per evaluation. */
 typedef struct {
@@ -171,7 +195,9 @@ PDHG_API pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_
 PDHG_API void pdhg_destroy(pdhg_ctx* ctx);
 
 /* Run PDHG iterations (Algorithm 1, "Perform PDHG iteration") until the
- * candidate's rel_kkt <= tol at an evaluation, or max_iters more iterations.
+ * candidate passes the termination test at an evaluation (rel_kkt <= tol; with
+ * gap_tol set, rel_p <= tol, rel_d <= tol and rel_gap <= gap_tol), or
+ * max_iters more iterations (feasibility polishing phases not counted).
  * Evaluations happen every eval_every iterations (counted from the first
  * iteration of the context) when tol > 0, restarts are on, or a snapshot
  * schedule is set. tol = 0 with restarts off runs exactly max_iters plain
@@ -234,6 +260,10 @@ PDHG_API pdhg_status pdhg_get_info(pdhg_ctx* ctx, pdhg_info* out);
 /* Copy up to cap evaluation records (oldest first) into recs; *count gets the
  * number stored (at most 65536 are kept). */
 PDHG_API pdhg_status pdhg_get_trace(pdhg_ctx* ctx, pdhg_trace_rec* recs, int64_t cap, int64_t* count);
+
+/* Copy up to cap feasibility polishing records (oldest first) into recs;
+ * *count gets the number of attempts so far. */
+PDHG_API pdhg_status pdhg_get_polish_log(pdhg_ctx* ctx, pdhg_polish_rec* recs, int64_t cap, int64_t* count);
 
 /* KKT measures (as pdhg_kkt) of a point (x, y), z = max(0, c - A^T y), of an LP
  * the caller keeps on the device, computed WITHOUT ALLOCATING ANY MEMORY. The

@@ -57,13 +57,20 @@ struct DevState {
   int candidate, kind, apply_mode, converged;
   int snapshot_flag, numeric;
   int frozen;  // batch: the instance has converged; its blocks skip all work
-  int pad0;
+  // termination test: TERM_LP (rel_p, rel_d <= tol and rel_gap <= gap_tol) for
+  // the LP itself; TERM_PRIMAL (rel_p <= tol) / TERM_DUAL (rel_d <= tol) in
+  // the phases of feasibility polishing
+  int term_mode;
   // reflected Halpern iteration: on, and the reflection rho
   int halpern, pad1;
   double rho;
   double cand_rel_kkt;
-  double scratch[4];
+  double gap_tol;       // relative-gap tolerance; <= 0: tol
+  double cand_rel_gap;  // the candidate's rel_gap (feasibility polishing trigger)
+  double scratch[2];
 };
+
+enum { TERM_LP = 0, TERM_PRIMAL = 1, TERM_DUAL = 2 };
 
 struct TraceRec {
   long long iteration;

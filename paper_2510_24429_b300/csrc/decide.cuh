@@ -38,12 +38,24 @@ static __device__ void decide_one(DevState* st, TraceRec* trace) {
   const double rel_p = sqrt(e.q[Q_RP2U]) / (1.0 + st->b_norm);
   const double rel_d = sqrt(e.q[Q_RD2U]) / (1.0 + st->c_norm);
   const double rel_g = fabs(cx - by) / (1.0 + fabs(cx) + fabs(by));
-  const double rel = fmax(rel_p, fmax(rel_d, rel_g));
+  // the termination measure: rel_kkt for the LP itself, rel_p / rel_d in the
+  // phases of feasibility polishing
+  const double rel = st->term_mode == TERM_PRIMAL ? rel_p
+                     : st->term_mode == TERM_DUAL ? rel_d
+                                                  : fmax(rel_p, fmax(rel_d, rel_g));
   st->numeric = !(isfinite(rel_p) && isfinite(rel_d) && isfinite(rel_g) && isfinite(cp) && isfinite(cd));
   st->candidate = which;
   st->cand_rel_kkt = rel;
+  st->cand_rel_gap = rel_g;
 
-  const int converged = st->tol > 0.0 && rel <= st->tol;
+  const double gtol = st->gap_tol > 0.0 ? st->gap_tol : st->tol;
+  int converged;
+  if (st->term_mode == TERM_PRIMAL)
+    converged = st->tol > 0.0 && rel_p <= st->tol;
+  else if (st->term_mode == TERM_DUAL)
+    converged = st->tol > 0.0 && rel_d <= st->tol;
+  else
+    converged = st->tol > 0.0 && rel_p <= st->tol && rel_d <= st->tol && rel_g <= gtol;
   int snap = 0;
   if (st->eps_target > 0.0 && rel <= st->eps_target) {
     snap = 1;

@@ -1004,6 +1004,25 @@ __global__ void k_apply32(const DevState* __restrict__ st, float* __restrict__ x
 
 // Start of the FP64 phase: the point just evaluated into st->cur becomes the
 // restart reference and the count since the last restart starts over.
+// Start of a feasibility polishing phase (st->cur holds the start point's
+// evaluation on the phase's problem): the start is the restart reference and
+// the previous candidate, counters at zero, no snapshots, the phase's test.
+__global__ void k_polish_begin(DevState* st, int term_mode) {
+  double p, d, g;
+  scaled_norms(st->cur, p, d, g);
+  st->rs_p = st->pc_p = p;
+  st->rs_d = st->pc_d = d;
+  st->rs_g = st->pc_g = g;
+  st->t = 0;
+  st->k = 0;
+  st->term_mode = term_mode;
+  st->eps_target = 0.0;
+  st->snapshot_every = 0;
+  st->next_snapshot = 0;
+  st->converged = 0;
+  st->snapshot_flag = 0;
+}
+
 __global__ void k_promote_state(DevState* st) {
   double p, d, g;
   scaled_norms(st->cur, p, d, g);
@@ -1302,6 +1321,7 @@ void launch_apply32(const DevState* st, float* x32, float* y32, double* x, doubl
   k_apply32<<<grid, TPB, 0, s>>>(st, x32, y32, x, y, xa, ya, xr, yr, xs, ys, n, m);
 }
 void launch_promote_state(DevState* st, cudaStream_t s) { k_promote_state<<<1, 1, 0, s>>>(st); }
+void launch_polish_begin(DevState* st, int term_mode, cudaStream_t s) { k_polish_begin<<<1, 1, 0, s>>>(st, term_mode); }
 
 template <class T>
 void launch_adj_step(const Hyb& A, const Hyb& At, const T* valsA, const T* valsAt, const T* xnext, T* gx, T* gy,

@@ -73,6 +73,9 @@ void launch_apply32(const DevState* st, float* x32, float* y32, double* x, doubl
                     cudaStream_t s);
 // restart reference := st->cur, t := 0 (start of the FP64 polishing phase)
 void launch_promote_state(DevState* st, cudaStream_t s);
+// restart reference := st->cur, k := t := 0, snapshots off, termination test
+// term_mode (start of a feasibility polishing phase)
+void launch_polish_begin(DevState* st, int term_mode, cudaStream_t s);
 // ---- adjoint ----------------------------------------------------------------
 // one reversed iteration: adjoint primal half-step over Ahat^T then adjoint
 // dual half-step over Ahat (values valsAt / valsA in precision T)

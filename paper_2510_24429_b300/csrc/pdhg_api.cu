@@ -136,6 +136,14 @@ struct pdhg_ctx {
   double best32 = 1e300;     // best relative KKT seen in the FP32 phase, and where
   int64_t best32_k = 0;
   bool converged = false;
+  // feasibility polishing: saved main state, start point, phase results and
+  // saved chat / bhat (allocated on the first attempt), the iteration count
+  // from which the next attempt may start, and the attempt log
+  double* fp_buf = nullptr;
+  int64_t fp_next = 0;
+  int64_t fp_iters = 0;
+  bool fp_polished = false;
+  std::vector<pdhg_polish_rec> fp_log;
   std::vector<void*> allocs;
   std::string err = "no error";
 };
@@ -943,6 +951,7 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   h.primal_weight_on = o.primal_weight;
   h.halpern = o.halpern;
   h.rho = o.halpern_reflect;
+  h.gap_tol = o.gap_tol;
   *ctx->h_st = h;
   CK(ctx, cudaMemcpyAsync(ctx->st, ctx->h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
   launch_finish_setup(ctx->st, ctx->scal, o.step_factor, o.primal_weight, s);
@@ -1307,6 +1316,7 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
   h.primal_weight_on = o.primal_weight;
   h.halpern = o.halpern;
   h.rho = o.halpern_reflect;
+  h.gap_tol = o.gap_tol;
   for (int i = 0; i < count; ++i) ctx->h_st[i] = h;
   CK(ctx, cudaMemcpyAsync(ctx->st, ctx->h_st, sizeof(DevState) * count, cudaMemcpyHostToDevice, s));
   launch_finish_setup_b(ctx->st, count, ctx->scal, 8, o.step_factor, o.primal_weight, s);
@@ -1517,6 +1527,144 @@ pdhg_status iterate_batch(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t*
   return fail(ctx, PDHG_ERR_NOT_CONVERGED, "iteration limit reached before every instance met the tolerance");
 }
 
+
+// ---- feasibility polishing -----------------------------------------------------
+
+// Whole evaluation blocks of a polishing phase until its test is met (the
+// decision kernel's converged flag) or `budget` iterations; a NaN/Inf ends the
+// phase as not met.
+pdhg_status polish_phase_run(pdhg_ctx* ctx, int64_t budget, bool graphs, int64_t* iters, bool* met) {
+  const int64_t E = ctx->opt.eval_every;
+  *iters = 0;
+  *met = false;
+  while (*iters < budget) {
+    pdhg_status rs = graphs ? run_block_graph(ctx, E) : enqueue_block(ctx, E);
+    if (rs != PDHG_OK) return rs;
+    ctx->k += E;
+    *iters += E;
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->h_st->numeric) break;
+    if (ctx->h_st->converged) {
+      *met = true;
+      break;
+    }
+  }
+  return PDHG_OK;
+}
+
+// Set up a phase: the current (x, y) is its start and restart reference, the
+// averages are empty, and the start is evaluated on the phase's problem.
+pdhg_status polish_phase_begin(pdhg_ctx* ctx, int term_mode) {
+  const int64_t n = ctx->n, m = ctx->m;
+  cudaStream_t s = ctx->stream;
+  CK(ctx, cudaMemsetAsync(ctx->xsum, 0, sizeof(double) * n, s));
+  CK(ctx, cudaMemsetAsync(ctx->ysum, 0, sizeof(double) * m, s));
+  CK(ctx, cudaMemcpyAsync(ctx->xr, ctx->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CK(ctx, cudaMemcpyAsync(ctx->yr, ctx->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  eval_point(ctx, ctx->x, ctx->y, nullptr, nullptr, &ctx->st->cur);
+  launch_polish_begin(ctx->st, term_mode, s);
+  ctx->launches += 3;
+  CK(ctx, cudaGetLastError());
+  ctx->k = 0;
+  return PDHG_OK;
+}
+
+// One attempt of feasibility polishing after an evaluation of the main solve
+// (h_st holds its decisions): a primal phase (chat = 0) from (x_c, 0) until
+// rel_p <= tol, then a dual phase (bhat = 0) from (0, y_c) until rel_d <= tol,
+// each for at most `budget` iterations, with the main solve's scaling, step
+// and current primal weight. The main state (iterates, sums, restart point,
+// device state, iteration count) is saved before and restored after; when the
+// pair (x_p, y_d) passes the termination test on the LP as given, it becomes
+// the current iterate and *solved is set.
+pdhg_status feas_polish(pdhg_ctx* ctx, double tol, int64_t budget, bool graphs, bool* solved) {
+  *solved = false;
+  const int64_t n = ctx->n, m = ctx->m;
+  cudaStream_t s = ctx->stream;
+  if (!ctx->fp_buf) CK(ctx, dalloc(ctx, &ctx->fp_buf, (size_t)6 * (n + m)));
+  double *sx = ctx->fp_buf, *sxs = sx + n, *sxr = sx + 2 * n, *xc = sx + 3 * n, *xp = sx + 4 * n, *sch = sx + 5 * n;
+  double *sy = ctx->fp_buf + 6 * n, *sys = sy + m, *syr = sy + 2 * m, *yc = sy + 3 * m, *yd = sy + 4 * m,
+         *sbh = sy + 5 * m;
+  const DevState saved = *ctx->h_st;
+  const int64_t k_saved = ctx->k;
+  const bool avg = saved.candidate == KIND_AVG;
+  const size_t bn = sizeof(double) * n, bm = sizeof(double) * m;
+  const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
+  double* save_n[][2] = {{sx, ctx->x}, {sxs, ctx->xsum}, {sxr, ctx->xr}, {xc, avg ? ctx->xavg : ctx->x},
+                         {sch, ctx->ch}};
+  double* save_m[][2] = {{sy, ctx->y}, {sys, ctx->ysum}, {syr, ctx->yr}, {yc, avg ? ctx->yavg : ctx->y},
+                         {sbh, ctx->bh}};
+  for (auto& p : save_n) CK(ctx, cudaMemcpyAsync(p[0], p[1], bn, d2d, s));
+  for (auto& p : save_m) CK(ctx, cudaMemcpyAsync(p[0], p[1], bm, d2d, s));
+  pdhg_polish_rec rec{};
+  rec.iteration = k_saved;
+  rec.budget = budget;
+  rec.rel_kkt = rec.rel_gap = INFINITY;
+
+  // primal phase: objective 0, start (x_c, 0)
+  CK(ctx, cudaMemsetAsync(ctx->ch, 0, bn, s));
+  CK(ctx, cudaMemcpyAsync(ctx->x, xc, bn, d2d, s));
+  CK(ctx, cudaMemsetAsync(ctx->y, 0, bm, s));
+  pdhg_status rs = polish_phase_begin(ctx, TERM_PRIMAL);
+  if (rs != PDHG_OK) return rs;
+  bool okp = false, okd = false;
+  rs = polish_phase_run(ctx, budget, graphs, &rec.primal_iters, &okp);
+  if (rs != PDHG_OK) return rs;
+  rec.primal_ok = okp;
+  CK(ctx, cudaMemcpyAsync(xp, ctx->x, bn, d2d, s));
+  CK(ctx, cudaMemcpyAsync(ctx->ch, sch, bn, d2d, s));
+  if (okp) {
+    // dual phase: right-hand side 0, start (0, y_c)
+    CK(ctx, cudaMemsetAsync(ctx->bh, 0, bm, s));
+    CK(ctx, cudaMemsetAsync(ctx->x, 0, bn, s));
+    CK(ctx, cudaMemcpyAsync(ctx->y, yc, bm, d2d, s));
+    rs = polish_phase_begin(ctx, TERM_DUAL);
+    if (rs != PDHG_OK) return rs;
+    rs = polish_phase_run(ctx, budget, graphs, &rec.dual_iters, &okd);
+    if (rs != PDHG_OK) return rs;
+    rec.dual_ok = okd;
+    CK(ctx, cudaMemcpyAsync(yd, ctx->y, bm, d2d, s));
+    CK(ctx, cudaMemcpyAsync(ctx->bh, sbh, bm, d2d, s));
+  }
+  ctx->fp_iters += rec.primal_iters + rec.dual_iters;
+  double rel_p = INFINITY, rel_d = INFINITY;
+  if (okp && okd) {
+    // the pair on the LP as given
+    eval_point(ctx, xp, yd, nullptr, nullptr, ctx->kkt_sums);
+    ctx->launches += 2;
+    CK(ctx, cudaGetLastError());
+    CK(ctx, cudaMemcpyAsync(ctx->h_kkt, ctx->kkt_sums, sizeof(EvalSums), cudaMemcpyDeviceToHost, s));
+    CK(ctx, cudaStreamSynchronize(s));
+    const double* q = ctx->h_kkt->q;
+    rel_p = sqrt(q[Q_RP2U]) / (1.0 + saved.b_norm);
+    rel_d = sqrt(q[Q_RD2U]) / (1.0 + saved.c_norm);
+    rec.rel_gap = fabs(q[Q_CX] - q[Q_BY]) / (1.0 + fabs(q[Q_CX]) + fabs(q[Q_BY]));
+    rec.rel_kkt = std::max(rel_p, std::max(rel_d, rec.rel_gap));
+  }
+  const double gtol = ctx->opt.gap_tol > 0.0 ? ctx->opt.gap_tol : tol;
+  *solved = okp && okd && rel_p <= tol && rel_d <= tol && rec.rel_gap <= gtol;
+  ctx->fp_log.push_back(rec);
+
+  // restore the main solve, or end it with the polished pair
+  for (auto& p : save_n)
+    if (p[1] != ctx->xavg && p[1] != ctx->ch) CK(ctx, cudaMemcpyAsync(p[1], p[0], bn, d2d, s));
+  for (auto& p : save_m)
+    if (p[1] != ctx->yavg && p[1] != ctx->bh) CK(ctx, cudaMemcpyAsync(p[1], p[0], bm, d2d, s));
+  *ctx->h_st = saved;
+  if (*solved) {
+    CK(ctx, cudaMemcpyAsync(ctx->x, xp, bn, d2d, s));
+    CK(ctx, cudaMemcpyAsync(ctx->y, yd, bm, d2d, s));
+    ctx->h_st->converged = 1;
+    ctx->h_st->cand_rel_kkt = rec.rel_kkt;
+    ctx->h_st->cand_rel_gap = rec.rel_gap;
+    ctx->fp_polished = true;
+  }
+  CK(ctx, cudaMemcpyAsync(ctx->st, ctx->h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  ctx->k = k_saved;
+  return PDHG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1554,6 +1702,9 @@ void pdhg_default_options(pdhg_options* o) {
   o->panel_rows = 0;
   o->halpern = 0;
   o->halpern_reflect = 1.0;
+  o->gap_tol = 0.0;
+  o->feas_polish = 0;
+  o->polish_div = 8;
 }
 
 pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
@@ -1601,6 +1752,11 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
       return fail(nullptr, PDHG_ERR_INVALID,
                   "persistent: the LP's vectors (7n + 6m doubles) exceed one block's shared memory (28672)");
   }
+
+  if (!(o.gap_tol >= 0.0) || o.feas_polish < 0 || o.feas_polish > 1 || o.polish_div < 1)
+    return fail(nullptr, PDHG_ERR_INVALID, "gap_tol must be >= 0, feas_polish 0 or 1 and polish_div >= 1");
+  if (o.feas_polish && (o.persistent || o.record_for_backward))
+    return fail(nullptr, PDHG_ERR_INVALID, "feas_polish = 1 needs no persistent loop and no recording");
 
   // CSR validation of host inputs (host logic, before any device work);
   // device inputs are checked on the device during setup
@@ -1740,6 +1896,20 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
       if (ctx->h_st->converged) {
         ctx->converged = true;
         break;
+      }
+      if (o.feas_polish && tol > 0.0 && !ctx->phase32 && ctx->k >= ctx->fp_next &&
+          ctx->h_st->cand_rel_gap <= (o.gap_tol > 0.0 ? o.gap_tol : tol)) {
+        // feasibility polishing; the next attempt once the iteration count has doubled
+        ctx->fp_next = 2 * ctx->k;
+        const int64_t per = (int64_t)o.polish_div * o.eval_every;
+        const int64_t budget = o.eval_every * std::max<int64_t>(1, (ctx->k + per - 1) / per);
+        bool solved = false;
+        rs = feas_polish(ctx, tol, budget, graphs, &solved);
+        if (rs != PDHG_OK) return rs;
+        if (solved) {
+          ctx->converged = true;
+          break;
+        }
       }
       bool stalled = false;
       if (ctx->phase32) {
@@ -1916,6 +2086,18 @@ pdhg_status pdhg_get_info(pdhg_ctx* ctx, pdhg_info* out) {
   out->kernel_launches_primal = ctx->launches_primal;
   out->kernel_launches_dual = ctx->launches_dual;
   out->kernel_launches = ctx->launches;
+  out->feas_polish_attempts = (int64_t)ctx->fp_log.size();
+  out->feas_polish_iterations = ctx->fp_iters;
+  out->feas_polished = ctx->fp_polished ? 1 : 0;
+  return PDHG_OK;
+}
+
+pdhg_status pdhg_get_polish_log(pdhg_ctx* ctx, pdhg_polish_rec* recs, int64_t cap, int64_t* count) {
+  if (!ctx) return PDHG_ERR_INVALID;
+  if (cap < 0 || (cap > 0 && !recs)) return fail(ctx, PDHG_ERR_INVALID, "bad record buffer");
+  const int64_t total = (int64_t)ctx->fp_log.size();
+  for (int64_t i = 0; i < std::min(cap, total); ++i) recs[i] = ctx->fp_log[i];
+  if (count) *count = total;
   return PDHG_OK;
 }
 
@@ -1986,6 +2168,8 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
     return fail(nullptr, PDHG_ERR_INVALID, "halpern = 1 needs halpern_reflect in [0, 1] and no persistent loop");
   if (o.persistent != 0 && (o.persistent != 1 || o.kernel_timing))
     return fail(nullptr, PDHG_ERR_INVALID, "persistent must be 0 or 1, and 1 excludes kernel timing");
+  if (o.feas_polish || !(o.gap_tol >= 0.0))
+    return fail(nullptr, PDHG_ERR_INVALID, "batch: no feasibility polishing (single LPs only), gap_tol >= 0");
   int64_t mt = 0, nt = 0, zt = 0;
   for (int i = 0; i < count; ++i) {
     const pdhg_lp_desc& L = lps[i];

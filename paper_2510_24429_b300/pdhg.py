@@ -59,7 +59,10 @@ class pdhg_options(C.Structure):
         ("panel_rows", C.c_int),
         ("halpern", C.c_int),
         ("halpern_reflect", C.c_double),
-        ("reserved", C.c_int * 4),
+        ("gap_tol", C.c_double),
+        ("feas_polish", C.c_int),
+        ("polish_div", C.c_int),
+        ("reserved", C.c_int * 2),
     ]
 
 
@@ -78,7 +81,14 @@ class pdhg_info(C.Structure):
         ("kernel_ms_dual", C.c_double), ("kernel_launches_primal", C.c_int64), ("kernel_launches_dual", C.c_int64),
         ("kernel_launches", C.c_int64),
         ("polish_started_at", C.c_int64),
+        ("feas_polish_attempts", C.c_int64), ("feas_polish_iterations", C.c_int64), ("feas_polished", C.c_int),
     ]
+
+
+class pdhg_polish_rec(C.Structure):
+    _fields_ = [("iteration", C.c_int64), ("budget", C.c_int64), ("primal_iters", C.c_int64),
+                ("dual_iters", C.c_int64), ("primal_ok", C.c_int32), ("dual_ok", C.c_int32), ("rel_kkt", C.c_double),
+                ("rel_gap", C.c_double)]
 
 
 class pdhg_trace_rec(C.Structure):
@@ -117,6 +127,7 @@ SIGNATURES = {
     "pdhg_get_info": (C.c_int, [_P, C.POINTER(pdhg_info)]),
     "pdhg_backward": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
     "pdhg_get_trace": (C.c_int, [_P, C.POINTER(pdhg_trace_rec), C.c_int64, C.POINTER(C.c_int64)]),
+    "pdhg_get_polish_log": (C.c_int, [_P, C.POINTER(pdhg_polish_rec), C.c_int64, C.POINTER(C.c_int64)]),
     "pdhg_last_error": (C.c_char_p, [_P]),
     "pdhg_create_batch": (C.c_int, [C.c_int, C.POINTER(pdhg_lp_desc), C.POINTER(pdhg_options), _P, C.POINTER(_P)]),
     "pdhg_batch_info": (C.c_int, [_P, _P, _P, _P, _P]),
@@ -316,6 +327,15 @@ def pdhg_get_trace(ctx) -> list[dict]:
     return [{k: getattr(r, k) for k, _ in pdhg_trace_rec._fields_} for r in recs[: cnt.value]]
 
 
+def pdhg_get_polish_log(ctx) -> list[dict]:
+    lib = load()
+    cnt = C.c_int64()
+    _check(lib.pdhg_get_polish_log(ctx, None, 0, C.byref(cnt)), ctx)
+    recs = (pdhg_polish_rec * max(1, cnt.value))()
+    _check(lib.pdhg_get_polish_log(ctx, recs, cnt.value, C.byref(cnt)), ctx)
+    return [{k: getattr(r, k) for k, _ in pdhg_polish_rec._fields_} for r in recs[: cnt.value]]
+
+
 def pdhg_last_error(ctx=None) -> str:
     return load().pdhg_last_error(ctx).decode()
 
@@ -509,6 +529,10 @@ class Solver:
 
     def trace(self):
         return pdhg_get_trace(self.ctx)
+
+    def polish_log(self):
+        """One record per feasibility polishing attempt."""
+        return pdhg_get_polish_log(self.ctx)
 
     def close(self):
         if self.ctx:

@@ -1,0 +1,147 @@
+"""Feasibility polishing (options feas_polish, polish_div) and the separate
+relative-gap tolerance (gap_tol) on the GPU against the oracle: the same
+attempts (iteration, budget, phase lengths, outcomes), the same polished pair
+to the converged-parity bar, and the pair passing the termination test."""
+import numpy as np
+import pytest
+
+from oracle import pdhg_oracle as O
+from paper_2510_24429_b300 import lpgen
+from paper_2510_24429_b300 import pdhg as P
+from tests.gpu_helpers import SHARED, assert_iterates_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2510_24429_b300 import build
+
+    build.build()
+    P.load()
+
+
+def _pair(lp, engine=None, **opts):
+    oopt = O.Options(**opts)
+    orc = O.Oracle(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, oopt)
+    copts = {k: (int(v) if isinstance(v, bool) else v) for k, v in ((k, getattr(oopt, k)) for k in SHARED)}
+    extra = dict(gap_tol=oopt.gap_tol, feas_polish=int(oopt.feas_polish), polish_div=oopt.polish_div,
+                 halpern=int(oopt.halpern), halpern_reflect=oopt.halpern_reflect)
+    sol = P.Solver(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, **copts, **extra, **(engine or {}))
+    return orc, sol
+
+
+def _compare_logs(glog, olog):
+    assert len(glog) == len(olog) >= 1
+    for g, o in zip(glog, olog):
+        assert (g["iteration"], g["budget"], g["primal_iters"], g["dual_iters"], bool(g["primal_ok"]),
+                bool(g["dual_ok"])) == (o["iteration"], o["budget"], o["primal_iters"], o["dual_iters"],
+                                        o["primal_ok"], o["dual_ok"]), (g, o)
+        if o["dual_ok"]:
+            assert g["rel_kkt"] == pytest.approx(o["rel_kkt"], rel=1e-6)
+            assert g["rel_gap"] == pytest.approx(o["rel_gap"], rel=1e-6)
+        else:
+            assert g["rel_kkt"] == np.inf
+
+
+@pytest.mark.parametrize("which", ["tiny", "2k"])
+def test_polished_solve_matches_oracle(which):
+    lp = lpgen.tiny_lp(0) if which == "tiny" else lpgen.generate(2000, 5000, 1, nnz_per_col=5, support=0.3)
+    tol, gtol = 1e-8, 1e-4
+    orc, sol = _pair(lp, feas_polish=True, gap_tol=gtol)
+    with sol:
+        assert orc.run(100000, tol)
+        st, done = sol.iterate(100000, tol)
+        assert st == P.PDHG_OK and done == orc.k
+        _compare_logs(sol.polish_log(), orc.polish_log)
+        info = sol.info()
+        assert info["converged"] == 1 and info["feas_polished"] == 1
+        assert info["feas_polish_attempts"] == len(orc.polish_log)
+        assert info["feas_polish_iterations"] == sum(r["primal_iters"] + r["dual_iters"] for r in orc.polish_log)
+        assert info["iterations"] == orc.k
+        assert_iterates_close(sol, orc, 1e-7)
+        k = sol.kkt()
+        assert k["rel_p"] <= tol and k["rel_d"] <= tol and k["rel_gap"] <= gtol
+        assert k["primal_obj"] == pytest.approx(float(lp.c @ orc.solution()[0]), rel=1e-7)
+
+
+def test_failed_attempts_leave_the_main_solve_unchanged():
+    """On a Zipf-shaped LP the first attempts fail (a phase runs out of budget,
+    or the pair's gap is too large); the solve goes on exactly as without
+    polishing: same iterates after 4000 iterations as the oracle, with and
+    without polishing."""
+    lp = lpgen.generate(20000, 60000, 0, nnz_per_col=None, zipf=(1.5, 10000, 600000), val_range=(0.1, 10.0),
+                        support=0.3)
+    tol, gtol = 1e-6, 1e-4
+    orc, sol = _pair(lp, feas_polish=True, gap_tol=gtol)
+    with sol:
+        orc.run(4000, tol)
+        st, done = sol.iterate(4000, tol)
+        assert done == 4000 and st == P.PDHG_ERR_NOT_CONVERGED
+        _compare_logs(sol.polish_log(), orc.polish_log)
+        assert len(orc.polish_log) >= 2 and not any(r["rel_kkt"] <= gtol for r in orc.polish_log if r["dual_ok"])
+        assert_iterates_close(sol, orc, 1e-8)
+        assert_iterates_close(sol, orc, 1e-8, P.PDHG_AVERAGE)
+        x_pol, y_pol, _ = sol.solution()
+    orc2, sol2 = _pair(lp, gap_tol=gtol)
+    with sol2:
+        sol2.iterate(4000, tol)
+        x, y, _ = sol2.solution()
+        assert sol2.info()["feas_polish_attempts"] == 0
+    assert np.array_equal(x, x_pol) and np.array_equal(y, y_pol)
+
+
+def test_gap_tolerance_alone(tiny_lp):
+    """gap_tol without polishing ends at the oracle's iteration; gap_tol = 0
+    and gap_tol = tol give the same run."""
+    for g in (1e-4, 1e-8, 0.0):
+        orc, sol = _pair(tiny_lp, gap_tol=g)
+        with sol:
+            assert orc.run(100000, 1e-8)
+            st, done = sol.iterate(100000, 1e-8)
+            assert st == P.PDHG_OK and done == orc.k, g
+            assert_iterates_close(sol, orc, 1e-7)
+
+
+def test_halpern_form_with_polishing(tiny_lp):
+    orc, sol = _pair(tiny_lp, feas_polish=True, gap_tol=1e-4, halpern=True)
+    with sol:
+        ok = orc.run(100000, 1e-8)
+        st, done = sol.iterate(100000, 1e-8)
+        assert ok and st == P.PDHG_OK and done == orc.k
+        _compare_logs(sol.polish_log(), orc.polish_log)
+        assert_iterates_close(sol, orc, 1e-7)
+
+
+def test_graph_replay_and_direct_launches_agree():
+    lp = lpgen.generate(2000, 5000, 1, nnz_per_col=5, support=0.3)
+    res = []
+    for graphs in (1, 0):
+        with P.Solver.from_lp(lp, feas_polish=1, gap_tol=1e-4, use_graphs=graphs) as s:
+            s.iterate(100000, 1e-8)
+            res.append((s.solution()[0], s.polish_log()))
+    assert np.array_equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
+
+
+def test_mixed_precision_polishes_in_fp64_only():
+    lp = lpgen.generate(2000, 5000, 1, nnz_per_col=5, support=0.3, fp32_values=True)
+    with P.Solver.from_lp(lp, precision=P.PDHG_MIXED, polish_switch=1e-5, feas_polish=1, gap_tol=1e-4) as s:
+        st, _ = s.iterate(100000, 1e-8)
+        info = s.info()
+        log = s.polish_log()
+        assert st == P.PDHG_OK
+        assert all(r["iteration"] >= info["polish_started_at"] >= 0 for r in log)
+        k = s.kkt()
+        assert k["rel_p"] <= 1e-8 and k["rel_d"] <= 1e-8 and k["rel_gap"] <= 1e-4
+
+
+def test_invalid_combinations(tiny_lp):
+    lp = tiny_lp
+    for bad in (dict(feas_polish=1, persistent=1), dict(feas_polish=2), dict(polish_div=0), dict(gap_tol=-1.0),
+                dict(feas_polish=1, record_for_backward=1, restarts=0, primal_weight=0)):
+        with pytest.raises(P.PDHGError) as ei:
+            P.Solver.from_lp(lp, **bad)
+        assert ei.value.status == P.PDHG_ERR_INVALID, bad
+    with pytest.raises(P.PDHGError) as ei:
+        P.BatchSolver([lp, lp], feas_polish=1)
+    assert ei.value.status == P.PDHG_ERR_INVALID
