@@ -99,9 +99,10 @@ typedef struct {
                              no recording, no kernel timing); 0: two launches per iteration (0) */
   int step_block;         /* threads per block of the step and evaluation kernels: 128, 256 or 512 (256) */
   int primal_panels;      /* panel-tiled primal half-step: y is cut into panels that fit in shared memory and
-                             A^T into per-panel segments whose partial sums are added per column; 1 = on in
-                             every precision, 0 = off, -1 = on in FP32 phases of single LPs with m >= 2^18
-                             and nnz >= 2^23 (-1) */
+                             the long rows of A^T (columns with >= long_row_min entries) into per-panel
+                             segments whose partial sums are added per column, while the other columns take
+                             the direct step; 1 = on, 0 = off, -1 = on for single LPs with m >= 2^18 and
+                             nnz >= 2^23 (-1) */
   int panel_rows;         /* entries of y per panel; 0 = as many as fit in shared memory (0; at most 28160) */
   int halpern;            /* 1: reflected Halpern iteration (the cuPDLP+ line, Section 4.1): z <- w ((1 + rho)
                              T(z) - rho z) + (1 - w) z_r with T the PDHG map, w = (t + 1) / (t + 2), t the

@@ -225,14 +225,15 @@ __device__ __forceinline__ void unit_dot(const Hyb& H, const T* __restrict__ val
   }
 }
 
-// every unit of H, one warp per unit in a grid-stride loop
+// every unit of H from unit u_begin on, one warp per unit in a grid-stride loop
 template <class T, class Op, class G>
-__device__ __forceinline__ void hyb_dot(const Hyb& H, const T* __restrict__ vals, const G& gather, Op& op) {
+__device__ __forceinline__ void hyb_dot(const Hyb& H, const T* __restrict__ vals, const G& gather, Op& op,
+                                        int u_begin = 0) {
   const unsigned long long pol = stream_policy();
   const int lane = threadIdx.x & 31;
   const int gwarp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
-  for (int u = gwarp; u < H.n_units; u += nwarps) unit_dot(H, vals, u, gather, op, pol, lane);
+  for (int u = u_begin + gwarp; u < H.n_units; u += nwarps) unit_dot(H, vals, u, gather, op, pol, lane);
 }
 
 struct NoState {};
@@ -430,11 +431,11 @@ template <class T>
 __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
     k_primal_step(Hyb At, const T* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
                   T* __restrict__ x, T* __restrict__ xbar, T* __restrict__ xsum, const DevState* __restrict__ sts,
-                  const int* __restrict__ binst, int accumulate) {
+                  const int* __restrict__ binst, int accumulate, int u_begin) {
   const DevState* st = block_state(sts, binst);
   if (st->frozen) return;
   PrimalOp<T> op{ch, x, xbar, xsum, (T)st->tau, accumulate};
-  hyb_dot(At, vals, GlobalGather<T>{y}, op);
+  hyb_dot(At, vals, GlobalGather<T>{y}, op, u_begin);
 }
 
 // weight w = (t + 1) / (t + 2) of the reflected Halpern step that runs as step
@@ -526,8 +527,17 @@ __global__ void __launch_bounds__(TPB) k_primal_combine(const int* __restrict__ 
     const T xj = __ldcs(x + j), cj = __ldcs(ch + j);
     const T sj = (accumulate || halp) ? __ldcs(xsum + j) : T(0);
     const int q0 = __ldg(cptr + j), q1 = __ldg(cptr + j + 1);
+    // added in panel order; eight loads in flight before their additions
     T g = T(0);
-    for (int q = q0; q < q1; ++q) g += __ldcs(partial + q);
+    int q = q0;
+    for (; q + 8 <= q1; q += 8) {
+      T a[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) a[e] = __ldcs(partial + q + e);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) g += a[e];
+    }
+    for (; q < q1; ++q) g += __ldcs(partial + q);
     const T xn = relu(xj - tau * (cj - g));
     xbar[j] = T(2) * xn - xj;  // default policy: gathered by the dual step next
     if (halp) {
@@ -580,11 +590,11 @@ template <class T>
 __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
     k_primal_step_halpern(Hyb At, const T* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
                           T* __restrict__ x, T* __restrict__ xbar, const T* __restrict__ xr,
-                          const DevState* __restrict__ sts, const int* __restrict__ binst, int it) {
+                          const DevState* __restrict__ sts, const int* __restrict__ binst, int it, int u_begin) {
   const DevState* st = block_state(sts, binst);
   if (st->frozen) return;
   PrimalHalpernOp<T> op{ch, x, xbar, xr, (T)st->tau, (T)halpern_weight(st, it), (T)st->rho};
-  hyb_dot(At, vals, GlobalGather<T>{y}, op);
+  hyb_dot(At, vals, GlobalGather<T>{y}, op, u_begin);
 }
 
 template <class T>
@@ -1179,16 +1189,17 @@ void launch_finish_setup(DevState* st, const double* scal, double step_factor, i
   k_finish_setup<<<1, 1, 0, s>>>(st, scal, step_factor, primal_weight);
 }
 void launch_primal_step(const Hyb& At, const double* y, const double* ch, double* x, double* xbar, double* xsum,
-                        const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst, int tpb) {
-  k_primal_step<double><<<grid, tpb, 0, s>>>(At, At.v, y, ch, x, xbar, xsum, st, binst, accumulate);
+                        const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst, int tpb,
+                        int u_begin) {
+  k_primal_step<double><<<grid, tpb, 0, s>>>(At, At.v, y, ch, x, xbar, xsum, st, binst, accumulate, u_begin);
 }
 void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
                       const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst, int tpb) {
   k_dual_step<double><<<grid, tpb, 0, s>>>(A, A.v, xbar, bh, y, ysum, st, binst, accumulate);
 }
 void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float* x, float* xbar, float* xsum,
-                          const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb) {
-  k_primal_step<float><<<grid, tpb, 0, s>>>(At, At.v32, y, ch, x, xbar, xsum, st, nullptr, accumulate);
+                          const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb, int u_begin) {
+  k_primal_step<float><<<grid, tpb, 0, s>>>(At, At.v32, y, ch, x, xbar, xsum, st, nullptr, accumulate, u_begin);
 }
 void launch_dual_step32(const Hyb& A, const float* xbar, const float* bh, float* y, float* ysum, const DevState* st,
                         int accumulate, int grid, cudaStream_t s, int tpb) {
@@ -1205,11 +1216,12 @@ template <class T>
 cudaError_t launch_primal_panels(const Hyb& Pn, const T* vals, const PanelLayout& L, const T* y, const T* ch, T* x,
                                  T* xbar, T* xsum, T* partial, const DevState* st, int accumulate, int n, int grid_n,
                                  cudaStream_t s, int halpern_it) {
+  if (L.ncols == 0) return cudaSuccess;
   const size_t smem = sizeof(T) * (size_t)L.rows;
   k_primal_panels<T><<<L.blocks, PANEL_TPB, smem, s>>>(Pn, vals, y, L.m, L.rows, L.binfo, L.ustart, L.segout,
                                                         partial);
-  k_primal_combine<T><<<(n + TPB - 1) / TPB, TPB, 0, s>>>(L.cptr, partial, ch, x, xbar, xsum, n, st, accumulate,
-                                                          halpern_it);
+  k_primal_combine<T><<<(L.ncols + TPB - 1) / TPB, TPB, 0, s>>>(L.cptr, partial, ch, x, xbar, xsum, L.ncols, st,
+                                                                accumulate, halpern_it);
   return cudaGetLastError();
 }
 template cudaError_t launch_primal_panels<double>(const Hyb&, const double*, const PanelLayout&, const double*,
@@ -1220,8 +1232,9 @@ template cudaError_t launch_primal_panels<float>(const Hyb&, const float*, const
                                                  int, int, cudaStream_t, int);
 template <class T>
 void launch_primal_step_halpern(const Hyb& At, const T* vals, const T* y, const T* ch, T* x, T* xbar, const T* xr,
-                                const DevState* st, int it, int grid, cudaStream_t s, int tpb, const int* binst) {
-  k_primal_step_halpern<T><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xr, st, binst, it);
+                                const DevState* st, int it, int grid, cudaStream_t s, int tpb, const int* binst,
+                                int u_begin) {
+  k_primal_step_halpern<T><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xr, st, binst, it, u_begin);
 }
 template <class T>
 void launch_dual_step_halpern(const Hyb& A, const T* vals, const T* xbar, const T* bh, T* y, const T* yr,
@@ -1230,10 +1243,10 @@ void launch_dual_step_halpern(const Hyb& A, const T* vals, const T* xbar, const 
 }
 template void launch_primal_step_halpern<double>(const Hyb&, const double*, const double*, const double*, double*,
                                                  double*, const double*, const DevState*, int, int, cudaStream_t,
-                                                 int, const int*);
+                                                 int, const int*, int);
 template void launch_primal_step_halpern<float>(const Hyb&, const float*, const float*, const float*, float*, float*,
                                                 const float*, const DevState*, int, int, cudaStream_t, int,
-                                                const int*);
+                                                const int*, int);
 template void launch_dual_step_halpern<double>(const Hyb&, const double*, const double*, const double*, double*,
                                                const double*, const DevState*, int, int, cudaStream_t, int,
                                                const int*);

@@ -39,9 +39,11 @@ void launch_finish_setup(DevState* st, const double* scal, double step_factor, i
 // x' = max(0, x - tau (chat - Ahat^T y)); xbar = 2x' - x; x <- x'; xsum += x'
 // st: the problem's state; for a batch, the instances' states and binst maps
 // every block to its instance (blocks of converged instances return at once)
+// (u_begin: first unit of At to process; the units before it are left to the
+// panel-tiled pass)
 void launch_primal_step(const Hyb& At, const double* y, const double* ch, double* x, double* xbar, double* xsum,
                         const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst = nullptr,
-                        int tpb = TPB);
+                        int tpb = TPB, int u_begin = 0);
 // y' = y + sigma (bhat - Ahat xbar); y <- y'; ysum += y'
 void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
                       const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst = nullptr,
@@ -52,7 +54,7 @@ void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double
 template <class T>
 void launch_primal_step_halpern(const Hyb& At, const T* vals, const T* y, const T* ch, T* x, T* xbar, const T* xr,
                                 const DevState* st, int it, int grid, cudaStream_t s, int tpb,
-                                const int* binst = nullptr);
+                                const int* binst = nullptr, int u_begin = 0);
 template <class T>
 void launch_dual_step_halpern(const Hyb& A, const T* vals, const T* xbar, const T* bh, T* y, const T* yr,
                               const DevState* st, int it, int grid, cudaStream_t s, int tpb,
@@ -60,7 +62,8 @@ void launch_dual_step_halpern(const Hyb& A, const T* vals, const T* xbar, const 
 // the same two half-steps in FP32 (values At.v32 / A.v32, FP32 vectors and
 // accumulation); tau and sigma are read from the FP64 state and rounded
 void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float* x, float* xbar, float* xsum,
-                          const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb = TPB);
+                          const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb = TPB,
+                          int u_begin = 0);
 void launch_dual_step32(const Hyb& A, const float* xbar, const float* bh, float* y, float* ysum, const DevState* st,
                         int accumulate, int grid, cudaStream_t s, int tpb = TPB);
 // precision conversions and the FP32 counterparts of make_average / apply
@@ -100,6 +103,8 @@ constexpr int PANEL_MINB32 = PDHG_PANEL_MINB32;
 constexpr int PANEL_SMEM_MAX = 220 * 1024;  // shared memory of one panel block
 struct PanelLayout {
   int m = 0;                // rows of A (length of y)
+  int ncols = 0;            // columns covered: internal columns [0, ncols), the long rows of A^T (units
+                            // [0, ncols) of At); the other columns take the direct primal step
   int rows = 0;             // panel height: entries of y per panel
   int panels = 0;           // ceil(m / rows)
   int* ustart = nullptr;    // [panels + 1] first unit of every panel in Pn

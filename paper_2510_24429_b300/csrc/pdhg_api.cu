@@ -191,6 +191,13 @@ int unit_grid(const pdhg_ctx* ctx, const Hyb& H) {
 // grid-stride launches (setup and evaluation kernels)
 int stride_grid(const pdhg_ctx* ctx, const Hyb& H) { return std::min(unit_grid(ctx, H), ctx->sms * 8); }
 
+// grid of the direct primal step over the units of Ahat^T that the panel pass
+// leaves to it (the short rows, units [pl.ncols, n_units))
+int short_grid(const pdhg_ctx* ctx) {
+  const long long units = std::max<long long>(1, ctx->At.n_units - ctx->pl.ncols);
+  return (int)((units + ctx->wpb - 1) / ctx->wpb);
+}
+
 pdhg_status set_device(pdhg_ctx* ctx) {
   int cur = -1;
   CK(ctx, cudaGetDevice(&cur));
@@ -532,18 +539,26 @@ int bit_length(unsigned long long v) {
 }
 
 // Panel layout of Ahat^T for the panel-tiled primal step (one LP): the entries
-// of every row j of A^T (sorted by internal row i) are cut into segments, one
-// per panel of ctx->pl.rows consecutive rows i; the segments of each panel,
+// of every long row j < nlong of A^T (the rows with at least long_row_min
+// entries, which come first in the internal numbering; sorted by internal row
+// i) are cut into segments, one per panel of ctx->pl.rows consecutive rows i;
+// short rows stay with the direct step (a one-entry segment would cost a
+// partial sum's write and read to save one gather). The segments of each panel,
 // sorted by decreasing length, become the rows of the Hyb ctx->Pn with row
 // indices relative to the panel. Segments are numbered column by column
 // (their partial sums' positions, segout), so that column j's partial sums
 // are positions [cptr[j], cptr[j+1]) in panel order.
 pdhg_status build_panels(pdhg_ctx* ctx, Scratch& sc, const long long* tp, const int* sval, const int* rowid,
-                         const int* iy, const double* val, unsigned max_col_len, long long* hist, long long* ws) {
+                         const int* iy, const double* val, unsigned max_col_len, long long nlong, long long* hist,
+                         long long* ws) {
   const pdhg_options& o = ctx->opt;
-  const long long N = ctx->n, Z = ctx->nnz;
+  const long long N = nlong;
   const int H = ctx->pl.rows, P = ctx->pl.panels;
   cudaStream_t s = ctx->stream;
+  long long Z = 0;  // entries of the long rows: tp[nlong]
+  CK(ctx, cudaMemcpyAsync(&Z, tp + N, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  ctx->pl.ncols = (int)N;
   int *head = nullptr, *panel = nullptr, *col = nullptr;
   long long* segpos = nullptr;
   CK(ctx, sc.take(&head, Z));
@@ -767,8 +782,15 @@ pdhg_status build_layouts(pdhg_ctx* ctx, Scratch& sc, const long long* lrp, cons
   launch_fill_units_T(ctx->At, slT, tp, sval, rowid, iy, val, s);
   CK(ctx, cudaGetLastError());
   if (ctx->panels_on) {
-    rs = build_panels(ctx, sc, tp, sval, rowid, iy, val, h_max[1], hist, ws);
-    if (rs != PDHG_OK) return rs;
+    // the long rows of A^T (a prefix of the internal columns) go to the panels
+    long long nlong = 0;
+    while (nlong < N && hT[nlong] >= o.long_row_min) ++nlong;
+    if (nlong == 0) {
+      ctx->panels_on = false;  // nothing to tile: the direct step takes every column
+    } else {
+      rs = build_panels(ctx, sc, tp, sval, rowid, iy, val, h_max[1], nlong, hist, ws);
+      if (rs != PDHG_OK) return rs;
+    }
   }
   if (batch) {
     ctx->nblocks = ctx->bstart_h[count];
@@ -1020,24 +1042,33 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
 
 // ---- one evaluation block -------------------------------------------------------
 
-// The primal half-step on (y, x, xbar, xsum) in FP32 or FP64: the panel-tiled
-// form (two kernels) in FP32 phases when its layout exists, and in FP64 phases
-// too when primal_panels = 1; else the direct one. (In FP64 the per-column
-// pass is bound by FP64 arithmetic, and the direct step is as fast.)
+// The primal half-step on (y, x, xbar, xsum) in FP32 or FP64: when the panel
+// layout exists, the direct step over the short columns plus the panel pass
+// and per-column combine over the long ones (three kernels); else the direct
+// step over every column.
 pdhg_status primal_step(pdhg_ctx* ctx, bool f32, const void* y, void* x, void* xbar, void* xsum, int accumulate,
                         int grT, int tpb) {
   cudaStream_t s = ctx->stream;
-  if (ctx->panels_on && (f32 || ctx->opt.primal_panels == 1)) {
-    const int gn = vec_grid(ctx, ctx->n);
+  if (ctx->panels_on) {
+    // short columns: the direct step over the units after the long rows; long
+    // columns: panel pass + per-column combine
+    const int gs = short_grid(ctx);
+    if (f32)
+      launch_primal_step32(ctx->At, (const float*)y, ctx->ch32, (float*)x, (float*)xbar, (float*)xsum, ctx->st,
+                           accumulate, gs, s, tpb, ctx->pl.ncols);
+    else
+      launch_primal_step(ctx->At, (const double*)y, ctx->ch, (double*)x, (double*)xbar, (double*)xsum, ctx->st,
+                         accumulate, gs, s, nullptr, tpb, ctx->pl.ncols);
+    const int gn = vec_grid(ctx, ctx->pl.ncols);
     cudaError_t e =
         f32 ? launch_primal_panels<float>(ctx->Pn, ctx->Pn.v32, ctx->pl, (const float*)y, ctx->ch32, (float*)x,
                                           (float*)xbar, (float*)xsum, ctx->pn_partial32, ctx->st, accumulate,
-                                          (int)ctx->n, gn, s)
+                                          ctx->pl.ncols, gn, s)
             : launch_primal_panels<double>(ctx->Pn, ctx->Pn.v, ctx->pl, (const double*)y, ctx->ch, (double*)x,
                                            (double*)xbar, (double*)xsum, ctx->pn_partial, ctx->st, accumulate,
-                                           (int)ctx->n, gn, s);
+                                           ctx->pl.ncols, gn, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "panel-tiled primal step");
-    ctx->launches += 1;  // the second kernel
+    ctx->launches += 2;  // the panel pass and the combine
   } else if (f32) {
     launch_primal_step32(ctx->At, (const float*)y, ctx->ch32, (float*)x, (float*)xbar, (float*)xsum, ctx->st,
                          accumulate, grT, s, tpb);
@@ -1062,16 +1093,29 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
     }
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
     if (o.halpern && !ctx->phase32) {
-      launch_primal_step_halpern<double>(ctx->At, ctx->At.v, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xr, ctx->st,
-                                         (int)it, grT, s, tpb);
+      if (ctx->panels_on) {  // the anchor (last restart point) in place of the sums
+        launch_primal_step_halpern<double>(ctx->At, ctx->At.v, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xr,
+                                           ctx->st, (int)it, short_grid(ctx), s, tpb, nullptr, ctx->pl.ncols);
+        cudaError_t e = launch_primal_panels<double>(ctx->Pn, ctx->Pn.v, ctx->pl, ctx->y, ctx->ch, ctx->x,
+                                                     ctx->xbar, ctx->xr, ctx->pn_partial, ctx->st, 0,
+                                                     ctx->pl.ncols, vec_grid(ctx, ctx->pl.ncols), s, (int)it);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "panel-tiled primal step");
+        ctx->launches += 2;
+      } else {
+        launch_primal_step_halpern<double>(ctx->At, ctx->At.v, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xr, ctx->st,
+                                           (int)it, grT, s, tpb);
+      }
     } else if (o.halpern) {
       // FP32 Halpern: the FP32 sums hold the FP32 anchor (no averages in this form)
       if (ctx->panels_on) {
+        launch_primal_step_halpern<float>(ctx->At, ctx->At.v32, ctx->y32, ctx->ch32, ctx->x32, ctx->xbar32,
+                                          ctx->xsum32, ctx->st, (int)it, short_grid(ctx), s, tpb, nullptr,
+                                          ctx->pl.ncols);
         cudaError_t e = launch_primal_panels<float>(ctx->Pn, ctx->Pn.v32, ctx->pl, ctx->y32, ctx->ch32, ctx->x32,
                                                     ctx->xbar32, ctx->xsum32, ctx->pn_partial32, ctx->st, 0,
-                                                    (int)ctx->n, vec_grid(ctx, ctx->n), s, (int)it);
+                                                    ctx->pl.ncols, vec_grid(ctx, ctx->pl.ncols), s, (int)it);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "panel-tiled primal step");
-        ctx->launches += 1;
+        ctx->launches += 2;
       } else {
         launch_primal_step_halpern<float>(ctx->At, ctx->At.v32, ctx->y32, ctx->ch32, ctx->x32, ctx->xbar32,
                                           ctx->xsum32, ctx->st, (int)it, grT, s, tpb);
@@ -1738,7 +1782,6 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     return fail(nullptr, PDHG_ERR_INVALID, "primal_panels must be -1, 0 or 1 and panel_rows in [0, 28160]");
   if (o.persistent && o.primal_panels == 1)
     return fail(nullptr, PDHG_ERR_INVALID, "persistent = 1 and primal_panels = 1 exclude each other");
-  // (FP64 phases of the Halpern form always run the direct primal step)
   if (o.halpern != 0 && (o.halpern != 1 || o.persistent || o.record_for_backward || o.dual_hot_cols ||
                          !(o.halpern_reflect >= 0.0) || !(o.halpern_reflect <= 1.0)))
     return fail(nullptr, PDHG_ERR_INVALID,
@@ -1776,8 +1819,8 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
   ctx->wpb = (o.step_block ? o.step_block : TPB) / 32;
   // auto: only where the matrix stream dwarfs the panels' copies of y (every
   // block copies one panel, ~H entries, per step)
-  ctx->panels_on = !o.persistent && (o.primal_panels == 1 || (o.primal_panels < 0 && o.precision != PDHG_FP64 &&
-                                                                m >= (1 << 18) && nnz >= (1 << 23)));
+  ctx->panels_on = !o.persistent && (o.primal_panels == 1 || (o.primal_panels < 0 && m >= (1 << 18) &&
+                                                                nnz >= (1 << 23)));
   if (ctx->panels_on) {
     const long long hmax = PANEL_SMEM_MAX / (long long)sizeof(double);
     const long long P0 = (m + hmax - 1) / hmax;

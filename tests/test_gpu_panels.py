@@ -1,5 +1,8 @@
 """Panel-tiled primal half-step (option primal_panels): y staged in shared
-memory panel by panel, per-(column, panel) partial sums added per column.
+memory panel by panel, per-(column, panel) partial sums added per column for
+the long columns (at least long_row_min entries); the short columns take the
+direct step in the same half-step. The tiny LP's columns all have 5 entries,
+so long_row_min=4 puts every column in the panels; a Zipf-shaped LP mixes both.
 
 The per-column sums are grouped by panel, so results differ from the direct
 step at rounding level only; against the oracle the same bars as the parity
@@ -35,14 +38,14 @@ def _solvers(lp, engine_opts, **opts):
 
 @pytest.mark.parametrize("rows", [1, 7, 32, 200])
 def test_plain_100_iterations_match_oracle(tiny_lp, rows):
-    orc, sol = _solvers(tiny_lp, dict(primal_panels=1, panel_rows=rows), **TINY_PLAIN)
+    orc, sol = _solvers(tiny_lp, dict(primal_panels=1, panel_rows=rows, long_row_min=4), **TINY_PLAIN)
     orc.run(100)
     assert sol.iterate(100) == (P.PDHG_OK, 100)
     assert_iterates_close(sol, orc, 1e-10)
 
 
 def test_panels_agree_with_direct_step(tiny_lp):
-    _, sp = _solvers(tiny_lp, dict(primal_panels=1, panel_rows=32), **TINY_PLAIN)
+    _, sp = _solvers(tiny_lp, dict(primal_panels=1, panel_rows=32, long_row_min=4), **TINY_PLAIN)
     _, sd = _solvers(tiny_lp, dict(primal_panels=0), **TINY_PLAIN)
     sp.iterate(2000)
     sd.iterate(2000)
@@ -51,20 +54,20 @@ def test_panels_agree_with_direct_step(tiny_lp):
 
 
 def test_restarted_run_matches_oracle(tiny_lp):
-    orc, sol = _solvers(tiny_lp, dict(primal_panels=1, panel_rows=32))
+    orc, sol = _solvers(tiny_lp, dict(primal_panels=1, panel_rows=32, long_row_min=4))
     orc.run(100)
     sol.iterate(100)
     assert [r["kind"] for r in sol.trace()] == [r.kind for r in orc.trace] != [0]
     assert_iterates_close(sol, orc, 1e-10)
     assert_iterates_close(sol, orc, 1e-10, P.PDHG_AVERAGE)
-    orc2, sol2 = _solvers(tiny_lp, dict(primal_panels=1, panel_rows=32))
+    orc2, sol2 = _solvers(tiny_lp, dict(primal_panels=1, panel_rows=32, long_row_min=4))
     orc2.run(3000, 1e-10)
     sol2.iterate(3000, 1e-10)
     assert compare_traces(sol2.trace(), orc2.trace) >= 20
 
 
 def test_converges_to_known_optimum(tiny_lp):
-    _, sol = _solvers(tiny_lp, dict(primal_panels=1, panel_rows=50))
+    _, sol = _solvers(tiny_lp, dict(primal_panels=1, panel_rows=50, long_row_min=4))
     st, _ = sol.iterate(200000, 1e-8)
     assert st == P.PDHG_OK
     k = sol.kkt()
@@ -76,7 +79,7 @@ def test_converges_to_known_optimum(tiny_lp):
 
 @pytest.mark.parametrize("prec", [P.PDHG_FP32, P.PDHG_MIXED])
 def test_fp32_and_mixed_with_panels(tiny_lp, prec):
-    with P.Solver.from_lp(tiny_lp, precision=prec, primal_panels=1, panel_rows=40) as sp, \
+    with P.Solver.from_lp(tiny_lp, precision=prec, primal_panels=1, panel_rows=40, long_row_min=4) as sp, \
             P.Solver.from_lp(tiny_lp, precision=prec, primal_panels=0) as sd:
         sp.iterate(640)
         sd.iterate(640)
@@ -95,7 +98,7 @@ def test_adjoint_with_panels(tiny_lp):
     rng = np.random.default_rng(5)
     gx = rng.standard_normal(tiny_lp.n)
     grads = []
-    for opts in (dict(primal_panels=1, panel_rows=16), dict(primal_panels=0)):
+    for opts in (dict(primal_panels=1, panel_rows=16, long_row_min=4), dict(primal_panels=0, long_row_min=4)):
         with P.Solver.from_lp(tiny_lp, **base, **opts) as s:
             s.iterate(60)
             grads.append(s.backward(gx))
@@ -106,10 +109,35 @@ def test_adjoint_with_panels(tiny_lp):
 def test_edge_shapes():
     for m, n, k in ((1, 1, 1), (1, 9, 1), (9, 1, 1), (5, 40, 3)):
         lp = lpgen.generate(m, n, 11, nnz_per_col=k, support=0.3)
-        orc, sol = _solvers(lp, dict(primal_panels=1, panel_rows=2), **TINY_PLAIN)
-        orc.run(50)
-        sol.iterate(50)
+        for lrm in (1, 2, 128):  # every column, the longer ones, none in the panels
+            orc, sol = _solvers(lp, dict(primal_panels=1, panel_rows=2, long_row_min=lrm), **TINY_PLAIN)
+            orc.run(50)
+            sol.iterate(50)
+            assert_iterates_close(sol, orc, 1e-10)
+
+
+@pytest.mark.parametrize("prec", [P.PDHG_FP64, P.PDHG_FP32])
+def test_long_and_short_columns_mixed(prec):
+    """Zipf-shaped column counts: columns with >= 32 entries in the panels, the
+    rest in the direct step of the same half-step; against the oracle (FP64)
+    or the direct FP32 engine."""
+    lp = lpgen.generate(3000, 9000, 2, nnz_per_col=None, zipf=(1.5, 10000, 90000), val_range=(0.1, 10.0),
+                        support=0.3, fp32_values=True)
+    eng = dict(primal_panels=1, panel_rows=256, long_row_min=32, precision=prec)
+    if prec == P.PDHG_FP64:
+        orc, sol = _solvers(lp, eng, **TINY_PLAIN)
+        orc.run(100)
+        assert sol.iterate(100) == (P.PDHG_OK, 100)
         assert_iterates_close(sol, orc, 1e-10)
+        orc2, sol2 = _solvers(lp, eng)
+        orc2.run(2000, 1e-9)
+        sol2.iterate(2000, 1e-9)
+        assert compare_traces(sol2.trace(), orc2.trace) >= 10
+    else:
+        with P.Solver.from_lp(lp, **eng) as sp, P.Solver.from_lp(lp, precision=prec, primal_panels=0) as sd:
+            sp.iterate(640)
+            sd.iterate(640)
+            assert rel_err(sp.solution()[0], sd.solution()[0]) <= 1e-4
 
 
 def test_option_checks(tiny_lp):
@@ -121,3 +149,20 @@ def test_option_checks(tiny_lp):
         P.Solver.from_lp(tiny_lp, primal_panels=1, persistent=1)
     with pytest.raises(P.PDHGError):
         P.BatchSolver([tiny_lp, tiny_lp], primal_panels=1)
+
+
+def test_halpern_fp64_with_panels():
+    """The reflected Halpern form in FP64 with the panel-tiled step (anchor =
+    last restart point in the combine and in the short-column step) against
+    the oracle's Halpern variant."""
+    lp = lpgen.generate(3000, 9000, 2, nnz_per_col=None, zipf=(1.5, 10000, 90000), val_range=(0.1, 10.0),
+                        support=0.3)
+    eng = dict(primal_panels=1, panel_rows=256, long_row_min=32, halpern=1)
+    orc, sol = _solvers(lp, eng, halpern=True, **TINY_PLAIN)
+    orc.run(100)
+    assert sol.iterate(100) == (P.PDHG_OK, 100)
+    assert_iterates_close(sol, orc, 1e-10)
+    orc2, sol2 = _solvers(lp, eng, halpern=True)
+    orc2.run(1500, 1e-9)
+    sol2.iterate(1500, 1e-9)
+    assert compare_traces(sol2.trace(), orc2.trace) >= 10
