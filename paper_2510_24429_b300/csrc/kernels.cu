@@ -511,11 +511,14 @@ __global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
 }
 
 // one thread per column; the update's operands are loaded before the partial
-// sums so that their latencies overlap (same arithmetic as PrimalOp)
+// sums so that their latencies overlap (same arithmetic as PrimalOp). The
+// partial sums are panel-major (panel p of column j at p * ncols + j, zero
+// where the column has no entry in the panel), so a warp's loads are
+// contiguous.
 // halpern_it >= 0: the reflected Halpern update with xsum as the anchor (the
 // Halpern form keeps its anchor where the sums would be; see PrimalHalpernOp)
 template <class T>
-__global__ void __launch_bounds__(TPB) k_primal_combine(const int* __restrict__ cptr, const T* __restrict__ partial,
+__global__ void __launch_bounds__(TPB) k_primal_combine(int panels, const T* __restrict__ partial,
                                                         const T* __restrict__ ch, T* __restrict__ x,
                                                         T* __restrict__ xbar, T* __restrict__ xsum, int n,
                                                         const DevState* __restrict__ st, int accumulate,
@@ -526,18 +529,18 @@ __global__ void __launch_bounds__(TPB) k_primal_combine(const int* __restrict__ 
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
     const T xj = __ldcs(x + j), cj = __ldcs(ch + j);
     const T sj = (accumulate || halp) ? __ldcs(xsum + j) : T(0);
-    const int q0 = __ldg(cptr + j), q1 = __ldg(cptr + j + 1);
     // added in panel order; eight loads in flight before their additions
+    const T* pj = partial + j;
     T g = T(0);
-    int q = q0;
-    for (; q + 8 <= q1; q += 8) {
+    int p = 0;
+    for (; p + 8 <= panels; p += 8) {
       T a[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) a[e] = __ldcs(partial + q + e);
+      for (int e = 0; e < 8; ++e) a[e] = __ldcs(pj + (long long)(p + e) * n);
 #pragma unroll
       for (int e = 0; e < 8; ++e) g += a[e];
     }
-    for (; q < q1; ++q) g += __ldcs(partial + q);
+    for (; p < panels; ++p) g += __ldcs(pj + (long long)p * n);
     const T xn = relu(xj - tau * (cj - g));
     xbar[j] = T(2) * xn - xj;  // default policy: gathered by the dual step next
     if (halp) {
@@ -1220,7 +1223,7 @@ cudaError_t launch_primal_panels(const Hyb& Pn, const T* vals, const PanelLayout
   const size_t smem = sizeof(T) * (size_t)L.rows;
   k_primal_panels<T><<<L.blocks, PANEL_TPB, smem, s>>>(Pn, vals, y, L.m, L.rows, L.binfo, L.ustart, L.segout,
                                                         partial);
-  k_primal_combine<T><<<(L.ncols + TPB - 1) / TPB, TPB, 0, s>>>(L.cptr, partial, ch, x, xbar, xsum, L.ncols, st,
+  k_primal_combine<T><<<(L.ncols + TPB - 1) / TPB, TPB, 0, s>>>(L.panels, partial, ch, x, xbar, xsum, L.ncols, st,
                                                                 accumulate, halpern_it);
   return cudaGetLastError();
 }

@@ -108,8 +108,8 @@ struct PanelLayout {
   int rows = 0;             // panel height: entries of y per panel
   int panels = 0;           // ceil(m / rows)
   int* ustart = nullptr;    // [panels + 1] first unit of every panel in Pn
-  int* segout = nullptr;    // [segments] column-major position of every segment row of Pn
-  int* cptr = nullptr;      // [n + 1] first segment position of every column
+  int* segout = nullptr;    // [segments] position of every segment row of Pn in the dense panel-major
+                            // partial sums (panel * ncols + column; slots of absent segments stay 0)
   int blocks = 0;           // blocks of the panel pass (one wave)
   int4* binfo = nullptr;    // [blocks] (panel, index among its panel's blocks, its panel's block count, 0)
 };
@@ -200,7 +200,8 @@ void launch_panel_rowinfo(const int* sp, const int* seg_col, const int* seg_pane
                           int* pbase, cudaStream_t s);
 void launch_panel_keys(const long long* seg_start, const int* seg_panel, long long S, int maxlen, int lbits,
                        int* seg_len, unsigned long long* keys, int* vals, int* pcount, cudaStream_t s);
-void launch_panel_cptr(const long long* tp, const long long* segpos, long long N, int* cptr, cudaStream_t s);
+void launch_panel_dense_out(const int* pcol, const int* pbase, int H, int ncols, long long S, int* out,
+                            cudaStream_t s);
 void launch_max_int(const int* v, long long len, unsigned* out, cudaStream_t s);
 void launch_fill_units_P(const Hyb& H, const int* slen, const int* sp, const long long* seg_start,
                          const int* seg_panel, const int* sval, const int* rowid, const int* iy, const double* v,

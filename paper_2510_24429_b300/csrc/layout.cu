@@ -194,10 +194,11 @@ __global__ void k_panel_rowinfo(const int* __restrict__ sp, const int* __restric
   }
 }
 
-// first segment of every column: cptr[j] = segpos[tp[j]] (cptr[N] = S)
-__global__ void k_panel_cptr(const long long* __restrict__ tp, const long long* __restrict__ segpos, long long N,
-                             int* __restrict__ cptr) {
-  for (long long j = gtid(); j <= N; j += gstride()) cptr[j] = (int)segpos[tp[j]];
+// partial-sum position of every segment row r in the dense panel-major array
+// of the panel pass: panel * ncols + column
+__global__ void k_panel_dense_out(const int* __restrict__ pcol, const int* __restrict__ pbase, int H, int ncols,
+                                  long long S, int* __restrict__ out) {
+  for (long long r = gtid(); r < S; r += gstride()) out[r] = (pbase[r] / H) * ncols + pcol[r];
 }
 
 __global__ void k_invert(const int* __restrict__ p, long long len, int* __restrict__ inv) {
@@ -519,8 +520,9 @@ void launch_panel_keys(const long long* seg_start, const int* seg_panel, long lo
                                                          pcount);
 }
 
-void launch_panel_cptr(const long long* tp, const long long* segpos, long long N, int* cptr, cudaStream_t s) {
-  k_panel_cptr<<<grid_of(N + 1), LT_TPB, 0, s>>>(tp, segpos, N, cptr);
+void launch_panel_dense_out(const int* pcol, const int* pbase, int H, int ncols, long long S, int* out,
+                            cudaStream_t s) {
+  if (S > 0) k_panel_dense_out<<<grid_of(S), LT_TPB, 0, s>>>(pcol, pbase, H, ncols, S, out);
 }
 
 void launch_max_int(const int* v, long long len, unsigned* out, cudaStream_t s) {

@@ -593,12 +593,10 @@ pdhg_status build_panels(pdhg_ctx* ctx, Scratch& sc, const long long* tp, const 
   const int alt = radix_sort_pairs<unsigned long long>(ka, va, kb, vb, S,
                                                         lbits + bit_length((unsigned long long)(P - 1)), hist, ws, s);
   const int* sp = alt ? vb : va;
-  CK(ctx, dalloc(ctx, &ctx->pl.segout, S));
-  CK(ctx, cudaMemcpyAsync(ctx->pl.segout, sp, sizeof(int) * S, cudaMemcpyDeviceToDevice, s));
   launch_gather_int(seg_len, sp, S, slen, s);
   launch_panel_rowinfo(sp, seg_col, seg_panel, H, S, ctx->pn_col, ctx->pn_base, s);
-  CK(ctx, dalloc(ctx, &ctx->pl.cptr, N + 1));
-  launch_panel_cptr(tp, segpos, N, ctx->pl.cptr, s);
+  CK(ctx, dalloc(ctx, &ctx->pl.segout, S));
+  launch_panel_dense_out(ctx->pn_col, ctx->pn_base, H, (int)N, S, ctx->pl.segout, s);
   std::vector<int> hs(S), hc(P);
   CK(ctx, cudaMemcpyAsync(hs.data(), slen, sizeof(int) * S, cudaMemcpyDeviceToHost, s));
   CK(ctx, cudaMemcpyAsync(hc.data(), pcount, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
@@ -644,7 +642,10 @@ pdhg_status build_panels(pdhg_ctx* ctx, Scratch& sc, const long long* tp, const 
   CK(ctx, dalloc(ctx, &ctx->pl.ustart, P + 1));
   CK(ctx, cudaMemcpyAsync(ctx->pl.ustart, ust.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice, s));
   launch_fill_units_P(ctx->Pn, slen, sp, seg_start, seg_panel, sval, rowid, iy, val, H, s);
-  CK(ctx, dalloc(ctx, &ctx->pn_partial, std::max<long long>(1, S)));
+  // dense panel-major partial sums; the slots of absent segments stay 0
+  const long long slots = std::max<long long>(1, (long long)P * N);
+  CK(ctx, dalloc(ctx, &ctx->pn_partial, slots));
+  CK(ctx, cudaMemsetAsync(ctx->pn_partial, 0, sizeof(double) * slots, s));
   CK(ctx, cudaGetLastError());
   CK(ctx, cudaStreamSynchronize(s));  // the host tables are released on return
   return PDHG_OK;
@@ -785,8 +786,11 @@ pdhg_status build_layouts(pdhg_ctx* ctx, Scratch& sc, const long long* lrp, cons
     // the long rows of A^T (a prefix of the internal columns) go to the panels
     long long nlong = 0;
     while (nlong < N && hT[nlong] >= o.long_row_min) ++nlong;
-    if (nlong == 0) {
-      ctx->panels_on = false;  // nothing to tile: the direct step takes every column
+    const long long dense = (long long)ctx->pl.panels * nlong;  // slots of the panel-major partial sums
+    if (nlong == 0 || dense > 64LL * Z + (1LL << 20) || dense >= (1LL << 31) - 1) {
+      // nothing to tile, or partial sums far larger than the matrix: the
+      // direct step takes every column
+      ctx->panels_on = false;
     } else {
       rs = build_panels(ctx, sc, tp, sval, rowid, iy, val, h_max[1], nlong, hist, ws);
       if (rs != PDHG_OK) return rs;
@@ -1007,7 +1011,9 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
     launch_narrow(At.v32, At.v, At.slots, vec_grid(ctx, At.slots), s);
     if (ctx->panels_on) {
       CK(ctx, dalloc(ctx, &ctx->Pn.v32, ctx->Pn.slots));
-      CK(ctx, dalloc(ctx, &ctx->pn_partial32, std::max<long long>(1, ctx->Pn.rows)));
+      const long long slots = std::max<long long>(1, (long long)ctx->pl.panels * ctx->pl.ncols);
+      CK(ctx, dalloc(ctx, &ctx->pn_partial32, slots));
+      CK(ctx, cudaMemsetAsync(ctx->pn_partial32, 0, sizeof(float) * slots, s));
       launch_narrow(ctx->Pn.v32, ctx->Pn.v, ctx->Pn.slots, vec_grid(ctx, ctx->Pn.slots), s);
     }
     launch_narrow(ctx->ch32, ctx->ch, n, gn, s);
