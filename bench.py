@@ -164,7 +164,10 @@ def profiled_traffic(kernel: str, workload: str):
 # ---------------------------------------------------------------------------
 # distributed plumbing (replicas only)
 # ---------------------------------------------------------------------------
-def dist_init(args):
+def dist_init(args, backend=None):
+    """Rank, world size and local rank from the launcher's environment; for
+    N > 1 one process group over the replicas (NCCL on GPUs; gloo where no GPU
+    is visible, which the CPU tests of this plumbing use)."""
     import torch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -173,8 +176,12 @@ def dist_init(args):
     if world > 1:
         import torch.distributed as dist
 
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        backend = backend or ("nccl" if torch.cuda.is_available() else "gloo")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     elif torch.cuda.is_available():
         torch.cuda.set_device(0)
     return rank, world, local
@@ -193,7 +200,7 @@ def max_over_ranks(v: float, world: int) -> float:
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
