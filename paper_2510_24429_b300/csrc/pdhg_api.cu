@@ -19,6 +19,8 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <functional>
+#include <future>
 #include <mutex>
 #include <new>
 #include <string>
@@ -219,7 +221,7 @@ void parallel_for(int T, F fn) {
 int host_threads(int64_t work) {
   if (work < (1 << 20)) return 1;
   const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-  return (int)std::min<int64_t>({(int64_t)hw, 16, work >> 19});
+  return (int)std::min<int64_t>({(int64_t)hw, 32, work >> 19});
 }
 
 bool all_finite(const double* v, int64_t len) {
@@ -236,46 +238,83 @@ bool all_finite(const double* v, int64_t len) {
   return std::all_of(ok.begin(), ok.end(), [](char c) { return c != 0; });
 }
 
-// Host checks of one LP (before any device work). The row pointers are
-// checked first, so that every row's entries lie in [0, nnz) when the entries
-// are checked (in parallel over row ranges; the first failing row decides the
-// message).
-pdhg_status validate_lp(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
-                        const double* val, const double* b, const double* c) {
+// Host checks of one LP, one pass over the entries in parallel over row
+// ranges: every row's pointers are checked before its entries are read, so no
+// read leaves [0, nnz). Precedence of the messages: a decreasing row_ptr
+// anywhere, then the first bad column index (by row range), then NaN/Inf in
+// the data. Touches no global state (it runs beside the context's set-up);
+// *msg gets the failure's description.
+pdhg_status check_lp(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                     const double* val, const double* b, const double* c, const char** msg) {
+  auto fail = [msg](pdhg_status st, const char* text) {
+    *msg = text;
+    return st;
+  };
   if (m < 1 || n < 1 || m >= (1LL << 31) - 1 || n >= (1LL << 31) - 1)
-    return fail(nullptr, PDHG_ERR_INVALID, "m and n must be in [1, 2^31 - 1)");
-  if (nnz < 0 || nnz >= (1LL << 31) - 1) return fail(nullptr, PDHG_ERR_INVALID, "nnz must be in [0, 2^31 - 1)");
+    return fail(PDHG_ERR_INVALID, "m and n must be in [1, 2^31 - 1)");
+  if (nnz < 0 || nnz >= (1LL << 31) - 1) return fail(PDHG_ERR_INVALID, "nnz must be in [0, 2^31 - 1)");
   if (!row_ptr || (nnz > 0 && (!col_idx || !val)) || !b || !c)
-    return fail(nullptr, PDHG_ERR_INVALID, "NULL array argument");
+    return fail(PDHG_ERR_INVALID, "NULL array argument");
   if (row_ptr[0] != 0 || row_ptr[m] != nnz)
-    return fail(nullptr, PDHG_ERR_INVALID, "row_ptr[0] != 0 or row_ptr[m] != nnz");
-  for (int64_t i = 0; i < m; ++i)
-    if (row_ptr[i + 1] < row_ptr[i]) return fail(nullptr, PDHG_ERR_INVALID, "row_ptr not non-decreasing");
-  const int T = host_threads(nnz);
-  std::vector<int> bad_kind(T, 0);
+    return fail(PDHG_ERR_INVALID, "row_ptr[0] != 0 or row_ptr[m] != nnz");
+  enum { OK = 0, BAD_PTR = 1, BAD_RANGE = 2, BAD_ORDER = 3 };
+  const int T = host_threads(nnz + m);
+  std::vector<int> bad(T, OK);
+  std::vector<char> finite(T, 1);
   parallel_for(T, [&](int t) {
     const int64_t r0 = m * t / T, r1 = m * (t + 1) / T;
-    for (int64_t i = r0; i < r1; ++i)
-      for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-        int kind = 0;
-        if (col_idx[k] < 0 || col_idx[k] >= n)
-          kind = 1;
-        else if (k > row_ptr[i] && col_idx[k] <= col_idx[k - 1])
-          kind = 2;
-        if (kind) {
-          bad_kind[t] = kind;
-          return;
-        }
+    const unsigned un = (unsigned)n;
+    const unsigned long long EXP = 0x7ff0000000000000ull;
+    unsigned long long nonfinite = 0;
+    for (int64_t i = r0; i < r1; ++i) {
+      const int64_t a = row_ptr[i], e = row_ptr[i + 1];
+      if (e < a || a < 0 || e > nnz) {
+        bad[t] = BAD_PTR;
+        break;
       }
+      // branch-free checks of the row (they vectorize); the rare failing row
+      // is scanned again for its first bad entry
+      unsigned out = 0, order = 0;
+      for (int64_t k = a; k < e; ++k) {
+        out |= (unsigned)col_idx[k] >= un;  // negative indices wrap to large values
+        unsigned long long bits;
+        memcpy(&bits, val + k, sizeof(bits));
+        nonfinite |= (unsigned long long)((bits & EXP) == EXP);
+      }
+      for (int64_t k = a + 1; k < e; ++k) order |= col_idx[k] <= col_idx[k - 1];
+      if (out | order) {
+        for (int64_t k = a; k < e; ++k) {
+          if ((unsigned)col_idx[k] >= un) {
+            bad[t] = BAD_RANGE;
+            break;
+          }
+          if (k > a && col_idx[k] <= col_idx[k - 1]) {
+            bad[t] = BAD_ORDER;
+            break;
+          }
+        }
+        break;
+      }
+    }
+    finite[t] = nonfinite == 0;
   });
+  if (std::find(bad.begin(), bad.end(), (int)BAD_PTR) != bad.end())
+    return fail(PDHG_ERR_INVALID, "row_ptr not non-decreasing");
   for (int t = 0; t < T; ++t) {
-    if (bad_kind[t] == 1) return fail(nullptr, PDHG_ERR_INVALID, "column index out of range");
-    if (bad_kind[t] == 2)
-      return fail(nullptr, PDHG_ERR_INVALID, "column indices not strictly increasing within a row");
+    if (bad[t] == BAD_RANGE) return fail(PDHG_ERR_INVALID, "column index out of range");
+    if (bad[t] == BAD_ORDER)
+      return fail(PDHG_ERR_INVALID, "column indices not strictly increasing within a row");
   }
-  if (!all_finite(val, nnz) || !all_finite(b, m) || !all_finite(c, n))
-    return fail(nullptr, PDHG_ERR_NUMERIC, "NaN or Inf in the input data");
+  if (std::find(finite.begin(), finite.end(), (char)0) != finite.end() || !all_finite(b, m) || !all_finite(c, n))
+    return fail(PDHG_ERR_NUMERIC, "NaN or Inf in the input data");
   return PDHG_OK;
+}
+
+pdhg_status validate_lp(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                        const double* val, const double* b, const double* c) {
+  const char* msg = "";
+  const pdhg_status st = check_lp(m, n, nnz, row_ptr, col_idx, val, b, c, &msg);
+  return st == PDHG_OK ? st : fail(nullptr, st, msg);
 }
 
 pdhg_status read_state(pdhg_ctx* ctx) {
@@ -806,8 +845,11 @@ pdhg_status build_layouts(pdhg_ctx* ctx, Scratch& sc, const long long* lrp, cons
   return PDHG_OK;
 }
 
+// host_checks: waits for the checks of host inputs (see pdhg_create) and
+// returns their status; called once the upload is queued, before anything
+// reads the uploaded data.
 pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx, const double* val, const double* b,
-                  const double* c, const double* x0, const double* y0) {
+                  const double* c, const double* x0, const double* y0, const std::function<pdhg_status()>& host_checks) {
   const int64_t m = ctx->m, n = ctx->n, nnz = ctx->nnz;
   const pdhg_options& o = ctx->opt;
   cudaStream_t s = ctx->stream;
@@ -879,6 +921,8 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
     d_v = v_;
     d_b = b_;
     d_c = c_;
+    const pdhg_status checked = host_checks();
+    if (checked != PDHG_OK) return checked;  // the caller reports the checks' message
   }
   pdhg_status rs = build_layouts(ctx, sc, d_rp, d_ci, d_v, {0}, {0, (long long)nnz});
   if (rs != PDHG_OK) return rs;
@@ -1807,17 +1851,34 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
   if (o.feas_polish && (o.persistent || o.record_for_backward))
     return fail(nullptr, PDHG_ERR_INVALID, "feas_polish = 1 needs no persistent loop and no recording");
 
-  // CSR validation of host inputs (host logic, before any device work);
-  // device inputs are checked on the device during setup
-  if (!o.inputs_on_device) {
-    pdhg_status vs = validate_lp(m, n, nnz, row_ptr, col_idx, val, b, c);
-    if (vs != PDHG_OK) return vs;
-    if ((x0 && !all_finite(x0, n)) || (y0 && !all_finite(y0, m)))
-      return fail(nullptr, PDHG_ERR_NUMERIC, "NaN or Inf in the input data");
-  }
+  // Checks of host inputs (CSR structure, finite data) on host threads, beside
+  // the context's set-up: stream creation, allocations and the upload depend
+  // only on the sizes, and setup reads nothing it uploaded before the checks
+  // have passed. Their failure takes precedence over any later error, so a
+  // malformed LP gets INVALID / NUMERIC whether or not a GPU is present.
+  // Device inputs are checked on the device during setup.
+  std::future<std::pair<pdhg_status, const char*>> checks;
+  if (!o.inputs_on_device)
+    checks = std::async(std::launch::async, [=]() {
+      const char* msg = "";
+      pdhg_status st = check_lp(m, n, nnz, row_ptr, col_idx, val, b, c, &msg);
+      if (st == PDHG_OK && ((x0 && !all_finite(x0, n)) || (y0 && !all_finite(y0, m)))) {
+        st = PDHG_ERR_NUMERIC;
+        msg = "NaN or Inf in the input data";
+      }
+      return std::make_pair(st, msg);
+    });
+  std::pair<pdhg_status, const char*> checked{PDHG_OK, ""};
+  std::function<pdhg_status()> await_checks = [&]() {
+    if (checks.valid()) checked = checks.get();
+    return checked.first;
+  };
 
   pdhg_ctx* ctx = new (std::nothrow) pdhg_ctx();
-  if (!ctx) return fail(nullptr, PDHG_ERR_OOM, "host allocation of the context failed");
+  if (!ctx) {
+    if (await_checks() != PDHG_OK) return fail(nullptr, checked.first, checked.second);
+    return fail(nullptr, PDHG_ERR_OOM, "host allocation of the context failed");
+  }
   ctx->m = m;
   ctx->n = n;
   ctx->nnz = nnz;
@@ -1849,13 +1910,17 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
-    pdhg_status st = cuda_fail(nullptr, e, "device/stream setup");
+    const pdhg_status v = await_checks();
+    pdhg_status st = v != PDHG_OK ? fail(nullptr, v, checked.second) : cuda_fail(nullptr, e, "device/stream setup");
     pdhg_destroy(ctx);
     return st;
   }
-  pdhg_status st = setup(ctx, row_ptr, col_idx, val, b, c, x0, y0);
+  pdhg_status st = setup(ctx, row_ptr, col_idx, val, b, c, x0, y0, await_checks);
   if (st != PDHG_OK) {
-    g_create_error = ctx->err;
+    if (await_checks() != PDHG_OK)
+      st = fail(nullptr, checked.first, checked.second);
+    else
+      g_create_error = ctx->err;
     pdhg_destroy(ctx);
     return st;
   }
