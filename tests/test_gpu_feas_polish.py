@@ -145,3 +145,24 @@ def test_invalid_combinations(tiny_lp):
     with pytest.raises(P.PDHGError) as ei:
         P.BatchSolver([lp, lp], feas_polish=1)
     assert ei.value.status == P.PDHG_ERR_INVALID
+
+
+def test_gap_tolerance_in_single_block_loop_and_batch(tiny_lp):
+    """The termination test with gap_tol is shared by every engine: the
+    single-block solve loop and a batch stop where the oracle does."""
+    g, tol = 1e-4, 1e-8
+    orc, _ = _pair(tiny_lp, gap_tol=g)
+    assert orc.run(100000, tol)
+    with P.Solver.from_lp(tiny_lp, gap_tol=g, persistent=1) as s:
+        st, done = s.iterate(100000, tol)
+        assert st == P.PDHG_OK and done == orc.k
+    lp1 = lpgen.tiny_lp(1)
+    orc1, _ = _pair(lp1, gap_tol=g)
+    assert orc1.run(100000, tol)
+    with P.BatchSolver([tiny_lp, lp1], gap_tol=g) as bs:
+        st, _ = bs.iterate(100000, tol)
+        info = bs.info()
+    # reductions group differently in a batch, so a rounding-level near-tie
+    # may move a restart by an evaluation or two (as in the batch tests)
+    assert st == P.PDHG_OK and info["converged"].all()
+    assert abs(int(info["iterations"][0]) - orc.k) <= 2 * 64 and abs(int(info["iterations"][1]) - orc1.k) <= 2 * 64
