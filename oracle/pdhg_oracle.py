@@ -77,8 +77,8 @@ class Options:
       * ``ruiz_iters``/``pock_chambolle``: 10 Ruiz passes then one
         Pock-Chambolle pass with alpha = 1.
       * ``power_iters``: a fixed number of power iterations on Ahat^T Ahat,
-        started from the all-ones vector, so that every implementation computes
-        the same estimate.
+        started from a fixed pseudo-random vector (``power_start``), so that
+        every implementation computes the same estimate.
       * ``step_factor``: eta = step_factor / ||Ahat||_2.
       * ``restarts``/``primal_weight`` off gives plain fixed-step PDHG with
         omega = 1 (the tiny-LP configuration).
@@ -228,13 +228,40 @@ def scale_problem(A: sp.csr_matrix, b: np.ndarray, c: np.ndarray, opt: Options):
     return Ah, d_r * b, d_c * c, d_r, d_c
 
 
+_SM_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_SM_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_SM_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(counter: np.ndarray) -> np.ndarray:
+    """SplitMix64 (Steele, Lea and Flood 2014, with the finalizer constants of
+    Vigna's reference splitmix64.c) as a counter-based generator: the output
+    for state counter * 0x9E3779B97F4A7C15 (mod 2^64), i.e. the counter-th
+    output of the sequential generator seeded with 0."""
+    z = np.asarray(counter, dtype=np.uint64) * _SM_GAMMA
+    z = (z ^ (z >> np.uint64(30))) * _SM_M1
+    z = (z ^ (z >> np.uint64(27))) * _SM_M2
+    return z ^ (z >> np.uint64(31))
+
+
+def power_start(n: int) -> np.ndarray:
+    """Start vector of the power iteration: w_j = 0.5 + u_j, u_j in [0, 1) the
+    top 53 bits of splitmix64(j + 1) (j the column of A), normalized to unit
+    length. A fixed pseudo-random vector is orthogonal to the leading singular
+    vector of no matrix met in practice; the all-ones vector is orthogonal to it
+    whenever Ahat 1 = 0 (e.g. Ahat = [1, -1]), and the estimate is then 0."""
+    u = (splitmix64(np.arange(1, n + 1, dtype=np.uint64)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    w = 0.5 + u
+    return w / np.linalg.norm(w)
+
+
 def power_norm(Ah: sp.csr_matrix, iters: int) -> float:
-    """Estimate ||Ahat||_2 by ``iters`` power iterations on Ahat^T Ahat from the
-    all-ones vector: u = Ahat v, w = Ahat^T u, estimate = ||u||, v <- w/||w||."""
+    """Estimate ||Ahat||_2 by ``iters`` power iterations on Ahat^T Ahat from
+    ``power_start``: u = Ahat v, w = Ahat^T u, estimate = ||u||, v <- w/||w||."""
     n = Ah.shape[1]
     if n == 0 or Ah.nnz == 0:
         return 0.0
-    v = np.ones(n) / math.sqrt(n)
+    v = power_start(n)
     est = 0.0
     for _ in range(iters):
         u = Ah @ v

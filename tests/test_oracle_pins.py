@@ -170,6 +170,27 @@ def test_power_iteration_vs_svd(tiny_lp):
     assert est <= s_max * (1 + 1e-12) and est >= 0.95 * s_max  # Rayleigh quotient never overshoots
 
 
+def test_power_iteration_when_ahat_maps_ones_to_zero():
+    """Ahat = [1, -1] maps the all-ones vector to zero, so a power iteration
+    started there estimates 0; the estimate must be sqrt(2) (closed form)."""
+    Ah = sp.csr_matrix(np.array([[1.0, -1.0]]))
+    assert O.power_norm(Ah, 3) == pytest.approx(math.sqrt(2.0), rel=1e-15)
+    Ah = sp.csr_matrix(np.array([[1.0, -1.0, 0.0], [0.0, 1.0, -1.0], [-1.0, 0.0, 1.0]]))  # a cycle's incidence
+    assert O.power_norm(Ah, 200) == pytest.approx(math.sqrt(3.0), rel=1e-12)
+
+
+def test_power_start_is_the_published_splitmix64():
+    """The start vector's generator against the published SplitMix64 outputs
+    (tests/golden/splitmix64_seed0.json), and the vector's definition."""
+    with open(os.path.join(os.path.dirname(__file__), "golden", "splitmix64_seed0.json")) as f:
+        ref = [int(h, 16) for h in json.load(f)["outputs_hex"]]
+    got = O.splitmix64(np.arange(1, len(ref) + 1, dtype=np.uint64))
+    assert [int(v) for v in got] == ref
+    v = O.power_start(4)
+    w = 0.5 + np.array([r >> 11 for r in ref], dtype=np.float64) * 2.0 ** -53
+    np.testing.assert_allclose(v, w / np.linalg.norm(w), rtol=1e-15)
+
+
 def test_restart_rules_hand_cases():
     opt = O.Options()
     # sufficient decay (boundary inclusive)
