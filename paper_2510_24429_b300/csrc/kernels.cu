@@ -909,11 +909,27 @@ __global__ void k_div_by_norm_b(double* __restrict__ v, const double* __restrict
 }
 
 // v = 1 / sqrt(count of instance i) on instance i's range (power-iteration start)
-__global__ void k_fill_unit_b(double* __restrict__ v, const int* __restrict__ off) {
+// Start vector of the power iteration, before normalization: 0.5 + u with u
+// the top 53 bits of SplitMix64 (Steele, Lea and Flood 2014; finalizer
+// constants of Vigna's reference splitmix64.c) at counter j + 1, j the caller's
+// column (local to the instance). A fixed pseudo-random vector, since the
+// all-ones vector is mapped to zero by matrices such as [1, -1].
+__device__ __forceinline__ double power_start_value(unsigned long long j) {
+  unsigned long long z = (j + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return 0.5 + (double)(z >> 11) * 0x1.0p-53;
+}
+
+// instance blockIdx.y owns internal columns [off[i], off[i+1]) (off == nullptr:
+// one problem of n columns); perm_x maps internal to the caller's columns
+__global__ void k_power_start(double* __restrict__ v, const int* __restrict__ perm_x, const int* __restrict__ off,
+                              int n) {
   const int i = blockIdx.y;
-  const double val = 1.0 / sqrt((double)(off[i + 1] - off[i]));
-  for (int j = off[i] + blockIdx.x * blockDim.x + threadIdx.x; j < off[i + 1]; j += gridDim.x * blockDim.x)
-    v[j] = val;
+  const int a = off ? off[i] : 0, e = off ? off[i + 1] : n;
+  for (int j = a + blockIdx.x * blockDim.x + threadIdx.x; j < e; j += gridDim.x * blockDim.x)
+    v[j] = power_start_value((unsigned long long)(perm_x[j] - a));
 }
 
 __global__ void k_finish_setup_b(DevState* sts, int count, const double* __restrict__ scal, int sstride,
@@ -1298,8 +1314,8 @@ void launch_div_by_norm_b(double* v, const double* w, const double* s2, int sstr
                           int gx, cudaStream_t s) {
   k_div_by_norm_b<<<dim3(gx, count), TPB, 0, s>>>(v, w, s2, sstride, off);
 }
-void launch_fill_unit_b(double* v, const int* off, int count, int gx, cudaStream_t s) {
-  k_fill_unit_b<<<dim3(gx, count), TPB, 0, s>>>(v, off);
+void launch_power_start(double* v, const int* perm_x, const int* off, int count, int n, int gx, cudaStream_t s) {
+  k_power_start<<<dim3(gx, count), TPB, 0, s>>>(v, perm_x, off, n);
 }
 void launch_finish_setup_b(DevState* sts, int count, const double* scal, int sstride, double step_factor,
                            int primal_weight, cudaStream_t s) {

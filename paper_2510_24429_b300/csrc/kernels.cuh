@@ -152,7 +152,9 @@ void launch_apply_b(const DevState* sts, double* x, double* y, const double* xa,
 void launch_sumsq_b(const double* v, const int* off, int count, double* out, int ostride, cudaStream_t s);
 void launch_div_by_norm_b(double* v, const double* w, const double* s2, int sstride, const int* off, int count,
                           int gx, cudaStream_t s);
-void launch_fill_unit_b(double* v, const int* off, int count, int gx, cudaStream_t s);
+// start vector of the power iteration (unnormalized) for every instance
+// (off == nullptr: one problem of n columns, count 1)
+void launch_power_start(double* v, const int* perm_x, const int* off, int count, int n, int gx, cudaStream_t s);
 void launch_finish_setup_b(DevState* sts, int count, const double* scal, int sstride, double step_factor,
                            int primal_weight, cudaStream_t s);
 void launch_eval_finalize(const double* partials, int nb, EvalSums* out, cudaStream_t s);

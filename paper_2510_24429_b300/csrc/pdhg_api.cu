@@ -986,13 +986,15 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   launch_reciprocal(ctx->idc, ctx->dc, (int)n, gn, s);
   CK(ctx, cudaGetLastError());
 
-  // ---- device: power iteration for ||Ahat||_2 from the all-ones vector ----
+  // ---- device: power iteration for ||Ahat||_2 from a fixed pseudo-random vector ----
   double* v = ctx->tmp_n;
   double* w = ctx->tmp_n2;
   double* u = ctx->tmp_m;
   const int nbs = std::min(ctx->sms * 4, std::max(gn, gm));
-  launch_fill(v, 1.0 / sqrt((double)n), n, gn, s);
   launch_fill(ctx->scal, 0.0, 16, 1, s);
+  launch_power_start(w, ctx->perm_x, nullptr, 1, (int)n, gn, s);
+  launch_sumsq(w, (int)n, ctx->partials, nbs, ctx->scal + 6, s);
+  launch_div_by_norm(v, w, ctx->scal + 6, (int)n, gn, s);
   for (int it = 0; it < o.power_iters; ++it) {
     launch_spmv(A, v, u, grA, s);
     launch_sumsq(u, (int)m, ctx->partials, nbs, ctx->scal + 0, s);
@@ -1386,8 +1388,10 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
   double* v = ctx->tmp_n;
   double* w = ctx->tmp_n2;
   double* u = ctx->tmp_m;
-  launch_fill_unit_b(v, ctx->xoff, count, gx, s);
   launch_fill(ctx->scal, 0.0, (long long)8 * count, vec_grid(ctx, 8 * count), s);
+  launch_power_start(w, ctx->perm_x, ctx->xoff, count, (int)n, gx, s);
+  launch_sumsq_b(w, ctx->xoff, count, ctx->scal + 6, 8, s);
+  launch_div_by_norm_b(v, w, ctx->scal + 6, 8, ctx->xoff, count, gx, s);
   for (int it = 0; it < o.power_iters; ++it) {
     launch_spmv(A, v, u, grA, s);
     launch_sumsq_b(u, ctx->yoff, count, ctx->scal + 0, 8, s);
