@@ -212,7 +212,13 @@ template <class F>
 void parallel_for(int T, F fn) {
   std::vector<std::thread> th;
   th.reserve(T > 1 ? T - 1 : 0);
-  for (int t = 1; t < T; ++t) th.emplace_back(fn, t);
+  for (int t = 1; t < T; ++t) {
+    try {
+      th.emplace_back(fn, t);
+    } catch (...) {  // no thread to be had: do the share here
+      fn(t);
+    }
+  }
   fn(0);
   for (auto& x : th) x.join();
 }
@@ -1861,18 +1867,25 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
   // have passed. Their failure takes precedence over any later error, so a
   // malformed LP gets INVALID / NUMERIC whether or not a GPU is present.
   // Device inputs are checked on the device during setup.
+  auto run_checks = [=]() {
+    const char* msg = "";
+    pdhg_status st = check_lp(m, n, nnz, row_ptr, col_idx, val, b, c, &msg);
+    if (st == PDHG_OK && ((x0 && !all_finite(x0, n)) || (y0 && !all_finite(y0, m)))) {
+      st = PDHG_ERR_NUMERIC;
+      msg = "NaN or Inf in the input data";
+    }
+    return std::make_pair(st, msg);
+  };
   std::future<std::pair<pdhg_status, const char*>> checks;
-  if (!o.inputs_on_device)
-    checks = std::async(std::launch::async, [=]() {
-      const char* msg = "";
-      pdhg_status st = check_lp(m, n, nnz, row_ptr, col_idx, val, b, c, &msg);
-      if (st == PDHG_OK && ((x0 && !all_finite(x0, n)) || (y0 && !all_finite(y0, m)))) {
-        st = PDHG_ERR_NUMERIC;
-        msg = "NaN or Inf in the input data";
-      }
-      return std::make_pair(st, msg);
-    });
   std::pair<pdhg_status, const char*> checked{PDHG_OK, ""};
+  if (!o.inputs_on_device) {
+    try {
+      checks = std::async(std::launch::async, run_checks);
+    } catch (...) {  // no thread to be had: check here, before any device work
+      checked = run_checks();
+      if (checked.first != PDHG_OK) return fail(nullptr, checked.first, checked.second);
+    }
+  }
   std::function<pdhg_status()> await_checks = [&]() {
     if (checks.valid()) checked = checks.get();
     return checked.first;
