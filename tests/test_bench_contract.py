@@ -30,8 +30,8 @@ def test_peak_is_the_measured_copy_bandwidth():
 
 def test_traffic_record_matches_the_kernel_sources():
     """The record of the benchmarked half-steps was taken on these sources:
-    after a change to the step kernels, capture it again (the commands are in
-    profiles/steps_fp64_zipf_1e6x3e6.md)."""
+    after a change to the step kernels, capture it again (the command is in the
+    FP64 step-kernel summary under profiles/)."""
     workload = "zipf-lp m=1e6 n=3e6 nnz~3e7 FP64"
     for kernel in ("primal half-step (FP64)", "k_dual_step"):
         t = bench.profiled_traffic(kernel, workload)
