@@ -40,7 +40,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_struct_layouts_match_header(tmp_path):
     structs = {"pdhg_options": P.pdhg_options, "pdhg_kkt_info": P.pdhg_kkt_info, "pdhg_info": P.pdhg_info,
-               "pdhg_trace_rec": P.pdhg_trace_rec}
+               "pdhg_trace_rec": P.pdhg_trace_rec, "pdhg_polish_rec": P.pdhg_polish_rec,
+               "pdhg_lp_desc": P.pdhg_lp_desc}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdhg.h"', "int main(void) {"]
     for sname, cls in structs.items():
         lines.append(f'printf("{sname} size %zu\\n", sizeof({sname}));')
@@ -64,6 +65,8 @@ def test_default_options(lib):
     assert (o.ruiz_iters, o.pock_chambolle, o.power_iters, o.eval_every) == (10, 1, 100, 64)
     assert (o.step_factor, o.beta_suff, o.beta_nec, o.beta_art, o.theta) == (0.9, 0.2, 0.8, 0.36, 0.5)
     assert o.precision == P.PDHG_FP64 and o.restarts == 1 and o.primal_weight == 1
+    assert (o.halpern, o.halpern_reflect, o.primal_panels, o.long_row_min) == (0, 1.0, -1, 128)
+    assert (o.feas_polish, o.polish_div, o.gap_tol, o.polish_switch) == (0, 8, 0.0, 1e-5)
     with pytest.raises(KeyError):
         P.pdhg_default_options(no_such_option=1)
 
@@ -97,7 +100,8 @@ def test_bad_sizes_and_options(lib):
         P.pdhg_create(0, 3, np.array([0], np.int64), ci[:0], v[:0], b[:0], c)
     assert ei.value.status == P.PDHG_ERR_INVALID
     for bad in (dict(eval_every=0), dict(eps_factor=1.5), dict(pc_alpha=3.0), dict(power_iters=0),
-                dict(precision=7)):
+                dict(precision=7), dict(gap_tol=-1.0), dict(feas_polish=2), dict(polish_div=0),
+                dict(feas_polish=1, persistent=1), dict(halpern=1, halpern_reflect=1.5), dict(primal_panels=3)):
         with pytest.raises(P.PDHGError) as ei:
             P.pdhg_create(2, 3, rp, ci, v, b, c, opt=P.pdhg_default_options(**bad))
         assert ei.value.status == P.PDHG_ERR_INVALID, bad
