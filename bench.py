@@ -519,9 +519,9 @@ def run_ours(args):
     # A entries, xbar gathered once, y/b/ysum read + y/ysum written
     bytes_dual = (4 + w) * nnz + w * n + 5 * w * m
     peak, peak_kind = measured_peaks()
-    # the primal half-step of a large LP is three kernels, timed together: the
-    # direct step over the short columns, the panel pass and the per-column
-    # combine over the long ones
+    # the primal half-step of a large LP is two kernels, timed together: the
+    # panel pass over the long columns, then their per-column combine fused
+    # with the direct step over the short ones
     pname, dname = (("primal half-step (FP32)", "k_dual_step<float>") if args.precision == "fp32"
                     else ("primal half-step (FP64)", "k_dual_step"))
     if t_primal >= t_dual:

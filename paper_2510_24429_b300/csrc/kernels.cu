@@ -510,48 +510,6 @@ __global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
     unit_dot(Pn, vals, u, SmemGather<T>{ys}, op, pol, lane);
 }
 
-// one thread per column; the update's operands are loaded before the partial
-// sums so that their latencies overlap (same arithmetic as PrimalOp). The
-// partial sums are panel-major (panel p of column j at p * ncols + j, zero
-// where the column has no entry in the panel), so a warp's loads are
-// contiguous.
-// halpern_it >= 0: the reflected Halpern update with xsum as the anchor (the
-// Halpern form keeps its anchor where the sums would be; see PrimalHalpernOp)
-template <class T>
-__global__ void __launch_bounds__(TPB) k_primal_combine(int panels, const T* __restrict__ partial,
-                                                        const T* __restrict__ ch, T* __restrict__ x,
-                                                        T* __restrict__ xbar, T* __restrict__ xsum, int n,
-                                                        const DevState* __restrict__ st, int accumulate,
-                                                        int halpern_it) {
-  const T tau = (T)st->tau;
-  const bool halp = halpern_it >= 0;
-  const T w = halp ? (T)halpern_weight(st, halpern_it) : T(0), rho = (T)st->rho;
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
-    const T xj = __ldcs(x + j), cj = __ldcs(ch + j);
-    const T sj = (accumulate || halp) ? __ldcs(xsum + j) : T(0);
-    // added in panel order; eight loads in flight before their additions
-    const T* pj = partial + j;
-    T g = T(0);
-    int p = 0;
-    for (; p + 8 <= panels; p += 8) {
-      T a[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) a[e] = __ldcs(pj + (long long)(p + e) * n);
-#pragma unroll
-      for (int e = 0; e < 8; ++e) g += a[e];
-    }
-    for (; p < panels; ++p) g += __ldcs(pj + (long long)p * n);
-    const T xn = relu(xj - tau * (cj - g));
-    xbar[j] = T(2) * xn - xj;  // default policy: gathered by the dual step next
-    if (halp) {
-      __stcs(x + j, w * ((T(1) + rho) * xn - rho * xj) + (T(1) - w) * sj);
-    } else {
-      __stcs(x + j, xn);
-      if (accumulate) __stcs(xsum + j, sj + xn);
-    }
-  }
-}
-
 // ---- reflected Halpern form of the two half-steps (option halpern) ----------
 // With (x~, y~) the PDHG map's output, w = (t + 1) / (t + 2) (t = iterations
 // since the last restart, before this step) and the last restart point
@@ -589,6 +547,53 @@ struct DualHalpernOp {
   }
 };
 
+// ---- the short columns' direct step fused with the long columns' combine ---
+// Pass 2 of the panel-tiled primal half-step: blocks [0, cblocks) add each long
+// column's panel-major partial sums (panel p of column j at p * ncols + j,
+// zero where the column has no entry in the panel; added in panel order with
+// eight loads in flight) and apply the update through the same op as the
+// direct step; the other blocks run the direct step over the short columns
+// (the units of At from u_begin on). One launch instead of two, so the
+// combine's latency-bound work overlaps the direct step.
+template <class T, class Op>
+__device__ __forceinline__ void short_and_combine(const Hyb& At, const T* __restrict__ vals, const T* __restrict__ y,
+                                                  Op& op, int u_begin, int cblocks, int panels,
+                                                  const T* __restrict__ partial, int ncols) {
+  if ((int)blockIdx.x < cblocks) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ncols; j += cblocks * blockDim.x) {
+      const typename Op::State sj = op.begin(j);
+      const T* pj = partial + j;
+      T g = T(0);
+      int p = 0;
+      for (; p + 8 <= panels; p += 8) {
+        T a[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) a[e] = __ldcs(pj + (long long)(p + e) * ncols);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) g += a[e];
+      }
+      for (; p < panels; ++p) g += __ldcs(pj + (long long)p * ncols);
+      op.finish(j, g, sj);
+    }
+    return;
+  }
+  const unsigned long long pol = stream_policy();
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (int)(((blockIdx.x - cblocks) * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)(((gridDim.x - cblocks) * (unsigned)blockDim.x) >> 5);
+  for (int u = u_begin + gwarp; u < At.n_units; u += nwarps) unit_dot(At, vals, u, GlobalGather<T>{y}, op, pol, lane);
+}
+
+template <class T>
+__global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
+    k_primal_short_combine(Hyb At, const T* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
+                           T* __restrict__ x, T* __restrict__ xbar, T* __restrict__ xsum,
+                           const DevState* __restrict__ st, int accumulate, int u_begin, int cblocks, int panels,
+                           const T* __restrict__ partial, int ncols) {
+  PrimalOp<T> op{ch, x, xbar, xsum, (T)st->tau, accumulate};
+  short_and_combine(At, vals, y, op, u_begin, cblocks, panels, partial, ncols);
+}
+
 template <class T>
 __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
     k_primal_step_halpern(Hyb At, const T* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
@@ -598,6 +603,16 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STE
   if (st->frozen) return;
   PrimalHalpernOp<T> op{ch, x, xbar, xr, (T)st->tau, (T)halpern_weight(st, it), (T)st->rho};
   hyb_dot(At, vals, GlobalGather<T>{y}, op, u_begin);
+}
+
+template <class T>
+__global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
+    k_primal_short_combine_halpern(Hyb At, const T* __restrict__ vals, const T* __restrict__ y,
+                                   const T* __restrict__ ch, T* __restrict__ x, T* __restrict__ xbar,
+                                   const T* __restrict__ xr, const DevState* __restrict__ st, int it, int u_begin,
+                                   int cblocks, int panels, const T* __restrict__ partial, int ncols) {
+  PrimalHalpernOp<T> op{ch, x, xbar, xr, (T)st->tau, (T)halpern_weight(st, it), (T)st->rho};
+  short_and_combine(At, vals, y, op, u_begin, cblocks, panels, partial, ncols);
 }
 
 template <class T>
@@ -1232,23 +1247,35 @@ cudaError_t configure_primal_panels() {
   return e;
 }
 template <class T>
-cudaError_t launch_primal_panels(const Hyb& Pn, const T* vals, const PanelLayout& L, const T* y, const T* ch, T* x,
-                                 T* xbar, T* xsum, T* partial, const DevState* st, int accumulate, int n, int grid_n,
-                                 cudaStream_t s, int halpern_it) {
-  if (L.ncols == 0) return cudaSuccess;
+void launch_panel_pass(const Hyb& Pn, const T* vals, const PanelLayout& L, const T* y, T* partial, cudaStream_t s) {
+  if (L.ncols == 0) return;
   const size_t smem = sizeof(T) * (size_t)L.rows;
   k_primal_panels<T><<<L.blocks, PANEL_TPB, smem, s>>>(Pn, vals, y, L.m, L.rows, L.binfo, L.ustart, L.segout,
                                                         partial);
-  k_primal_combine<T><<<(L.ncols + TPB - 1) / TPB, TPB, 0, s>>>(L.panels, partial, ch, x, xbar, xsum, L.ncols, st,
-                                                                accumulate, halpern_it);
-  return cudaGetLastError();
 }
-template cudaError_t launch_primal_panels<double>(const Hyb&, const double*, const PanelLayout&, const double*,
-                                                  const double*, double*, double*, double*, double*,
-                                                  const DevState*, int, int, int, cudaStream_t, int);
-template cudaError_t launch_primal_panels<float>(const Hyb&, const float*, const PanelLayout&, const float*,
-                                                 const float*, float*, float*, float*, float*, const DevState*, int,
-                                                 int, int, cudaStream_t, int);
+template void launch_panel_pass<double>(const Hyb&, const double*, const PanelLayout&, const double*, double*,
+                                        cudaStream_t);
+template void launch_panel_pass<float>(const Hyb&, const float*, const PanelLayout&, const float*, float*,
+                                       cudaStream_t);
+template <class T>
+void launch_primal_short_combine(const Hyb& At, const T* vals, const T* y, const T* ch, T* x, T* xbar, T* xsum,
+                                 const DevState* st, int accumulate, int short_grid, const PanelLayout& L,
+                                 const T* partial, int tpb, cudaStream_t s, int halpern_it) {
+  const int cblocks = (L.ncols + tpb - 1) / tpb;
+  const int grid = cblocks + short_grid;
+  if (halpern_it >= 0)
+    k_primal_short_combine_halpern<T><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xsum, st, halpern_it, L.ncols,
+                                                             cblocks, L.panels, partial, L.ncols);
+  else
+    k_primal_short_combine<T><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xsum, st, accumulate, L.ncols, cblocks,
+                                                     L.panels, partial, L.ncols);
+}
+template void launch_primal_short_combine<double>(const Hyb&, const double*, const double*, const double*, double*,
+                                                  double*, double*, const DevState*, int, int, const PanelLayout&,
+                                                  const double*, int, cudaStream_t, int);
+template void launch_primal_short_combine<float>(const Hyb&, const float*, const float*, const float*, float*, float*,
+                                                 float*, const DevState*, int, int, const PanelLayout&, const float*,
+                                                 int, cudaStream_t, int);
 template <class T>
 void launch_primal_step_halpern(const Hyb& At, const T* vals, const T* y, const T* ch, T* x, T* xbar, const T* xr,
                                 const DevState* st, int it, int grid, cudaStream_t s, int tpb, const int* binst,
@@ -1390,6 +1417,10 @@ void prefer_l1_for_step_kernels() {
   cudaFuncSetAttribute(k_dual_step<double>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_primal_step<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_dual_step<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_primal_short_combine<double>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_primal_short_combine<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_primal_short_combine_halpern<double>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_primal_short_combine_halpern<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_dual_step_hot, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(HOT_MAX * sizeof(double)));
 }

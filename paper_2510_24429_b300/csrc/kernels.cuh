@@ -115,12 +115,17 @@ struct PanelLayout {
 };
 // allow the panel kernels their shared memory (once per device, outside graph capture)
 cudaError_t configure_primal_panels();
-// both passes (grid_n: grid of the per-column pass); halpern_it >= 0: the
-// reflected Halpern update of step halpern_it with xsum as the anchor
+// pass 1: per-(column, panel) partial sums of the long columns
 template <class T>
-cudaError_t launch_primal_panels(const Hyb& Pn, const T* vals, const PanelLayout& L, const T* y, const T* ch, T* x,
-                                 T* xbar, T* xsum, T* partial, const DevState* st, int accumulate, int n, int grid_n,
-                                 cudaStream_t s, int halpern_it = -1);
+void launch_panel_pass(const Hyb& Pn, const T* vals, const PanelLayout& L, const T* y, T* partial, cudaStream_t s);
+// pass 2 fused with the short columns' direct step (short_grid: blocks of tpb
+// threads for the units of At from L.ncols on): the long columns' sums and
+// update, and the direct step; halpern_it >= 0: the reflected Halpern update
+// of step halpern_it with xsum as the anchor
+template <class T>
+void launch_primal_short_combine(const Hyb& At, const T* vals, const T* y, const T* ch, T* x, T* xbar, T* xsum,
+                                 const DevState* st, int accumulate, int short_grid, const PanelLayout& L,
+                                 const T* partial, int tpb, cudaStream_t s, int halpern_it = -1);
 // the same step, persistent (grid = number of SMs), with xbar[0, hot) staged
 // in shared memory; hot <= HOT_MAX
 void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,

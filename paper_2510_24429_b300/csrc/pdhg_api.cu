@@ -1100,33 +1100,35 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
 
 // ---- one evaluation block -------------------------------------------------------
 
+// The panel-tiled primal half-step of precision T: the panel pass over the
+// long columns, then one launch that adds their partial sums and applies the
+// update (plain, or the reflected Halpern one of step halpern_it with xsum as
+// the anchor) beside the direct step over the short columns.
+template <class T>
+pdhg_status panel_half_step(pdhg_ctx* ctx, const T* vals, const T* valsT, const T* y, const T* ch, T* x, T* xbar,
+                            T* xsum, T* partial, int accumulate, int tpb, int halpern_it) {
+  cudaStream_t s = ctx->stream;
+  launch_panel_pass<T>(ctx->Pn, vals, ctx->pl, y, partial, s);
+  launch_primal_short_combine<T>(ctx->At, valsT, y, ch, x, xbar, xsum, ctx->st, accumulate, short_grid(ctx), ctx->pl,
+                                 partial, tpb, s, halpern_it);
+  CK(ctx, cudaGetLastError());
+  ctx->launches += 1;  // two launches; the caller counts one primal step
+  return PDHG_OK;
+}
+
 // The primal half-step on (y, x, xbar, xsum) in FP32 or FP64: when the panel
-// layout exists, the direct step over the short columns plus the panel pass
-// and per-column combine over the long ones (three kernels); else the direct
+// layout exists, the panel pass over the long columns and the combine fused
+// with the direct step over the short ones (two kernels); else the direct
 // step over every column.
 pdhg_status primal_step(pdhg_ctx* ctx, bool f32, const void* y, void* x, void* xbar, void* xsum, int accumulate,
                         int grT, int tpb) {
   cudaStream_t s = ctx->stream;
   if (ctx->panels_on) {
-    // short columns: the direct step over the units after the long rows; long
-    // columns: panel pass + per-column combine
-    const int gs = short_grid(ctx);
     if (f32)
-      launch_primal_step32(ctx->At, (const float*)y, ctx->ch32, (float*)x, (float*)xbar, (float*)xsum, ctx->st,
-                           accumulate, gs, s, tpb, ctx->pl.ncols);
-    else
-      launch_primal_step(ctx->At, (const double*)y, ctx->ch, (double*)x, (double*)xbar, (double*)xsum, ctx->st,
-                         accumulate, gs, s, nullptr, tpb, ctx->pl.ncols);
-    const int gn = vec_grid(ctx, ctx->pl.ncols);
-    cudaError_t e =
-        f32 ? launch_primal_panels<float>(ctx->Pn, ctx->Pn.v32, ctx->pl, (const float*)y, ctx->ch32, (float*)x,
-                                          (float*)xbar, (float*)xsum, ctx->pn_partial32, ctx->st, accumulate,
-                                          ctx->pl.ncols, gn, s)
-            : launch_primal_panels<double>(ctx->Pn, ctx->Pn.v, ctx->pl, (const double*)y, ctx->ch, (double*)x,
-                                           (double*)xbar, (double*)xsum, ctx->pn_partial, ctx->st, accumulate,
-                                           ctx->pl.ncols, gn, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "panel-tiled primal step");
-    ctx->launches += 2;  // the panel pass and the combine
+      return panel_half_step<float>(ctx, ctx->Pn.v32, ctx->At.v32, (const float*)y, ctx->ch32, (float*)x,
+                                    (float*)xbar, (float*)xsum, ctx->pn_partial32, accumulate, tpb, -1);
+    return panel_half_step<double>(ctx, ctx->Pn.v, ctx->At.v, (const double*)y, ctx->ch, (double*)x, (double*)xbar,
+                                   (double*)xsum, ctx->pn_partial, accumulate, tpb, -1);
   } else if (f32) {
     launch_primal_step32(ctx->At, (const float*)y, ctx->ch32, (float*)x, (float*)xbar, (float*)xsum, ctx->st,
                          accumulate, grT, s, tpb);
@@ -1152,13 +1154,9 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
     if (o.halpern && !ctx->phase32) {
       if (ctx->panels_on) {  // the anchor (last restart point) in place of the sums
-        launch_primal_step_halpern<double>(ctx->At, ctx->At.v, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xr,
-                                           ctx->st, (int)it, short_grid(ctx), s, tpb, nullptr, ctx->pl.ncols);
-        cudaError_t e = launch_primal_panels<double>(ctx->Pn, ctx->Pn.v, ctx->pl, ctx->y, ctx->ch, ctx->x,
-                                                     ctx->xbar, ctx->xr, ctx->pn_partial, ctx->st, 0,
-                                                     ctx->pl.ncols, vec_grid(ctx, ctx->pl.ncols), s, (int)it);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "panel-tiled primal step");
-        ctx->launches += 2;
+        pdhg_status rs = panel_half_step<double>(ctx, ctx->Pn.v, ctx->At.v, ctx->y, ctx->ch, ctx->x, ctx->xbar,
+                                                 ctx->xr, ctx->pn_partial, 0, tpb, (int)it);
+        if (rs != PDHG_OK) return rs;
       } else {
         launch_primal_step_halpern<double>(ctx->At, ctx->At.v, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xr, ctx->st,
                                            (int)it, grT, s, tpb);
@@ -1166,14 +1164,9 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
     } else if (o.halpern) {
       // FP32 Halpern: the FP32 sums hold the FP32 anchor (no averages in this form)
       if (ctx->panels_on) {
-        launch_primal_step_halpern<float>(ctx->At, ctx->At.v32, ctx->y32, ctx->ch32, ctx->x32, ctx->xbar32,
-                                          ctx->xsum32, ctx->st, (int)it, short_grid(ctx), s, tpb, nullptr,
-                                          ctx->pl.ncols);
-        cudaError_t e = launch_primal_panels<float>(ctx->Pn, ctx->Pn.v32, ctx->pl, ctx->y32, ctx->ch32, ctx->x32,
-                                                    ctx->xbar32, ctx->xsum32, ctx->pn_partial32, ctx->st, 0,
-                                                    ctx->pl.ncols, vec_grid(ctx, ctx->pl.ncols), s, (int)it);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "panel-tiled primal step");
-        ctx->launches += 2;
+        pdhg_status rs = panel_half_step<float>(ctx, ctx->Pn.v32, ctx->At.v32, ctx->y32, ctx->ch32, ctx->x32,
+                                                ctx->xbar32, ctx->xsum32, ctx->pn_partial32, 0, tpb, (int)it);
+        if (rs != PDHG_OK) return rs;
       } else {
         launch_primal_step_halpern<float>(ctx->At, ctx->At.v32, ctx->y32, ctx->ch32, ctx->x32, ctx->xbar32,
                                           ctx->xsum32, ctx->st, (int)it, grT, s, tpb);
