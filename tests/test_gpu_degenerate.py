@@ -76,3 +76,19 @@ def test_degenerate_optima_converge_like_the_oracle(make):
         assert k["rel_kkt"] <= 1e-9
         if make is D.zero_rhs_tiny:
             assert np.linalg.norm(sol.solution()[0]) <= 1e-8
+
+
+@pytest.mark.parametrize("engine", [dict(), dict(use_graphs=0), dict(persistent=1)], ids=["graphs", "direct", "loop"])
+def test_overflow_in_the_iterates_is_reported(tiny_lp, engine):
+    """Failure detection without a GPU fault: a finite warm start of 1.7e308
+    overflows when it is scaled (x / D_c with D_c entries below 1) and in the
+    extrapolation 2x' - x, and the evaluation that follows reports
+    PDHG_ERR_NUMERIC; the context still answers queries afterwards."""
+    lp = tiny_lp
+    x0 = np.full(lp.n, 1.7e308)
+    with P.Solver.from_lp(lp, x0=x0, **engine) as s:
+        with pytest.raises(P.PDHGError) as ei:
+            s.iterate(640, 1e-8)
+        assert ei.value.status == P.PDHG_ERR_NUMERIC
+        info = s.info()
+        assert info["iterations"] <= 640
