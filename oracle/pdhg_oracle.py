@@ -206,13 +206,20 @@ def ruiz_scaling(A: sp.csr_matrix, iters: int):
     return sp.csr_matrix(Ah), d_r, d_c
 
 
+def _abs_power(A: sp.csr_matrix, p: float) -> sp.csr_matrix:
+    """|A_ij|^p on the stored entries, with 0^p = 0 also for p = 0 (a stored
+    zero counts as absent)."""
+    B = abs(A).tocsr(copy=True)
+    B.data = np.where(B.data > 0, B.data ** p, 0.0)
+    return B
+
+
 def pock_chambolle_scaling(A: sp.csr_matrix, alpha: float = 1.0):
-    """Pock-Chambolle diagonal preconditioning with parameter alpha:
+    """Pock-Chambolle diagonal preconditioning with parameter alpha in [0, 2]:
     r_i = 1/sqrt(sum_j |A_ij|^alpha), s_j = 1/sqrt(sum_i |A_ij|^(2 - alpha)).
     Returns (Ahat, r, s)."""
-    absA = abs(A)
-    row_sum = np.asarray(absA.power(alpha).sum(axis=1)).ravel()
-    col_sum = np.asarray(absA.power(2.0 - alpha).sum(axis=0)).ravel()
+    row_sum = np.asarray(_abs_power(A, alpha).sum(axis=1)).ravel()
+    col_sum = np.asarray(_abs_power(A, 2.0 - alpha).sum(axis=0)).ravel()
     r = _inv_sqrt_or_one(row_sum)
     s = _inv_sqrt_or_one(col_sum)
     return sp.csr_matrix(sp.diags(r) @ A @ sp.diags(s)), r, s

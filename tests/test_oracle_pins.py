@@ -161,6 +161,19 @@ def test_pock_chambolle_norm_bound(tiny_lp):
     assert np.linalg.norm(Jh.toarray(), 2) == pytest.approx(1.0, rel=1e-14)
 
 
+def test_pock_chambolle_other_alphas():
+    """Closed forms on A = [[2, 0], [1, 3]]: alpha = 0 gives row factors
+    1/sqrt(#entries) and column factors 1/sqrt(sum a^2); alpha = 2 the other
+    way round."""
+    A = sp.csr_matrix(np.array([[2.0, 0.0], [1.0, 3.0]]))
+    _, r, s = O.pock_chambolle_scaling(A, 0.0)
+    np.testing.assert_allclose(r, [1.0, 1 / math.sqrt(2.0)], rtol=1e-15)
+    np.testing.assert_allclose(s, [1 / math.sqrt(5.0), 1 / 3.0], rtol=1e-15)
+    _, r, s = O.pock_chambolle_scaling(A, 2.0)
+    np.testing.assert_allclose(r, [1 / 2.0, 1 / math.sqrt(10.0)], rtol=1e-15)
+    np.testing.assert_allclose(s, [1 / math.sqrt(2.0), 1.0], rtol=1e-15)
+
+
 def test_power_iteration_vs_svd(tiny_lp):
     A = O.csr_matrix(tiny_lp.m, tiny_lp.n, tiny_lp.row_ptr, tiny_lp.col_idx, tiny_lp.val)
     Ah, _, _ = O.ruiz_scaling(A, 10)
@@ -193,13 +206,15 @@ def test_power_start_is_the_published_splitmix64():
 
 def test_restart_rules_hand_cases():
     opt = O.Options()
-    # sufficient decay (boundary inclusive)
+    # sufficient decay (boundary inclusive; no progress test involved: 0.2 < 0.3)
     assert O.restart_decision(0.2, 1.0, 0.1, 1, 100, opt)
+    assert O.restart_decision(0.2, 1.0, 0.3, 1, 100, opt)
     assert O.restart_decision(0.1, 1.0, 0.05, 1, 100, opt)
     # necessary decay and no progress since the previous evaluation
     assert O.restart_decision(0.5, 1.0, 0.4, 1, 100, opt)
-    # necessary decay but still progressing -> no restart
+    # necessary decay but still progressing -> no restart (equal counts as progressing)
     assert not O.restart_decision(0.5, 1.0, 0.6, 1, 100, opt)
+    assert not O.restart_decision(0.5, 1.0, 0.5, 1, 100, opt)
     # no decay at all
     assert not O.restart_decision(0.9, 1.0, 0.5, 1, 100, opt)
     # artificial: t >= 0.36 k (boundary inclusive)
@@ -210,10 +225,13 @@ def test_restart_rules_hand_cases():
     assert O.choose_candidate((1, 1, 1), (1, 1, 0.5), 2.0) == O.RESTART_TO_AVERAGE
     assert O.weighted_kkt((3.0, 4.0, 0.0), 1.0) == 5.0
     assert O.weighted_kkt((1.0, 1.0, 1.0), 4.0) == pytest.approx(math.sqrt(5.25), rel=1e-16)
+    assert O.weighted_kkt((3.0, 4.0, 0.0), 4.0) == pytest.approx(math.sqrt(40.0), rel=1e-16)  # 4*9 + 16/4
     # primal weight: geometric smoothing of dy/dx
     assert O.primal_weight_update(1.0, 1.0, 4.0, 0.5) == pytest.approx(2.0, rel=1e-15)
     assert O.primal_weight_update(4.0, 1.0, 4.0, 0.5) == pytest.approx(4.0, rel=1e-15)
     assert O.primal_weight_update(3.0, 1e-11, 4.0, 0.5) == 3.0
+    # theta weighs the new ratio: exp(0.25 ln 4 + 0.75 ln 1) = sqrt(2)
+    assert O.primal_weight_update(1.0, 1.0, 4.0, 0.25) == pytest.approx(math.sqrt(2.0), rel=1e-15)
 
 
 def test_average_is_mean_of_iterates_since_restart(tiny_lp):
