@@ -309,3 +309,16 @@ def test_cuda_graph_replay_equals_direct_launches(tiny_lp):
     for s0, s1 in zip(sols[0][0], sols[1][0]):
         for a, b in zip(s0, s1):
             np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.5, 2.0])
+def test_pock_chambolle_alphas_match_oracle(tiny_lp, alpha):
+    """Pock-Chambolle with alpha != 1 (the default): setup and 100 plain
+    iterations against the oracle."""
+    orc, sol = pair(tiny_lp, pc_alpha=alpha, restarts=False, primal_weight=False)
+    info = sol.info()
+    assert info["norm_estimate"] == pytest.approx(orc.norm_est, rel=1e-12)
+    orc.run(100)
+    sol.iterate(100)
+    assert_iterates_close(sol, orc, 1e-10)
+    sol.close()
