@@ -531,14 +531,13 @@ class Oracle:
         return converged
 
     # -- feasibility polishing ---------------------------------------------
-    def feasibility_phase(self, xh0, yh0, kind: str, tol: float, budget: int):
-        """PDHG on the problem with the objective (kind "primal") or the
-        right-hand side (kind "dual") set to zero, from the scaled point
-        (xh0, yh0), with this solver's scaling, eta and current primal weight,
-        fresh averages and restart reference, and the same restart rules; it
-        stops at the first evaluation where rel_p (primal) or rel_d (dual) of
-        its candidate is <= tol, or after ``budget`` iterations. Returns
-        (xhat, yhat, iterations, reached)."""
+    def phase_solver(self, xh0, yh0, kind: str) -> "Oracle":
+        """The solver of one polishing phase, before its first iteration: PDHG
+        on the problem with the objective (kind "primal") or the right-hand
+        side (kind "dual") set to zero, from the scaled point (xh0, yh0), with
+        this solver's scaling, eta and current primal weight, empty averages,
+        the start as its restart reference, the same restart rules, and rel_p
+        (primal) or rel_d (dual) of its candidate as the termination measure."""
         sub = Oracle.__new__(Oracle)
         sub.__dict__.update(self.__dict__)
         sub.opt = dataclasses.replace(self.opt, eps_cross=0.0, snapshot_every=0, feas_polish=False)
@@ -560,6 +559,13 @@ class Oracle:
         sub.x_r, sub.y_r = sub.x.copy(), sub.y.copy()
         sub.n_restart = sub.scaled_norms(sub.x, sub.y)
         sub.n_prev = sub.n_restart
+        return sub
+
+    def feasibility_phase(self, xh0, yh0, kind: str, tol: float, budget: int):
+        """One polishing phase (see ``phase_solver``): it stops at the first
+        evaluation where its termination measure is <= tol, or after
+        ``budget`` iterations. Returns (xhat, yhat, iterations, reached)."""
+        sub = self.phase_solver(xh0, yh0, kind)
         reached = sub.run(budget, tol)
         return sub.x, sub.y, sub.k, reached
 

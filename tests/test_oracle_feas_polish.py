@@ -139,3 +139,21 @@ def test_gap_tolerance_equal_to_tol_is_the_single_eps_test(tiny_lp):
         last = o.trace[-1]
         assert last.rel_kkt <= 1e-7 and all(r.rel_kkt > 1e-7 for r in o.trace[:-1])
     assert runs[0][0] == runs[1][0] and np.array_equal(runs[0][1], runs[1][1])
+
+
+def test_phase_stops_on_its_own_measure_and_starts_its_own_restart_reference(tiny_lp):
+    """At (x*, y*) the primal phase's problem (c = 0) is primal feasible
+    (rel_p = 0) but not dual optimal (A^T y* != 0), and the dual phase's
+    problem (b = 0) dual feasible but not primal (A x* != 0): each phase must
+    stop there, on rel_p resp. rel_d alone. Each phase's first restart
+    reference is its own start, not the main solver's."""
+    lp = tiny_lp
+    o = O.Oracle(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, O.Options())
+    xs, ys = lp.x_star / o.d_c, lp.y_star / o.d_r
+    for kind in ("primal", "dual"):
+        sub = o.phase_solver(xs, ys, kind)
+        full = sub.kkt_of(sub.x, sub.y)
+        assert full["rel_kkt"] > 1e-3 and full["rel_p" if kind == "primal" else "rel_d"] <= 1e-12
+        assert sub.evaluate(1e-8)
+        start = o.phase_solver(xs, np.zeros(lp.m), kind)
+        assert start.n_restart == start.scaled_norms(xs, np.zeros(lp.m)) != o.n_restart

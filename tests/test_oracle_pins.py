@@ -29,10 +29,27 @@ def test_kkt_hand_computed_2x3():
     g = _golden_2x3()
     A = sp.csr_matrix(np.array(g["A"], dtype=float))
     b, c = np.array(g["b"], float), np.array(g["c"], float)
-    p = g["kkt_point"]
-    info = O.kkt(A, b, c, np.array(p["x"], float), np.array(p["y"], float))
-    for key, expr in p["expect"].items():
-        assert info[key] == pytest.approx(_expr(expr), rel=1e-15, abs=1e-15), key
+    for point in ("kkt_point", "kkt_point_negative_residual"):
+        p = g[point]
+        info = O.kkt(A, b, c, np.array(p["x"], float), np.array(p["y"], float))
+        for key, expr in p["expect"].items():
+            assert info[key] == pytest.approx(_expr(expr), rel=1e-15, abs=1e-15), (point, key)
+
+
+def test_scaled_measures_of_the_restart_rules_2x3():
+    """Without scaling (no Ruiz or Pock-Chambolle passes) the restart rules'
+    measures (||r_P||, ||r_D||, |c^T x - b^T y|) equal the hand-computed
+    unscaled ones."""
+    g = _golden_2x3()
+    A = sp.csr_matrix(np.array(g["A"], dtype=float))
+    b, c = np.array(g["b"], float), np.array(g["c"], float)
+    o = O.Oracle(2, 3, A.indptr, A.indices, A.data, b, c, O.Options(ruiz_iters=0, pock_chambolle=False))
+    for point in ("kkt_point", "kkt_point_negative_residual"):
+        p = g[point]
+        e = p["expect"]
+        got = o.scaled_norms(np.array(p["x"], float), np.array(p["y"], float))
+        want = (_expr(e["rp_norm2"]), _expr(e["rd_norm2"]), _expr(e["gap"]))
+        assert got == pytest.approx(want, rel=1e-15, abs=1e-15), point
 
 
 def test_step_hand_computed_2x3():
