@@ -9,16 +9,20 @@ from oracle import pdhg_oracle as O
 from paper_2510_24429_b300 import lpgen
 
 
-def _setup(K=60, seed=0):
+def _setup(K=60, seed=0, primal_weight=False):
     lp = lpgen.tiny_lp(seed)
     orc = O.Oracle(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c,
-                   O.Options(restarts=False, primal_weight=False))
+                   O.Options(restarts=False, primal_weight=primal_weight))
     xt = lpgen.x_target(lp, seed=7)
     return lp, orc, xt, K
 
 
-def test_adjoint_matches_central_differences():
-    lp, orc, xt, K = _setup()
+@pytest.mark.parametrize("primal_weight", [False, True])
+def test_adjoint_matches_central_differences(primal_weight):
+    """primal_weight=True keeps omega at omega0 != 1 (no restarts, so no
+    updates), so tau != sigma and a swapped step size fails."""
+    lp, orc, xt, K = _setup(primal_weight=primal_weight)
+    assert primal_weight == (abs(orc.tau - orc.sigma) > 1e-3 * orc.tau)
     xs, _ = O.unrolled_forward(orc, K)
     gxK = orc.d_c * xs[-1] - xt
     gc, gb = O.unrolled_adjoint(orc, K, gxK)
