@@ -125,6 +125,25 @@ def test_attempt_schedule_follows_its_rules():
         assert r["primal_iters"] <= budget and r["dual_iters"] <= budget
         assert r["primal_iters"] % 64 == 0 and r["dual_iters"] % 64 == 0
     assert o.polish_log[0]["budget"] == 64 * math.ceil(o.polish_log[0]["iteration"] / 512)
+    # the dual phase runs only after a successful primal phase
+    assert all(r["dual_iters"] == 0 for r in o.polish_log if not r["primal_ok"])
+
+
+def test_a_pair_with_a_large_gap_does_not_end_the_solve():
+    """On the Zipf-shaped LP the attempt at 6400 iterations reaches both
+    feasibility targets but its pair's relative gap is above gap_tol: the
+    solve goes on; every accepted pair has rel_gap <= gap_tol."""
+    lp = lpgen.generate(20000, 60000, 0, nnz_per_col=None, zipf=(1.5, 10000, 600000), val_range=(0.1, 10.0),
+                        support=0.3)
+    tol, gtol = 1e-6, 1e-4
+    o = O.Oracle(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c,
+                 O.Options(feas_polish=True, gap_tol=gtol))
+    o.run(6464, tol)
+    both = [r for r in o.polish_log if r["primal_ok"] and r["dual_ok"]]
+    assert any(r["rel_gap"] > gtol for r in both)
+    for r in both:
+        ended_here = o.done and o.k == r["iteration"]
+        assert ended_here == (r["rel_gap"] <= gtol)
 
 
 def test_gap_tolerance_equal_to_tol_is_the_single_eps_test(tiny_lp):

@@ -36,6 +36,32 @@ def test_kkt_hand_computed_2x3():
             assert info[key] == pytest.approx(_expr(expr), rel=1e-15, abs=1e-15), (point, key)
 
 
+def test_kkt_with_a_given_z_2x3():
+    """With z given (here 0) the dual residual A^T y + z - c can be negative:
+    its infinity norm is the largest magnitude."""
+    g = _golden_2x3()
+    A = sp.csr_matrix(np.array(g["A"], dtype=float))
+    b, c = np.array(g["b"], float), np.array(g["c"], float)
+    p = g["kkt_point_given_z"]
+    info = O.kkt(A, b, c, np.array(p["x"], float), np.array(p["y"], float), np.array(p["z"], float))
+    for key, expr in p["expect"].items():
+        assert info[key] == pytest.approx(_expr(expr), rel=1e-15, abs=1e-15), key
+
+
+def test_power_iteration_two_steps_closed_form():
+    """On diag(2, 1) from the start w = 0.5 + u (u from the first two
+    SplitMix64 outputs, tests/golden/splitmix64_seed0.json): the second
+    estimate is ||A v1|| with v1 along A^T A w = (4 w1, w2), i.e.
+    sqrt(64 w1^2 + w2^2) / sqrt(16 w1^2 + w2^2)."""
+    with open(os.path.join(os.path.dirname(__file__), "golden", "splitmix64_seed0.json")) as f:
+        ref = [int(h, 16) for h in json.load(f)["outputs_hex"]]
+    w1, w2 = (0.5 + (r >> 11) * 2.0 ** -53 for r in ref[:2])
+    Ah = sp.csr_matrix(np.diag([2.0, 1.0]))
+    assert O.power_norm(Ah, 1) == pytest.approx(math.sqrt(4 * w1 * w1 + w2 * w2) / math.hypot(w1, w2), rel=1e-15)
+    assert O.power_norm(Ah, 2) == pytest.approx(math.sqrt(64 * w1 * w1 + w2 * w2) / math.hypot(4 * w1, w2),
+                                                rel=1e-15)
+
+
 def test_scaled_measures_of_the_restart_rules_2x3():
     """Without scaling (no Ruiz or Pock-Chambolle passes) the restart rules'
     measures (||r_P||, ||r_D||, |c^T x - b^T y|) equal the hand-computed

@@ -82,3 +82,20 @@ def test_algorithm1_target_is_inclusive_and_needs_no_tolerance():
     plain = _oracle(lp, restarts=False, primal_weight=False, eps_cross=1.0)
     plain.run(128)
     assert len(plain.snapshots) >= 1
+
+
+def test_decision_margin_sees_the_sufficient_decay_boundary():
+    """The margin recorded with each evaluation (how close any of its
+    comparisons came to a tie) is ~0 when the candidate's weighted error sits
+    exactly on the sufficient-decay boundary (reference = 5 x candidate)."""
+    lp = lpgen.tiny_lp(0)
+    o = _oracle(lp)
+    o.run(63)
+    o.iterate_once()  # k = 64, before its evaluation
+    n_cur = o.scaled_norms(o.x, o.y)
+    n_avg = o.scaled_norms(o.x_avg, o.y_avg)
+    cand = n_avg if O.choose_candidate(n_cur, n_avg, o.omega) == O.RESTART_TO_AVERAGE else n_cur
+    o.n_restart = tuple(5.0 * v for v in cand)
+    o.n_prev = tuple(10.0 * v for v in cand)
+    o.evaluate(0.0)
+    assert o.trace[-1].margin <= 1e-14
