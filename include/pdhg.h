@@ -262,8 +262,11 @@ PDHG_API pdhg_status pdhg_get_info(pdhg_ctx* ctx, pdhg_info* out);
  * number stored (at most 65536 are kept). */
 PDHG_API pdhg_status pdhg_get_trace(pdhg_ctx* ctx, pdhg_trace_rec* recs, int64_t cap, int64_t* count);
 
-/* Copy up to cap feasibility polishing records (oldest first) into recs;
- * *count gets the number of attempts so far. */
+/* Feasibility polishing (the PDLP variant Section 5 describes; see the
+ * feas_polish option): copy up to cap attempt records, oldest first, into the
+ * caller-owned host array recs (NULL allowed when cap = 0); *count (nullable)
+ * gets the number of attempts so far. INVALID if cap < 0, or recs is NULL with
+ * cap > 0. Host-only, no device work. */
 PDHG_API pdhg_status pdhg_get_polish_log(pdhg_ctx* ctx, pdhg_polish_rec* recs, int64_t cap, int64_t* count);
 
 /* KKT measures (as pdhg_kkt) of a point (x, y), z = max(0, c - A^T y), of an LP
