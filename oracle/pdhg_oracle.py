@@ -171,11 +171,6 @@ def kkt(A: sp.csr_matrix, b: np.ndarray, c: np.ndarray, x: np.ndarray, y: np.nda
     return out
 
 
-def satisfies_termination(info: dict, eps: float) -> bool:
-    """The three inequalities of the PDHG termination test (Section 2)."""
-    return info["rel_p"] <= eps and info["rel_d"] <= eps and info["rel_gap"] <= eps
-
-
 # ---------------------------------------------------------------------------
 # Diagonal scaling (PDLP preprocessing; the paper is silent on its details)
 # ---------------------------------------------------------------------------
