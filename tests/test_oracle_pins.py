@@ -29,7 +29,7 @@ def test_kkt_hand_computed_2x3():
     g = _golden_2x3()
     A = sp.csr_matrix(np.array(g["A"], dtype=float))
     b, c = np.array(g["b"], float), np.array(g["c"], float)
-    for point in ("kkt_point", "kkt_point_negative_residual"):
+    for point in ("kkt_point", "kkt_point_negative_residual", "kkt_point_negative_x"):
         p = g[point]
         info = O.kkt(A, b, c, np.array(p["x"], float), np.array(p["y"], float))
         for key, expr in p["expect"].items():

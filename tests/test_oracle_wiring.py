@@ -84,6 +84,11 @@ def test_algorithm1_target_is_inclusive_and_needs_no_tolerance():
     assert len(plain.snapshots) >= 1
 
 
+def test_relative_difference_of_the_margin():
+    """The margin's relative difference |a - b| / max(|a|, |b|), 0 for a = b = 0."""
+    assert O._rel_gap(1.0, 2.0) == 0.5 and O._rel_gap(-3.0, 1.0) == pytest.approx(4.0 / 3.0) and O._rel_gap(0.0, 0.0) == 0.0
+
+
 def test_decision_margin_sees_the_sufficient_decay_boundary():
     """The margin recorded with each evaluation (how close any of its
     comparisons came to a tie) is ~0 when the candidate's weighted error sits
