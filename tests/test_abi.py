@@ -94,6 +94,30 @@ def test_invalid_input_rejected_before_device_work(lib, mutate, status):
     assert P.pdhg_last_error(None)
 
 
+def test_each_host_check_on_its_own(lib):
+    """Each check of pdhg_create's host inputs, with the others passing."""
+    # A = [[1, 2, 0], [0, 0, 0], [0, 1, 1]]-shaped data for a 3x3 LP
+    ci, v = np.array([0, 1, 1, 2], np.int32), np.array([1.0, 2.0, 1.0, 1.0])
+    b, c = np.array([3.0, 0.0, 2.0]), np.array([1.0, 1.0, 1.0])
+    cases = [
+        # row 1 ends before it starts; rows 0 and 2 are well formed on their own
+        (np.array([0, 2, 1, 3], np.int64), np.array([0, 1, 2], np.int32), v[:3], b, c, None,
+         P.PDHG_ERR_INVALID, "non-decreasing"),
+        (np.array([0, 2, 2, 3], np.int64), ci, v, b, c, None, P.PDHG_ERR_INVALID, "row_ptr[m]"),
+        (np.array([0, 2, 2, 4], np.int64), np.array([0, 1, -1, 2], np.int32), v, b, c, None,
+         P.PDHG_ERR_INVALID, "out of range"),
+        (np.array([0, 2, 2, 4], np.int64), ci, v, np.array([3.0, np.nan, 2.0]), c, None,
+         P.PDHG_ERR_NUMERIC, "NaN"),
+        (np.array([0, 2, 2, 4], np.int64), ci, v, b, c, np.array([0.0, np.inf, 0.0]),
+         P.PDHG_ERR_NUMERIC, "NaN"),  # Inf in the warm start
+    ]
+    for rp, cc, vv, bb, cv, x0, status, msg in cases:
+        with pytest.raises(P.PDHGError) as ei:
+            P.pdhg_create(3, 3, rp, cc, vv, bb, cv, x0=x0)
+        assert ei.value.status == status, (rp, cc, bb, x0)
+        assert msg in P.pdhg_last_error(None), (msg, P.pdhg_last_error(None))
+
+
 def test_bad_sizes_and_options(lib):
     rp, ci, v, b, c = _tiny_csr()
     with pytest.raises(P.PDHGError) as ei:
