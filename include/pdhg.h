@@ -14,6 +14,10 @@
  * General rules for every call:
  *   - Every call returns a pdhg_status; nothing aborts, traps or exits.
  *     pdhg_last_error() gives a one-line description of the last failure.
+ *     A NULL context gives PDHG_ERR_INVALID (with no message). A failed CUDA
+ *     call gives PDHG_ERR_CUDA, or PDHG_ERR_OOM for a failed allocation; its
+ *     message names the call. Host-side checks run before any device work, so
+ *     a call that fails them leaves the context unchanged.
  *   - A pdhg_ctx is not thread-safe: one host thread at a time per context.
  *     Different contexts are independent.
  *   - Pointers passed in are borrowed for the duration of the call only; the
@@ -182,12 +186,16 @@ typedef struct {
 /* Fill *opt with the defaults listed above. */
 PDHG_API void pdhg_default_options(pdhg_options* opt);
 
-/* Create a solver for one LP. A (m x n, CSR: row_ptr[m+1], col_idx[nnz],
- * val[nnz]), b[m], c[n]; x0[n] and y0[m] are an optional warm start (NULL =
- * zeros). Setup: copy, transpose, Ruiz + Pock-Chambolle scaling, power
- * iteration for eta, primal weight omega0, and the evaluation of the starting
- * point. INVALID for malformed CSR or sizes out of range, NUMERIC for NaN/Inf
- * in the data. On failure *out is NULL. */
+/* Create a solver for one LP, the primal/dual pair of Section 2. A (m x n,
+ * CSR: row_ptr[m+1], col_idx[nnz], val[nnz]), b[m], c[n]; x0[n] and y0[m] are
+ * an optional warm start (NULL = zeros). Host pointers, or device pointers when
+ * opt->inputs_on_device = 1; all are borrowed for the call (the context keeps
+ * its own copies). opt NULL = the defaults. Setup: copy, transpose, Ruiz +
+ * Pock-Chambolle scaling, power iteration for eta, primal weight omega0, and
+ * the evaluation of the starting point. Errors: INVALID for sizes out of range,
+ * NULL arrays, malformed CSR or options out of range; NUMERIC for NaN/Inf in
+ * A, b, c or the warm start; CUDA / OOM from the device. On failure *out is
+ * NULL and pdhg_last_error(NULL) describes the failure (per host thread). */
 PDHG_API pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
                                  const double* val, const double* b, const double* c, const double* x0,
                                  const double* y0, const pdhg_options* opt, void* cuda_stream, pdhg_ctx** out);
@@ -206,24 +214,32 @@ PDHG_API void pdhg_destroy(pdhg_ctx* ctx);
  * PDHG_ERR_NOT_CONVERGED; *iters_done (nullable) gets the count run. */
 PDHG_API pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done);
 
-/* KKT measures (see pdhg_kkt_info) of the current iterate, the running average
- * or the last restart point, in FP64 on the problem as given. */
+/* KKT measures (see pdhg_kkt_info; Section 2's residuals, gap and the three
+ * relative ratios of its termination test) of the current iterate, the running
+ * average or the last restart point (which = PDHG_CURRENT, PDHG_AVERAGE,
+ * PDHG_LAST_RESTART), in FP64 on the problem as given; *out is caller-owned.
+ * INVALID for a NULL out or another selector, STATE on a batch context. */
 PDHG_API pdhg_status pdhg_kkt(pdhg_ctx* ctx, int which, pdhg_kkt_info* out);
 
-/* Copy (x, y, z) of the chosen point, on the problem as given, into caller
- * buffers x[n], y[m], z[n] (any may be NULL). Host pointers unless
- * on_device != 0. z = max(0, c - A^T y). Synchronous. */
+/* Copy (x, y, z) of the chosen point (selector as in pdhg_kkt), on the
+ * problem as given (Section 2's variables), into caller buffers x[n], y[m],
+ * z[n] (any may be NULL). Host pointers unless on_device != 0.
+ * z = max(0, c - A^T y). Synchronous. INVALID for another selector, STATE on
+ * a batch context. */
 PDHG_API pdhg_status pdhg_get_solution(pdhg_ctx* ctx, int which, double* x, double* y, double* z, int on_device);
 
-/* Scheduled snapshots (Algorithm 1 thresholds eps_cross * eps_factor^j, and/or
- * every snapshot_every iterations): the evaluation's candidate point, unscaled,
- * packed on the GPU and copied to pinned host memory on a side stream while the
- * iteration continues. *count gets the number taken so far, *ready whether the
- * latest copy has landed (both nullable). Non-blocking. */
+/* Scheduled snapshots (Algorithm 1, Section 3.1: thresholds
+ * eps_cross * eps_factor^j, and/or every snapshot_every iterations): the
+ * evaluation's candidate point, unscaled, packed on the GPU and copied to
+ * pinned host memory on a side stream while the iteration continues. *count
+ * gets the number taken so far, *ready whether the latest copy has landed
+ * (both nullable). Non-blocking; CUDA if the copy's event reports an error. */
 PDHG_API pdhg_status pdhg_snapshot_poll(pdhg_ctx* ctx, int64_t* count, int* ready);
 
-/* Copy the latest scheduled snapshot into host buffers x[n], y[m], z[n]
- * (any may be NULL); waits for its copy to land. STATE if none was taken. */
+/* Copy the latest scheduled snapshot (Algorithm 1's (x_k, y_k, z_k)) into
+ * caller-owned host buffers x[n], y[m], z[n] (any may be NULL) and its
+ * iteration and rel_kkt (nullable); waits for its copy to land. STATE if none
+ * was taken. */
 PDHG_API pdhg_status pdhg_snapshot(pdhg_ctx* ctx, double* x, double* y, double* z, int64_t* iteration,
                                    double* rel_kkt);
 
@@ -255,11 +271,14 @@ PDHG_API pdhg_status pdhg_snapshot_wait(pdhg_ctx* ctx, int64_t after, int64_t ti
 PDHG_API pdhg_status pdhg_backward(pdhg_ctx* ctx, const double* dL_dxK, const double* dL_dyK, double* dL_dc,
                                    double* dL_db, int on_device);
 
-/* Engine scalars. */
+/* Engine scalars (iteration counts, restarts, step sizes, primal weight,
+ * precision in use, polishing counts; see pdhg_info) into the caller-owned
+ * *out. INVALID for a NULL out. */
 PDHG_API pdhg_status pdhg_get_info(pdhg_ctx* ctx, pdhg_info* out);
 
-/* Copy up to cap evaluation records (oldest first) into recs; *count gets the
- * number stored (at most 65536 are kept). */
+/* Copy up to cap evaluation records (oldest first: at each evaluation the
+ * candidate's rel_kkt, the restart decision and the primal weight) into the caller-owned
+ * host array recs; *count gets the number stored (at most 65536 are kept). */
 PDHG_API pdhg_status pdhg_get_trace(pdhg_ctx* ctx, pdhg_trace_rec* recs, int64_t cap, int64_t* count);
 
 /* Feasibility polishing (the PDLP variant Section 5 describes; see the
