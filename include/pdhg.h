@@ -317,7 +317,8 @@ PDHG_API pdhg_status pdhg_kkt_noalloc(int64_t m, int64_t n, const int64_t* a_row
                                       const double* at_val, const double* b, const double* c, const double* x,
                                       const double* y, int blocks, void* cuda_stream, pdhg_kkt_info* out);
 
-/* One LP of a batch (host pointers; same CSR rules as pdhg_create). */
+/* One LP of a batch (host pointers, borrowed for the call; same CSR rules as
+ * pdhg_create). */
 typedef struct {
   int64_t m, n, nnz;
   const int64_t* row_ptr;
@@ -335,22 +336,30 @@ typedef struct {
  * blocks return at once). FP64, host inputs, starting point zero; snapshots,
  * recording and warm starts are not available for batches. Use pdhg_iterate
  * (runs until every instance meets tol, or max_iters), pdhg_batch_info and
- * pdhg_batch_solution; pdhg_kkt and pdhg_get_solution return STATE. */
+ * pdhg_batch_solution; pdhg_kkt and pdhg_get_solution return STATE.
+ * Errors: INVALID for count < 1, a NULL lps, an instance that fails
+ * pdhg_create's checks (the message names it), totals of m, n or nnz at or
+ * above 2^31 - 1, or options a batch does not take (primal_panels = 1,
+ * feas_polish); NUMERIC for NaN/Inf in an instance; CUDA / OOM from the
+ * device. On failure *out is NULL. */
 PDHG_API pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_options* opt,
                                        void* cuda_stream, pdhg_ctx** out);
 
-/* Per-instance arrays of length count (any may be NULL): iterations run,
- * converged (rel_kkt <= tol at an evaluation), last candidate rel_kkt,
- * restarts. Also valid for a single-LP context (count = 1). */
+/* Per-instance arrays of length count, caller-owned host memory (any may be
+ * NULL): iterations run, converged (rel_kkt <= tol at an evaluation), last
+ * candidate rel_kkt, restarts. Also valid for a single-LP context
+ * (count = 1). */
 PDHG_API pdhg_status pdhg_batch_info(pdhg_ctx* ctx, int64_t* iterations, int* converged, double* rel_kkt,
                                      int64_t* restarts);
 
 /* pdhg_kkt for one instance of a batch (the same measures, on that instance's
- * problem as given): its current, average or last-restart point. */
+ * problem as given): its current, average or last-restart point. INVALID for
+ * a NULL out, an instance outside [0, count) or another selector. */
 PDHG_API pdhg_status pdhg_batch_kkt(pdhg_ctx* ctx, int instance, int which, pdhg_kkt_info* out);
 
-/* (x, y, z) of one instance on its problem as given, into host buffers of its
- * n, m, n (any may be NULL). */
+/* (x, y, z) of one instance on its problem as given, into caller-owned host
+ * buffers of its n, m, n (any may be NULL). INVALID for an instance outside
+ * [0, count). */
 PDHG_API pdhg_status pdhg_batch_solution(pdhg_ctx* ctx, int instance, double* x, double* y, double* z);
 
 /* Layout autotuner (no counterpart in the paper: a tuning aid for the step
@@ -363,7 +372,11 @@ PDHG_API pdhg_status pdhg_batch_solution(pdhg_ctx* ctx, int instance, double* x,
  * (see pdhg_profile_key) is returned without any device work (*from_cache = 1;
  * from_cache may be NULL), and a newly timed choice is appended as one line
  * "key step_block rows_per_thread long_row_min ms_per_iteration". Host inputs
- * only; each candidate builds and frees its own context on cuda_stream. */
+ * only; each candidate builds and frees its own context on cuda_stream.
+ * Errors: INVALID for a NULL tuned, device inputs, or bad sizes, row
+ * pointers or column indices; otherwise the first failing candidate's
+ * status from pdhg_create or pdhg_iterate (for example INVALID for unsorted
+ * columns, NUMERIC, CUDA, OOM). */
 PDHG_API pdhg_status pdhg_autotune(int count, const pdhg_lp_desc* lps, const pdhg_options* opt,
                                    const char* cache_path, void* cuda_stream, pdhg_options* tuned,
                                    int* from_cache);
@@ -372,7 +385,8 @@ PDHG_API pdhg_status pdhg_autotune(int count, const pdhg_lp_desc* lps, const pdh
  * cap bytes including the terminating NUL): precision, the number of
  * instances, m, n and nnz on a log2 scale in steps of 1/2, and the share of
  * the rows of A and of A^T in each power-of-two length class, rounded to 10%.
- * Host logic only. */
+ * Host logic only. INVALID for a NULL buf, cap < 1, a key longer than
+ * cap - 1, or bad sizes, row pointers or column indices. */
 PDHG_API pdhg_status pdhg_profile_key(int count, const pdhg_lp_desc* lps, int precision, char* buf, int64_t cap);
 
 /* Description of the last failure of ctx, or of the last failed context-free
