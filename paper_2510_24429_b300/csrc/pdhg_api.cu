@@ -1827,7 +1827,9 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
                 "record_for_backward needs restarts = 0, primal_weight = 0 (fixed steps), precision FP64 or FP32 "
                 "and checkpoint_every >= 1");
   if (o.eval_every < 1 || o.ruiz_iters < 0 || o.power_iters < 1 || !(o.step_factor > 0.0) || o.pc_alpha < 0.0 ||
-      o.pc_alpha > 2.0 || o.long_row_min < 1 || o.dual_hot_cols < 0 || o.dual_hot_cols > HOT_MAX || !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4) || o.snapshot_every < 0 || o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
+      o.pc_alpha > 2.0 || o.long_row_min < 1 || o.dual_hot_cols < 0 || o.dual_hot_cols > HOT_MAX ||
+      !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4) || o.snapshot_every < 0 ||
+      o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
     return fail(nullptr, PDHG_ERR_INVALID, "option out of range");
   if (!(o.step_block == 0 || o.step_block == 128 || o.step_block == 256 || o.step_block == 512))
     return fail(nullptr, PDHG_ERR_INVALID, "step_block must be 128, 256 or 512");
