@@ -252,7 +252,8 @@ PDHG_API pdhg_status pdhg_snapshot(pdhg_ctx* ctx, double* x, double* y, double* 
  * copied is protected from reuse until the copy is done (the iterating thread
  * waits for it, at most 60 s, before overwriting that ring slot). Returns
  * PDHG_ERR_TIMEOUT when no newer snapshot completes within timeout_ms (a host
- * wait: nothing waits on the GPU); does not update pdhg_last_error. The
+ * wait: nothing waits on the GPU) and INVALID for after < 0 or
+ * timeout_ms < 0; does not update pdhg_last_error. The
  * context must outlive the calls (destroy it only after its consumers have
  * returned). */
 PDHG_API pdhg_status pdhg_snapshot_wait(pdhg_ctx* ctx, int64_t after, int64_t timeout_ms, double* x, double* y,

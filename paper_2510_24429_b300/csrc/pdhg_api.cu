@@ -125,7 +125,6 @@ struct pdhg_ctx {
   std::condition_variable snap_cv;
   int64_t snap_seq[SNAP_SLOTS] = {};  // 1-based index of the complete snapshot in a slot, 0 while written
   int snap_readers[SNAP_SLOTS] = {};
-  int64_t snap_latest = 0;  // index of the newest complete snapshot
   SnapLanded snap_cb[SNAP_SLOTS] = {};
   // kernel timing
   cudaEvent_t ev[3 * EV_POOL] = {};
@@ -444,7 +443,6 @@ void CUDART_CB snapshot_landed(void* p) {
   {
     std::lock_guard<std::mutex> lk(ctx->snap_mu);
     ctx->snap_seq[d->slot] = d->seq;
-    ctx->snap_latest = std::max(ctx->snap_latest, d->seq);
   }
   ctx->snap_cv.notify_all();
 }
@@ -2156,17 +2154,22 @@ pdhg_status pdhg_snapshot(pdhg_ctx* ctx, double* x, double* y, double* z, int64_
 
 pdhg_status pdhg_snapshot_wait(pdhg_ctx* ctx, int64_t after, int64_t timeout_ms, double* x, double* y, double* z,
                                int64_t* index, int64_t* iteration, double* rel_kkt) {
-  if (!ctx || timeout_ms < 0) return PDHG_ERR_INVALID;
+  if (!ctx || after < 0 || timeout_ms < 0) return PDHG_ERR_INVALID;
   int slot = -1;
   int64_t seq = 0;
   {
     std::unique_lock<std::mutex> lk(ctx->snap_mu);
-    if (!ctx->snap_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return ctx->snap_latest > after; }))
-      return PDHG_ERR_TIMEOUT;
-    seq = ctx->snap_latest;
-    for (int s = 0; s < SNAP_SLOTS; ++s)
-      if (ctx->snap_seq[s] == seq) slot = s;
-    if (slot < 0) return PDHG_ERR_STATE;
+    // the slot of the newest complete snapshot numbered above `after`. A slot
+    // being rewritten holds 0, so when the newest complete snapshot's slot is
+    // reused before its successors land, this waits for a successor.
+    auto newest = [&] {
+      slot = -1;
+      for (int s = 0; s < SNAP_SLOTS; ++s)
+        if (ctx->snap_seq[s] > after && (slot < 0 || ctx->snap_seq[s] > ctx->snap_seq[slot])) slot = s;
+      return slot >= 0;
+    };
+    if (!ctx->snap_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), newest)) return PDHG_ERR_TIMEOUT;
+    seq = ctx->snap_seq[slot];
     ctx->snap_readers[slot] += 1;
   }
   const double* h = ctx->snap_host[slot];
