@@ -136,3 +136,23 @@ def test_null_context_is_safe(lib):
     assert lib.pdhg_iterate(None, 1, 0.0, None) == P.PDHG_ERR_INVALID
     assert lib.pdhg_kkt(None, 0, None) == P.PDHG_ERR_INVALID
     assert lib.pdhg_snapshot(None, None, None, None, None, None) == P.PDHG_ERR_INVALID
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without libpdhg.so the binding raises on first use: there is no CPU path."""
+    pkg = tmp_path / "paper_2510_24429_b300"
+    pkg.mkdir()
+    for f in ("__init__.py", "pdhg.py", "lpgen.py"):
+        (pkg / f).write_text(open(os.path.join(ROOT, "paper_2510_24429_b300", f)).read())
+    code = (
+        "from paper_2510_24429_b300 import lpgen, pdhg as P\n"
+        "lp = lpgen.tiny_lp(0)\n"
+        "try:\n"
+        "    P.Solver.from_lp(lp)\n"
+        "except RuntimeError as e:\n"
+        "    print('RAISED', e)\n"
+    )
+    r = subprocess.run(["python", "-c", code], cwd=tmp_path, capture_output=True, text=True, timeout=300,
+                       env={**os.environ, "PYTHONPATH": str(tmp_path)})
+    assert r.returncode == 0, r.stderr
+    assert "RAISED libpdhg.so not built" in r.stdout and str(pkg) in r.stdout, r.stdout
