@@ -127,6 +127,8 @@ class Options:
 
 
 def csr_matrix(m, n, row_ptr, col_idx, val) -> sp.csr_matrix:
+    """The constraint matrix A of Section 2's primal LP (rows = constraints)
+    from its CSR arrays."""
     return sp.csr_matrix((np.asarray(val, dtype=np.float64), np.asarray(col_idx), np.asarray(row_ptr)), shape=(m, n))
 
 
@@ -176,6 +178,10 @@ def kkt(A: sp.csr_matrix, b: np.ndarray, c: np.ndarray, x: np.ndarray, y: np.nda
 # ---------------------------------------------------------------------------
 
 def _inv_sqrt_or_one(v: np.ndarray) -> np.ndarray:
+    """1/sqrt(v) where v > 0, else 1: the scaling factor of a row or column,
+    with an empty row or column left unscaled (Ruiz and Pock-Chambolle
+    scaling, a reading: the paper names its solver's line of work, Section 4.1,
+    not its scaling)."""
     out = np.ones_like(v)
     nz = v > 0
     out[nz] = 1.0 / np.sqrt(v[nz])
@@ -203,7 +209,8 @@ def ruiz_scaling(A: sp.csr_matrix, iters: int):
 
 def _abs_power(A: sp.csr_matrix, p: float) -> sp.csr_matrix:
     """|A_ij|^p on the stored entries, with 0^p = 0 also for p = 0 (a stored
-    zero counts as absent)."""
+    zero counts as absent): the entry powers of Pock-Chambolle scaling with
+    parameter alpha (a reading, as for the rest of the scaling)."""
     B = abs(A).tocsr(copy=True)
     B.data = np.where(B.data > 0, B.data ** p, 0.0)
     return B
@@ -221,7 +228,9 @@ def pock_chambolle_scaling(A: sp.csr_matrix, alpha: float = 1.0):
 
 
 def scale_problem(A: sp.csr_matrix, b: np.ndarray, c: np.ndarray, opt: Options):
-    """Ahat = D_r A D_c, bhat = D_r b, chat = D_c c."""
+    """Ahat = D_r A D_c, bhat = D_r b, chat = D_c c: the diagonally scaled LP
+    that the PDLP line of work (Section 1, Section 4.1) iterates on; Ruiz
+    passes then one Pock-Chambolle pass (readings at ``Options``)."""
     Ah, d_r, d_c = ruiz_scaling(A, opt.ruiz_iters)
     if opt.pock_chambolle:
         Ah, r, s = pock_chambolle_scaling(Ah, opt.pc_alpha)
@@ -282,7 +291,9 @@ def power_norm(Ah: sp.csr_matrix, iters: int) -> float:
 
 def pdhg_iteration(Ah, AhT, bh, ch, x, y, tau, sigma):
     """x' = max(0, x - tau (chat - Ahat^T y)); xbar = 2x' - x;
-    y' = y + sigma (bhat - Ahat xbar). Returns (x', xbar, y')."""
+    y' = y + sigma (bhat - Ahat xbar). Returns (x', xbar, y'). The "Perform
+    PDHG iteration" step of Algorithm 1 (Section 3.1), in the PDLP form the
+    paper's solver follows (Section 4.1; the formula is a reading)."""
     x_new = np.maximum(0.0, x - tau * (ch - AhT @ y))
     xbar = 2.0 * x_new - x
     y_new = y + sigma * (bh - Ah @ xbar)
@@ -307,13 +318,16 @@ def halpern_iteration(Ah, AhT, bh, ch, x, y, x_anchor, y_anchor, tau, sigma, t, 
 
 def weighted_kkt(norms, omega: float) -> float:
     """KKT_omega = sqrt(omega ||r_P||^2 + ||r_D||^2 / omega + gap^2) from the
-    (||r_P||, ||r_D||, gap) of a point of the scaled problem."""
+    (||r_P||, ||r_D||, gap) of a point of the scaled problem: Section 2's
+    residuals and gap combined with the primal weight, the measure of PDLP's
+    KKT-error restart scheme (a reading; the paper gives no restart rule)."""
     p, d, g = norms
     return math.sqrt(omega * p * p + d * d / omega + g * g)
 
 
 def choose_candidate(n_cur, n_avg, omega) -> int:
-    """The average wins only if its weighted KKT error is strictly smaller."""
+    """The restart candidate of PDLP's scheme (a reading): the average wins
+    only if its weighted KKT error is strictly smaller."""
     return RESTART_TO_AVERAGE if weighted_kkt(n_avg, omega) < weighted_kkt(n_cur, omega) else RESTART_TO_CURRENT
 
 
@@ -329,13 +343,18 @@ def restart_decision(k_cand, k_last_restart, k_prev_cand, t_since, k_total, opt:
 
 
 def _rel_gap(a: float, b: float) -> float:
+    """|a - b| / max(|a|, |b|) (0 when both are 0): the relative margin of a
+    restart comparison, recorded so that a test can tell a decision taken at
+    rounding level from a clear one; no part of the method."""
     d = max(abs(a), abs(b))
     return abs(a - b) / d if d > 0 else 0.0
 
 
 def primal_weight_update(omega: float, dx: float, dy: float, theta: float) -> float:
     """omega <- exp(theta ln(dy/dx) + (1 - theta) ln omega) when both moves are
-    above 1e-10; unchanged otherwise."""
+    above 1e-10; unchanged otherwise. PDLP's primal-weight update at a restart
+    (a reading; the paper gives none), dx and dy the moves of x and y since the
+    previous restart point on the scaled problem."""
     if dx > 1e-10 and dy > 1e-10:
         return math.exp(theta * math.log(dy / dx) + (1.0 - theta) * math.log(omega))
     return omega
@@ -347,6 +366,10 @@ def primal_weight_update(omega: float, dx: float, dy: float, theta: float) -> fl
 
 @dataclasses.dataclass
 class EvalRecord:
+    """What one evaluation of Algorithm 1's loop decided (Section 3.1; the
+    restart fields follow PDLP's scheme, a reading), recorded for comparison
+    with the engine's trace."""
+
     iteration: int
     kind: int  # NO_RESTART / RESTART_TO_CURRENT / RESTART_TO_AVERAGE
     candidate: int  # RESTART_TO_CURRENT / RESTART_TO_AVERAGE
@@ -361,7 +384,10 @@ class EvalRecord:
 
 
 class Oracle:
-    """Plain FP64 PDHG for ``min c^T x, Ax = b, x >= 0``."""
+    """Plain FP64 PDHG for ``min c^T x, Ax = b, x >= 0`` (Section 2's LP):
+    the PDHG loop of Algorithm 1 (Section 3.1) with its evaluations, restarts
+    and snapshots; the crossover threads Algorithm 1 launches are not part of
+    it."""
 
     def __init__(self, m, n, row_ptr, col_idx, val, b, c, opt: Options | None = None,
                  x0=None, y0=None):
@@ -405,40 +431,54 @@ class Oracle:
     # -- step sizes --------------------------------------------------------
     @property
     def tau(self) -> float:
+        """Primal step eta / omega (PDLP's step split by the primal weight, a
+        reading)."""
         return self.eta / self.omega
 
     @property
     def sigma(self) -> float:
+        """Dual step eta * omega (as ``tau``)."""
         return self.eta * self.omega
 
     # -- measures on the scaled problem (restart rules) --------------------
     def scaled_norms(self, xh, yh):
-        """(||bhat - Ahat xhat||, ||max(0, Ahat^T yhat - chat)||, |chat^T xhat - bhat^T yhat|)."""
+        """(||bhat - Ahat xhat||, ||max(0, Ahat^T yhat - chat)||, |chat^T xhat - bhat^T yhat|):
+        Section 2's residual norms and gap on the scaled problem, the inputs of
+        the restart rules (a reading: they measure on the problem they iterate)."""
         rp = self.bh - self.Ah @ xh
         rd = np.maximum(0.0, self.AhT @ yh - self.ch)
         return (float(np.linalg.norm(rp)), float(np.linalg.norm(rd)), abs(float(self.ch @ xh) - float(self.bh @ yh)))
 
     # -- unscaled quantities -----------------------------------------------
     def unscale(self, xh, yh):
-        """(x, y, z) of the problem as given from a scaled point."""
+        """(x, y, z) of the problem as given from a scaled point:
+        x = D_c xhat, y = D_r yhat and Section 2's z = max(0, c - A^T y)."""
         x = self.d_c * xh
         y = self.d_r * yh
         return x, y, dual_slack(self.A, self.c, y)
 
     def kkt_of(self, xh, yh) -> dict:
+        """Section 2's KKT measures (``kkt``) of a scaled point, on the problem
+        as given."""
         x, y, z = self.unscale(xh, yh)
         return kkt(self.A, self.b, self.c, x, y, z)
 
     @property
     def x_avg(self):
+        """Uniform average of the x iterates since the last restart (PDLP's
+        averaged restart candidate, a reading); the current x before any."""
         return self.x_sum / self.t if self.t > 0 else self.x.copy()
 
     @property
     def y_avg(self):
+        """As ``x_avg``, for y."""
         return self.y_sum / self.t if self.t > 0 else self.y.copy()
 
     # -- iteration -----------------------------------------------------------
     def iterate_once(self):
+        """One iteration of Algorithm 1's PDHG loop (Section 3.1): the PDHG map
+        (or its reflected Halpern form), then the running sums of the average
+        since the last restart."""
         if self.opt.halpern:
             self.x, self.y = halpern_iteration(self.Ah, self.AhT, self.bh, self.ch, self.x, self.y, self.x_r, self.y_r,
                                                self.tau, self.sigma, self.t, self.opt.halpern_reflect)
@@ -454,8 +494,11 @@ class Oracle:
         self.k += 1
 
     def evaluate(self, tol: float) -> bool:
-        """One evaluation: candidate choice, termination, snapshots, restart and
-        primal-weight update. Returns True when the method has converged."""
+        """One evaluation: candidate choice, termination (Section 2's relative
+        test), Algorithm 1's snapshots (Section 3.1), restart and primal-weight
+        update (PDLP's scheme, a reading), then a feasibility polishing attempt
+        when its rules allow (Section 5, readings at ``Options``). Returns True
+        when the method has converged."""
         opt = self.opt
         if opt.restarts and self.t > 0 and not opt.halpern:
             xa, ya = self.x_avg, self.y_avg
@@ -532,7 +575,9 @@ class Oracle:
         side (kind "dual") set to zero, from the scaled point (xh0, yh0), with
         this solver's scaling, eta and current primal weight, empty averages,
         the start as its restart reference, the same restart rules, and rel_p
-        (primal) or rel_d (dual) of its candidate as the termination measure."""
+        (primal) or rel_d (dual) of its candidate as the termination measure.
+        Section 5's polishing phases; their start points and measures are
+        readings (see ``Options``)."""
         sub = Oracle.__new__(Oracle)
         sub.__dict__.update(self.__dict__)
         sub.opt = dataclasses.replace(self.opt, eps_cross=0.0, snapshot_every=0, feas_polish=False)
@@ -559,21 +604,25 @@ class Oracle:
     def feasibility_phase(self, xh0, yh0, kind: str, tol: float, budget: int):
         """One polishing phase (see ``phase_solver``): it stops at the first
         evaluation where its termination measure is <= tol, or after
-        ``budget`` iterations. Returns (xhat, yhat, iterations, reached)."""
+        ``budget`` iterations (Section 5's polishing, readings at
+        ``Options``). Returns (xhat, yhat, iterations, reached)."""
         sub = self.phase_solver(xh0, yh0, kind)
         reached = sub.run(budget, tol)
         return sub.x, sub.y, sub.k, reached
 
     def polish_budget(self) -> int:
         """Iterations allowed to each phase: the main iterations so far divided
-        by polish_div, rounded up to whole evaluation periods (at least one)."""
+        by polish_div, rounded up to whole evaluation periods (at least one);
+        a reading, since Section 5 gives no budget."""
         e = self.opt.eval_every
         return e * max(1, -(-self.k // (self.opt.polish_div * e)))
 
     def feasibility_polish(self, xh_c, yh_c, tol: float):
-        """One attempt: primal phase from (x_c, 0), then (if it reached rel_p <=
-        tol) dual phase from (0, y_c); returns the scaled pair (x_p, y_d) when
-        it passes the termination test on the LP as given, else None."""
+        """One attempt of Section 5's feasibility polishing (the phases and
+        their order are readings): primal phase from (x_c, 0), then (if it
+        reached rel_p <= tol) dual phase from (0, y_c); returns the scaled pair
+        (x_p, y_d) when it passes Section 2's termination test on the LP as
+        given, else None."""
         budget = self.polish_budget()
         rec = dict(iteration=self.k, budget=budget, primal_iters=0, primal_ok=False, dual_iters=0, dual_ok=False,
                    rel_kkt=math.inf)
@@ -595,13 +644,15 @@ class Oracle:
         return None
 
     def _snapshot(self, xh, yh, rel, why):
+        """Record (x_k, y_k, z_k) on the problem as given: the copy Algorithm 1
+        hands to a crossover thread (Section 3.1)."""
         x, y, z = self.unscale(xh, yh)
         self.snapshots.append(dict(iteration=self.k, x=x, y=y, z=z, rel_kkt=rel, why=why))
 
     def run(self, max_iters: int, tol: float = 0.0) -> bool:
-        """Iterate until the candidate passes the termination test (rel_p, rel_d
-        <= tol and rel_gap <= gap_tol, or tol) at an evaluation or max_iters
-        iterations.
+        """Algorithm 1's PDHG loop (Section 3.1): iterate until the candidate
+        passes the termination test of Section 2 (rel_p, rel_d <= tol and
+        rel_gap <= gap_tol, or tol) at an evaluation or max_iters iterations.
         Evaluations happen every ``eval_every`` iterations when restarts are on or
         tol > 0; with restarts off and tol = 0 this is plain fixed-step PDHG."""
         evaluating = self.opt.restarts or tol > 0 or self.opt.eps_cross > 0 or self.opt.snapshot_every > 0
@@ -616,7 +667,8 @@ class Oracle:
 
     # -- results ---------------------------------------------------------------
     def solution(self):
-        """Unscaled (x, y, z) of the current iterate."""
+        """Unscaled (x, y, z) of the current iterate: Section 2's primal x, dual
+        y and reduced costs z = max(0, c - A^T y)."""
         return self.unscale(self.x, self.y)
 
 
@@ -628,7 +680,9 @@ def unrolled_forward(orc: Oracle, K: int, c=None, b=None):
     """K plain PDHG iterations of ``orc``'s scaled problem from its current
     point, optionally with a different objective c or right-hand side b (the
     scaling, eta and omega stay those of ``orc``). Returns the scaled iterates
-    x_0..x_K and y_0..y_K."""
+    x_0..x_K and y_0..y_K. The map of Algorithm 1's "Perform PDHG iteration"
+    step (Section 3.1) applied K times; differentiating it has no counterpart
+    in the paper."""
     ch = orc.d_c * (orc.c if c is None else np.asarray(c, dtype=np.float64))
     bh = orc.d_r * (orc.b if b is None else np.asarray(b, dtype=np.float64))
     xs, ys = [orc.x.copy()], [orc.y.copy()]
@@ -642,6 +696,8 @@ def unrolled_forward(orc: Oracle, K: int, c=None, b=None):
 def unrolled_adjoint(orc: Oracle, K: int, gx_K, gy_K=None):
     """Reverse pass through K unrolled iterations: given dL/dx_K and dL/dy_K
     on the problem as given (x = D_c xhat, y = D_r yhat), return (dL/dc, dL/db).
+    The chain rule through the map of ``unrolled_forward``; no counterpart in
+    the paper.
 
     One iteration, u = x - tau (chat - Ahat^T y), x' = max(u, 0),
     v = 2x' - x, y' = y + sigma (bhat - Ahat v), is reversed as
@@ -667,7 +723,9 @@ def unrolled_adjoint(orc: Oracle, K: int, gx_K, gy_K=None):
 
 
 def unrolled_loss(orc: Oracle, K: int, x_target, c=None, b=None) -> float:
-    """0.5 ||x_K - x_target||^2 with x_K on the problem as given."""
+    """0.5 ||x_K - x_target||^2 with x_K on the problem as given: the loss
+    through which the unrolled iterations are differentiated (no counterpart in
+    the paper; a test function for ``unrolled_adjoint``)."""
     xs, _ = unrolled_forward(orc, K, c=c, b=b)
     r = orc.d_c * xs[-1] - x_target
     return 0.5 * float(r @ r)
