@@ -139,11 +139,39 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+def code_tokens(text: str) -> str:
+    """C++/CUDA source with comments removed and whitespace runs collapsed to
+    one space (string and character literals kept as written): what the
+    compiler sees, so that a comment-only edit leaves it unchanged."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        ch = text[i]
+        if text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif ch in "\"'":
+            j = i + 1
+            while j < n and text[j] != ch:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(ch)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_sha():
+    """Hash of the step kernels' code (comments and layout excluded): the
+    traffic record stays valid only while it is unchanged."""
     h = hashlib.sha256()
     for f in ("kernels.cu", "common.cuh", "kernels.cuh"):
-        with open(os.path.join(ROOT, "paper_2510_24429_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2510_24429_b300", "csrc", f), encoding="utf-8") as fh:
+            h.update(code_tokens(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -37,3 +37,11 @@ def test_traffic_record_matches_the_kernel_sources():
         t = bench.profiled_traffic(kernel, workload)
         assert t is not None, f"{kernel}: traffic record stale or missing"
         assert 0.9e8 < t < 2e9
+
+
+def test_code_hash_ignores_comments_and_layout_only():
+    a = "int f(int x) { return x + 1; } // one\n"
+    b = "/* doc */\nint f(int x)  {\n  return x + 1;  // another\n}\n"
+    c = "int f(int x) { return x + 2; }"
+    assert bench.code_tokens(a) == bench.code_tokens(b) != bench.code_tokens(c)
+    assert bench.code_tokens('s = "/* kept */ // kept"; t = \'/\';') == 's = "/* kept */ // kept"; t = \'/\';'
