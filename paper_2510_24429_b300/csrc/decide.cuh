@@ -1,6 +1,8 @@
 // The decisions of one evaluation (restart scheme, primal weight,
 // termination, snapshot schedule), shared by the multi-launch engine and the
-// single-block solve loop (internal).
+// single-block solve loop (internal). Termination is Section 2's relative test,
+// the snapshot schedule Algorithm 1's thresholds (Section 3.1); the restart
+// scheme and primal weight are PDLP's (readings: the paper gives neither).
 #pragma once
 
 #include "common.cuh"

@@ -1,5 +1,12 @@
 // CUDA kernels of the PDHG engine (sm_103a).
 //
+// They run the "Perform PDHG iteration" step of Algorithm 1 (Section 3.1) on
+// the LP pair of Section 2, in the PDLP form the paper's solver follows
+// (Section 1, Section 4.1; the paper gives no formula, so the iteration, the
+// scaling and the restart scheme are readings), and compute Section 2's
+// residuals and relative termination test. The paper notes that PDHG is
+// memory-bandwidth bound (Section 5).
+//
 // The iteration is bandwidth bound: each half-step streams one copy of the
 // scaled matrix (Ahat for the dual step, Ahat^T for the primal step) exactly
 // once, gathers one vector, and fuses the vector update of the step into the
@@ -239,7 +246,9 @@ __device__ __forceinline__ void hyb_dot(const Hyb& H, const T* __restrict__ vals
 struct NoState {};
 
 // ---------------------------------------------------------------------------
-// setup kernels
+// setup kernels: Ruiz and Pock-Chambolle scaling, the power iteration for
+// ||Ahat||_2 and the step sizes (readings: the paper names its solver's line
+// of work, Section 4.1, but not its set-up)
 // ---------------------------------------------------------------------------
 struct AbsMaxOp {
   const double* __restrict__ v;
@@ -400,7 +409,9 @@ __global__ void k_finish_setup(DevState* st, const double* __restrict__ scal, do
 }
 
 // ---------------------------------------------------------------------------
-// the two fused half-steps of one PDHG iteration
+// the two fused half-steps of one PDHG iteration (Algorithm 1, Section 3.1):
+// x' = max(0, x - tau (chat - Ahat^T y)), xbar = 2x' - x, then
+// y' = y + sigma (bhat - Ahat xbar)
 // ---------------------------------------------------------------------------
 template <class T>
 struct PrimalOp {
@@ -511,6 +522,8 @@ __global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
 }
 
 // ---- reflected Halpern form of the two half-steps (option halpern) ----------
+// (the cuPDLP+ line the paper's solver follows, Section 4.1; a reading, as the
+// paper gives no formula)
 // With (x~, y~) the PDHG map's output, w = (t + 1) / (t + 2) (t = iterations
 // since the last restart, before this step) and the last restart point
 // (xr, yr) as anchor: x <- w ((1 + rho) x~ - rho x) + (1 - w) xr, likewise y;
@@ -675,7 +688,10 @@ __global__ void k_add_counters(DevState* st, long long dk) {
 }
 
 // ---------------------------------------------------------------------------
-// evaluation
+// evaluation: Section 2's residuals r_P = b - A x and r_D = A^T y + z - c with
+// z = max(0, c - A^T y), the objectives, the gap and x^T z, for the current
+// point and the average, on the problem as given; Algorithm 1's "maxresid" is
+// the largest of the three relative measures (Section 3.1)
 // ---------------------------------------------------------------------------
 __global__ void k_make_average(const double* __restrict__ xs, const double* __restrict__ ys,
                                const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ xa,
@@ -820,7 +836,8 @@ __global__ void k_decide(DevState* st, TraceRec* trace) { decide_one(st, trace);
 
 // ---------------------------------------------------------------------------
 // batch: per-instance counterparts (instance = blockIdx.y for vector kernels,
-// one thread per instance for scalar kernels)
+// one thread per instance for scalar kernels); many independent LPs at once,
+// each following the single-LP method (no counterpart in the paper)
 // ---------------------------------------------------------------------------
 __global__ void k_decide_b(DevState* sts, int count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -979,7 +996,8 @@ __global__ void k_apply(const DevState* __restrict__ st, double* __restrict__ x,
 }
 
 // ---------------------------------------------------------------------------
-// mixed precision: FP32 iteration state, FP64 evaluation and restarts
+// mixed precision: FP32 iteration state, FP64 evaluation and restarts (no
+// counterpart in the paper, whose PDHG runs in FP64)
 // ---------------------------------------------------------------------------
 __global__ void k_narrow(float* __restrict__ dst, const double* __restrict__ src, long long len) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
@@ -1048,9 +1066,10 @@ __global__ void k_apply32(const DevState* __restrict__ st, float* __restrict__ x
 
 // Start of the FP64 phase: the point just evaluated into st->cur becomes the
 // restart reference and the count since the last restart starts over.
-// Start of a feasibility polishing phase (st->cur holds the start point's
-// evaluation on the phase's problem): the start is the restart reference and
-// the previous candidate, counters at zero, no snapshots, the phase's test.
+// Start of a feasibility polishing phase (Section 5; the phases are readings).
+// st->cur holds the start point's evaluation on the phase's problem: the start
+// is the restart reference and the previous candidate, counters at zero, no
+// snapshots, the phase's test.
 __global__ void k_polish_begin(DevState* st, int term_mode) {
   double p, d, g;
   scaled_norms(st->cur, p, d, g);
@@ -1077,7 +1096,8 @@ __global__ void k_promote_state(DevState* st) {
 }
 
 // ---------------------------------------------------------------------------
-// adjoint of one PDHG iteration (fixed step, no restarts)
+// adjoint of one PDHG iteration (fixed step, no restarts; differentiation has
+// no counterpart in the paper)
 //   forward: u = x - tau (chat - Ahat^T y), x' = max(u, 0), v = 2x' - x,
 //            y' = y + sigma (bhat - Ahat v)
 //   reverse: g_v = -sigma Ahat^T g_y',  g_u = [x' > 0] (g_x' + 2 g_v),
@@ -1149,6 +1169,9 @@ __global__ void k_adj_unseed(double* __restrict__ out, const T* __restrict__ g, 
     out[perm[i]] = d[i] * (double)g[i];
 }
 
+// Snapshot packing: the candidate (x, y) unscaled, with z = max(0, c - A^T y),
+// in the caller's numbering: the copy (x_k, y_k, z_k) Algorithm 1 hands to a
+// crossover thread (Section 3.1).
 struct PackDualOp {
   using State = NoState;
   const int* __restrict__ perm;

@@ -3,7 +3,9 @@
 // columns by decreasing length, the transpose, and the packing of the rows
 // into long-row units and slices. All of it is integer work and data
 // movement, done once per context; the unit tables themselves (a few bytes
-// per 32 rows) are computed on the host from the sorted row lengths.
+// per 32 rows) are computed on the host from the sorted row lengths. The
+// layout is this engine's own; the paper only states A as a sparse matrix of
+// its LP (Section 2).
 //
 // Orders are deterministic: the renumbering is a stable sort (rows of equal
 // length keep their order), and every row of the transpose lists its entries

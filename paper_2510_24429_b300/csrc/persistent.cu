@@ -1,5 +1,7 @@
 // The whole solve loop of a small LP in one thread block (option
-// `persistent`). One launch runs PDHG iterations, the evaluation of the
+// `persistent`): Algorithm 1's PDHG loop (Section 3.1) without its crossover
+// threads, in one launch; the single-block form has no counterpart in the
+// paper. One launch runs PDHG iterations, the evaluation of the
 // current and average points every eval_every iterations, the restart and
 // primal-weight decisions and the termination test, with every vector of the
 // LP held in shared memory and the two half-steps separated by block
