@@ -67,6 +67,14 @@ enum { PDHG_CURRENT = 0, PDHG_AVERAGE = 1, PDHG_LAST_RESTART = 2 };
 /* restart kinds in the evaluation trace */
 enum { PDHG_NO_RESTART = 0, PDHG_RESTART_TO_CURRENT = 1, PDHG_RESTART_TO_AVERAGE = 2 };
 
+/* Options (pdhg_default_options gives the values in parentheses). Scaling,
+ * step size, restarts and the primal weight follow the PDLP line of work that
+ * the paper's solver follows (Section 1, Section 4.1). The paper fixes none of
+ * them, so they and their defaults (PDLP's published ones) are readings.
+ * eps_cross and eps_factor are Algorithm 1's snapshot thresholds (Section 3.1).
+ * feas_polish and gap_tol follow Section 5 and Section 2. The other options
+ * choose the engine's form (precision, layout, launch shape, recording); the
+ * paper has no counterpart for them. */
 typedef struct {
   int precision;          /* PDHG_FP64 (default); PDHG_FP32: both half-steps in FP32 (matrix values,
                              vectors, accumulation) with FP64 evaluation and restart decisions;
