@@ -176,3 +176,23 @@ def test_phase_stops_on_its_own_measure_and_starts_its_own_restart_reference(tin
         assert sub.evaluate(1e-8)
         start = o.phase_solver(xs, np.zeros(lp.m), kind)
         assert start.n_restart == start.scaled_norms(xs, np.zeros(lp.m)) != o.n_restart
+
+
+def test_polished_pair_is_judged_with_the_gap_tolerance():
+    """A polishing attempt from a primal-feasible x_c and a dual-feasible y_c
+    (each a fixed point of its phase) returns the pair (x_c, y_c), whose
+    relative gap is 5/6 on the 2x3 LP (x_c = (3, 0, 2), y_c = 0). The pair ends
+    the solve exactly when gap_tol admits 5/6 (Section 2's test with a separate
+    gap tolerance; the phases are Section 5's polishing)."""
+    A = sp.csr_matrix(np.array([[1.0, 2.0, 0.0], [0.0, 1.0, 1.0]]))
+    b, c = np.array([3.0, 2.0]), np.array([1.0, 1.0, 1.0])
+    x_c, y_c = np.array([3.0, 0.0, 2.0]), np.zeros(2)
+    for gap_tol, accepted in ((0.9, True), (0.8, False)):
+        o = O.Oracle(2, 3, A.indptr, A.indices, A.data, b, c, O.Options(gap_tol=gap_tol, feas_polish=True))
+        pair = o.feasibility_polish(x_c / o.d_c, y_c / o.d_r, 1e-9)
+        rec = o.polish_log[-1]
+        assert rec["primal_ok"] and rec["dual_ok"] and rec["rel_gap"] == pytest.approx(5 / 6, rel=1e-9)
+        assert (pair is not None) is accepted, gap_tol
+        if accepted:
+            xp, yd = pair
+            assert np.allclose(o.d_c * xp, x_c, rtol=0, atol=1e-12) and np.allclose(o.d_r * yd, y_c, atol=1e-12)

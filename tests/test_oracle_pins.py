@@ -29,7 +29,8 @@ def test_kkt_hand_computed_2x3():
     g = _golden_2x3()
     A = sp.csr_matrix(np.array(g["A"], dtype=float))
     b, c = np.array(g["b"], float), np.array(g["c"], float)
-    for point in ("kkt_point", "kkt_point_negative_residual", "kkt_point_negative_x"):
+    for point in ("kkt_point", "kkt_point_negative_residual", "kkt_point_negative_x",
+                  "kkt_point_negative_x_with_slack"):
         p = g[point]
         info = O.kkt(A, b, c, np.array(p["x"], float), np.array(p["y"], float))
         for key, expr in p["expect"].items():
@@ -315,3 +316,22 @@ def test_algorithm1_snapshot_schedule(tiny_lp):
         # the snapshot is the unscaled (x, y, z) with z the dual slack of y
         A = O.csr_matrix(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val)
         assert O.kkt(A, lp.b, lp.c, snap["x"], snap["y"], snap["z"])["rel_kkt"] == pytest.approx(snap["rel_kkt"], rel=1e-12)
+
+
+def test_separate_gap_tolerance_decides_termination():
+    """Section 2's termination test with its own gap tolerance, on a pair that is
+    primal feasible (A x = b, x >= 0) and dual feasible (A^T y <= c) but not
+    optimal: x = (3, 0, 2), y = 0 on the 2x3 LP, so rel_p = rel_d = 0 and
+    rel_gap = |5 - 0| / (1 + 5 + 0) = 5/6. The evaluation of this starting point
+    accepts it exactly when the gap tolerance admits 5/6."""
+    g = _golden_2x3()
+    A = sp.csr_matrix(np.array(g["A"], dtype=float))
+    b, c = np.array(g["b"], float), np.array(g["c"], float)
+    x0, y0 = np.array([3.0, 0.0, 2.0]), np.zeros(2)
+    assert np.array_equal(A @ x0, b) and np.all(A.T @ y0 <= c)
+    for gap_tol, accepted in ((0.9, True), (5 / 6 + 1e-9, True), (0.8, False), (0.0, False)):
+        o = O.Oracle(2, 3, A.indptr, A.indices, A.data, b, c, O.Options(restarts=False, gap_tol=gap_tol),
+                     x0=x0, y0=y0)
+        kk = o.kkt_of(o.x, o.y)
+        assert kk["rel_p"] <= 1e-15 and kk["rel_d"] == 0.0 and kk["rel_gap"] == pytest.approx(5 / 6, rel=1e-15)
+        assert o.evaluate(1e-9) is accepted, gap_tol
