@@ -156,3 +156,23 @@ def test_missing_library_fails_loudly(tmp_path):
                        env={**os.environ, "PYTHONPATH": str(tmp_path)})
     assert r.returncode == 0, r.stderr
     assert "RAISED libpdhg.so not built" in r.stdout and str(pkg) in r.stdout, r.stdout
+
+
+def test_header_and_library_from_plain_c(lib, tmp_path):
+    """include/pdhg.h compiles as strict C99 and the library links and runs
+    from a C program (tests/c_abi/from_c.c): defaults, host checks, NULL
+    safety, and a short solve where a GPU is present."""
+    import shutil
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = tmp_path / "from_c"
+    libdir = os.path.dirname(B.LIB)
+    src = os.path.join(ROOT, "tests", "c_abi", "from_c.c")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        src, "-o", str(exe), "-L", libdir, "-lpdhg", f"-Wl,-rpath,{libdir}", "-lm"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
