@@ -314,7 +314,10 @@ PDHG_API pdhg_status pdhg_get_polish_log(pdhg_ctx* ctx, pdhg_polish_rec* recs, i
  *   declares statically (every GPU that loads the library holds it until the
  *   process exits). Larger values return PDHG_ERR_INVALID.
  *   The first call on a device looks up that array's device address (once per
- *   device); make that first call before any stream capture.
+ *   device) and keeps it for the life of the process; make that first call
+ *   before any stream capture. The kept address does not survive a
+ *   cudaDeviceReset, nor a switch to a context other than the device's
+ *   primary one: after either, do not call this entry point again.
  *   All calls on a device share the array and leave their partial sums in it;
  *   each call overwrites what it reads, so nothing needs clearing, but calls
  *   that overlap on the GPU (unordered streams or threads) race and return

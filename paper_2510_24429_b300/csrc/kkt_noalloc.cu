@@ -62,12 +62,16 @@ std::mutex g_scratch_mu;
 
 __device__ __forceinline__ double na_relu(double v) { return v < 0.0 ? 0.0 : v; }
 
-// one warp per row, lane-strided dot product; result in lane 0
+// one warp per row, lane-strided dot product; result in lane 0. A warp per
+// row suits small LPs and LPs with evenly filled rows; a row of thousands of
+// entries is reduced by one warp alone (the engine's own evaluation splits
+// such rows over panels instead).
 __device__ __forceinline__ double na_row_dot(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                              const double* __restrict__ v, const double* __restrict__ vec,
                                              long long row, int lane) {
+  const long long beg = rp[row], end = rp[row + 1];
   double acc = 0.0;
-  for (long long k = rp[row] + lane; k < rp[row + 1]; k += 32) acc += v[k] * vec[ci[k]];
+  for (long long k = beg + lane; k < end; k += 32) acc += v[k] * vec[ci[k]];
   return pdhg::warp_sum(acc);
 }
 
@@ -227,7 +231,12 @@ PDHG_API pdhg_status pdhg_kkt_noalloc(int64_t m, int64_t n, const int64_t* a_row
   out->rel_gap = out->gap / (1.0 + fabs(out->primal_obj) + fabs(out->dual_obj));
   out->rel_kkt = std::max(out->rel_p, std::max(out->rel_d, out->rel_gap));
   out->iteration = -1;
-  if (!std::isfinite(out->rel_kkt)) return na_fail(PDHG_ERR_NUMERIC, "NaN or Inf in the KKT measures");
+  // std::max and the fmax of the reductions drop a NaN operand, so rel_kkt
+  // alone can look finite while a term is not: every sum is checked
+  bool finite = true;
+  for (int i = 0; i < NA_COUNT; ++i) finite = finite && std::isfinite(q[i]);
+  if (!finite || !std::isfinite(out->rel_p) || !std::isfinite(out->rel_d) || !std::isfinite(out->rel_gap))
+    return na_fail(PDHG_ERR_NUMERIC, "NaN or Inf in the KKT measures");
   return PDHG_OK;
 }
 

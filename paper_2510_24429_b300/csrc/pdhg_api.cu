@@ -159,6 +159,13 @@ pdhg_status fail(pdhg_ctx* ctx, pdhg_status s, const std::string& msg) {
   return s;
 }
 
+// largest of three ratios, NaN if any is NaN (std::max would drop a NaN
+// second operand and report a finite rel_kkt for a point with a NaN term)
+double max3_nan(double a, double b, double c) {
+  if (std::isnan(a) || std::isnan(b) || std::isnan(c)) return NAN;
+  return std::max(a, std::max(b, c));
+}
+
 pdhg_status cuda_fail(pdhg_ctx* ctx, cudaError_t e, const char* what) {
   std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
   return fail(ctx, e == cudaErrorMemoryAllocation ? PDHG_ERR_OOM : PDHG_ERR_CUDA, msg);
@@ -2095,7 +2102,7 @@ pdhg_status pdhg_kkt(pdhg_ctx* ctx, int which, pdhg_kkt_info* out) {
   out->rel_p = out->rp_norm2 / (1.0 + ctx->h_st->b_norm);
   out->rel_d = out->rd_norm2 / (1.0 + ctx->h_st->c_norm);
   out->rel_gap = out->gap / (1.0 + fabs(out->primal_obj) + fabs(out->dual_obj));
-  out->rel_kkt = std::max(out->rel_p, std::max(out->rel_d, out->rel_gap));
+  out->rel_kkt = max3_nan(out->rel_p, out->rel_d, out->rel_gap);
   out->iteration = ctx->h_st->k;
   return PDHG_OK;
 }
@@ -2405,7 +2412,7 @@ pdhg_status pdhg_batch_kkt(pdhg_ctx* ctx, int instance, int which, pdhg_kkt_info
   out->rel_p = out->rp_norm2 / (1.0 + h.b_norm);
   out->rel_d = out->rd_norm2 / (1.0 + h.c_norm);
   out->rel_gap = out->gap / (1.0 + fabs(out->primal_obj) + fabs(out->dual_obj));
-  out->rel_kkt = std::max(out->rel_p, std::max(out->rel_d, out->rel_gap));
+  out->rel_kkt = max3_nan(out->rel_p, out->rel_d, out->rel_gap);
   out->iteration = h.k;
   return PDHG_OK;
 }

@@ -354,10 +354,24 @@ def pdhg_kkt_noalloc(m, n, a_row_ptr, a_col_idx, a_val, at_row_ptr, at_col_idx, 
     for a, dt in zip(args, want):
         if not (_is_torch(a) and a.is_cuda and a.is_contiguous() and a.dtype == dt):
             raise ValueError("pdhg_kkt_noalloc takes contiguous CUDA tensors of the documented dtypes")
+    # the kernels read the sizes given to them, so every length is checked
+    # here (reading metadata only; nothing is allocated)
+    m, n = int(m), int(n)
+    lengths = {"a_row_ptr": (a_row_ptr, m + 1), "at_row_ptr": (at_row_ptr, n + 1), "b": (b, m), "y": (y, m),
+               "c": (c, n), "x": (x, n)}
+    for name, (a, want_len) in lengths.items():
+        if a.numel() != want_len:
+            raise ValueError(f"pdhg_kkt_noalloc: {name} has {a.numel()} entries, expected {want_len}")
+    nnz = a_col_idx.numel()
+    if not all(a.numel() == nnz for a in (a_val, at_col_idx, at_val)):
+        raise ValueError("pdhg_kkt_noalloc: a_col_idx, a_val, at_col_idx and at_val must have the same length")
+    dev = torch.cuda.current_device()
+    if any(a.device.index != dev for a in args):
+        raise ValueError(f"pdhg_kkt_noalloc: every tensor must be on the current device (cuda:{dev})")
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     info = pdhg_kkt_info()
-    st = load().pdhg_kkt_noalloc(int(m), int(n), *[a.data_ptr() for a in args], int(blocks),
+    st = load().pdhg_kkt_noalloc(m, n, *[a.data_ptr() for a in args], int(blocks),
                                  C.c_void_p(stream) if stream else None, C.byref(info))
     _check(st, None)
     return {k: getattr(info, k) for k, _ in pdhg_kkt_info._fields_}

@@ -176,3 +176,27 @@ def test_header_and_library_from_plain_c(lib, tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+
+
+def test_noalloc_host_checks(lib):
+    """pdhg_kkt_noalloc's argument checks run on the host before any device
+    call: sizes out of range, NULL arrays, a NULL out and too many blocks are
+    INVALID (the pointers below are never dereferenced)."""
+    out = P.pdhg_kkt_info()
+    fake = C.c_void_p(16)  # never read: every case fails a host check first
+    arrays = [fake] * 10
+
+    def call(m, n, arrs=arrays, blocks=0, o=C.byref(out)):
+        return lib.pdhg_kkt_noalloc(m, n, *arrs, blocks, None, o)
+
+    for m, n in ((0, 5), (5, 0), (-1, 5), (5, 2 ** 31), (2 ** 31, 5)):
+        assert call(m, n) == P.PDHG_ERR_INVALID, (m, n)
+        assert "2^31" in P.pdhg_last_error(None)
+    for i in range(10):
+        arrs = list(arrays)
+        arrs[i] = None
+        assert call(5, 5, arrs) == P.PDHG_ERR_INVALID, i
+        assert "NULL" in P.pdhg_last_error(None)
+    assert call(5, 5, blocks=1025) == P.PDHG_ERR_INVALID
+    assert call(5, 5, blocks=-1) == P.PDHG_ERR_INVALID
+    assert call(5, 5, o=None) == P.PDHG_ERR_INVALID
