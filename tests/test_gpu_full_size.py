@@ -2,11 +2,17 @@
 configuration the benchmark times (the panel-tiled primal half-step of large
 LPs, CUDA-graph replay):
 
-* the m=1e6, n=3e6, nnz=3e7 LP: the reflected Halpern form in FP64 after two
-  iterations against the oracle's Halpern variant (1e-10), and the FP32 engine
-  after two iterations against the FP64 oracle (FP32 rounding, 1e-4);
+* the m=1e6, n=3e6, nnz=3e7 LP in the benchmark's own configuration (restarts,
+  primal weight, evaluations every 64 iterations, snapshots): 192 FP64
+  iterations against the oracle - three evaluations, two restarts with primal
+  weight updates, every decision equal, the current, average and last-restart
+  points at 1e-10 and the snapshot at 1e-8; the reflected Halpern form in FP64
+  after 100 iterations against the oracle's Halpern variant (1e-10); the FP32
+  engine after 100 iterations against the FP64 oracle (FP32 rounding, error
+  printed, bound 1e-4);
 * the adjoint LP (m=1e5, n=3e5, 6 entries per column): the reverse pass through
-  50 unrolled FP64 iterations against the oracle's reverse pass (1e-9);
+  500 unrolled FP64 iterations (the configured K, checkpoints every 50, so ten
+  recomputed segments) against the oracle's reverse pass (1e-9);
 * the 256-LP batch (m log-uniform in [1e3, 1e5]) solved to 1e-6: every
   instance checked against properties that hold at any size - its solution's
   residuals and gap recomputed on the host with scipy meet the tolerance, and
@@ -24,7 +30,7 @@ import scipy.sparse as sp
 from oracle import pdhg_oracle as O
 from paper_2510_24429_b300 import lpgen
 from paper_2510_24429_b300 import pdhg as P
-from tests.gpu_helpers import SHARED, assert_iterates_close, rel_err
+from tests.gpu_helpers import SHARED, assert_iterates_close, compare_traces, max_rel_err, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -52,6 +58,7 @@ def _fresh(orc, **changes):
     for k in ("x", "y", "x_sum", "y_sum", "x_r", "y_r"):
         setattr(o, k, getattr(orc, k).copy())
     o.trace, o.snapshots, o.polish_log = [], [], []
+    o.next_snapshot, o.eps_target = o.opt.snapshot_every, o.opt.eps_cross  # the schedule of the new options
     return o
 
 
@@ -60,26 +67,75 @@ def _solver(lp, orc, **engine):
     return P.Solver(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, **copts, **engine)
 
 
-def test_large_halpern_fp64_two_iterations(large):
+def test_large_restarted_fp64_matches_oracle(large):
+    """The benchmark's configuration at full size: restarts and primal weight
+    on, evaluations every 64 iterations, a periodic snapshot, panel-tiled
+    primal half-step, CUDA-graph replay. 192 iterations: the evaluations at 64
+    and 128 restart (the artificial rule: t >= 0.36 k) and update omega, the
+    one at 192 decides on the decay rules. Every decision and omega must be
+    equal, the three points agree at 1e-10 and the snapshot taken at iteration
+    128 at 1e-8."""
+    lp, orc0 = large
+    orc = _fresh(orc0, restarts=True, snapshot_every=128)
+    orc.run(192)
+    with _solver(lp, orc) as sol:
+        info = sol.info()
+        assert info["norm_estimate"] == pytest.approx(orc.norm_est, rel=1e-10)
+        st, done = sol.iterate(192)
+        assert done == 192
+        tr = sol.trace()
+        assert len(tr) == len(orc.trace) == 3
+        assert compare_traces(tr, orc.trace) == 3, (tr, orc.trace)
+        for g, o in zip(tr, orc.trace):
+            assert g["omega"] == pytest.approx(o.omega, rel=1e-10)
+            assert g["rel_kkt"] == pytest.approx(o.rel_kkt, rel=1e-9)
+        assert [r["kind"] for r in tr[:2]] != [0, 0] and sol.info()["restarts"] >= 2
+        errs = {}
+        for which, name in ((P.PDHG_CURRENT, "current"), (P.PDHG_AVERAGE, "average"),
+                            (P.PDHG_LAST_RESTART, "last restart")):
+            assert_iterates_close(sol, orc, 1e-10, which)
+            x, y, _ = sol.solution(which)
+            xo, yo, _ = (orc.solution() if which == P.PDHG_CURRENT else
+                         orc.unscale(orc.x_avg, orc.y_avg) if which == P.PDHG_AVERAGE else
+                         orc.unscale(orc.x_r, orc.y_r))
+            errs[name] = (rel_err(x, xo), rel_err(y, yo))
+        print("large LP, restarted FP64 vs oracle after 192 iterations (x, y):",
+              {k: f"{a:.1e} {b:.1e}" for k, (a, b) in errs.items()})
+        cnt, _ = sol.snapshot_poll()
+        assert cnt == len(orc.snapshots) == 1
+        snap = sol.snapshot()
+        ref = orc.snapshots[-1]
+        assert snap["iteration"] == ref["iteration"] == 128
+        for key in ("x", "y", "z"):
+            assert max_rel_err(snap[key], ref[key]) <= 1e-8, key
+
+
+def test_large_halpern_fp64_100_iterations(large):
     lp, orc0 = large
     orc = _fresh(orc0, halpern=True)
-    orc.run(2)
+    orc.run(100)
     with _solver(lp, orc, halpern=1) as sol:
-        sol.iterate(2)
+        sol.iterate(100)
         assert_iterates_close(sol, orc, 1e-10)
+        x, y, _ = sol.solution()
+    xo, yo, _ = orc.solution()
+    print(f"large LP, Halpern FP64 vs oracle after 100 iterations: x {rel_err(x, xo):.1e}, y {rel_err(y, yo):.1e}")
 
 
-def test_large_fp32_two_iterations_close_to_fp64_oracle(large):
+def test_large_fp32_100_iterations_close_to_fp64_oracle(large):
+    """FP32 half-steps against the FP64 oracle: the error is FP32 rounding
+    (unit roundoff 6e-8) carried through 100 iterations; it is printed and
+    bounded by 1e-4."""
     lp, orc0 = large
     orc = _fresh(orc0)
-    orc.run(2)
+    orc.run(100)
     with _solver(lp, orc, precision=P.PDHG_FP32) as sol:
         assert sol.info()["precision_now"] == P.PDHG_FP32
-        sol.iterate(2)
+        sol.iterate(100)
         x, y, _ = sol.solution()
     xo, yo, _ = orc.solution()
     ex, ey = rel_err(x, xo), rel_err(y, yo)
-    print(f"large LP, FP32 vs FP64 oracle after 2 iterations: x {ex:.2e}, y {ey:.2e}")
+    print(f"large LP, FP32 vs FP64 oracle after 100 iterations: x {ex:.2e}, y {ey:.2e}")
     assert 0 < max(ex, ey) and ex < 1e-4 and ey < 1e-4
 
 
@@ -87,7 +143,7 @@ def test_adjoint_lp_reverse_pass_matches_oracle():
     lp = lpgen.adjoint_lp(0)
     orc = O.Oracle(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c,
                    O.Options(restarts=False, primal_weight=False))
-    K = 50
+    K = 500
     rng = np.random.default_rng(3)
     gx, gy = rng.standard_normal(lp.n), rng.standard_normal(lp.m)
     gc_o, gb_o = O.unrolled_adjoint(orc, K, gx, gy)

@@ -12,7 +12,8 @@ import pytest
 from oracle import pdhg_oracle as O
 from paper_2510_24429_b300 import lpgen
 from paper_2510_24429_b300 import pdhg as P
-from tests.gpu_helpers import TINY_PLAIN, assert_iterates_close, compare_traces, max_rel_err, pair, rel_err
+from tests.gpu_helpers import (LONG_RUN_ITERATES, LONG_RUN_OMEGA, LONG_RUN_RELKKT, TINY_PLAIN, assert_iterates_close,
+                               compare_at, compare_traces, max_rel_err, pair, rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -72,10 +73,11 @@ def test_restarted_pdhg_100_iterations(tiny_lp):
 
 
 def test_restarted_trace_and_iterates(tiny_lp):
-    """Decisions must be identical over a long restarted run. The primal-weight
-    update divides by ||x_cand - x_restart||, which is small late in a run, so
-    rounding-level differences in the iterates grow by ||x|| / ||dx|| in omega;
-    omega and the iterates are held to 1e-6 here."""
+    """Decisions must be identical over a long restarted run, and omega,
+    rel. KKT and the iterates stay within 100x (or more) of the spread that a
+    change of summation order alone causes (measured on the oracle:
+    tests/test_oracle_rounding_spread.py). If a near-tie splits the traces,
+    the iterates are compared at the last evaluation both runs agreed on."""
     orc, sol = pair(tiny_lp)
     orc.run(3000, 1e-10)
     sol.iterate(3000, 1e-10)
@@ -84,13 +86,15 @@ def test_restarted_trace_and_iterates(tiny_lp):
     agreed = compare_traces(tr, orc.trace)
     assert agreed >= 20
     for g, o in zip(tr[:agreed], orc.trace[:agreed]):
-        assert g["omega"] == pytest.approx(o.omega, rel=1e-6)
-        assert g["rel_kkt"] == pytest.approx(o.rel_kkt, rel=1e-5)
+        assert g["omega"] == pytest.approx(o.omega, rel=LONG_RUN_OMEGA)
+        assert g["rel_kkt"] == pytest.approx(o.rel_kkt, **LONG_RUN_RELKKT)
     assert sum(1 for r in tr[:agreed] if r["kind"]) >= 3
     if agreed == len(tr):
-        assert_iterates_close(sol, orc, 1e-6)
-        assert_iterates_close(sol, orc, 1e-6, P.PDHG_AVERAGE)
-        assert_iterates_close(sol, orc, 1e-6, P.PDHG_LAST_RESTART)
+        assert_iterates_close(sol, orc, LONG_RUN_ITERATES)
+        assert_iterates_close(sol, orc, LONG_RUN_ITERATES, P.PDHG_AVERAGE)
+        assert_iterates_close(sol, orc, LONG_RUN_ITERATES, P.PDHG_LAST_RESTART)
+    else:
+        compare_at(tiny_lp, tr[agreed - 1]["iteration"], 1e-10)
 
 
 def test_converged_objective(tiny_lp):
@@ -168,8 +172,13 @@ def test_resume_equals_single_call(tiny_lp):
     for chunk in (1, 63, 200, 736):
         sol.iterate(chunk)
     assert sol.info()["iterations"] == 1000
-    if compare_traces(sol.trace(), orc.trace) == len(orc.trace):
-        assert_iterates_close(sol, orc, 1e-6)
+    tr = sol.trace()
+    agreed = compare_traces(tr, orc.trace)
+    if agreed == len(orc.trace):
+        assert_iterates_close(sol, orc, LONG_RUN_ITERATES)
+    else:
+        assert agreed > 0
+        compare_at(tiny_lp, tr[agreed - 1]["iteration"], 0.0)
 
 
 # ---------------------------------------------------------------------------
@@ -227,8 +236,12 @@ def test_edge_shapes(lp):
     orc, sol = pair(lp)
     orc.run(640, 1e-9)
     sol.iterate(640, 1e-9)
-    if compare_traces(sol.trace(), orc.trace) == len(orc.trace):
-        assert_iterates_close(sol, orc, 1e-7)
+    tr = sol.trace()
+    agreed = compare_traces(tr, orc.trace)
+    if agreed == len(orc.trace):
+        assert_iterates_close(sol, orc, LONG_RUN_ITERATES)
+    elif agreed > 0:
+        compare_at(lp, tr[agreed - 1]["iteration"], 1e-9)
 
 
 # ---------------------------------------------------------------------------

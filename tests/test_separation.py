@@ -51,7 +51,7 @@ def test_bench_imports_the_oracle_only_inside_its_cpu_legs():
             for node in ast.walk(fn):
                 if isinstance(node, ast.ImportFrom) and node.module and node.module.split(".")[0] == "oracle":
                     users.add(fn.name)
-    assert users == {"oracle_rate", "run_reference"}, users
+    assert users == {"oracle_seconds_per_iteration", "_oracle_replica", "run_reference"}, users
 
 
 def test_nothing_committed_uses_the_working_folder():
