@@ -402,13 +402,30 @@ def run_batch(P, torch, count=256, tol=1e-6, seed=0):
         ih = bh.info()
     halpern = {"seconds_to_all_converged": sec_h, "all_converged": bool(ih["converged"].all()),
                "iterations_max": int(ih["iterations"].max()), "iterations_median": float(np.median(ih["iterations"]))}
+    # the same batch as ONE cooperative launch per solve (persistent = 2),
+    # replayed from a CUDA graph; both forms of the iteration
+    coop = {}
+    for form, extra in (("pdlp", {}), ("halpern", {"halpern": 1})):
+        with P.BatchSolver(lps, persistent=2, **layout, **extra) as bc:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            stc, _ = bc.iterate(200_000, tol)
+            torch.cuda.synchronize()
+            sec_c = time.perf_counter() - t0
+            ic, ec = bc.info(), bc.engine_info()
+        itc = ic["iterations"].astype(np.float64)
+        gbs_c = float((itc * per_iter_bytes).sum() / sec_c / 1e9)
+        coop[form] = {"seconds_to_all_converged": sec_c, "all_converged": bool(ic["converged"].all()),
+                      "iterations_max": int(itc.max()), "hbm_gbs_active": gbs_c, "hbm_frac_active": gbs_c / peak,
+                      "gpu_launches": ec["kernel_launches"], "graph_launches": ec["graph_launches"],
+                      "grid_blocks": ec["persistent_grid"]}
     return {"workload": f"{count} LPs, m log-uniform in [1e3, 1e5] (sum {sum(sizes)}), n = 2.5 m, 5 per column, "
                         f"nnz {sum(lp.nnz for lp in lps)}, FP64, each to rel. KKT {tol:g}",
             "seconds_to_all_converged": sec, "setup_s": setup_s, "all_converged": bool(info["converged"].all()),
             "iterations_max": int(it.max()), "iterations_median": float(np.median(it)),
             "aggregate_iters_per_s": float(it.sum() / sec), "hbm_gbs_active": gbs, "hbm_frac_active": gbs / peak,
             "gpu_launches": eng["kernel_launches"], "autotuned_layout": layout, "autotune_s": tune_s,
-            "halpern": halpern}
+            "halpern": halpern, "one_cooperative_launch": coop}
 
 
 # ---------------------------------------------------------------------------
@@ -684,6 +701,23 @@ def run_ours(args):
                                  "achieved_gbs": (bytes_dual / (t_dual / 1000.0) if kname == pname
                                                   else bytes_primal / (t_primal / 1000.0)) / 1e9}}
     iter_bytes = bytes_primal + bytes_dual
+    # the FP64 pipe as a second bound (FP64 runs only): algorithmic FP64
+    # operations per launch - one FMA per stored entry, plus 5 per column in
+    # the primal update (c - g, x - tau (.), the projection, 2x' - x, the
+    # running sum) and 3 per row in the dual one (b - h, y + sigma (.), the
+    # running sum) - against the FMA rate measured on this GPU in this run
+    if args.precision == "fp64":
+        fma_rate, fma_ms = P.pdhg_fp64_fma_rate(stream.cuda_stream)
+        ops = {pname: nnz + 5 * n, dname: nnz + 3 * m}
+        times = {pname: t_primal, dname: t_dual}
+        fp64 = {name_: {"ops_per_launch": ops[name_], "ms_per_launch": times[name_],
+                        "achieved": ops[name_] / (times[name_] / 1000.0) / 1e9,
+                        "frac": ops[name_] / (times[name_] / 1000.0) / fma_rate} for name_ in ops}
+        roofline["fp64"] = {"bound": "fp64", "unit": "G FP64 ops/s", "peak": fma_rate / 1e9,
+                            "peak_kind": "measured FP64 FMA lane rate (pdhg_fp64_fma_rate, this run)",
+                            "nominal_peak": 625.0, "kernels": fp64,
+                            "frac": fp64[kname]["frac"], "achieved": fp64[kname]["achieved"]}
+        roofline["binding"] = "fp64" if roofline["fp64"]["frac"] > roofline["frac"] else "hbm"
 
     extras = {}
     if not args.skip_extras and rank == 0:

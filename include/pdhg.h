@@ -101,14 +101,20 @@ typedef struct {
                              take over when the FP32 phase stalls (no 10% gain in 16384 iterations) */
   int long_row_min;       /* rows with at least this many entries get a warp each (128) */
   int rows_per_thread;    /* most rows one thread reduces at once in short rows: 1, 2 or 4 (4) */
-  int dual_hot_cols;      /* entries of xbar the dual step stages in shared memory, 0 = off; <= 24576 (0) */
+  int dual_hot_cols;      /* entries of xbar (the first ones, i.e. the longest columns of A) the dual step
+                             stages in shared memory: 0 = off; at most 56320, and at most 28160 are staged in
+                             FP64 phases (0) */
   int record_for_backward; /* 1: keep checkpoints for pdhg_backward; needs restarts = 0, primal_weight = 0,
                               precision FP64 or FP32 (0) */
   int64_t checkpoint_every; /* iterations between adjoint checkpoints (50) */
   int persistent;         /* 1: run the solve loop of each LP in one thread block: a single launch does the
                              iterations, evaluations, restarts and termination test with the LP's vectors in
                              shared memory (LPs with 7n + 6m <= 28672, i.e. up to ~224 KiB of vectors; FP64,
-                             no recording, no kernel timing); 0: two launches per iteration (0) */
+                             no recording, no kernel timing); 2 (batches): one cooperative launch over the whole
+                             GPU runs every instance's iterations, evaluations, restarts and termination test,
+                             the phases separated by grid-wide barriers whose waits are bounded by
+                             barrier_cycles (replayed from a CUDA graph when use_graphs = 1; no kernel timing);
+                             0: two launches per iteration (0) */
   int step_block;         /* threads per block of the step and evaluation kernels: 128, 256 or 512 (256) */
   int primal_panels;      /* panel-tiled primal half-step: y is cut into panels that fit in shared memory and
                              the long rows of A^T (columns with >= long_row_min entries) into per-panel
@@ -134,7 +140,11 @@ typedef struct {
                              goes on unchanged. Single LPs, FP64 phases only (in PDHG_MIXED after the switch),
                              not persistent, no recording (0) */
   int polish_div;         /* polishing phase budget divisor (8) */
-  int reserved[2];
+  int singleton_order;    /* 1: number the columns with one entry by the row of that entry (single LPs), so
+                             that the step kernels gather them nearly in order; 0: by the caller's order (0) */
+  int reserved;
+  int64_t barrier_cycles; /* persistent = 2: clock cycles one grid-barrier wait may last before the launch
+                             gives up with PDHG_ERR_TIMEOUT; 0 = 2^31 (about a second) (0) */
 } pdhg_options;
 
 /* Scalars of one point on the problem as given (unscaled), all FP64.
@@ -171,6 +181,8 @@ typedef struct {
   int64_t feas_polish_attempts;   /* feasibility polishing attempts so far */
   int64_t feas_polish_iterations; /* iterations run in polishing phases (not counted in `iterations`) */
   int feas_polished;              /* 1: the current iterate is a polished pair (x_p, y_d) that passed the test */
+  int persistent_grid;            /* persistent = 2: blocks of the cooperative launch (0 before the first) */
+  int64_t graph_launches;         /* CUDA-graph launches by pdhg_iterate so far */
 } pdhg_info;
 
 /* One feasibility polishing attempt. */
@@ -401,8 +413,22 @@ PDHG_API pdhg_status pdhg_autotune(int count, const pdhg_lp_desc* lps, const pdh
  * cap - 1, or bad sizes, row pointers or column indices. */
 PDHG_API pdhg_status pdhg_profile_key(int count, const pdhg_lp_desc* lps, int precision, char* buf, int64_t cap);
 
+/* The current device's FP64 fused multiply-add throughput (no counterpart in
+ * the paper: a measurement aid). The FP64 iteration issues one FP64 FMA per
+ * stored matrix entry and a few FP64 operations per row and column, and this
+ * GPU runs FP64 at a small fraction of its FP32 rate, so the FP64 pipe is a
+ * second bound of the FP64 step kernels beside HBM bandwidth. A full-occupancy
+ * grid runs independent FMA chains for a fixed count (about 0.1 s on a B300),
+ * timed with CUDA events on cuda_stream (NULL = legacy default stream); the
+ * call waits for it. *fma_per_s gets FMAs (lane operations) per second, *ms
+ * (nullable) the kernel's time. Allocates no device memory. INVALID for a
+ * NULL fma_per_s, CUDA from the device; pdhg_last_error(NULL) describes the
+ * failure. */
+PDHG_API pdhg_status pdhg_fp64_fma_rate(void* cuda_stream, double* fma_per_s, double* ms);
+
 /* Description of the last failure of ctx, or of the last failed context-free
- * call (pdhg_create, pdhg_kkt_noalloc) when ctx is NULL. Never NULL. */
+ * call (pdhg_create, pdhg_kkt_noalloc, pdhg_fp64_fma_rate) when ctx is NULL. Never
+ * NULL. */
 PDHG_API const char* pdhg_last_error(const pdhg_ctx* ctx);
 
 #ifdef __cplusplus

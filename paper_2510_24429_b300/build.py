@@ -8,7 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpdhg.so")
-SOURCES = ["kernels.cu", "layout.cu", "persistent.cu", "pdhg_api.cu", "kkt_noalloc.cu", "autotune.cu"]
+SOURCES = ["kernels.cu", "layout.cu", "persistent.cu", "pdhg_api.cu", "kkt_noalloc.cu", "autotune.cu",
+           "fp64_rate.cu"]
 HEADERS = ["common.cuh", "kernels.cuh", "decide.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -127,17 +127,12 @@ __device__ __forceinline__ void hyb_rows(const Hyb& H, Op& op) {
 }
 
 // How the dot-product visitor reads the gathered vector: through L1 from
-// global memory, or, for the first `hot` entries, from a shared-memory copy.
+// global memory (GlobalGather), or, for the first `hot` entries, from a
+// shared-memory copy (HotGatherT, below).
 template <class T>
 struct GlobalGather {
   const T* __restrict__ vec;
   __device__ __forceinline__ T operator()(int c) const { return __ldg(vec + c); }
-};
-struct HotGather {
-  const double* __restrict__ vec;
-  const double* hot_vals;  // shared memory copy of vec[0, hot)
-  int hot;
-  __device__ __forceinline__ double operator()(int c) const { return c < hot ? hot_vals[c] : __ldg(vec + c); }
 };
 
 // Dot-product visitor (hot path): acc_r = sum over row r of a_rk vec[col_k].
@@ -233,13 +228,20 @@ __device__ __forceinline__ void unit_dot(const Hyb& H, const T* __restrict__ val
 }
 
 // every unit of H from unit u_begin on, one warp per unit in a grid-stride loop
+// over a grid of nblk blocks, of which this block is block bid (by default the
+// launch's own grid; the persistent batch solve passes the virtual block it
+// stands in for)
 template <class T, class Op, class G>
 __device__ __forceinline__ void hyb_dot(const Hyb& H, const T* __restrict__ vals, const G& gather, Op& op,
-                                        int u_begin = 0) {
+                                        int u_begin = 0, int bid = -1, int nblk = 0) {
+  if (bid < 0) {
+    bid = (int)blockIdx.x;
+    nblk = (int)gridDim.x;
+  }
   const unsigned long long pol = stream_policy();
   const int lane = threadIdx.x & 31;
-  const int gwarp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-  const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
+  const int gwarp = (int)(((unsigned)bid * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)(((unsigned)nblk * blockDim.x) >> 5);
   for (int u = u_begin + gwarp; u < H.n_units; u += nwarps) unit_dot(H, vals, u, gather, op, pol, lane);
 }
 
@@ -666,20 +668,56 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STE
   hyb_dot(A, vals, GlobalGather<T>{xbar}, op);
 }
 
-// The dual step as a persistent kernel (one 1024-thread block per SM) that
+// The dual step as a persistent kernel (one HOT_TPB-thread block per SM) that
 // first copies xbar[0, hot) into shared memory. With the variables numbered by
-// decreasing column length, these are the most frequently gathered entries,
-// and their gathers then stay off the L1-to-L2 request path that bounds the
-// random gathers.
-__global__ void __launch_bounds__(HOT_TPB, 1) k_dual_step_hot(Hyb A, const double* __restrict__ xbar, int hot,
-                                                             const double* __restrict__ bh, double* __restrict__ y,
-                                                             double* __restrict__ ysum,
-                                                             const DevState* __restrict__ st, int accumulate) {
-  extern __shared__ double sh_hot[];
-  for (int i = threadIdx.x; i < hot; i += blockDim.x) sh_hot[i] = xbar[i];
+// decreasing column length, these are the most frequently gathered entries
+// (on the large Zipf LP the first 27,648 columns hold 55% of A's entries, the
+// first 56,320 hold 75%), and their gathers then stay off the L1-to-L2
+// request path that bounds the random gathers; the others go through L1.
+// The copy is issued as 16-byte cp.async transfers, all in flight at once.
+template <class T>
+struct HotGatherT {
+  const T* __restrict__ vec;
+  const T* hot_vals;  // shared memory copy of vec[0, hot)
+  int hot;
+  __device__ __forceinline__ T operator()(int c) const { return c < hot ? hot_vals[c] : __ldg(vec + c); }
+};
+
+template <class T>
+__device__ __forceinline__ const T* stage_hot(const T* __restrict__ xbar, int hot) {
+  extern __shared__ __align__(16) unsigned char hot_smem[];
+  T* sh = reinterpret_cast<T*>(hot_smem);
+  constexpr int PER = 16 / (int)sizeof(T);
+  const int nv = (reinterpret_cast<unsigned long long>(xbar) & 15ull) == 0 ? hot / PER : 0;
+  const unsigned dst0 = (unsigned)__cvta_generic_to_shared(sh);
+  for (int v = threadIdx.x; v < nv; v += blockDim.x)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst0 + 16u * (unsigned)v), "l"(xbar + v * PER)
+                 : "memory");
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (int t = nv * PER + threadIdx.x; t < hot; t += blockDim.x) sh[t] = xbar[t];
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
-  DualOp<double> op{bh, y, ysum, st->sigma, accumulate};
-  hyb_dot(A, A.v, HotGather{xbar, sh_hot, hot}, op);
+  return sh;
+}
+
+template <class T>
+__global__ void __launch_bounds__(HOT_TPB, 1)
+    k_dual_step_hot(Hyb A, const T* __restrict__ vals, const T* __restrict__ xbar, int hot,
+                    const T* __restrict__ bh, T* __restrict__ y, T* __restrict__ ysum,
+                    const DevState* __restrict__ st, int accumulate) {
+  const T* sh = stage_hot(xbar, hot);
+  DualOp<T> op{bh, y, ysum, (T)st->sigma, accumulate};
+  hyb_dot(A, vals, HotGatherT<T>{xbar, sh, hot}, op);
+}
+
+template <class T>
+__global__ void __launch_bounds__(HOT_TPB, 1)
+    k_dual_step_hot_halpern(Hyb A, const T* __restrict__ vals, const T* __restrict__ xbar, int hot,
+                            const T* __restrict__ bh, T* __restrict__ y, const T* __restrict__ yr,
+                            const DevState* __restrict__ st, int it) {
+  const T* sh = stage_hot(xbar, hot);
+  DualHalpernOp<T> op{bh, y, yr, (T)st->sigma, (T)halpern_weight(st, it), (T)st->rho};
+  hyb_dot(A, vals, HotGatherT<T>{xbar, sh, hot}, op);
 }
 
 __global__ void k_add_counters(DevState* st, long long dk) {
@@ -731,13 +769,15 @@ struct EvalDualOp {
   }
 };
 
-__global__ void __launch_bounds__(STEP_TPB_MAX) k_eval_dual(Hyb At, const double* __restrict__ py,
-                                                   const double* __restrict__ ch, const double* __restrict__ idc,
-                                                   const double* __restrict__ px, const double* __restrict__ xr,
-                                                   double* __restrict__ partials, const DevState* __restrict__ sts,
-                                                   const int* __restrict__ binst) {
-  if (binst && sts[binst[blockIdx.x]].frozen) {
-    if (threadIdx.x < 6) partials[(size_t)blockIdx.x * NQ + Q_RD2S + threadIdx.x] = 0.0;
+// the evaluation partial sums of the rows of At in block bid of nblk (one
+// row of partials per block; blocks of a frozen batch instance write zeros)
+template <class G>
+__device__ __forceinline__ void eval_dual_block(const Hyb& At, const G& gather_py, const double* __restrict__ ch,
+                                                const double* __restrict__ idc, const double* __restrict__ px,
+                                                const double* __restrict__ xr, double* __restrict__ partials,
+                                                bool frozen, int bid, int nblk) {
+  if (frozen) {
+    if (threadIdx.x < 6) partials[(size_t)bid * NQ + Q_RD2S + threadIdx.x] = 0.0;
     return;
   }
   EvalDualOp op;
@@ -745,11 +785,11 @@ __global__ void __launch_bounds__(STEP_TPB_MAX) k_eval_dual(Hyb At, const double
   op.idc = idc;
   op.px = px;
   op.xr = xr;
-  hyb_dot(At, At.v, GlobalGather<double>{py}, op);
+  hyb_dot(At, At.v, gather_py, op, 0, bid, nblk);
   const bool mx[6] = {false, false, true, false, false, false};
   block_reduce<6>(op.acc, mx);
   if (threadIdx.x == 0) {
-    double* p = partials + (size_t)blockIdx.x * NQ;
+    double* p = partials + (size_t)bid * NQ;
     p[Q_RD2S] = op.acc[0];
     p[Q_RD2U] = op.acc[1];
     p[Q_RDINF] = op.acc[2];
@@ -757,6 +797,15 @@ __global__ void __launch_bounds__(STEP_TPB_MAX) k_eval_dual(Hyb At, const double
     p[Q_XZ] = op.acc[4];
     p[Q_DX2] = op.acc[5];
   }
+}
+
+__global__ void __launch_bounds__(STEP_TPB_MAX) k_eval_dual(Hyb At, const double* __restrict__ py,
+                                                   const double* __restrict__ ch, const double* __restrict__ idc,
+                                                   const double* __restrict__ px, const double* __restrict__ xr,
+                                                   double* __restrict__ partials, const DevState* __restrict__ sts,
+                                                   const int* __restrict__ binst) {
+  eval_dual_block(At, GlobalGather<double>{py}, ch, idc, px, xr, partials, binst && sts[binst[blockIdx.x]].frozen,
+                  (int)blockIdx.x, (int)gridDim.x);
 }
 
 struct EvalPrimalOp {
@@ -783,13 +832,13 @@ struct EvalPrimalOp {
   }
 };
 
-__global__ void __launch_bounds__(STEP_TPB_MAX) k_eval_primal(Hyb A, const double* __restrict__ px,
-                                                     const double* __restrict__ bh, const double* __restrict__ idr,
-                                                     const double* __restrict__ py, const double* __restrict__ yr,
-                                                     double* __restrict__ partials, const DevState* __restrict__ sts,
-                                                     const int* __restrict__ binst) {
-  if (binst && sts[binst[blockIdx.x]].frozen) {
-    if (threadIdx.x < 5) partials[(size_t)blockIdx.x * NQ + Q_RP2S + threadIdx.x] = 0.0;
+template <class G>
+__device__ __forceinline__ void eval_primal_block(const Hyb& A, const G& gather_px, const double* __restrict__ bh,
+                                                  const double* __restrict__ idr, const double* __restrict__ py,
+                                                  const double* __restrict__ yr, double* __restrict__ partials,
+                                                  bool frozen, int bid, int nblk) {
+  if (frozen) {
+    if (threadIdx.x < 5) partials[(size_t)bid * NQ + Q_RP2S + threadIdx.x] = 0.0;
     return;
   }
   EvalPrimalOp op;
@@ -797,17 +846,26 @@ __global__ void __launch_bounds__(STEP_TPB_MAX) k_eval_primal(Hyb A, const doubl
   op.idr = idr;
   op.py = py;
   op.yr = yr;
-  hyb_dot(A, A.v, GlobalGather<double>{px}, op);
+  hyb_dot(A, A.v, gather_px, op, 0, bid, nblk);
   const bool mx[5] = {false, false, true, false, false};
   block_reduce<5>(op.acc, mx);
   if (threadIdx.x == 0) {
-    double* p = partials + (size_t)blockIdx.x * NQ;
+    double* p = partials + (size_t)bid * NQ;
     p[Q_RP2S] = op.acc[0];
     p[Q_RP2U] = op.acc[1];
     p[Q_RPINF] = op.acc[2];
     p[Q_BY] = op.acc[3];
     p[Q_DY2] = op.acc[4];
   }
+}
+
+__global__ void __launch_bounds__(STEP_TPB_MAX) k_eval_primal(Hyb A, const double* __restrict__ px,
+                                                     const double* __restrict__ bh, const double* __restrict__ idr,
+                                                     const double* __restrict__ py, const double* __restrict__ yr,
+                                                     double* __restrict__ partials, const DevState* __restrict__ sts,
+                                                     const int* __restrict__ binst) {
+  eval_primal_block(A, GlobalGather<double>{px}, bh, idr, py, yr, partials,
+                    binst && sts[binst[blockIdx.x]].frozen, (int)blockIdx.x, (int)gridDim.x);
 }
 
 // warp q sums quantity q over the blocks in a fixed order
@@ -1202,6 +1260,213 @@ __global__ void k_pack_y(const int* __restrict__ perm, const double* __restrict_
     oy[perm[i]] = dr[i] * py[i];
 }
 
+// ---------------------------------------------------------------------------
+// A whole batch in one cooperative launch (option persistent = 2; no
+// counterpart in the paper): every instance's iterations, evaluations,
+// restart and primal-weight decisions and termination test, with grid-wide
+// barriers between the phases instead of kernel boundaries. The grid's blocks
+// take the batch's blocks (the unit-grid blocks of the multi-launch engine,
+// each belonging to one instance) in turn, and every block runs the same
+// per-block code as the multi-launch kernels, so the two forms compute the
+// same numbers in the same order. Vectors written during the launch are
+// gathered with coherent loads (not the read-only path the separate kernels
+// use).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_acquire_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier. Thread 0 of each block arrives on a counter; the last to
+// arrive resets it and advances the generation; the others wait for the
+// generation to change, for at most `budget` clock cycles and only while no
+// block has reported an error. Every block of a cooperative launch is
+// resident, so the wait ends unless a block has stopped early. Returns false
+// in every thread of the block when the wait gave up (the first block to give
+// up records BATCH_ERR_TIMEOUT and the barrier's tag) or an error is set: the
+// caller then returns, and so does every other block at its next barrier.
+__device__ bool grid_barrier(BatchCtl* c, long long budget, int tag) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = ld_acquire_u32(&c->gen);
+    __threadfence();
+    if (atomicAdd(&c->arrive, 1u) == gridDim.x - 1) {
+      atomicExch(&c->arrive, 0u);
+      __threadfence();
+      atomicAdd(&c->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire_u32(&c->gen) == g) {
+        if (ld_acquire_s32(&c->error) != BATCH_ERR_NONE) {
+          ok = 0;
+          break;
+        }
+        if (clock64() - t0 > budget) {
+          if (atomicCAS(&c->error, BATCH_ERR_NONE, BATCH_ERR_TIMEOUT) == BATCH_ERR_NONE) c->where = tag;
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    if (ok && ld_acquire_s32(&c->error) != BATCH_ERR_NONE) ok = 0;
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// a vector written by other blocks of the same launch: plain (coherent) loads
+template <class T>
+struct CoherentGather {
+  const T* vec;
+  __device__ __forceinline__ T operator()(int c) const { return vec[c]; }
+};
+
+__global__ void __launch_bounds__(STEP_TPB_MAX, 2) k_batch_solve(BatchArgs a) {
+  BatchCtl* ctl = a.ctl;
+  const long long budget = ctl->budget, k0 = ctl->k0, max_iters = ctl->max_iters;
+  const int G = (int)gridDim.x, nvb = a.nvb, E = a.eval_every;
+  const int tid = (int)threadIdx.x, tpb = (int)blockDim.x;
+  int tag = 0;
+  long long done = 0;
+  while (done < max_iters) {
+    const long long nb = min((long long)E - (k0 + done) % E, max_iters - done);
+    for (long long it = 0; it < nb; ++it) {
+      // primal half-step over every block of an active instance
+      for (int vb = blockIdx.x; vb < nvb; vb += G) {
+        const DevState* st = a.sts + a.binst[vb];
+        if (st->frozen) continue;
+        if (a.halpern) {
+          PrimalHalpernOp<double> op{a.ch, a.x, a.xbar, a.xr, st->tau, halpern_weight(st, (int)it), st->rho};
+          hyb_dot(a.At, a.At.v, CoherentGather<double>{a.y}, op, 0, vb, nvb);
+        } else {
+          PrimalOp<double> op{a.ch, a.x, a.xbar, a.xsum, st->tau, a.restarts};
+          hyb_dot(a.At, a.At.v, CoherentGather<double>{a.y}, op, 0, vb, nvb);
+        }
+      }
+      if (!grid_barrier(ctl, budget, ++tag)) return;
+      // dual half-step
+      for (int vb = blockIdx.x; vb < nvb; vb += G) {
+        const DevState* st = a.sts + a.binst[vb];
+        if (st->frozen) continue;
+        if (a.halpern) {
+          DualHalpernOp<double> op{a.bh, a.y, a.yr, st->sigma, halpern_weight(st, (int)it), st->rho};
+          hyb_dot(a.A, a.A.v, CoherentGather<double>{a.xbar}, op, 0, vb, nvb);
+        } else {
+          DualOp<double> op{a.bh, a.y, a.ysum, st->sigma, a.restarts};
+          hyb_dot(a.A, a.A.v, CoherentGather<double>{a.xbar}, op, 0, vb, nvb);
+        }
+      }
+      if (!grid_barrier(ctl, budget, ++tag)) return;
+    }
+    done += nb;
+    if ((k0 + done) % E != 0) {
+      // a launch that ends inside an evaluation period: only the counters
+      for (int i = blockIdx.x * tpb + tid; i < a.count; i += G * tpb) {
+        DevState* st = a.sts + i;
+        if (st->frozen) continue;
+        st->k += nb;
+        st->t += nb;
+      }
+      break;
+    }
+    // evaluation 1: the averages since the last restart (t after this period)
+    if (a.restarts && !a.halpern) {
+      for (int i = 0; i < a.count; ++i) {
+        const DevState* st = a.sts + i;
+        if (st->frozen) continue;
+        const long long t = st->t + nb;
+        const double inv = t > 0 ? 1.0 / (double)t : 0.0;
+        for (int j = a.xoff[i] + blockIdx.x * tpb + tid; j < a.xoff[i + 1]; j += G * tpb)
+          a.xavg[j] = t > 0 ? a.xsum[j] * inv : a.x[j];
+        for (int r = a.yoff[i] + blockIdx.x * tpb + tid; r < a.yoff[i + 1]; r += G * tpb)
+          a.yavg[r] = t > 0 ? a.ysum[r] * inv : a.y[r];
+      }
+      if (!grid_barrier(ctl, budget, ++tag)) return;
+    }
+    // evaluation 2: per-block partial sums of the average and the current point
+    for (int vb = blockIdx.x; vb < nvb; vb += G) {
+      const bool frozen = a.sts[a.binst[vb]].frozen != 0;
+      if (a.restarts && !a.halpern) {
+        eval_dual_block(a.At, CoherentGather<double>{a.yavg}, a.ch, a.idc, a.xavg, a.xr, a.part_avg, frozen, vb, nvb);
+        eval_primal_block(a.A, CoherentGather<double>{a.xavg}, a.bh, a.idr, a.yavg, a.yr, a.part_avg, frozen, vb,
+                          nvb);
+      }
+      eval_dual_block(a.At, CoherentGather<double>{a.y}, a.ch, a.idc, a.x, a.xr, a.part_cur, frozen, vb, nvb);
+      eval_primal_block(a.A, CoherentGather<double>{a.x}, a.bh, a.idr, a.y, a.yr, a.part_cur, frozen, vb, nvb);
+    }
+    if (!grid_barrier(ctl, budget, ++tag)) return;
+    // evaluation 3: per-instance sums (warp q sums quantity q over the
+    // instance's blocks in a fixed order), then the decisions
+    for (int i = blockIdx.x; i < a.count; i += G) {
+      DevState* st = a.sts + i;
+      if (st->frozen) continue;
+      const int warp = tid >> 5, lane = tid & 31;
+      for (int q2 = warp; q2 < 2 * NQ; q2 += tpb >> 5) {
+        const bool avg = q2 >= NQ;
+        if (avg && !(a.restarts && !a.halpern)) continue;
+        const int q = avg ? q2 - NQ : q2;
+        const double* part = avg ? a.part_avg : a.part_cur;
+        const bool is_max = (q == Q_RDINF || q == Q_RPINF);
+        double acc = 0.0;
+        for (int b = a.bstart[i] + lane; b < a.bstart[i + 1]; b += 32) {
+          const double v = part[(size_t)b * NQ + q];
+          acc = is_max ? fmax(acc, v) : acc + v;
+        }
+        acc = is_max ? warp_max(acc) : warp_sum(acc);
+        if (lane == 0) (avg ? st->avg : st->cur).q[q] = acc;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        st->k += nb;
+        st->t += nb;
+        decide_one(st, nullptr);
+        if (st->converged) {
+          st->frozen = 1;
+          atomicSub(&ctl->active, 1);
+        } else if (st->numeric) {
+          atomicCAS(&ctl->error, BATCH_ERR_NONE, BATCH_ERR_NUMERIC);
+        }
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(ctl, budget, ++tag)) return;
+    // evaluation 4: restarts (and the average taken at convergence)
+    for (int i = 0; i < a.count; ++i) {
+      const int mode = a.sts[i].apply_mode;
+      if (mode == APPLY_NONE) continue;
+      const bool take_avg = mode == APPLY_RESTART_AVG || mode == APPLY_TAKE_AVG, restart = mode != APPLY_TAKE_AVG;
+      for (int j = a.xoff[i] + blockIdx.x * tpb + tid; j < a.xoff[i + 1]; j += G * tpb) {
+        if (take_avg) a.x[j] = a.xavg[j];
+        if (restart) {
+          a.xr[j] = a.x[j];
+          a.xsum[j] = 0.0;
+        }
+      }
+      for (int r = a.yoff[i] + blockIdx.x * tpb + tid; r < a.yoff[i + 1]; r += G * tpb) {
+        if (take_avg) a.y[r] = a.yavg[r];
+        if (restart) {
+          a.yr[r] = a.y[r];
+          a.ysum[r] = 0.0;
+        }
+      }
+    }
+    if (!grid_barrier(ctl, budget, ++tag)) return;
+    if (ld_acquire_s32(&ctl->active) == 0) break;
+  }
+  if (blockIdx.x == 0 && tid == 0) ctl->done = done;
+}
+
 }  // namespace
 
 void launch_row_absmax(const Hyb& M, double* out, int grid, cudaStream_t s) {
@@ -1321,10 +1586,19 @@ template void launch_dual_step_halpern<double>(const Hyb&, const double*, const 
                                                const int*);
 template void launch_dual_step_halpern<float>(const Hyb&, const float*, const float*, const float*, float*,
                                               const float*, const DevState*, int, int, cudaStream_t, int, const int*);
-void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,
-                          const DevState* st, int accumulate, int grid, cudaStream_t s) {
-  k_dual_step_hot<<<grid, HOT_TPB, (size_t)hot * sizeof(double), s>>>(A, xbar, hot, bh, y, ysum, st, accumulate);
+template <class T>
+void launch_dual_step_hot(const Hyb& A, const T* vals, const T* xbar, int hot, const T* bh, T* y, T* ysum,
+                          const DevState* st, int accumulate, int grid, cudaStream_t s, int halpern_it) {
+  const size_t smem = (size_t)hot * sizeof(T);
+  if (halpern_it >= 0)
+    k_dual_step_hot_halpern<T><<<grid, HOT_TPB, smem, s>>>(A, vals, xbar, hot, bh, y, ysum, st, halpern_it);
+  else
+    k_dual_step_hot<T><<<grid, HOT_TPB, smem, s>>>(A, vals, xbar, hot, bh, y, ysum, st, accumulate);
 }
+template void launch_dual_step_hot<double>(const Hyb&, const double*, const double*, int, const double*, double*,
+                                           double*, const DevState*, int, int, cudaStream_t, int);
+template void launch_dual_step_hot<float>(const Hyb&, const float*, const float*, int, const float*, float*, float*,
+                                          const DevState*, int, int, cudaStream_t, int);
 void launch_add_counters(DevState* st, long long dk, cudaStream_t s) { k_add_counters<<<1, 1, 0, s>>>(st, dk); }
 void launch_make_average(const double* xs, const double* ys, const double* x, const double* y, double* xa,
                          double* ya, int n, int m, const DevState* st, int grid, cudaStream_t s) {
@@ -1356,6 +1630,20 @@ void launch_apply_b(const DevState* sts, double* x, double* y, const double* xa,
                     double* yr, double* xs, double* ys, const int* xoff, const int* yoff, int count, int gx,
                     cudaStream_t s) {
   k_apply_b<<<dim3(gx, count), TPB, 0, s>>>(sts, x, y, xa, ya, xr, yr, xs, ys, xoff, yoff);
+}
+cudaError_t batch_solve_grid(int tpb, int* grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve, tpb, 0);
+  if (e != cudaSuccess) return e;
+  *grid = sms * std::max(per_sm, 1);
+  return cudaSuccess;
+}
+cudaError_t launch_batch_solve(const BatchArgs& a, int grid, int tpb, cudaStream_t s) {
+  BatchArgs args = a;
+  void* params[] = {&args};
+  return cudaLaunchCooperativeKernel((const void*)k_batch_solve, dim3(grid), dim3(tpb), params, 0, s);
 }
 void launch_sumsq_b(const double* v, const int* off, int count, double* out, int ostride, cudaStream_t s) {
   k_sumsq_b<<<count, TPB, 0, s>>>(v, off, out, ostride);
@@ -1444,8 +1732,10 @@ void prefer_l1_for_step_kernels() {
   cudaFuncSetAttribute(k_primal_short_combine<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_primal_short_combine_halpern<double>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_primal_short_combine_halpern<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-  cudaFuncSetAttribute(k_dual_step_hot, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(HOT_MAX * sizeof(double)));
+  cudaFuncSetAttribute(k_dual_step_hot<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, HOT_SMEM_MAX);
+  cudaFuncSetAttribute(k_dual_step_hot<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, HOT_SMEM_MAX);
+  cudaFuncSetAttribute(k_dual_step_hot_halpern<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, HOT_SMEM_MAX);
+  cudaFuncSetAttribute(k_dual_step_hot_halpern<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, HOT_SMEM_MAX);
 }
 
 }  // namespace pdhg

@@ -8,8 +8,9 @@ namespace pdhg {
 constexpr int TPB = 256;  // threads per block of every row kernel
 constexpr int WARPS_PER_BLOCK = TPB / 32;
 constexpr int STEP_TPB_MAX = 512;  // largest block of the step and evaluation kernels (option step_block)
-constexpr int HOT_TPB = 1024;       // threads per block of the persistent dual step
-constexpr int HOT_MAX = 24576;      // most xbar entries it stages in shared memory (192 KiB)
+constexpr int HOT_TPB = 1024;              // threads per block of the persistent dual step
+constexpr int HOT_SMEM_MAX = 220 * 1024;   // shared memory it stages xbar[0, hot) in
+constexpr int HOT_MAX = HOT_SMEM_MAX / 4;  // most xbar entries it stages (FP32; half of it in FP64)
 
 // ---- setup (scaling, power iteration, vector helpers) ----------------------
 void launch_row_absmax(const Hyb& M, double* out, int grid, cudaStream_t s);
@@ -126,10 +127,13 @@ template <class T>
 void launch_primal_short_combine(const Hyb& At, const T* vals, const T* y, const T* ch, T* x, T* xbar, T* xsum,
                                  const DevState* st, int accumulate, int short_grid, const PanelLayout& L,
                                  const T* partial, int tpb, cudaStream_t s, int halpern_it = -1);
-// the same step, persistent (grid = number of SMs), with xbar[0, hot) staged
-// in shared memory; hot <= HOT_MAX
-void launch_dual_step_hot(const Hyb& A, const double* xbar, int hot, const double* bh, double* y, double* ysum,
-                          const DevState* st, int accumulate, int grid, cudaStream_t s);
+// the dual step, persistent (grid = number of SMs), with xbar[0, hot) staged
+// in shared memory (hot * sizeof(T) <= HOT_SMEM_MAX), values vals in
+// precision T; halpern_it >= 0: the reflected Halpern form of step
+// halpern_it, with ysum holding the anchor
+template <class T>
+void launch_dual_step_hot(const Hyb& A, const T* vals, const T* xbar, int hot, const T* bh, T* y, T* ysum,
+                          const DevState* st, int accumulate, int grid, cudaStream_t s, int halpern_it = -1);
 void launch_add_counters(DevState* st, long long dk, cudaStream_t s);
 
 // ---- evaluation -------------------------------------------------------------
@@ -157,6 +161,34 @@ void launch_apply_b(const DevState* sts, double* x, double* y, const double* xa,
 void launch_sumsq_b(const double* v, const int* off, int count, double* out, int ostride, cudaStream_t s);
 void launch_div_by_norm_b(double* v, const double* w, const double* s2, int sstride, const int* off, int count,
                           int gx, cudaStream_t s);
+// ---- the whole batch in one cooperative launch (option persistent = 2) ----
+enum { BATCH_ERR_NONE = 0, BATCH_ERR_TIMEOUT = 1, BATCH_ERR_NUMERIC = 2 };
+// device-resident control of one launch (the host writes the first four
+// fields before each launch, so a captured graph serves every call)
+struct BatchCtl {
+  long long k0;         // iterations of the context before this launch (the evaluation schedule)
+  long long max_iters;  // iterations this launch may run
+  long long budget;     // clock cycles one barrier wait may last
+  long long done;       // iterations run (written at the end)
+  unsigned arrive, gen; // the grid barrier's counter and generation
+  int error;            // BATCH_ERR_*
+  int where;            // tag (count) of the barrier at which a wait gave up
+  int active;           // instances not frozen
+  int pad;
+};
+struct BatchArgs {
+  Hyb A, At;
+  const int *binst, *bstart, *xoff, *yoff;  // block -> instance; instance -> blocks, columns, rows
+  int nvb, count, eval_every, restarts, halpern;
+  double *x, *xbar, *xsum, *xr, *xavg, *y, *ysum, *yr, *yavg;
+  const double *ch, *bh, *idc, *idr;
+  double *part_avg, *part_cur;  // per-block evaluation sums, nvb * NQ each
+  DevState* sts;
+  BatchCtl* ctl;
+};
+// blocks of the cooperative grid (all resident: SMs x blocks per SM at tpb threads)
+cudaError_t batch_solve_grid(int tpb, int* grid);
+cudaError_t launch_batch_solve(const BatchArgs& a, int grid, int tpb, cudaStream_t s);
 // start vector of the power iteration (unnormalized) for every instance
 // (off == nullptr: one problem of n columns, count 1)
 void launch_power_start(double* v, const int* perm_x, const int* off, int count, int n, int gx, cudaStream_t s);
@@ -192,7 +224,12 @@ void launch_globalize(const long long* lrp, const int* lci, const long long* rpo
 void launch_lengths(const long long* grp, long long M, const int* gci, long long Z, long long N, int* lenA,
                     int* lenT, unsigned* maxes, cudaStream_t s);
 void launch_length_keys(const int* len, long long cnt, const int* inst, int maxlen, int lbits,
-                        unsigned long long* keys, int* vals, cudaStream_t s);
+                        unsigned long long* keys, int* vals, cudaStream_t s, const int* sec = nullptr,
+                        int sbits = 0);
+// sec[c] = internal row (iy) of column c's only entry if column c has one
+// entry, else 0 (the secondary key that orders one-entry columns by row)
+void launch_singleton_rows(const int* gci, const int* rowid, long long Z, const int* lenT, const int* iy, int* sec,
+                           long long N, cudaStream_t s);
 // transpose sort keys, fed in internal row order (rpi: exclusive scan of the
 // internal rows' lengths)
 void launch_transpose_keys(const long long* grp, const int* py, const long long* rpi, long long M, const int* gci,

@@ -108,12 +108,26 @@ __global__ void k_max_int(const int* __restrict__ v, long long len, unsigned* __
 // sort keys of the renumbering: instance in the high bits, then
 // (maxlen - length), so that an ascending stable sort orders every instance's
 // rows by decreasing length and keeps the instances in place
+// sec (optional, sbits wide) is a secondary key below the length: rows of
+// equal length are ordered by it (stably where it ties)
 __global__ void k_length_keys(const int* __restrict__ len, long long cnt, const int* __restrict__ inst, int maxlen,
-                              int lbits, unsigned long long* __restrict__ keys, int* __restrict__ vals) {
+                              int lbits, const int* __restrict__ sec, int sbits, unsigned long long* __restrict__ keys,
+                              int* __restrict__ vals) {
   for (long long i = gtid(); i < cnt; i += gstride()) {
     const unsigned long long hi = inst ? (unsigned long long)inst[i] : 0ull;
-    keys[i] = (hi << lbits) | (unsigned long long)(maxlen - len[i]);
+    const unsigned long long lo = sec ? (unsigned long long)(unsigned)sec[i] : 0ull;
+    keys[i] = (((hi << lbits) | (unsigned long long)(maxlen - len[i])) << sbits) | lo;
     vals[i] = (int)i;
+  }
+}
+
+// secondary sort key of the columns: the internal row of a column's only
+// entry for one-entry columns, 0 for the others (sec zeroed before)
+__global__ void k_singleton_rows(const int* __restrict__ gci, const int* __restrict__ rowid, long long Z,
+                                 const int* __restrict__ lenT, const int* __restrict__ iy, int* __restrict__ sec) {
+  for (long long k = gtid(); k < Z; k += gstride()) {
+    const int c = gci[k];
+    if (lenT[c] == 1) sec[c] = iy[rowid[k]];
   }
 }
 
@@ -491,8 +505,14 @@ void launch_lengths(const long long* grp, long long M, const int* gci, long long
 }
 
 void launch_length_keys(const int* len, long long cnt, const int* inst, int maxlen, int lbits,
-                        unsigned long long* keys, int* vals, cudaStream_t s) {
-  k_length_keys<<<grid_of(cnt), LT_TPB, 0, s>>>(len, cnt, inst, maxlen, lbits, keys, vals);
+                        unsigned long long* keys, int* vals, cudaStream_t s, const int* sec, int sbits) {
+  k_length_keys<<<grid_of(cnt), LT_TPB, 0, s>>>(len, cnt, inst, maxlen, lbits, sec, sbits, keys, vals);
+}
+
+void launch_singleton_rows(const int* gci, const int* rowid, long long Z, const int* lenT, const int* iy, int* sec,
+                           long long N, cudaStream_t s) {
+  cudaMemsetAsync(sec, 0, sizeof(int) * N, s);
+  if (Z > 0) k_singleton_rows<<<grid_of(Z), LT_TPB, 0, s>>>(gci, rowid, Z, lenT, iy, sec);
 }
 
 void launch_transpose_keys(const long long* grp, const int* py, const long long* rpi, long long M, const int* gci,

@@ -93,6 +93,16 @@ struct pdhg_ctx {
   // CUDA graphs of one evaluation block, per precision phase (FP64, FP32)
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   int64_t graph_launches[2] = {0, 0};
+  int64_t graph_replays = 0;  // graph launches by pdhg_iterate
+  // batch with persistent = 2: the cooperative launch's control block (device
+  // and pinned host copies), its second set of evaluation partial sums, its
+  // grid, and the graph that replays it
+  BatchCtl* bctl = nullptr;
+  BatchCtl* h_bctl = nullptr;
+  double* partials_avg = nullptr;
+  int bgrid = 0;
+  cudaGraphExec_t bgraph = nullptr;
+  bool bgraph_failed = false;
   // recording for the adjoint: (x_k, y_k) every checkpoint_every iterations
   std::vector<void*> ck_x, ck_y;
   void *w_x = nullptr, *w_y = nullptr, *w_xbar = nullptr, *w_seg = nullptr;
@@ -769,18 +779,29 @@ pdhg_status build_layouts(pdhg_ctx* ctx, Scratch& sc, const long long* lrp, cons
   const int* insts[2] = {rinst, cinst};
   const long long cnts[2] = {M, N};
   int* perms[2] = {ctx->perm_y, ctx->perm_x};
-  for (int side = 0; side < 2; ++side) {
-    const int lbits = bit_length(h_max[side]);
-    launch_length_keys(lens[side], cnts[side], insts[side], (int)h_max[side], lbits, k64a, va, s);
-    const int alt = radix_sort_pairs<unsigned long long>(k64a, va, k64b, vb, cnts[side], lbits + ibits, hist, ws, s);
-    CK(ctx, cudaMemcpyAsync(perms[side], alt ? vb : va, sizeof(int) * cnts[side], cudaMemcpyDeviceToDevice, s));
-  }
-  int *iy = nullptr, *ix = nullptr, *slA = nullptr, *slT = nullptr;
+  int *iy = nullptr, *ix = nullptr, *slA = nullptr, *slT = nullptr, *sec = nullptr;
   CK(ctx, sc.take(&iy, M));
   CK(ctx, sc.take(&ix, N));
   CK(ctx, sc.take(&slA, M));
   CK(ctx, sc.take(&slT, N));
-  launch_invert(ctx->perm_y, M, iy, s);
+  // option singleton_order (single LPs): columns with one entry ordered by
+  // the internal row of that entry, so that consecutive such columns gather
+  // neighbouring entries of y (primal step) and a row's one-entry columns sit
+  // side by side in xbar (dual step)
+  const int rbits = bit_length((unsigned long long)std::max<long long>(M - 1, 1));
+  const bool singles = o.singleton_order && !batch && bit_length(h_max[1]) + rbits <= 62;
+  if (singles) CK(ctx, sc.take(&sec, N));
+  for (int side = 0; side < 2; ++side) {
+    const int lbits = bit_length(h_max[side]);
+    const int sbits = side == 1 && singles ? rbits : 0;
+    if (sbits) launch_singleton_rows(gci, rowid, Z, lenT, iy, sec, N, s);
+    launch_length_keys(lens[side], cnts[side], insts[side], (int)h_max[side], lbits, k64a, va, s,
+                       sbits ? sec : nullptr, sbits);
+    const int alt = radix_sort_pairs<unsigned long long>(k64a, va, k64b, vb, cnts[side], lbits + ibits + sbits, hist,
+                                                         ws, s);
+    CK(ctx, cudaMemcpyAsync(perms[side], alt ? vb : va, sizeof(int) * cnts[side], cudaMemcpyDeviceToDevice, s));
+    if (side == 0) launch_invert(ctx->perm_y, M, iy, s);  // the rows' numbering, which side 1 may sort by
+  }
   launch_invert(ctx->perm_x, N, ix, s);
   launch_gather_int(lenA, ctx->perm_y, M, slA, s);
   launch_gather_int(lenT, ctx->perm_x, N, slT, s);
@@ -1150,7 +1171,9 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
   const pdhg_options& o = ctx->opt;
   cudaStream_t s = ctx->stream;
   const int grT = unit_grid(ctx, ctx->At), grA = unit_grid(ctx, ctx->A), tpb = 32 * ctx->wpb;
-  const int hot = (int)std::min<int64_t>(o.dual_hot_cols, ctx->n);
+  // entries of xbar the dual step stages in shared memory, per precision
+  const int hot = (int)std::min<int64_t>({(int64_t)o.dual_hot_cols, ctx->n,
+                                          (int64_t)(HOT_SMEM_MAX / (ctx->phase32 ? 4 : 8))});
   for (int64_t it = 0; it < nb; ++it) {
     if (o.record_for_backward) {
       pdhg_status rs = record_checkpoint(ctx, ctx->k + it);
@@ -1184,18 +1207,32 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
       if (rs != PDHG_OK) return rs;
     }
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
-    if (o.halpern && !ctx->phase32)
-      launch_dual_step_halpern<double>(ctx->A, ctx->A.v, ctx->xbar, ctx->bh, ctx->y, ctx->yr, ctx->st, (int)it, grA,
-                                       s, tpb);
-    else if (o.halpern)
-      launch_dual_step_halpern<float>(ctx->A, ctx->A.v32, ctx->xbar32, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st,
-                                      (int)it, grA, s, tpb);
-    else if (ctx->phase32)
-      launch_dual_step32(ctx->A, ctx->xbar32, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st, o.restarts, grA, s, tpb);
-    else if (hot > 0)
-      launch_dual_step_hot(ctx->A, ctx->xbar, hot, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, ctx->sms, s);
-    else
+    if (o.halpern && !ctx->phase32) {
+      if (hot > 0)
+        launch_dual_step_hot<double>(ctx->A, ctx->A.v, ctx->xbar, hot, ctx->bh, ctx->y, ctx->yr, ctx->st, 0,
+                                     ctx->sms, s, (int)it);
+      else
+        launch_dual_step_halpern<double>(ctx->A, ctx->A.v, ctx->xbar, ctx->bh, ctx->y, ctx->yr, ctx->st, (int)it,
+                                         grA, s, tpb);
+    } else if (o.halpern) {
+      if (hot > 0)
+        launch_dual_step_hot<float>(ctx->A, ctx->A.v32, ctx->xbar32, hot, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st,
+                                    0, ctx->sms, s, (int)it);
+      else
+        launch_dual_step_halpern<float>(ctx->A, ctx->A.v32, ctx->xbar32, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st,
+                                        (int)it, grA, s, tpb);
+    } else if (ctx->phase32) {
+      if (hot > 0)
+        launch_dual_step_hot<float>(ctx->A, ctx->A.v32, ctx->xbar32, hot, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st,
+                                    o.restarts, ctx->sms, s);
+      else
+        launch_dual_step32(ctx->A, ctx->xbar32, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st, o.restarts, grA, s, tpb);
+    } else if (hot > 0) {
+      launch_dual_step_hot<double>(ctx->A, ctx->A.v, ctx->xbar, hot, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts,
+                                   ctx->sms, s);
+    } else {
       launch_dual_step(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, grA, s, nullptr, tpb);
+    }
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 2], s));
   }
   launch_add_counters(ctx->st, nb, s);
@@ -1266,6 +1303,7 @@ pdhg_status run_block_graph(pdhg_ctx* ctx, int64_t nb) {
   }
   CK(ctx, cudaGraphLaunch(ctx->graph_exec[slot], ctx->stream));
   ctx->launches += ctx->graph_launches[slot];
+  ctx->graph_replays += 1;
   return PDHG_OK;
 }
 
@@ -1573,6 +1611,138 @@ pdhg_status iterate_persistent(pdhg_ctx* ctx, int64_t max_iters, double tol, int
   return fail(ctx, PDHG_ERR_NOT_CONVERGED, "iteration limit reached before the tolerance");
 }
 
+// The launch (plus the copies around it) of one pdhg_iterate call on a batch
+// with persistent = 2: the control block to the device, the cooperative solve,
+// the states and the control block back.
+pdhg_status enqueue_batch_solve(pdhg_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  BatchArgs a{};
+  a.A = ctx->A;
+  a.At = ctx->At;
+  a.binst = ctx->binst;
+  a.bstart = ctx->bstart;
+  a.xoff = ctx->xoff;
+  a.yoff = ctx->yoff;
+  a.nvb = ctx->nblocks;
+  a.count = ctx->count;
+  a.eval_every = ctx->opt.eval_every;
+  a.restarts = ctx->opt.restarts;
+  a.halpern = ctx->opt.halpern;
+  a.x = ctx->x;
+  a.xbar = ctx->xbar;
+  a.xsum = ctx->xsum;
+  a.xr = ctx->xr;
+  a.xavg = ctx->xavg;
+  a.y = ctx->y;
+  a.ysum = ctx->ysum;
+  a.yr = ctx->yr;
+  a.yavg = ctx->yavg;
+  a.ch = ctx->ch;
+  a.bh = ctx->bh;
+  a.idc = ctx->idc;
+  a.idr = ctx->idr;
+  a.part_avg = ctx->partials_avg;
+  a.part_cur = ctx->partials;
+  a.sts = ctx->st;
+  a.ctl = ctx->bctl;
+  CK(ctx, cudaMemcpyAsync(ctx->bctl, ctx->h_bctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
+  CK(ctx, launch_batch_solve(a, ctx->bgrid, 32 * ctx->wpb, s));
+  CK(ctx, cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevState) * ctx->count, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaMemcpyAsync(ctx->h_bctl, ctx->bctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+  return PDHG_OK;
+}
+
+// pdhg_iterate for a batch with persistent = 2: ONE cooperative launch runs
+// every active instance until it meets the tolerance, or max_iters
+// iterations; the varying inputs (iteration count so far, budget) sit in the
+// device control block, so a captured CUDA graph of the launch and its copies
+// serves every call. A barrier wait that gives up ends the launch with
+// PDHG_ERR_TIMEOUT (the context's iterates are then partly updated, but the
+// context still answers queries).
+pdhg_status iterate_batch_coop(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done) {
+  cudaStream_t s = ctx->stream;
+  const int count = ctx->count;
+  for (int i = 0; i < count; ++i) ctx->h_st[i].tol = tol;
+  for (int i = 0; i < count; ++i)
+    CK(ctx, cudaMemcpyAsync(&ctx->st[i].tol, &ctx->h_st[i].tol, sizeof(double), cudaMemcpyHostToDevice, s));
+  if (!ctx->bctl) {
+    CK(ctx, dalloc(ctx, &ctx->bctl, 1));
+    CK(ctx, dalloc(ctx, &ctx->partials_avg, (size_t)ctx->nblocks * NQ));
+    CK(ctx, cudaMallocHost(&ctx->h_bctl, sizeof(BatchCtl)));
+    memset(ctx->h_bctl, 0, sizeof(BatchCtl));
+    CK(ctx, batch_solve_grid(32 * ctx->wpb, &ctx->bgrid));
+  }
+  int active = 0;
+  for (int i = 0; i < count; ++i) active += ctx->h_st[i].frozen ? 0 : 1;
+  if (iters_done) *iters_done = 0;
+  if (active == 0 || max_iters == 0) {
+    CK(ctx, cudaStreamSynchronize(s));
+    ctx->converged = active == 0;
+    return ctx->converged || tol == 0.0 ? PDHG_OK
+                                        : fail(ctx, PDHG_ERR_NOT_CONVERGED, "iteration limit reached before every "
+                                                                            "instance met the tolerance");
+  }
+  BatchCtl& h = *ctx->h_bctl;
+  h.k0 = ctx->k;
+  h.max_iters = max_iters;
+  h.budget = ctx->opt.barrier_cycles > 0 ? ctx->opt.barrier_cycles : (1LL << 31);
+  h.done = -1;
+  h.arrive = 0;
+  h.gen = 0;
+  h.error = BATCH_ERR_NONE;
+  h.where = 0;
+  h.active = active;
+  bool replayed = false;
+  if (ctx->opt.use_graphs && !ctx->bgraph_failed) {
+    if (!ctx->bgraph) {
+      // capture once; if the cooperative launch cannot be captured, launch it
+      // directly from then on
+      cudaGraph_t g = nullptr;
+      CK(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      pdhg_status rs = enqueue_batch_solve(ctx);
+      cudaError_t e = cudaStreamEndCapture(s, &g);
+      if (rs == PDHG_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ctx->bgraph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (rs != PDHG_OK || e != cudaSuccess) {
+        ctx->bgraph = nullptr;
+        ctx->bgraph_failed = true;
+        cudaGetLastError();  // clear a capture error; the direct launch below reports its own
+      }
+    }
+    if (ctx->bgraph) {
+      CK(ctx, cudaGraphLaunch(ctx->bgraph, s));
+      ctx->graph_replays += 1;
+      replayed = true;
+    }
+  }
+  if (!replayed) {
+    pdhg_status rs = enqueue_batch_solve(ctx);
+    if (rs != PDHG_OK) return rs;
+  }
+  ctx->launches += 1;
+  CK(ctx, cudaStreamSynchronize(s));
+  int64_t done = h.done;
+  if (done < 0) {  // the launch ended early: the iterations the instances ran
+    done = 0;
+    for (int i = 0; i < count; ++i) done = std::max<int64_t>(done, ctx->h_st[i].k - ctx->k);
+  }
+  ctx->k += done;
+  if (iters_done) *iters_done = done;
+  if (h.error == BATCH_ERR_TIMEOUT)
+    return fail(ctx, PDHG_ERR_TIMEOUT,
+                "a grid-barrier wait of the cooperative batch launch gave up (barrier " + std::to_string(h.where) +
+                    " of the launch, after " + std::to_string((long long)h.budget) + " clock cycles)");
+  bool all_done = true;
+  for (int i = 0; i < count; ++i) {
+    if (ctx->h_st[i].numeric && !ctx->h_st[i].frozen)
+      return fail(ctx, PDHG_ERR_NUMERIC, "NaN or Inf in the iterates of instance " + std::to_string(i));
+    all_done = all_done && ctx->h_st[i].frozen;
+  }
+  ctx->converged = all_done;
+  if (all_done || tol == 0.0) return PDHG_OK;
+  return fail(ctx, PDHG_ERR_NOT_CONVERGED, "iteration limit reached before every instance met the tolerance");
+}
+
 pdhg_status iterate_batch(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done) {
   const pdhg_options& o = ctx->opt;
   cudaStream_t s = ctx->stream;
@@ -1797,6 +1967,8 @@ void pdhg_default_options(pdhg_options* o) {
   o->long_row_min = 128;
   o->rows_per_thread = 4;
   o->dual_hot_cols = 0;
+  o->singleton_order = 0;
+  o->barrier_cycles = 0;
   o->record_for_backward = 0;
   o->checkpoint_every = 50;
   o->step_block = 256;
@@ -1836,16 +2008,20 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
       !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4) || o.snapshot_every < 0 ||
       o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
     return fail(nullptr, PDHG_ERR_INVALID, "option out of range");
+  if (o.singleton_order < 0 || o.singleton_order > 1)
+    return fail(nullptr, PDHG_ERR_INVALID, "singleton_order must be 0 or 1");
   if (!(o.step_block == 0 || o.step_block == 128 || o.step_block == 256 || o.step_block == 512))
     return fail(nullptr, PDHG_ERR_INVALID, "step_block must be 128, 256 or 512");
   if (o.primal_panels < -1 || o.primal_panels > 1 || o.panel_rows < 0 || o.panel_rows > PANEL_SMEM_MAX / 8)
     return fail(nullptr, PDHG_ERR_INVALID, "primal_panels must be -1, 0 or 1 and panel_rows in [0, 28160]");
   if (o.persistent && o.primal_panels == 1)
     return fail(nullptr, PDHG_ERR_INVALID, "persistent = 1 and primal_panels = 1 exclude each other");
-  if (o.halpern != 0 && (o.halpern != 1 || o.persistent || o.record_for_backward || o.dual_hot_cols ||
-                         !(o.halpern_reflect >= 0.0) || !(o.halpern_reflect <= 1.0)))
+  if (o.halpern != 0 && (o.halpern != 1 || o.persistent || o.record_for_backward || !(o.halpern_reflect >= 0.0) ||
+                         !(o.halpern_reflect <= 1.0)))
     return fail(nullptr, PDHG_ERR_INVALID,
-                "halpern = 1 needs halpern_reflect in [0, 1], and no persistent loop, recording or hot columns");
+                "halpern = 1 needs halpern_reflect in [0, 1], and no persistent loop or recording");
+  if (o.persistent == 2)
+    return fail(nullptr, PDHG_ERR_INVALID, "persistent = 2 (one cooperative launch) is for batches");
   if (o.persistent) {
     if (o.persistent != 1 || o.precision != PDHG_FP64 || o.record_for_backward || o.kernel_timing ||
         o.dual_hot_cols)
@@ -1961,6 +2137,8 @@ void pdhg_destroy(pdhg_ctx* ctx) {
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   for (int g = 0; g < 2; ++g)
     if (ctx->graph_exec[g]) cudaGraphExecDestroy(ctx->graph_exec[g]);
+  if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+  if (ctx->h_bctl) cudaFreeHost(ctx->h_bctl);
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
   if (ctx->h_kkt) cudaFreeHost(ctx->h_kkt);
   if (ctx->side) cudaStreamDestroy(ctx->side);
@@ -1974,6 +2152,7 @@ pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* 
   if (max_iters < 0 || !(tol >= 0.0)) return fail(ctx, PDHG_ERR_INVALID, "max_iters < 0 or tol < 0");
   pdhg_status rs = set_device(ctx);
   if (rs != PDHG_OK) return rs;
+  if (ctx->opt.persistent == 2) return iterate_batch_coop(ctx, max_iters, tol, iters_done);
   if (ctx->opt.persistent) return iterate_persistent(ctx, max_iters, tol, iters_done);
   if (ctx->count > 1) return iterate_batch(ctx, max_iters, tol, iters_done);
   const pdhg_options& o = ctx->opt;
@@ -2225,6 +2404,8 @@ pdhg_status pdhg_get_info(pdhg_ctx* ctx, pdhg_info* out) {
   out->feas_polish_attempts = (int64_t)ctx->fp_log.size();
   out->feas_polish_iterations = ctx->fp_iters;
   out->feas_polished = ctx->fp_polished ? 1 : 0;
+  out->persistent_grid = ctx->bgrid;
+  out->graph_launches = ctx->graph_replays;
   return PDHG_OK;
 }
 
@@ -2300,10 +2481,12 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
     return fail(nullptr, PDHG_ERR_INVALID, "step_block must be 128, 256 or 512");
   if (o.primal_panels == 1)
     return fail(nullptr, PDHG_ERR_INVALID, "primal_panels = 1 is for single LPs (batches use the direct primal step)");
-  if (o.halpern && (o.persistent || !(o.halpern_reflect >= 0.0) || !(o.halpern_reflect <= 1.0)))
-    return fail(nullptr, PDHG_ERR_INVALID, "halpern = 1 needs halpern_reflect in [0, 1] and no persistent loop");
-  if (o.persistent != 0 && (o.persistent != 1 || o.kernel_timing))
-    return fail(nullptr, PDHG_ERR_INVALID, "persistent must be 0 or 1, and 1 excludes kernel timing");
+  if (o.halpern && (o.persistent == 1 || !(o.halpern_reflect >= 0.0) || !(o.halpern_reflect <= 1.0)))
+    return fail(nullptr, PDHG_ERR_INVALID,
+                "halpern = 1 needs halpern_reflect in [0, 1] and no single-block loop (persistent = 1)");
+  if (o.persistent < 0 || o.persistent > 2 || (o.persistent && o.kernel_timing) || o.barrier_cycles < 0)
+    return fail(nullptr, PDHG_ERR_INVALID,
+                "persistent must be 0, 1 or 2 and excludes kernel timing; barrier_cycles must be >= 0");
   if (o.feas_polish || !(o.gap_tol >= 0.0))
     return fail(nullptr, PDHG_ERR_INVALID, "batch: no feasibility polishing (single LPs only), gap_tol >= 0");
   int64_t mt = 0, nt = 0, zt = 0;
@@ -2317,7 +2500,7 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
     mt += L.m;
     nt += L.n;
     zt += L.nnz;
-    if (o.persistent && 7 * L.n + 6 * L.m > PERSIST_MAX_DOUBLES)
+    if (o.persistent == 1 && 7 * L.n + 6 * L.m > PERSIST_MAX_DOUBLES)
       return fail(nullptr, PDHG_ERR_INVALID,
                   "persistent: the vectors of instance " + std::to_string(i) +
                       " (7n + 6m doubles) exceed one block's shared memory (28672)");

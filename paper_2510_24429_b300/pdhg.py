@@ -62,7 +62,9 @@ class pdhg_options(C.Structure):
         ("gap_tol", C.c_double),
         ("feas_polish", C.c_int),
         ("polish_div", C.c_int),
-        ("reserved", C.c_int * 2),
+        ("singleton_order", C.c_int),
+        ("reserved", C.c_int),
+        ("barrier_cycles", C.c_int64),
     ]
 
 
@@ -82,6 +84,7 @@ class pdhg_info(C.Structure):
         ("kernel_launches", C.c_int64),
         ("polish_started_at", C.c_int64),
         ("feas_polish_attempts", C.c_int64), ("feas_polish_iterations", C.c_int64), ("feas_polished", C.c_int),
+        ("persistent_grid", C.c_int), ("graph_launches", C.c_int64),
     ]
 
 
@@ -138,6 +141,7 @@ SIGNATURES = {
     "pdhg_autotune": (C.c_int, [C.c_int, C.POINTER(pdhg_lp_desc), C.POINTER(pdhg_options), C.c_char_p, _P,
                                 C.POINTER(pdhg_options), C.POINTER(C.c_int)]),
     "pdhg_profile_key": (C.c_int, [C.c_int, C.POINTER(pdhg_lp_desc), C.c_int, C.c_char_p, C.c_int64]),
+    "pdhg_fp64_fma_rate": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 }
 
 
@@ -405,6 +409,14 @@ def pdhg_autotune(lps, opt: pdhg_options | None = None, cache_path: str | None =
     _check(load().pdhg_autotune(len(lps), descs, C.byref(opt), cache_path.encode() if cache_path else None,
                                 C.c_void_p(stream) if stream else None, C.byref(tuned), C.byref(hit)), None)
     return tuned, bool(hit.value)
+
+
+def pdhg_fp64_fma_rate(stream=None) -> tuple[float, float]:
+    """(FP64 FMAs per second, kernel milliseconds) measured on the current
+    device."""
+    rate, ms = C.c_double(0.0), C.c_double(0.0)
+    _check(load().pdhg_fp64_fma_rate(C.c_void_p(stream) if stream else None, C.byref(rate), C.byref(ms)), None)
+    return rate.value, ms.value
 
 
 def pdhg_profile_key(lps, precision: int = 0) -> str:

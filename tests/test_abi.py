@@ -67,6 +67,7 @@ def test_default_options(lib):
     assert o.precision == P.PDHG_FP64 and o.restarts == 1 and o.primal_weight == 1
     assert (o.halpern, o.halpern_reflect, o.primal_panels, o.long_row_min) == (0, 1.0, -1, 128)
     assert (o.feas_polish, o.polish_div, o.gap_tol, o.polish_switch) == (0, 8, 0.0, 1e-5)
+    assert (o.dual_hot_cols, o.singleton_order) == (0, 0)
     with pytest.raises(KeyError):
         P.pdhg_default_options(no_such_option=1)
 
@@ -200,3 +201,8 @@ def test_noalloc_host_checks(lib):
     assert call(5, 5, blocks=1025) == P.PDHG_ERR_INVALID
     assert call(5, 5, blocks=-1) == P.PDHG_ERR_INVALID
     assert call(5, 5, o=None) == P.PDHG_ERR_INVALID
+
+
+def test_fp64_rate_host_check(lib):
+    assert lib.pdhg_fp64_fma_rate(None, None, None) == P.PDHG_ERR_INVALID
+    assert "NULL" in P.pdhg_last_error(None)

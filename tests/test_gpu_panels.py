@@ -166,3 +166,51 @@ def test_halpern_fp64_with_panels():
     orc2.run(1500, 1e-9)
     sol2.iterate(1500, 1e-9)
     assert compare_traces(sol2.trace(), orc2.trace) >= 10
+
+
+@pytest.mark.parametrize("prec", [P.PDHG_FP64, P.PDHG_FP32, P.PDHG_MIXED])
+@pytest.mark.parametrize("halpern", [0, 1])
+def test_hot_columns_dual_step_is_bit_identical(prec, halpern):
+    """The dual step that stages xbar's first entries (the longest columns) in
+    shared memory gathers the same values in the same order as the direct
+    step, so whole restarted runs are bit-identical: a staged part smaller
+    than, and one larger than, the vector (every column staged), in FP64,
+    FP32 and the mixed form (whose FP64 phase stages at most half as many)."""
+    lp = lpgen.generate(3000, 9000, 2, nnz_per_col=None, zipf=(1.5, 10000, 90000), val_range=(0.1, 10.0),
+                        support=0.3, fp32_values=True)
+    eng = dict(primal_panels=1, panel_rows=256, long_row_min=32, precision=prec, halpern=halpern,
+               polish_switch=1e-4)
+    with P.Solver.from_lp(lp, **eng) as ref:
+        ref.iterate(1500, 1e-7)
+        want = ref.solution(), [(r["iteration"], r["kind"], r["omega"]) for r in ref.trace()]
+    for hot in (1000, 56320):
+        with P.Solver.from_lp(lp, dual_hot_cols=hot, **eng) as sol:
+            sol.iterate(1500, 1e-7)
+            got = sol.solution(), [(r["iteration"], r["kind"], r["omega"]) for r in sol.trace()]
+        for a, b in zip(got[0], want[0]):
+            np.testing.assert_array_equal(a, b)
+        assert got[1] == want[1]
+    with pytest.raises(P.PDHGError):
+        P.Solver.from_lp(lp, dual_hot_cols=56321)
+
+
+@pytest.mark.parametrize("panels", [0, 1])
+def test_singleton_order_matches_oracle(panels):
+    """Columns with one entry numbered by the row of that entry (option
+    singleton_order): a renumbering only, so the iterates agree with the
+    oracle at 1e-10 after 100 plain iterations and restarted runs take the
+    same decisions; checked with and without the panel-tiled primal step."""
+    lp = lpgen.generate(3000, 9000, 2, nnz_per_col=None, zipf=(1.5, 10000, 90000), val_range=(0.1, 10.0),
+                        support=0.3)
+    assert int((np.bincount(lp.col_idx, minlength=lp.n) == 1).sum()) > lp.n // 2
+    eng = dict(primal_panels=panels, panel_rows=256, long_row_min=32, singleton_order=1)
+    orc, sol = _solvers(lp, eng, **TINY_PLAIN)
+    orc.run(100)
+    assert sol.iterate(100) == (P.PDHG_OK, 100)
+    assert_iterates_close(sol, orc, 1e-10)
+    orc2, sol2 = _solvers(lp, eng)
+    orc2.run(1500, 1e-9)
+    sol2.iterate(1500, 1e-9)
+    assert compare_traces(sol2.trace(), orc2.trace) >= 10
+    with pytest.raises(P.PDHGError):
+        P.Solver.from_lp(lp, singleton_order=2)
