@@ -141,7 +141,7 @@ typedef struct {
                              not persistent, no recording (0) */
   int polish_div;         /* polishing phase budget divisor (8) */
   int singleton_order;    /* 1: number the columns with one entry by the row of that entry (single LPs), so
-                             that the step kernels gather them nearly in order; 0: by the caller's order (0) */
+                             that the step kernels gather them nearly in order; 0: by the caller's order (1) */
   int reserved;
   int64_t barrier_cycles; /* persistent = 2: clock cycles one grid-barrier wait may last before the launch
                              gives up with PDHG_ERR_TIMEOUT; 0 = 2^31 (about a second) (0) */

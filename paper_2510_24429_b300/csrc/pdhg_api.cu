@@ -1967,7 +1967,7 @@ void pdhg_default_options(pdhg_options* o) {
   o->long_row_min = 128;
   o->rows_per_thread = 4;
   o->dual_hot_cols = 0;
-  o->singleton_order = 0;
+  o->singleton_order = 1;
   o->barrier_cycles = 0;
   o->record_for_backward = 0;
   o->checkpoint_every = 50;

@@ -67,7 +67,7 @@ def test_default_options(lib):
     assert o.precision == P.PDHG_FP64 and o.restarts == 1 and o.primal_weight == 1
     assert (o.halpern, o.halpern_reflect, o.primal_panels, o.long_row_min) == (0, 1.0, -1, 128)
     assert (o.feas_polish, o.polish_div, o.gap_tol, o.polish_switch) == (0, 8, 0.0, 1e-5)
-    assert (o.dual_hot_cols, o.singleton_order) == (0, 0)
+    assert (o.dual_hot_cols, o.singleton_order, o.barrier_cycles) == (0, 1, 0)
     with pytest.raises(KeyError):
         P.pdhg_default_options(no_such_option=1)
 

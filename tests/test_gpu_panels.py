@@ -183,7 +183,7 @@ def test_hot_columns_dual_step_is_bit_identical(prec, halpern):
     with P.Solver.from_lp(lp, **eng) as ref:
         ref.iterate(1500, 1e-7)
         want = ref.solution(), [(r["iteration"], r["kind"], r["omega"]) for r in ref.trace()]
-    for hot in (1000, 56320):
+    for hot in (1000, 20000, 56320):  # 1, 2 and 3 resident blocks per SM (FP32; FP64 stages half)
         with P.Solver.from_lp(lp, dual_hot_cols=hot, **eng) as sol:
             sol.iterate(1500, 1e-7)
             got = sol.solution(), [(r["iteration"], r["kind"], r["omega"]) for r in sol.trace()]
@@ -214,3 +214,4 @@ def test_singleton_order_matches_oracle(panels):
     assert compare_traces(sol2.trace(), orc2.trace) >= 10
     with pytest.raises(P.PDHGError):
         P.Solver.from_lp(lp, singleton_order=2)
+
