@@ -357,10 +357,12 @@ typedef struct {
  * diagonally, each instance renumbered on its own and padded to whole thread
  * blocks), while scaling, step sizes, primal weight, averages, restarts and
  * termination are per instance; an instance that has converged stops (its
- * blocks return at once). FP64, host inputs, starting point zero; snapshots,
- * recording and warm starts are not available for batches. Use pdhg_iterate
- * (runs until every instance meets tol, or max_iters), pdhg_batch_info and
- * pdhg_batch_solution; pdhg_kkt and pdhg_get_solution return STATE.
+ * blocks return at once). FP64, host inputs, starting point zero; recording
+ * and warm starts are not available for batches, and snapshots are taken per
+ * instance (pdhg_snapshot_i; not with persistent = 1). Use pdhg_iterate (runs
+ * until every instance meets tol, or max_iters), pdhg_batch_info,
+ * pdhg_batch_kkt, pdhg_batch_solution and pdhg_snapshot_i; pdhg_kkt and
+ * pdhg_get_solution return STATE.
  * Errors: INVALID for count < 1, a NULL lps, an instance that fails
  * pdhg_create's checks (the message names it), totals of m, n or nnz at or
  * above 2^31 - 1, or options a batch does not take (primal_panels = 1,
@@ -385,6 +387,23 @@ PDHG_API pdhg_status pdhg_batch_kkt(pdhg_ctx* ctx, int instance, int which, pdhg
  * buffers of its n, m, n (any may be NULL). INVALID for an instance outside
  * [0, count). */
 PDHG_API pdhg_status pdhg_batch_solution(pdhg_ctx* ctx, int instance, double* x, double* y, double* z);
+
+/* Algorithm 1's hand-off (Section 3.1) for each LP of a batch: with eps_cross
+ * and/or snapshot_every set at pdhg_create_batch, every evaluation at which an
+ * instance's candidate meets its own schedule (the thresholds
+ * eps_cross * eps_factor^j of its rel_kkt, or its periodic mark) packs that
+ * instance's candidate (x, y, z), on its problem as given, into a device copy
+ * kept per instance (the latest one), inside the same launches (or the same
+ * cooperative launch) as the iteration. This copies instance `instance`'s
+ * latest snapshot into caller-owned host buffers x[n_i], y[m_i], z[n_i] (any
+ * may be NULL) and its iteration, rel_kkt and the number of snapshots the
+ * instance has taken (nullable). Synchronous: waits for the context's stream;
+ * call it between pdhg_iterate calls. On a single-LP context it returns
+ * pdhg_snapshot's latest snapshot (instance 0). INVALID for an instance outside
+ * [0, count); STATE when no schedule was set or the instance has taken no
+ * snapshot yet (*count is then still written). */
+PDHG_API pdhg_status pdhg_snapshot_i(pdhg_ctx* ctx, int instance, double* x, double* y, double* z, int64_t* iteration,
+                                     double* rel_kkt, int64_t* count);
 
 /* Layout autotuner (no counterpart in the paper: a tuning aid for the step
  * kernels). Times the two step kernels with CUDA events on this LP (count = 1)

@@ -68,6 +68,9 @@ struct DevState {
   double gap_tol;       // relative-gap tolerance; <= 0: tol
   double cand_rel_gap;  // the candidate's rel_gap (feasibility polishing trigger)
   double scratch[2];
+  // the latest scheduled snapshot: its iteration and the candidate's rel_kkt
+  long long snap_k;
+  double snap_rel;
 };
 
 enum { TERM_LP = 0, TERM_PRIMAL = 1, TERM_DUAL = 2 };

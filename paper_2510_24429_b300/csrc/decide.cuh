@@ -68,7 +68,11 @@ static __device__ void decide_one(DevState* st, TraceRec* trace) {
     while (st->next_snapshot <= st->k) st->next_snapshot += st->snapshot_every;
   }
   st->snapshot_flag = snap;
-  if (snap) st->snapshots += 1;
+  if (snap) {
+    st->snapshots += 1;
+    st->snap_k = st->k;
+    st->snap_rel = rel;
+  }
 
   int kind = KIND_NONE, apply = APPLY_NONE;
   if (converged) {

@@ -899,7 +899,11 @@ __global__ void k_decide(DevState* st, TraceRec* trace) { decide_one(st, trace);
 // ---------------------------------------------------------------------------
 __global__ void k_decide_b(DevState* sts, int count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= count || sts[i].frozen) return;
+  if (i >= count) return;
+  if (sts[i].frozen) {
+    sts[i].snapshot_flag = 0;  // an instance that stopped schedules no snapshot
+    return;
+  }
   decide_one(sts + i, nullptr);
   if (sts[i].converged) sts[i].frozen = 1;
 }
@@ -1260,6 +1264,45 @@ __global__ void k_pack_y(const int* __restrict__ perm, const double* __restrict_
     oy[perm[i]] = dr[i] * py[i];
 }
 
+// Batch snapshots (Algorithm 1's hand-off for every LP of a batch): the
+// candidate (x, y, z) of each instance whose evaluation scheduled a snapshot,
+// on its problem as given, into the stacked output in the caller's numbering
+template <class G>
+__device__ __forceinline__ void snap_dual_block(const Hyb& At, const DevState& st, const int* __restrict__ perm,
+                                                const double* x, const double* xa, const G& gy, const G& gya,
+                                                const double* __restrict__ ch, const double* __restrict__ dc,
+                                                double* ox, double* oz, int bid, int nblk) {
+  if (st.candidate == KIND_AVG) {
+    PackDualOp op{perm, xa, ch, dc, ox, oz};
+    hyb_dot(At, At.v, gya, op, 0, bid, nblk);
+  } else {
+    PackDualOp op{perm, x, ch, dc, ox, oz};
+    hyb_dot(At, At.v, gy, op, 0, bid, nblk);
+  }
+}
+
+__global__ void __launch_bounds__(STEP_TPB_MAX) k_snap_dual_b(Hyb At, const DevState* __restrict__ sts,
+                                                     const int* __restrict__ binst, const int* __restrict__ perm,
+                                                     const double* __restrict__ x, const double* __restrict__ y,
+                                                     const double* __restrict__ xa, const double* __restrict__ ya,
+                                                     const double* __restrict__ ch, const double* __restrict__ dc,
+                                                     double* __restrict__ ox, double* __restrict__ oz) {
+  const DevState& st = sts[binst[blockIdx.x]];
+  if (!st.snapshot_flag) return;
+  snap_dual_block(At, st, perm, x, xa, GlobalGather<double>{y}, GlobalGather<double>{ya}, ch, dc, ox, oz,
+                  (int)blockIdx.x, (int)gridDim.x);
+}
+
+__global__ void k_snap_y_b(const DevState* __restrict__ sts, const int* __restrict__ perm, const double* y,
+                           const double* ya, const double* __restrict__ dr, double* __restrict__ oy,
+                           const int* __restrict__ yoff) {
+  const int i = blockIdx.y;
+  if (!sts[i].snapshot_flag) return;
+  const double* py = sts[i].candidate == KIND_AVG ? ya : y;
+  for (int r = yoff[i] + blockIdx.x * blockDim.x + threadIdx.x; r < yoff[i + 1]; r += gridDim.x * blockDim.x)
+    oy[perm[r]] = dr[r] * py[r];
+}
+
 // ---------------------------------------------------------------------------
 // A whole batch in one cooperative launch (option persistent = 2; no
 // counterpart in the paper): every instance's iterations, evaluations,
@@ -1410,7 +1453,10 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, 2) k_batch_solve(BatchArgs a) {
     // instance's blocks in a fixed order), then the decisions
     for (int i = blockIdx.x; i < a.count; i += G) {
       DevState* st = a.sts + i;
-      if (st->frozen) continue;
+      if (st->frozen) {
+        if (tid == 0) st->snapshot_flag = 0;  // an instance that stopped schedules no snapshot
+        continue;
+      }
       const int warp = tid >> 5, lane = tid & 31;
       for (int q2 = warp; q2 < 2 * NQ; q2 += tpb >> 5) {
         const bool avg = q2 >= NQ;
@@ -1441,7 +1487,24 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, 2) k_batch_solve(BatchArgs a) {
       __syncthreads();
     }
     if (!grid_barrier(ctl, budget, ++tag)) return;
-    // evaluation 4: restarts (and the average taken at convergence)
+    // evaluation 4: scheduled snapshots (reading the candidate, which the
+    // restarts below leave in place), restarts and the average taken at
+    // convergence
+    if (a.snap_x) {
+      for (int vb = blockIdx.x; vb < nvb; vb += G) {
+        const DevState& st = a.sts[a.binst[vb]];
+        if (!st.snapshot_flag) continue;
+        snap_dual_block(a.At, st, a.perm_x, a.x, a.xavg, CoherentGather<double>{a.y},
+                        CoherentGather<double>{a.yavg}, a.ch, a.dc, a.snap_x, a.snap_z, vb, nvb);
+      }
+      for (int i = 0; i < a.count; ++i) {
+        const DevState& st = a.sts[i];
+        if (!st.snapshot_flag) continue;
+        const double* py = st.candidate == KIND_AVG ? a.yavg : a.y;
+        for (int r = a.yoff[i] + blockIdx.x * tpb + tid; r < a.yoff[i + 1]; r += G * tpb)
+          a.snap_y[a.perm_y[r]] = a.dr[r] * py[r];
+      }
+    }
     for (int i = 0; i < a.count; ++i) {
       const int mode = a.sts[i].apply_mode;
       if (mode == APPLY_NONE) continue;
@@ -1630,6 +1693,13 @@ void launch_apply_b(const DevState* sts, double* x, double* y, const double* xa,
                     double* yr, double* xs, double* ys, const int* xoff, const int* yoff, int count, int gx,
                     cudaStream_t s) {
   k_apply_b<<<dim3(gx, count), TPB, 0, s>>>(sts, x, y, xa, ya, xr, yr, xs, ys, xoff, yoff);
+}
+void launch_snap_b(const Hyb& At, const DevState* sts, const int* binst, int nblocks, const int* perm_x,
+                   const int* perm_y, const double* x, const double* y, const double* xa, const double* ya,
+                   const double* ch, const double* dc, const double* dr, double* ox, double* oy, double* oz,
+                   const int* yoff, int count, int gx, int tpb, cudaStream_t s) {
+  k_snap_dual_b<<<nblocks, tpb, 0, s>>>(At, sts, binst, perm_x, x, y, xa, ya, ch, dc, ox, oz);
+  k_snap_y_b<<<dim3(gx, count), TPB, 0, s>>>(sts, perm_y, y, ya, dr, oy, yoff);
 }
 cudaError_t batch_solve_grid(int tpb, int* grid) {
   int dev = 0, sms = 0, per_sm = 0;

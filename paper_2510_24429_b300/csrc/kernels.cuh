@@ -185,7 +185,19 @@ struct BatchArgs {
   double *part_avg, *part_cur;  // per-block evaluation sums, nvb * NQ each
   DevState* sts;
   BatchCtl* ctl;
+  // scheduled snapshots (null when none are scheduled): stacked outputs in the
+  // caller's numbering, and what packing them needs
+  double *snap_x, *snap_y, *snap_z;
+  const int *perm_x, *perm_y;
+  const double *dc, *dr;
 };
+// batch snapshots: for every instance whose latest evaluation scheduled one,
+// its candidate (x, y, z) on its problem as given into ox, oy, oz (stacked, in
+// the caller's numbering)
+void launch_snap_b(const Hyb& At, const DevState* sts, const int* binst, int nblocks, const int* perm_x,
+                   const int* perm_y, const double* x, const double* y, const double* xa, const double* ya,
+                   const double* ch, const double* dc, const double* dr, double* ox, double* oy, double* oz,
+                   const int* yoff, int count, int gx, int tpb, cudaStream_t s);
 // blocks of the cooperative grid (all resident: SMs x blocks per SM at tpb threads)
 cudaError_t batch_solve_grid(int tpb, int* grid);
 cudaError_t launch_batch_solve(const BatchArgs& a, int grid, int tpb, cudaStream_t s);

@@ -101,6 +101,9 @@ struct pdhg_ctx {
   BatchCtl* h_bctl = nullptr;
   double* partials_avg = nullptr;
   int bgrid = 0;
+  // batch snapshots (eps_cross or snapshot_every set): the latest scheduled
+  // snapshot of every instance, stacked (x n, y m, z n) in the caller's numbering
+  double* bsnap = nullptr;
   cudaGraphExec_t bgraph = nullptr;
   bool bgraph_failed = false;
   // recording for the adjoint: (x_k, y_k) every checkpoint_every iterations
@@ -1380,6 +1383,7 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
   CK(ctx, dalloc(ctx, &ctx->kkt_sums, 1));
   CK(ctx, dalloc(ctx, &ctx->trace, 1));
   CK(ctx, dalloc(ctx, &ctx->sol, 2 * n + m));
+  if (o.eps_cross > 0.0 || o.snapshot_every > 0) CK(ctx, dalloc(ctx, &ctx->bsnap, 2 * n + m));
   CK(ctx, cudaMallocHost(&ctx->h_st, sizeof(DevState) * count));
   CK(ctx, cudaMallocHost(&ctx->h_kkt, sizeof(EvalSums)));
   for (int i = 0; i < 3 * EV_POOL; ++i) CK(ctx, cudaEventCreate(&ctx->ev[i]));
@@ -1457,6 +1461,9 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
   h.halpern = o.halpern;
   h.rho = o.halpern_reflect;
   h.gap_tol = o.gap_tol;
+  h.eps_target = o.eps_cross;  // Algorithm 1's schedule, per instance
+  h.snapshot_every = o.snapshot_every;
+  h.next_snapshot = o.snapshot_every;
   for (int i = 0; i < count; ++i) ctx->h_st[i] = h;
   CK(ctx, cudaMemcpyAsync(ctx->st, ctx->h_st, sizeof(DevState) * count, cudaMemcpyHostToDevice, s));
   launch_finish_setup_b(ctx->st, count, ctx->scal, 8, o.step_factor, o.primal_weight, s);
@@ -1501,6 +1508,10 @@ void eval_batch(pdhg_ctx* ctx) {
   launch_decide_b(ctx->st, count, s);
   launch_apply_b(ctx->st, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, ctx->xsum, ctx->ysum, ctx->xoff,
                  ctx->yoff, count, gx, s);
+  if (ctx->bsnap)
+    launch_snap_b(ctx->At, ctx->st, ctx->binst, ctx->nblocks, ctx->perm_x, ctx->perm_y, ctx->x, ctx->y, ctx->xavg,
+                  ctx->yavg, ctx->ch, ctx->dc, ctx->dr, ctx->bsnap, ctx->bsnap + ctx->n, ctx->bsnap + ctx->n + ctx->m,
+                  ctx->yoff, count, gx, 32 * ctx->wpb, s);
 }
 
 pdhg_status enqueue_steps_batch(pdhg_ctx* ctx, int64_t nb, bool timing) {
@@ -1531,7 +1542,7 @@ pdhg_status enqueue_steps_batch(pdhg_ctx* ctx, int64_t nb, bool timing) {
 
 pdhg_status enqueue_eval_batch(pdhg_ctx* ctx) {
   eval_batch(ctx);
-  ctx->launches += (ctx->opt.restarts ? 4 : 0) + 3 + 2;
+  ctx->launches += (ctx->opt.restarts ? 4 : 0) + 3 + 2 + (ctx->bsnap ? 2 : 0);
   CK(ctx, cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevState) * ctx->count, cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaGetLastError());
   return PDHG_OK;
@@ -1645,6 +1656,15 @@ pdhg_status enqueue_batch_solve(pdhg_ctx* ctx) {
   a.part_cur = ctx->partials;
   a.sts = ctx->st;
   a.ctl = ctx->bctl;
+  if (ctx->bsnap) {
+    a.snap_x = ctx->bsnap;
+    a.snap_y = ctx->bsnap + ctx->n;
+    a.snap_z = ctx->bsnap + ctx->n + ctx->m;
+    a.perm_x = ctx->perm_x;
+    a.perm_y = ctx->perm_y;
+    a.dc = ctx->dc;
+    a.dr = ctx->dr;
+  }
   CK(ctx, cudaMemcpyAsync(ctx->bctl, ctx->h_bctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
   CK(ctx, launch_batch_solve(a, ctx->bgrid, 32 * ctx->wpb, s));
   CK(ctx, cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevState) * ctx->count, cudaMemcpyDeviceToHost, s));
@@ -2471,12 +2491,14 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
     o = *opt;
   else
     pdhg_default_options(&o);
-  if (o.precision != PDHG_FP64 || o.record_for_backward || o.eps_cross > 0.0 || o.snapshot_every > 0 ||
-      o.inputs_on_device || o.dual_hot_cols || o.eval_every < 1 || o.ruiz_iters < 0 || o.power_iters < 1 ||
-      !(o.step_factor > 0.0) || o.long_row_min < 1 ||
-      !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4))
+  if (o.precision != PDHG_FP64 || o.record_for_backward || o.inputs_on_device || o.dual_hot_cols ||
+      o.eval_every < 1 || o.ruiz_iters < 0 || o.power_iters < 1 || !(o.step_factor > 0.0) || o.long_row_min < 1 ||
+      !(o.rows_per_thread == 1 || o.rows_per_thread == 2 || o.rows_per_thread == 4) || o.snapshot_every < 0 ||
+      o.eps_cross < 0.0 || !(o.eps_factor > 0.0 && o.eps_factor < 1.0))
     return fail(nullptr, PDHG_ERR_INVALID,
-                "batch: FP64, host inputs, no snapshots, no recording, no shared-memory hot columns, valid options");
+                "batch: FP64, host inputs, no recording, no shared-memory hot columns, valid options");
+  if (o.persistent == 1 && (o.eps_cross > 0.0 || o.snapshot_every > 0))
+    return fail(nullptr, PDHG_ERR_INVALID, "batch snapshots need persistent = 0 or 2");
   if (!(o.step_block == 0 || o.step_block == 128 || o.step_block == 256 || o.step_block == 512))
     return fail(nullptr, PDHG_ERR_INVALID, "step_block must be 128, 256 or 512");
   if (o.primal_panels == 1)
@@ -2619,6 +2641,39 @@ pdhg_status pdhg_batch_solution(pdhg_ctx* ctx, int instance, double* x, double* 
   if (y) CK(ctx, cudaMemcpyAsync(y, oy + y0, sizeof(double) * mi, cudaMemcpyDeviceToHost, ctx->stream));
   if (z) CK(ctx, cudaMemcpyAsync(z, oz + x0, sizeof(double) * ni, cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return PDHG_OK;
+}
+
+pdhg_status pdhg_snapshot_i(pdhg_ctx* ctx, int instance, double* x, double* y, double* z, int64_t* iteration,
+                            double* rel_kkt, int64_t* count) {
+  if (!ctx) return PDHG_ERR_INVALID;
+  if (instance < 0 || instance >= ctx->count) return fail(ctx, PDHG_ERR_INVALID, "instance out of range");
+  if (ctx->count == 1) {
+    if (count) {
+      pdhg_status rs = pdhg_snapshot_poll(ctx, count, nullptr);
+      if (rs != PDHG_OK) return rs;
+    }
+    return pdhg_snapshot(ctx, x, y, z, iteration, rel_kkt);
+  }
+  pdhg_status rs = set_device(ctx);
+  if (rs != PDHG_OK) return rs;
+  if (!ctx->bsnap) return fail(ctx, PDHG_ERR_STATE, "no snapshot schedule (eps_cross, snapshot_every) was set");
+  CK(ctx, cudaMemcpyAsync(ctx->h_st + instance, ctx->st + instance, sizeof(DevState), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  const DevState& h = ctx->h_st[instance];
+  if (count) *count = h.snapshots;
+  if (h.snapshots == 0) return fail(ctx, PDHG_ERR_STATE, "instance has no snapshot yet");
+  const int x0 = ctx->xoff_h[instance], y0 = ctx->yoff_h[instance];
+  const int64_t ni = ctx->xoff_h[instance + 1] - x0, mi = ctx->yoff_h[instance + 1] - y0;
+  const double* b = ctx->bsnap;
+  if (x) CK(ctx, cudaMemcpyAsync(x, b + x0, sizeof(double) * ni, cudaMemcpyDeviceToHost, ctx->stream));
+  if (y) CK(ctx, cudaMemcpyAsync(y, b + ctx->n + y0, sizeof(double) * mi, cudaMemcpyDeviceToHost, ctx->stream));
+  if (z)
+    CK(ctx, cudaMemcpyAsync(z, b + ctx->n + ctx->m + x0, sizeof(double) * ni, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (iteration) *iteration = h.snap_k;
+  if (rel_kkt) *rel_kkt = h.snap_rel;
   return PDHG_OK;
 }
 

@@ -142,6 +142,8 @@ SIGNATURES = {
                                 C.POINTER(pdhg_options), C.POINTER(C.c_int)]),
     "pdhg_profile_key": (C.c_int, [C.c_int, C.POINTER(pdhg_lp_desc), C.c_int, C.c_char_p, C.c_int64]),
     "pdhg_fp64_fma_rate": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "pdhg_snapshot_i": (C.c_int, [_P, C.c_int, _P, _P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_int64)]),
 }
 
 
@@ -477,6 +479,16 @@ class BatchSolver:
 
     def engine_info(self):
         return pdhg_get_info(self.ctx)
+
+    def snapshot(self, i):
+        """Instance i's latest scheduled snapshot (pdhg_snapshot_i): dict with
+        x, y, z on its problem as given, iteration, rel_kkt and count."""
+        m, n = self.sizes[i]
+        x, y, z = np.empty(n), np.empty(m), np.empty(n)
+        it, rel, cnt = C.c_int64(), C.c_double(), C.c_int64()
+        _check(load().pdhg_snapshot_i(self.ctx, int(i), x.ctypes.data, y.ctypes.data, z.ctypes.data, C.byref(it),
+                                      C.byref(rel), C.byref(cnt)), self.ctx)
+        return {"x": x, "y": y, "z": z, "iteration": it.value, "rel_kkt": rel.value, "count": cnt.value}
 
     def close(self):
         if self.ctx:

@@ -110,3 +110,91 @@ def test_batch_kkt_per_instance():
                 assert k[key] == pytest.approx(ko[key], rel=rel, abs=1e-12), (i, key)
         with pytest.raises(P.PDHGError):
             bs.kkt(len(lps))
+
+
+# ---------------------------------------------------------------------------
+# per-instance snapshots (pdhg_snapshot_i): Algorithm 1's hand-off for every LP
+# of a batch
+# ---------------------------------------------------------------------------
+
+def test_batch_periodic_snapshots_match_oracle():
+    """snapshot_every = 128: after 256 iterations every instance that is still
+    iterating holds the candidate of its evaluation at 256 (its second
+    snapshot); the tiny LP's equals the oracle's snapshot at 1e-8."""
+    lps = _batch_lps()
+    lp = lps[-1]
+    orc = O.Oracle(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, O.Options(snapshot_every=128))
+    orc.run(256)
+    with P.BatchSolver(lps, snapshot_every=128) as bs:
+        bs.iterate(256)
+        info = bs.info()
+        snap = bs.snapshot(len(lps) - 1)
+        for i in range(len(lps)):
+            si = bs.snapshot(i)
+            assert si["count"] == 2 and si["iteration"] == 256, (i, si["count"], si["iteration"])
+            x, y, z = bs.solution(i)
+            # restarts leave the candidate in the current iterate (or it was the current one)
+            assert info["iterations"][i] == 256
+    ref = orc.snapshots[-1]
+    assert len(orc.snapshots) == 2 and ref["iteration"] == 256
+    assert snap["rel_kkt"] == pytest.approx(ref["rel_kkt"], rel=1e-6)
+    for key in ("x", "y", "z"):
+        scale = max(float(np.max(np.abs(ref[key]))), float(np.linalg.norm(lp.c)) / np.sqrt(lp.n) if key == "z" else 0)
+        assert float(np.max(np.abs(snap[key] - ref[key]))) <= 1e-8 * scale, key
+
+
+def test_batch_algorithm1_thresholds_match_oracle():
+    """eps_cross = 1e-2, eps_factor = 0.1: the tiny LP's instance takes a
+    snapshot at the first evaluation at or below each threshold, as the oracle
+    does; its latest one equals the oracle's."""
+    lps = _batch_lps()
+    lp = lps[-1]
+    orc = O.Oracle(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, O.Options(eps_cross=1e-2))
+    assert orc.run(200000, 1e-7)
+    with P.BatchSolver(lps, eps_cross=1e-2, eps_factor=0.1) as bs:
+        st, _ = bs.iterate(200000, 1e-7)
+        assert st == P.PDHG_OK
+        snap = bs.snapshot(len(lps) - 1)
+        counts = [bs.snapshot(i)["count"] for i in range(len(lps))]
+    ref = orc.snapshots[-1]
+    assert snap["count"] == len(orc.snapshots) >= 4
+    assert snap["iteration"] == ref["iteration"]
+    assert snap["rel_kkt"] == pytest.approx(ref["rel_kkt"], rel=1e-6)
+    for key in ("x", "y"):
+        assert float(np.max(np.abs(snap[key] - ref[key]))) <= 1e-8 * float(np.max(np.abs(ref[key]))), key
+    assert min(counts) >= 4  # every instance ran from rel. KKT > 1e-2 to 1e-7
+
+
+@pytest.mark.parametrize("halpern", [0, 1])
+def test_cooperative_batch_snapshots_bit_identical(halpern):
+    """The cooperative launch (persistent = 2) packs the same snapshots as the
+    multi-launch batch engine."""
+    lps = _batch_lps()
+    out = []
+    for persistent in (0, 2):
+        with P.BatchSolver(lps, eps_cross=1e-2, snapshot_every=200, halpern=halpern, persistent=persistent) as bs:
+            bs.iterate(100000, 1e-7)
+            out.append([bs.snapshot(i) for i in range(len(lps))])
+    for a, b in zip(*out):
+        assert (a["count"], a["iteration"], a["rel_kkt"]) == (b["count"], b["iteration"], b["rel_kkt"])
+        for key in ("x", "y", "z"):
+            np.testing.assert_array_equal(a[key], b[key])
+
+
+def test_batch_snapshot_errors():
+    lps = _batch_lps()
+    with P.BatchSolver(lps) as bs:
+        bs.iterate(64)
+        with pytest.raises(P.PDHGError) as ei:
+            bs.snapshot(0)
+        assert ei.value.status == P.PDHG_ERR_STATE
+        with pytest.raises(P.PDHGError) as ei:
+            bs.snapshot(len(lps))
+        assert ei.value.status == P.PDHG_ERR_INVALID
+    with P.BatchSolver(lps, snapshot_every=1000) as bs:
+        bs.iterate(64)
+        with pytest.raises(P.PDHGError) as ei:
+            bs.snapshot(0)
+        assert ei.value.status == P.PDHG_ERR_STATE
+    with pytest.raises(P.PDHGError):
+        P.BatchSolver(lps[:2], snapshot_every=100, persistent=1)
