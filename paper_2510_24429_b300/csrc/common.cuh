@@ -116,8 +116,13 @@ struct Hyb {
   int* ci = nullptr;          // [slots] column index (internal numbering)
   double* v = nullptr;        // [slots] value
   float* v32 = nullptr;       // [slots] value rounded to FP32 (FP32 / mixed precision only)
+  unsigned* check = nullptr;  // checked build (PDHG_CHECKED): the context's error word
   int units() const { return n_units; }
 };
+
+// bits of the checked build's error word: what a kernel found out of range
+// (and skipped instead of accessing)
+enum { CHECK_UNIT = 1, CHECK_COLUMN = 2 };
 
 // ---------------------------------------------------------------------------
 // device helpers

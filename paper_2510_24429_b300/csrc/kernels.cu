@@ -100,12 +100,34 @@ struct Pair<float> {
 // loop; op.entry(acc, k, r) sees every slot k of row r (padding included:
 // value 0, column 0), op.finish(r, acc) the combined result (max or sum).
 // For long rows only lane 0 calls finish.
+// Checked build (PDHG_CHECKED): unit u's entry range lies within the layout's
+// slots, its slice shape divides the range, and its rows lie within the
+// layout's rows; otherwise the unit is skipped and CHECK_UNIT set. (Padding
+// units of a batch have no valid rows and pass.)
+__device__ __forceinline__ bool unit_ok(const Hyb& H, int u) {
+#ifdef PDHG_CHECKED
+  const int4 info = H.uinfo[u];
+  const long long b = H.uoff[u], e = H.uoff[u + 1];
+  bool ok = 0 <= b && b <= e && e <= H.slots;
+  if (info.y == 0)
+    ok = ok && info.x >= 0 && info.x < H.rows;
+  else
+    ok = ok && (info.y == 1 || info.y == 2 || info.y == 4) && (e - b) % (32 * info.y) == 0 && info.z >= 0 &&
+         info.z <= 32 * info.y && (info.z == 0 || (info.x >= 0 && (long long)info.x + info.z <= H.rows));
+  if (!ok && H.check) atomicOr(H.check, (unsigned)CHECK_UNIT);
+  return ok;
+#else
+  return true;
+#endif
+}
+
 template <bool MAX, class Op>
 __device__ __forceinline__ void hyb_rows(const Hyb& H, Op& op) {
   const int lane = threadIdx.x & 31;
   const int gwarp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
   for (int u = gwarp; u < H.n_units; u += nwarps) {
+    if (!unit_ok(H, u)) continue;
     const int4 info = H.uinfo[u];
     const long long base = H.uoff[u], end = H.uoff[u + 1];
     if (info.y == 0) {
@@ -182,11 +204,33 @@ __device__ __forceinline__ void slice_dot(const Hyb& H, const T* __restrict__ va
   }
 }
 
+// Checked build: a gathered column index outside [0, cols) sets CHECK_COLUMN
+// and reads nothing (the product uses 0)
+template <class T, class G>
+struct CheckedGather {
+  G g;
+  int cols;
+  unsigned* word;
+  __device__ __forceinline__ T operator()(int c) const {
+    if ((unsigned)c >= (unsigned)cols) {
+      if (word) atomicOr(word, (unsigned)CHECK_COLUMN);
+      return T(0);
+    }
+    return g(c);
+  }
+};
+
 // One unit of H (a long row, or a slice of 32*R rows) for the dot-product
 // visitor below.
 template <class T, class Op, class G>
-__device__ __forceinline__ void unit_dot(const Hyb& H, const T* __restrict__ vals, int u, const G& gather, Op& op,
+__device__ __forceinline__ void unit_dot(const Hyb& H, const T* __restrict__ vals, int u, const G& gather_in, Op& op,
                                          unsigned long long pol, int lane) {
+#ifdef PDHG_CHECKED
+  if (!unit_ok(H, u)) return;
+  const CheckedGather<T, G> gather{gather_in, H.cols, H.check};
+#else
+  const G& gather = gather_in;
+#endif
   const int4 info = H.uinfo[u];
   const long long beg = H.uoff[u], end = H.uoff[u + 1];
   if (info.y == 0) {

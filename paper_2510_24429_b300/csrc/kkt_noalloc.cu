@@ -55,6 +55,13 @@ enum {
   NA_COUNT
 };
 
+#ifdef PDHG_CHECKED
+// checked build: set when a column index of the caller's CSR lies outside the
+// vector it indexes (that entry is then skipped); read and cleared by the
+// finalizing kernel of the same call
+static __device__ unsigned g_na_check;
+#endif
+
 // device address of g_kkt_scratch per device (host code cannot use the
 // symbol's name as an address)
 double* g_scratch_ptr[KKT_NA_MAX_DEVICES] = {};
@@ -68,14 +75,25 @@ __device__ __forceinline__ double na_relu(double v) { return v < 0.0 ? 0.0 : v; 
 // such rows over panels instead).
 __device__ __forceinline__ double na_row_dot(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                              const double* __restrict__ v, const double* __restrict__ vec,
-                                             long long row, int lane) {
+                                             long long row, int lane, long long veclen) {
   const long long beg = rp[row], end = rp[row + 1];
   double acc = 0.0;
-  for (long long k = beg + lane; k < end; k += 32) acc += v[k] * vec[ci[k]];
+  for (long long k = beg + lane; k < end; k += 32) {
+    const int c = ci[k];
+#ifdef PDHG_CHECKED
+    if ((unsigned long long)(unsigned)c >= (unsigned long long)veclen) {
+      atomicOr(&g_na_check, 1u);
+      continue;
+    }
+#else
+    (void)veclen;
+#endif
+    acc += v[k] * vec[c];
+  }
   return pdhg::warp_sum(acc);
 }
 
-__global__ void __launch_bounds__(KKT_NA_TPB) k_na_dual(long long n, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(KKT_NA_TPB) k_na_dual(long long n, long long m, const int64_t* __restrict__ rp,
                                                         const int32_t* __restrict__ ci, const double* __restrict__ v,
                                                         const double* __restrict__ c, const double* __restrict__ x,
                                                         const double* __restrict__ y, double* __restrict__ scratch) {
@@ -85,7 +103,7 @@ __global__ void __launch_bounds__(KKT_NA_TPB) k_na_dual(long long n, const int64
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long j = warp; j < n; j += nwarps) {
-    const double g = na_row_dot(rp, ci, v, y, j, lane);
+    const double g = na_row_dot(rp, ci, v, y, j, lane, m);
     if (lane == 0) {
       const double cj = c[j], xj = x[j];
       const double rd = na_relu(g - cj);
@@ -107,7 +125,7 @@ __global__ void __launch_bounds__(KKT_NA_TPB) k_na_dual(long long n, const int64
   }
 }
 
-__global__ void __launch_bounds__(KKT_NA_TPB) k_na_primal(long long m, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(KKT_NA_TPB) k_na_primal(long long m, long long n, const int64_t* __restrict__ rp,
                                                           const int32_t* __restrict__ ci,
                                                           const double* __restrict__ v, const double* __restrict__ b,
                                                           const double* __restrict__ x, const double* __restrict__ y,
@@ -118,7 +136,7 @@ __global__ void __launch_bounds__(KKT_NA_TPB) k_na_primal(long long m, const int
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long i = warp; i < m; i += nwarps) {
-    const double h = na_row_dot(rp, ci, v, x, i, lane);
+    const double h = na_row_dot(rp, ci, v, x, i, lane, n);
     if (lane == 0) {
       const double bi = b[i];
       const double r = bi - h;
@@ -150,6 +168,12 @@ __global__ void k_na_finalize(int nb, double* __restrict__ scratch) {
   }
   acc = is_max ? pdhg::warp_max(acc) : pdhg::warp_sum(acc);
   if (lane == 0) scratch[KKT_NA_SCRATCH_DOUBLES + q] = acc;
+#ifdef PDHG_CHECKED
+  if (threadIdx.x == 0) {
+    scratch[KKT_NA_SCRATCH_DOUBLES + NA_COUNT] = (double)g_na_check;
+    g_na_check = 0u;
+  }
+#endif
 }
 
 // Device address of the scratch array on the current device, looked up once
@@ -209,15 +233,20 @@ PDHG_API pdhg_status pdhg_kkt_noalloc(int64_t m, int64_t n, const int64_t* a_row
     nb = std::min(KKT_NA_MAX_BLOCKS, 4 * sms);
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  k_na_dual<<<nb, KKT_NA_TPB, 0, s>>>(n, at_row_ptr, at_col_idx, at_val, c, x, y, scratch);
-  k_na_primal<<<nb, KKT_NA_TPB, 0, s>>>(m, a_row_ptr, a_col_idx, a_val, b, x, y, scratch);
+  k_na_dual<<<nb, KKT_NA_TPB, 0, s>>>(n, m, at_row_ptr, at_col_idx, at_val, c, x, y, scratch);
+  k_na_primal<<<nb, KKT_NA_TPB, 0, s>>>(m, n, a_row_ptr, a_col_idx, a_val, b, x, y, scratch);
   k_na_finalize<<<1, 32 * NA_COUNT, 0, s>>>(nb, scratch);
   double q[KKT_NA_Q];
   e = cudaGetLastError();
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(q, scratch + KKT_NA_SCRATCH_DOUBLES, sizeof(double) * NA_COUNT, cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(q, scratch + KKT_NA_SCRATCH_DOUBLES, sizeof(double) * (NA_COUNT + 1), cudaMemcpyDeviceToHost,
+                        s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return na_fail(PDHG_ERR_CUDA, cudaGetErrorString(e));
+#ifdef PDHG_CHECKED
+  if (q[NA_COUNT] != 0.0)
+    return na_fail(PDHG_ERR_INVALID, "checked build: a column index outside its vector was found and skipped");
+#endif
   out->rp_norm2 = sqrt(q[NA_RP2]);
   out->rp_norminf = q[NA_RPINF];
   out->rd_norm2 = sqrt(q[NA_RD2]);

@@ -28,11 +28,29 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pdhg.h"
 #include "common.cuh"
 #include "kernels.cuh"
 
 using namespace pdhg;
+
+namespace {
+
+// An NVTX range over a phase of the engine's host code (setup, an evaluation
+// block, a snapshot, the reverse pass, ...), so that a profiler's timeline
+// (Nsight Systems, or ncu --nvtx) shows which phase enqueued which launches.
+// NVTX3 is header-only: without a tool attached a range costs a call through
+// a null function pointer.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+
+}  // namespace
 
 namespace {
 
@@ -104,6 +122,8 @@ struct pdhg_ctx {
   // batch snapshots (eps_cross or snapshot_every set): the latest scheduled
   // snapshot of every instance, stacked (x n, y m, z n) in the caller's numbering
   double* bsnap = nullptr;
+  // checked build (PDHG_CHECKED): the error word the kernels' range checks set
+  unsigned* check = nullptr;
   cudaGraphExec_t bgraph = nullptr;
   bool bgraph_failed = false;
   // recording for the adjoint: (x_k, y_k) every checkpoint_every iterations
@@ -189,6 +209,27 @@ pdhg_status cuda_fail(pdhg_ctx* ctx, cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                                 \
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
+
+// Checked build: the kernels' error word, read (and cleared) after the work
+// of a call; a set bit means an index outside its array was found and skipped
+pdhg_status read_check(pdhg_ctx* ctx) {
+#ifdef PDHG_CHECKED
+  if (!ctx->check) return PDHG_OK;
+  unsigned w = 0;
+  CK(ctx, cudaMemcpyAsync(&w, ctx->check, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (w) {
+    CK(ctx, cudaMemsetAsync(ctx->check, 0, sizeof(unsigned), ctx->stream));
+    return fail(ctx, PDHG_ERR_INVALID,
+                std::string("checked build: out-of-range ") +
+                    ((w & CHECK_UNIT) ? "unit extent or row " : "") + ((w & CHECK_COLUMN) ? "column index " : "") +
+                    "found in the device layout and skipped");
+  }
+#else
+  (void)ctx;
+#endif
+  return PDHG_OK;
+}
 
 template <class T>
 cudaError_t dalloc(pdhg_ctx* ctx, T** p, size_t count) {
@@ -405,6 +446,7 @@ pdhg_status primal_step(pdhg_ctx* ctx, bool f32, const void* y, void* x, void* x
 
 template <class T>
 pdhg_status backward_impl(pdhg_ctx* ctx, const double* dx, const double* dy, double* dc, double* db) {
+  Range nvtx_range("pdhg/backward");
   const int64_t K = ctx->k, C = ctx->opt.checkpoint_every, n = ctx->n, m = ctx->m;
   const bool f32 = std::is_same<T, float>::value;
   cudaStream_t s = ctx->stream;
@@ -468,6 +510,7 @@ void CUDART_CB snapshot_landed(void* p) {
 }
 
 pdhg_status take_snapshot(pdhg_ctx* ctx) {
+  Range nvtx_range("pdhg/snapshot");
   const int slot = (int)(ctx->snap_count % SNAP_SLOTS);
   if (!ctx->snap_host[slot]) {
     // ring slots are allocated on first use (pinned memory is slow to allocate)
@@ -573,6 +616,13 @@ void pad_units_to(HostUnits& H, int target, int empty_row) {
 }
 
 pdhg_status upload_units(pdhg_ctx* ctx, const HostUnits& h, int rows, int cols, Hyb& d) {
+#ifdef PDHG_CHECKED
+  if (!ctx->check) {
+    CK(ctx, dalloc(ctx, &ctx->check, 1));
+    CK(ctx, cudaMemsetAsync(ctx->check, 0, sizeof(unsigned), ctx->stream));
+  }
+  d.check = ctx->check;
+#endif
   d.rows = rows;
   d.cols = cols;
   d.n_units = h.n_units();
@@ -723,6 +773,7 @@ pdhg_status build_panels(pdhg_ctx* ctx, Scratch& sc, const long long* tp, const 
 // length, stable, each instance keeping its own range.
 pdhg_status build_layouts(pdhg_ctx* ctx, Scratch& sc, const long long* lrp, const int* lci, const double* val,
                           const std::vector<long long>& rpoff_h, const std::vector<long long>& zoff_h) {
+  Range nvtx_range("pdhg/layout");
   const pdhg_options& o = ctx->opt;
   const int count = ctx->count;
   const bool batch = count > 1;
@@ -885,6 +936,7 @@ pdhg_status build_layouts(pdhg_ctx* ctx, Scratch& sc, const long long* lrp, cons
 // reads the uploaded data.
 pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx, const double* val, const double* b,
                   const double* c, const double* x0, const double* y0, const std::function<pdhg_status()>& host_checks) {
+  Range nvtx_range("pdhg/setup");
   const int64_t m = ctx->m, n = ctx->n, nnz = ctx->nnz;
   const pdhg_options& o = ctx->opt;
   cudaStream_t s = ctx->stream;
@@ -1247,6 +1299,7 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
 // One evaluation: candidate measures, decisions, their application, and the
 // copy of the state struct to pinned host memory (the host waits for it).
 pdhg_status enqueue_eval(pdhg_ctx* ctx) {
+  Range nvtx_range("pdhg/evaluation");
   const pdhg_options& o = ctx->opt;
   cudaStream_t s = ctx->stream;
   const int n = (int)ctx->n, m = (int)ctx->m;
@@ -1286,6 +1339,7 @@ pdhg_status enqueue_eval_batch(pdhg_ctx* ctx);
 // after. Kernel arguments are fixed pointers and the step sizes, tolerance
 // and counters live in device memory, so one capture serves every block.
 pdhg_status run_block_graph(pdhg_ctx* ctx, int64_t nb) {
+  Range nvtx_range("pdhg/evaluation_block_graph");
   const int slot = ctx->phase32 ? 1 : 0;
   if (!ctx->graph_exec[slot]) {
     const int64_t launches0 = ctx->launches;
@@ -1319,6 +1373,7 @@ pdhg_status enqueue_block(pdhg_ctx* ctx, int64_t nb) {
 // ---- batch -------------------------------------------------------------------
 
 pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
+  Range nvtx_range("pdhg/setup_batch");
   const pdhg_options& o = ctx->opt;
   ctx->count = count;
   ctx->xoff_h.assign(count + 1, 0);
@@ -1541,6 +1596,7 @@ pdhg_status enqueue_steps_batch(pdhg_ctx* ctx, int64_t nb, bool timing) {
 }
 
 pdhg_status enqueue_eval_batch(pdhg_ctx* ctx) {
+  Range nvtx_range("pdhg/evaluation_batch");
   eval_batch(ctx);
   ctx->launches += (ctx->opt.restarts ? 4 : 0) + 3 + 2 + (ctx->bsnap ? 2 : 0);
   CK(ctx, cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevState) * ctx->count, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1680,6 +1736,7 @@ pdhg_status enqueue_batch_solve(pdhg_ctx* ctx) {
 // PDHG_ERR_TIMEOUT (the context's iterates are then partly updated, but the
 // context still answers queries).
 pdhg_status iterate_batch_coop(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done) {
+  Range nvtx_range("pdhg/batch_cooperative_launch");
   cudaStream_t s = ctx->stream;
   const int count = ctx->count;
   for (int i = 0; i < count; ++i) ctx->h_st[i].tol = tol;
@@ -1870,6 +1927,7 @@ pdhg_status polish_phase_begin(pdhg_ctx* ctx, int term_mode) {
 // pair (x_p, y_d) passes the termination test on the LP as given, it becomes
 // the current iterate and *solved is set.
 pdhg_status feas_polish(pdhg_ctx* ctx, double tol, int64_t budget, bool graphs, bool* solved) {
+  Range nvtx_range("pdhg/feasibility_polishing");
   *solved = false;
   const int64_t n = ctx->n, m = ctx->m;
   cudaStream_t s = ctx->stream;
@@ -2129,6 +2187,7 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     return st;
   }
   pdhg_status st = setup(ctx, row_ptr, col_idx, val, b, c, x0, y0, await_checks);
+  if (st == PDHG_OK) st = read_check(ctx);
   if (st != PDHG_OK) {
     if (await_checks() != PDHG_OK)
       st = fail(nullptr, checked.first, checked.second);
@@ -2166,7 +2225,19 @@ void pdhg_destroy(pdhg_ctx* ctx) {
   delete ctx;
 }
 
+static pdhg_status iterate_impl(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done);
+
 pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done) {
+  Range nvtx_range("pdhg/iterate");
+  pdhg_status rs = iterate_impl(ctx, max_iters, tol, iters_done);
+  if (ctx && (rs == PDHG_OK || rs == PDHG_ERR_NOT_CONVERGED)) {
+    const pdhg_status cs = read_check(ctx);  // checked build only
+    if (cs != PDHG_OK) return cs;
+  }
+  return rs;
+}
+
+static pdhg_status iterate_impl(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done) {
   if (iters_done) *iters_done = 0;
   if (!ctx) return PDHG_ERR_INVALID;
   if (max_iters < 0 || !(tol >= 0.0)) return fail(ctx, PDHG_ERR_INVALID, "max_iters < 0 or tol < 0");
@@ -2553,6 +2624,7 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
     return st;
   }
   pdhg_status st = setup_batch(ctx, count, lps);
+  if (st == PDHG_OK) st = read_check(ctx);
   if (st != PDHG_OK) {
     g_create_error = ctx->err;
     pdhg_destroy(ctx);

@@ -483,7 +483,7 @@ class BatchSolver:
     def snapshot(self, i):
         """Instance i's latest scheduled snapshot (pdhg_snapshot_i): dict with
         x, y, z on its problem as given, iteration, rel_kkt and count."""
-        m, n = self.sizes[i]
+        m, n = self.sizes[i] if 0 <= i < len(self.sizes) else (1, 1)  # out of range: the library says INVALID
         x, y, z = np.empty(n), np.empty(m), np.empty(n)
         it, rel, cnt = C.c_int64(), C.c_double(), C.c_int64()
         _check(load().pdhg_snapshot_i(self.ctx, int(i), x.ctypes.data, y.ctypes.data, z.ctypes.data, C.byref(it),

