@@ -66,7 +66,7 @@ import numpy as np
 import scipy.sparse as sp
 
 # restart kinds recorded in the trace
-NO_RESTART, RESTART_TO_CURRENT, RESTART_TO_AVERAGE = 0, 1, 2
+NO_RESTART, RESTART_TO_CURRENT, RESTART_TO_AVERAGE, RESTART_TO_PDHG_STEP = 0, 1, 2, 3
 
 
 @dataclasses.dataclass
@@ -124,6 +124,22 @@ class Options:
     # the two residuals (the single-eps test of Section 2). Feasibility
     # polishing pays off when the gap tolerance is the looser one.
     gap_tol: float = 0.0
+    # restart scheme: 0 = PDLP's weighted KKT error (readings above); 1 = the
+    # fixed-point residual scheme of the cuPDLP+ line the paper's solver
+    # follows (Section 4.1, which gives no formula, so these are readings), for
+    # the reflected Halpern form: at an evaluation the candidate is the current
+    # point z, its measure is r(z) = ||z - T(z)||_M (T the PDHG map, M the
+    # metric in which T is firmly nonexpansive, see ``fixed_point_residual``);
+    # the three restart rules above compare r(z) with r at the last restart and
+    # at the previous evaluation; a restart moves to T(z), which becomes the
+    # anchor; and the primal weight follows a PID controller on
+    # e = ln(omega dx / dy): ln omega -= pid_kp e + pid_ki sum(e) + pid_kd (e -
+    # e_prev), dx and dy the moves of the restart point (with pid_kp = theta
+    # and the other gains 0 it is PDLP's update)
+    restart_scheme: int = 0
+    pid_kp: float = 0.99
+    pid_ki: float = 0.01
+    pid_kd: float = 0.0
 
 
 def csr_matrix(m, n, row_ptr, col_idx, val) -> sp.csr_matrix:
@@ -360,6 +376,34 @@ def primal_weight_update(omega: float, dx: float, dy: float, theta: float) -> fl
     return omega
 
 
+def fixed_point_residual(Ah, AhT, bh, ch, xh, yh, tau, sigma):
+    """(r, x~, y~): the PDHG map's output (x~, y~) = T(xh, yh) and the
+    fixed-point residual r = ||z - T(z)||_M of z = (xh, yh) in the metric
+    ||(dx, dy)||_M^2 = ||dx||^2 / tau + 2 dy^T Ahat dx + ||dy||^2 / sigma, in
+    which the PDHG map is firmly nonexpansive (tau sigma ||Ahat||^2 < 1). The
+    measure of the cuPDLP+ restart scheme (Section 4.1 names the line of work;
+    the formula is a reading)."""
+    xt, _, yt = pdhg_iteration(Ah, AhT, bh, ch, xh, yh, tau, sigma)
+    dx, dy = xt - xh, yt - yh
+    q = float(dx @ dx) / tau + 2.0 * float(dy @ (Ah @ dx)) + float(dy @ dy) / sigma
+    return math.sqrt(max(q, 0.0)), xt, yt
+
+
+def pid_primal_weight(omega: float, dx: float, dy: float, integral: float, e_prev: float, kp: float, ki: float,
+                      kd: float):
+    """(omega', integral', e) after one PID step on the error
+    e = ln(omega dx / dy), which is 0 when the weighted moves omega dx and dy
+    balance: ln omega' = ln omega - kp e - ki (integral + e) - kd (e - e_prev).
+    Unchanged when a move is at most 1e-10. The cuPDLP+ primal weight (a
+    reading; the paper gives no formula); kp = theta, ki = kd = 0 is PDLP's
+    update ``primal_weight_update``."""
+    if not (dx > 1e-10 and dy > 1e-10):
+        return omega, integral, e_prev
+    e = math.log(omega * dx / dy)
+    integral = integral + e
+    return math.exp(math.log(omega) - kp * e - ki * integral - kd * (e - e_prev)), integral, e
+
+
 # ---------------------------------------------------------------------------
 # The solver
 # ---------------------------------------------------------------------------
@@ -392,6 +436,8 @@ class Oracle:
     def __init__(self, m, n, row_ptr, col_idx, val, b, c, opt: Options | None = None,
                  x0=None, y0=None):
         self.opt = opt or Options()
+        if self.opt.restart_scheme not in (0, 1) or (self.opt.restart_scheme == 1 and self.opt.feas_polish):
+            raise ValueError("restart_scheme must be 0 or 1, and 1 is not combined with feasibility polishing")
         self.A = csr_matrix(m, n, row_ptr, col_idx, val)
         self.b = np.asarray(b, dtype=np.float64).copy()
         self.c = np.asarray(c, dtype=np.float64).copy()
@@ -427,6 +473,10 @@ class Oracle:
         self.x_r, self.y_r = self.x.copy(), self.y.copy()
         self.n_restart = self.scaled_norms(self.x, self.y)
         self.n_prev = self.n_restart
+        # fixed-point residual scheme: r at the last restart and at the
+        # previous evaluation, and the PID controller's state
+        self.r_restart = self.r_prev = self.fixed_point_measure(self.x, self.y)[0]
+        self.pid_integral, self.pid_prev = 0.0, 0.0
 
     # -- step sizes --------------------------------------------------------
     @property
@@ -448,6 +498,11 @@ class Oracle:
         rp = self.bh - self.Ah @ xh
         rd = np.maximum(0.0, self.AhT @ yh - self.ch)
         return (float(np.linalg.norm(rp)), float(np.linalg.norm(rd)), abs(float(self.ch @ xh) - float(self.bh @ yh)))
+
+    def fixed_point_measure(self, xh, yh):
+        """``fixed_point_residual`` of a scaled point with the current step
+        sizes: (r, x~, y~)."""
+        return fixed_point_residual(self.Ah, self.AhT, self.bh, self.ch, xh, yh, self.tau, self.sigma)
 
     # -- unscaled quantities -----------------------------------------------
     def unscale(self, xh, yh):
@@ -500,6 +555,8 @@ class Oracle:
         when its rules allow (Section 5, readings at ``Options``). Returns True
         when the method has converged."""
         opt = self.opt
+        if opt.restart_scheme == 1:
+            return self.evaluate_fixed_point(tol)
         if opt.restarts and self.t > 0 and not opt.halpern:
             xa, ya = self.x_avg, self.y_avg
             n_cur = self.scaled_norms(self.x, self.y)
@@ -566,6 +623,47 @@ class Oracle:
             if polished is not None:
                 self.x, self.y = polished
                 converged = True
+        return converged
+
+    def evaluate_fixed_point(self, tol: float) -> bool:
+        """One evaluation under the fixed-point residual restart scheme
+        (``Options.restart_scheme`` = 1, the cuPDLP+ line, readings): the
+        candidate is the current point; termination and Algorithm 1's
+        snapshots as in ``evaluate``; the three restart rules on r(z); a
+        restart moves the iterate and the anchor to T(z) and updates the
+        primal weight by ``pid_primal_weight``."""
+        opt = self.opt
+        kk = self.kkt_of(self.x, self.y)
+        rel = kk[self.term]
+        gtol = opt.gap_tol if opt.gap_tol > 0 else tol
+        converged = tol > 0 and kk["rel_p"] <= tol and kk["rel_d"] <= tol and kk["rel_gap"] <= gtol
+        if self.eps_target > 0 and rel <= self.eps_target:
+            self._snapshot(self.x, self.y, rel, "threshold")
+            self.eps_target *= opt.eps_factor
+        if opt.snapshot_every > 0 and self.k >= self.next_snapshot:
+            self._snapshot(self.x, self.y, rel, "periodic")
+            while self.next_snapshot <= self.k:
+                self.next_snapshot += opt.snapshot_every
+        kind = NO_RESTART
+        margin = math.inf
+        if not converged and opt.restarts:
+            r_c, xt, yt = self.fixed_point_measure(self.x, self.y)
+            margin = min(_rel_gap(r_c, opt.beta_suff * self.r_restart), _rel_gap(r_c, opt.beta_nec * self.r_restart),
+                         _rel_gap(r_c, self.r_prev))
+            if restart_decision(r_c, self.r_restart, self.r_prev, self.t, self.k, opt):
+                kind = RESTART_TO_PDHG_STEP
+                if opt.primal_weight:
+                    dx = float(np.linalg.norm(xt - self.x_r))
+                    dy = float(np.linalg.norm(yt - self.y_r))
+                    self.omega, self.pid_integral, self.pid_prev = pid_primal_weight(
+                        self.omega, dx, dy, self.pid_integral, self.pid_prev, opt.pid_kp, opt.pid_ki, opt.pid_kd)
+                self.x, self.y = xt.copy(), yt.copy()
+                self.x_r, self.y_r = xt.copy(), yt.copy()
+                self.r_restart = r_c
+                self.t = 0
+                self.restart_count += 1
+            self.r_prev = r_c
+        self.trace.append(EvalRecord(self.k, kind, RESTART_TO_CURRENT, self.omega, rel, margin, kk["rel_gap"]))
         return converged
 
     # -- feasibility polishing ---------------------------------------------
