@@ -64,8 +64,9 @@ enum { PDHG_FP64 = 0, PDHG_FP32 = 1, PDHG_MIXED = 2 };
 /* which point pdhg_kkt / pdhg_get_solution look at */
 enum { PDHG_CURRENT = 0, PDHG_AVERAGE = 1, PDHG_LAST_RESTART = 2 };
 
-/* restart kinds in the evaluation trace */
-enum { PDHG_NO_RESTART = 0, PDHG_RESTART_TO_CURRENT = 1, PDHG_RESTART_TO_AVERAGE = 2 };
+/* restart kinds in the evaluation trace (PDHG_RESTART_TO_PDHG_STEP: the
+ * fixed-point residual scheme's restart at T(z) of the current point) */
+enum { PDHG_NO_RESTART = 0, PDHG_RESTART_TO_CURRENT = 1, PDHG_RESTART_TO_AVERAGE = 2, PDHG_RESTART_TO_PDHG_STEP = 3 };
 
 /* Options (pdhg_default_options gives the values in parentheses). Scaling,
  * step size, restarts and the primal weight follow the PDLP line of work that
@@ -145,6 +146,15 @@ typedef struct {
   int reserved;
   int64_t barrier_cycles; /* persistent = 2: clock cycles one grid-barrier wait may last before the launch
                              gives up with PDHG_ERR_TIMEOUT; 0 = 2^31 (about a second) (0) */
+  int restart_scheme;     /* 0: PDLP's restarts on the weighted KKT error (0); 1 (with halpern = 1, single
+                             LPs, no feasibility polishing): the cuPDLP+ scheme the paper's solver follows
+                             (Section 4.1, which gives no formula; readings): the three restart rules on the
+                             fixed-point residual r(z) = ||z - T(z)||_M of the current point (T the PDHG map, M
+                             the metric ||(dx,dy)||^2 = ||dx||^2/tau + 2 dy^T Ahat dx + ||dy||^2/sigma); a
+                             restart moves the iterate and the anchor to T(z); the primal weight takes a PID
+                             step on e = ln(omega dx / dy), dx and dy the moves of the restart point */
+  int reserved2;
+  double pid_kp, pid_ki, pid_kd; /* restart_scheme = 1: PID gains of the primal weight (0.99, 0.01, 0) */
 } pdhg_options;
 
 /* Scalars of one point on the problem as given (unscaled), all FP64.

@@ -24,6 +24,13 @@ enum {
   Q_RPINF,     // max |rp / d_r|
   Q_BY,        // sum bhat * yhat               (b^T y)
   Q_DY2,       // sum (yhat - yhat_restart)^2
+  // fixed-point residual restart scheme (restart_scheme = 1): with the PDHG
+  // step (x~, y~) = T(xhat, yhat)
+  Q_FX2,       // sum (x~ - xhat)^2
+  Q_FXR2,      // sum (x~ - xhat_restart)^2
+  Q_FY2,       // sum (y~ - yhat)^2
+  Q_FXY,       // sum (y~ - yhat) (Ahat (x~ - xhat))
+  Q_FYR2,      // sum (y~ - yhat_restart)^2
   NQ
 };
 
@@ -31,9 +38,10 @@ struct EvalSums {
   double q[NQ];
 };
 
-// apply modes written by the decision kernel
-enum { APPLY_NONE = 0, APPLY_RESTART_CUR = 1, APPLY_RESTART_AVG = 2, APPLY_TAKE_AVG = 3 };
-enum { KIND_NONE = 0, KIND_CUR = 1, KIND_AVG = 2 };
+// apply modes written by the decision kernel (APPLY_RESTART_STEP: restart at
+// the PDHG step T(z) of the current point, held where the average would be)
+enum { APPLY_NONE = 0, APPLY_RESTART_CUR = 1, APPLY_RESTART_AVG = 2, APPLY_TAKE_AVG = 3, APPLY_RESTART_STEP = 4 };
+enum { KIND_NONE = 0, KIND_CUR = 1, KIND_AVG = 2, KIND_STEP = 3 };
 
 // Scalars of the method, resident in device memory so that kernels (and CUDA
 // graphs) read the current step sizes without host round trips.
@@ -71,6 +79,11 @@ struct DevState {
   // the latest scheduled snapshot: its iteration and the candidate's rel_kkt
   long long snap_k;
   double snap_rel;
+  // fixed-point residual restart scheme (restart_scheme = 1): the residual at
+  // the last restart and at the previous evaluation, the PID gains and state
+  int restart_scheme, pad2;
+  double r_restart, r_prev;
+  double pid_kp, pid_ki, pid_kd, pid_int, pid_prev;
 };
 
 enum { TERM_LP = 0, TERM_PRIMAL = 1, TERM_DUAL = 2 };

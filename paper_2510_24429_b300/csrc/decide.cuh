@@ -19,6 +19,24 @@ __device__ __forceinline__ double weighted_kkt(double p, double d, double g, dou
   return sqrt(omega * p * p + d * d / omega + g * g);
 }
 
+// The fixed-point residual ||z - T(z)||_M of an evaluated point in the
+// metric ||(dx, dy)||_M^2 = ||dx||^2 / tau + 2 dy^T Ahat dx + ||dy||^2 / sigma
+// (the cuPDLP+ restart measure; a reading)
+__device__ __forceinline__ double fixed_residual(const EvalSums& e, double tau, double sigma) {
+  const double q = e.q[Q_FX2] / tau + 2.0 * e.q[Q_FXY] + e.q[Q_FY2] / sigma;
+  return sqrt(q > 0.0 ? q : 0.0);
+}
+
+// One PID step of the primal weight on e = ln(omega dx / dy) (the cuPDLP+
+// primal weight; a reading): ln omega -= kp e + ki (sum of e) + kd (e - e_prev)
+__device__ __forceinline__ void pid_primal_weight(DevState* st, double dx, double dy) {
+  if (!(dx > 1e-10 && dy > 1e-10)) return;
+  const double e = log(st->omega * dx / dy);
+  st->pid_int += e;
+  st->omega = exp(log(st->omega) - st->pid_kp * e - st->pid_ki * st->pid_int - st->pid_kd * (e - st->pid_prev));
+  st->pid_prev = e;
+}
+
 // One evaluation's decisions (single thread): candidate, termination,
 // snapshot schedule (Algorithm 1), restart test, primal-weight update.
 static __device__ void decide_one(DevState* st, TraceRec* trace) {
@@ -77,6 +95,24 @@ static __device__ void decide_one(DevState* st, TraceRec* trace) {
   int kind = KIND_NONE, apply = APPLY_NONE;
   if (converged) {
     apply = which == KIND_AVG ? APPLY_TAKE_AVG : APPLY_NONE;
+  } else if (st->restarts_on && st->restart_scheme == 1) {
+    // the cuPDLP+ scheme (readings): PDLP's three rules on the fixed-point
+    // residual of the current point; a restart moves to its PDHG step T(z)
+    // (the iterate and the anchor) and takes a PID step of the primal weight
+    // on the moves of the restart point
+    const double rc = fixed_residual(st->cur, st->tau, st->sigma);
+    const bool restart = (rc <= st->beta_suff * st->r_restart) ||
+                         (rc <= st->beta_nec * st->r_restart && rc > st->r_prev) ||
+                         ((double)st->t >= st->beta_art * (double)st->k);
+    if (restart) {
+      kind = KIND_STEP;
+      if (st->primal_weight_on) pid_primal_weight(st, sqrt(st->cur.q[Q_FXR2]), sqrt(st->cur.q[Q_FYR2]));
+      apply = APPLY_RESTART_STEP;
+      st->r_restart = rc;
+      st->t = 0;
+      st->restarts += 1;
+    }
+    st->r_prev = rc;
   } else if (st->restarts_on) {
     const double om = st->omega;
     const double kc = weighted_kkt(cp, cd, cg, om);

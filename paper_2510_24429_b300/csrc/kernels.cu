@@ -793,7 +793,11 @@ struct EvalDualOp {
   const double* __restrict__ idc;  // 1 / D_c
   const double* __restrict__ px;
   const double* __restrict__ xr;
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+  // fixed-point residual scheme (xt != null): the primal part of the PDHG step
+  // from this point, x~ = max(0, x - tau (chat - g)), is written to xt
+  double tau = 0.0;
+  double* __restrict__ xt = nullptr;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   __device__ __forceinline__ State begin(int) { return {}; }
   __device__ __forceinline__ void finish(int j, double g, const State&) {
     const double c = ch[j];
@@ -810,6 +814,13 @@ struct EvalDualOp {
       const double d = xj - xr[j];
       acc[5] += d * d;
     }
+    if (xt) {
+      const double x1 = relu(xj - tau * (c - g));
+      xt[j] = x1;
+      const double d = x1 - xj, dr = x1 - xr[j];
+      acc[6] += d * d;
+      acc[7] += dr * dr;
+    }
   }
 };
 
@@ -819,9 +830,11 @@ template <class G>
 __device__ __forceinline__ void eval_dual_block(const Hyb& At, const G& gather_py, const double* __restrict__ ch,
                                                 const double* __restrict__ idc, const double* __restrict__ px,
                                                 const double* __restrict__ xr, double* __restrict__ partials,
-                                                bool frozen, int bid, int nblk) {
+                                                bool frozen, int bid, int nblk, double tau = 0.0,
+                                                double* __restrict__ xt = nullptr) {
   if (frozen) {
     if (threadIdx.x < 6) partials[(size_t)bid * NQ + Q_RD2S + threadIdx.x] = 0.0;
+    if (threadIdx.x < 2) partials[(size_t)bid * NQ + Q_FX2 + threadIdx.x] = 0.0;
     return;
   }
   EvalDualOp op;
@@ -829,9 +842,11 @@ __device__ __forceinline__ void eval_dual_block(const Hyb& At, const G& gather_p
   op.idc = idc;
   op.px = px;
   op.xr = xr;
+  op.tau = tau;
+  op.xt = xt;
   hyb_dot(At, At.v, gather_py, op, 0, bid, nblk);
-  const bool mx[6] = {false, false, true, false, false, false};
-  block_reduce<6>(op.acc, mx);
+  const bool mx[8] = {false, false, true, false, false, false, false, false};
+  block_reduce<8>(op.acc, mx);
   if (threadIdx.x == 0) {
     double* p = partials + (size_t)bid * NQ;
     p[Q_RD2S] = op.acc[0];
@@ -840,6 +855,8 @@ __device__ __forceinline__ void eval_dual_block(const Hyb& At, const G& gather_p
     p[Q_CX] = op.acc[3];
     p[Q_XZ] = op.acc[4];
     p[Q_DX2] = op.acc[5];
+    p[Q_FX2] = op.acc[6];
+    p[Q_FXR2] = op.acc[7];
   }
 }
 
@@ -858,7 +875,12 @@ struct EvalPrimalOp {
   const double* __restrict__ idr;  // 1 / D_r
   const double* __restrict__ py;
   const double* __restrict__ yr;
-  double acc[5] = {0, 0, 0, 0, 0};
+  // fixed-point residual scheme (ht != null): ht = Ahat x~; the dual part of
+  // the PDHG step, y~ = y + sigma (bhat - (2 Ahat x~ - Ahat x)), is written to yt
+  double sigma = 0.0;
+  const double* __restrict__ ht = nullptr;
+  double* __restrict__ yt = nullptr;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   __device__ __forceinline__ State begin(int) { return {}; }
   __device__ __forceinline__ void finish(int i, double h, const State&) {
     const double b = bh[i];
@@ -873,6 +895,15 @@ struct EvalPrimalOp {
       const double d = yi - yr[i];
       acc[4] += d * d;
     }
+    if (ht) {
+      const double h1 = ht[i];
+      const double y1 = yi + sigma * (b - (2.0 * h1 - h));
+      yt[i] = y1;
+      const double d = y1 - yi, dr = y1 - yr[i];
+      acc[5] += d * d;
+      acc[6] += d * (h1 - h);
+      acc[7] += dr * dr;
+    }
   }
 };
 
@@ -880,9 +911,12 @@ template <class G>
 __device__ __forceinline__ void eval_primal_block(const Hyb& A, const G& gather_px, const double* __restrict__ bh,
                                                   const double* __restrict__ idr, const double* __restrict__ py,
                                                   const double* __restrict__ yr, double* __restrict__ partials,
-                                                  bool frozen, int bid, int nblk) {
+                                                  bool frozen, int bid, int nblk, double sigma = 0.0,
+                                                  const double* __restrict__ ht = nullptr,
+                                                  double* __restrict__ yt = nullptr) {
   if (frozen) {
     if (threadIdx.x < 5) partials[(size_t)bid * NQ + Q_RP2S + threadIdx.x] = 0.0;
+    if (threadIdx.x < 3) partials[(size_t)bid * NQ + Q_FY2 + threadIdx.x] = 0.0;
     return;
   }
   EvalPrimalOp op;
@@ -890,9 +924,12 @@ __device__ __forceinline__ void eval_primal_block(const Hyb& A, const G& gather_
   op.idr = idr;
   op.py = py;
   op.yr = yr;
+  op.sigma = sigma;
+  op.ht = ht;
+  op.yt = yt;
   hyb_dot(A, A.v, gather_px, op, 0, bid, nblk);
-  const bool mx[5] = {false, false, true, false, false};
-  block_reduce<5>(op.acc, mx);
+  const bool mx[8] = {false, false, true, false, false, false, false, false};
+  block_reduce<8>(op.acc, mx);
   if (threadIdx.x == 0) {
     double* p = partials + (size_t)bid * NQ;
     p[Q_RP2S] = op.acc[0];
@@ -900,6 +937,9 @@ __device__ __forceinline__ void eval_primal_block(const Hyb& A, const G& gather_
     p[Q_RPINF] = op.acc[2];
     p[Q_BY] = op.acc[3];
     p[Q_DY2] = op.acc[4];
+    p[Q_FY2] = op.acc[5];
+    p[Q_FXY] = op.acc[6];
+    p[Q_FYR2] = op.acc[7];
   }
 }
 
@@ -910,6 +950,28 @@ __global__ void __launch_bounds__(STEP_TPB_MAX) k_eval_primal(Hyb A, const doubl
                                                      const int* __restrict__ binst) {
   eval_primal_block(A, GlobalGather<double>{px}, bh, idr, py, yr, partials,
                     binst && sts[binst[blockIdx.x]].frozen, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// the evaluation of the current point with the fixed-point residual's parts
+// (restart_scheme = 1, single LPs): the dual pass also writes x~, the primal
+// pass (after ht = Ahat x~) also writes y~
+__global__ void __launch_bounds__(STEP_TPB_MAX) k_eval_dual_fp(Hyb At, const double* __restrict__ py,
+                                                      const double* __restrict__ ch, const double* __restrict__ idc,
+                                                      const double* __restrict__ px, const double* __restrict__ xr,
+                                                      double* __restrict__ partials, const DevState* __restrict__ st,
+                                                      double* __restrict__ xt) {
+  eval_dual_block(At, GlobalGather<double>{py}, ch, idc, px, xr, partials, false, (int)blockIdx.x, (int)gridDim.x,
+                  st->tau, xt);
+}
+__global__ void __launch_bounds__(STEP_TPB_MAX) k_eval_primal_fp(Hyb A, const double* __restrict__ px,
+                                                        const double* __restrict__ bh,
+                                                        const double* __restrict__ idr,
+                                                        const double* __restrict__ py, const double* __restrict__ yr,
+                                                        double* __restrict__ partials,
+                                                        const DevState* __restrict__ st,
+                                                        const double* __restrict__ ht, double* __restrict__ yt) {
+  eval_primal_block(A, GlobalGather<double>{px}, bh, idr, py, yr, partials, false, (int)blockIdx.x, (int)gridDim.x,
+                    st->sigma, ht, yt);
 }
 
 // warp q sums quantity q over the blocks in a fixed order
@@ -932,6 +994,7 @@ __global__ void k_init_restart_ref(DevState* st) {
   st->rs_p = st->pc_p = p;
   st->rs_d = st->pc_d = d;
   st->rs_g = st->pc_g = g;
+  st->r_restart = st->r_prev = fixed_residual(st->cur, st->tau, st->sigma);  // 0 unless evaluated with it
 }
 
 __global__ void k_decide(DevState* st, TraceRec* trace) { decide_one(st, trace); }
@@ -1084,15 +1147,16 @@ __global__ void k_apply(const DevState* __restrict__ st, double* __restrict__ x,
   if (mode == APPLY_NONE) return;
   const int len = n > m ? n : m;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+    // APPLY_RESTART_STEP: xa, ya hold the PDHG step T(z) of the current point
     if (i < n) {
-      if (mode == APPLY_RESTART_AVG || mode == APPLY_TAKE_AVG) x[i] = xa[i];
+      if (mode == APPLY_RESTART_AVG || mode == APPLY_TAKE_AVG || mode == APPLY_RESTART_STEP) x[i] = xa[i];
       if (mode != APPLY_TAKE_AVG) {
         xr[i] = x[i];
         xs[i] = 0.0;
       }
     }
     if (i < m) {
-      if (mode == APPLY_RESTART_AVG || mode == APPLY_TAKE_AVG) y[i] = ya[i];
+      if (mode == APPLY_RESTART_AVG || mode == APPLY_TAKE_AVG || mode == APPLY_RESTART_STEP) y[i] = ya[i];
       if (mode != APPLY_TAKE_AVG) {
         yr[i] = y[i];
         ys[i] = 0.0;
@@ -1144,7 +1208,7 @@ __global__ void k_apply32(const DevState* __restrict__ st, float* __restrict__ x
         x[i] = xa[i];
         x32[i] = (float)xa[i];
       } else {
-        if (mode == APPLY_RESTART_AVG) {
+        if (mode == APPLY_RESTART_AVG || mode == APPLY_RESTART_STEP) {
           const float v = (float)xa[i];
           x32[i] = v;
           x[i] = (double)v;
@@ -1158,7 +1222,7 @@ __global__ void k_apply32(const DevState* __restrict__ st, float* __restrict__ x
         y[i] = ya[i];
         y32[i] = (float)ya[i];
       } else {
-        if (mode == APPLY_RESTART_AVG) {
+        if (mode == APPLY_RESTART_AVG || mode == APPLY_RESTART_STEP) {
           const float v = (float)ya[i];
           y32[i] = v;
           y[i] = (double)v;
@@ -1198,6 +1262,7 @@ __global__ void k_promote_state(DevState* st) {
   st->rs_p = st->pc_p = p;
   st->rs_d = st->pc_d = d;
   st->rs_g = st->pc_g = g;
+  st->r_restart = st->r_prev = fixed_residual(st->cur, st->tau, st->sigma);  // restart_scheme = 1
   st->t = 0;
 }
 
@@ -1716,6 +1781,14 @@ void launch_eval_point(const Hyb& A, const Hyb& At, const double* px, const doub
                        double* partials, int nb, cudaStream_t s, const DevState* sts, const int* binst, int tpb) {
   k_eval_dual<<<nb, tpb, 0, s>>>(At, py, ch, idc, px, xr, partials, sts, binst);
   k_eval_primal<<<nb, tpb, 0, s>>>(A, px, bh, idr, py, yr, partials, sts, binst);
+}
+void launch_eval_point_fp(const Hyb& A, const Hyb& At, const double* px, const double* py, const double* bh,
+                          const double* ch, const double* idr, const double* idc, const double* xr, const double* yr,
+                          double* partials, int nb, const DevState* st, double* xt, double* ht, double* yt,
+                          int spmv_grid, cudaStream_t s, int tpb) {
+  k_eval_dual_fp<<<nb, tpb, 0, s>>>(At, py, ch, idc, px, xr, partials, st, xt);
+  k_spmv<<<spmv_grid, TPB, 0, s>>>(A, xt, ht);
+  k_eval_primal_fp<<<nb, tpb, 0, s>>>(A, px, bh, idr, py, yr, partials, st, ht, yt);
 }
 void launch_decide_b(DevState* sts, int count, cudaStream_t s) { k_decide_b<<<(count + 127) / 128, 128, 0, s>>>(sts, count); }
 void launch_add_counters_b(DevState* sts, int count, long long dk, cudaStream_t s) {

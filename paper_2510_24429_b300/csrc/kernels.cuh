@@ -145,6 +145,13 @@ void launch_eval_point(const Hyb& A, const Hyb& At, const double* px, const doub
                        const double* ch, const double* idr, const double* idc, const double* xr, const double* yr,
                        double* partials, int nb, cudaStream_t s, const DevState* sts = nullptr,
                        const int* binst = nullptr, int tpb = TPB);
+// The current point's evaluation with the parts of its fixed-point residual
+// (restart_scheme = 1; single LPs): writes the PDHG step T(px, py) into
+// (xt, yt), using ht (m entries) for Ahat xt; tau and sigma from *st
+void launch_eval_point_fp(const Hyb& A, const Hyb& At, const double* px, const double* py, const double* bh,
+                          const double* ch, const double* idr, const double* idc, const double* xr, const double* yr,
+                          double* partials, int nb, const DevState* st, double* xt, double* ht, double* yt,
+                          int spmv_grid, cudaStream_t s, int tpb);
 // ---- batch (count instances; xoff/yoff: instance ranges of the column and row vectors) ----
 void launch_decide_b(DevState* sts, int count, cudaStream_t s);
 void launch_add_counters_b(DevState* sts, int count, long long dk, cudaStream_t s);

@@ -397,6 +397,16 @@ void eval_point(pdhg_ctx* ctx, const double* px, const double* py, const double*
   launch_eval_finalize(ctx->partials, ctx->nb_eval, dst, ctx->stream);
 }
 
+// The current point's evaluation with its fixed-point residual (option
+// restart_scheme = 1): the PDHG step T(x, y) goes to (xavg, yavg), which this
+// form (reflected Halpern, no averages) does not otherwise use.
+void eval_point_fp(pdhg_ctx* ctx, EvalSums* dst) {
+  launch_eval_point_fp(ctx->A, ctx->At, ctx->x, ctx->y, ctx->bh, ctx->ch, ctx->idr, ctx->idc, ctx->xr, ctx->yr,
+                       ctx->partials, ctx->nb_eval, ctx->st, ctx->xavg, ctx->tmp_m, ctx->yavg,
+                       stride_grid(ctx, ctx->A), ctx->stream, 32 * ctx->wpb);
+  launch_eval_finalize(ctx->partials, ctx->nb_eval, dst, ctx->stream);
+}
+
 // During the FP32 phase: refresh the FP64 copies of the current iterate.
 void widen_current(pdhg_ctx* ctx) {
   launch_widen(ctx->x, ctx->x32, ctx->n, vec_grid(ctx, ctx->n), ctx->stream);
@@ -1111,6 +1121,10 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   h.halpern = o.halpern;
   h.rho = o.halpern_reflect;
   h.gap_tol = o.gap_tol;
+  h.restart_scheme = o.restart_scheme;
+  h.pid_kp = o.pid_kp;
+  h.pid_ki = o.pid_ki;
+  h.pid_kd = o.pid_kd;
   *ctx->h_st = h;
   CK(ctx, cudaMemcpyAsync(ctx->st, ctx->h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
   launch_finish_setup(ctx->st, ctx->scal, o.step_factor, o.primal_weight, s);
@@ -1167,8 +1181,12 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
     CK(ctx, cudaMemcpyAsync(ctx->yr, ctx->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
     ctx->phase32 = true;
   }
-  // restart reference = the starting point
-  eval_point(ctx, ctx->x, ctx->y, nullptr, nullptr, &ctx->st->cur);
+  // restart reference = the starting point (with its fixed-point residual
+  // under restart_scheme = 1)
+  if (o.restart_scheme == 1)
+    eval_point_fp(ctx, &ctx->st->cur);
+  else
+    eval_point(ctx, ctx->x, ctx->y, nullptr, nullptr, &ctx->st->cur);
   launch_init_restart_ref(ctx->st, s);
   CK(ctx, cudaGetLastError());
   rs = read_state(ctx);
@@ -1317,14 +1335,17 @@ pdhg_status enqueue_eval(pdhg_ctx* ctx) {
       launch_make_average(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, n, m, ctx->st, gv, s);
     eval_point(ctx, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, &ctx->st->avg);
   }
-  eval_point(ctx, ctx->x, ctx->y, ctx->xr, ctx->yr, &ctx->st->cur);
+  if (o.restart_scheme == 1)
+    eval_point_fp(ctx, &ctx->st->cur);
+  else
+    eval_point(ctx, ctx->x, ctx->y, ctx->xr, ctx->yr, &ctx->st->cur);
   launch_decide(ctx->st, ctx->trace, s);
   if (p32)
     launch_apply32(ctx->st, ctx->x32, ctx->y32, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, ctx->xsum32,
                    ctx->ysum32, n, m, gv, s);
   else
     launch_apply(ctx->st, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, ctx->xsum, ctx->ysum, n, m, gv, s);
-  ctx->launches += (o.restarts && !o.halpern ? 4 : 0) + 3 + 2;
+  ctx->launches += (o.restarts && !o.halpern ? 4 : 0) + 3 + 2 + (o.restart_scheme == 1 ? 1 : 0);
   CK(ctx, cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevState) * ctx->count, cudaMemcpyDeviceToHost, s));
   CK(ctx, cudaGetLastError());
   return PDHG_OK;
@@ -2047,6 +2068,10 @@ void pdhg_default_options(pdhg_options* o) {
   o->dual_hot_cols = 0;
   o->singleton_order = 1;
   o->barrier_cycles = 0;
+  o->restart_scheme = 0;
+  o->pid_kp = 0.99;
+  o->pid_ki = 0.01;
+  o->pid_kd = 0.0;
   o->record_for_backward = 0;
   o->checkpoint_every = 50;
   o->step_block = 256;
@@ -2114,6 +2139,12 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     return fail(nullptr, PDHG_ERR_INVALID, "gap_tol must be >= 0, feas_polish 0 or 1 and polish_div >= 1");
   if (o.feas_polish && (o.persistent || o.record_for_backward))
     return fail(nullptr, PDHG_ERR_INVALID, "feas_polish = 1 needs no persistent loop and no recording");
+  if (o.restart_scheme < 0 || o.restart_scheme > 1 ||
+      (o.restart_scheme == 1 && (o.halpern != 1 || o.feas_polish || o.persistent)) || !std::isfinite(o.pid_kp) ||
+      !std::isfinite(o.pid_ki) || !std::isfinite(o.pid_kd))
+    return fail(nullptr, PDHG_ERR_INVALID,
+                "restart_scheme must be 0 or 1 (1: with halpern = 1, no feasibility polishing or persistent loop) "
+                "and the PID gains finite");
 
   // Checks of host inputs (CSR structure, finite data) on host threads, beside
   // the context's set-up: stream creation, allocations and the upload depend
@@ -2327,7 +2358,10 @@ static pdhg_status iterate_impl(pdhg_ctx* ctx, int64_t max_iters, double tol, in
         // FP64 polishing phase: continue in FP64 from the FP32 iterate (held
         // exactly in x, y), keeping D_r, D_c, eta and omega; the iterate
         // becomes the restart reference and the FP64 averages start empty
-        eval_point(ctx, ctx->x, ctx->y, nullptr, nullptr, &ctx->st->cur);
+        if (o.restart_scheme == 1)
+          eval_point_fp(ctx, &ctx->st->cur);  // the fixed-point residual at the switch
+        else
+          eval_point(ctx, ctx->x, ctx->y, nullptr, nullptr, &ctx->st->cur);
         launch_promote_state(ctx->st, s);
         CK(ctx, cudaMemsetAsync(ctx->xsum, 0, sizeof(double) * n, s));
         CK(ctx, cudaMemsetAsync(ctx->ysum, 0, sizeof(double) * m, s));
@@ -2580,8 +2614,9 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
   if (o.persistent < 0 || o.persistent > 2 || (o.persistent && o.kernel_timing) || o.barrier_cycles < 0)
     return fail(nullptr, PDHG_ERR_INVALID,
                 "persistent must be 0, 1 or 2 and excludes kernel timing; barrier_cycles must be >= 0");
-  if (o.feas_polish || !(o.gap_tol >= 0.0))
-    return fail(nullptr, PDHG_ERR_INVALID, "batch: no feasibility polishing (single LPs only), gap_tol >= 0");
+  if (o.feas_polish || !(o.gap_tol >= 0.0) || o.restart_scheme != 0)
+    return fail(nullptr, PDHG_ERR_INVALID,
+                "batch: no feasibility polishing or fixed-point restart scheme (single LPs only), gap_tol >= 0");
   int64_t mt = 0, nt = 0, zt = 0;
   for (int i = 0; i < count; ++i) {
     const pdhg_lp_desc& L = lps[i];

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "libpdhg.so")
 STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "TIMEOUT", "NUMERIC", "STATE", "NOT_CONVERGED"]
 PDHG_FP64, PDHG_FP32, PDHG_MIXED = 0, 1, 2
 PDHG_CURRENT, PDHG_AVERAGE, PDHG_LAST_RESTART = 0, 1, 2
-PDHG_NO_RESTART, PDHG_RESTART_TO_CURRENT, PDHG_RESTART_TO_AVERAGE = 0, 1, 2
+PDHG_NO_RESTART, PDHG_RESTART_TO_CURRENT, PDHG_RESTART_TO_AVERAGE, PDHG_RESTART_TO_PDHG_STEP = 0, 1, 2, 3
 
 
 class pdhg_options(C.Structure):
@@ -65,6 +65,11 @@ class pdhg_options(C.Structure):
         ("singleton_order", C.c_int),
         ("reserved", C.c_int),
         ("barrier_cycles", C.c_int64),
+        ("restart_scheme", C.c_int),
+        ("reserved2", C.c_int),
+        ("pid_kp", C.c_double),
+        ("pid_ki", C.c_double),
+        ("pid_kd", C.c_double),
     ]
 
 
@@ -215,7 +220,7 @@ def pdhg_default_options(**overrides) -> pdhg_options:
     o = pdhg_options()
     load().pdhg_default_options(C.byref(o))
     for k, v in overrides.items():
-        if not hasattr(o, k) or k == "reserved":
+        if not hasattr(o, k) or k.startswith("reserved"):
             raise KeyError(f"unknown option {k}")
         setattr(o, k, v)
     return o

@@ -122,6 +122,27 @@ def test_large_halpern_fp64_100_iterations(large):
     print(f"large LP, Halpern FP64 vs oracle after 100 iterations: x {rel_err(x, xo):.1e}, y {rel_err(y, yo):.1e}")
 
 
+def test_large_fixed_point_scheme_matches_oracle(large):
+    """The cuPDLP+ restart scheme (restart_scheme = 1, reflected Halpern, PID
+    primal weight) at full size: 192 iterations, three evaluations (two
+    artificial restarts to T(z) with PID steps), decisions equal, iterates at
+    1e-10."""
+    lp, orc0 = large
+    orc = _fresh(orc0, restarts=True, halpern=True, restart_scheme=1)
+    orc.r_restart = orc.r_prev = orc.fixed_point_measure(orc.x, orc.y)[0]
+    orc.pid_integral, orc.pid_prev = 0.0, 0.0
+    orc.run(192)
+    with _solver(lp, orc, halpern=1, restart_scheme=1) as sol:
+        sol.iterate(192)
+        tr = sol.trace()
+        assert compare_traces(tr, orc.trace) == 3
+        assert sum(1 for r in tr if r["kind"] == P.PDHG_RESTART_TO_PDHG_STEP) >= 2
+        for g, o in zip(tr, orc.trace):
+            assert g["omega"] == pytest.approx(o.omega, rel=1e-10)
+        assert_iterates_close(sol, orc, 1e-10)
+        assert_iterates_close(sol, orc, 1e-10, P.PDHG_LAST_RESTART)
+
+
 def test_large_fp32_100_iterations_close_to_fp64_oracle(large):
     """FP32 half-steps against the FP64 oracle: the error is FP32 rounding
     (unit roundoff 6e-8) carried through 100 iterations; it is printed and
