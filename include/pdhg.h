@@ -122,7 +122,8 @@ typedef struct {
                              segments whose partial sums are added per column, while the other columns take
                              the direct step; 1 = on, 0 = off, -1 = on for single LPs with m >= 2^18 and
                              nnz >= 2^23 (-1) */
-  int panel_rows;         /* entries of y per panel; 0 = as many as fit in shared memory (0; at most 28160) */
+  int panel_rows;         /* entries of y per panel; 0 = as many as fit in shared memory (0; at most 28160, or
+                             56320 with precision PDHG_FP32, whose panels hold FP32 entries only) */
   int halpern;            /* 1: reflected Halpern iteration (the cuPDLP+ line, Section 4.1): z <- w ((1 + rho)
                              T(z) - rho z) + (1 - w) z_r with T the PDHG map, w = (t + 1) / (t + 2), t the
                              iterations since the last restart, z_r the last restart point; no averaging (the
@@ -143,7 +144,11 @@ typedef struct {
   int polish_div;         /* polishing phase budget divisor (8) */
   int singleton_order;    /* 1: number the columns with one entry by the row of that entry (single LPs), so
                              that the step kernels gather them nearly in order; 0: by the caller's order (1) */
-  int reserved;
+  int panel_min_len;      /* panel-tiled primal step: columns whose units (see long_row_min, rows_per_thread)
+                             hold only columns with at least this many entries go to the panels; 0 = 32 for
+                             the layout of FP32 steps and long_row_min for FP64 steps (0). PDHG_FP32 layouts
+                             also take twice the rows per panel (FP32 entries of y); PDHG_MIXED keeps one
+                             layout of each kind, for its FP32 and its FP64 phase */
   int64_t barrier_cycles; /* persistent = 2: clock cycles one grid-barrier wait may last before the launch
                              gives up with PDHG_ERR_TIMEOUT; 0 = 2^31 (about a second) (0) */
   int restart_scheme;     /* 0: PDLP's restarts on the weighted KKT error (0); 1 (with halpern = 1, single
@@ -153,7 +158,14 @@ typedef struct {
                              the metric ||(dx,dy)||^2 = ||dx||^2/tau + 2 dy^T Ahat dx + ||dy||^2/sigma); a
                              restart moves the iterate and the anchor to T(z); the primal weight takes a PID
                              step on e = ln(omega dx / dy), dx and dy the moves of the restart point */
-  int reserved2;
+  int values32;           /* FP64 steps on FP32 copies of A's unscaled values, read with FP64 arithmetic: the
+                             values are then exact when every value of A is an FP32 number (checked at
+                             create), and the steps stream 4 bytes less per entry; they apply the scaling
+                             D_r, D_c per row and column and gather D_c xbar and D_r y. -1 = on for PDHG_MIXED
+                             (its FP64 phase) when A's values are all FP32 numbers, off otherwise; 0 = off;
+                             1 = on (PDHG_FP64 or PDHG_MIXED; PDHG_ERR_INVALID if a value of A is not an FP32
+                             number). Single LPs, not persistent, no recording; the dual step then stages no
+                             entries of xbar (dual_hot_cols) in FP64 phases (-1) */
   double pid_kp, pid_ki, pid_kd; /* restart_scheme = 1: PID gains of the primal weight (0.99, 0.01, 0) */
 } pdhg_options;
 
@@ -193,6 +205,7 @@ typedef struct {
   int feas_polished;              /* 1: the current iterate is a polished pair (x_p, y_d) that passed the test */
   int persistent_grid;            /* persistent = 2: blocks of the cooperative launch (0 before the first) */
   int64_t graph_launches;         /* CUDA-graph launches by pdhg_iterate so far */
+  int values32;                   /* 1: FP64 steps read the FP32 copies of A's unscaled values (option values32) */
 } pdhg_info;
 
 /* One feasibility polishing attempt. */

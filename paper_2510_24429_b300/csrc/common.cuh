@@ -129,6 +129,7 @@ struct Hyb {
   int* ci = nullptr;          // [slots] column index (internal numbering)
   double* v = nullptr;        // [slots] value
   float* v32 = nullptr;       // [slots] value rounded to FP32 (FP32 / mixed precision only)
+  float* u32 = nullptr;       // [slots] unscaled value, exactly (option values32 only)
   unsigned* check = nullptr;  // checked build (PDHG_CHECKED): the context's error word
   int units() const { return n_units; }
 };
@@ -140,7 +141,10 @@ enum { CHECK_UNIT = 1, CHECK_COLUMN = 2 };
 // ---------------------------------------------------------------------------
 // device helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double relu(double v) { return v < 0.0 ? 0.0 : v; }  // NaN passes through
+// max(0, v) for FP64 by the sign bit, on the integer pipe (the FP64 pipe is
+// the scarce one): -0 and negative numbers give +0, NaN passes through (NaNs
+// that arithmetic makes are positive)
+__device__ __forceinline__ double relu(double v) { return __double2hiint(v) < 0 ? 0.0 : v; }
 __device__ __forceinline__ float relu(float v) { return v < 0.0f ? 0.0f : v; }
 
 // slot of entry e of row (32 q + lane) in a slice of 32 R rows padded to Lp

@@ -22,6 +22,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
+#include <utility>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -162,10 +164,41 @@ struct GlobalGather {
 // entries) and finish(r, acc, state). Long rows: a warp per row, 4 entries per
 // lane per step (two pairs from two contiguous halves). Slices: R rows per thread, 2 entries per load, so a thread
 // has 2R independent gathers in flight per step.
-template <int R, class T, class Op, class G>
-__device__ __forceinline__ void slice_dot(const Hyb& H, const T* __restrict__ vals, int row0, int nvalid,
+// The values have type V and the gathered vector, the products and the sums
+// type T (the type the gather returns): V = T, or FP32 values with FP64
+// arithmetic (every FP32 value is exactly an FP64 value).
+template <class G>
+using GatherT = typename std::decay<decltype(std::declval<const G&>()(0))>::type;
+
+// A value of type V as the arithmetic type T. FP32 to FP64 moves the bit
+// fields with integer operations (the sign, the exponent rebiased by
+// 1023 - 127 = 896, the 23 mantissa bits at the top of the 52), exact for
+// zeros and normal numbers, the only FP32 values option values32 admits: a
+// conversion instruction would run on the FP64 pipe, which the FP64 steps'
+// multiply-adds already keep busy.
+template <class T, class V>
+struct AsAcc {
+  static __device__ __forceinline__ T get(V v) { return v; }
+};
+template <>
+struct AsAcc<double, float> {
+  static __device__ __forceinline__ double get(float v) {
+    const unsigned f = __float_as_uint(v);
+    const unsigned mag = f & 0x7fffffffu;
+    const unsigned hi = (f & 0x80000000u) | (mag ? (mag >> 3) + 0x38000000u : 0u);
+    return __hiloint2double((int)hi, (int)(f << 29));
+  }
+};
+template <class T, class V>
+__device__ __forceinline__ T as_acc(V v) {
+  return AsAcc<T, V>::get(v);
+}
+
+template <int R, class V, class Op, class G>
+__device__ __forceinline__ void slice_dot(const Hyb& H, const V* __restrict__ vals, int row0, int nvalid,
                                           long long base, int Lp, const G& gather, Op& op, unsigned long long pol,
                                           int lane) {
+  using T = GatherT<G>;
   typename Op::State st[R];
   T acc[R];
 #pragma unroll
@@ -179,7 +212,7 @@ __device__ __forceinline__ void slice_dot(const Hyb& H, const T* __restrict__ va
     for (int q = 0; q < R; ++q) {
       const long long k = base + 32 * q + lane;
       const int c = ld_stream(H.ci + k, pol);
-      acc[q] += ld_stream(vals + k, pol) * gather(c);
+      acc[q] += as_acc<T>(ld_stream(vals + k, pol)) * gather(c);
     }
   } else {
     const int L2 = Lp >> 1;
@@ -189,10 +222,10 @@ __device__ __forceinline__ void slice_dot(const Hyb& H, const T* __restrict__ va
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         const int2 c = ld_stream2(H.ci + k + 64 * q, pol);
-        const typename Pair<T>::type a = ld_stream2(vals + k + 64 * q, pol);
+        const typename Pair<V>::type a = ld_stream2(vals + k + 64 * q, pol);
         const T g0 = gather(c.x), g1 = gather(c.y);
-        acc[q] += a.x * g0;
-        acc[q] += a.y * g1;
+        acc[q] += as_acc<T>(a.x) * g0;
+        acc[q] += as_acc<T>(a.y) * g1;
       }
       k += 64 * R;
     }
@@ -222,9 +255,10 @@ struct CheckedGather {
 
 // One unit of H (a long row, or a slice of 32*R rows) for the dot-product
 // visitor below.
-template <class T, class Op, class G>
-__device__ __forceinline__ void unit_dot(const Hyb& H, const T* __restrict__ vals, int u, const G& gather_in, Op& op,
+template <class V, class Op, class G>
+__device__ __forceinline__ void unit_dot(const Hyb& H, const V* __restrict__ vals, int u, const G& gather_in, Op& op,
                                          unsigned long long pol, int lane) {
+  using T = GatherT<G>;
 #ifdef PDHG_CHECKED
   if (!unit_ok(H, u)) return;
   const CheckedGather<T, G> gather{gather_in, H.cols, H.check};
@@ -244,19 +278,19 @@ __device__ __forceinline__ void unit_dot(const Hyb& H, const T* __restrict__ val
 #pragma unroll 2
     for (long long k = beg + 2 * lane; k < end; k += 128) {
       const int2 c0 = ld_stream2(H.ci + k, pol);
-      const typename Pair<T>::type a = ld_stream2(vals + k, pol);
+      const typename Pair<V>::type a = ld_stream2(vals + k, pol);
       const bool second = k + 64 < end;
       const int2 c1 = second ? ld_stream2(H.ci + k + 64, pol) : make_int2(0, 0);
-      typename Pair<T>::type b;
-      b.x = T(0);
-      b.y = T(0);
+      typename Pair<V>::type b;
+      b.x = V(0);
+      b.y = V(0);
       if (second) b = ld_stream2(vals + k + 64, pol);
       const T g0 = gather(c0.x), g1 = gather(c0.y);
       const T g2 = gather(c1.x), g3 = gather(c1.y);
-      acc += a.x * g0;
-      acc += a.y * g1;
-      acc += b.x * g2;
-      acc += b.y * g3;
+      acc += as_acc<T>(a.x) * g0;
+      acc += as_acc<T>(a.y) * g1;
+      acc += as_acc<T>(b.x) * g2;
+      acc += as_acc<T>(b.y) * g3;
     }
     acc = warp_sum(acc);
     if (lane == 0) op.finish(row, acc, st);
@@ -275,8 +309,8 @@ __device__ __forceinline__ void unit_dot(const Hyb& H, const T* __restrict__ val
 // over a grid of nblk blocks, of which this block is block bid (by default the
 // launch's own grid; the persistent batch solve passes the virtual block it
 // stands in for)
-template <class T, class Op, class G>
-__device__ __forceinline__ void hyb_dot(const Hyb& H, const T* __restrict__ vals, const G& gather, Op& op,
+template <class V, class Op, class G>
+__device__ __forceinline__ void hyb_dot(const Hyb& H, const V* __restrict__ vals, const G& gather, Op& op,
                                         int u_begin = 0, int bid = -1, int nblk = 0) {
   if (bid < 0) {
     bid = (int)blockIdx.x;
@@ -459,7 +493,20 @@ __global__ void k_finish_setup(DevState* st, const double* __restrict__ scal, do
 // x' = max(0, x - tau (chat - Ahat^T y)), xbar = 2x' - x, then
 // y' = y + sigma (bhat - Ahat xbar)
 // ---------------------------------------------------------------------------
-template <class T>
+// Unscaled values (SC = true; FP32 copies of A's values, FP64 arithmetic):
+// the step kernels then gather D_c xbar and D_r y in place of xbar and y,
+// since Ahat xbar = D_r (A (D_c xbar)) and Ahat^T y = D_c (A^T (D_r y)); the
+// primal step scales its row sums by D_c and writes D_c xbar, the dual step
+// scales its row sums by D_r and writes D_r y' beside y'. SC = false: the
+// scaled values, and dsc / yg are unused.
+template <class T, bool SC>
+struct ColScale {
+  const T* __restrict__ d;
+  __device__ __forceinline__ T load(int j) const { return SC ? __ldcs(d + j) : T(1); }
+  __device__ __forceinline__ T apply(T d_j, T v) const { return SC ? d_j * v : v; }
+};
+
+template <class T, bool SC = false>
 struct PrimalOp {
   using State = NoState;
   const T* __restrict__ ch;
@@ -468,11 +515,13 @@ struct PrimalOp {
   T* __restrict__ xsum;
   T tau;
   int accumulate;
+  ColScale<T, SC> dc;
   __device__ __forceinline__ State begin(int) { return {}; }
   __device__ __forceinline__ void finish(int j, T g, const State&) {
+    const T d = dc.load(j);
     const T xj = __ldcs(x + j);
-    const T xn = relu(xj - tau * (__ldcs(ch + j) - g));
-    xbar[j] = T(2) * xn - xj;  // default policy: gathered by the dual step next
+    const T xn = relu(xj - tau * (__ldcs(ch + j) - dc.apply(d, g)));
+    xbar[j] = dc.apply(d, T(2) * xn - xj);  // default policy: gathered by the dual step next
     __stcs(x + j, xn);
     if (accumulate) __stcs(xsum + j, __ldcs(xsum + j) + xn);
   }
@@ -484,14 +533,14 @@ __device__ __forceinline__ const DevState* block_state(const DevState* sts, cons
   return binst ? sts + binst[blockIdx.x] : sts;
 }
 
-template <class T>
+template <class T, class V = T>
 __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
-    k_primal_step(Hyb At, const T* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
+    k_primal_step(Hyb At, const V* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
                   T* __restrict__ x, T* __restrict__ xbar, T* __restrict__ xsum, const DevState* __restrict__ sts,
-                  const int* __restrict__ binst, int accumulate, int u_begin) {
+                  const int* __restrict__ binst, int accumulate, int u_begin, const T* __restrict__ dsc) {
   const DevState* st = block_state(sts, binst);
   if (st->frozen) return;
-  PrimalOp<T> op{ch, x, xbar, xsum, (T)st->tau, accumulate};
+  PrimalOp<T, !std::is_same<T, V>::value> op{ch, x, xbar, xsum, (T)st->tau, accumulate, {dsc}};
   hyb_dot(At, vals, GlobalGather<T>{y}, op, u_begin);
 }
 
@@ -500,6 +549,17 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STE
 __device__ __forceinline__ double halpern_weight(const DevState* st, int it) {
   const double t = (double)(st->t + it);
   return (t + 1.0) / (t + 2.0);
+}
+
+// The same, computed by one thread of the block and shared: an FP64 division
+// in every thread of a step kernel would cost the FP64 pipe more than a
+// hundred of the step's multiply-adds per row. Every thread of the block
+// must call it.
+__device__ __forceinline__ double block_halpern_weight(const DevState* st, int it) {
+  __shared__ double w_shared;
+  if (threadIdx.x == 0) w_shared = halpern_weight(st, it);
+  __syncthreads();
+  return w_shared;
 }
 
 // ---- panel-tiled primal half-step (option primal_panels) --------------------
@@ -531,9 +591,9 @@ struct PartialOp {
 };
 
 // FP32 panels take half the shared memory, so two blocks could share an SM
-template <class T>
+template <class T, class V = T>
 __global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
-    k_primal_panels(Hyb Pn, const T* __restrict__ vals, const T* __restrict__ y, int m, int H,
+    k_primal_panels(Hyb Pn, const V* __restrict__ vals, const T* __restrict__ y, int m, int H,
                     const int4* __restrict__ binfo, const int* __restrict__ ustart, const int* __restrict__ segout,
                     T* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char panel_smem[];
@@ -574,7 +634,17 @@ __global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
 // since the last restart, before this step) and the last restart point
 // (xr, yr) as anchor: x <- w ((1 + rho) x~ - rho x) + (1 - w) xr, likewise y;
 // the dual step still gathers xbar = 2 x~ - x.
+// The Halpern combination w ((1 + rho) t - rho z) + (1 - w) r, written as
+// w (t + rho (t - z)) + (1 - w) r; for the default rho = 1 the reflection
+// t + (t - z) = 2t - z is the extrapolated point the step computes anyway, so
+// the update costs one multiply and one multiply-add more
 template <class T>
+__device__ __forceinline__ T halpern_mix(T t, T z, T refl, T r, T w, T omw, T rho) {
+  const T u = rho == T(1) ? refl : t + rho * (t - z);
+  return w * u + omw * r;
+}
+
+template <class T, bool SC = false>
 struct PrimalHalpernOp {
   using State = NoState;
   const T* __restrict__ ch;
@@ -582,27 +652,35 @@ struct PrimalHalpernOp {
   T* __restrict__ xbar;
   const T* __restrict__ xr;
   T tau, w, rho;
+  ColScale<T, SC> dc;
   __device__ __forceinline__ State begin(int) { return {}; }
   __device__ __forceinline__ void finish(int j, T g, const State&) {
+    const T d = dc.load(j);
     const T xj = __ldcs(x + j);
-    const T xt = relu(xj - tau * (__ldcs(ch + j) - g));
-    xbar[j] = T(2) * xt - xj;
-    __stcs(x + j, w * ((T(1) + rho) * xt - rho * xj) + (T(1) - w) * __ldcs(xr + j));
+    const T xt = relu(xj - tau * (__ldcs(ch + j) - dc.apply(d, g)));
+    const T xb = T(2) * xt - xj;
+    xbar[j] = dc.apply(d, xb);
+    __stcs(x + j, halpern_mix(xt, xj, xb, __ldcs(xr + j), w, T(1) - w, rho));
   }
 };
 
-template <class T>
+template <class T, bool SC = false>
 struct DualHalpernOp {
   using State = NoState;
   const T* __restrict__ bh;
   T* __restrict__ y;
   const T* __restrict__ yr;
   T sigma, w, rho;
+  ColScale<T, SC> dr;
+  T* __restrict__ yg;  // SC: D_r y', gathered by the primal step next
   __device__ __forceinline__ State begin(int) { return {}; }
   __device__ __forceinline__ void finish(int i, T h, const State&) {
+    const T d = dr.load(i);
     const T yi = y[i];
-    const T yt = yi + sigma * (__ldcs(bh + i) - h);
-    y[i] = w * ((T(1) + rho) * yt - rho * yi) + (T(1) - w) * __ldcs(yr + i);
+    const T yt = yi + sigma * (__ldcs(bh + i) - dr.apply(d, h));
+    const T yn = halpern_mix(yt, yi, T(2) * yt - yi, __ldcs(yr + i), w, T(1) - w, rho);
+    y[i] = yn;
+    if (SC) yg[i] = d * yn;
   }
 };
 
@@ -614,8 +692,8 @@ struct DualHalpernOp {
 // direct step; the other blocks run the direct step over the short columns
 // (the units of At from u_begin on). One launch instead of two, so the
 // combine's latency-bound work overlaps the direct step.
-template <class T, class Op>
-__device__ __forceinline__ void short_and_combine(const Hyb& At, const T* __restrict__ vals, const T* __restrict__ y,
+template <class T, class V, class Op>
+__device__ __forceinline__ void short_and_combine(const Hyb& At, const V* __restrict__ vals, const T* __restrict__ y,
                                                   Op& op, int u_begin, int cblocks, int panels,
                                                   const T* __restrict__ partial, int ncols) {
   if ((int)blockIdx.x < cblocks) {
@@ -643,49 +721,54 @@ __device__ __forceinline__ void short_and_combine(const Hyb& At, const T* __rest
   for (int u = u_begin + gwarp; u < At.n_units; u += nwarps) unit_dot(At, vals, u, GlobalGather<T>{y}, op, pol, lane);
 }
 
-template <class T>
+template <class T, class V = T>
 __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
-    k_primal_short_combine(Hyb At, const T* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
+    k_primal_short_combine(Hyb At, const V* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
                            T* __restrict__ x, T* __restrict__ xbar, T* __restrict__ xsum,
                            const DevState* __restrict__ st, int accumulate, int u_begin, int cblocks, int panels,
-                           const T* __restrict__ partial, int ncols) {
-  PrimalOp<T> op{ch, x, xbar, xsum, (T)st->tau, accumulate};
+                           const T* __restrict__ partial, int ncols, const T* __restrict__ dsc) {
+  PrimalOp<T, !std::is_same<T, V>::value> op{ch, x, xbar, xsum, (T)st->tau, accumulate, {dsc}};
   short_and_combine(At, vals, y, op, u_begin, cblocks, panels, partial, ncols);
 }
 
-template <class T>
+template <class T, class V = T>
 __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
-    k_primal_step_halpern(Hyb At, const T* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
+    k_primal_step_halpern(Hyb At, const V* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
                           T* __restrict__ x, T* __restrict__ xbar, const T* __restrict__ xr,
-                          const DevState* __restrict__ sts, const int* __restrict__ binst, int it, int u_begin) {
+                          const DevState* __restrict__ sts, const int* __restrict__ binst, int it, int u_begin,
+                          const T* __restrict__ dsc) {
   const DevState* st = block_state(sts, binst);
   if (st->frozen) return;
-  PrimalHalpernOp<T> op{ch, x, xbar, xr, (T)st->tau, (T)halpern_weight(st, it), (T)st->rho};
+  PrimalHalpernOp<T, !std::is_same<T, V>::value> op{ch,  x, xbar, xr, (T)st->tau, (T)block_halpern_weight(st, it),
+                                                    (T)st->rho, {dsc}};
   hyb_dot(At, vals, GlobalGather<T>{y}, op, u_begin);
 }
 
-template <class T>
+template <class T, class V = T>
 __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
-    k_primal_short_combine_halpern(Hyb At, const T* __restrict__ vals, const T* __restrict__ y,
+    k_primal_short_combine_halpern(Hyb At, const V* __restrict__ vals, const T* __restrict__ y,
                                    const T* __restrict__ ch, T* __restrict__ x, T* __restrict__ xbar,
                                    const T* __restrict__ xr, const DevState* __restrict__ st, int it, int u_begin,
-                                   int cblocks, int panels, const T* __restrict__ partial, int ncols) {
-  PrimalHalpernOp<T> op{ch, x, xbar, xr, (T)st->tau, (T)halpern_weight(st, it), (T)st->rho};
+                                   int cblocks, int panels, const T* __restrict__ partial, int ncols,
+                                   const T* __restrict__ dsc) {
+  PrimalHalpernOp<T, !std::is_same<T, V>::value> op{ch,  x, xbar, xr, (T)st->tau, (T)block_halpern_weight(st, it),
+                                                    (T)st->rho, {dsc}};
   short_and_combine(At, vals, y, op, u_begin, cblocks, panels, partial, ncols);
 }
 
-template <class T>
+template <class T, class V = T>
 __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
-    k_dual_step_halpern(Hyb A, const T* __restrict__ vals, const T* __restrict__ xbar, const T* __restrict__ bh,
+    k_dual_step_halpern(Hyb A, const V* __restrict__ vals, const T* __restrict__ xbar, const T* __restrict__ bh,
                         T* __restrict__ y, const T* __restrict__ yr, const DevState* __restrict__ sts,
-                        const int* __restrict__ binst, int it) {
+                        const int* __restrict__ binst, int it, const T* __restrict__ dsc, T* __restrict__ yg) {
   const DevState* st = block_state(sts, binst);
   if (st->frozen) return;
-  DualHalpernOp<T> op{bh, y, yr, (T)st->sigma, (T)halpern_weight(st, it), (T)st->rho};
+  DualHalpernOp<T, !std::is_same<T, V>::value> op{
+      bh, y, yr, (T)st->sigma, (T)block_halpern_weight(st, it), (T)st->rho, {dsc}, yg};
   hyb_dot(A, vals, GlobalGather<T>{xbar}, op);
 }
 
-template <class T>
+template <class T, bool SC = false>
 struct DualOp {
   using State = NoState;
   const T* __restrict__ bh;
@@ -693,22 +776,26 @@ struct DualOp {
   T* __restrict__ ysum;
   T sigma;
   int accumulate;
+  ColScale<T, SC> dr;
+  T* __restrict__ yg;  // SC: D_r y', gathered by the primal step next
   __device__ __forceinline__ State begin(int) { return {}; }
   __device__ __forceinline__ void finish(int i, T h, const State&) {
-    const T yn = y[i] + sigma * (__ldcs(bh + i) - h);
-    y[i] = yn;  // default policy: gathered by the primal step next
+    const T d = dr.load(i);
+    const T yn = y[i] + sigma * (__ldcs(bh + i) - dr.apply(d, h));
+    y[i] = yn;  // default policy: gathered by the primal step next (SC: yg is)
+    if (SC) yg[i] = d * yn;
     if (accumulate) __stcs(ysum + i, __ldcs(ysum + i) + yn);
   }
 };
 
-template <class T>
+template <class T, class V = T>
 __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
-    k_dual_step(Hyb A, const T* __restrict__ vals, const T* __restrict__ xbar, const T* __restrict__ bh,
+    k_dual_step(Hyb A, const V* __restrict__ vals, const T* __restrict__ xbar, const T* __restrict__ bh,
                 T* __restrict__ y, T* __restrict__ ysum, const DevState* __restrict__ sts,
-                const int* __restrict__ binst, int accumulate) {
+                const int* __restrict__ binst, int accumulate, const T* __restrict__ dsc, T* __restrict__ yg) {
   const DevState* st = block_state(sts, binst);
   if (st->frozen) return;
-  DualOp<T> op{bh, y, ysum, (T)st->sigma, accumulate};
+  DualOp<T, !std::is_same<T, V>::value> op{bh, y, ysum, (T)st->sigma, accumulate, {dsc}, yg};
   hyb_dot(A, vals, GlobalGather<T>{xbar}, op);
 }
 
@@ -760,7 +847,7 @@ __global__ void __launch_bounds__(HOT_TPB, 1)
                             const T* __restrict__ bh, T* __restrict__ y, const T* __restrict__ yr,
                             const DevState* __restrict__ st, int it) {
   const T* sh = stage_hot(xbar, hot);
-  DualHalpernOp<T> op{bh, y, yr, (T)st->sigma, (T)halpern_weight(st, it), (T)st->rho};
+  DualHalpernOp<T> op{bh, y, yr, (T)st->sigma, (T)block_halpern_weight(st, it), (T)st->rho};
   hyb_dot(A, vals, HotGatherT<T>{xbar, sh, hot}, op);
 }
 
@@ -1169,6 +1256,17 @@ __global__ void k_apply(const DevState* __restrict__ st, double* __restrict__ x,
 // mixed precision: FP32 iteration state, FP64 evaluation and restarts (no
 // counterpart in the paper, whose PDHG runs in FP64)
 // ---------------------------------------------------------------------------
+// values32 admits zeros and normal FP32 numbers (the step kernels rebuild
+// their FP64 bit patterns with integer operations, which subnormals defeat)
+__global__ void k_fp32_inexact(const double* __restrict__ v, long long len, int* __restrict__ flag) {
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+    const double a = v[i];
+    bad |= (double)(float)a != a || (a != 0.0 && fabs(a) < 1.1754943508222875e-38);  // FP32's smallest normal
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
 __global__ void k_narrow(float* __restrict__ dst, const double* __restrict__ src, long long len) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
     dst[i] = (float)src[i];
@@ -1685,79 +1783,110 @@ void launch_finish_setup(DevState* st, const double* scal, double step_factor, i
 void launch_primal_step(const Hyb& At, const double* y, const double* ch, double* x, double* xbar, double* xsum,
                         const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst, int tpb,
                         int u_begin) {
-  k_primal_step<double><<<grid, tpb, 0, s>>>(At, At.v, y, ch, x, xbar, xsum, st, binst, accumulate, u_begin);
+  k_primal_step<double><<<grid, tpb, 0, s>>>(At, At.v, y, ch, x, xbar, xsum, st, binst, accumulate, u_begin, nullptr);
 }
 void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
                       const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst, int tpb) {
-  k_dual_step<double><<<grid, tpb, 0, s>>>(A, A.v, xbar, bh, y, ysum, st, binst, accumulate);
+  k_dual_step<double><<<grid, tpb, 0, s>>>(A, A.v, xbar, bh, y, ysum, st, binst, accumulate, nullptr, nullptr);
 }
 void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float* x, float* xbar, float* xsum,
                           const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb, int u_begin) {
-  k_primal_step<float><<<grid, tpb, 0, s>>>(At, At.v32, y, ch, x, xbar, xsum, st, nullptr, accumulate, u_begin);
+  k_primal_step<float><<<grid, tpb, 0, s>>>(At, At.v32, y, ch, x, xbar, xsum, st, nullptr, accumulate, u_begin,
+                                              nullptr);
 }
 void launch_dual_step32(const Hyb& A, const float* xbar, const float* bh, float* y, float* ysum, const DevState* st,
                         int accumulate, int grid, cudaStream_t s, int tpb) {
-  k_dual_step<float><<<grid, tpb, 0, s>>>(A, A.v32, xbar, bh, y, ysum, st, nullptr, accumulate);
+  k_dual_step<float><<<grid, tpb, 0, s>>>(A, A.v32, xbar, bh, y, ysum, st, nullptr, accumulate, nullptr, nullptr);
+}
+void launch_primal_step_u(const Hyb& At, const double* yg, const double* ch, double* x, double* xbar, double* xsum,
+                          const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb, int u_begin,
+                          const double* dc) {
+  k_primal_step<double, float><<<grid, tpb, 0, s>>>(At, At.u32, yg, ch, x, xbar, xsum, st, nullptr, accumulate,
+                                                     u_begin, dc);
+}
+void launch_dual_step_u(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
+                        const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb, const double* dr,
+                        double* yg) {
+  k_dual_step<double, float><<<grid, tpb, 0, s>>>(A, A.u32, xbar, bh, y, ysum, st, nullptr, accumulate, dr, yg);
 }
 cudaError_t configure_primal_panels() {
   cudaError_t e = cudaFuncSetAttribute(k_primal_panels<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        PANEL_SMEM_MAX);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_primal_panels<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_MAX);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_primal_panels<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             PANEL_SMEM_MAX);
   return e;
 }
-template <class T>
-void launch_panel_pass(const Hyb& Pn, const T* vals, const PanelLayout& L, const T* y, T* partial, cudaStream_t s) {
+template <class T, class V>
+void launch_panel_pass(const Hyb& Pn, const V* vals, const PanelLayout& L, const T* y, T* partial, cudaStream_t s) {
   if (L.ncols == 0) return;
   const size_t smem = sizeof(T) * (size_t)L.rows;
-  k_primal_panels<T><<<L.blocks, PANEL_TPB, smem, s>>>(Pn, vals, y, L.m, L.rows, L.binfo, L.ustart, L.segout,
-                                                        partial);
+  k_primal_panels<T, V><<<L.blocks, PANEL_TPB, smem, s>>>(Pn, vals, y, L.m, L.rows, L.binfo, L.ustart, L.segout,
+                                                           partial);
 }
-template void launch_panel_pass<double>(const Hyb&, const double*, const PanelLayout&, const double*, double*,
-                                        cudaStream_t);
-template void launch_panel_pass<float>(const Hyb&, const float*, const PanelLayout&, const float*, float*,
-                                       cudaStream_t);
-template <class T>
-void launch_primal_short_combine(const Hyb& At, const T* vals, const T* y, const T* ch, T* x, T* xbar, T* xsum,
+template void launch_panel_pass<double, double>(const Hyb&, const double*, const PanelLayout&, const double*, double*,
+                                                cudaStream_t);
+template void launch_panel_pass<float, float>(const Hyb&, const float*, const PanelLayout&, const float*, float*,
+                                              cudaStream_t);
+template void launch_panel_pass<double, float>(const Hyb&, const float*, const PanelLayout&, const double*, double*,
+                                               cudaStream_t);
+template <class T, class V>
+void launch_primal_short_combine(const Hyb& At, const V* vals, const T* y, const T* ch, T* x, T* xbar, T* xsum,
                                  const DevState* st, int accumulate, int short_grid, const PanelLayout& L,
-                                 const T* partial, int tpb, cudaStream_t s, int halpern_it) {
+                                 const T* partial, int tpb, cudaStream_t s, int halpern_it, const T* dc) {
   const int cblocks = (L.ncols + tpb - 1) / tpb;
   const int grid = cblocks + short_grid;
   if (halpern_it >= 0)
-    k_primal_short_combine_halpern<T><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xsum, st, halpern_it, L.ncols,
-                                                             cblocks, L.panels, partial, L.ncols);
+    k_primal_short_combine_halpern<T, V><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xsum, st, halpern_it,
+                                                                L.ulong, cblocks, L.panels, partial, L.ncols, dc);
   else
-    k_primal_short_combine<T><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xsum, st, accumulate, L.ncols, cblocks,
-                                                     L.panels, partial, L.ncols);
+    k_primal_short_combine<T, V><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xsum, st, accumulate, L.ulong,
+                                                        cblocks, L.panels, partial, L.ncols, dc);
 }
-template void launch_primal_short_combine<double>(const Hyb&, const double*, const double*, const double*, double*,
-                                                  double*, double*, const DevState*, int, int, const PanelLayout&,
-                                                  const double*, int, cudaStream_t, int);
-template void launch_primal_short_combine<float>(const Hyb&, const float*, const float*, const float*, float*, float*,
-                                                 float*, const DevState*, int, int, const PanelLayout&, const float*,
-                                                 int, cudaStream_t, int);
-template <class T>
-void launch_primal_step_halpern(const Hyb& At, const T* vals, const T* y, const T* ch, T* x, T* xbar, const T* xr,
+template void launch_primal_short_combine<double, double>(const Hyb&, const double*, const double*, const double*,
+                                                          double*, double*, double*, const DevState*, int, int,
+                                                          const PanelLayout&, const double*, int, cudaStream_t, int,
+                                                          const double*);
+template void launch_primal_short_combine<float, float>(const Hyb&, const float*, const float*, const float*, float*,
+                                                        float*, float*, const DevState*, int, int,
+                                                        const PanelLayout&, const float*, int, cudaStream_t, int,
+                                                        const float*);
+template void launch_primal_short_combine<double, float>(const Hyb&, const float*, const double*, const double*,
+                                                         double*, double*, double*, const DevState*, int, int,
+                                                         const PanelLayout&, const double*, int, cudaStream_t, int,
+                                                         const double*);
+template <class T, class V>
+void launch_primal_step_halpern(const Hyb& At, const V* vals, const T* y, const T* ch, T* x, T* xbar, const T* xr,
                                 const DevState* st, int it, int grid, cudaStream_t s, int tpb, const int* binst,
-                                int u_begin) {
-  k_primal_step_halpern<T><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xr, st, binst, it, u_begin);
+                                int u_begin, const T* dc) {
+  k_primal_step_halpern<T, V><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xr, st, binst, it, u_begin, dc);
 }
-template <class T>
-void launch_dual_step_halpern(const Hyb& A, const T* vals, const T* xbar, const T* bh, T* y, const T* yr,
-                              const DevState* st, int it, int grid, cudaStream_t s, int tpb, const int* binst) {
-  k_dual_step_halpern<T><<<grid, tpb, 0, s>>>(A, vals, xbar, bh, y, yr, st, binst, it);
+template <class T, class V>
+void launch_dual_step_halpern(const Hyb& A, const V* vals, const T* xbar, const T* bh, T* y, const T* yr,
+                              const DevState* st, int it, int grid, cudaStream_t s, int tpb, const int* binst,
+                              const T* dr, T* yg) {
+  k_dual_step_halpern<T, V><<<grid, tpb, 0, s>>>(A, vals, xbar, bh, y, yr, st, binst, it, dr, yg);
 }
-template void launch_primal_step_halpern<double>(const Hyb&, const double*, const double*, const double*, double*,
-                                                 double*, const double*, const DevState*, int, int, cudaStream_t,
-                                                 int, const int*, int);
-template void launch_primal_step_halpern<float>(const Hyb&, const float*, const float*, const float*, float*, float*,
-                                                const float*, const DevState*, int, int, cudaStream_t, int,
-                                                const int*, int);
-template void launch_dual_step_halpern<double>(const Hyb&, const double*, const double*, const double*, double*,
-                                               const double*, const DevState*, int, int, cudaStream_t, int,
-                                               const int*);
-template void launch_dual_step_halpern<float>(const Hyb&, const float*, const float*, const float*, float*,
-                                              const float*, const DevState*, int, int, cudaStream_t, int, const int*);
+template void launch_primal_step_halpern<double, double>(const Hyb&, const double*, const double*, const double*,
+                                                         double*, double*, const double*, const DevState*, int, int,
+                                                         cudaStream_t, int, const int*, int, const double*);
+template void launch_primal_step_halpern<float, float>(const Hyb&, const float*, const float*, const float*, float*,
+                                                       float*, const float*, const DevState*, int, int, cudaStream_t,
+                                                       int, const int*, int, const float*);
+template void launch_primal_step_halpern<double, float>(const Hyb&, const float*, const double*, const double*,
+                                                        double*, double*, const double*, const DevState*, int, int,
+                                                        cudaStream_t, int, const int*, int, const double*);
+template void launch_dual_step_halpern<double, double>(const Hyb&, const double*, const double*, const double*,
+                                                       double*, const double*, const DevState*, int, int,
+                                                       cudaStream_t, int, const int*, const double*, double*);
+template void launch_dual_step_halpern<float, float>(const Hyb&, const float*, const float*, const float*, float*,
+                                                     const float*, const DevState*, int, int, cudaStream_t, int,
+                                                     const int*, const float*, float*);
+template void launch_dual_step_halpern<double, float>(const Hyb&, const float*, const double*, const double*, double*,
+                                                      const double*, const DevState*, int, int, cudaStream_t, int,
+                                                      const int*, const double*, double*);
 template <class T>
 void launch_dual_step_hot(const Hyb& A, const T* vals, const T* xbar, int hot, const T* bh, T* y, T* ysum,
                           const DevState* st, int accumulate, int grid, cudaStream_t s, int halpern_it) {
@@ -1877,6 +2006,9 @@ void launch_apply32(const DevState* st, float* x32, float* y32, double* x, doubl
                     cudaStream_t s) {
   k_apply32<<<grid, TPB, 0, s>>>(st, x32, y32, x, y, xa, ya, xr, yr, xs, ys, n, m);
 }
+void launch_fp32_inexact(const double* v, long long len, int* flag, cudaStream_t s) {
+  if (len > 0) k_fp32_inexact<<<(int)std::min<long long>(4096, (len + TPB - 1) / TPB), TPB, 0, s>>>(v, len, flag);
+}
 void launch_promote_state(DevState* st, cudaStream_t s) { k_promote_state<<<1, 1, 0, s>>>(st); }
 void launch_polish_begin(DevState* st, int term_mode, cudaStream_t s) { k_polish_begin<<<1, 1, 0, s>>>(st, term_mode); }
 
@@ -1915,6 +2047,8 @@ void prefer_l1_for_step_kernels() {
   cudaFuncSetAttribute(k_dual_step<double>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_primal_step<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_dual_step<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_primal_step<double, float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_dual_step<double, float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_primal_short_combine<double>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_primal_short_combine<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_primal_short_combine_halpern<double>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);

@@ -49,17 +49,20 @@ void launch_primal_step(const Hyb& At, const double* y, const double* ch, double
 void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
                       const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst = nullptr,
                       int tpb = TPB);
-// reflected Halpern form of the two half-steps (values vals in precision T):
-// it = index of the step within the launches since st->t was last updated;
-// xr, yr = the anchor (the last restart point)
-template <class T>
-void launch_primal_step_halpern(const Hyb& At, const T* vals, const T* y, const T* ch, T* x, T* xbar, const T* xr,
+// reflected Halpern form of the two half-steps (values vals of type V,
+// vectors and arithmetic in precision T): it = index of the step within the
+// launches since st->t was last updated; xr, yr = the anchor (the last
+// restart point). V = float with T = double: the unscaled values (Hyb::u32),
+// with the scaling D_c (dc) and D_r (dr); y is then D_r y as written to yg
+// by the dual step, and xbar holds D_c xbar.
+template <class T, class V = T>
+void launch_primal_step_halpern(const Hyb& At, const V* vals, const T* y, const T* ch, T* x, T* xbar, const T* xr,
                                 const DevState* st, int it, int grid, cudaStream_t s, int tpb,
-                                const int* binst = nullptr, int u_begin = 0);
-template <class T>
-void launch_dual_step_halpern(const Hyb& A, const T* vals, const T* xbar, const T* bh, T* y, const T* yr,
+                                const int* binst = nullptr, int u_begin = 0, const T* dc = nullptr);
+template <class T, class V = T>
+void launch_dual_step_halpern(const Hyb& A, const V* vals, const T* xbar, const T* bh, T* y, const T* yr,
                               const DevState* st, int it, int grid, cudaStream_t s, int tpb,
-                              const int* binst = nullptr);
+                              const int* binst = nullptr, const T* dr = nullptr, T* yg = nullptr);
 // the same two half-steps in FP32 (values At.v32 / A.v32, FP32 vectors and
 // accumulation); tau and sigma are read from the FP64 state and rounded
 void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float* x, float* xbar, float* xsum,
@@ -67,6 +70,18 @@ void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float*
                           int u_begin = 0);
 void launch_dual_step32(const Hyb& A, const float* xbar, const float* bh, float* y, float* ysum, const DevState* st,
                         int accumulate, int grid, cudaStream_t s, int tpb = TPB);
+// the two half-steps in FP64 on the unscaled values in FP32 (At.u32 / A.u32,
+// exact when every value of A is an FP32 number): the primal step gathers
+// yg = D_r y and scales its sums by dc = D_c, writing D_c xbar to xbar; the
+// dual step gathers that, scales its sums by dr = D_r and writes D_r y' to yg
+void launch_primal_step_u(const Hyb& At, const double* yg, const double* ch, double* x, double* xbar, double* xsum,
+                          const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb, int u_begin,
+                          const double* dc);
+void launch_dual_step_u(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
+                        const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb, const double* dr,
+                        double* yg);
+// flag[0] = 1 if some v[i] is not exactly an FP32 number (flag is not cleared)
+void launch_fp32_inexact(const double* v, long long len, int* flag, cudaStream_t s);
 // precision conversions and the FP32 counterparts of make_average / apply
 void launch_narrow(float* dst, const double* src, long long len, int grid, cudaStream_t s);
 void launch_widen(double* dst, const float* src, long long len, int grid, cudaStream_t s);
@@ -104,8 +119,9 @@ constexpr int PANEL_MINB32 = PDHG_PANEL_MINB32;
 constexpr int PANEL_SMEM_MAX = 220 * 1024;  // shared memory of one panel block
 struct PanelLayout {
   int m = 0;                // rows of A (length of y)
-  int ncols = 0;            // columns covered: internal columns [0, ncols), the long rows of A^T (units
-                            // [0, ncols) of At); the other columns take the direct primal step
+  int ncols = 0;            // columns covered: internal columns [0, ncols), the longest rows of A^T
+  int ulong = 0;            // ... which are the rows of units [0, ulong) of At; the direct primal step
+                            // takes the units from ulong on
   int rows = 0;             // panel height: entries of y per panel
   int panels = 0;           // ceil(m / rows)
   int* ustart = nullptr;    // [panels + 1] first unit of every panel in Pn
@@ -117,16 +133,18 @@ struct PanelLayout {
 // allow the panel kernels their shared memory (once per device, outside graph capture)
 cudaError_t configure_primal_panels();
 // pass 1: per-(column, panel) partial sums of the long columns
-template <class T>
-void launch_panel_pass(const Hyb& Pn, const T* vals, const PanelLayout& L, const T* y, T* partial, cudaStream_t s);
+template <class T, class V = T>
+void launch_panel_pass(const Hyb& Pn, const V* vals, const PanelLayout& L, const T* y, T* partial, cudaStream_t s);
 // pass 2 fused with the short columns' direct step (short_grid: blocks of tpb
 // threads for the units of At from L.ncols on): the long columns' sums and
 // update, and the direct step; halpern_it >= 0: the reflected Halpern update
 // of step halpern_it with xsum as the anchor
-template <class T>
-void launch_primal_short_combine(const Hyb& At, const T* vals, const T* y, const T* ch, T* x, T* xbar, T* xsum,
+// (V = float with T = double: the unscaled values, with dc = D_c, as above)
+template <class T, class V = T>
+void launch_primal_short_combine(const Hyb& At, const V* vals, const T* y, const T* ch, T* x, T* xbar, T* xsum,
                                  const DevState* st, int accumulate, int short_grid, const PanelLayout& L,
-                                 const T* partial, int tpb, cudaStream_t s, int halpern_it = -1);
+                                 const T* partial, int tpb, cudaStream_t s, int halpern_it = -1,
+                                 const T* dc = nullptr);
 // the dual step, persistent (grid = number of SMs), with xbar[0, hot) staged
 // in shared memory (hot * sizeof(T) <= HOT_SMEM_MAX), values vals in
 // precision T; halpern_it >= 0: the reflected Halpern form of step

@@ -67,6 +67,17 @@ constexpr int64_t STALL_ITERS = 16384;
 // reported by pdhg_last_error(NULL)
 void pdhg_set_global_error(const char* msg) { g_create_error = msg; }
 
+// The panel-tiled primal half-step's layout of Ahat^T (option primal_panels):
+// the Hyb of segments, the panel table, the partial sums (FP64, FP32), and for
+// setup only the column and first row of every segment row (for its scaling)
+struct PanelSet {
+  Hyb Pn;
+  PanelLayout pl;
+  double* partial = nullptr;
+  float* partial32 = nullptr;
+  int *col = nullptr, *base = nullptr;
+};
+
 struct pdhg_ctx {
   int64_t m = 0, n = 0, nnz = 0;
   pdhg_options opt{};
@@ -99,15 +110,18 @@ struct pdhg_ctx {
   size_t persist_smem = 0;
   // warps per block of the step and evaluation kernels (option step_block)
   int wpb = WARPS_PER_BLOCK;
-  // panel-tiled primal step (option primal_panels): the panel layout of Ahat^T,
-  // its partial sums (FP64, FP32), blocks per panel, and for setup only the
-  // column and first row of every segment row (for its scaling)
+  // panel-tiled primal step (option primal_panels): pan[0] is the layout of
+  // FP64 steps (and of FP32 steps without pan[1]); pan[1] (pan32) an FP32-tuned
+  // layout - shorter columns in the panels, twice the rows per panel - for the
+  // FP32 phase of PDHG_MIXED
   bool panels_on = false;
-  Hyb Pn;
-  PanelLayout pl;
-  double* pn_partial = nullptr;
-  float* pn_partial32 = nullptr;
-  int *pn_col = nullptr, *pn_base = nullptr;
+  bool pan32 = false;
+  PanelSet pan[2];
+  // option values32: the FP64 steps read A.u32 / At.u32 / pan[0].Pn.u32 (A's
+  // unscaled values, exactly) and gather yg = D_r y (written by the dual step,
+  // refreshed from y at the start of every block) and D_c xbar (in xbar)
+  bool vals_u = false;
+  double* yg = nullptr;
   // CUDA graphs of one evaluation block, per precision phase (FP64, FP32)
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   int64_t graph_launches[2] = {0, 0};
@@ -255,8 +269,8 @@ int stride_grid(const pdhg_ctx* ctx, const Hyb& H) { return std::min(unit_grid(c
 
 // grid of the direct primal step over the units of Ahat^T that the panel pass
 // leaves to it (the short rows, units [pl.ncols, n_units))
-int short_grid(const pdhg_ctx* ctx) {
-  const long long units = std::max<long long>(1, ctx->At.n_units - ctx->pl.ncols);
+int short_grid(const pdhg_ctx* ctx, const PanelSet& ps) {
+  const long long units = std::max<long long>(1, ctx->At.n_units - ps.pl.ulong);
   return (int)((units + ctx->wpb - 1) / ctx->wpb);
 }
 
@@ -664,24 +678,24 @@ int bit_length(unsigned long long v) {
 // Panel layout of Ahat^T for the panel-tiled primal step (one LP): the entries
 // of every long row j < nlong of A^T (the rows with at least long_row_min
 // entries, which come first in the internal numbering; sorted by internal row
-// i) are cut into segments, one per panel of ctx->pl.rows consecutive rows i;
+// i) are cut into segments, one per panel of ps.pl.rows consecutive rows i;
 // short rows stay with the direct step (a one-entry segment would cost a
 // partial sum's write and read to save one gather). The segments of each panel,
-// sorted by decreasing length, become the rows of the Hyb ctx->Pn with row
+// sorted by decreasing length, become the rows of the Hyb ps.Pn with row
 // indices relative to the panel. Segments are numbered column by column
 // (their partial sums' positions, segout), so that column j's partial sums
 // are positions [cptr[j], cptr[j+1]) in panel order.
-pdhg_status build_panels(pdhg_ctx* ctx, Scratch& sc, const long long* tp, const int* sval, const int* rowid,
-                         const int* iy, const double* val, unsigned max_col_len, long long nlong, long long* hist,
-                         long long* ws) {
+pdhg_status build_panels(pdhg_ctx* ctx, PanelSet& ps, Scratch& sc, const long long* tp, const int* sval,
+                         const int* rowid, const int* iy, const double* val, unsigned max_col_len, long long nlong,
+                         long long* hist, long long* ws) {
   const pdhg_options& o = ctx->opt;
   const long long N = nlong;
-  const int H = ctx->pl.rows, P = ctx->pl.panels;
+  const int H = ps.pl.rows, P = ps.pl.panels;
   cudaStream_t s = ctx->stream;
   long long Z = 0;  // entries of the long rows: tp[nlong]
   CK(ctx, cudaMemcpyAsync(&Z, tp + N, sizeof(long long), cudaMemcpyDeviceToHost, s));
   CK(ctx, cudaStreamSynchronize(s));
-  ctx->pl.ncols = (int)N;
+  ps.pl.ncols = (int)N;
   int *head = nullptr, *panel = nullptr, *col = nullptr;
   long long* segpos = nullptr;
   CK(ctx, sc.take(&head, Z));
@@ -707,8 +721,8 @@ pdhg_status build_panels(pdhg_ctx* ctx, Scratch& sc, const long long* tp, const 
   CK(ctx, sc.take(&vb, S));
   CK(ctx, sc.take(&pcount, P));
   CK(ctx, sc.take(&slen, S));
-  CK(ctx, sc.take(&ctx->pn_col, S));
-  CK(ctx, sc.take(&ctx->pn_base, S));
+  CK(ctx, sc.take(&ps.col, S));
+  CK(ctx, sc.take(&ps.base, S));
   launch_panel_segments(head, panel, col, segpos, Z, S, seg_start, seg_panel, seg_col, s);
   CK(ctx, cudaMemsetAsync(pcount, 0, sizeof(int) * P, s));
   const int lbits = bit_length(max_col_len);
@@ -717,9 +731,9 @@ pdhg_status build_panels(pdhg_ctx* ctx, Scratch& sc, const long long* tp, const 
                                                         lbits + bit_length((unsigned long long)(P - 1)), hist, ws, s);
   const int* sp = alt ? vb : va;
   launch_gather_int(seg_len, sp, S, slen, s);
-  launch_panel_rowinfo(sp, seg_col, seg_panel, H, S, ctx->pn_col, ctx->pn_base, s);
-  CK(ctx, dalloc(ctx, &ctx->pl.segout, S));
-  launch_panel_dense_out(ctx->pn_col, ctx->pn_base, H, (int)N, S, ctx->pl.segout, s);
+  launch_panel_rowinfo(sp, seg_col, seg_panel, H, S, ps.col, ps.base, s);
+  CK(ctx, dalloc(ctx, &ps.pl.segout, S));
+  launch_panel_dense_out(ps.col, ps.base, H, (int)N, S, ps.pl.segout, s);
   std::vector<int> hs(S), hc(P);
   CK(ctx, cudaMemcpyAsync(hs.data(), slen, sizeof(int) * S, cudaMemcpyDeviceToHost, s));
   CK(ctx, cudaMemcpyAsync(hc.data(), pcount, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
@@ -757,18 +771,18 @@ pdhg_status build_panels(pdhg_ctx* ctx, Scratch& sc, const long long* tp, const 
   std::vector<int> binfo;
   for (int p = 0; p < P; ++p)
     for (int b = 0; b < nb[p]; ++b) binfo.insert(binfo.end(), {p, b, nb[p], 0});
-  ctx->pl.blocks = (int)(binfo.size() / 4);
-  CK(ctx, dalloc(ctx, &ctx->pl.binfo, ctx->pl.blocks));
-  CK(ctx, cudaMemcpyAsync(ctx->pl.binfo, binfo.data(), sizeof(int) * binfo.size(), cudaMemcpyHostToDevice, s));
-  pdhg_status rs = upload_units(ctx, uP, (int)S, H, ctx->Pn);
+  ps.pl.blocks = (int)(binfo.size() / 4);
+  CK(ctx, dalloc(ctx, &ps.pl.binfo, ps.pl.blocks));
+  CK(ctx, cudaMemcpyAsync(ps.pl.binfo, binfo.data(), sizeof(int) * binfo.size(), cudaMemcpyHostToDevice, s));
+  pdhg_status rs = upload_units(ctx, uP, (int)S, H, ps.Pn);
   if (rs != PDHG_OK) return rs;
-  CK(ctx, dalloc(ctx, &ctx->pl.ustart, P + 1));
-  CK(ctx, cudaMemcpyAsync(ctx->pl.ustart, ust.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice, s));
-  launch_fill_units_P(ctx->Pn, slen, sp, seg_start, seg_panel, sval, rowid, iy, val, H, s);
+  CK(ctx, dalloc(ctx, &ps.pl.ustart, P + 1));
+  CK(ctx, cudaMemcpyAsync(ps.pl.ustart, ust.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice, s));
+  launch_fill_units_P(ps.Pn, slen, sp, seg_start, seg_panel, sval, rowid, iy, val, H, s);
   // dense panel-major partial sums; the slots of absent segments stay 0
   const long long slots = std::max<long long>(1, (long long)P * N);
-  CK(ctx, dalloc(ctx, &ctx->pn_partial, slots));
-  CK(ctx, cudaMemsetAsync(ctx->pn_partial, 0, sizeof(double) * slots, s));
+  CK(ctx, dalloc(ctx, &ps.partial, slots));
+  CK(ctx, cudaMemsetAsync(ps.partial, 0, sizeof(double) * slots, s));
   CK(ctx, cudaGetLastError());
   CK(ctx, cudaStreamSynchronize(s));  // the host tables are released on return
   return PDHG_OK;
@@ -918,17 +932,38 @@ pdhg_status build_layouts(pdhg_ctx* ctx, Scratch& sc, const long long* lrp, cons
   launch_fill_units_T(ctx->At, slT, tp, sval, rowid, iy, val, s);
   CK(ctx, cudaGetLastError());
   if (ctx->panels_on) {
-    // the long rows of A^T (a prefix of the internal columns) go to the panels
-    long long nlong = 0;
-    while (nlong < N && hT[nlong] >= o.long_row_min) ++nlong;
-    const long long dense = (long long)ctx->pl.panels * nlong;  // slots of the panel-major partial sums
-    if (nlong == 0 || dense > 64LL * Z + (1LL << 20) || dense >= (1LL << 31) - 1) {
-      // nothing to tile, or partial sums far larger than the matrix: the
-      // direct step takes every column
-      ctx->panels_on = false;
-    } else {
-      rs = build_panels(ctx, sc, tp, sval, rowid, iy, val, h_max[1], nlong, hist, ws);
-      if (rs != PDHG_OK) return rs;
+    // the longest rows of A^T (a prefix of the internal columns, whole units
+    // of the A^T layout: every unit whose shortest row has at least pmin
+    // entries) go to the panels; the direct step takes the units after them.
+    // pmin: panel_min_len if set; else 32 for a layout of FP32 steps (its
+    // partial sums cost half as much) and long_row_min for FP64 steps.
+    auto prefix = [&](int pmin, int* ulong_out) -> long long {
+      int ulong = 0;
+      while (ulong < uT.n_units()) {
+        const int* ui = &uT.uinfo[4 * (size_t)ulong];
+        const int last = ui[1] == 0 ? ui[0] : ui[0] + ui[2] - 1;  // the unit's shortest valid row
+        if ((ui[2] == 0 && ui[1] != 0) || hT[last] < pmin) break;
+        ++ulong;
+      }
+      *ulong_out = ulong;
+      return ulong < uT.n_units() ? uT.uinfo[4 * (size_t)ulong] : N;
+    };
+    const int nsets = ctx->pan32 ? 2 : 1;
+    for (int k = 0; k < nsets && ctx->panels_on; ++k) {
+      PanelSet& ps = ctx->pan[k];
+      const bool fp32_steps = k == 1 || o.precision == PDHG_FP32;
+      const int pmin = o.panel_min_len > 0 ? o.panel_min_len : (fp32_steps ? 32 : o.long_row_min);
+      const long long nlong = prefix(pmin, &ps.pl.ulong);
+      const long long dense = (long long)ps.pl.panels * nlong;  // slots of the panel-major partial sums
+      if (nlong == 0 || dense > 64LL * Z + (1LL << 20) || dense >= (1LL << 31) - 1) {
+        // nothing to tile, or partial sums far larger than the matrix: the
+        // direct step takes every column
+        if (k == 0) ctx->panels_on = false;
+        ctx->pan32 = false;
+      } else {
+        rs = build_panels(ctx, ps, sc, tp, sval, rowid, iy, val, h_max[1], nlong, hist, ws);
+        if (rs != PDHG_OK) return rs;
+      }
     }
   }
   if (batch) {
@@ -1048,6 +1083,30 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   launch_gather_double(d_b, ctx->perm_y, m, ctx->b, s);
   launch_gather_double(d_c, ctx->perm_x, n, ctx->c, s);
 
+  // ---- device: FP32 copies of the unscaled values (option values32) ----
+  if (o.values32 != 0 && o.precision != PDHG_FP32 && !o.persistent && !o.record_for_backward &&
+      (o.values32 == 1 || o.precision == PDHG_MIXED)) {
+    int* flag = nullptr;
+    CK(ctx, sc.take(&flag, 1));
+    CK(ctx, cudaMemsetAsync(flag, 0, sizeof(int), s));
+    launch_fp32_inexact(A.v, A.slots, flag, s);
+    int inexact = 0;
+    CK(ctx, cudaMemcpyAsync(&inexact, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(ctx, cudaStreamSynchronize(s));
+    if (inexact && o.values32 == 1)
+      return fail(ctx, PDHG_ERR_INVALID, "values32 = 1: a value of A is not an FP32 number");
+    ctx->vals_u = !inexact;
+  }
+  if (ctx->vals_u) {
+    Hyb* hs[] = {&A, &At, ctx->panels_on ? &ctx->pan[0].Pn : nullptr};
+    for (Hyb* h : hs) {
+      if (!h) continue;
+      CK(ctx, dalloc(ctx, &h->u32, h->slots));
+      launch_narrow(h->u32, h->v, h->slots, vec_grid(ctx, h->slots), s);
+    }
+    CK(ctx, dalloc(ctx, &ctx->yg, m));
+  }
+
   // ---- device: scaling ----
   const int gn = vec_grid(ctx, n), gm = vec_grid(ctx, m);
   const int grA = stride_grid(ctx, A), grT = stride_grid(ctx, At);
@@ -1062,7 +1121,8 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
     launch_inv_sqrt_or_one(sf, sf, (int)n, gn, s);
     launch_scale(A, r, sf, 0, grA, s);
     launch_scale(At, r, sf, 1, grT, s);
-    if (ctx->panels_on) launch_scale(ctx->Pn, r, sf, 2, stride_grid(ctx, ctx->Pn), s, ctx->pn_col, ctx->pn_base);
+    for (int k = 0; ctx->panels_on && k < (ctx->pan32 ? 2 : 1); ++k)
+      launch_scale(ctx->pan[k].Pn, r, sf, 2, stride_grid(ctx, ctx->pan[k].Pn), s, ctx->pan[k].col, ctx->pan[k].base);
     launch_mul_inplace(ctx->dr, r, (int)m, gm, s);
     launch_mul_inplace(ctx->dc, sf, (int)n, gn, s);
   }
@@ -1073,7 +1133,8 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
     launch_inv_sqrt_or_one(sf, sf, (int)n, gn, s);
     launch_scale(A, r, sf, 0, grA, s);
     launch_scale(At, r, sf, 1, grT, s);
-    if (ctx->panels_on) launch_scale(ctx->Pn, r, sf, 2, stride_grid(ctx, ctx->Pn), s, ctx->pn_col, ctx->pn_base);
+    for (int k = 0; ctx->panels_on && k < (ctx->pan32 ? 2 : 1); ++k)
+      launch_scale(ctx->pan[k].Pn, r, sf, 2, stride_grid(ctx, ctx->pan[k].Pn), s, ctx->pan[k].col, ctx->pan[k].base);
     launch_mul_inplace(ctx->dr, r, (int)m, gm, s);
     launch_mul_inplace(ctx->dc, sf, (int)n, gn, s);
   }
@@ -1157,11 +1218,13 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
     launch_narrow(A.v32, A.v, A.slots, vec_grid(ctx, A.slots), s);
     launch_narrow(At.v32, At.v, At.slots, vec_grid(ctx, At.slots), s);
     if (ctx->panels_on) {
-      CK(ctx, dalloc(ctx, &ctx->Pn.v32, ctx->Pn.slots));
-      const long long slots = std::max<long long>(1, (long long)ctx->pl.panels * ctx->pl.ncols);
-      CK(ctx, dalloc(ctx, &ctx->pn_partial32, slots));
-      CK(ctx, cudaMemsetAsync(ctx->pn_partial32, 0, sizeof(float) * slots, s));
-      launch_narrow(ctx->Pn.v32, ctx->Pn.v, ctx->Pn.slots, vec_grid(ctx, ctx->Pn.slots), s);
+      // the FP32 steps' panel layout: pan[1] when it exists, else pan[0]
+      PanelSet& ps = ctx->pan[ctx->pan32 ? 1 : 0];
+      CK(ctx, dalloc(ctx, &ps.Pn.v32, ps.Pn.slots));
+      const long long slots = std::max<long long>(1, (long long)ps.pl.panels * ps.pl.ncols);
+      CK(ctx, dalloc(ctx, &ps.partial32, slots));
+      CK(ctx, cudaMemsetAsync(ps.partial32, 0, sizeof(float) * slots, s));
+      launch_narrow(ps.Pn.v32, ps.Pn.v, ps.Pn.slots, vec_grid(ctx, ps.Pn.slots), s);
     }
     launch_narrow(ctx->ch32, ctx->ch, n, gn, s);
     launch_narrow(ctx->bh32, ctx->bh, m, gm, s);
@@ -1191,7 +1254,7 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   CK(ctx, cudaGetLastError());
   rs = read_state(ctx);
   if (rs != PDHG_OK) return rs;
-  ctx->pn_col = ctx->pn_base = nullptr;  // setup scratch, released on return
+  for (PanelSet& ps : ctx->pan) ps.col = ps.base = nullptr;  // setup scratch, released on return
   if (!std::isfinite(ctx->h_st->norm_est) || !std::isfinite(ctx->h_st->omega))
     return fail(ctx, PDHG_ERR_NUMERIC, "non-finite norm estimate or primal weight after scaling");
   return PDHG_OK;
@@ -1203,13 +1266,16 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
 // long columns, then one launch that adds their partial sums and applies the
 // update (plain, or the reflected Halpern one of step halpern_it with xsum as
 // the anchor) beside the direct step over the short columns.
-template <class T>
-pdhg_status panel_half_step(pdhg_ctx* ctx, const T* vals, const T* valsT, const T* y, const T* ch, T* x, T* xbar,
-                            T* xsum, T* partial, int accumulate, int tpb, int halpern_it) {
+// With V = float and T = double: the unscaled values, y = D_r y and dc = D_c
+// (option values32).
+template <class T, class V = T>
+pdhg_status panel_half_step(pdhg_ctx* ctx, const PanelSet& ps, const V* vals, const V* valsT, const T* y, const T* ch,
+                            T* x, T* xbar, T* xsum, T* partial, int accumulate, int tpb, int halpern_it,
+                            const T* dc = nullptr) {
   cudaStream_t s = ctx->stream;
-  launch_panel_pass<T>(ctx->Pn, vals, ctx->pl, y, partial, s);
-  launch_primal_short_combine<T>(ctx->At, valsT, y, ch, x, xbar, xsum, ctx->st, accumulate, short_grid(ctx), ctx->pl,
-                                 partial, tpb, s, halpern_it);
+  launch_panel_pass<T, V>(ps.Pn, vals, ps.pl, y, partial, s);
+  launch_primal_short_combine<T, V>(ctx->At, valsT, y, ch, x, xbar, xsum, ctx->st, accumulate, short_grid(ctx, ps),
+                                    ps.pl, partial, tpb, s, halpern_it, dc);
   CK(ctx, cudaGetLastError());
   ctx->launches += 1;  // two launches; the caller counts one primal step
   return PDHG_OK;
@@ -1222,12 +1288,23 @@ pdhg_status panel_half_step(pdhg_ctx* ctx, const T* vals, const T* valsT, const 
 pdhg_status primal_step(pdhg_ctx* ctx, bool f32, const void* y, void* x, void* xbar, void* xsum, int accumulate,
                         int grT, int tpb) {
   cudaStream_t s = ctx->stream;
+  if (!f32 && ctx->vals_u) {  // FP64 on the unscaled FP32 values: y is D_r y here
+    if (ctx->panels_on)
+      return panel_half_step<double, float>(ctx, ctx->pan[0], ctx->pan[0].Pn.u32, ctx->At.u32, (const double*)y,
+                                            ctx->ch, (double*)x, (double*)xbar, (double*)xsum, ctx->pan[0].partial,
+                                            accumulate, tpb, -1, ctx->dc);
+    launch_primal_step_u(ctx->At, (const double*)y, ctx->ch, (double*)x, (double*)xbar, (double*)xsum, ctx->st,
+                         accumulate, grT, s, tpb, 0, ctx->dc);
+    return PDHG_OK;
+  }
   if (ctx->panels_on) {
-    if (f32)
-      return panel_half_step<float>(ctx, ctx->Pn.v32, ctx->At.v32, (const float*)y, ctx->ch32, (float*)x,
-                                    (float*)xbar, (float*)xsum, ctx->pn_partial32, accumulate, tpb, -1);
-    return panel_half_step<double>(ctx, ctx->Pn.v, ctx->At.v, (const double*)y, ctx->ch, (double*)x, (double*)xbar,
-                                   (double*)xsum, ctx->pn_partial, accumulate, tpb, -1);
+    if (f32) {
+      const PanelSet& ps = ctx->pan[ctx->pan32 ? 1 : 0];
+      return panel_half_step<float>(ctx, ps, ps.Pn.v32, ctx->At.v32, (const float*)y, ctx->ch32, (float*)x,
+                                    (float*)xbar, (float*)xsum, ps.partial32, accumulate, tpb, -1);
+    }
+    return panel_half_step<double>(ctx, ctx->pan[0], ctx->pan[0].Pn.v, ctx->At.v, (const double*)y, ctx->ch,
+                                   (double*)x, (double*)xbar, (double*)xsum, ctx->pan[0].partial, accumulate, tpb, -1);
   } else if (f32) {
     launch_primal_step32(ctx->At, (const float*)y, ctx->ch32, (float*)x, (float*)xbar, (float*)xsum, ctx->st,
                          accumulate, grT, s, tpb);
@@ -1244,19 +1321,39 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
   const pdhg_options& o = ctx->opt;
   cudaStream_t s = ctx->stream;
   const int grT = unit_grid(ctx, ctx->At), grA = unit_grid(ctx, ctx->A), tpb = 32 * ctx->wpb;
-  // entries of xbar the dual step stages in shared memory, per precision
-  const int hot = (int)std::min<int64_t>({(int64_t)o.dual_hot_cols, ctx->n,
-                                          (int64_t)(HOT_SMEM_MAX / (ctx->phase32 ? 4 : 8))});
+  // entries of xbar the dual step stages in shared memory, per precision (none
+  // in FP64 phases on the unscaled values)
+  const bool vu = ctx->vals_u && !ctx->phase32;
+  const int hot = vu ? 0
+                     : (int)std::min<int64_t>({(int64_t)o.dual_hot_cols, ctx->n,
+                                               (int64_t)(HOT_SMEM_MAX / (ctx->phase32 ? 4 : 8))});
+  // the primal step's gather vector D_r y from y (which evaluations, restarts
+  // and phase changes set between blocks)
+  if (vu) {
+    launch_mul(ctx->yg, ctx->dr, ctx->y, (int)ctx->m, vec_grid(ctx, ctx->m), s);
+    ctx->launches += 1;
+  }
+  double* const yg64 = vu ? ctx->yg : ctx->y;  // what the FP64 primal steps gather
   for (int64_t it = 0; it < nb; ++it) {
     if (o.record_for_backward) {
       pdhg_status rs = record_checkpoint(ctx, ctx->k + it);
       if (rs != PDHG_OK) return rs;
     }
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
-    if (o.halpern && !ctx->phase32) {
+    if (o.halpern && vu) {
+      if (ctx->panels_on) {
+        pdhg_status rs = panel_half_step<double, float>(ctx, ctx->pan[0], ctx->pan[0].Pn.u32, ctx->At.u32, yg64,
+                                                        ctx->ch, ctx->x, ctx->xbar, ctx->xr, ctx->pan[0].partial, 0,
+                                                        tpb, (int)it, ctx->dc);
+        if (rs != PDHG_OK) return rs;
+      } else {
+        launch_primal_step_halpern<double, float>(ctx->At, ctx->At.u32, yg64, ctx->ch, ctx->x, ctx->xbar, ctx->xr,
+                                                  ctx->st, (int)it, grT, s, tpb, nullptr, 0, ctx->dc);
+      }
+    } else if (o.halpern && !ctx->phase32) {
       if (ctx->panels_on) {  // the anchor (last restart point) in place of the sums
-        pdhg_status rs = panel_half_step<double>(ctx, ctx->Pn.v, ctx->At.v, ctx->y, ctx->ch, ctx->x, ctx->xbar,
-                                                 ctx->xr, ctx->pn_partial, 0, tpb, (int)it);
+        pdhg_status rs = panel_half_step<double>(ctx, ctx->pan[0], ctx->pan[0].Pn.v, ctx->At.v, ctx->y, ctx->ch,
+                                                 ctx->x, ctx->xbar, ctx->xr, ctx->pan[0].partial, 0, tpb, (int)it);
         if (rs != PDHG_OK) return rs;
       } else {
         launch_primal_step_halpern<double>(ctx->At, ctx->At.v, ctx->y, ctx->ch, ctx->x, ctx->xbar, ctx->xr, ctx->st,
@@ -1265,8 +1362,9 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
     } else if (o.halpern) {
       // FP32 Halpern: the FP32 sums hold the FP32 anchor (no averages in this form)
       if (ctx->panels_on) {
-        pdhg_status rs = panel_half_step<float>(ctx, ctx->Pn.v32, ctx->At.v32, ctx->y32, ctx->ch32, ctx->x32,
-                                                ctx->xbar32, ctx->xsum32, ctx->pn_partial32, 0, tpb, (int)it);
+        const PanelSet& ps = ctx->pan[ctx->pan32 ? 1 : 0];
+        pdhg_status rs = panel_half_step<float>(ctx, ps, ps.Pn.v32, ctx->At.v32, ctx->y32, ctx->ch32, ctx->x32,
+                                                ctx->xbar32, ctx->xsum32, ps.partial32, 0, tpb, (int)it);
         if (rs != PDHG_OK) return rs;
       } else {
         launch_primal_step_halpern<float>(ctx->At, ctx->At.v32, ctx->y32, ctx->ch32, ctx->x32, ctx->xbar32,
@@ -1275,12 +1373,19 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
     } else {
       pdhg_status rs = ctx->phase32 ? primal_step(ctx, true, ctx->y32, ctx->x32, ctx->xbar32, ctx->xsum32,
                                                   o.restarts, grT, tpb)
-                                    : primal_step(ctx, false, ctx->y, ctx->x, ctx->xbar, ctx->xsum, o.restarts, grT,
+                                    : primal_step(ctx, false, yg64, ctx->x, ctx->xbar, ctx->xsum, o.restarts, grT,
                                                   tpb);
       if (rs != PDHG_OK) return rs;
     }
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
-    if (o.halpern && !ctx->phase32) {
+    if (vu) {
+      if (o.halpern)
+        launch_dual_step_halpern<double, float>(ctx->A, ctx->A.u32, ctx->xbar, ctx->bh, ctx->y, ctx->yr, ctx->st,
+                                                (int)it, grA, s, tpb, nullptr, ctx->dr, ctx->yg);
+      else
+        launch_dual_step_u(ctx->A, ctx->xbar, ctx->bh, ctx->y, ctx->ysum, ctx->st, o.restarts, grA, s, tpb, ctx->dr,
+                           ctx->yg);
+    } else if (o.halpern && !ctx->phase32) {
       if (hot > 0)
         launch_dual_step_hot<double>(ctx->A, ctx->A.v, ctx->xbar, hot, ctx->bh, ctx->y, ctx->yr, ctx->st, 0,
                                      ctx->sms, s, (int)it);
@@ -1485,7 +1590,8 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
     launch_inv_sqrt_or_one(sf, sf, (int)n, gn, s);
     launch_scale(A, r, sf, 0, grA, s);
     launch_scale(At, r, sf, 1, grT, s);
-    if (ctx->panels_on) launch_scale(ctx->Pn, r, sf, 2, stride_grid(ctx, ctx->Pn), s, ctx->pn_col, ctx->pn_base);
+    for (int k = 0; ctx->panels_on && k < (ctx->pan32 ? 2 : 1); ++k)
+      launch_scale(ctx->pan[k].Pn, r, sf, 2, stride_grid(ctx, ctx->pan[k].Pn), s, ctx->pan[k].col, ctx->pan[k].base);
     launch_mul_inplace(ctx->dr, r, (int)m, gm, s);
     launch_mul_inplace(ctx->dc, sf, (int)n, gn, s);
   }
@@ -1496,7 +1602,8 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
     launch_inv_sqrt_or_one(sf, sf, (int)n, gn, s);
     launch_scale(A, r, sf, 0, grA, s);
     launch_scale(At, r, sf, 1, grT, s);
-    if (ctx->panels_on) launch_scale(ctx->Pn, r, sf, 2, stride_grid(ctx, ctx->Pn), s, ctx->pn_col, ctx->pn_base);
+    for (int k = 0; ctx->panels_on && k < (ctx->pan32 ? 2 : 1); ++k)
+      launch_scale(ctx->pan[k].Pn, r, sf, 2, stride_grid(ctx, ctx->pan[k].Pn), s, ctx->pan[k].col, ctx->pan[k].base);
     launch_mul_inplace(ctx->dr, r, (int)m, gm, s);
     launch_mul_inplace(ctx->dc, sf, (int)n, gn, s);
   }
@@ -2067,8 +2174,10 @@ void pdhg_default_options(pdhg_options* o) {
   o->rows_per_thread = 4;
   o->dual_hot_cols = 0;
   o->singleton_order = 1;
+  o->panel_min_len = 0;
   o->barrier_cycles = 0;
   o->restart_scheme = 0;
+  o->values32 = -1;
   o->pid_kp = 0.99;
   o->pid_ki = 0.01;
   o->pid_kd = 0.0;
@@ -2113,10 +2222,15 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     return fail(nullptr, PDHG_ERR_INVALID, "option out of range");
   if (o.singleton_order < 0 || o.singleton_order > 1)
     return fail(nullptr, PDHG_ERR_INVALID, "singleton_order must be 0 or 1");
+  if (o.panel_min_len < 0) return fail(nullptr, PDHG_ERR_INVALID, "panel_min_len must be >= 0");
   if (!(o.step_block == 0 || o.step_block == 128 || o.step_block == 256 || o.step_block == 512))
     return fail(nullptr, PDHG_ERR_INVALID, "step_block must be 128, 256 or 512");
-  if (o.primal_panels < -1 || o.primal_panels > 1 || o.panel_rows < 0 || o.panel_rows > PANEL_SMEM_MAX / 8)
-    return fail(nullptr, PDHG_ERR_INVALID, "primal_panels must be -1, 0 or 1 and panel_rows in [0, 28160]");
+  // a context that only ever runs FP32 steps (PDHG_FP32) can hold twice the
+  // entries of y in a panel
+  const long long panel_max = PANEL_SMEM_MAX / (o.precision == PDHG_FP32 ? 4 : 8);
+  if (o.primal_panels < -1 || o.primal_panels > 1 || o.panel_rows < 0 || o.panel_rows > panel_max)
+    return fail(nullptr, PDHG_ERR_INVALID,
+                "primal_panels must be -1, 0 or 1 and panel_rows in [0, 28160] (56320 with precision PDHG_FP32)");
   if (o.persistent && o.primal_panels == 1)
     return fail(nullptr, PDHG_ERR_INVALID, "persistent = 1 and primal_panels = 1 exclude each other");
   if (o.halpern != 0 && (o.halpern != 1 || o.persistent || o.record_for_backward || !(o.halpern_reflect >= 0.0) ||
@@ -2145,6 +2259,10 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     return fail(nullptr, PDHG_ERR_INVALID,
                 "restart_scheme must be 0 or 1 (1: with halpern = 1, no feasibility polishing or persistent loop) "
                 "and the PID gains finite");
+  if (o.values32 < -1 || o.values32 > 1 ||
+      (o.values32 == 1 && (o.precision == PDHG_FP32 || o.persistent || o.record_for_backward)))
+    return fail(nullptr, PDHG_ERR_INVALID,
+                "values32 must be -1, 0 or 1 (1: precision FP64 or MIXED, no persistent loop, no recording)");
 
   // Checks of host inputs (CSR structure, finite data) on host threads, beside
   // the context's set-up: stream creation, allocations and the upload depend
@@ -2190,15 +2308,19 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
   // block copies one panel, ~H entries, per step)
   ctx->panels_on = !o.persistent && (o.primal_panels == 1 || (o.primal_panels < 0 && m >= (1 << 18) &&
                                                                 nnz >= (1 << 23)));
-  if (ctx->panels_on) {
-    const long long hmax = PANEL_SMEM_MAX / (long long)sizeof(double);
+  // PDHG_MIXED keeps a second, FP32-tuned panel layout for its FP32 phase
+  ctx->pan32 = ctx->panels_on && o.precision == PDHG_MIXED;
+  for (int k = 0; ctx->panels_on && k < (ctx->pan32 ? 2 : 1); ++k) {
+    // panel rows: as many as fit in shared memory in the precision of the
+    // layout's steps, a multiple of 16 entries, which keeps every panel's
+    // start 16-byte aligned for the asynchronous copies of y
+    const bool fp32_steps = k == 1 || o.precision == PDHG_FP32;
+    const long long hmax = PANEL_SMEM_MAX / (fp32_steps ? 4LL : 8LL);
     const long long P0 = (m + hmax - 1) / hmax;
-    // a multiple of 16 entries keeps every panel's start 16-byte aligned for
-    // the asynchronous copies of y (FP32 and FP64)
     const long long H = o.panel_rows > 0 ? o.panel_rows : std::min(hmax, ((m + P0 - 1) / P0 + 15) / 16 * 16);
-    ctx->pl.m = (int)m;
-    ctx->pl.rows = (int)H;
-    ctx->pl.panels = (int)((m + H - 1) / H);
+    ctx->pan[k].pl.m = (int)m;
+    ctx->pan[k].pl.rows = (int)H;
+    ctx->pan[k].pl.panels = (int)((m + H - 1) / H);
   }
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -2356,19 +2478,28 @@ static pdhg_status iterate_impl(pdhg_ctx* ctx, int64_t max_iters, double tol, in
       }
       if (ctx->phase32 && o.precision == PDHG_MIXED && (ctx->h_st->cand_rel_kkt <= o.polish_switch || stalled)) {
         // FP64 polishing phase: continue in FP64 from the FP32 iterate (held
-        // exactly in x, y), keeping D_r, D_c, eta and omega; the iterate
-        // becomes the restart reference and the FP64 averages start empty
-        if (o.restart_scheme == 1)
-          eval_point_fp(ctx, &ctx->st->cur);  // the fixed-point residual at the switch
-        else
-          eval_point(ctx, ctx->x, ctx->y, nullptr, nullptr, &ctx->st->cur);
-        launch_promote_state(ctx->st, s);
-        CK(ctx, cudaMemsetAsync(ctx->xsum, 0, sizeof(double) * n, s));
-        CK(ctx, cudaMemsetAsync(ctx->ysum, 0, sizeof(double) * m, s));
-        CK(ctx, cudaMemcpyAsync(ctx->xr, ctx->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        CK(ctx, cudaMemcpyAsync(ctx->yr, ctx->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+        // exactly in x, y), keeping D_r, D_c, eta and omega.
+        if (!o.halpern) {
+          // PDLP-style restarts: the same restart epoch goes on - the
+          // restart reference (xr, yr, its norms) and the count since the
+          // last restart stay, and the running sums carry over from FP32 -
+          // so the switch is no restart (one would drop the average)
+          launch_widen(ctx->xsum, ctx->xsum32, n, vec_grid(ctx, n), s);
+          launch_widen(ctx->ysum, ctx->ysum32, m, vec_grid(ctx, m), s);
+          ctx->launches += 2;
+        } else {
+          // reflected Halpern forms: the iterate becomes the anchor and the
+          // restart reference, and the Halpern count starts over
+          if (o.restart_scheme == 1)
+            eval_point_fp(ctx, &ctx->st->cur);  // the fixed-point residual at the switch
+          else
+            eval_point(ctx, ctx->x, ctx->y, nullptr, nullptr, &ctx->st->cur);
+          launch_promote_state(ctx->st, s);
+          CK(ctx, cudaMemcpyAsync(ctx->xr, ctx->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+          CK(ctx, cudaMemcpyAsync(ctx->yr, ctx->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+          ctx->launches += 2;
+        }
         CK(ctx, cudaGetLastError());
-        ctx->launches += 4;
         ctx->phase32 = false;
         ctx->promoted_at = ctx->k;
       }
@@ -2531,6 +2662,7 @@ pdhg_status pdhg_get_info(pdhg_ctx* ctx, pdhg_info* out) {
   out->feas_polished = ctx->fp_polished ? 1 : 0;
   out->persistent_grid = ctx->bgrid;
   out->graph_launches = ctx->graph_replays;
+  out->values32 = ctx->vals_u ? 1 : 0;
   return PDHG_OK;
 }
 
@@ -2614,9 +2746,10 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
   if (o.persistent < 0 || o.persistent > 2 || (o.persistent && o.kernel_timing) || o.barrier_cycles < 0)
     return fail(nullptr, PDHG_ERR_INVALID,
                 "persistent must be 0, 1 or 2 and excludes kernel timing; barrier_cycles must be >= 0");
-  if (o.feas_polish || !(o.gap_tol >= 0.0) || o.restart_scheme != 0)
+  if (o.feas_polish || !(o.gap_tol >= 0.0) || o.restart_scheme != 0 || o.values32 == 1 || o.values32 < -1)
     return fail(nullptr, PDHG_ERR_INVALID,
-                "batch: no feasibility polishing or fixed-point restart scheme (single LPs only), gap_tol >= 0");
+                "batch: no feasibility polishing, fixed-point restart scheme or values32 (single LPs only), "
+                "gap_tol >= 0");
   int64_t mt = 0, nt = 0, zt = 0;
   for (int i = 0; i < count; ++i) {
     const pdhg_lp_desc& L = lps[i];

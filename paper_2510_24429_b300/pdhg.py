@@ -63,10 +63,10 @@ class pdhg_options(C.Structure):
         ("feas_polish", C.c_int),
         ("polish_div", C.c_int),
         ("singleton_order", C.c_int),
-        ("reserved", C.c_int),
+        ("panel_min_len", C.c_int),
         ("barrier_cycles", C.c_int64),
         ("restart_scheme", C.c_int),
-        ("reserved2", C.c_int),
+        ("values32", C.c_int),
         ("pid_kp", C.c_double),
         ("pid_ki", C.c_double),
         ("pid_kd", C.c_double),
@@ -89,7 +89,7 @@ class pdhg_info(C.Structure):
         ("kernel_launches", C.c_int64),
         ("polish_started_at", C.c_int64),
         ("feas_polish_attempts", C.c_int64), ("feas_polish_iterations", C.c_int64), ("feas_polished", C.c_int),
-        ("persistent_grid", C.c_int), ("graph_launches", C.c_int64),
+        ("persistent_grid", C.c_int), ("graph_launches", C.c_int64), ("values32", C.c_int),
     ]
 
 

@@ -68,6 +68,8 @@ def test_default_options(lib):
     assert (o.halpern, o.halpern_reflect, o.primal_panels, o.long_row_min) == (0, 1.0, -1, 128)
     assert (o.feas_polish, o.polish_div, o.gap_tol, o.polish_switch) == (0, 8, 0.0, 1e-5)
     assert (o.dual_hot_cols, o.singleton_order, o.barrier_cycles) == (0, 1, 0)
+    assert (o.panel_min_len, o.restart_scheme, o.values32) == (0, 0, -1)
+    assert (o.pid_kp, o.pid_ki, o.pid_kd) == (0.99, 0.01, 0.0)
     with pytest.raises(KeyError):
         P.pdhg_default_options(no_such_option=1)
 

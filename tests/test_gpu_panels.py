@@ -215,3 +215,41 @@ def test_singleton_order_matches_oracle(panels):
     with pytest.raises(P.PDHGError):
         P.Solver.from_lp(lp, singleton_order=2)
 
+
+
+@pytest.mark.parametrize("pmin", [4, 12])
+def test_panel_min_len_matches_oracle(pmin):
+    """Shorter columns in the panels (option panel_min_len below long_row_min:
+    whole units of short columns go to the panels, the rest to the direct
+    step): the same iterates as the oracle at 1e-10."""
+    lp = lpgen.generate(3000, 9000, 2, nnz_per_col=None, zipf=(1.5, 10000, 90000), val_range=(0.1, 10.0),
+                        support=0.3)
+    eng = dict(primal_panels=1, panel_rows=256, long_row_min=32, panel_min_len=pmin)
+    orc, sol = _solvers(lp, eng, **TINY_PLAIN)
+    orc.run(100)
+    assert sol.iterate(100) == (P.PDHG_OK, 100)
+    assert_iterates_close(sol, orc, 1e-10)
+    with pytest.raises(P.PDHGError):
+        P.Solver.from_lp(lp, panel_min_len=-1)
+
+
+def test_mixed_fp32_phase_uses_the_fp32_layout():
+    """PDHG_MIXED keeps an FP32-tuned panel layout for its FP32 phase (shorter
+    columns in the panels, twice the rows per panel) beside the FP64 one; it
+    is the layout a PDHG_FP32 context builds, so until the switch to FP64 the
+    two contexts' iterates are bit-identical. After the switch the FP64 phase
+    (on the FP64 layout) still reaches the known optimum."""
+    lp = lpgen.generate(3000, 9000, 2, nnz_per_col=None, zipf=(1.5, 10000, 90000), val_range=(0.1, 10.0),
+                        support=0.3, fp32_values=True)
+    eng = dict(primal_panels=1, long_row_min=64)
+    with P.Solver.from_lp(lp, precision=P.PDHG_MIXED, polish_switch=1e-30, **eng) as mx, \
+            P.Solver.from_lp(lp, precision=P.PDHG_FP32, **eng) as f32:
+        mx.iterate(640)
+        f32.iterate(640)
+        assert mx.info()["precision_now"] == P.PDHG_FP32
+        for a, b in zip(mx.solution(), f32.solution()):
+            np.testing.assert_array_equal(a, b)
+    with P.Solver.from_lp(lp, precision=P.PDHG_MIXED, **eng) as mx:
+        st, _ = mx.iterate(100_000, 1e-8)
+        assert st == P.PDHG_OK and mx.info()["polish_started_at"] > 0
+        assert mx.kkt()["primal_obj"] == pytest.approx(lp.f_star, rel=1e-7)
