@@ -724,22 +724,30 @@ def run_ours(args):
     if not args.skip_extras and rank == 0:
         # ---- time to tolerance (fresh solve, setup excluded) ----
         # Three forms of the iteration, each in FP64 and in the mixed form
-        # (FP32 iterations, FP64 evaluations, FP64 from polish_switch on):
+        # (FP32 iterations, FP64 evaluations and restart decisions):
         # PDLP-style (restarts on the weighted KKT error, averages); the
         # reflected Halpern form with the same restarts; and the cuPDLP+ form
         # (reflected Halpern, restarts on the fixed-point residual, PID primal
-        # weight; its mixed form switches at 3e-6, as the Halpern one).
+        # weight).
         # On the bench's LP at 1e-4 and 1e-6; on four more LPs of the
         # generator (seeds + 1 .. + 4) at 1e-6, since the iteration count to a
         # tolerance moves with the restart trajectory.
         ttt = {}
+        # The mixed forms run their FP32 phase on corrections to the last
+        # restart point, held in FP64 (refine32, the default of PDHG_MIXED),
+        # and switch to FP64 only on a stall; the cuPDLP+ form also runs
+        # without that refinement (FP32 iterate rounded at restarts, FP64
+        # from rel. KKT 3e-6 on), as a record of the two-phase form.
         forms = (("fp64", P.PDHG_FP64, {}), ("mixed", P.PDHG_MIXED, {}),
                  ("fp64_halpern", P.PDHG_FP64, HALPERN),
-                 ("mixed_halpern", P.PDHG_MIXED, {**HALPERN, "polish_switch": 3e-6}),
+                 ("mixed_halpern", P.PDHG_MIXED, HALPERN),
                  ("fp64_cupdlp_plus", P.PDHG_FP64, CUPDLP_PLUS),
-                 ("mixed_cupdlp_plus", P.PDHG_MIXED, {**CUPDLP_PLUS, "polish_switch": 3e-6}))
+                 ("mixed_cupdlp_plus", P.PDHG_MIXED, CUPDLP_PLUS),
+                 ("mixed_cupdlp_plus_unrefined", P.PDHG_MIXED, {**CUPDLP_PLUS, "refine32": 0,
+                                                                "polish_switch": 3e-6}))
         pairs = (("", "fp64", "mixed"), ("_halpern", "fp64_halpern", "mixed_halpern"),
-                 ("_cupdlp_plus", "fp64_cupdlp_plus", "mixed_cupdlp_plus"))
+                 ("_cupdlp_plus", "fp64_cupdlp_plus", "mixed_cupdlp_plus"),
+                 ("_cupdlp_plus_unrefined", "fp64_cupdlp_plus", "mixed_cupdlp_plus_unrefined"))
 
         def solve(lpx, tol, prec, extra, max_iters=300_000, **more):
             with P.Solver(lpx.m, lpx.n, lpx.row_ptr, lpx.col_idx, lpx.val, lpx.b, lpx.c, stream=stream.cuda_stream,
@@ -754,6 +762,7 @@ def run_ours(args):
                         "objective_rel_error_vs_known_optimum": abs(k["primal_obj"] - lpx.f_star) /
                         (1 + abs(lpx.f_star)),
                         "fp64_from_iteration": sx.info()["polish_started_at"] if prec == P.PDHG_MIXED else 0,
+                        "fp32_on_corrections": sx.info()["refine32"],
                         "snapshots": sx.snapshot_poll()[0]}
 
         for pname, prec, extra in forms:
@@ -789,8 +798,11 @@ def run_ours(args):
         # iterations: the cuPDLP+ form (the one that reaches it within the cap;
         # the PDLP-style form needs ~284K iterations and the Halpern form with
         # KKT restarts stalls near 1e-7 on this LP), at most 250K iterations
-        ttt["1e-08"] = {"fp64_cupdlp_plus": solve(lp, 1e-8, P.PDHG_FP64, CUPDLP_PLUS, max_iters=250_000,
-                                                  snapshot_every=SNAPSHOT_EVERY)}
+        ttt["1e-08"] = {name: solve(lp, 1e-8, prec, CUPDLP_PLUS, max_iters=250_000, snapshot_every=SNAPSHOT_EVERY)
+                        for name, prec in (("fp64_cupdlp_plus", P.PDHG_FP64), ("mixed_cupdlp_plus", P.PDHG_MIXED))}
+        a8, b8 = ttt["1e-08"]["fp64_cupdlp_plus"], ttt["1e-08"]["mixed_cupdlp_plus"]
+        ttt["1e-08"]["speedup_mixed_vs_fp64_cupdlp_plus"] = (a8["seconds"] / b8["seconds"]
+                                                             if a8["converged"] and b8["converged"] else None)
         extras["time_to_tol"] = ttt
         # FP32 half-step times on the same LP (the mixed form's first phase)
         with P.Solver(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, stream=stream.cuda_stream,

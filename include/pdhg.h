@@ -79,7 +79,8 @@ enum { PDHG_NO_RESTART = 0, PDHG_RESTART_TO_CURRENT = 1, PDHG_RESTART_TO_AVERAGE
 typedef struct {
   int precision;          /* PDHG_FP64 (default); PDHG_FP32: both half-steps in FP32 (matrix values,
                              vectors, accumulation) with FP64 evaluation and restart decisions;
-                             PDHG_MIXED: as PDHG_FP32 until rel. KKT <= polish_switch, then FP64 */
+                             PDHG_MIXED: as PDHG_FP32 (on corrections to an FP64 restart point, see
+                             refine32) until rel. KKT <= polish_switch or the FP32 phase stalls, then FP64 */
   int ruiz_iters;         /* Ruiz equilibration passes (10) */
   int pock_chambolle;     /* 1: one Pock-Chambolle pass after Ruiz (1) */
   double pc_alpha;        /* Pock-Chambolle alpha in [0, 2] (1.0) */
@@ -98,8 +99,10 @@ typedef struct {
   int inputs_on_device;   /* 1: pointers given to pdhg_create are device pointers */
   int use_graphs;         /* 1: replay evaluation blocks as CUDA graphs (1) */
   int kernel_timing;      /* 1: time the two step kernels with CUDA events (0) */
-  double polish_switch;   /* PDHG_MIXED: rel. KKT at which FP64 iterations take over (1e-5); they also
-                             take over when the FP32 phase stalls (no 10% gain in 16384 iterations) */
+  double polish_switch;   /* PDHG_MIXED: rel. KKT at which FP64 iterations take over; they also take over
+                             when the FP32 phase stalls (no 10% gain in 16384 iterations, 65536 when the
+                             phase is refined). -1 = automatic:
+                             0 (on a stall only) when the FP32 phase is refined (refine32), else 1e-5 (-1) */
   int long_row_min;       /* rows with at least this many entries get a warp each (128) */
   int rows_per_thread;    /* most rows one thread reduces at once in short rows: 1, 2 or 4 (4) */
   int dual_hot_cols;      /* entries of xbar (the first ones, i.e. the longest columns of A) the dual step
@@ -167,6 +170,25 @@ typedef struct {
                              number). Single LPs, not persistent, no recording; the dual step then stages no
                              entries of xbar (dual_hot_cols) in FP64 phases (-1) */
   double pid_kp, pid_ki, pid_kd; /* restart_scheme = 1: PID gains of the primal weight (0.99, 0.01, 0) */
+  int stream_steps;       /* 1: the half-steps of single LPs run as streamed kernels: every warp keeps the
+                             next pieces of its matrix units and its rows of the step's vectors in flight in
+                             a ring of shared-memory slots filled by bulk copies (TMA), and issues only the
+                             gathers from registers; same arithmetic in the same order as the direct step
+                             kernels, so bit-identical results. A bounded wait that runs out ends the call
+                             with PDHG_ERR_TIMEOUT. Not with persistent, dual_hot_cols or batches; the
+                             range-checked build ignores it (0) */
+  int stream_warps;       /* stream_steps: warps per block, 1..16 (8) */
+  int stream_depth;       /* stream_steps: shared-memory slots per warp, 2..8; the block's shared memory,
+                             warps x depth x (512 x (4 + value bytes) + 544 x vector bytes + 8), must stay
+                             within 227 KB (3) */
+  int refine32;           /* 1 (precision FP32 or MIXED): the FP32 iteration runs on FP32 corrections to the
+                             last restart point, which is held in FP64: a restart moves that point (in FP64)
+                             and recomputes, with FP64 sparse products, the FP32 iteration's costs - the
+                             residuals chat - Ahat^T y_r and bhat - Ahat x_r at the point - and the bounds
+                             -x_r of the primal corrections; the FP32 rounding then scales with the corrections,
+                             which shrink as the solve converges, rather than with the iterate. Single LPs,
+                             no recording or persistent loop. 0 = off; -1 = on for PDHG_MIXED, off for
+                             PDHG_FP32 (-1) */
 } pdhg_options;
 
 /* Scalars of one point on the problem as given (unscaled), all FP64.
@@ -206,6 +228,8 @@ typedef struct {
   int persistent_grid;            /* persistent = 2: blocks of the cooperative launch (0 before the first) */
   int64_t graph_launches;         /* CUDA-graph launches by pdhg_iterate so far */
   int values32;                   /* 1: FP64 steps read the FP32 copies of A's unscaled values (option values32) */
+  int stream_steps;               /* 1: the half-steps run as streamed kernels (option stream_steps) */
+  int refine32;                   /* 1: FP32 phases run on corrections to an FP64 point (option refine32) */
 } pdhg_info;
 
 /* One feasibility polishing attempt. */

@@ -13,9 +13,9 @@ LIB = os.path.join(HERE, "libpdhg.so")
 # sets a device error word (reported as PDHG_ERR_INVALID) and is skipped, so
 # nothing traps. For tests on small cases, not for timing.
 LIB_CHECKED = os.path.join(HERE, "libpdhg_checked.so")
-SOURCES = ["kernels.cu", "layout.cu", "persistent.cu", "pdhg_api.cu", "kkt_noalloc.cu", "autotune.cu",
+SOURCES = ["kernels.cu", "stream.cu", "layout.cu", "persistent.cu", "pdhg_api.cu", "kkt_noalloc.cu", "autotune.cu",
            "fp64_rate.cu"]
-HEADERS = ["common.cuh", "kernels.cuh", "decide.cuh"]
+HEADERS = ["common.cuh", "kernels.cuh", "decide.cuh", "step_ops.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

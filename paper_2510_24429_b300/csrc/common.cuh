@@ -84,6 +84,10 @@ struct DevState {
   int restart_scheme, pad2;
   double r_restart, r_prev;
   double pid_kp, pid_ki, pid_kd, pid_int, pid_prev;
+  // a bounded wait of a streamed step kernel ran out (its results are then
+  // incomplete; the host reports PDHG_ERR_TIMEOUT)
+  unsigned wait_err;
+  int pad3;
 };
 
 enum { TERM_LP = 0, TERM_PRIMAL = 1, TERM_DUAL = 2 };

@@ -28,6 +28,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "decide.cuh"
+#include "step_ops.cuh"
 
 // Minimum resident blocks per SM requested for the two step kernels. The
 // kernels are latency bound, so occupancy matters more than registers: with
@@ -87,17 +88,6 @@ __device__ __forceinline__ float2 ld_stream2(const float* p, unsigned long long 
       : "l"(p), "l"(pol));
   return r;
 }
-template <class T>
-struct Pair;
-template <>
-struct Pair<double> {
-  using type = double2;
-};
-template <>
-struct Pair<float> {
-  using type = float2;
-};
-
 // Scalar visitor (setup kernels): every warp takes units in a grid-stride
 // loop; op.entry(acc, k, r) sees every slot k of row r (padding included:
 // value 0, column 0), op.finish(r, acc) the combined result (max or sum).
@@ -169,30 +159,6 @@ struct GlobalGather {
 // arithmetic (every FP32 value is exactly an FP64 value).
 template <class G>
 using GatherT = typename std::decay<decltype(std::declval<const G&>()(0))>::type;
-
-// A value of type V as the arithmetic type T. FP32 to FP64 moves the bit
-// fields with integer operations (the sign, the exponent rebiased by
-// 1023 - 127 = 896, the 23 mantissa bits at the top of the 52), exact for
-// zeros and normal numbers, the only FP32 values option values32 admits: a
-// conversion instruction would run on the FP64 pipe, which the FP64 steps'
-// multiply-adds already keep busy.
-template <class T, class V>
-struct AsAcc {
-  static __device__ __forceinline__ T get(V v) { return v; }
-};
-template <>
-struct AsAcc<double, float> {
-  static __device__ __forceinline__ double get(float v) {
-    const unsigned f = __float_as_uint(v);
-    const unsigned mag = f & 0x7fffffffu;
-    const unsigned hi = (f & 0x80000000u) | (mag ? (mag >> 3) + 0x38000000u : 0u);
-    return __hiloint2double((int)hi, (int)(f << 29));
-  }
-};
-template <class T, class V>
-__device__ __forceinline__ T as_acc(V v) {
-  return AsAcc<T, V>::get(v);
-}
 
 template <int R, class V, class Op, class G>
 __device__ __forceinline__ void slice_dot(const Hyb& H, const V* __restrict__ vals, int row0, int nvalid,
@@ -506,6 +472,20 @@ struct ColScale {
   __device__ __forceinline__ T apply(T d_j, T v) const { return SC ? d_j * v : v; }
 };
 
+// The primal projection max(0, v), or with option refine32 (FP32 phases on
+// corrections to an FP64 restart point x_r) max(lo_j, v), lo = -x_r rounded
+// toward zero, so that x_r + v stays >= 0. NaN passes through either way.
+template <class T>
+__device__ __forceinline__ T project(const T* __restrict__, int, T v) {
+  return relu(v);
+}
+template <>
+__device__ __forceinline__ float project<float>(const float* __restrict__ lo, int j, float v) {
+  if (!lo) return relu(v);
+  const float l = __ldcs(lo + j);
+  return v < l ? l : v;
+}
+
 template <class T, bool SC = false>
 struct PrimalOp {
   using State = NoState;
@@ -516,11 +496,12 @@ struct PrimalOp {
   T tau;
   int accumulate;
   ColScale<T, SC> dc;
+  const T* __restrict__ lo;  // option refine32 (FP32): lower bounds of the corrections; nullptr: 0
   __device__ __forceinline__ State begin(int) { return {}; }
   __device__ __forceinline__ void finish(int j, T g, const State&) {
     const T d = dc.load(j);
     const T xj = __ldcs(x + j);
-    const T xn = relu(xj - tau * (__ldcs(ch + j) - dc.apply(d, g)));
+    const T xn = project(lo, j, xj - tau * (__ldcs(ch + j) - dc.apply(d, g)));
     xbar[j] = dc.apply(d, T(2) * xn - xj);  // default policy: gathered by the dual step next
     __stcs(x + j, xn);
     if (accumulate) __stcs(xsum + j, __ldcs(xsum + j) + xn);
@@ -537,18 +518,12 @@ template <class T, class V = T>
 __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STEP_TPB_MAX)
     k_primal_step(Hyb At, const V* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
                   T* __restrict__ x, T* __restrict__ xbar, T* __restrict__ xsum, const DevState* __restrict__ sts,
-                  const int* __restrict__ binst, int accumulate, int u_begin, const T* __restrict__ dsc) {
+                  const int* __restrict__ binst, int accumulate, int u_begin, const T* __restrict__ dsc,
+                  const T* __restrict__ lo) {
   const DevState* st = block_state(sts, binst);
   if (st->frozen) return;
-  PrimalOp<T, !std::is_same<T, V>::value> op{ch, x, xbar, xsum, (T)st->tau, accumulate, {dsc}};
+  PrimalOp<T, !std::is_same<T, V>::value> op{ch, x, xbar, xsum, (T)st->tau, accumulate, {dsc}, lo};
   hyb_dot(At, vals, GlobalGather<T>{y}, op, u_begin);
-}
-
-// weight w = (t + 1) / (t + 2) of the reflected Halpern step that runs as step
-// `it` after st->t was last updated (t = iterations since the last restart)
-__device__ __forceinline__ double halpern_weight(const DevState* st, int it) {
-  const double t = (double)(st->t + it);
-  return (t + 1.0) / (t + 2.0);
 }
 
 // The same, computed by one thread of the block and shared: an FP64 division
@@ -634,16 +609,6 @@ __global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
 // since the last restart, before this step) and the last restart point
 // (xr, yr) as anchor: x <- w ((1 + rho) x~ - rho x) + (1 - w) xr, likewise y;
 // the dual step still gathers xbar = 2 x~ - x.
-// The Halpern combination w ((1 + rho) t - rho z) + (1 - w) r, written as
-// w (t + rho (t - z)) + (1 - w) r; for the default rho = 1 the reflection
-// t + (t - z) = 2t - z is the extrapolated point the step computes anyway, so
-// the update costs one multiply and one multiply-add more
-template <class T>
-__device__ __forceinline__ T halpern_mix(T t, T z, T refl, T r, T w, T omw, T rho) {
-  const T u = rho == T(1) ? refl : t + rho * (t - z);
-  return w * u + omw * r;
-}
-
 template <class T, bool SC = false>
 struct PrimalHalpernOp {
   using State = NoState;
@@ -653,11 +618,12 @@ struct PrimalHalpernOp {
   const T* __restrict__ xr;
   T tau, w, rho;
   ColScale<T, SC> dc;
+  const T* __restrict__ lo;  // option refine32 (FP32): lower bounds of the corrections; nullptr: 0
   __device__ __forceinline__ State begin(int) { return {}; }
   __device__ __forceinline__ void finish(int j, T g, const State&) {
     const T d = dc.load(j);
     const T xj = __ldcs(x + j);
-    const T xt = relu(xj - tau * (__ldcs(ch + j) - dc.apply(d, g)));
+    const T xt = project(lo, j, xj - tau * (__ldcs(ch + j) - dc.apply(d, g)));
     const T xb = T(2) * xt - xj;
     xbar[j] = dc.apply(d, xb);
     __stcs(x + j, halpern_mix(xt, xj, xb, __ldcs(xr + j), w, T(1) - w, rho));
@@ -726,8 +692,9 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STE
     k_primal_short_combine(Hyb At, const V* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
                            T* __restrict__ x, T* __restrict__ xbar, T* __restrict__ xsum,
                            const DevState* __restrict__ st, int accumulate, int u_begin, int cblocks, int panels,
-                           const T* __restrict__ partial, int ncols, const T* __restrict__ dsc) {
-  PrimalOp<T, !std::is_same<T, V>::value> op{ch, x, xbar, xsum, (T)st->tau, accumulate, {dsc}};
+                           const T* __restrict__ partial, int ncols, const T* __restrict__ dsc,
+                           const T* __restrict__ lo) {
+  PrimalOp<T, !std::is_same<T, V>::value> op{ch, x, xbar, xsum, (T)st->tau, accumulate, {dsc}, lo};
   short_and_combine(At, vals, y, op, u_begin, cblocks, panels, partial, ncols);
 }
 
@@ -736,11 +703,11 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STE
     k_primal_step_halpern(Hyb At, const V* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
                           T* __restrict__ x, T* __restrict__ xbar, const T* __restrict__ xr,
                           const DevState* __restrict__ sts, const int* __restrict__ binst, int it, int u_begin,
-                          const T* __restrict__ dsc) {
+                          const T* __restrict__ dsc, const T* __restrict__ lo) {
   const DevState* st = block_state(sts, binst);
   if (st->frozen) return;
   PrimalHalpernOp<T, !std::is_same<T, V>::value> op{ch,  x, xbar, xr, (T)st->tau, (T)block_halpern_weight(st, it),
-                                                    (T)st->rho, {dsc}};
+                                                    (T)st->rho, {dsc}, lo};
   hyb_dot(At, vals, GlobalGather<T>{y}, op, u_begin);
 }
 
@@ -750,9 +717,9 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STE
                                    const T* __restrict__ ch, T* __restrict__ x, T* __restrict__ xbar,
                                    const T* __restrict__ xr, const DevState* __restrict__ st, int it, int u_begin,
                                    int cblocks, int panels, const T* __restrict__ partial, int ncols,
-                                   const T* __restrict__ dsc) {
+                                   const T* __restrict__ dsc, const T* __restrict__ lo) {
   PrimalHalpernOp<T, !std::is_same<T, V>::value> op{ch,  x, xbar, xr, (T)st->tau, (T)block_halpern_weight(st, it),
-                                                    (T)st->rho, {dsc}};
+                                                    (T)st->rho, {dsc}, lo};
   short_and_combine(At, vals, y, op, u_begin, cblocks, panels, partial, ncols);
 }
 
@@ -1332,6 +1299,119 @@ __global__ void k_apply32(const DevState* __restrict__ st, float* __restrict__ x
   }
 }
 
+// ---- option refine32: FP32 phases on corrections to an FP64 restart point ----
+// (reading: the paper names no precision scheme; FP64 holds the restart
+// point, the KKT residuals and the restart test, FP32 the iteration)
+__global__ void k_widen_delta(double* __restrict__ dst, const double* __restrict__ ref, const float* __restrict__ d,
+                              long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = ref[i] + (double)d[i];
+}
+
+__global__ void k_widen_sum_delta(double* __restrict__ dst, const double* __restrict__ ref,
+                                  const float* __restrict__ s32, long long len, const DevState* __restrict__ st) {
+  const double t = (double)st->t;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = t * ref[i] + (double)s32[i];
+}
+
+__global__ void k_make_average32_delta(const float* __restrict__ xs, const float* __restrict__ ys,
+                                       const float* __restrict__ x, const float* __restrict__ y,
+                                       const double* __restrict__ xr, const double* __restrict__ yr,
+                                       double* __restrict__ xa, double* __restrict__ ya, int n, int m,
+                                       const DevState* __restrict__ st) {
+  const long long t = st->t;
+  const double it = t > 0 ? 1.0 / (double)t : 0.0;
+  const int len = n > m ? n : m;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+    if (i < n) xa[i] = xr[i] + (t > 0 ? (double)xs[i] * it : (double)x[i]);
+    if (i < m) ya[i] = yr[i] + (t > 0 ? (double)ys[i] * it : (double)y[i]);
+  }
+}
+
+__global__ void k_apply32_delta(const DevState* __restrict__ st, float* __restrict__ x32, float* __restrict__ y32,
+                                double* __restrict__ x, double* __restrict__ y, const double* __restrict__ xa,
+                                const double* __restrict__ ya, double* __restrict__ xr, double* __restrict__ yr,
+                                float* __restrict__ xs, float* __restrict__ ys, int n, int m) {
+  const int mode = st->apply_mode;
+  if (mode == APPLY_NONE) return;
+  const bool from_a = mode == APPLY_RESTART_AVG || mode == APPLY_RESTART_STEP;
+  const int len = n > m ? n : m;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+    if (i < n) {
+      if (mode == APPLY_TAKE_AVG) {
+        x[i] = xa[i];
+        x32[i] = (float)(xa[i] - xr[i]);
+      } else {
+        const double v = from_a ? xa[i] : x[i];
+        x[i] = v;
+        xr[i] = v;
+        x32[i] = 0.0f;
+        xs[i] = 0.0f;  // the sums restart; the Halpern anchor is the reference itself
+      }
+    }
+    if (i < m) {
+      if (mode == APPLY_TAKE_AVG) {
+        y[i] = ya[i];
+        y32[i] = (float)(ya[i] - yr[i]);
+      } else {
+        const double v = from_a ? ya[i] : y[i];
+        y[i] = v;
+        yr[i] = v;
+        y32[i] = 0.0f;
+        ys[i] = 0.0f;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ bool restarted(const DevState* st) {
+  const int mode = st->apply_mode;
+  return mode == APPLY_RESTART_CUR || mode == APPLY_RESTART_AVG || mode == APPLY_RESTART_STEP;
+}
+
+// rows j of Ahat^T: ch32_j = chat_j - (Ahat^T yr)_j, lo32_j = -xr_j rounded up
+struct RecenterDualOp {
+  using State = NoState;
+  const double* __restrict__ ch;
+  const double* __restrict__ xr;
+  float* __restrict__ ch32;
+  float* __restrict__ lo32;
+  __device__ __forceinline__ State begin(int) { return {}; }
+  __device__ __forceinline__ void finish(int j, double g, const State&) {
+    ch32[j] = (float)(ch[j] - g);
+    lo32[j] = __double2float_ru(-xr[j]);
+  }
+};
+
+// rows i of Ahat: bh32_i = bhat_i - (Ahat xr)_i
+struct RecenterPrimalOp {
+  using State = NoState;
+  const double* __restrict__ bh;
+  float* __restrict__ bh32;
+  __device__ __forceinline__ State begin(int) { return {}; }
+  __device__ __forceinline__ void finish(int i, double h, const State&) { bh32[i] = (float)(bh[i] - h); }
+};
+
+__global__ void __launch_bounds__(STEP_TPB_MAX) k_recenter_dual(Hyb At, const double* __restrict__ yr,
+                                                                const double* __restrict__ ch,
+                                                                const double* __restrict__ xr, float* __restrict__ ch32,
+                                                                float* __restrict__ lo32,
+                                                                const DevState* __restrict__ st, int force) {
+  if (!force && !restarted(st)) return;
+  RecenterDualOp op{ch, xr, ch32, lo32};
+  hyb_dot(At, At.v, GlobalGather<double>{yr}, op);
+}
+
+__global__ void __launch_bounds__(STEP_TPB_MAX) k_recenter_primal(Hyb A, const double* __restrict__ xr,
+                                                                  const double* __restrict__ bh,
+                                                                  float* __restrict__ bh32,
+                                                                  const DevState* __restrict__ st, int force) {
+  if (!force && !restarted(st)) return;
+  RecenterPrimalOp op{bh, bh32};
+  hyb_dot(A, A.v, GlobalGather<double>{xr}, op);
+}
+
 // Start of the FP64 phase: the point just evaluated into st->cur becomes the
 // restart reference and the count since the last restart starts over.
 // Start of a feasibility polishing phase (Section 5; the phases are readings).
@@ -1783,16 +1863,18 @@ void launch_finish_setup(DevState* st, const double* scal, double step_factor, i
 void launch_primal_step(const Hyb& At, const double* y, const double* ch, double* x, double* xbar, double* xsum,
                         const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst, int tpb,
                         int u_begin) {
-  k_primal_step<double><<<grid, tpb, 0, s>>>(At, At.v, y, ch, x, xbar, xsum, st, binst, accumulate, u_begin, nullptr);
+  k_primal_step<double><<<grid, tpb, 0, s>>>(At, At.v, y, ch, x, xbar, xsum, st, binst, accumulate, u_begin, nullptr,
+                                              nullptr);
 }
 void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
                       const DevState* st, int accumulate, int grid, cudaStream_t s, const int* binst, int tpb) {
   k_dual_step<double><<<grid, tpb, 0, s>>>(A, A.v, xbar, bh, y, ysum, st, binst, accumulate, nullptr, nullptr);
 }
 void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float* x, float* xbar, float* xsum,
-                          const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb, int u_begin) {
+                          const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb, int u_begin,
+                          const float* lo) {
   k_primal_step<float><<<grid, tpb, 0, s>>>(At, At.v32, y, ch, x, xbar, xsum, st, nullptr, accumulate, u_begin,
-                                              nullptr);
+                                              nullptr, lo);
 }
 void launch_dual_step32(const Hyb& A, const float* xbar, const float* bh, float* y, float* ysum, const DevState* st,
                         int accumulate, int grid, cudaStream_t s, int tpb) {
@@ -1802,7 +1884,7 @@ void launch_primal_step_u(const Hyb& At, const double* yg, const double* ch, dou
                           const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb, int u_begin,
                           const double* dc) {
   k_primal_step<double, float><<<grid, tpb, 0, s>>>(At, At.u32, yg, ch, x, xbar, xsum, st, nullptr, accumulate,
-                                                     u_begin, dc);
+                                                     u_begin, dc, nullptr);
 }
 void launch_dual_step_u(const Hyb& A, const double* xbar, const double* bh, double* y, double* ysum,
                         const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb, const double* dr,
@@ -1835,33 +1917,35 @@ template void launch_panel_pass<double, float>(const Hyb&, const float*, const P
 template <class T, class V>
 void launch_primal_short_combine(const Hyb& At, const V* vals, const T* y, const T* ch, T* x, T* xbar, T* xsum,
                                  const DevState* st, int accumulate, int short_grid, const PanelLayout& L,
-                                 const T* partial, int tpb, cudaStream_t s, int halpern_it, const T* dc) {
+                                 const T* partial, int tpb, cudaStream_t s, int halpern_it, const T* dc,
+                                 const T* lo) {
   const int cblocks = (L.ncols + tpb - 1) / tpb;
   const int grid = cblocks + short_grid;
   if (halpern_it >= 0)
     k_primal_short_combine_halpern<T, V><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xsum, st, halpern_it,
-                                                                L.ulong, cblocks, L.panels, partial, L.ncols, dc);
+                                                                L.ulong, cblocks, L.panels, partial, L.ncols, dc,
+                                                                lo);
   else
     k_primal_short_combine<T, V><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xsum, st, accumulate, L.ulong,
-                                                        cblocks, L.panels, partial, L.ncols, dc);
+                                                        cblocks, L.panels, partial, L.ncols, dc, lo);
 }
 template void launch_primal_short_combine<double, double>(const Hyb&, const double*, const double*, const double*,
                                                           double*, double*, double*, const DevState*, int, int,
                                                           const PanelLayout&, const double*, int, cudaStream_t, int,
-                                                          const double*);
+                                                          const double*, const double*);
 template void launch_primal_short_combine<float, float>(const Hyb&, const float*, const float*, const float*, float*,
                                                         float*, float*, const DevState*, int, int,
                                                         const PanelLayout&, const float*, int, cudaStream_t, int,
-                                                        const float*);
+                                                        const float*, const float*);
 template void launch_primal_short_combine<double, float>(const Hyb&, const float*, const double*, const double*,
                                                          double*, double*, double*, const DevState*, int, int,
                                                          const PanelLayout&, const double*, int, cudaStream_t, int,
-                                                         const double*);
+                                                         const double*, const double*);
 template <class T, class V>
 void launch_primal_step_halpern(const Hyb& At, const V* vals, const T* y, const T* ch, T* x, T* xbar, const T* xr,
                                 const DevState* st, int it, int grid, cudaStream_t s, int tpb, const int* binst,
-                                int u_begin, const T* dc) {
-  k_primal_step_halpern<T, V><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xr, st, binst, it, u_begin, dc);
+                                int u_begin, const T* dc, const T* lo) {
+  k_primal_step_halpern<T, V><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xr, st, binst, it, u_begin, dc, lo);
 }
 template <class T, class V>
 void launch_dual_step_halpern(const Hyb& A, const V* vals, const T* xbar, const T* bh, T* y, const T* yr,
@@ -1871,13 +1955,15 @@ void launch_dual_step_halpern(const Hyb& A, const V* vals, const T* xbar, const 
 }
 template void launch_primal_step_halpern<double, double>(const Hyb&, const double*, const double*, const double*,
                                                          double*, double*, const double*, const DevState*, int, int,
-                                                         cudaStream_t, int, const int*, int, const double*);
+                                                         cudaStream_t, int, const int*, int, const double*,
+                                                         const double*);
 template void launch_primal_step_halpern<float, float>(const Hyb&, const float*, const float*, const float*, float*,
                                                        float*, const float*, const DevState*, int, int, cudaStream_t,
-                                                       int, const int*, int, const float*);
+                                                       int, const int*, int, const float*, const float*);
 template void launch_primal_step_halpern<double, float>(const Hyb&, const float*, const double*, const double*,
                                                         double*, double*, const double*, const DevState*, int, int,
-                                                        cudaStream_t, int, const int*, int, const double*);
+                                                        cudaStream_t, int, const int*, int, const double*,
+                                                        const double*);
 template void launch_dual_step_halpern<double, double>(const Hyb&, const double*, const double*, const double*,
                                                        double*, const double*, const DevState*, int, int,
                                                        cudaStream_t, int, const int*, const double*, double*);
@@ -2005,6 +2091,29 @@ void launch_apply32(const DevState* st, float* x32, float* y32, double* x, doubl
                     const double* ya, double* xr, double* yr, float* xs, float* ys, int n, int m, int grid,
                     cudaStream_t s) {
   k_apply32<<<grid, TPB, 0, s>>>(st, x32, y32, x, y, xa, ya, xr, yr, xs, ys, n, m);
+}
+void launch_widen_delta(double* dst, const double* ref, const float* d, long long len, int grid, cudaStream_t s) {
+  k_widen_delta<<<grid, TPB, 0, s>>>(dst, ref, d, len);
+}
+void launch_widen_sum_delta(double* dst, const double* ref, const float* sum32, long long len, const DevState* st,
+                            int grid, cudaStream_t s) {
+  k_widen_sum_delta<<<grid, TPB, 0, s>>>(dst, ref, sum32, len, st);
+}
+void launch_make_average32_delta(const float* xs, const float* ys, const float* x, const float* y, const double* xr,
+                                 const double* yr, double* xa, double* ya, int n, int m, const DevState* st, int grid,
+                                 cudaStream_t s) {
+  k_make_average32_delta<<<grid, TPB, 0, s>>>(xs, ys, x, y, xr, yr, xa, ya, n, m, st);
+}
+void launch_apply32_delta(const DevState* st, float* x32, float* y32, double* x, double* y, const double* xa,
+                          const double* ya, double* xr, double* yr, float* xs, float* ys, int n, int m, int grid,
+                          cudaStream_t s) {
+  k_apply32_delta<<<grid, TPB, 0, s>>>(st, x32, y32, x, y, xa, ya, xr, yr, xs, ys, n, m);
+}
+void launch_recenter(const Hyb& A, const Hyb& At, const double* xr, const double* yr, const double* bh,
+                     const double* ch, float* bh32, float* ch32, float* lo32, const DevState* st, int force, int grA,
+                     int grT, cudaStream_t s) {
+  k_recenter_dual<<<grT, TPB, 0, s>>>(At, yr, ch, xr, ch32, lo32, st, force);
+  k_recenter_primal<<<grA, TPB, 0, s>>>(A, xr, bh, bh32, st, force);
 }
 void launch_fp32_inexact(const double* v, long long len, int* flag, cudaStream_t s) {
   if (len > 0) k_fp32_inexact<<<(int)std::min<long long>(4096, (len + TPB - 1) / TPB), TPB, 0, s>>>(v, len, flag);

@@ -58,7 +58,8 @@ void launch_dual_step(const Hyb& A, const double* xbar, const double* bh, double
 template <class T, class V = T>
 void launch_primal_step_halpern(const Hyb& At, const V* vals, const T* y, const T* ch, T* x, T* xbar, const T* xr,
                                 const DevState* st, int it, int grid, cudaStream_t s, int tpb,
-                                const int* binst = nullptr, int u_begin = 0, const T* dc = nullptr);
+                                const int* binst = nullptr, int u_begin = 0, const T* dc = nullptr,
+                                const T* lo = nullptr);
 template <class T, class V = T>
 void launch_dual_step_halpern(const Hyb& A, const V* vals, const T* xbar, const T* bh, T* y, const T* yr,
                               const DevState* st, int it, int grid, cudaStream_t s, int tpb,
@@ -67,7 +68,7 @@ void launch_dual_step_halpern(const Hyb& A, const V* vals, const T* xbar, const 
 // accumulation); tau and sigma are read from the FP64 state and rounded
 void launch_primal_step32(const Hyb& At, const float* y, const float* ch, float* x, float* xbar, float* xsum,
                           const DevState* st, int accumulate, int grid, cudaStream_t s, int tpb = TPB,
-                          int u_begin = 0);
+                          int u_begin = 0, const float* lo = nullptr);
 void launch_dual_step32(const Hyb& A, const float* xbar, const float* bh, float* y, float* ysum, const DevState* st,
                         int accumulate, int grid, cudaStream_t s, int tpb = TPB);
 // the two half-steps in FP64 on the unscaled values in FP32 (At.u32 / A.u32,
@@ -90,6 +91,28 @@ void launch_make_average32(const float* xs, const float* ys, const float* x, con
 void launch_apply32(const DevState* st, float* x32, float* y32, double* x, double* y, const double* xa,
                     const double* ya, double* xr, double* yr, float* xs, float* ys, int n, int m, int grid,
                     cudaStream_t s);
+// option refine32: FP32 phases iterate on FP32 corrections (x32, y32) to the
+// last restart point (xr, yr), held in FP64. x = xr + x32, y = yr + y32
+void launch_widen_delta(double* dst, const double* ref, const float* d, long long len, int grid, cudaStream_t s);
+// FP64 averages xa = xr + xs / t (t = st->t; t == 0: the current point)
+void launch_make_average32_delta(const float* xs, const float* ys, const float* x, const float* y, const double* xr,
+                                 const double* yr, double* xa, double* ya, int n, int m, const DevState* st, int grid,
+                                 cudaStream_t s);
+// the decision applied in refined FP32 phases: a restart moves the FP64
+// reference (xr, yr) to the new point and clears the corrections and sums;
+// taking the average sets the corrections to xa - xr
+void launch_apply32_delta(const DevState* st, float* x32, float* y32, double* x, double* y, const double* xa,
+                          const double* ya, double* xr, double* yr, float* xs, float* ys, int n, int m, int grid,
+                          cudaStream_t s);
+// re-centring after a restart (or always, with force): ch32 = chat - Ahat^T yr,
+// lo32 = -xr rounded toward zero (At: Ahat^T); bh32 = bhat - Ahat xr (A: Ahat),
+// computed in FP64 and rounded to FP32
+void launch_recenter(const Hyb& A, const Hyb& At, const double* xr, const double* yr, const double* bh,
+                     const double* ch, float* bh32, float* ch32, float* lo32, const DevState* st, int force, int grA,
+                     int grT, cudaStream_t s);
+// PDLP-style sums at the switch to FP64: xsum = t xr + xsum32 (t = st->t)
+void launch_widen_sum_delta(double* dst, const double* ref, const float* sum32, long long len, const DevState* st,
+                            int grid, cudaStream_t s);
 // restart reference := st->cur, t := 0 (start of the FP64 polishing phase)
 void launch_promote_state(DevState* st, cudaStream_t s);
 // restart reference := st->cur, k := t := 0, snapshots off, termination test
@@ -132,6 +155,44 @@ struct PanelLayout {
 };
 // allow the panel kernels their shared memory (once per device, outside graph capture)
 cudaError_t configure_primal_panels();
+// ---- streamed step kernels (option stream_steps, stream.cu) ----------------
+// Every warp owns `depth` shared-memory slots; a slot holds one bulk-copied
+// piece of at most STREAM_PIECE matrix slots (indices and values) and the
+// staged rows (at most STREAM_PRE_CAP per vector, alignment included) of up to
+// STREAM_NPRE of the step's vectors.
+constexpr int STREAM_PIECE = 512;  // a multiple of 128 (the long-row lane pattern)
+constexpr int STREAM_PRE_CAP = 136;
+constexpr int STREAM_NPRE = 4;
+constexpr int STREAM_TPB_MAX = 512;
+constexpr int STREAM_SMEM_MAX = 227 * 1024 - 256;  // dynamic shared memory of one block (static part beside it)
+constexpr size_t stream_slot_bytes(size_t t, size_t v) {
+  return (size_t)STREAM_PIECE * (4 + v) + (size_t)STREAM_NPRE * STREAM_PRE_CAP * t;
+}
+struct StreamCfg {
+  int warps = 8;   // warps per block
+  int depth = 3;   // slots per warp
+  int blocks = 0;  // grid (resident blocks per SM x SMs), set by configure_stream
+  size_t smem = 0; // dynamic shared memory per block, set by configure_stream
+};
+size_t stream_smem(const StreamCfg& c, size_t t, size_t v);
+// allow the kernels of value type V / arithmetic T their shared memory and
+// size the grid (once per context, outside graph capture)
+template <class T, class V>
+cudaError_t configure_stream(StreamCfg& c, int sms);
+// the dual half-step over every unit of A (halpern_it >= 0: the Halpern form
+// with anchor ysum_or_yr; else y_sum += y' when accumulate); V = float with
+// T = double: the unscaled values with D_r (dr) and the gathered copy yg
+template <class T, class V>
+void launch_stream_dual(const Hyb& A, const V* vals, const T* xbar, const T* bh, T* y, T* ysum_or_yr, DevState* st,
+                        int accumulate, int halpern_it, const T* dr, T* yg, const StreamCfg& c, cudaStream_t s);
+// the primal half-step over the units of At from u_begin on and, when
+// ncols > 0, the combine of the long columns [0, ncols) from their panel
+// partial sums (panels of them, panel-major); lo: the FP32 projection bounds
+// of option refine32 (nullptr: 0)
+template <class T, class V>
+void launch_stream_primal(const Hyb& At, const V* vals, const T* y, const T* ch, T* x, T* xbar, T* xsum_or_xr,
+                          DevState* st, int accumulate, int halpern_it, int u_begin, int ncols, int panels,
+                          const T* partial, const T* dc, const StreamCfg& c, cudaStream_t s, const T* lo = nullptr);
 // pass 1: per-(column, panel) partial sums of the long columns
 template <class T, class V = T>
 void launch_panel_pass(const Hyb& Pn, const V* vals, const PanelLayout& L, const T* y, T* partial, cudaStream_t s);
@@ -144,7 +205,7 @@ template <class T, class V = T>
 void launch_primal_short_combine(const Hyb& At, const V* vals, const T* y, const T* ch, T* x, T* xbar, T* xsum,
                                  const DevState* st, int accumulate, int short_grid, const PanelLayout& L,
                                  const T* partial, int tpb, cudaStream_t s, int halpern_it = -1,
-                                 const T* dc = nullptr);
+                                 const T* dc = nullptr, const T* lo = nullptr);
 // the dual step, persistent (grid = number of SMs), with xbar[0, hot) staged
 // in shared memory (hot * sizeof(T) <= HOT_SMEM_MAX), values vals in
 // precision T; halpern_it >= 0: the reflected Halpern form of step

@@ -58,8 +58,14 @@ thread_local std::string g_create_error = "no error";
 constexpr int EV_POOL = 256;
 constexpr int SNAP_SLOTS = 3;  // pinned host ring of completed snapshots
 // PDHG_MIXED: iterations without a 10% gain in the FP32 phase before FP64
-// takes over (PDHG itself plateaus for a few thousand iterations at times)
+// takes over (PDHG itself plateaus for a few thousand iterations at times).
+// A refined FP32 phase (refine32) follows the FP64 iteration's trajectory, so
+// its plateaus are the method's own: it gets four times the window (on the
+// 1e6 x 3e6 LP the cuPDLP+ form's plateaus between 1e-6 and 1e-8 passed the
+// shorter window, and the refined FP32 iteration alone reached 1e-8 in as
+// many iterations as FP64)
 constexpr int64_t STALL_ITERS = 16384;
+constexpr int64_t STALL_ITERS_REFINED = 4 * STALL_ITERS;
 
 }  // namespace
 
@@ -122,6 +128,14 @@ struct pdhg_ctx {
   // refreshed from y at the start of every block) and D_c xbar (in xbar)
   bool vals_u = false;
   double* yg = nullptr;
+  // option refine32: FP32 phases iterate on corrections to (xr, yr); lo32 =
+  // the primal corrections' lower bounds -xr (rounded toward zero)
+  bool refine = false;
+  float* lo32 = nullptr;
+  // option stream_steps: the streamed step kernels' launch shapes for
+  // (T, V) = (double, double), (float, float), (double, float)
+  bool stream_on = false;
+  StreamCfg scfg[3];
   // CUDA graphs of one evaluation block, per precision phase (FP64, FP32)
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   int64_t graph_launches[2] = {0, 0};
@@ -248,7 +262,9 @@ pdhg_status read_check(pdhg_ctx* ctx) {
 template <class T>
 cudaError_t dalloc(pdhg_ctx* ctx, T** p, size_t count) {
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  // 64 bytes of slack: the streamed step kernels bulk-copy vectors in whole
+  // 16-byte units, up to 12 bytes past a vector's last entry
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T) + 64);
   if (e == cudaSuccess) ctx->allocs.push_back(q);
   *p = static_cast<T*>(q);
   return e;
@@ -422,17 +438,33 @@ void eval_point_fp(pdhg_ctx* ctx, EvalSums* dst) {
 }
 
 // During the FP32 phase: refresh the FP64 copies of the current iterate.
+// (option refine32: the FP64 restart point plus the FP32 corrections)
 void widen_current(pdhg_ctx* ctx) {
+  if (ctx->refine) {
+    launch_widen_delta(ctx->x, ctx->xr, ctx->x32, ctx->n, vec_grid(ctx, ctx->n), ctx->stream);
+    launch_widen_delta(ctx->y, ctx->yr, ctx->y32, ctx->m, vec_grid(ctx, ctx->m), ctx->stream);
+    return;
+  }
   launch_widen(ctx->x, ctx->x32, ctx->n, vec_grid(ctx, ctx->n), ctx->stream);
   launch_widen(ctx->y, ctx->y32, ctx->m, vec_grid(ctx, ctx->m), ctx->stream);
+}
+
+// During the FP32 phase: the FP64 average of the current restart epoch.
+void average32(pdhg_ctx* ctx) {
+  const int n = (int)ctx->n, m = (int)ctx->m, gv = vec_grid(ctx, std::max(ctx->n, ctx->m));
+  if (ctx->refine)
+    launch_make_average32_delta(ctx->xsum32, ctx->ysum32, ctx->x32, ctx->y32, ctx->xr, ctx->yr, ctx->xavg,
+                                ctx->yavg, n, m, ctx->st, gv, ctx->stream);
+  else
+    launch_make_average32(ctx->xsum32, ctx->ysum32, ctx->x32, ctx->y32, ctx->xavg, ctx->yavg, n, m, ctx->st, gv,
+                          ctx->stream);
 }
 
 void point_of(pdhg_ctx* ctx, int which, const double** px, const double** py) {
   if (ctx->phase32) widen_current(ctx);
   if (which == PDHG_AVERAGE) {
     if (ctx->phase32)
-      launch_make_average32(ctx->xsum32, ctx->ysum32, ctx->x32, ctx->y32, ctx->xavg, ctx->yavg, (int)ctx->n,
-                            (int)ctx->m, ctx->st, vec_grid(ctx, std::max(ctx->n, ctx->m)), ctx->stream);
+      average32(ctx);
     else
       launch_make_average(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, (int)ctx->n, (int)ctx->m,
                           ctx->st, vec_grid(ctx, std::max(ctx->n, ctx->m)), ctx->stream);
@@ -1106,6 +1138,33 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
     }
     CK(ctx, dalloc(ctx, &ctx->yg, m));
   }
+#ifndef PDHG_CHECKED
+  // ---- option stream_steps: launch shapes of the streamed step kernels ----
+  if (o.stream_steps) {
+    // (T, V) per configuration, and whether this context runs it
+    const size_t tv[3][2] = {{8, 8}, {4, 4}, {8, 4}};
+    const bool used[3] = {o.precision != PDHG_FP32 && !ctx->vals_u, o.precision != PDHG_FP64, ctx->vals_u};
+    for (int i = 0; i < 3; ++i) {
+      if (!used[i]) continue;
+      StreamCfg& c = ctx->scfg[i];
+      c.depth = o.stream_depth;
+      const size_t per_warp = (size_t)c.depth * (stream_slot_bytes(tv[i][0], tv[i][1]) + 8);
+      c.warps = o.stream_warps ? o.stream_warps : (int)std::min<size_t>(16, (size_t)STREAM_SMEM_MAX / per_warp);
+      if (c.warps < 1 || stream_smem(c, tv[i][0], tv[i][1]) > (size_t)STREAM_SMEM_MAX)
+        return fail(ctx, PDHG_ERR_INVALID, "stream_steps: stream_warps x stream_depth slots exceed 227 KB of "
+                                           "shared memory");
+      cudaError_t e = cudaSuccess;
+      if (i == 0)
+        e = configure_stream<double, double>(c, ctx->sms);
+      else if (i == 1)
+        e = configure_stream<float, float>(c, ctx->sms);
+      else
+        e = configure_stream<double, float>(c, ctx->sms);
+      CK(ctx, e);
+    }
+    ctx->stream_on = true;
+  }
+#endif
 
   // ---- device: scaling ----
   const int gn = vec_grid(ctx, n), gm = vec_grid(ctx, m);
@@ -1226,6 +1285,24 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
       CK(ctx, cudaMemsetAsync(ps.partial32, 0, sizeof(float) * slots, s));
       launch_narrow(ps.Pn.v32, ps.Pn.v, ps.Pn.slots, vec_grid(ctx, ps.Pn.slots), s);
     }
+    if (o.refine32 == 1 || (o.refine32 == -1 && o.precision == PDHG_MIXED && !o.record_for_backward &&
+                            !o.persistent)) {
+      // option refine32: the FP32 iteration runs on corrections to the FP64
+      // restart point (xr, yr) = the starting point, copied above: the
+      // corrections and sums start at zero, and the FP32 costs are the
+      // residuals chat - Ahat^T yr and bhat - Ahat xr at the reference
+      ctx->refine = true;
+      CK(ctx, dalloc(ctx, &ctx->lo32, n));
+      CK(ctx, cudaMemsetAsync(ctx->x32, 0, sizeof(float) * n, s));
+      CK(ctx, cudaMemsetAsync(ctx->y32, 0, sizeof(float) * m, s));
+      CK(ctx, cudaMemsetAsync(ctx->xsum32, 0, sizeof(float) * n, s));
+      CK(ctx, cudaMemsetAsync(ctx->ysum32, 0, sizeof(float) * m, s));
+      launch_recenter(A, At, ctx->xr, ctx->yr, ctx->bh, ctx->ch, ctx->bh32, ctx->ch32, ctx->lo32, ctx->st, 1, grA, grT,
+                      s);
+      ctx->phase32 = true;
+    }
+  }
+  if (o.precision != PDHG_FP64 && !ctx->refine) {
     launch_narrow(ctx->ch32, ctx->ch, n, gn, s);
     launch_narrow(ctx->bh32, ctx->bh, m, gm, s);
     launch_narrow(ctx->x32, ctx->x, n, gn, s);
@@ -1271,11 +1348,11 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
 template <class T, class V = T>
 pdhg_status panel_half_step(pdhg_ctx* ctx, const PanelSet& ps, const V* vals, const V* valsT, const T* y, const T* ch,
                             T* x, T* xbar, T* xsum, T* partial, int accumulate, int tpb, int halpern_it,
-                            const T* dc = nullptr) {
+                            const T* dc = nullptr, const T* lo = nullptr) {
   cudaStream_t s = ctx->stream;
   launch_panel_pass<T, V>(ps.Pn, vals, ps.pl, y, partial, s);
   launch_primal_short_combine<T, V>(ctx->At, valsT, y, ch, x, xbar, xsum, ctx->st, accumulate, short_grid(ctx, ps),
-                                    ps.pl, partial, tpb, s, halpern_it, dc);
+                                    ps.pl, partial, tpb, s, halpern_it, dc, lo);
   CK(ctx, cudaGetLastError());
   ctx->launches += 1;  // two launches; the caller counts one primal step
   return PDHG_OK;
@@ -1301,18 +1378,72 @@ pdhg_status primal_step(pdhg_ctx* ctx, bool f32, const void* y, void* x, void* x
     if (f32) {
       const PanelSet& ps = ctx->pan[ctx->pan32 ? 1 : 0];
       return panel_half_step<float>(ctx, ps, ps.Pn.v32, ctx->At.v32, (const float*)y, ctx->ch32, (float*)x,
-                                    (float*)xbar, (float*)xsum, ps.partial32, accumulate, tpb, -1);
+                                    (float*)xbar, (float*)xsum, ps.partial32, accumulate, tpb, -1, nullptr,
+                                    ctx->lo32);
     }
     return panel_half_step<double>(ctx, ctx->pan[0], ctx->pan[0].Pn.v, ctx->At.v, (const double*)y, ctx->ch,
                                    (double*)x, (double*)xbar, (double*)xsum, ctx->pan[0].partial, accumulate, tpb, -1);
   } else if (f32) {
     launch_primal_step32(ctx->At, (const float*)y, ctx->ch32, (float*)x, (float*)xbar, (float*)xsum, ctx->st,
-                         accumulate, grT, s, tpb);
+                         accumulate, grT, s, tpb, 0, ctx->lo32);
   } else {
     launch_primal_step(ctx->At, (const double*)y, ctx->ch, (double*)x, (double*)xbar, (double*)xsum, ctx->st,
                        accumulate, grT, s, nullptr, tpb);
   }
   return PDHG_OK;
+}
+
+// The primal half-step of iteration `it` of the block as streamed kernels
+// (option stream_steps), in the phase's precision and form: with the panel
+// layout, the panel pass over the long columns, then one streamed launch that
+// combines their partial sums and steps the short columns; else one streamed
+// launch over every column.
+void stream_primal(pdhg_ctx* ctx, int it, const double* yg64) {
+  const pdhg_options& o = ctx->opt;
+  cudaStream_t s = ctx->stream;
+  const int hit = o.halpern ? it : -1, acc = o.halpern ? 0 : o.restarts;
+  if (ctx->phase32) {
+    const PanelSet* ps = ctx->panels_on ? &ctx->pan[ctx->pan32 ? 1 : 0] : nullptr;
+    if (ps) launch_panel_pass<float, float>(ps->Pn, ps->Pn.v32, ps->pl, ctx->y32, ps->partial32, s);
+    launch_stream_primal<float, float>(ctx->At, ctx->At.v32, ctx->y32, ctx->ch32, ctx->x32, ctx->xbar32,
+                                       ctx->xsum32, ctx->st, acc, hit, ps ? ps->pl.ulong : 0, ps ? ps->pl.ncols : 0,
+                                       ps ? ps->pl.panels : 0, ps ? ps->partial32 : nullptr, nullptr, ctx->scfg[1], s,
+                                       ctx->lo32);
+  } else {
+    const bool vu = ctx->vals_u;
+    const PanelSet* ps = ctx->panels_on ? &ctx->pan[0] : nullptr;
+    double* sum = o.halpern ? ctx->xr : ctx->xsum;
+    if (vu) {
+      if (ps) launch_panel_pass<double, float>(ps->Pn, ps->Pn.u32, ps->pl, yg64, ps->partial, s);
+      launch_stream_primal<double, float>(ctx->At, ctx->At.u32, yg64, ctx->ch, ctx->x, ctx->xbar, sum, ctx->st, acc,
+                                          hit, ps ? ps->pl.ulong : 0, ps ? ps->pl.ncols : 0, ps ? ps->pl.panels : 0,
+                                          ps ? ps->partial : nullptr, ctx->dc, ctx->scfg[2], s);
+    } else {
+      if (ps) launch_panel_pass<double, double>(ps->Pn, ps->Pn.v, ps->pl, ctx->y, ps->partial, s);
+      launch_stream_primal<double, double>(ctx->At, ctx->At.v, ctx->y, ctx->ch, ctx->x, ctx->xbar, sum, ctx->st,
+                                           acc, hit, ps ? ps->pl.ulong : 0, ps ? ps->pl.ncols : 0,
+                                           ps ? ps->pl.panels : 0, ps ? ps->partial : nullptr, nullptr, ctx->scfg[0],
+                                           s);
+    }
+  }
+  if (ctx->panels_on) ctx->launches += 1;  // two launches; the caller counts one
+}
+
+// The dual half-step of iteration `it` of the block as one streamed launch.
+void stream_dual(pdhg_ctx* ctx, int it) {
+  const pdhg_options& o = ctx->opt;
+  cudaStream_t s = ctx->stream;
+  const int hit = o.halpern ? it : -1, acc = o.halpern ? 0 : o.restarts;
+  if (ctx->phase32)
+    launch_stream_dual<float, float>(ctx->A, ctx->A.v32, ctx->xbar32, ctx->bh32, ctx->y32, ctx->ysum32, ctx->st, acc,
+                                     hit, nullptr, nullptr, ctx->scfg[1], s);
+  else if (ctx->vals_u)
+    launch_stream_dual<double, float>(ctx->A, ctx->A.u32, ctx->xbar, ctx->bh, ctx->y, o.halpern ? ctx->yr : ctx->ysum,
+                                      ctx->st, acc, hit, ctx->dr, ctx->yg, ctx->scfg[2], s);
+  else
+    launch_stream_dual<double, double>(ctx->A, ctx->A.v, ctx->xbar, ctx->bh, ctx->y,
+                                       o.halpern ? ctx->yr : ctx->ysum, ctx->st, acc, hit, nullptr, nullptr,
+                                       ctx->scfg[0], s);
 }
 
 // The step launches of nb iterations (plus adjoint checkpoints and kernel
@@ -1340,6 +1471,13 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
       if (rs != PDHG_OK) return rs;
     }
     if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it], s));
+    if (ctx->stream_on) {
+      stream_primal(ctx, (int)it, yg64);
+      if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 1], s));
+      stream_dual(ctx, (int)it);
+      if (timing) CK(ctx, cudaEventRecord(ctx->ev[3 * it + 2], s));
+      continue;
+    }
     if (o.halpern && vu) {
       if (ctx->panels_on) {
         pdhg_status rs = panel_half_step<double, float>(ctx, ctx->pan[0], ctx->pan[0].Pn.u32, ctx->At.u32, yg64,
@@ -1364,11 +1502,13 @@ pdhg_status enqueue_steps(pdhg_ctx* ctx, int64_t nb, bool timing) {
       if (ctx->panels_on) {
         const PanelSet& ps = ctx->pan[ctx->pan32 ? 1 : 0];
         pdhg_status rs = panel_half_step<float>(ctx, ps, ps.Pn.v32, ctx->At.v32, ctx->y32, ctx->ch32, ctx->x32,
-                                                ctx->xbar32, ctx->xsum32, ps.partial32, 0, tpb, (int)it);
+                                                ctx->xbar32, ctx->xsum32, ps.partial32, 0, tpb, (int)it, nullptr,
+                                                ctx->lo32);
         if (rs != PDHG_OK) return rs;
       } else {
         launch_primal_step_halpern<float>(ctx->At, ctx->At.v32, ctx->y32, ctx->ch32, ctx->x32, ctx->xbar32,
-                                          ctx->xsum32, ctx->st, (int)it, grT, s, tpb);
+                                          ctx->xsum32, ctx->st, (int)it, grT, s, tpb, nullptr, 0, nullptr,
+                                          ctx->lo32);
       }
     } else {
       pdhg_status rs = ctx->phase32 ? primal_step(ctx, true, ctx->y32, ctx->x32, ctx->xbar32, ctx->xsum32,
@@ -1434,8 +1574,7 @@ pdhg_status enqueue_eval(pdhg_ctx* ctx) {
   }
   if (o.restarts && !o.halpern) {  // Halpern: no averages
     if (p32)
-      launch_make_average32(ctx->xsum32, ctx->ysum32, ctx->x32, ctx->y32, ctx->xavg, ctx->yavg, n, m, ctx->st, gv,
-                            s);
+      average32(ctx);
     else
       launch_make_average(ctx->xsum, ctx->ysum, ctx->x, ctx->y, ctx->xavg, ctx->yavg, n, m, ctx->st, gv, s);
     eval_point(ctx, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, &ctx->st->avg);
@@ -1445,7 +1584,14 @@ pdhg_status enqueue_eval(pdhg_ctx* ctx) {
   else
     eval_point(ctx, ctx->x, ctx->y, ctx->xr, ctx->yr, &ctx->st->cur);
   launch_decide(ctx->st, ctx->trace, s);
-  if (p32)
+  if (p32 && ctx->refine) {
+    // a restart moves the FP64 reference and re-centres the FP32 iteration
+    launch_apply32_delta(ctx->st, ctx->x32, ctx->y32, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr,
+                         ctx->xsum32, ctx->ysum32, n, m, gv, s);
+    launch_recenter(ctx->A, ctx->At, ctx->xr, ctx->yr, ctx->bh, ctx->ch, ctx->bh32, ctx->ch32, ctx->lo32, ctx->st, 0,
+                    stride_grid(ctx, ctx->A), stride_grid(ctx, ctx->At), s);
+    ctx->launches += 2;
+  } else if (p32)
     launch_apply32(ctx->st, ctx->x32, ctx->y32, ctx->x, ctx->y, ctx->xavg, ctx->yavg, ctx->xr, ctx->yr, ctx->xsum32,
                    ctx->ysum32, n, m, gv, s);
   else
@@ -2169,7 +2315,7 @@ void pdhg_default_options(pdhg_options* o) {
   o->inputs_on_device = 0;
   o->use_graphs = 1;
   o->kernel_timing = 0;
-  o->polish_switch = 1e-5;
+  o->polish_switch = -1.0;
   o->long_row_min = 128;
   o->rows_per_thread = 4;
   o->dual_hot_cols = 0;
@@ -2191,6 +2337,10 @@ void pdhg_default_options(pdhg_options* o) {
   o->gap_tol = 0.0;
   o->feas_polish = 0;
   o->polish_div = 8;
+  o->stream_steps = 0;
+  o->stream_warps = 0;
+  o->stream_depth = 3;
+  o->refine32 = -1;
 }
 
 pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
@@ -2263,6 +2413,17 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
       (o.values32 == 1 && (o.precision == PDHG_FP32 || o.persistent || o.record_for_backward)))
     return fail(nullptr, PDHG_ERR_INVALID,
                 "values32 must be -1, 0 or 1 (1: precision FP64 or MIXED, no persistent loop, no recording)");
+  if (o.stream_steps < 0 || o.stream_steps > 1 || o.stream_warps < 0 || o.stream_warps > STREAM_TPB_MAX / 32 ||
+      o.stream_depth < 2 || o.stream_depth > 8 || (o.stream_steps && (o.persistent || o.dual_hot_cols)))
+    return fail(nullptr, PDHG_ERR_INVALID,
+                "stream_steps must be 0 or 1 (1: no persistent loop or hot columns), stream_warps in [0, 16] and "
+                "stream_depth in [2, 8]");
+  if (o.refine32 < -1 || o.refine32 > 1 ||
+      (o.refine32 == 1 && (o.precision == PDHG_FP64 || o.record_for_backward || o.persistent)))
+    return fail(nullptr, PDHG_ERR_INVALID,
+                "refine32 must be -1, 0 or 1 (1: precision FP32 or MIXED, no recording or persistent loop)");
+  if (!(o.polish_switch >= 0.0 || o.polish_switch == -1.0))
+    return fail(nullptr, PDHG_ERR_INVALID, "polish_switch must be >= 0 or -1 (automatic)");
 
   // Checks of host inputs (CSR structure, finite data) on host threads, beside
   // the context's set-up: stream creation, allocations and the upload depend
@@ -2438,6 +2599,10 @@ static pdhg_status iterate_impl(pdhg_ctx* ctx, int64_t max_iters, double tol, in
     }
     if (eval_now) {
       CK(ctx, cudaStreamSynchronize(s));  // the state copy of the evaluation has landed
+      if (ctx->h_st->wait_err) {
+        if (iters_done) *iters_done = done;
+        return fail(ctx, PDHG_ERR_TIMEOUT, "a bounded wait of a streamed step kernel ran out");
+      }
       if (ctx->h_st->numeric) {
         if (iters_done) *iters_done = done;
         return fail(ctx, PDHG_ERR_NUMERIC, "NaN or Inf in the iterates");
@@ -2474,9 +2639,10 @@ static pdhg_status iterate_impl(pdhg_ctx* ctx, int64_t max_iters, double tol, in
           ctx->best32 = r;
           ctx->best32_k = ctx->k;
         }
-        stalled = ctx->k - ctx->best32_k >= STALL_ITERS;
+        stalled = ctx->k - ctx->best32_k >= (ctx->refine ? STALL_ITERS_REFINED : STALL_ITERS);
       }
-      if (ctx->phase32 && o.precision == PDHG_MIXED && (ctx->h_st->cand_rel_kkt <= o.polish_switch || stalled)) {
+      const double pswitch = o.polish_switch >= 0.0 ? o.polish_switch : (ctx->refine ? 0.0 : 1e-5);
+      if (ctx->phase32 && o.precision == PDHG_MIXED && (ctx->h_st->cand_rel_kkt <= pswitch || stalled)) {
         // FP64 polishing phase: continue in FP64 from the FP32 iterate (held
         // exactly in x, y), keeping D_r, D_c, eta and omega.
         if (!o.halpern) {
@@ -2484,8 +2650,13 @@ static pdhg_status iterate_impl(pdhg_ctx* ctx, int64_t max_iters, double tol, in
           // restart reference (xr, yr, its norms) and the count since the
           // last restart stay, and the running sums carry over from FP32 -
           // so the switch is no restart (one would drop the average)
-          launch_widen(ctx->xsum, ctx->xsum32, n, vec_grid(ctx, n), s);
-          launch_widen(ctx->ysum, ctx->ysum32, m, vec_grid(ctx, m), s);
+          if (ctx->refine) {  // sums of corrections: t terms of the reference each
+            launch_widen_sum_delta(ctx->xsum, ctx->xr, ctx->xsum32, n, ctx->st, vec_grid(ctx, n), s);
+            launch_widen_sum_delta(ctx->ysum, ctx->yr, ctx->ysum32, m, ctx->st, vec_grid(ctx, m), s);
+          } else {
+            launch_widen(ctx->xsum, ctx->xsum32, n, vec_grid(ctx, n), s);
+            launch_widen(ctx->ysum, ctx->ysum32, m, vec_grid(ctx, m), s);
+          }
           ctx->launches += 2;
         } else {
           // reflected Halpern forms: the iterate becomes the anchor and the
@@ -2503,6 +2674,15 @@ static pdhg_status iterate_impl(pdhg_ctx* ctx, int64_t max_iters, double tol, in
         ctx->phase32 = false;
         ctx->promoted_at = ctx->k;
       }
+    }
+  }
+  if (ctx->stream_on) {  // a bounded wait that ran out after the last evaluation
+    unsigned werr = 0;
+    CK(ctx, cudaMemcpyAsync(&werr, &ctx->st->wait_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(ctx, cudaStreamSynchronize(s));
+    if (werr) {
+      if (iters_done) *iters_done = done;
+      return fail(ctx, PDHG_ERR_TIMEOUT, "a bounded wait of a streamed step kernel ran out");
     }
   }
   CK(ctx, cudaStreamSynchronize(s));
@@ -2663,6 +2843,8 @@ pdhg_status pdhg_get_info(pdhg_ctx* ctx, pdhg_info* out) {
   out->persistent_grid = ctx->bgrid;
   out->graph_launches = ctx->graph_replays;
   out->values32 = ctx->vals_u ? 1 : 0;
+  out->stream_steps = ctx->stream_on ? 1 : 0;
+  out->refine32 = ctx->refine ? 1 : 0;
   return PDHG_OK;
 }
 
@@ -2746,10 +2928,11 @@ pdhg_status pdhg_create_batch(int count, const pdhg_lp_desc* lps, const pdhg_opt
   if (o.persistent < 0 || o.persistent > 2 || (o.persistent && o.kernel_timing) || o.barrier_cycles < 0)
     return fail(nullptr, PDHG_ERR_INVALID,
                 "persistent must be 0, 1 or 2 and excludes kernel timing; barrier_cycles must be >= 0");
-  if (o.feas_polish || !(o.gap_tol >= 0.0) || o.restart_scheme != 0 || o.values32 == 1 || o.values32 < -1)
+  if (o.feas_polish || !(o.gap_tol >= 0.0) || o.restart_scheme != 0 || o.values32 == 1 || o.values32 < -1 ||
+      o.stream_steps || o.refine32 == 1)
     return fail(nullptr, PDHG_ERR_INVALID,
-                "batch: no feasibility polishing, fixed-point restart scheme or values32 (single LPs only), "
-                "gap_tol >= 0");
+                "batch: no feasibility polishing, fixed-point restart scheme, values32 or stream_steps (single LPs "
+                "only), gap_tol >= 0");
   int64_t mt = 0, nt = 0, zt = 0;
   for (int i = 0; i < count; ++i) {
     const pdhg_lp_desc& L = lps[i];

@@ -70,6 +70,10 @@ class pdhg_options(C.Structure):
         ("pid_kp", C.c_double),
         ("pid_ki", C.c_double),
         ("pid_kd", C.c_double),
+        ("stream_steps", C.c_int),
+        ("stream_warps", C.c_int),
+        ("stream_depth", C.c_int),
+        ("refine32", C.c_int),
     ]
 
 
@@ -90,6 +94,7 @@ class pdhg_info(C.Structure):
         ("polish_started_at", C.c_int64),
         ("feas_polish_attempts", C.c_int64), ("feas_polish_iterations", C.c_int64), ("feas_polished", C.c_int),
         ("persistent_grid", C.c_int), ("graph_launches", C.c_int64), ("values32", C.c_int),
+        ("stream_steps", C.c_int), ("refine32", C.c_int),
     ]
 
 

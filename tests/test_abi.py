@@ -66,10 +66,11 @@ def test_default_options(lib):
     assert (o.step_factor, o.beta_suff, o.beta_nec, o.beta_art, o.theta) == (0.9, 0.2, 0.8, 0.36, 0.5)
     assert o.precision == P.PDHG_FP64 and o.restarts == 1 and o.primal_weight == 1
     assert (o.halpern, o.halpern_reflect, o.primal_panels, o.long_row_min) == (0, 1.0, -1, 128)
-    assert (o.feas_polish, o.polish_div, o.gap_tol, o.polish_switch) == (0, 8, 0.0, 1e-5)
+    assert (o.feas_polish, o.polish_div, o.gap_tol, o.polish_switch) == (0, 8, 0.0, -1.0)
     assert (o.dual_hot_cols, o.singleton_order, o.barrier_cycles) == (0, 1, 0)
     assert (o.panel_min_len, o.restart_scheme, o.values32) == (0, 0, -1)
     assert (o.pid_kp, o.pid_ki, o.pid_kd) == (0.99, 0.01, 0.0)
+    assert (o.stream_steps, o.stream_warps, o.stream_depth, o.refine32) == (0, 0, 3, -1)
     with pytest.raises(KeyError):
         P.pdhg_default_options(no_such_option=1)
 

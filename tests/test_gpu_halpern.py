@@ -107,7 +107,9 @@ def test_fp32_panels_match_direct_fp32(tiny_lp):
 @pytest.mark.parametrize("panels", [0, 1])
 def test_mixed_reaches_tolerance_and_optimum(tiny_lp, panels):
     lp = tiny_lp
-    with P.Solver.from_lp(lp, precision=P.PDHG_MIXED, halpern=1, primal_panels=panels, panel_rows=48) as sol:
+    # an explicit switch: the refined FP32 phase (the default) to 1e-5, then FP64
+    with P.Solver.from_lp(lp, precision=P.PDHG_MIXED, halpern=1, primal_panels=panels, panel_rows=48,
+                          polish_switch=1e-5) as sol:
         st, done = sol.iterate(200000, 1e-8)
         info = sol.info()
         k = sol.kkt()

@@ -242,14 +242,16 @@ def test_mixed_fp32_phase_uses_the_fp32_layout():
     lp = lpgen.generate(3000, 9000, 2, nnz_per_col=None, zipf=(1.5, 10000, 90000), val_range=(0.1, 10.0),
                         support=0.3, fp32_values=True)
     eng = dict(primal_panels=1, long_row_min=64)
+    # the mixed form's FP32 phase runs on corrections to its restart point
+    # (refine32, its default); the FP32 context is asked for the same
     with P.Solver.from_lp(lp, precision=P.PDHG_MIXED, polish_switch=1e-30, **eng) as mx, \
-            P.Solver.from_lp(lp, precision=P.PDHG_FP32, **eng) as f32:
+            P.Solver.from_lp(lp, precision=P.PDHG_FP32, refine32=1, **eng) as f32:
         mx.iterate(640)
         f32.iterate(640)
         assert mx.info()["precision_now"] == P.PDHG_FP32
         for a, b in zip(mx.solution(), f32.solution()):
             np.testing.assert_array_equal(a, b)
-    with P.Solver.from_lp(lp, precision=P.PDHG_MIXED, **eng) as mx:
+    with P.Solver.from_lp(lp, precision=P.PDHG_MIXED, polish_switch=1e-5, **eng) as mx:
         st, _ = mx.iterate(100_000, 1e-8)
         assert st == P.PDHG_OK and mx.info()["polish_started_at"] > 0
         assert mx.kkt()["primal_obj"] == pytest.approx(lp.f_star, rel=1e-7)
