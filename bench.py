@@ -43,6 +43,8 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--small", action="store_true", help="a 1/10-size LP (m=1e5, n=3e5, nnz~3e6) for profiling")
+    p.add_argument("--medium", action="store_true",
+                   help="a 3/10-size LP (m=3e5, n=9e5, nnz~9e6; its matrices exceed the L2) for ncu section captures")
     p.add_argument("--skip-extras", action="store_true", help="skip e2e, time-to-tolerance and the CPU baseline")
     p.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
                    help="arithmetic of the timed iterations (fp32: the FP32 engine, for profiling it)")
@@ -64,6 +66,8 @@ def make_lp(args):
 
     if args.small:
         return lpgen.large_lp(args.seed, m=100_000, n=300_000, nnz=3_000_000), "zipf-lp m=1e5 n=3e5 nnz~3e6 FP64"
+    if args.medium:
+        return lpgen.large_lp(args.seed, m=300_000, n=900_000, nnz=9_000_000), "zipf-lp m=3e5 n=9e5 nnz~9e6 FP64"
     return lpgen.large_lp(args.seed), "zipf-lp m=1e6 n=3e6 nnz~3e7 FP64"
 
 

@@ -189,6 +189,11 @@ typedef struct {
                              which shrink as the solve converges, rather than with the iterate. Single LPs,
                              no recording or persistent loop. 0 = off; -1 = on for PDHG_MIXED, off for
                              PDHG_FP32 (-1) */
+  int panel_overlap;      /* panel-tiled primal step: 1 = the short-column step is a programmatic dependent
+                             launch of the panel pass, so its blocks start on SMs as the panel pass's blocks
+                             finish; only its per-column combine of the panels' partial sums waits for the
+                             whole pass (same results); 0 = the two launches in sequence; -1 = 1 for FP32
+                             steps, 0 for FP64 steps (where it measured slower) (-1) */
 } pdhg_options;
 
 /* Scalars of one point on the problem as given (unscaled), all FP64.

@@ -134,6 +134,7 @@ struct Hyb {
   double* v = nullptr;        // [slots] value
   float* v32 = nullptr;       // [slots] value rounded to FP32 (FP32 / mixed precision only)
   float* u32 = nullptr;       // [slots] unscaled value, exactly (option values32 only)
+  unsigned short* ci16 = nullptr;  // [slots] the column indices in 16 bits (panel layout: rows within a panel)
   unsigned* check = nullptr;  // checked build (PDHG_CHECKED): the context's error word
   int units() const { return n_units; }
 };

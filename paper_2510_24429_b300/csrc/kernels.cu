@@ -88,6 +88,31 @@ __device__ __forceinline__ float2 ld_stream2(const float* p, unsigned long long 
       : "l"(p), "l"(pol));
   return r;
 }
+
+// How the row kernels read a layout's column indices: 32-bit (every layout),
+// or 16-bit (the panel layout's indices relative to a panel of at most 65536
+// rows, half the index bytes). pair(k) reads entries k, k+1 (k even) with one
+// load; one(k) reads entry k.
+struct IdxI32 {
+  const int* __restrict__ p;
+  __device__ __forceinline__ int2 pair(long long k, unsigned long long pol) const { return ld_stream2(p + k, pol); }
+  __device__ __forceinline__ int one(long long k, unsigned long long pol) const { return ld_stream(p + k, pol); }
+};
+struct IdxU16 {
+  const unsigned short* __restrict__ p;
+  __device__ __forceinline__ int2 pair(long long k, unsigned long long pol) const {
+    unsigned v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;"
+        : "=r"(v)
+        : "l"(p + k), "l"(pol));
+    return make_int2((int)(v & 0xffffu), (int)(v >> 16));  // entry k in the low half
+  }
+  __device__ __forceinline__ int one(long long k, unsigned long long pol) const {
+    unsigned short v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p + k), "l"(pol));
+    return (int)v;
+  }
+};
 // Scalar visitor (setup kernels): every warp takes units in a grid-stride
 // loop; op.entry(acc, k, r) sees every slot k of row r (padding included:
 // value 0, column 0), op.finish(r, acc) the combined result (max or sum).
@@ -160,8 +185,8 @@ struct GlobalGather {
 template <class G>
 using GatherT = typename std::decay<decltype(std::declval<const G&>()(0))>::type;
 
-template <int R, class V, class Op, class G>
-__device__ __forceinline__ void slice_dot(const Hyb& H, const V* __restrict__ vals, int row0, int nvalid,
+template <int R, class V, class Op, class G, class IX>
+__device__ __forceinline__ void slice_dot(const IX& ix, const V* __restrict__ vals, int row0, int nvalid,
                                           long long base, int Lp, const G& gather, Op& op, unsigned long long pol,
                                           int lane) {
   using T = GatherT<G>;
@@ -177,7 +202,7 @@ __device__ __forceinline__ void slice_dot(const Hyb& H, const V* __restrict__ va
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const long long k = base + 32 * q + lane;
-      const int c = ld_stream(H.ci + k, pol);
+      const int c = ix.one(k, pol);
       acc[q] += as_acc<T>(ld_stream(vals + k, pol)) * gather(c);
     }
   } else {
@@ -187,7 +212,7 @@ __device__ __forceinline__ void slice_dot(const Hyb& H, const V* __restrict__ va
     for (int e2 = 0; e2 < L2; ++e2) {
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        const int2 c = ld_stream2(H.ci + k + 64 * q, pol);
+        const int2 c = ix.pair(k + 64 * q, pol);
         const typename Pair<V>::type a = ld_stream2(vals + k + 64 * q, pol);
         const T g0 = gather(c.x), g1 = gather(c.y);
         acc[q] += as_acc<T>(a.x) * g0;
@@ -221,9 +246,9 @@ struct CheckedGather {
 
 // One unit of H (a long row, or a slice of 32*R rows) for the dot-product
 // visitor below.
-template <class V, class Op, class G>
-__device__ __forceinline__ void unit_dot(const Hyb& H, const V* __restrict__ vals, int u, const G& gather_in, Op& op,
-                                         unsigned long long pol, int lane) {
+template <class V, class Op, class G, class IX>
+__device__ __forceinline__ void unit_dot_ix(const Hyb& H, const IX& ix, const V* __restrict__ vals, int u,
+                                            const G& gather_in, Op& op, unsigned long long pol, int lane) {
   using T = GatherT<G>;
 #ifdef PDHG_CHECKED
   if (!unit_ok(H, u)) return;
@@ -243,10 +268,10 @@ __device__ __forceinline__ void unit_dot(const Hyb& H, const V* __restrict__ val
     // warp reads whole sectors (256 B of indices, 512 B of values)
 #pragma unroll 2
     for (long long k = beg + 2 * lane; k < end; k += 128) {
-      const int2 c0 = ld_stream2(H.ci + k, pol);
+      const int2 c0 = ix.pair(k, pol);
       const typename Pair<V>::type a = ld_stream2(vals + k, pol);
       const bool second = k + 64 < end;
-      const int2 c1 = second ? ld_stream2(H.ci + k + 64, pol) : make_int2(0, 0);
+      const int2 c1 = second ? ix.pair(k + 64, pol) : make_int2(0, 0);
       typename Pair<V>::type b;
       b.x = V(0);
       b.y = V(0);
@@ -263,12 +288,19 @@ __device__ __forceinline__ void unit_dot(const Hyb& H, const V* __restrict__ val
   } else {
     const int Lp = (int)((end - beg) / (32 * info.y));
     if (info.y == 4)
-      slice_dot<4>(H, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
+      slice_dot<4>(ix, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
     else if (info.y == 2)
-      slice_dot<2>(H, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
+      slice_dot<2>(ix, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
     else
-      slice_dot<1>(H, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
+      slice_dot<1>(ix, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
   }
+}
+
+// unit u with the layout's 32-bit column indices
+template <class V, class Op, class G>
+__device__ __forceinline__ void unit_dot(const Hyb& H, const V* __restrict__ vals, int u, const G& gather, Op& op,
+                                         unsigned long long pol, int lane) {
+  unit_dot_ix(H, IdxI32{H.ci}, vals, u, gather, op, pol, lane);
 }
 
 // every unit of H from unit u_begin on, one warp per unit in a grid-stride loop
@@ -566,13 +598,16 @@ struct PartialOp {
 };
 
 // FP32 panels take half the shared memory, so two blocks could share an SM
-template <class T, class V = T>
+template <class T, class V = T, bool I16 = false>
 __global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
     k_primal_panels(Hyb Pn, const V* __restrict__ vals, const T* __restrict__ y, int m, int H,
                     const int4* __restrict__ binfo, const int* __restrict__ ustart, const int* __restrict__ segout,
                     T* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char panel_smem[];
   T* ys = reinterpret_cast<T*>(panel_smem);
+  // the short-column step launched after this pass may start on SMs as their
+  // panel blocks finish (programmatic dependent launch; see short_and_combine)
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   // panels get blocks in proportion to their stored entries (the first panels,
   // holding the longest rows of A, have the most)
   const int4 bi = binfo[blockIdx.x];
@@ -599,7 +634,10 @@ __global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
   PartialOp<T> op{partial, segout};
   const int u1 = ustart[p + 1];
   for (int u = ustart[p] + sub * nw + (threadIdx.x >> 5); u < u1; u += kpp * nw)
-    unit_dot(Pn, vals, u, SmemGather<T>{ys}, op, pol, lane);
+    if (I16)
+      unit_dot_ix(Pn, IdxU16{Pn.ci16}, vals, u, SmemGather<T>{ys}, op, pol, lane);
+    else
+      unit_dot(Pn, vals, u, SmemGather<T>{ys}, op, pol, lane);
 }
 
 // ---- reflected Halpern form of the two half-steps (option halpern) ----------
@@ -609,7 +647,7 @@ __global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
 // since the last restart, before this step) and the last restart point
 // (xr, yr) as anchor: x <- w ((1 + rho) x~ - rho x) + (1 - w) xr, likewise y;
 // the dual step still gathers xbar = 2 x~ - x.
-template <class T, bool SC = false>
+template <class T, bool SC = false, bool R1 = false>
 struct PrimalHalpernOp {
   using State = NoState;
   const T* __restrict__ ch;
@@ -626,11 +664,11 @@ struct PrimalHalpernOp {
     const T xt = project(lo, j, xj - tau * (__ldcs(ch + j) - dc.apply(d, g)));
     const T xb = T(2) * xt - xj;
     xbar[j] = dc.apply(d, xb);
-    __stcs(x + j, halpern_mix(xt, xj, xb, __ldcs(xr + j), w, T(1) - w, rho));
+    __stcs(x + j, halpern_mix_r<R1>(xt, xj, xb, __ldcs(xr + j), w, T(1) - w, rho));
   }
 };
 
-template <class T, bool SC = false>
+template <class T, bool SC = false, bool R1 = false>
 struct DualHalpernOp {
   using State = NoState;
   const T* __restrict__ bh;
@@ -644,7 +682,7 @@ struct DualHalpernOp {
     const T d = dr.load(i);
     const T yi = y[i];
     const T yt = yi + sigma * (__ldcs(bh + i) - dr.apply(d, h));
-    const T yn = halpern_mix(yt, yi, T(2) * yt - yi, __ldcs(yr + i), w, T(1) - w, rho);
+    const T yn = halpern_mix_r<R1>(yt, yi, T(2) * yt - yi, __ldcs(yr + i), w, T(1) - w, rho);
     y[i] = yn;
     if (SC) yg[i] = d * yn;
   }
@@ -661,9 +699,20 @@ struct DualHalpernOp {
 template <class T, class V, class Op>
 __device__ __forceinline__ void short_and_combine(const Hyb& At, const V* __restrict__ vals, const T* __restrict__ y,
                                                   Op& op, int u_begin, int cblocks, int panels,
-                                                  const T* __restrict__ partial, int ncols) {
-  if ((int)blockIdx.x < cblocks) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ncols; j += cblocks * blockDim.x) {
+                                                  const T* __restrict__ partial, int ncols, int cfirst) {
+  // blocks [cfirst, cfirst + cblocks) combine the long columns, the others
+  // step the short columns; cfirst is about one wave of blocks, so that the
+  // combine (latency bound) overlaps short-column work and, when this launch
+  // overlaps the panel pass (programmatic dependent launch), is scheduled
+  // once the panel pass has (nearly) finished
+  const int sblocks = (int)gridDim.x - cblocks;
+  const int bx = (int)blockIdx.x;
+  if (bx >= cfirst && bx < cfirst + cblocks) {
+    // the partial sums of the panel pass: wait for it (returns at once when
+    // the launch is not a programmatic dependent one)
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    const int cb = bx - cfirst;
+    for (int j = cb * blockDim.x + threadIdx.x; j < ncols; j += cblocks * blockDim.x) {
       const typename Op::State sj = op.begin(j);
       const T* pj = partial + j;
       T g = T(0);
@@ -680,10 +729,14 @@ __device__ __forceinline__ void short_and_combine(const Hyb& At, const V* __rest
     }
     return;
   }
+  // the short columns: they read y (the dual step's, complete before the
+  // panel pass began) and write only their own columns, so they may run
+  // beside the panel pass's last blocks
   const unsigned long long pol = stream_policy();
   const int lane = threadIdx.x & 31;
-  const int gwarp = (int)(((blockIdx.x - cblocks) * (unsigned)blockDim.x + threadIdx.x) >> 5);
-  const int nwarps = (int)(((gridDim.x - cblocks) * (unsigned)blockDim.x) >> 5);
+  const int sb = bx < cfirst ? bx : bx - cblocks;  // index among the short-column blocks
+  const int gwarp = (int)((sb * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((sblocks * (unsigned)blockDim.x) >> 5);
   for (int u = u_begin + gwarp; u < At.n_units; u += nwarps) unit_dot(At, vals, u, GlobalGather<T>{y}, op, pol, lane);
 }
 
@@ -692,10 +745,10 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STE
     k_primal_short_combine(Hyb At, const V* __restrict__ vals, const T* __restrict__ y, const T* __restrict__ ch,
                            T* __restrict__ x, T* __restrict__ xbar, T* __restrict__ xsum,
                            const DevState* __restrict__ st, int accumulate, int u_begin, int cblocks, int panels,
-                           const T* __restrict__ partial, int ncols, const T* __restrict__ dsc,
+                           const T* __restrict__ partial, int ncols, int cfirst, const T* __restrict__ dsc,
                            const T* __restrict__ lo) {
   PrimalOp<T, !std::is_same<T, V>::value> op{ch, x, xbar, xsum, (T)st->tau, accumulate, {dsc}, lo};
-  short_and_combine(At, vals, y, op, u_begin, cblocks, panels, partial, ncols);
+  short_and_combine(At, vals, y, op, u_begin, cblocks, panels, partial, ncols, cfirst);
 }
 
 template <class T, class V = T>
@@ -706,9 +759,15 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STE
                           const T* __restrict__ dsc, const T* __restrict__ lo) {
   const DevState* st = block_state(sts, binst);
   if (st->frozen) return;
-  PrimalHalpernOp<T, !std::is_same<T, V>::value> op{ch,  x, xbar, xr, (T)st->tau, (T)block_halpern_weight(st, it),
-                                                    (T)st->rho, {dsc}, lo};
-  hyb_dot(At, vals, GlobalGather<T>{y}, op, u_begin);
+  constexpr bool SC = !std::is_same<T, V>::value;
+  const T w = (T)block_halpern_weight(st, it), rho = (T)st->rho;
+  if (rho == T(1)) {  // the reflection of the default form, known to every entry's update
+    PrimalHalpernOp<T, SC, true> op{ch, x, xbar, xr, (T)st->tau, w, rho, {dsc}, lo};
+    hyb_dot(At, vals, GlobalGather<T>{y}, op, u_begin);
+  } else {
+    PrimalHalpernOp<T, SC, false> op{ch, x, xbar, xr, (T)st->tau, w, rho, {dsc}, lo};
+    hyb_dot(At, vals, GlobalGather<T>{y}, op, u_begin);
+  }
 }
 
 template <class T, class V = T>
@@ -716,11 +775,17 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STE
     k_primal_short_combine_halpern(Hyb At, const V* __restrict__ vals, const T* __restrict__ y,
                                    const T* __restrict__ ch, T* __restrict__ x, T* __restrict__ xbar,
                                    const T* __restrict__ xr, const DevState* __restrict__ st, int it, int u_begin,
-                                   int cblocks, int panels, const T* __restrict__ partial, int ncols,
+                                   int cblocks, int panels, const T* __restrict__ partial, int ncols, int cfirst,
                                    const T* __restrict__ dsc, const T* __restrict__ lo) {
-  PrimalHalpernOp<T, !std::is_same<T, V>::value> op{ch,  x, xbar, xr, (T)st->tau, (T)block_halpern_weight(st, it),
-                                                    (T)st->rho, {dsc}, lo};
-  short_and_combine(At, vals, y, op, u_begin, cblocks, panels, partial, ncols);
+  constexpr bool SC = !std::is_same<T, V>::value;
+  const T w = (T)block_halpern_weight(st, it), rho = (T)st->rho;
+  if (rho == T(1)) {
+    PrimalHalpernOp<T, SC, true> op{ch, x, xbar, xr, (T)st->tau, w, rho, {dsc}, lo};
+    short_and_combine(At, vals, y, op, u_begin, cblocks, panels, partial, ncols, cfirst);
+  } else {
+    PrimalHalpernOp<T, SC, false> op{ch, x, xbar, xr, (T)st->tau, w, rho, {dsc}, lo};
+    short_and_combine(At, vals, y, op, u_begin, cblocks, panels, partial, ncols, cfirst);
+  }
 }
 
 template <class T, class V = T>
@@ -730,9 +795,15 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, PDHG_STEP_MIN_BLOCKS * TPB / STE
                         const int* __restrict__ binst, int it, const T* __restrict__ dsc, T* __restrict__ yg) {
   const DevState* st = block_state(sts, binst);
   if (st->frozen) return;
-  DualHalpernOp<T, !std::is_same<T, V>::value> op{
-      bh, y, yr, (T)st->sigma, (T)block_halpern_weight(st, it), (T)st->rho, {dsc}, yg};
-  hyb_dot(A, vals, GlobalGather<T>{xbar}, op);
+  constexpr bool SC = !std::is_same<T, V>::value;
+  const T w = (T)block_halpern_weight(st, it), rho = (T)st->rho;
+  if (rho == T(1)) {
+    DualHalpernOp<T, SC, true> op{bh, y, yr, (T)st->sigma, w, rho, {dsc}, yg};
+    hyb_dot(A, vals, GlobalGather<T>{xbar}, op);
+  } else {
+    DualHalpernOp<T, SC, false> op{bh, y, yr, (T)st->sigma, w, rho, {dsc}, yg};
+    hyb_dot(A, vals, GlobalGather<T>{xbar}, op);
+  }
 }
 
 template <class T, bool SC = false>
@@ -814,8 +885,14 @@ __global__ void __launch_bounds__(HOT_TPB, 1)
                             const T* __restrict__ bh, T* __restrict__ y, const T* __restrict__ yr,
                             const DevState* __restrict__ st, int it) {
   const T* sh = stage_hot(xbar, hot);
-  DualHalpernOp<T> op{bh, y, yr, (T)st->sigma, (T)block_halpern_weight(st, it), (T)st->rho};
-  hyb_dot(A, vals, HotGatherT<T>{xbar, sh, hot}, op);
+  const T w = (T)block_halpern_weight(st, it), rho = (T)st->rho;
+  if (rho == T(1)) {  // as k_dual_step_halpern: the reflection known at compile time
+    DualHalpernOp<T, false, true> op{bh, y, yr, (T)st->sigma, w, rho};
+    hyb_dot(A, vals, HotGatherT<T>{xbar, sh, hot}, op);
+  } else {
+    DualHalpernOp<T, false, false> op{bh, y, yr, (T)st->sigma, w, rho};
+    hyb_dot(A, vals, HotGatherT<T>{xbar, sh, hot}, op);
+  }
 }
 
 __global__ void k_add_counters(DevState* st, long long dk) {
@@ -1232,6 +1309,11 @@ __global__ void k_fp32_inexact(const double* __restrict__ v, long long len, int*
     bad |= (double)(float)a != a || (a != 0.0 && fabs(a) < 1.1754943508222875e-38);  // FP32's smallest normal
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+__global__ void k_narrow_index(unsigned short* __restrict__ dst, const int* __restrict__ src, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (unsigned short)src[i];
 }
 
 __global__ void k_narrow(float* __restrict__ dst, const double* __restrict__ src, long long len) {
@@ -1676,7 +1758,11 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, 2) k_batch_solve(BatchArgs a) {
       for (int vb = blockIdx.x; vb < nvb; vb += G) {
         const DevState* st = a.sts + a.binst[vb];
         if (st->frozen) continue;
-        if (a.halpern) {
+        if (a.halpern && st->rho == 1.0) {  // as the multi-launch kernels: reflection 1 at compile time
+          PrimalHalpernOp<double, false, true> op{a.ch, a.x, a.xbar, a.xr, st->tau, halpern_weight(st, (int)it),
+                                                  st->rho};
+          hyb_dot(a.At, a.At.v, CoherentGather<double>{a.y}, op, 0, vb, nvb);
+        } else if (a.halpern) {
           PrimalHalpernOp<double> op{a.ch, a.x, a.xbar, a.xr, st->tau, halpern_weight(st, (int)it), st->rho};
           hyb_dot(a.At, a.At.v, CoherentGather<double>{a.y}, op, 0, vb, nvb);
         } else {
@@ -1689,7 +1775,10 @@ __global__ void __launch_bounds__(STEP_TPB_MAX, 2) k_batch_solve(BatchArgs a) {
       for (int vb = blockIdx.x; vb < nvb; vb += G) {
         const DevState* st = a.sts + a.binst[vb];
         if (st->frozen) continue;
-        if (a.halpern) {
+        if (a.halpern && st->rho == 1.0) {
+          DualHalpernOp<double, false, true> op{a.bh, a.y, a.yr, st->sigma, halpern_weight(st, (int)it), st->rho};
+          hyb_dot(a.A, a.A.v, CoherentGather<double>{a.xbar}, op, 0, vb, nvb);
+        } else if (a.halpern) {
           DualHalpernOp<double> op{a.bh, a.y, a.yr, st->sigma, halpern_weight(st, (int)it), st->rho};
           hyb_dot(a.A, a.A.v, CoherentGather<double>{a.xbar}, op, 0, vb, nvb);
         } else {
@@ -1892,21 +1981,28 @@ void launch_dual_step_u(const Hyb& A, const double* xbar, const double* bh, doub
   k_dual_step<double, float><<<grid, tpb, 0, s>>>(A, A.u32, xbar, bh, y, ysum, st, nullptr, accumulate, dr, yg);
 }
 cudaError_t configure_primal_panels() {
-  cudaError_t e = cudaFuncSetAttribute(k_primal_panels<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       PANEL_SMEM_MAX);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_primal_panels<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_MAX);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_primal_panels<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             PANEL_SMEM_MAX);
+  cudaError_t e = cudaSuccess;
+  auto allow = [&](const void* f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_MAX);
+  };
+  allow((const void*)k_primal_panels<double, double, false>);
+  allow((const void*)k_primal_panels<float, float, false>);
+  allow((const void*)k_primal_panels<double, float, false>);
+  allow((const void*)k_primal_panels<double, double, true>);
+  allow((const void*)k_primal_panels<float, float, true>);
+  allow((const void*)k_primal_panels<double, float, true>);
   return e;
 }
 template <class T, class V>
 void launch_panel_pass(const Hyb& Pn, const V* vals, const PanelLayout& L, const T* y, T* partial, cudaStream_t s) {
   if (L.ncols == 0) return;
   const size_t smem = sizeof(T) * (size_t)L.rows;
-  k_primal_panels<T, V><<<L.blocks, PANEL_TPB, smem, s>>>(Pn, vals, y, L.m, L.rows, L.binfo, L.ustart, L.segout,
-                                                           partial);
+  if (Pn.ci16)  // 16-bit panel-relative row indices
+    k_primal_panels<T, V, true><<<L.blocks, PANEL_TPB, smem, s>>>(Pn, vals, y, L.m, L.rows, L.binfo, L.ustart,
+                                                                  L.segout, partial);
+  else
+    k_primal_panels<T, V, false><<<L.blocks, PANEL_TPB, smem, s>>>(Pn, vals, y, L.m, L.rows, L.binfo, L.ustart,
+                                                                   L.segout, partial);
 }
 template void launch_panel_pass<double, double>(const Hyb&, const double*, const PanelLayout&, const double*, double*,
                                                 cudaStream_t);
@@ -1918,29 +2014,41 @@ template <class T, class V>
 void launch_primal_short_combine(const Hyb& At, const V* vals, const T* y, const T* ch, T* x, T* xbar, T* xsum,
                                  const DevState* st, int accumulate, int short_grid, const PanelLayout& L,
                                  const T* partial, int tpb, cudaStream_t s, int halpern_it, const T* dc,
-                                 const T* lo) {
+                                 const T* lo, int overlap, int wave_blocks) {
   const int cblocks = (L.ncols + tpb - 1) / tpb;
   const int grid = cblocks + short_grid;
+  const int cfirst = std::min(short_grid, wave_blocks);
+  // overlap (and a panel pass just launched): a programmatic dependent launch,
+  // whose short-column blocks start as the panel blocks finish
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)tpb);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = overlap && L.ncols > 0 ? 1 : 0;
   if (halpern_it >= 0)
-    k_primal_short_combine_halpern<T, V><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xsum, st, halpern_it,
-                                                                L.ulong, cblocks, L.panels, partial, L.ncols, dc,
-                                                                lo);
+    cudaLaunchKernelEx(&cfg, k_primal_short_combine_halpern<T, V>, At, vals, y, ch, x, xbar, (const T*)xsum,
+                       (const DevState*)st, halpern_it, L.ulong, cblocks, L.panels, partial, L.ncols, cfirst, dc, lo);
   else
-    k_primal_short_combine<T, V><<<grid, tpb, 0, s>>>(At, vals, y, ch, x, xbar, xsum, st, accumulate, L.ulong,
-                                                        cblocks, L.panels, partial, L.ncols, dc, lo);
+    cudaLaunchKernelEx(&cfg, k_primal_short_combine<T, V>, At, vals, y, ch, x, xbar, xsum, (const DevState*)st,
+                       accumulate, L.ulong, cblocks, L.panels, partial, L.ncols, cfirst, dc, lo);
 }
 template void launch_primal_short_combine<double, double>(const Hyb&, const double*, const double*, const double*,
                                                           double*, double*, double*, const DevState*, int, int,
                                                           const PanelLayout&, const double*, int, cudaStream_t, int,
-                                                          const double*, const double*);
+                                                          const double*, const double*, int, int);
 template void launch_primal_short_combine<float, float>(const Hyb&, const float*, const float*, const float*, float*,
                                                         float*, float*, const DevState*, int, int,
                                                         const PanelLayout&, const float*, int, cudaStream_t, int,
-                                                        const float*, const float*);
+                                                        const float*, const float*, int, int);
 template void launch_primal_short_combine<double, float>(const Hyb&, const float*, const double*, const double*,
                                                          double*, double*, double*, const DevState*, int, int,
                                                          const PanelLayout&, const double*, int, cudaStream_t, int,
-                                                         const double*, const double*);
+                                                         const double*, const double*, int, int);
 template <class T, class V>
 void launch_primal_step_halpern(const Hyb& At, const V* vals, const T* y, const T* ch, T* x, T* xbar, const T* xr,
                                 const DevState* st, int it, int grid, cudaStream_t s, int tpb, const int* binst,
@@ -2091,6 +2199,9 @@ void launch_apply32(const DevState* st, float* x32, float* y32, double* x, doubl
                     const double* ya, double* xr, double* yr, float* xs, float* ys, int n, int m, int grid,
                     cudaStream_t s) {
   k_apply32<<<grid, TPB, 0, s>>>(st, x32, y32, x, y, xa, ya, xr, yr, xs, ys, n, m);
+}
+void launch_narrow_index(unsigned short* dst, const int* src, long long len, int grid, cudaStream_t s) {
+  if (len > 0) k_narrow_index<<<grid, TPB, 0, s>>>(dst, src, len);
 }
 void launch_widen_delta(double* dst, const double* ref, const float* d, long long len, int grid, cudaStream_t s) {
   k_widen_delta<<<grid, TPB, 0, s>>>(dst, ref, d, len);

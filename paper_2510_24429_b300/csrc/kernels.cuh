@@ -8,6 +8,7 @@ namespace pdhg {
 constexpr int TPB = 256;  // threads per block of every row kernel
 constexpr int WARPS_PER_BLOCK = TPB / 32;
 constexpr int STEP_TPB_MAX = 512;  // largest block of the step and evaluation kernels (option step_block)
+constexpr int STEP_BLOCKS_PER_SM = 6;  // resident 256-thread step blocks per SM (the kernels' register cap)
 constexpr int HOT_TPB = 1024;              // threads per block of the persistent dual step
 constexpr int HOT_SMEM_MAX = 220 * 1024;   // shared memory it stages xbar[0, hot) in
 constexpr int HOT_MAX = HOT_SMEM_MAX / 4;  // most xbar entries it stages (FP32; half of it in FP64)
@@ -86,6 +87,8 @@ void launch_fp32_inexact(const double* v, long long len, int* flag, cudaStream_t
 // precision conversions and the FP32 counterparts of make_average / apply
 void launch_narrow(float* dst, const double* src, long long len, int grid, cudaStream_t s);
 void launch_widen(double* dst, const float* src, long long len, int grid, cudaStream_t s);
+// 16-bit copies of column indices below 65536 (the panel layout's panel-relative rows)
+void launch_narrow_index(unsigned short* dst, const int* src, long long len, int grid, cudaStream_t s);
 void launch_make_average32(const float* xs, const float* ys, const float* x, const float* y, double* xa, double* ya,
                            int n, int m, const DevState* st, int grid, cudaStream_t s);
 void launch_apply32(const DevState* st, float* x32, float* y32, double* x, double* y, const double* xa,
@@ -205,7 +208,8 @@ template <class T, class V = T>
 void launch_primal_short_combine(const Hyb& At, const V* vals, const T* y, const T* ch, T* x, T* xbar, T* xsum,
                                  const DevState* st, int accumulate, int short_grid, const PanelLayout& L,
                                  const T* partial, int tpb, cudaStream_t s, int halpern_it = -1,
-                                 const T* dc = nullptr, const T* lo = nullptr);
+                                 const T* dc = nullptr, const T* lo = nullptr, int overlap = 0,
+                                 int wave_blocks = 0);
 // the dual step, persistent (grid = number of SMs), with xbar[0, hot) staged
 // in shared memory (hot * sizeof(T) <= HOT_SMEM_MAX), values vals in
 // precision T; halpern_it >= 0: the reflected Halpern form of step

@@ -811,6 +811,12 @@ pdhg_status build_panels(pdhg_ctx* ctx, PanelSet& ps, Scratch& sc, const long lo
   CK(ctx, dalloc(ctx, &ps.pl.ustart, P + 1));
   CK(ctx, cudaMemcpyAsync(ps.pl.ustart, ust.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice, s));
   launch_fill_units_P(ps.Pn, slen, sp, seg_start, seg_panel, sval, rowid, iy, val, H, s);
+  // the panel pass reads the panel-relative row indices (< H <= 56320) in 16
+  // bits: 2 bytes less per entry of the long columns
+  if (H <= 65536 && ps.Pn.slots > 0) {
+    CK(ctx, dalloc(ctx, &ps.Pn.ci16, ps.Pn.slots));
+    launch_narrow_index(ps.Pn.ci16, ps.Pn.ci, ps.Pn.slots, vec_grid(ctx, ps.Pn.slots), s);
+  }
   // dense panel-major partial sums; the slots of absent segments stay 0
   const long long slots = std::max<long long>(1, (long long)P * N);
   CK(ctx, dalloc(ctx, &ps.partial, slots));
@@ -1352,7 +1358,9 @@ pdhg_status panel_half_step(pdhg_ctx* ctx, const PanelSet& ps, const V* vals, co
   cudaStream_t s = ctx->stream;
   launch_panel_pass<T, V>(ps.Pn, vals, ps.pl, y, partial, s);
   launch_primal_short_combine<T, V>(ctx->At, valsT, y, ch, x, xbar, xsum, ctx->st, accumulate, short_grid(ctx, ps),
-                                    ps.pl, partial, tpb, s, halpern_it, dc, lo);
+                                    ps.pl, partial, tpb, s, halpern_it, dc, lo,
+                                    ctx->opt.panel_overlap >= 0 ? ctx->opt.panel_overlap : (sizeof(T) == 4 ? 1 : 0),
+                                    ctx->sms * STEP_BLOCKS_PER_SM * TPB / tpb);
   CK(ctx, cudaGetLastError());
   ctx->launches += 1;  // two launches; the caller counts one primal step
   return PDHG_OK;
@@ -2341,6 +2349,7 @@ void pdhg_default_options(pdhg_options* o) {
   o->stream_warps = 0;
   o->stream_depth = 3;
   o->refine32 = -1;
+  o->panel_overlap = -1;
 }
 
 pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
@@ -2422,6 +2431,8 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
       (o.refine32 == 1 && (o.precision == PDHG_FP64 || o.record_for_backward || o.persistent)))
     return fail(nullptr, PDHG_ERR_INVALID,
                 "refine32 must be -1, 0 or 1 (1: precision FP32 or MIXED, no recording or persistent loop)");
+  if (o.panel_overlap < -1 || o.panel_overlap > 1)
+    return fail(nullptr, PDHG_ERR_INVALID, "panel_overlap must be -1, 0 or 1");
   if (!(o.polish_switch >= 0.0 || o.polish_switch == -1.0))
     return fail(nullptr, PDHG_ERR_INVALID, "polish_switch must be >= 0 or -1 (automatic)");
 

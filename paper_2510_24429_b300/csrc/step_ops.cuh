@@ -52,12 +52,13 @@ __device__ __forceinline__ double halpern_weight(const DevState* st, int it) {
 }
 
 // The Halpern combination w ((1 + rho) t - rho z) + (1 - w) r, written as
-// w (t + rho (t - z)) + (1 - w) r; for the default rho = 1 the reflection
-// t + (t - z) = 2t - z is the extrapolated point the step computes anyway, so
-// the update costs one multiply and one multiply-add more
-template <class T>
-__device__ __forceinline__ T halpern_mix(T t, T z, T refl, T r, T w, T omw, T rho) {
-  const T u = rho == T(1) ? refl : t + rho * (t - z);
+// w (t + rho (t - z)) + (1 - w) r; for the default rho = 1 (R1, chosen once per
+// kernel, so that no entry computes both forms) the reflection t + (t - z) =
+// 2t - z is the extrapolated point the step computes anyway, and the update
+// costs one multiply and one multiply-add more
+template <bool R1, class T>
+__device__ __forceinline__ T halpern_mix_r(T t, T z, T refl, T r, T w, T omw, T rho) {
+  const T u = R1 ? refl : t + rho * (t - z);
   return w * u + omw * r;
 }
 

@@ -137,7 +137,7 @@ struct SPrimalOp {
 };
 
 // PrimalHalpernOp: staged x, chat, anchor x_r, D_c (SC) or the bounds (lo)
-template <class T, bool SC>
+template <class T, bool SC, bool R1>
 struct SPrimalHalpernOp {
   T* __restrict__ x;
   T* __restrict__ xbar;
@@ -149,7 +149,7 @@ struct SPrimalHalpernOp {
     const T xt = sproject(use_lo, p + 3 * CAP, j, xj - tau * (p[CAP + j] - (SC ? d * g : g)));
     const T xb = T(2) * xt - xj;
     xbar[j] = SC ? d * xb : xb;
-    __stcs(x + j, halpern_mix(xt, xj, xb, p[2 * CAP + j], w, T(1) - w, rho));
+    __stcs(x + j, halpern_mix_r<R1>(xt, xj, xb, p[2 * CAP + j], w, T(1) - w, rho));
   }
 };
 
@@ -171,7 +171,7 @@ struct SDualOp {
 };
 
 // DualHalpernOp: staged y, bhat, anchor y_r, D_r (SC)
-template <class T, bool SC>
+template <class T, bool SC, bool R1>
 struct SDualHalpernOp {
   T* __restrict__ y;
   T* __restrict__ yg;
@@ -180,7 +180,7 @@ struct SDualHalpernOp {
     const T d = SC ? p[3 * CAP + i] : T(1);
     const T yi = p[i];
     const T yt = yi + sigma * (p[CAP + i] - (SC ? d * h : h));
-    const T yn = halpern_mix(yt, yi, T(2) * yt - yi, p[2 * CAP + i], w, T(1) - w, rho);
+    const T yn = halpern_mix_r<R1>(yt, yi, T(2) * yt - yi, p[2 * CAP + i], w, T(1) - w, rho);
     y[i] = yn;
     if (SC) yg[i] = d * yn;
   }
@@ -511,9 +511,16 @@ __global__ void __launch_bounds__(STREAM_TPB_MAX, 1)
                   const T* __restrict__ dr, T* __restrict__ yg, int depth, unsigned slot_bytes) {
   constexpr bool SC = !std::is_same<T, V>::value;
   if (HALP) {
-    const T w = (T)stream_halpern_weight(st, it);
-    SDualHalpernOp<T, SC> op{y, yg, (T)st->sigma, w, (T)st->rho};
-    stream_body<T, V>(A, vals, xbar, op, y, bh, ysum_or_yr, SC ? dr : nullptr, 0, 0, 0, 0, nullptr, depth, slot_bytes, st);
+    const T w = (T)stream_halpern_weight(st, it), rho = (T)st->rho;
+    if (rho == T(1)) {  // the reflection known at compile time, as in the direct kernels
+      SDualHalpernOp<T, SC, true> op{y, yg, (T)st->sigma, w, rho};
+      stream_body<T, V>(A, vals, xbar, op, y, bh, ysum_or_yr, SC ? dr : nullptr, 0, 0, 0, 0, nullptr, depth,
+                        slot_bytes, st);
+    } else {
+      SDualHalpernOp<T, SC, false> op{y, yg, (T)st->sigma, w, rho};
+      stream_body<T, V>(A, vals, xbar, op, y, bh, ysum_or_yr, SC ? dr : nullptr, 0, 0, 0, 0, nullptr, depth,
+                        slot_bytes, st);
+    }
   } else {
     SDualOp<T, SC> op{y, ysum_or_yr, yg, (T)st->sigma, accumulate};
     stream_body<T, V>(A, vals, xbar, op, y, bh, accumulate ? ysum_or_yr : nullptr, SC ? dr : nullptr, 0, 0, 0, 0,
@@ -536,10 +543,16 @@ __global__ void __launch_bounds__(STREAM_TPB_MAX, 1)
   const T* p3 = SC ? dc : lo;  // the fourth staged vector
   const int use_lo = !SC && lo != nullptr;
   if (HALP) {
-    const T w = (T)stream_halpern_weight(st, it);
-    SPrimalHalpernOp<T, SC> op{x, xbar, (T)st->tau, w, (T)st->rho, use_lo};
-    stream_body<T, V>(At, vals, y, op, x, ch, xsum_or_xr, p3, u_begin, ncomb, ncols, panels, partial, depth,
-                      slot_bytes, st);
+    const T w = (T)stream_halpern_weight(st, it), rho = (T)st->rho;
+    if (rho == T(1)) {
+      SPrimalHalpernOp<T, SC, true> op{x, xbar, (T)st->tau, w, rho, use_lo};
+      stream_body<T, V>(At, vals, y, op, x, ch, xsum_or_xr, p3, u_begin, ncomb, ncols, panels, partial, depth,
+                        slot_bytes, st);
+    } else {
+      SPrimalHalpernOp<T, SC, false> op{x, xbar, (T)st->tau, w, rho, use_lo};
+      stream_body<T, V>(At, vals, y, op, x, ch, xsum_or_xr, p3, u_begin, ncomb, ncols, panels, partial, depth,
+                        slot_bytes, st);
+    }
   } else {
     SPrimalOp<T, SC> op{x, xbar, xsum_or_xr, (T)st->tau, accumulate, use_lo};
     stream_body<T, V>(At, vals, y, op, x, ch, accumulate ? xsum_or_xr : nullptr, p3, u_begin, ncomb, ncols,

@@ -74,6 +74,7 @@ class pdhg_options(C.Structure):
         ("stream_warps", C.c_int),
         ("stream_depth", C.c_int),
         ("refine32", C.c_int),
+        ("panel_overlap", C.c_int),
     ]
 
 

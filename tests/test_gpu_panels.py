@@ -255,3 +255,24 @@ def test_mixed_fp32_phase_uses_the_fp32_layout():
         st, _ = mx.iterate(100_000, 1e-8)
         assert st == P.PDHG_OK and mx.info()["polish_started_at"] > 0
         assert mx.kkt()["primal_obj"] == pytest.approx(lp.f_star, rel=1e-7)
+
+
+@pytest.mark.parametrize("extra", [dict(), dict(halpern=1, restart_scheme=1), dict(precision=P.PDHG_FP32),
+                                   dict(precision=P.PDHG_MIXED, polish_switch=1e-4),
+                                   dict(halpern=1, kernel_timing=1)])
+def test_overlapped_short_step_is_bit_identical(extra):
+    """panel_overlap (the default for FP32 steps): the short-column step starts as the panel
+    pass's blocks finish and only its combine blocks wait for the partial sums.
+    Every sum keeps its order, so restarted runs (graph-replayed, or direct
+    launches with kernel timing) equal the sequential launches' bit for bit."""
+    lp = lpgen.generate(3000, 9000, 2, nnz_per_col=None, zipf=(1.5, 10000, 90000), val_range=(0.1, 10.0),
+                        support=0.3, fp32_values=True)
+    eng = dict(primal_panels=1, panel_rows=256, long_row_min=32, **extra)
+    out = []
+    for overlap in (0, 1):
+        with P.Solver.from_lp(lp, panel_overlap=overlap, **eng) as s:
+            s.iterate(1280, 1e-12)
+            out.append((s.solution(), [(r["iteration"], r["kind"], r["omega"]) for r in s.trace()]))
+    for a, b in zip(out[0][0], out[1][0]):
+        np.testing.assert_array_equal(a, b)
+    assert out[0][1] == out[1][1]
