@@ -819,10 +819,21 @@ def run_ours(args):
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
             j1 = s4.info()
+            p32 = (j1["kernel_ms_primal"] - j0["kernel_ms_primal"]) / ITERS_PER_STEP
+            d32 = (j1["kernel_ms_dual"] - j0["kernel_ms_dual"]) / ITERS_PER_STEP
+            # algorithmic bytes of the FP32 half-steps (4-byte values and indices)
+            bp32 = 8 * lp.nnz + 4 * lp.m + 24 * lp.n
+            bd32 = 8 * lp.nnz + 4 * lp.n + 20 * lp.m
             extras["fp32_iteration"] = {
-                "iters_per_s": ITERS_PER_STEP / el,
-                "primal_ms": (j1["kernel_ms_primal"] - j0["kernel_ms_primal"]) / ITERS_PER_STEP,
-                "dual_ms": (j1["kernel_ms_dual"] - j0["kernel_ms_dual"]) / ITERS_PER_STEP}
+                "iters_per_s": ITERS_PER_STEP / el, "primal_ms": p32, "dual_ms": d32,
+                "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
+                             "primal": {"algorithmic_bytes_per_launch": bp32, "achieved": bp32 / (p32 / 1000.0) / 1e9,
+                                        "frac": bp32 / (p32 / 1000.0) / 1e9 / peak,
+                                        "traffic": profiled_traffic("primal half-step (FP32)",
+                                                                    name.replace("FP64", "FP32"))},
+                             "dual": {"algorithmic_bytes_per_launch": bd32, "achieved": bd32 / (d32 / 1000.0) / 1e9,
+                                      "frac": bd32 / (d32 / 1000.0) / 1e9 / peak,
+                                      "traffic": profiled_traffic("k_dual_step<float>", name.replace("FP64", "FP32"))}}}
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
