@@ -196,6 +196,14 @@ typedef struct {
                              steps, 0 for FP64 steps (where it measured slower) (-1) */
 } pdhg_options;
 
+/* Per-evaluation log: when the environment variable PDHG_LOG names a file at
+ * pdhg_create, the context appends one JSON line per evaluation of
+ * pdhg_iterate (single LPs): iteration, the candidate's rel_p, rel_d, rel_gap
+ * and rel_kkt (Section 2's relative termination test), its objectives, the
+ * candidate kind, the restart decision, the restart count, omega, the
+ * arithmetic of the iteration (fp32 / fp64), converged, and the seconds since
+ * create. A file that cannot be opened leaves the log off. Off by default. */
+
 /* Scalars of one point on the problem as given (unscaled), all FP64.
  * r_P = b - A x, r_D = A^T y + z - c with z = max(0, c - A^T y) (Section 2);
  * rel_* are the three ratios of the relative termination test (Section 2) and

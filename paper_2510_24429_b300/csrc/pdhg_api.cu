@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -132,6 +133,10 @@ struct pdhg_ctx {
   // the primal corrections' lower bounds -xr (rounded toward zero)
   bool refine = false;
   float* lo32 = nullptr;
+  // PDHG_LOG (environment, read at create): one JSON line per evaluation is
+  // appended to that file
+  FILE* log = nullptr;
+  std::chrono::steady_clock::time_point t_create = std::chrono::steady_clock::now();
   // option stream_steps: the streamed step kernels' launch shapes for
   // (T, V) = (double, double), (float, float), (double, float)
   bool stream_on = false;
@@ -2521,12 +2526,17 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
     pdhg_destroy(ctx);
     return st;
   }
+  // the per-evaluation log (off unless PDHG_LOG names a file; a file that
+  // cannot be opened leaves it off)
+  const char* log_path = getenv("PDHG_LOG");
+  if (log_path && *log_path) ctx->log = fopen(log_path, "a");
   *out = ctx;
   return PDHG_OK;
 }
 
 void pdhg_destroy(pdhg_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->log) fclose(ctx->log);
   int cur = -1;
   if (cudaGetDevice(&cur) == cudaSuccess && cur != ctx->device) cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
@@ -2551,6 +2561,32 @@ void pdhg_destroy(pdhg_ctx* ctx) {
 }
 
 static pdhg_status iterate_impl(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done);
+
+// One JSON line per evaluation (PDHG_LOG): the evaluation's candidate on the
+// problem as given - Section 2's relative residuals and gap, their maximum -
+// and the decisions taken there, from the state copy the host reads anyway.
+void log_evaluation(pdhg_ctx* ctx) {
+  const DevState& h = *ctx->h_st;
+  const EvalSums& e = h.candidate == KIND_AVG ? h.avg : h.cur;
+  const double cx = e.q[Q_CX], by = e.q[Q_BY];
+  const double rel_p = sqrt(e.q[Q_RP2U]) / (1.0 + h.b_norm);
+  const double rel_d = sqrt(e.q[Q_RD2U]) / (1.0 + h.c_norm);
+  const double rel_g = fabs(cx - by) / (1.0 + fabs(cx) + fabs(by));
+  const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - ctx->t_create).count();
+  static const char* const kinds[] = {"none", "current", "average", "step"};
+  static const char* const applies[] = {"none", "restart_current", "restart_average", "take_average",
+                                        "restart_step"};
+  fprintf(ctx->log,
+          "{\"iteration\": %lld, \"rel_p\": %.17g, \"rel_d\": %.17g, \"rel_gap\": %.17g, \"rel_kkt\": %.17g, "
+          "\"primal_obj\": %.17g, \"dual_obj\": %.17g, \"candidate\": \"%s\", \"restart\": \"%s\", "
+          "\"restarts\": %lld, \"omega\": %.17g, \"precision\": \"%s\", \"converged\": %d, "
+          "\"elapsed_s\": %.6f}\n",
+          (long long)h.k, rel_p, rel_d, rel_g, h.cand_rel_kkt, cx, by,
+          kinds[h.candidate >= 0 && h.candidate <= 3 ? h.candidate : 0],
+          applies[h.apply_mode >= 0 && h.apply_mode <= 4 ? h.apply_mode : 0], (long long)h.restarts, h.omega,
+          ctx->phase32 ? "fp32" : "fp64", h.converged, sec);
+  fflush(ctx->log);
+}
 
 pdhg_status pdhg_iterate(pdhg_ctx* ctx, int64_t max_iters, double tol, int64_t* iters_done) {
   Range nvtx_range("pdhg/iterate");
@@ -2618,6 +2654,7 @@ static pdhg_status iterate_impl(pdhg_ctx* ctx, int64_t max_iters, double tol, in
         if (iters_done) *iters_done = done;
         return fail(ctx, PDHG_ERR_NUMERIC, "NaN or Inf in the iterates");
       }
+      if (ctx->log) log_evaluation(ctx);
       if (ctx->h_st->snapshot_flag) {
         rs = take_snapshot(ctx);
         if (rs != PDHG_OK) return rs;
