@@ -194,6 +194,12 @@ typedef struct {
                              finish; only its per-column combine of the panels' partial sums waits for the
                              whole pass (same results); 0 = the two launches in sequence; -1 = 1 for FP32
                              steps, 0 for FP64 steps (where it measured slower) (-1) */
+  int panel_balance;      /* panel-tiled primal step: 1 = panel heights follow the long columns' entries, so
+                             that every panel gets a whole number of the panel pass's blocks (one wave) with
+                             equal entries per block, each panel at most panel_rows rows (or as many as fit in
+                             shared memory when panel_rows = 0); 0 = every panel panel_rows rows; -1 = 1 when
+                             panel_rows = 0, else 0 (-1). Results differ from equal heights by rounding only
+                             (the partial sums are cut at other rows) */
 } pdhg_options;
 
 /* Per-evaluation log: when the environment variable PDHG_LOG names a file at
@@ -243,6 +249,8 @@ typedef struct {
   int values32;                   /* 1: FP64 steps read the FP32 copies of A's unscaled values (option values32) */
   int stream_steps;               /* 1: the half-steps run as streamed kernels (option stream_steps) */
   int refine32;                   /* 1: FP32 phases run on corrections to an FP64 point (option refine32) */
+  int panels;                     /* panels of the panel-tiled primal step's layout for the phase in use (0: the
+                                     direct step over every column) */
 } pdhg_info;
 
 /* One feasibility polishing attempt. */

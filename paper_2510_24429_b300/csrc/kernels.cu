@@ -185,7 +185,7 @@ struct GlobalGather {
 template <class G>
 using GatherT = typename std::decay<decltype(std::declval<const G&>()(0))>::type;
 
-template <int R, class V, class Op, class G, class IX>
+template <int R, int UN, class V, class Op, class G, class IX>
 __device__ __forceinline__ void slice_dot(const IX& ix, const V* __restrict__ vals, int row0, int nvalid,
                                           long long base, int Lp, const G& gather, Op& op, unsigned long long pol,
                                           int lane) {
@@ -208,7 +208,7 @@ __device__ __forceinline__ void slice_dot(const IX& ix, const V* __restrict__ va
   } else {
     const int L2 = Lp >> 1;
     long long k = base + 2 * lane;
-#pragma unroll 2
+#pragma unroll UN
     for (int e2 = 0; e2 < L2; ++e2) {
 #pragma unroll
       for (int q = 0; q < R; ++q) {
@@ -246,7 +246,7 @@ struct CheckedGather {
 
 // One unit of H (a long row, or a slice of 32*R rows) for the dot-product
 // visitor below.
-template <class V, class Op, class G, class IX>
+template <int UN = 2, class V, class Op, class G, class IX>
 __device__ __forceinline__ void unit_dot_ix(const Hyb& H, const IX& ix, const V* __restrict__ vals, int u,
                                             const G& gather_in, Op& op, unsigned long long pol, int lane) {
   using T = GatherT<G>;
@@ -288,11 +288,11 @@ __device__ __forceinline__ void unit_dot_ix(const Hyb& H, const IX& ix, const V*
   } else {
     const int Lp = (int)((end - beg) / (32 * info.y));
     if (info.y == 4)
-      slice_dot<4>(ix, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
+      slice_dot<4, UN>(ix, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
     else if (info.y == 2)
-      slice_dot<2>(ix, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
+      slice_dot<2, UN>(ix, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
     else
-      slice_dot<1>(ix, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
+      slice_dot<1, UN>(ix, vals, info.x, info.z, beg, Lp, gather, op, pol, lane);
   }
 }
 
@@ -600,7 +600,7 @@ struct PartialOp {
 // FP32 panels take half the shared memory, so two blocks could share an SM
 template <class T, class V = T, bool I16 = false>
 __global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
-    k_primal_panels(Hyb Pn, const V* __restrict__ vals, const T* __restrict__ y, int m, int H,
+    k_primal_panels(Hyb Pn, const V* __restrict__ vals, const T* __restrict__ y, const int* __restrict__ pfirst,
                     const int4* __restrict__ binfo, const int* __restrict__ ustart, const int* __restrict__ segout,
                     T* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char panel_smem[];
@@ -612,7 +612,7 @@ __global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
   // holding the longest rows of A, have the most)
   const int4 bi = binfo[blockIdx.x];
   const int p = bi.x, sub = bi.y, kpp = bi.z;
-  const int i0 = p * H, len = min(H, m - i0);
+  const int i0 = pfirst[p], len = pfirst[p + 1] - i0;
   // the panel of y into shared memory with asynchronous 16-byte copies, all in
   // flight at once, when the panel starts on a 16-byte boundary (the default
   // panel height is a multiple of 16 entries); the rest with plain loads
@@ -632,12 +632,19 @@ __global__ void __launch_bounds__(PANEL_TPB, sizeof(T) == 4 ? PANEL_MINB32 : 1)
   const unsigned long long pol = stream_policy();
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   PartialOp<T> op{partial, segout};
-  const int u1 = ustart[p + 1];
-  for (int u = ustart[p] + sub * nw + (threadIdx.x >> 5); u < u1; u += kpp * nw)
+  // the panel's units (sorted by decreasing length) are dealt to its blocks'
+  // warps in rounds of W, alternately forwards and backwards, so that no warp
+  // (and no block) gets the longest unit of every round
+  const int ub = ustart[p], cnt = ustart[p + 1] - ub, W = kpp * nw, g = sub * nw + (threadIdx.x >> 5);
+  for (int r0 = 0, fwd = 1; r0 < cnt; r0 += W, fwd ^= 1) {
+    const int o = r0 + (fwd ? g : W - 1 - g);
+    if (o >= cnt) continue;
     if (I16)
-      unit_dot_ix(Pn, IdxU16{Pn.ci16}, vals, u, SmemGather<T>{ys}, op, pol, lane);
+      unit_dot_ix<sizeof(T) == 4 ? PANEL_UNROLL32 : PANEL_UNROLL64>(Pn, IdxU16{Pn.ci16}, vals, ub + o,
+                                                                    SmemGather<T>{ys}, op, pol, lane);
     else
-      unit_dot(Pn, vals, u, SmemGather<T>{ys}, op, pol, lane);
+      unit_dot(Pn, vals, ub + o, SmemGather<T>{ys}, op, pol, lane);
+  }
 }
 
 // ---- reflected Halpern form of the two half-steps (option halpern) ----------
@@ -1998,10 +2005,10 @@ void launch_panel_pass(const Hyb& Pn, const V* vals, const PanelLayout& L, const
   if (L.ncols == 0) return;
   const size_t smem = sizeof(T) * (size_t)L.rows;
   if (Pn.ci16)  // 16-bit panel-relative row indices
-    k_primal_panels<T, V, true><<<L.blocks, PANEL_TPB, smem, s>>>(Pn, vals, y, L.m, L.rows, L.binfo, L.ustart,
+    k_primal_panels<T, V, true><<<L.blocks, PANEL_TPB, smem, s>>>(Pn, vals, y, L.pfirst, L.binfo, L.ustart,
                                                                   L.segout, partial);
   else
-    k_primal_panels<T, V, false><<<L.blocks, PANEL_TPB, smem, s>>>(Pn, vals, y, L.m, L.rows, L.binfo, L.ustart,
+    k_primal_panels<T, V, false><<<L.blocks, PANEL_TPB, smem, s>>>(Pn, vals, y, L.pfirst, L.binfo, L.ustart,
                                                                    L.segout, partial);
 }
 template void launch_panel_pass<double, double>(const Hyb&, const double*, const PanelLayout&, const double*, double*,

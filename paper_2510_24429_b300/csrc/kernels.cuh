@@ -142,14 +142,19 @@ constexpr int PANEL_TPB = PDHG_PANEL_TPB;     // threads per block of the panel 
 // resident FP32 panel blocks per SM the compiler plans for: one (64 registers, no spills) ran
 // faster than two (32 registers, spilling) on the 1e6 x 3e6 LP
 constexpr int PANEL_MINB32 = PDHG_PANEL_MINB32;
+// entry pairs of a panel segment row a thread loads ahead (the slice loop's
+// unroll) in the panel pass, FP32 and FP64 steps: 4 ran 3% faster than 2 in
+// FP32 on the 1e6 x 3e6 Zipf LP; in FP64, 4 and 6 were 0.5% and 2% slower
+constexpr int PANEL_UNROLL32 = 4, PANEL_UNROLL64 = 2;
 constexpr int PANEL_SMEM_MAX = 220 * 1024;  // shared memory of one panel block
 struct PanelLayout {
   int m = 0;                // rows of A (length of y)
   int ncols = 0;            // columns covered: internal columns [0, ncols), the longest rows of A^T
   int ulong = 0;            // ... which are the rows of units [0, ulong) of At; the direct primal step
                             // takes the units from ulong on
-  int rows = 0;             // panel height: entries of y per panel
-  int panels = 0;           // ceil(m / rows)
+  int rows = 0;             // the tallest panel's height (entries of y in shared memory)
+  int panels = 0;           // number of panels
+  int* pfirst = nullptr;    // [panels + 1] first row of every panel (multiples of 16; pfirst[panels] = m)
   int* ustart = nullptr;    // [panels + 1] first unit of every panel in Pn
   int* segout = nullptr;    // [segments] position of every segment row of Pn in the dense panel-major
                             // partial sums (panel * ncols + column; slots of absent segments stay 0)
@@ -336,22 +341,25 @@ void launch_singleton_rows(const int* gci, const int* rowid, long long Z, const 
 // internal rows' lengths)
 void launch_transpose_keys(const long long* grp, const int* py, const long long* rpi, long long M, const int* gci,
                            const int* ix, unsigned* keys, int* vals, cudaStream_t s);
-// panel layout of A^T (segments = runs of one row of A^T inside one panel of
-// panel_rows internal rows); see build_panels in pdhg_api.cu
-void launch_panel_heads(const long long* tp, long long N, const int* sval, const int* rowid, const int* iy, int H,
-                        int* head, int* panel, int* col, cudaStream_t s);
+// panel layout of A^T (segments = runs of one row of A^T inside one panel;
+// panel p holds the internal rows [pfirst[p], pfirst[p + 1])); see
+// build_panels in pdhg_api.cu. cnt[i] += the entries of the first Z sorted
+// entries of A^T in internal row i (cnt zeroed by the caller)
+void launch_row_counts(long long Z, const int* sval, const int* rowid, const int* iy, int* cnt, cudaStream_t s);
+void launch_panel_heads(const long long* tp, long long N, const int* sval, const int* rowid, const int* iy,
+                        const int* pfirst, int P, int* head, int* panel, int* col, cudaStream_t s);
 void launch_panel_segments(const int* head, const int* panel, const int* col, const long long* segpos, long long Z,
                            long long S, long long* seg_start, int* seg_panel, int* seg_col, cudaStream_t s);
-void launch_panel_rowinfo(const int* sp, const int* seg_col, const int* seg_panel, int H, long long S, int* pcol,
-                          int* pbase, cudaStream_t s);
+void launch_panel_rowinfo(const int* sp, const int* seg_col, const int* seg_panel, const int* pfirst, long long S,
+                          int* pcol, int* pbase, cudaStream_t s);
 void launch_panel_keys(const long long* seg_start, const int* seg_panel, long long S, int maxlen, int lbits,
                        int* seg_len, unsigned long long* keys, int* vals, int* pcount, cudaStream_t s);
-void launch_panel_dense_out(const int* pcol, const int* pbase, int H, int ncols, long long S, int* out,
+void launch_panel_dense_out(const int* pcol, const int* sp, const int* seg_panel, int ncols, long long S, int* out,
                             cudaStream_t s);
 void launch_max_int(const int* v, long long len, unsigned* out, cudaStream_t s);
 void launch_fill_units_P(const Hyb& H, const int* slen, const int* sp, const long long* seg_start,
                          const int* seg_panel, const int* sval, const int* rowid, const int* iy, const double* v,
-                         int panel_rows, cudaStream_t s);
+                         const int* pfirst, cudaStream_t s);
 void launch_invert(const int* p, long long len, int* inv, cudaStream_t s);
 void launch_gather_int(const int* src, const int* p, long long len, int* out, cudaStream_t s);
 void launch_gather_double(const double* src, const int* p, long long len, double* out, cudaStream_t s);

@@ -152,18 +152,39 @@ __global__ void k_transpose_keys(const long long* __restrict__ grp, const int* _
 
 // ---- panel layout of A^T (panel-tiled primal step) ---------------------------
 
+// panel p holds the internal rows [pfirst[p], pfirst[p + 1]); the panel of row i
+__device__ __forceinline__ int panel_of(const int* __restrict__ pfirst, int P, int i) {
+  int lo = 0, hi = P;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pfirst[mid] <= i)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// cnt[i] += the entries of A^T's first rows (positions [0, Z) of the sorted
+// A^T entries) in internal row i of A: the weights of the panel heights
+__global__ void k_row_counts(long long Z, const int* __restrict__ sval, const int* __restrict__ rowid,
+                             const int* __restrict__ iy, int* __restrict__ cnt) {
+  for (long long q = gtid(); q < Z; q += gstride()) atomicAdd(cnt + iy[rowid[sval[q]]], 1);
+}
+
 // head[p] = 1 where a segment (a maximal run of one row of A^T inside one
-// panel of H internal rows) starts; panel[p] = its panel
+// panel) starts; panel[p] = its panel
 __global__ void k_panel_heads(const long long* __restrict__ tp, long long N, const int* __restrict__ sval,
-                              const int* __restrict__ rowid, const int* __restrict__ iy, int H,
-                              int* __restrict__ head, int* __restrict__ panel, int* __restrict__ col) {
+                              const int* __restrict__ rowid, const int* __restrict__ iy,
+                              const int* __restrict__ pfirst, int P, int* __restrict__ head, int* __restrict__ panel,
+                              int* __restrict__ col) {
   const int lane = threadIdx.x & 31;
   const long long w0 = gtid() >> 5, nw = gstride() >> 5;
   for (long long j = w0; j < N; j += nw) {
     const long long a = tp[j], b = tp[j + 1];
     for (long long q = a + lane; q < b; q += 32) {
-      const int pq = iy[rowid[sval[q]]] / H;
-      const int pp = q > a ? iy[rowid[sval[q - 1]]] / H : -1;
+      const int pq = panel_of(pfirst, P, iy[rowid[sval[q]]]);
+      const int pp = q > a ? panel_of(pfirst, P, iy[rowid[sval[q - 1]]]) : -1;
       head[q] = pq != pp;
       panel[q] = pq;
       col[q] = (int)j;
@@ -201,20 +222,20 @@ __global__ void k_panel_keys(const long long* __restrict__ seg_start, const int*
 
 // column and first row of A of every segment row r (segment sp[r])
 __global__ void k_panel_rowinfo(const int* __restrict__ sp, const int* __restrict__ seg_col,
-                                const int* __restrict__ seg_panel, int H, long long S, int* __restrict__ pcol,
-                                int* __restrict__ pbase) {
+                                const int* __restrict__ seg_panel, const int* __restrict__ pfirst, long long S,
+                                int* __restrict__ pcol, int* __restrict__ pbase) {
   for (long long r = gtid(); r < S; r += gstride()) {
     const int sid = sp[r];
     pcol[r] = seg_col[sid];
-    pbase[r] = seg_panel[sid] * H;
+    pbase[r] = pfirst[seg_panel[sid]];
   }
 }
 
 // partial-sum position of every segment row r in the dense panel-major array
 // of the panel pass: panel * ncols + column
-__global__ void k_panel_dense_out(const int* __restrict__ pcol, const int* __restrict__ pbase, int H, int ncols,
-                                  long long S, int* __restrict__ out) {
-  for (long long r = gtid(); r < S; r += gstride()) out[r] = (pbase[r] / H) * ncols + pcol[r];
+__global__ void k_panel_dense_out(const int* __restrict__ pcol, const int* __restrict__ sp,
+                                  const int* __restrict__ seg_panel, int ncols, long long S, int* __restrict__ out) {
+  for (long long r = gtid(); r < S; r += gstride()) out[r] = seg_panel[sp[r]] * ncols + pcol[r];
 }
 
 __global__ void k_invert(const int* __restrict__ p, long long len, int* __restrict__ inv) {
@@ -397,11 +418,11 @@ struct SrcPanel {
   const int* rowid;
   const int* iy;
   const double* v;
-  int H;
+  const int* pfirst;
   __device__ long long start(int row) const { return seg_start[sp[row]]; }
   __device__ void get(int row, long long p, int& c, double& x) const {
     const int k = sval[p];
-    c = iy[rowid[k]] - seg_panel[sp[row]] * H;
+    c = iy[rowid[k]] - pfirst[seg_panel[sp[row]]];
     x = v[k];
   }
 };
@@ -520,9 +541,13 @@ void launch_transpose_keys(const long long* grp, const int* py, const long long*
   k_transpose_keys<<<grid_of(32 * M), LT_TPB, 0, s>>>(grp, py, rpi, M, gci, ix, keys, vals);
 }
 
-void launch_panel_heads(const long long* tp, long long N, const int* sval, const int* rowid, const int* iy, int H,
-                        int* head, int* panel, int* col, cudaStream_t s) {
-  k_panel_heads<<<grid_of(32 * N), LT_TPB, 0, s>>>(tp, N, sval, rowid, iy, H, head, panel, col);
+void launch_row_counts(long long Z, const int* sval, const int* rowid, const int* iy, int* cnt, cudaStream_t s) {
+  if (Z > 0) k_row_counts<<<grid_of(Z), LT_TPB, 0, s>>>(Z, sval, rowid, iy, cnt);
+}
+
+void launch_panel_heads(const long long* tp, long long N, const int* sval, const int* rowid, const int* iy,
+                        const int* pfirst, int P, int* head, int* panel, int* col, cudaStream_t s) {
+  k_panel_heads<<<grid_of(32 * N), LT_TPB, 0, s>>>(tp, N, sval, rowid, iy, pfirst, P, head, panel, col);
 }
 
 void launch_panel_segments(const int* head, const int* panel, const int* col, const long long* segpos, long long Z,
@@ -531,9 +556,9 @@ void launch_panel_segments(const int* head, const int* panel, const int* col, co
                                                                  seg_col);
 }
 
-void launch_panel_rowinfo(const int* sp, const int* seg_col, const int* seg_panel, int H, long long S, int* pcol,
-                          int* pbase, cudaStream_t s) {
-  if (S > 0) k_panel_rowinfo<<<grid_of(S), LT_TPB, 0, s>>>(sp, seg_col, seg_panel, H, S, pcol, pbase);
+void launch_panel_rowinfo(const int* sp, const int* seg_col, const int* seg_panel, const int* pfirst, long long S,
+                          int* pcol, int* pbase, cudaStream_t s) {
+  if (S > 0) k_panel_rowinfo<<<grid_of(S), LT_TPB, 0, s>>>(sp, seg_col, seg_panel, pfirst, S, pcol, pbase);
 }
 
 void launch_panel_keys(const long long* seg_start, const int* seg_panel, long long S, int maxlen, int lbits,
@@ -542,9 +567,9 @@ void launch_panel_keys(const long long* seg_start, const int* seg_panel, long lo
                                                          pcount);
 }
 
-void launch_panel_dense_out(const int* pcol, const int* pbase, int H, int ncols, long long S, int* out,
+void launch_panel_dense_out(const int* pcol, const int* sp, const int* seg_panel, int ncols, long long S, int* out,
                             cudaStream_t s) {
-  if (S > 0) k_panel_dense_out<<<grid_of(S), LT_TPB, 0, s>>>(pcol, pbase, H, ncols, S, out);
+  if (S > 0) k_panel_dense_out<<<grid_of(S), LT_TPB, 0, s>>>(pcol, sp, seg_panel, ncols, S, out);
 }
 
 void launch_max_int(const int* v, long long len, unsigned* out, cudaStream_t s) {
@@ -554,9 +579,9 @@ void launch_max_int(const int* v, long long len, unsigned* out, cudaStream_t s) 
 
 void launch_fill_units_P(const Hyb& H, const int* slen, const int* sp, const long long* seg_start,
                          const int* seg_panel, const int* sval, const int* rowid, const int* iy, const double* v,
-                         int panel_rows, cudaStream_t s) {
+                         const int* pfirst, cudaStream_t s) {
   if (H.n_units == 0) return;
-  SrcPanel src{sp, seg_start, seg_panel, sval, rowid, iy, v, panel_rows};
+  SrcPanel src{sp, seg_start, seg_panel, sval, rowid, iy, v, pfirst};
   k_fill_units<SrcPanel><<<grid_of(32LL * H.n_units), LT_TPB, 0, s>>>(H.uinfo, H.uoff, H.n_units, slen, src, H.ci,
                                                                       H.v);
 }

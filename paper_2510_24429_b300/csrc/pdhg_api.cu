@@ -712,10 +712,100 @@ int bit_length(unsigned long long v) {
   return b;
 }
 
+// Panel heights for the panel-tiled primal step. Equal heights (option
+// panel_balance = 0): every panel ps.pl.rows rows. Balanced (the default
+// without panel_rows): the heights follow the entries of the long columns:
+// every panel gets a whole number k of the panel pass's blocks and about k * T
+// entries (T = the entries per block of one wave), at most hmax rows (what
+// fits in shared memory, or panel_rows rounded down to 16); a panel whose
+// first T entries need more rows gets hmax rows and one block. T is the smallest (by bisection) that
+// fits in one wave. Rows are sorted by decreasing length, so the first panels
+// are short and the last ones tall. With equal heights the blocks' shares
+// differ by the rounding of each panel's entries to whole blocks (one block
+// carried 1.22 times the mean on the 1e6 x 3e6 Zipf LP). Panel starts are
+// multiples of 16 rows (16-byte aligned copies of y into shared memory).
+pdhg_status plan_panels(pdhg_ctx* ctx, PanelSet& ps, Scratch& sc, const long long* tp, const int* sval,
+                        const int* rowid, const int* iy, long long nlong, long long hmax) {
+  const long long m = ctx->m;
+  cudaStream_t s = ctx->stream;
+  const int total = PANEL_MINB32 * ctx->sms;
+  std::vector<int> pf;
+  auto uniform = [&](long long H) {
+    pf.clear();
+    for (long long i = 0; i < m; i += H) pf.push_back((int)i);
+    pf.push_back((int)m);
+  };
+  uniform(ps.pl.rows);
+  const pdhg_options& o = ctx->opt;
+  const bool balance = o.panel_balance == 1 || (o.panel_balance == -1 && o.panel_rows == 0);
+  if (o.panel_rows > 0) hmax = std::min(hmax, (long long)o.panel_rows / 16 * 16);
+  if (balance && hmax >= 16 && (long long)pf.size() - 1 <= total) {
+    long long Z = 0;
+    CK(ctx, cudaMemcpyAsync(&Z, tp + nlong, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CK(ctx, cudaStreamSynchronize(s));
+    int* cnt = nullptr;
+    CK(ctx, sc.take(&cnt, m));
+    CK(ctx, cudaMemsetAsync(cnt, 0, sizeof(int) * m, s));
+    launch_row_counts(Z, sval, rowid, iy, cnt, s);
+    std::vector<int> hc(m);
+    CK(ctx, cudaMemcpyAsync(hc.data(), cnt, sizeof(int) * m, cudaMemcpyDeviceToHost, s));
+    CK(ctx, cudaStreamSynchronize(s));
+    std::vector<long long> cum(m + 1, 0);
+    for (long long i = 0; i < m; ++i) cum[i + 1] = cum[i] + hc[i];
+    // the first row e (a multiple of 16, or m) with cum[e] >= target
+    auto row_for = [&](double target) -> long long {
+      const long long e = std::lower_bound(cum.begin(), cum.end(), (long long)std::ceil(target)) - cum.begin();
+      return std::min(m, (e + 15) / 16 * 16);
+    };
+    // panel starts for entries per block T; returns the blocks they take
+    auto greedy = [&](double T, std::vector<int>* out) -> long long {
+      long long st = 0, blocks = 0;
+      if (out) out->assign(1, 0);
+      while (st < m) {
+        long long k = 0, e = st;
+        for (;;) {
+          const long long ek = row_for((double)cum[st] + (double)(k + 1) * T);
+          if (ek - st > hmax) break;
+          ++k;
+          e = ek;
+          if (ek >= m) break;
+        }
+        if (k == 0) {
+          k = 1;
+          e = std::min(m, st + hmax);
+        }
+        blocks += k;
+        st = e;
+        if (out) out->push_back((int)st);
+      }
+      return blocks;
+    };
+    double lo = (double)cum[m] / total, hi = lo;
+    while (greedy(hi, nullptr) > total && hi < 1e18) hi *= 2;
+    if (greedy(hi, nullptr) <= total) {
+      for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (greedy(mid, nullptr) <= total)
+          hi = mid;
+        else
+          lo = mid;
+      }
+      greedy(hi, &pf);
+    }
+  }
+  int H = 0;
+  for (size_t p = 0; p + 1 < pf.size(); ++p) H = std::max(H, pf[p + 1] - pf[p]);
+  ps.pl.rows = H;
+  ps.pl.panels = (int)pf.size() - 1;
+  CK(ctx, dalloc(ctx, &ps.pl.pfirst, pf.size()));
+  CK(ctx, cudaMemcpyAsync(ps.pl.pfirst, pf.data(), sizeof(int) * pf.size(), cudaMemcpyHostToDevice, s));
+  return PDHG_OK;
+}
+
 // Panel layout of Ahat^T for the panel-tiled primal step (one LP): the entries
 // of every long row j < nlong of A^T (the rows with at least long_row_min
 // entries, which come first in the internal numbering; sorted by internal row
-// i) are cut into segments, one per panel of ps.pl.rows consecutive rows i;
+// i) are cut into segments, one per panel (consecutive rows i, see plan_panels);
 // short rows stay with the direct step (a one-entry segment would cost a
 // partial sum's write and read to save one gather). The segments of each panel,
 // sorted by decreasing length, become the rows of the Hyb ps.Pn with row
@@ -728,6 +818,7 @@ pdhg_status build_panels(pdhg_ctx* ctx, PanelSet& ps, Scratch& sc, const long lo
   const pdhg_options& o = ctx->opt;
   const long long N = nlong;
   const int H = ps.pl.rows, P = ps.pl.panels;
+  const int* pfirst = ps.pl.pfirst;
   cudaStream_t s = ctx->stream;
   long long Z = 0;  // entries of the long rows: tp[nlong]
   CK(ctx, cudaMemcpyAsync(&Z, tp + N, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -739,7 +830,7 @@ pdhg_status build_panels(pdhg_ctx* ctx, PanelSet& ps, Scratch& sc, const long lo
   CK(ctx, sc.take(&panel, Z));
   CK(ctx, sc.take(&col, Z));
   CK(ctx, sc.take(&segpos, Z + 1));
-  launch_panel_heads(tp, N, sval, rowid, iy, H, head, panel, col, s);
+  launch_panel_heads(tp, N, sval, rowid, iy, pfirst, P, head, panel, col, s);
   launch_scan_int(head, Z, segpos, ws, s);
   long long S = 0;
   CK(ctx, cudaMemcpyAsync(&S, segpos + Z, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -768,9 +859,9 @@ pdhg_status build_panels(pdhg_ctx* ctx, PanelSet& ps, Scratch& sc, const long lo
                                                         lbits + bit_length((unsigned long long)(P - 1)), hist, ws, s);
   const int* sp = alt ? vb : va;
   launch_gather_int(seg_len, sp, S, slen, s);
-  launch_panel_rowinfo(sp, seg_col, seg_panel, H, S, ps.col, ps.base, s);
+  launch_panel_rowinfo(sp, seg_col, seg_panel, pfirst, S, ps.col, ps.base, s);
   CK(ctx, dalloc(ctx, &ps.pl.segout, S));
-  launch_panel_dense_out(ps.col, ps.base, H, (int)N, S, ps.pl.segout, s);
+  launch_panel_dense_out(ps.col, sp, seg_panel, (int)N, S, ps.pl.segout, s);
   std::vector<int> hs(S), hc(P);
   CK(ctx, cudaMemcpyAsync(hs.data(), slen, sizeof(int) * S, cudaMemcpyDeviceToHost, s));
   CK(ctx, cudaMemcpyAsync(hc.data(), pcount, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
@@ -815,7 +906,7 @@ pdhg_status build_panels(pdhg_ctx* ctx, PanelSet& ps, Scratch& sc, const long lo
   if (rs != PDHG_OK) return rs;
   CK(ctx, dalloc(ctx, &ps.pl.ustart, P + 1));
   CK(ctx, cudaMemcpyAsync(ps.pl.ustart, ust.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice, s));
-  launch_fill_units_P(ps.Pn, slen, sp, seg_start, seg_panel, sval, rowid, iy, val, H, s);
+  launch_fill_units_P(ps.Pn, slen, sp, seg_start, seg_panel, sval, rowid, iy, val, pfirst, s);
   // the panel pass reads the panel-relative row indices (< H <= 56320) in 16
   // bits: 2 bytes less per entry of the long columns
   if (H <= 65536 && ps.Pn.slots > 0) {
@@ -997,6 +1088,10 @@ pdhg_status build_layouts(pdhg_ctx* ctx, Scratch& sc, const long long* lrp, cons
       const bool fp32_steps = k == 1 || o.precision == PDHG_FP32;
       const int pmin = o.panel_min_len > 0 ? o.panel_min_len : (fp32_steps ? 32 : o.long_row_min);
       const long long nlong = prefix(pmin, &ps.pl.ulong);
+      if (nlong > 0) {
+        rs = plan_panels(ctx, ps, sc, tp, sval, rowid, iy, nlong, PANEL_SMEM_MAX / (fp32_steps ? 4LL : 8LL));
+        if (rs != PDHG_OK) return rs;
+      }
       const long long dense = (long long)ps.pl.panels * nlong;  // slots of the panel-major partial sums
       if (nlong == 0 || dense > 64LL * Z + (1LL << 20) || dense >= (1LL << 31) - 1) {
         // nothing to tile, or partial sums far larger than the matrix: the
@@ -2355,6 +2450,7 @@ void pdhg_default_options(pdhg_options* o) {
   o->stream_depth = 3;
   o->refine32 = -1;
   o->panel_overlap = -1;
+  o->panel_balance = -1;
 }
 
 pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
@@ -2438,6 +2534,8 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
                 "refine32 must be -1, 0 or 1 (1: precision FP32 or MIXED, no recording or persistent loop)");
   if (o.panel_overlap < -1 || o.panel_overlap > 1)
     return fail(nullptr, PDHG_ERR_INVALID, "panel_overlap must be -1, 0 or 1");
+  if (o.panel_balance < -1 || o.panel_balance > 1)
+    return fail(nullptr, PDHG_ERR_INVALID, "panel_balance must be -1, 0 or 1");
   if (!(o.polish_switch >= 0.0 || o.polish_switch == -1.0))
     return fail(nullptr, PDHG_ERR_INVALID, "polish_switch must be >= 0 or -1 (automatic)");
 
@@ -2893,6 +2991,7 @@ pdhg_status pdhg_get_info(pdhg_ctx* ctx, pdhg_info* out) {
   out->values32 = ctx->vals_u ? 1 : 0;
   out->stream_steps = ctx->stream_on ? 1 : 0;
   out->refine32 = ctx->refine ? 1 : 0;
+  out->panels = !ctx->panels_on ? 0 : ctx->pan[ctx->phase32 && ctx->pan32 ? 1 : 0].pl.panels;
   return PDHG_OK;
 }
 

@@ -75,6 +75,7 @@ class pdhg_options(C.Structure):
         ("stream_depth", C.c_int),
         ("refine32", C.c_int),
         ("panel_overlap", C.c_int),
+        ("panel_balance", C.c_int),
     ]
 
 
@@ -95,7 +96,7 @@ class pdhg_info(C.Structure):
         ("polish_started_at", C.c_int64),
         ("feas_polish_attempts", C.c_int64), ("feas_polish_iterations", C.c_int64), ("feas_polished", C.c_int),
         ("persistent_grid", C.c_int), ("graph_launches", C.c_int64), ("values32", C.c_int),
-        ("stream_steps", C.c_int), ("refine32", C.c_int),
+        ("stream_steps", C.c_int), ("refine32", C.c_int), ("panels", C.c_int),
     ]
 
 

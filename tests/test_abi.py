@@ -70,7 +70,8 @@ def test_default_options(lib):
     assert (o.dual_hot_cols, o.singleton_order, o.barrier_cycles) == (0, 1, 0)
     assert (o.panel_min_len, o.restart_scheme, o.values32) == (0, 0, -1)
     assert (o.pid_kp, o.pid_ki, o.pid_kd) == (0.99, 0.01, 0.0)
-    assert (o.stream_steps, o.stream_warps, o.stream_depth, o.refine32, o.panel_overlap) == (0, 0, 3, -1, -1)
+    assert (o.stream_steps, o.stream_warps, o.stream_depth, o.refine32, o.panel_overlap, o.panel_balance) == (
+        0, 0, 3, -1, -1, -1)
     with pytest.raises(KeyError):
         P.pdhg_default_options(no_such_option=1)
 

@@ -140,6 +140,36 @@ def test_long_and_short_columns_mixed(prec):
             assert rel_err(sp.solution()[0], sd.solution()[0]) <= 1e-4
 
 
+@pytest.mark.parametrize("prec", [P.PDHG_FP64, P.PDHG_FP32])
+def test_balanced_panel_heights(prec):
+    """panel_balance = 1: panel heights cut where the long columns' entries
+    fill a whole number of the panel pass's blocks (panel_rows the tallest
+    allowed). Against the oracle at 1e-10 after 100 iterations (FP64) and
+    against equal heights at rounding level (FP32); the panel count is
+    reported in the info."""
+    lp = lpgen.generate(3000, 9000, 2, nnz_per_col=None, zipf=(1.5, 10000, 90000), val_range=(0.1, 10.0),
+                        support=0.3, fp32_values=True)
+    for rows in (64, 256):
+        eng = dict(primal_panels=1, panel_rows=rows, long_row_min=32, precision=prec)
+        if prec == P.PDHG_FP64:
+            orc, sol = _solvers(lp, dict(eng, panel_balance=1), **TINY_PLAIN)
+            with sol:
+                assert sol.info()["panels"] >= -(-lp.m // rows)
+                orc.run(100)
+                assert sol.iterate(100) == (P.PDHG_OK, 100)
+                assert_iterates_close(sol, orc, 1e-10)
+        else:
+            out = []
+            for bal in (0, 1):
+                with P.Solver.from_lp(lp, panel_balance=bal, **eng) as s:
+                    assert s.info()["panels"] >= -(-lp.m // rows)
+                    assert s.iterate(640) == (P.PDHG_OK, 640)
+                    out.append(s.solution()[0])
+            assert rel_err(out[0], out[1]) <= 1e-4
+    with pytest.raises(P.PDHGError):
+        P.Solver.from_lp(lp, primal_panels=1, panel_balance=2)
+
+
 def test_option_checks(tiny_lp):
     with pytest.raises(P.PDHGError):
         P.Solver.from_lp(tiny_lp, primal_panels=1, panel_rows=28161)
