@@ -122,6 +122,7 @@ struct pdhg_ctx {
   // layout - shorter columns in the panels, twice the rows per panel - for the
   // FP32 phase of PDHG_MIXED
   bool panels_on = false;
+  bool check_on_device = false;  // host inputs: checked on the device after the upload (a GPU was found)
   bool pan32 = false;
   PanelSet pan[2];
   // option values32: the FP64 steps read A.u32 / At.u32 / pan[0].Pn.u32 (A's
@@ -1114,9 +1115,10 @@ pdhg_status build_layouts(pdhg_ctx* ctx, Scratch& sc, const long long* lrp, cons
   return PDHG_OK;
 }
 
-// host_checks: waits for the checks of host inputs (see pdhg_create) and
-// returns their status; called once the upload is queued, before anything
-// reads the uploaded data.
+// host_checks: waits for the host threads' checks of host inputs (see
+// pdhg_create) and returns their status; called once the upload is queued,
+// before anything reads the uploaded data. With ctx->check_on_device the
+// uploaded copies are checked on the device instead.
 pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx, const double* val, const double* b,
                   const double* c, const double* x0, const double* y0, const std::function<pdhg_status()>& host_checks) {
   Range nvtx_range("pdhg/setup");
@@ -1139,25 +1141,6 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
     d_c = c;
     d_x0 = x0;
     d_y0 = y0;
-    // the checks pdhg_create makes on host inputs, on the device
-    int* flags = nullptr;
-    CK(ctx, sc.take(&flags, 1));
-    CK(ctx, cudaMemsetAsync(flags, 0, sizeof(int), s));
-    launch_validate_csr(m, n, nnz, d_rp, d_ci, d_v, flags, s);
-    launch_check_finite(d_b, m, flags, s);
-    launch_check_finite(d_c, n, flags, s);
-    if (d_x0) launch_check_finite(d_x0, n, flags, s);
-    if (d_y0) launch_check_finite(d_y0, m, flags, s);
-    int hf = 0;
-    CK(ctx, cudaGetLastError());
-    CK(ctx, cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(ctx, cudaStreamSynchronize(s));
-    if (hf & LAYOUT_BAD_ROW_PTR)
-      return fail(ctx, PDHG_ERR_INVALID, "row_ptr[0] != 0, row_ptr[m] != nnz or row_ptr not non-decreasing");
-    if (hf & LAYOUT_BAD_COLUMN) return fail(ctx, PDHG_ERR_INVALID, "column index out of range");
-    if (hf & LAYOUT_UNSORTED)
-      return fail(ctx, PDHG_ERR_INVALID, "column indices not strictly increasing within a row");
-    if (hf & LAYOUT_NOT_FINITE) return fail(ctx, PDHG_ERR_NUMERIC, "NaN or Inf in the input data");
   } else {
     long long* rp_ = nullptr;
     int* ci_ = nullptr;
@@ -1191,8 +1174,32 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
     d_v = v_;
     d_b = b_;
     d_c = c_;
-    const pdhg_status checked = host_checks();
-    if (checked != PDHG_OK) return checked;  // the caller reports the checks' message
+    if (!ctx->check_on_device) {
+      const pdhg_status checked = host_checks();
+      if (checked != PDHG_OK) return checked;  // the caller reports the checks' message
+    }
+  }
+  if (o.inputs_on_device || ctx->check_on_device) {
+    // the checks pdhg_create makes on host inputs without a GPU, on the
+    // device: the CSR structure and finite data, before anything reads them
+    int* flags = nullptr;
+    CK(ctx, sc.take(&flags, 1));
+    CK(ctx, cudaMemsetAsync(flags, 0, sizeof(int), s));
+    launch_validate_csr(m, n, nnz, d_rp, d_ci, d_v, flags, s);
+    launch_check_finite(d_b, m, flags, s);
+    launch_check_finite(d_c, n, flags, s);
+    if (d_x0) launch_check_finite(d_x0, n, flags, s);
+    if (d_y0) launch_check_finite(d_y0, m, flags, s);
+    int hf = 0;
+    CK(ctx, cudaGetLastError());
+    CK(ctx, cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(ctx, cudaStreamSynchronize(s));
+    if (hf & LAYOUT_BAD_ROW_PTR)
+      return fail(ctx, PDHG_ERR_INVALID, "row_ptr[0] != 0, row_ptr[m] != nnz or row_ptr not non-decreasing");
+    if (hf & LAYOUT_BAD_COLUMN) return fail(ctx, PDHG_ERR_INVALID, "column index out of range");
+    if (hf & LAYOUT_UNSORTED)
+      return fail(ctx, PDHG_ERR_INVALID, "column indices not strictly increasing within a row");
+    if (hf & LAYOUT_NOT_FINITE) return fail(ctx, PDHG_ERR_NUMERIC, "NaN or Inf in the input data");
   }
   pdhg_status rs = build_layouts(ctx, sc, d_rp, d_ci, d_v, {0}, {0, (long long)nnz});
   if (rs != PDHG_OK) return rs;
@@ -1318,9 +1325,11 @@ pdhg_status setup(pdhg_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
   launch_power_start(w, ctx->perm_x, nullptr, 1, (int)n, gn, s);
   launch_sumsq(w, (int)n, ctx->partials, nbs, ctx->scal + 6, s);
   launch_div_by_norm(v, w, ctx->scal + 6, (int)n, gn, s);
+  // the estimate is ||Ahat v|| of the last iteration (a zero ||w|| leaves v,
+  // so the later iterations repeat it), so only that one's norm is taken
   for (int it = 0; it < o.power_iters; ++it) {
     launch_spmv(A, v, u, grA, s);
-    launch_sumsq(u, (int)m, ctx->partials, nbs, ctx->scal + 0, s);
+    if (it == o.power_iters - 1) launch_sumsq(u, (int)m, ctx->partials, nbs, ctx->scal + 0, s);
     launch_spmv(At, u, w, grT, s);
     launch_sumsq(w, (int)n, ctx->partials, nbs, ctx->scal + 5, s);
     launch_div_by_norm(v, w, ctx->scal + 5, (int)n, gn, s);
@@ -1875,9 +1884,9 @@ pdhg_status setup_batch(pdhg_ctx* ctx, int count, const pdhg_lp_desc* lps) {
   launch_power_start(w, ctx->perm_x, ctx->xoff, count, (int)n, gx, s);
   launch_sumsq_b(w, ctx->xoff, count, ctx->scal + 6, 8, s);
   launch_div_by_norm_b(v, w, ctx->scal + 6, 8, ctx->xoff, count, gx, s);
-  for (int it = 0; it < o.power_iters; ++it) {
+  for (int it = 0; it < o.power_iters; ++it) {  // the last iteration's ||Ahat v|| per instance (as above)
     launch_spmv(A, v, u, grA, s);
-    launch_sumsq_b(u, ctx->yoff, count, ctx->scal + 0, 8, s);
+    if (it == o.power_iters - 1) launch_sumsq_b(u, ctx->yoff, count, ctx->scal + 0, 8, s);
     launch_spmv(At, u, w, grT, s);
     launch_sumsq_b(w, ctx->xoff, count, ctx->scal + 5, 8, s);
     launch_div_by_norm_b(v, w, ctx->scal + 5, 8, ctx->xoff, count, gx, s);
@@ -2539,12 +2548,16 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
   if (!(o.polish_switch >= 0.0 || o.polish_switch == -1.0))
     return fail(nullptr, PDHG_ERR_INVALID, "polish_switch must be >= 0 or -1 (automatic)");
 
-  // Checks of host inputs (CSR structure, finite data) on host threads, beside
-  // the context's set-up: stream creation, allocations and the upload depend
-  // only on the sizes, and setup reads nothing it uploaded before the checks
-  // have passed. Their failure takes precedence over any later error, so a
-  // malformed LP gets INVALID / NUMERIC whether or not a GPU is present.
-  // Device inputs are checked on the device during setup.
+  // Checks of host inputs (CSR structure, finite data). With a GPU they run on
+  // the device, on the uploaded copies, before setup reads them (on the host
+  // they took ~23 ms of the 1e6 x 3e6 LP's set-up beside the upload, and
+  // slowed the upload). Without one (no device or no driver), or when the
+  // device set-up fails before the upload, they run on host threads, so a
+  // malformed LP gets INVALID / NUMERIC whether or not a GPU is present; on
+  // host threads they run beside the context's set-up: stream creation,
+  // allocations and the upload depend only on the sizes, and setup reads
+  // nothing it uploaded before the checks have passed, and their failure takes
+  // precedence over any later error. Device inputs are checked on the device.
   auto run_checks = [=]() {
     const char* msg = "";
     pdhg_status st = check_lp(m, n, nnz, row_ptr, col_idx, val, b, c, &msg);
@@ -2556,7 +2569,9 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
   };
   std::future<std::pair<pdhg_status, const char*>> checks;
   std::pair<pdhg_status, const char*> checked{PDHG_OK, ""};
-  if (!o.inputs_on_device) {
+  int ndev = 0;
+  const bool dev_checks = !o.inputs_on_device && cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0;
+  if (!o.inputs_on_device && !dev_checks) {
     try {
       checks = std::async(std::launch::async, run_checks);
     } catch (...) {  // no thread to be had: check here, before any device work
@@ -2578,6 +2593,7 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
   ctx->n = n;
   ctx->nnz = nnz;
   ctx->opt = o;
+  ctx->check_on_device = dev_checks;
   ctx->wpb = (o.step_block ? o.step_block : TPB) / 32;
   // auto: only where the matrix stream dwarfs the panels' copies of y (every
   // block copies one panel, ~H entries, per step)
@@ -2609,6 +2625,7 @@ pdhg_status pdhg_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
+    if (dev_checks) checked = run_checks();  // the input's errors come first
     const pdhg_status v = await_checks();
     pdhg_status st = v != PDHG_OK ? fail(nullptr, v, checked.second) : cuda_fail(nullptr, e, "device/stream setup");
     pdhg_destroy(ctx);
