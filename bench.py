@@ -171,10 +171,11 @@ def code_tokens(text: str) -> str:
 
 
 def kernel_source_sha():
-    """Hash of the step kernels' code (comments and layout excluded): the
-    traffic record stays valid only while it is unchanged."""
+    """Hash of the step kernels' code and of the code that lays out their
+    matrices (comments and formatting excluded): the traffic record stays
+    valid only while it is unchanged."""
     h = hashlib.sha256()
-    for f in ("kernels.cu", "common.cuh", "kernels.cuh", "step_ops.cuh"):
+    for f in ("kernels.cu", "common.cuh", "kernels.cuh", "step_ops.cuh", "layout.cu", "pdhg_api.cu"):
         with open(os.path.join(ROOT, "paper_2510_24429_b300", "csrc", f), encoding="utf-8") as fh:
             h.update(code_tokens(fh.read()).encode())
     return h.hexdigest()[:16]
