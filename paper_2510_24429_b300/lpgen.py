@@ -131,18 +131,30 @@ def zipf_tail(s: float, cap: int) -> np.ndarray:
     return zeta(s, k) / zeta(s, 1.0)
 
 
-def zipf_column_counts(seed: int, n: int, s: float, cap: int, nnz_target: int, m: int) -> np.ndarray:
-    """Per-column counts k_j = max(1, rint(alpha * min(Z_j, cap))), Z_j ~ Zipf(s),
-    with alpha chosen by bisection so that sum_j k_j is as close as possible to
-    ``nnz_target``. The shape of the tail is the Zipf law; alpha only rescales it
-    so that the mean count matches the requested nnz."""
+def zipf_draws(seed: int, n: int, s: float, cap: int) -> np.ndarray:
+    """min(Z_j, cap) for j < n, Z_j ~ Zipf(s) by inversion of the tail (float64)."""
     tail = zipf_tail(s, cap)
     u = 1.0 - rand_uniform(seed, S_ZIPF, np.arange(n, dtype=np.uint64))  # (0, 1]
     # Z = largest k with tail[k] >= u; tail is decreasing, so search the reversed array.
     rev = tail[::-1]
     pos = np.searchsorted(rev, u, side="left")  # rev[pos-1] < u <= rev[pos]
     Z = cap - pos  # index into tail
-    Z = np.clip(Z, 1, cap).astype(np.float64)
+    return np.clip(Z, 1, cap).astype(np.float64)
+
+
+def zipf_exact_counts(seed: int, n: int, s: float, cap: int, m: int) -> np.ndarray:
+    """The literal capped Zipf law: k_j = min(Z_j, cap, m), the draws of
+    ``zipf_column_counts`` without its rescaling (mean count
+    sum_{k <= cap} P(Z >= k), about 153 for s = 1.5 and cap = 1e4)."""
+    return np.minimum(zipf_draws(seed, n, s, cap), m).astype(np.int64)
+
+
+def zipf_column_counts(seed: int, n: int, s: float, cap: int, nnz_target: int, m: int) -> np.ndarray:
+    """Per-column counts k_j = max(1, rint(alpha * min(Z_j, cap))), Z_j ~ Zipf(s),
+    with alpha chosen by bisection so that sum_j k_j is as close as possible to
+    ``nnz_target``. The shape of the tail is the Zipf law; alpha only rescales it
+    so that the mean count matches the requested nnz."""
+    Z = zipf_draws(seed, n, s, cap)
 
     zu, zn = np.unique(Z, return_counts=True)
 
@@ -268,3 +280,147 @@ def adjoint_lp(seed: int = 0, m: int = 100_000, n: int = 300_000, nnz_per_col: i
 def x_target(lp: LP, seed: int, scale: float = 0.01) -> np.ndarray:
     """x* + N(0, scale^2) noise for the unrolled-PDHG loss."""
     return lp.x_star + scale * rand_normal(seed, S_TARGET, np.arange(lp.n, dtype=np.uint64))
+
+
+# ---------------------------------------------------------------------------
+# The same recipe as torch tensor operations on any torch device, for LPs too
+# large to build in host memory (the literal capped-Zipf variant of the large
+# workload has ~4.6e8 entries; the numpy build above would need ~40 GB of host
+# memory). Same counters and streams: the matrix, x* and z* equal generate()'s
+# bit for bit; y*, b and c agree to rounding (torch's log1p and cos, and its
+# summation order). 64-bit draws are held as int64 bit patterns; products wrap
+# modulo 2^64 like the uint64 arithmetic above, and right shifts are logical.
+# ---------------------------------------------------------------------------
+
+def _s64(v: int) -> int:
+    v &= 0xFFFFFFFFFFFFFFFF
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+_GAMMA_S, _M1_S, _M2_S = _s64(int(GAMMA)), _s64(int(_M1)), _s64(int(_M2))
+
+
+def _shr(z, k: int):
+    return (z >> k) & ((1 << (64 - k)) - 1)
+
+
+def _mix64_t(z):
+    z = (z ^ _shr(z, 30)) * _M1_S
+    z = (z ^ _shr(z, 27)) * _M2_S
+    return z ^ _shr(z, 31)
+
+
+def rand_bits_t(seed: int, stream: int, idx):
+    """``rand_bits`` for an int64 tensor of counters (bit patterns in int64)."""
+    return _mix64_t(_s64(int(_key(seed, stream))) + (idx + 1) * _GAMMA_S)
+
+
+def rand_uniform_t(seed: int, stream: int, idx):
+    import torch
+
+    return _shr(rand_bits_t(seed, stream, idx), 11).to(torch.float64) * (2.0 ** -53)
+
+
+def rand_normal_t(seed: int, stream: int, idx):
+    import torch
+
+    u1 = rand_uniform_t(seed, stream, 2 * idx)
+    u2 = rand_uniform_t(seed, stream, 2 * idx + 1)
+    return torch.sqrt(-2.0 * torch.log1p(-u1)) * torch.cos(2.0 * math.pi * u2)
+
+
+@dataclasses.dataclass
+class TorchLP:
+    """An LP of the generator as torch tensors on one device (CSR by rows)."""
+
+    m: int
+    n: int
+    row_ptr: "object"  # int64 [m+1]
+    col_idx: "object"  # int32 [nnz]
+    val: "object"  # float64 [nnz]
+    b: "object"
+    c: "object"
+    x_star: "object"
+    y_star: "object"
+    z_star: "object"
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    @property
+    def f_star(self) -> float:
+        return float((self.c * self.x_star).sum())
+
+
+def generate_t(m: int, n: int, seed: int, counts: np.ndarray, *, val_range=(0.1, 1.0), support=0.3,
+               star_range=(0.5, 2.0), device="cuda", name: str = "") -> TorchLP:
+    """``generate`` with the given per-column counts, as torch operations on
+    ``device``."""
+    import torch
+
+    counts = np.asarray(counts, dtype=np.int64)
+    if np.any(counts > m):
+        raise ValueError("column count exceeds m")
+    nnz = int(counts.sum())
+    ct = torch.as_tensor(counts, device=device)
+    col = torch.repeat_interleave(torch.arange(n, device=device, dtype=torch.int64), ct)
+    slots = torch.arange(nnz, device=device, dtype=torch.int64)
+    rows = torch.floor(rand_uniform_t(seed, S_ROWS, slots) * m).to(torch.int64)
+    # rows distinct within a column: of equal (column, row) pairs the later
+    # slots are drawn again, from counters past the earlier attempts'
+    attempt = 0
+    while True:
+        ks, order = torch.sort(col * m + rows, stable=True)
+        dup = torch.nonzero(ks[1:] == ks[:-1]).squeeze(1) + 1
+        del ks
+        if dup.numel() == 0:
+            break
+        attempt += 1
+        redo = order[dup]
+        rows[redo] = torch.floor(rand_uniform_t(seed, S_ROWS, redo + attempt * nnz) * m).to(torch.int64)
+        if attempt > 10000:  # pragma: no cover - impossible for counts << m
+            raise RuntimeError("row draw did not terminate")
+    del order
+    lo, hi = val_range
+    vals = lo + (hi - lo) * rand_uniform_t(seed, S_MAG, slots)
+    vals = torch.where(_shr(rand_bits_t(seed, S_SIGN, slots), 63) == 1, -vals, vals)
+    del slots
+    # the optimum
+    n_sup = int(support) if isinstance(support, (int, np.integer)) else int(round(float(support) * n))
+    jj = torch.arange(n, device=device, dtype=torch.int64)
+    # unsigned order of the 64-bit keys: flip the sign bit, then sort as int64
+    keys = rand_bits_t(seed, S_SUPPORT, jj) ^ _s64(1 << 63)
+    on = torch.zeros(n, dtype=torch.bool, device=device)
+    on[torch.sort(keys, stable=True).indices[:n_sup]] = True
+    slo, shi = star_range
+    x_star = torch.where(on, slo + (shi - slo) * rand_uniform_t(seed, S_XS, jj), torch.zeros((), dtype=torch.float64,
+                                                                                          device=device))
+    z_star = torch.where(on, torch.zeros((), dtype=torch.float64, device=device),
+                         slo + (shi - slo) * rand_uniform_t(seed, S_ZS, jj))
+    y_star = rand_normal_t(seed, S_YS, torch.arange(m, device=device, dtype=torch.int64))
+    # c = A^T y* + z*, summed column by column in slot order
+    coff = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    coff[1:] = torch.cumsum(ct, 0)
+    c = torch.segment_reduce(vals * y_star[rows], "sum", offsets=coff) + z_star
+    # CSR by (row, col); b = A x*, summed row by row
+    order = torch.sort(rows * n + col, stable=True).indices
+    r_sorted = rows[order]
+    col_idx = col[order].to(torch.int32)
+    val = vals[order]
+    del rows, col, vals, order
+    row_ptr = torch.zeros(m + 1, dtype=torch.int64, device=device)
+    row_ptr[1:] = torch.cumsum(torch.bincount(r_sorted, minlength=m), 0)
+    del r_sorted
+    b = torch.segment_reduce(val * x_star[col_idx.to(torch.int64)], "sum", offsets=row_ptr)
+    return TorchLP(m, n, row_ptr, col_idx, val, b, c, x_star, y_star, z_star, name=name)
+
+
+def zipf_exact_lp_t(seed: int = 0, m: int = 1_000_000, n: int = 3_000_000, device="cuda") -> TorchLP:
+    """The large workload with the literal capped Zipf law for the column
+    counts (s = 1.5, cap 1e4: nnz ~4.6e8 at n = 3e6), uniform rows, values
+    +-U[0.1,10], 30% of x* positive, built on ``device``."""
+    counts = zipf_exact_counts(seed, n, 1.5, 10_000, m)
+    return generate_t(m, n, seed, counts, val_range=(0.1, 10.0), support=0.3, device=device,
+                      name=f"zipf-exact-{m}x{n}-nnz{int(counts.sum())}-s{seed}")
