@@ -533,10 +533,16 @@ struct PrimalOp {
   __device__ __forceinline__ void finish(int j, T g, const State&) {
     const T d = dc.load(j);
     const T xj = __ldcs(x + j);
-    const T xn = project(lo, j, xj - tau * (__ldcs(ch + j) - dc.apply(d, g)));
+    // every load before the first store: the compiler keeps loads after
+    // stores to other arrays (it cannot tell that they do not overlap), so a
+    // load placed after a store waits for it; the order measured 1.5-2.6%
+    // faster
+    const T cj = __ldcs(ch + j);
+    const T sj = accumulate ? __ldcs(xsum + j) : T(0);
+    const T xn = project(lo, j, xj - tau * (cj - dc.apply(d, g)));
     xbar[j] = dc.apply(d, T(2) * xn - xj);  // default policy: gathered by the dual step next
     __stcs(x + j, xn);
-    if (accumulate) __stcs(xsum + j, __ldcs(xsum + j) + xn);
+    if (accumulate) __stcs(xsum + j, sj + xn);
   }
 };
 
@@ -668,10 +674,11 @@ struct PrimalHalpernOp {
   __device__ __forceinline__ void finish(int j, T g, const State&) {
     const T d = dc.load(j);
     const T xj = __ldcs(x + j);
-    const T xt = project(lo, j, xj - tau * (__ldcs(ch + j) - dc.apply(d, g)));
+    const T cj = __ldcs(ch + j), rj = __ldcs(xr + j);
+    const T xt = project(lo, j, xj - tau * (cj - dc.apply(d, g)));
     const T xb = T(2) * xt - xj;
     xbar[j] = dc.apply(d, xb);
-    __stcs(x + j, halpern_mix_r<R1>(xt, xj, xb, __ldcs(xr + j), w, T(1) - w, rho));
+    __stcs(x + j, halpern_mix_r<R1>(xt, xj, xb, rj, w, T(1) - w, rho));
   }
 };
 
@@ -826,10 +833,12 @@ struct DualOp {
   __device__ __forceinline__ State begin(int) { return {}; }
   __device__ __forceinline__ void finish(int i, T h, const State&) {
     const T d = dr.load(i);
-    const T yn = y[i] + sigma * (__ldcs(bh + i) - dr.apply(d, h));
+    const T yi = y[i], bi = __ldcs(bh + i);  // every load before the first store (see PrimalOp)
+    const T si = accumulate ? __ldcs(ysum + i) : T(0);
+    const T yn = yi + sigma * (bi - dr.apply(d, h));
     y[i] = yn;  // default policy: gathered by the primal step next (SC: yg is)
     if (SC) yg[i] = d * yn;
-    if (accumulate) __stcs(ysum + i, __ldcs(ysum + i) + yn);
+    if (accumulate) __stcs(ysum + i, si + yn);
   }
 };
 
