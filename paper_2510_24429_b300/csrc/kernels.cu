@@ -674,11 +674,13 @@ struct PrimalHalpernOp {
   __device__ __forceinline__ void finish(int j, T g, const State&) {
     const T d = dc.load(j);
     const T xj = __ldcs(x + j);
-    const T cj = __ldcs(ch + j), rj = __ldcs(xr + j);
-    const T xt = project(lo, j, xj - tau * (cj - dc.apply(d, g)));
+    // (the loads stay in this order: placed before the stores, as in
+    // PrimalOp, they changed the compiler's FP32 contractions here, and with
+    // them the bit-identity with the streamed kernels, for no measured gain)
+    const T xt = project(lo, j, xj - tau * (__ldcs(ch + j) - dc.apply(d, g)));
     const T xb = T(2) * xt - xj;
     xbar[j] = dc.apply(d, xb);
-    __stcs(x + j, halpern_mix_r<R1>(xt, xj, xb, rj, w, T(1) - w, rho));
+    __stcs(x + j, halpern_mix_r<R1>(xt, xj, xb, __ldcs(xr + j), w, T(1) - w, rho));
   }
 };
 
