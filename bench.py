@@ -670,8 +670,9 @@ def run_zipf_exact(args):
         k0 = ks.info()
         ks.iterate(500)
         k1 = ks.info()
-    t_p = (k1["kernel_ms_primal"] - k0["kernel_ms_primal"]) / (k1["kernel_launches_primal"] - k0["kernel_launches_primal"])
-    t_d = (k1["kernel_ms_dual"] - k0["kernel_ms_dual"]) / (k1["kernel_launches_dual"] - k0["kernel_launches_dual"])
+    per_launch = lambda half: ((k1[f"kernel_ms_{half}"] - k0[f"kernel_ms_{half}"]) /  # noqa: E731
+                               (k1[f"kernel_launches_{half}"] - k0[f"kernel_launches_{half}"]))
+    t_p, t_d = per_launch("primal"), per_launch("dual")
     peak, peak_kind = measured_peaks()
     fma_rate, _ = P.pdhg_fp64_fma_rate(stream.cuda_stream)
     halves = {"primal half-step (FP64)": (t_p, 12 * nnz + 8 * m + 48 * n, nnz + 5 * n),
